@@ -1,0 +1,298 @@
+"""Seeded synthetic instances of the dynamic multi-commodity min-cost flow problem.
+
+This module only builds input data (graphs, costs, capacities, marginals).  It holds
+none of the method's arithmetic: both the CUDA solver and the FP64 oracle consume the
+``Instance`` objects built here.
+
+Conventions (shared by every consumer, restated in ``include/ots.h``):
+
+* The road network is a directed graph with ``n_nodes`` nodes and ``n_edges`` directed
+  edges ``edge_src[e] -> edge_dst[e]``.
+* A *state* is a directed edge (the edge-state model of Section 3.1, marginals on edges).
+  Waiting is modelled by one self-loop state per node (the vertex augmentation of
+  Section 3.3): states ``0..n_edges-1`` are the edges, state ``n_edges + v`` is the wait
+  loop of node ``v``.  ``n_states = n_edges + n_nodes``.
+* Costs are per state and per time interval (``C_L`` of Section 3.2, identical rows for
+  every commodity unless ``commodity_cost`` is given), capacities are per state
+  (``d`` of Section 3.2, ``inf`` = uncapacitated).
+* Sources / sinks are ``(commodity, state, mass)`` triples: the non-zeros of
+  ``R^(0,1)`` and ``R^(0,T)`` of Section 3.2.  All sources and sinks sit on wait-loop
+  states of nodes.
+
+Workload recipes follow the five configurations of the benchmark (see ``CONFIGS``).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+
+@dataclass
+class Instance:
+    name: str
+    n_nodes: int
+    edge_src: np.ndarray          # int32 [E]
+    edge_dst: np.ndarray          # int32 [E]
+    edge_cost: np.ndarray         # float64 [E], cost per interval on the edge
+    edge_cap: np.ndarray          # float64 [E], inf = none
+    wait_cost: np.ndarray         # float64 [V], cost per interval on the node's wait loop
+    wait_cap: np.ndarray          # float64 [V], inf = none
+    L: int
+    T: int
+    eps: float
+    src_comm: np.ndarray          # int32 [n_src]
+    src_state: np.ndarray         # int32 [n_src]
+    src_mass: np.ndarray          # float64 [n_src]
+    snk_comm: np.ndarray          # int32 [n_snk]
+    snk_state: np.ndarray         # int32 [n_snk]
+    snk_mass: np.ndarray          # float64 [n_snk]
+    pos: Optional[np.ndarray] = None              # [V, 2] node positions (not used by solvers)
+    commodity_cost: Optional[np.ndarray] = None   # [L, S] per-commodity state costs
+    meta: dict = field(default_factory=dict)
+
+    # ---- derived sizes / per-state views (data assembly only) ----
+    @property
+    def n_edges(self) -> int:
+        return int(self.edge_src.shape[0])
+
+    @property
+    def n_states(self) -> int:
+        return self.n_edges + self.n_nodes
+
+    def state_cost(self) -> np.ndarray:
+        """Per-state cost vector [S]: edge costs then wait-loop costs."""
+        return np.concatenate([self.edge_cost, self.wait_cost]).astype(np.float64)
+
+    def state_cap(self) -> np.ndarray:
+        """Per-state capacity vector [S]: edge capacities then wait-loop capacities."""
+        return np.concatenate([self.edge_cap, self.wait_cap]).astype(np.float64)
+
+    def state_tail_head(self):
+        """(tail, head) node of every state; a wait loop has tail == head."""
+        loops = np.arange(self.n_nodes, dtype=np.int32)
+        tail = np.concatenate([self.edge_src, loops]).astype(np.int32)
+        head = np.concatenate([self.edge_dst, loops]).astype(np.int32)
+        return tail, head
+
+    def total_mass(self) -> float:
+        return float(np.sum(self.src_mass))
+
+    def n_updates_per_iteration(self) -> int:
+        """Work units of one Sinkhorn sweep: 2 (T-1) nnz(K) L.
+
+        nnz(K) counts the transitions of the line graph with wait loops, i.e. the
+        ordered state pairs (i, j) with head(i) == tail(j).
+        """
+        tail, head = self.state_tail_head()
+        indeg = np.bincount(head, minlength=self.n_nodes).astype(np.int64)
+        outdeg = np.bincount(tail, minlength=self.n_nodes).astype(np.int64)
+        nnz = int(np.sum(indeg * outdeg))
+        return 2 * (self.T - 1) * nnz * self.L
+
+    def nnz_line_graph(self) -> int:
+        tail, head = self.state_tail_head()
+        indeg = np.bincount(head, minlength=self.n_nodes).astype(np.int64)
+        outdeg = np.bincount(tail, minlength=self.n_nodes).astype(np.int64)
+        return int(np.sum(indeg * outdeg))
+
+
+# ----------------------------------------------------------------------------------
+# graph builders
+# ----------------------------------------------------------------------------------
+
+def grid_graph(rows: int, cols: int):
+    """4-neighbour grid, both directions.  Node id = r * cols + c."""
+    src, dst = [], []
+    for r in range(rows):
+        for c in range(cols):
+            v = r * cols + c
+            for dr, dc in ((0, 1), (1, 0), (0, -1), (-1, 0)):
+                rr, cc = r + dr, c + dc
+                if 0 <= rr < rows and 0 <= cc < cols:
+                    src.append(v)
+                    dst.append(rr * cols + cc)
+    pos = np.stack(np.meshgrid(np.arange(cols, dtype=np.float64),
+                               np.arange(rows, dtype=np.float64)), -1).reshape(-1, 2)
+    return np.asarray(src, np.int32), np.asarray(dst, np.int32), pos
+
+
+def _connected(n: int, src: np.ndarray, dst: np.ndarray) -> bool:
+    return bool(np.all(hop_distances(n, src, dst, 0) >= 0))
+
+
+def rgg_graph(n: int, mean_degree: float, rng: np.random.Generator, max_tries: int = 200):
+    """Random geometric graph in the unit square.
+
+    The radius is calibrated per draw so that the mean degree is exactly ``mean_degree``
+    (the ``n * mean_degree / 2`` shortest pairs become undirected edges); draws that are
+    not connected are rejected.  Nodes are renumbered along a coarse spatial sort so that
+    neighbouring nodes have nearby ids.
+    """
+    n_und = int(round(n * mean_degree / 2))
+    for _ in range(max_tries):
+        pos = rng.random((n, 2))
+        d = np.sqrt(((pos[:, None, :] - pos[None, :, :]) ** 2).sum(-1))
+        iu, ju = np.triu_indices(n, 1)
+        dist = d[iu, ju]
+        order = np.argsort(dist, kind="stable")[:n_und]
+        a, b = iu[order], ju[order]
+        src = np.concatenate([a, b]).astype(np.int32)
+        dst = np.concatenate([b, a]).astype(np.int32)
+        if _connected(n, src, dst):
+            # spatial renumbering: strips of width ~ radius, snake order inside
+            r = float(dist[order[-1]])
+            nstrip = max(1, int(1.0 / max(r, 1e-3)))
+            strip = np.minimum((pos[:, 1] * nstrip).astype(np.int64), nstrip - 1)
+            key = np.where(strip % 2 == 0, pos[:, 0], -pos[:, 0])
+            perm = np.lexsort((key, strip))          # new order -> old id
+            inv = np.empty(n, np.int64)
+            inv[perm] = np.arange(n)
+            src2, dst2 = inv[src].astype(np.int32), inv[dst].astype(np.int32)
+            eorder = np.lexsort((dst2, src2))
+            length = np.sqrt(((pos[src] - pos[dst]) ** 2).sum(-1))
+            return src2[eorder], dst2[eorder], pos[perm], length[eorder], r
+    raise RuntimeError("could not draw a connected random geometric graph")
+
+
+def hop_distances(n: int, src: np.ndarray, dst: np.ndarray, s: int) -> np.ndarray:
+    """BFS hop distance from node s (-1 = unreachable)."""
+    order = np.argsort(src, kind="stable")
+    ptr = np.zeros(n + 1, np.int64)
+    np.add.at(ptr, src.astype(np.int64) + 1, 1)
+    ptr = np.cumsum(ptr)
+    nbr = dst[order]
+    dist = np.full(n, -1, np.int64)
+    dist[s] = 0
+    frontier = [s]
+    while frontier:
+        nxt = []
+        for v in frontier:
+            for w in nbr[ptr[v]:ptr[v + 1]]:
+                if dist[w] < 0:
+                    dist[w] = dist[v] + 1
+                    nxt.append(int(w))
+        frontier = nxt
+    return dist
+
+
+def _od_pairs(n: int, src, dst, L: int, max_hops: int, rng, grid_cols: Optional[int] = None):
+    """L origin-destination node pairs, uniform over pairs with 1 <= hops <= max_hops."""
+    out = []
+    cache = {}
+    while len(out) < L:
+        s = int(rng.integers(n))
+        z = int(rng.integers(n))
+        if s == z:
+            continue
+        if grid_cols is not None:
+            hops = abs(s // grid_cols - z // grid_cols) + abs(s % grid_cols - z % grid_cols)
+        else:
+            if s not in cache:
+                cache[s] = hop_distances(n, src, dst, s)
+            hops = int(cache[s][z])
+        if 1 <= hops <= max_hops:
+            out.append((s, z))
+    return out
+
+
+def _single_pair_instance(name, n, src, dst, edge_cost, edge_cap, wait_cost, L, T, eps,
+                          pairs, masses, pos=None, meta=None):
+    E = src.shape[0]
+    comm = np.arange(L, dtype=np.int32)
+    s_state = np.asarray([E + s for s, _ in pairs], np.int32)
+    z_state = np.asarray([E + z for _, z in pairs], np.int32)
+    return Instance(
+        name=name, n_nodes=n, edge_src=src, edge_dst=dst,
+        edge_cost=np.asarray(edge_cost, np.float64), edge_cap=np.asarray(edge_cap, np.float64),
+        wait_cost=np.full(n, wait_cost, np.float64), wait_cap=np.full(n, np.inf),
+        L=L, T=T, eps=eps,
+        src_comm=comm.copy(), src_state=s_state, src_mass=np.asarray(masses, np.float64),
+        snk_comm=comm.copy(), snk_state=z_state, snk_mass=np.asarray(masses, np.float64).copy(),
+        pos=pos, meta=dict(meta or {}))
+
+
+# ----------------------------------------------------------------------------------
+# workload recipes
+# ----------------------------------------------------------------------------------
+
+def config1(seed: int = 0, rows: int = 5, cols: int = 5, T: int = 10, eps: float = 0.05,
+            move_cost: float = 1.0, wait_cost: float = 0.1, n_src: int = 3, n_snk: int = 3):
+    """Single commodity on a grid: Dirichlet(1) sources and sinks over 3 nodes each."""
+    rng = np.random.default_rng(seed)
+    src, dst, pos = grid_graph(rows, cols)
+    n, E = rows * cols, src.shape[0]
+    s_nodes = rng.choice(n, n_src, replace=False)
+    z_nodes = rng.choice(n, n_snk, replace=False)
+    s_mass = rng.dirichlet(np.ones(n_src))
+    z_mass = rng.dirichlet(np.ones(n_snk))
+    return Instance(
+        name=f"grid{rows}x{cols}-L1-T{T}", n_nodes=n, edge_src=src, edge_dst=dst,
+        edge_cost=np.full(E, move_cost), edge_cap=np.full(E, np.inf),
+        wait_cost=np.full(n, wait_cost), wait_cap=np.full(n, np.inf),
+        L=1, T=T, eps=eps,
+        src_comm=np.zeros(n_src, np.int32), src_state=(E + s_nodes).astype(np.int32),
+        src_mass=s_mass.astype(np.float64),
+        snk_comm=np.zeros(n_snk, np.int32), snk_state=(E + z_nodes).astype(np.int32),
+        snk_mass=z_mass.astype(np.float64),
+        pos=pos, meta={"config": 1, "seed": seed})
+
+
+def rgg_instance(seed: int = 0, n: int = 400, L: int = 64, T: int = 50, eps: float = 0.01,
+                 mean_degree: float = 6.0, wait_cost: float = 0.05, cap_lo: float = 0.2,
+                 cap_hi: float = 1.0, cap_div: float = 8.0, name: Optional[str] = None):
+    """Random geometric graph, Euclidean edge costs, single-node OD pairs per commodity."""
+    rng = np.random.default_rng(seed)
+    src, dst, pos, length, r = rgg_graph(n, mean_degree, rng)
+    pairs = _od_pairs(n, src, dst, L, T - 2, rng)
+    mass = rng.uniform(0.5, 2.0, L)
+    cap = rng.uniform(cap_lo, cap_hi, src.shape[0]) * mass.sum() / cap_div
+    return _single_pair_instance(name or f"rgg{n}-L{L}-T{T}", n, src, dst, length, cap,
+                                 wait_cost, L, T, eps, pairs, mass, pos,
+                                 {"config": 2, "seed": seed, "radius": r})
+
+
+def config2(seed: int = 0):
+    """Multi-commodity with capacities on a random geometric graph (n=400, L=64, T=50)."""
+    return rgg_instance(seed=seed, n=400, L=64, T=50, eps=0.01)
+
+
+def grid_traffic_instance(seed: int = 0, rows: int = 100, cols: int = 100, L: int = 1024,
+                          T: int = 100, eps: float = 0.005, wait_cost: float = 0.2,
+                          cap_lo: float = 0.5, cap_hi: float = 3.0, name: Optional[str] = None):
+    """Perturbed grid road graph, Lognormal(0, 0.3) travel costs, uniform OD pairs."""
+    rng = np.random.default_rng(seed)
+    src, dst, pos = grid_graph(rows, cols)
+    pos = pos + rng.uniform(-0.1, 0.1, pos.shape)
+    E = src.shape[0]
+    cost = rng.lognormal(0.0, 0.3, E)
+    cap = rng.uniform(cap_lo, cap_hi, E)
+    pairs = _od_pairs(rows * cols, src, dst, L, T - 2, rng, grid_cols=cols)
+    mass = rng.uniform(0.1, 1.0, L)
+    return _single_pair_instance(name or f"grid{rows}x{cols}-L{L}-T{T}", rows * cols, src, dst,
+                                 cost, cap, wait_cost, L, T, eps, pairs, mass, pos,
+                                 {"config": 3, "seed": seed})
+
+
+def config3(seed: int = 0):
+    """Traffic-scale: 100x100 grid, L=1024 OD commodities, T=100, eps=0.005."""
+    return grid_traffic_instance(seed=seed)
+
+
+def config4(seed: int = 0, count: int = 256):
+    """Batch of uneven instances: n~U{50..2000} RGG, T~U{10..80}, L~U{1..128}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(rng.integers(50, 2001))
+        T = int(rng.integers(10, 81))
+        L = int(rng.integers(1, 129))
+        sub = int(rng.integers(2**31 - 1))
+        inst = rgg_instance(seed=sub, n=n, L=L, T=T, eps=0.01, name=f"b{k}-rgg{n}-L{L}-T{T}")
+        inst.meta.update({"config": 4, "batch_index": k})
+        out.append(inst)
+    return out
+
+
+CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4}

@@ -1,0 +1,258 @@
+"""Independent mathematics used to pin the oracle (no code shared with the oracle).
+
+Everything here is written from the definitions in the paper, in FP64 linear domain, on
+tiny instances only:
+
+* the transport tensor M = K .* U over all L * S^T paths and its projections by direct
+  summation (eq. proj_discrete, eq. proj_discrete_bi, eq. K_multicommodity, eq. U_multicommodity);
+* the generic Sinkhorn scheme of Proposition 5 run on that full tensor;
+* the Markov bridge for one source and one sink (Remark in Section 4.2);
+* the reduction of an uncapacitated single-commodity problem to a two-marginal OT problem
+  with the dense kernel K_eff = K (diag(k) K)^(T-2), solved by textbook Sinkhorn;
+* the exact LP of problem eq. multicommodity (Theorem 2) via scipy's HiGHS.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+
+def tail_head(inst):
+    V = inst.n_nodes
+    tail = np.concatenate([np.asarray(inst.edge_src), np.arange(V)])
+    head = np.concatenate([np.asarray(inst.edge_dst), np.arange(V)])
+    return tail, head
+
+
+def dense_K(inst) -> np.ndarray:
+    """K_ij = 1 if edge i leads to edge j (second vertex of i is the first vertex of j)."""
+    tail, head = tail_head(inst)
+    return (head[:, None] == tail[None, :]).astype(np.float64)
+
+
+def dense_marginals(inst):
+    S = inst.n_edges + inst.n_nodes
+    R01 = np.zeros((inst.L, S))
+    R0T = np.zeros((inst.L, S))
+    for c, s, m in zip(inst.src_comm, inst.src_state, inst.src_mass):
+        R01[c, s] += m
+    for c, s, m in zip(inst.snk_comm, inst.snk_state, inst.snk_mass):
+        R0T[c, s] += m
+    return R01, R0T
+
+
+def cost_matrix(inst) -> np.ndarray:
+    """C_L as an L x S matrix."""
+    if getattr(inst, "commodity_cost", None) is not None:
+        return np.asarray(inst.commodity_cost, np.float64)
+    c = np.concatenate([inst.edge_cost, inst.wait_cost]).astype(np.float64)
+    return np.tile(c, (inst.L, 1))
+
+
+def capacity(inst) -> np.ndarray:
+    return np.concatenate([inst.edge_cap, inst.wait_cap]).astype(np.float64)
+
+
+def all_paths(S: int, T: int) -> np.ndarray:
+    return np.array(list(itertools.product(range(S), repeat=T)), dtype=np.int64)
+
+
+class Tensor:
+    """The full tensor of eq. K_multicommodity for a tiny instance (L x S^T entries)."""
+
+    def __init__(self, inst):
+        self.inst = inst
+        self.L, self.T, self.S = inst.L, inst.T, inst.n_edges + inst.n_nodes
+        self.paths = all_paths(self.S, self.T)                     # [N, T]
+        K = dense_K(inst)
+        KL = np.exp(-cost_matrix(inst) / inst.eps)                  # [L, S]
+        p = self.paths
+        kpath = np.ones(len(p))
+        for t in range(self.T - 1):                                 # prod_{t=1}^{T-1} K_{i_t i_{t+1}}
+            kpath *= K[p[:, t], p[:, t + 1]]
+        keep = kpath > 0                                            # drop infeasible paths
+        self.paths = p[keep]
+        self.kpath = kpath[keep]
+        # prod_{t=2}^{T-1} (K_L)_{i_0 i_t}
+        self.kl = np.ones((self.L, len(self.paths)))
+        for t in range(1, self.T - 1):
+            self.kl *= KL[:, self.paths[:, t]]
+
+    def M(self, u, U01, U0T):
+        """K .* U (eq. U_multicommodity); u is [T+1, S] with rows 2..T-1 used."""
+        p = self.paths
+        w = self.kl * self.kpath[None, :] * U01[:, p[:, 0]] * U0T[:, p[:, -1]]
+        for t in range(1, self.T - 1):
+            w = w * u[t + 1][p[:, t]][None, :]
+        return w
+
+    def proj0t(self, M, t):
+        """P_{0,t}(M), 1-based t (eq. proj_discrete_bi with the commodity mode)."""
+        out = np.zeros((self.L, self.S))
+        for l in range(self.L):
+            out[l] = np.bincount(self.paths[:, t - 1], weights=M[l], minlength=self.S)
+        return out
+
+    def proj_tt(self, M, t):
+        """P_{t,t+1}(M) summed over commodities, [S, S]."""
+        out = np.zeros((self.S, self.S))
+        np.add.at(out, (self.paths[:, t - 1], self.paths[:, t]), M.sum(0))
+        return out
+
+
+def tensor_sinkhorn(inst, iters=20000, tol=1e-13, reverse=True):
+    """Proposition 5 on the full tensor: U01, then u_t (reverse order by default), then U0T."""
+    tz = Tensor(inst)
+    L, S, T = tz.L, tz.S, tz.T
+    R01, R0T = dense_marginals(inst)
+    d = capacity(inst)
+    u = np.ones((T + 1, S))
+    U01 = (R01 > 0).astype(float)
+    U0T = (R0T > 0).astype(float)
+    order = list(range(T - 1, 1, -1)) if reverse else list(range(2, T))
+    for k in range(iters):
+        M = tz.M(u, U01, U0T)
+        P1 = tz.proj0t(M, 1)
+        err = np.abs(P1 - R01).sum() / R01.sum()
+        U01 = np.where(R01 > 0, U01 * R01 / np.where(P1 > 0, P1, 1), 0.0)
+        for t in order:
+            M = tz.M(u, U01, U0T)
+            Pt = tz.proj0t(M, t).sum(0)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                upd = np.where(Pt > 0, u[t] * d / Pt, 1.0)
+            u[t] = np.minimum(upd, 1.0)
+        M = tz.M(u, U01, U0T)
+        PT = tz.proj0t(M, T)
+        U0T = np.where(R0T > 0, U0T * R0T / np.where(PT > 0, PT, 1), 0.0)
+        M = tz.M(u, U01, U0T)
+        excess = sum(np.maximum(tz.proj0t(M, t).sum(0) - d, 0).sum() for t in range(2, T))
+        if err < tol and excess / R01.sum() < tol:
+            break
+    M = tz.M(u, U01, U0T)
+    return tz, M, (u, U01, U0T)
+
+
+def bridge_flows(inst, l=0):
+    """Single source s, single sink z, no capacities: P_{0,t} by dense linear products.
+
+    F_1 = e_s, F_t = (F_{t-1} .* k_{t-1}) K;  G_T = e_z, G_t = K (k_{t+1} .* G_{t+1});
+    k_t = (K_L)_l for t = 2..T-1 and 1 at t = 1, T;  P_{0,t} = mass F_t .* k_t .* G_t / F_T[z].
+    """
+    K = dense_K(inst)
+    S, T = K.shape[0], inst.T
+    kl = np.exp(-cost_matrix(inst)[l] / inst.eps)
+    s = int(inst.src_state[list(inst.src_comm).index(l)])
+    z = int(inst.snk_state[list(inst.snk_comm).index(l)])
+    mass = float(inst.src_mass[list(inst.src_comm).index(l)])
+    k = [None] + [np.ones(S)] + [kl] * (T - 2) + [np.ones(S)]   # 1-based k[t]
+    F = [None] * (T + 1)
+    G = [None] * (T + 1)
+    F[1] = np.eye(S)[s]
+    for t in range(2, T + 1):
+        F[t] = (F[t - 1] * k[t - 1]) @ K
+    G[T] = np.eye(S)[z]
+    for t in range(T - 1, 0, -1):
+        G[t] = K @ (k[t + 1] * G[t + 1])
+    Z = F[T][z]
+    return np.array([mass * F[t] * k[t] * G[t] / Z for t in range(1, T + 1)])
+
+
+def two_marginal_flows(inst, iters=200000, tol=1e-14):
+    """Uncapacitated single commodity: the coupling of (t=1, t=T) is two-marginal entropic OT
+    with K_eff = K diag(k) K ... diag(k) K  (T-1 factors K); textbook Sinkhorn a <- mu1 ./ (K_eff b),
+    b <- muT ./ (K_eff^T a); then P_t = (a^T K D..K)_s k_t (K D..K b)_s."""
+    K = dense_K(inst)
+    S, T = K.shape[0], inst.T
+    kl = np.exp(-cost_matrix(inst)[0] / inst.eps)
+    D = np.diag(kl)
+    R01, R0T = dense_marginals(inst)
+    mu1, muT = R01[0], R0T[0]
+    Keff = K.copy()
+    for _ in range(T - 2):
+        Keff = Keff @ D @ K
+    sup1, supT = mu1 > 0, muT > 0
+    A = Keff[np.ix_(sup1, supT)]
+    a = np.ones(sup1.sum())
+    b = np.ones(supT.sum())
+    for _ in range(iters):
+        a = mu1[sup1] / (A @ b)
+        b_new = muT[supT] / (A.T @ a)
+        if np.max(np.abs(b_new - b) / b) < tol:
+            b = b_new
+            break
+        b = b_new
+    af = np.zeros(S); af[sup1] = a
+    bf = np.zeros(S); bf[supT] = b
+    fw = [None] * (T + 1)
+    bw = [None] * (T + 1)
+    fw[1] = af
+    for t in range(2, T + 1):
+        fw[t] = (fw[t - 1] * (kl if t - 1 >= 2 else 1.0)) @ K
+    bw[T] = bf
+    for t in range(T - 1, 0, -1):
+        bw[t] = K @ ((kl if t + 1 <= T - 1 else 1.0) * bw[t + 1])
+    out = []
+    for t in range(1, T + 1):
+        kt = kl if 2 <= t <= T - 1 else 1.0
+        out.append(fw[t] * kt * bw[t])
+    return np.array(out)
+
+
+def lp_optimum(inst):
+    """Exact LP of eq. multicommodity in node-edge form on the time-expanded state graph.
+
+    Variables y[l, t, (i,j)] >= 0: flow of commodity l moving from state i at interval t to
+    state j at interval t+1 (t = 1..T-1, K_ij = 1).  Constraints: out-flow at t = 1 equals
+    R01, in-flow at t = T equals R0T, conservation at t = 2..T-1, and
+    sum_l (flow in state j at t) <= d_j for t = 2..T-1.  Cost: sum_{t=2}^{T-1} C_L[l, j] x flow.
+    Returns the optimal value."""
+    import scipy.sparse as sp
+    from scipy.optimize import linprog
+
+    K = dense_K(inst)
+    I, J = np.nonzero(K)
+    nnz = len(I)
+    L, T, S = inst.L, inst.T, K.shape[0]
+    R01, R0T = dense_marginals(inst)
+    C = cost_matrix(inst)
+    d = capacity(inst)
+    nvar = L * (T - 1) * nnz
+    var = lambda l, t: (l * (T - 1) + (t - 1)) * nnz   # t = 1..T-1
+    rows, cols, vals, beq = [], [], [], []
+    r = 0
+    for l in range(L):
+        for i in range(S):                                   # t = 1 out-flow = R01
+            m = I == i
+            rows += [r] * m.sum(); cols += list(var(l, 1) + np.nonzero(m)[0]); vals += [1.0] * m.sum()
+            beq.append(R01[l, i]); r += 1
+        for j in range(S):                                   # t = T in-flow = R0T
+            m = J == j
+            rows += [r] * m.sum(); cols += list(var(l, T - 1) + np.nonzero(m)[0]); vals += [1.0] * m.sum()
+            beq.append(R0T[l, j]); r += 1
+        for t in range(2, T):                                # conservation in state s at interval t
+            for s in range(S):
+                mi, mo = J == s, I == s
+                rows += [r] * (mi.sum() + mo.sum())
+                cols += list(var(l, t - 1) + np.nonzero(mi)[0]) + list(var(l, t) + np.nonzero(mo)[0])
+                vals += [1.0] * mi.sum() + [-1.0] * mo.sum()
+                beq.append(0.0); r += 1
+    Aeq = sp.csr_matrix((vals, (rows, cols)), shape=(r, nvar))
+    rows, cols, vals, bub = [], [], [], []
+    r = 0
+    for t in range(2, T):
+        for s in range(S):
+            if not np.isfinite(d[s]):
+                continue
+            mo = np.nonzero(I == s)[0]
+            for l in range(L):
+                rows += [r] * len(mo); cols += list(var(l, t) + mo); vals += [1.0] * len(mo)
+            bub.append(d[s]); r += 1
+    Aub = sp.csr_matrix((vals, (rows, cols)), shape=(r, nvar)) if r else None
+    c = np.zeros(nvar)
+    for l in range(L):
+        for t in range(2, T):
+            c[var(l, t):var(l, t) + nnz] = C[l, I]
+    res = linprog(c, A_ub=Aub, b_ub=bub if r else None, A_eq=Aeq, b_eq=beq, bounds=(0, None), method="highs")
+    assert res.status == 0, res.message
+    return float(res.fun)
