@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of the Sinkhorn iterations of Algorithm 2 on one GB300 per rank.
+
+A step is one full solve of the traffic-scale workload (perturbed 100x100 grid road graph,
+L = 1024 origin-destination commodities, T = 100, eps = 0.005) from the initial duals until
+the relative source mismatch and the relative capacity excess are both <= 1e-6.
+
+  value   edge*commodity*timestep updates per second, whole job: 2 (T-1) nnz(K) L updates per
+          Sinkhorn pass (nnz(K) = transitions of the line graph with wait loops), summed over
+          ranks, divided by the slowest rank's device time (CUDA events on the solver stream)
+  e2e     the same metric through the C ABI from host buffers: create (host -> device copy
+          of the problem), solve, read the flows back (device -> host), destroy
+  roofline  the forward-step kernel (the dominant kernel): algorithmic bytes per launch over
+          its mean duration inside the timed passes, against the measured HBM copy bandwidth
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same instance
+
+--impl reference times the oracle itself (the CPU reference of this build) on the same
+workload and metric.  With torchrun (N > 1) every rank solves its own replica (seed = rank):
+independent problems, no collective on the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edge*commodity*timestep updates/s (full Sinkhorn solves to marginal err <= 1e-6)"
+UNIT = "updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(seed: int):
+    from paper_2106_14485_gb300 import instances
+    return instances.config3(seed)
+
+
+def workload_config(inst, tol):
+    return {"workload": f"traffic-scale grid 100x100 road graph, L={inst.L} OD commodities, T={inst.T}, "
+                        f"eps={inst.eps}, capacities U[0.5,3], solve to marginal err <= {tol:g}",
+            "nodes": inst.n_nodes, "states": inst.n_states, "nnz_K": inst.nnz_line_graph(),
+            "L": inst.L, "T": inst.T, "eps": inst.eps, "tol": tol,
+            "cache": "inputs larger than L2: message panels of several GB per problem",
+            "parallelism": "independent replicas per GPU"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def forward_bytes_per_launch(info, inst):
+    """Algorithmic bytes of one forward-step launch: read A_{t-1} and B_{t+1}, write A_t
+    (6 bytes per entry: fp32 hi + fp16 lo) for V x L node rows, plus the per-state vectors
+    (cost, capacity, old/new duals, weights, CSR: 56 bytes per state) and the node CSR."""
+    V, S, L = info["n_nodes"], info["n_states"], inst.L
+    return 18 * V * L + 56 * S + 4 * (V + 1)
+
+
+def backward_bytes_per_launch(info, inst):
+    V, S, L = info["n_nodes"], info["n_states"], inst.L
+    return 12 * V * L + 16 * S + 4 * (V + 1)
+
+
+def cpu_baseline(inst, budget_s: float):
+    """The oracle as it stands, on a bounded sample of the same instance: backward message
+    products (Algorithm 2, Psi_{t-1} = (Psi_t .* K_L) diag(u_t) K^T) over the first l1
+    commodities, repeated until the time budget is used."""
+    from oracle.oracle import Oracle, get_threads
+    o = Oracle(inst)
+    nnz = o.nnz
+    l1 = 16
+    t0 = time.perf_counter()
+    o.sample_backward_products(1, l1)
+    one = max(time.perf_counter() - t0, 1e-3)
+    k = max(1, int(budget_s / one))
+    t0 = time.perf_counter()
+    o.sample_backward_products(k, l1)
+    dt = time.perf_counter() - t0
+    updates = (k + 1) * nnz * l1            # k products after one boundary product, each nnz * l1 terms
+    return {"value": updates / dt, "unit": UNIT, "cores": get_threads(), "kind": "oracle",
+            "sample": f"{k} backward message products of the traffic-scale instance on commodities "
+                      f"0..{l1 - 1} ({updates:.3e} updates, {dt:.1f} s, FP64 log domain)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    inst = workload(0)
+    from oracle.oracle import Oracle, get_threads
+    o = Oracle(inst)
+    nnz = o.nnz
+    l1 = 16
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    t0 = time.perf_counter()
+    o.sample_backward_products(1, l1)
+    one = max(time.perf_counter() - t0, 1e-3)
+    k = max(1, int(per_step / one))
+    for _ in range(args.warmup):
+        o.sample_backward_products(k, l1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.sample_backward_products(k, l1)
+    dt = time.perf_counter() - t0
+    updates = args.steps * (k + 1) * nnz * l1
+    value = updates / dt
+    sample = (f"each step: {k} backward message products of the traffic-scale instance on commodities "
+              f"0..{l1 - 1} (FP64 log domain, {get_threads()} threads)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(inst, args.tol), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": get_threads(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    from paper_2106_14485_gb300 import build, ots
+    build.build()
+    ots.load_library()
+
+    inst = workload(rank)
+    upd_per_pass = inst.n_updates_per_iteration()
+    h = ots.ots_create_problem(inst, device=local)
+    info = ots.ots_problem_info(h)
+    stream = torch.cuda.ExternalStream(ots.ots_problem_stream(h), device=local)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        r = ots.ots_sinkhorn_solve(h, tol=args.tol)
+    barrier()
+    launches0 = ots.ots_problem_info(h)["kernels_launched"]
+    passes = 0
+    fwd_ms, bwd_ms = [], []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = ots.ots_sinkhorn_solve(h, tol=args.tol)
+            passes += r["iterations"]
+            tm = ots.ots_last_pass_timing(h)
+            fwd_ms.append(tm["forward_ms"] / (inst.T - 2))
+            bwd_ms.append(tm["backward_ms"] / (inst.T - 2))
+        ev1.record(stream)
+        ev1.synchronize()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = ots.ots_problem_info(h)["kernels_launched"] - launches0
+    final = r
+    barrier()
+
+    updates = passes * upd_per_pass
+    if pg is not None:
+        t = torch.tensor([elapsed_ms, float(updates), float(args.steps)], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        pg.all_reduce(mx[:1], op=pg.ReduceOp.MAX)
+        pg.all_reduce(t[1:], op=pg.ReduceOp.SUM)
+        elapsed_ms, updates_all, solves_all = float(mx[0]), float(t[1]), float(t[2])
+    else:
+        updates_all, solves_all = float(updates), float(args.steps)
+    value = updates_all / (elapsed_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        h_e = None
+        t_e = 0.0
+        upd_e = 0
+        h2d = d2h = 0
+        ots.ots_destroy_problem(h)
+        for k in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h_e = ots.ots_create_problem(inst, device=local)
+            re = ots.ots_sinkhorn_solve(h_e, tol=args.tol)
+            F = ots.ots_get_flows(h_e)
+            st = ots.ots_problem_info(h_e)
+            ots.ots_destroy_problem(h_e)
+            t_e += time.perf_counter() - t0
+            upd_e += re["iterations"] * upd_per_pass
+            h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
+        assert F.shape[0] == inst.T
+        e2e_val = upd_e / t_e
+        if pg is not None:
+            t = torch.tensor([t_e, float(upd_e)], dtype=torch.float64, device="cuda")
+            mx = t.clone()
+            pg.all_reduce(mx[:1], op=pg.ReduceOp.MAX)
+            pg.all_reduce(t[1:], op=pg.ReduceOp.SUM)
+            e2e_val = float(t[1]) / float(mx[0])
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "seconds_per_step": t_e / args.steps}
+
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return 0
+
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    fwd_launch_ms = float(np.mean(fwd_ms))
+    fb = forward_bytes_per_launch(info, inst)
+    achieved = fb / (fwd_launch_ms * 1e-3) / 1e9
+    bb = backward_bytes_per_launch(info, inst)
+    bwd_launch_ms = float(np.mean(bwd_ms))
+    roof = {"kernel": "k_forward (fused capacity update + node-level LSE message step)",
+            "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "peak_source": peak_src, "traffic": None, "bytes_per_launch": fb, "launch_ms": fwd_launch_ms,
+            "backward": {"kernel": "k_backward", "achieved": bb / (bwd_launch_ms * 1e-3) / 1e9,
+                         "frac": bb / (bwd_launch_ms * 1e-3) / 1e9 / hbm, "bytes_per_launch": bb,
+                         "launch_ms": bwd_launch_ms}}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(inst, args.cpu_seconds)
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 float-float (fp32 hi + fp16 lo log2 messages), f64 reductions",
+            "data": "synthetic", "config": workload_config(inst, args.tol),
+            "solves_per_s": solves_all / (elapsed_ms / 1e3),
+            "passes_per_solve": passes / args.steps, "final_src_residual": final["src_residual"],
+            "final_cap_violation": final["cap_violation"],
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

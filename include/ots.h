@@ -1,0 +1,209 @@
+/*
+ * ots.h -- C ABI of the GB300 solver for entropy-regularised dynamic multi-commodity
+ * minimum-cost flow by graph-structured multi-marginal optimal transport
+ * (Haasler, Ringh, Chen, Karlsson, arXiv 2106.14485).
+ *
+ * The library solves problem eq. multicommodity_reg (Section 4.3): minimise
+ *     <C, M> + eps D(M)  over M >= 0 (L x n^T),
+ *     P_{0,1}(M) = R01,  P_{0,T}(M) = R0T,  P_t(M) <= d  (t = 2..T-1),
+ * with the Sinkhorn iterations of Algorithm 2, all on one CUDA device.
+ *
+ * State model.  A state is a directed edge of the road network (Section 3.1: marginals
+ * live on edges, n = |E|).  With add_wait_loops = 1 the library adds one self-loop state
+ * per node (storage in the vertices, Section 3.3), so
+ *     state e in [0, n_edges)          is edge e (edge_src[e] -> edge_dst[e]),
+ *     state n_edges + v                 is the wait loop of node v.
+ * The transition kernel is the line graph: state i may be followed by state j iff the
+ * head of i is the tail of j (Section 3.1, C_ij = 0 or infinity).  Costs are per state
+ * and per time interval (the matrix C_L of Section 3.2, eq. cost_multicommodity) and
+ * apply at t = 2..T-1; capacities d are per state and bind at t = 2..T-1.
+ *
+ * Memory and ownership.  Every pointer in ots_problem_desc is a HOST pointer; the library
+ * copies what it needs during ots_create_problem and keeps no reference to the caller's
+ * arrays.  Device memory is obtained once per problem, either from the optional allocator
+ * callbacks in the descriptor or from cudaMalloc.  Output buffers of the getters are host
+ * buffers allocated by the caller.
+ *
+ * Errors.  Every entry point returns an ots_status (no exceptions cross the ABI, nothing
+ * aborts).  ots_last_error() gives a human-readable message for the calling thread.
+ *
+ * Threads.  One problem handle must not be used by two threads at once; distinct handles
+ * are independent.  All device work of a handle runs on its stream (desc.stream, or a
+ * stream the library creates); the getters synchronise that stream.
+ */
+#ifndef OTS_H
+#define OTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ots_status {
+  OTS_OK = 0,
+  OTS_ERR_INVALID_ARG = 1,   /* bad size, index out of range, eps <= 0, T < 3, negative
+                                mass or capacity, per-commodity source mass != sink mass
+                                (relative 1e-9), unsupported option */
+  OTS_ERR_INFEASIBLE = 2,    /* a sink state no source of its commodity reaches in T-1
+                                transitions, or a source that reaches no sink */
+  OTS_ERR_NOT_CONVERGED = 3, /* max_iters passes without reaching tol (e.g. capacities
+                                that admit no feasible flow: the duals then diverge) */
+  OTS_ERR_TIMEOUT = 4,       /* timeout_ms elapsed before convergence */
+  OTS_ERR_OOM = 5,           /* device or host allocation failed */
+  OTS_ERR_CUDA = 6,          /* a CUDA runtime call failed (see ots_last_error) */
+  OTS_ERR_NUMERIC = 7        /* a NaN appeared in the convergence measures */
+} ots_status;
+
+typedef struct ots_problem ots_problem;
+
+/* Optional device allocator: returns a device pointer (256-byte aligned) or NULL. */
+typedef void *(*ots_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*ots_free_fn)(void *ptr, void *ctx);
+
+/* Problem description (Section 3.2, eq. multicommodity; Section 3.3 wait loops). */
+typedef struct ots_problem_desc {
+  int32_t n_nodes;               /* |V| >= 1 */
+  int32_t n_edges;               /* |E| >= 0, directed */
+  const int32_t *edge_src;       /* [n_edges] tail node of each edge */
+  const int32_t *edge_dst;       /* [n_edges] head node of each edge */
+  const double *edge_cost;       /* [n_edges] cost per interval on the edge (row of C_L,
+                                    identical for every commodity); NULL = 0 */
+  const double *edge_capacity;   /* [n_edges] d on edges, INFINITY = none; NULL = none */
+  int32_t add_wait_loops;        /* 1: add a wait-loop state per node; 0: states = edges */
+  const double *wait_cost;       /* [n_nodes] cost per interval on the wait loop; NULL = 0 */
+  const double *wait_capacity;   /* [n_nodes] d on wait loops, INFINITY = none; NULL = none */
+  const double *commodity_cost;  /* optional [L x n_states] row-major C_L with per-commodity
+                                    rows; overrides edge_cost / wait_cost when non-NULL */
+  int32_t T;                     /* number of marginals / time intervals, T >= 3 */
+  int32_t L;                     /* number of commodities, L >= 1 */
+  double eps;                    /* entropy regularisation eps > 0 (eq. omt_multi_graph_reg) */
+  int32_t n_sources;             /* non-zeros of R01 as (commodity, state, mass) triples;   */
+  const int32_t *src_commodity;  /* repeated (commodity, state) pairs add up              */
+  const int32_t *src_state;
+  const double *src_mass;        /* > 0 */
+  int32_t n_sinks;               /* non-zeros of R0T, same layout */
+  const int32_t *snk_commodity;
+  const int32_t *snk_state;
+  const double *snk_mass;
+  int32_t device;                /* CUDA device ordinal */
+  void *stream;                  /* cudaStream_t for all work of this problem; NULL = own */
+  ots_alloc_fn alloc;            /* optional device allocator (both or neither) */
+  ots_free_fn free_fn;
+  void *alloc_ctx;
+} ots_problem_desc;
+
+/* Options of ots_sinkhorn_solve. */
+typedef struct ots_solve_opts {
+  double tol;            /* stop when the relative L1 source mismatch and the relative
+                            capacity excess are both <= tol (default 1e-6) */
+  int32_t max_iters;     /* Sinkhorn passes (default 100000) */
+  int32_t check_every;   /* passes between host reads of the measures (default 10) */
+  double timeout_ms;     /* 0 = none */
+  int32_t warm_start;    /* 1: continue from the current duals; 0: start from u = 1,
+                            U01 = U0T = 1 on the supports (default 0) */
+  int32_t use_graph;     /* 1: run each pass as one captured CUDA graph (default 1) */
+  int32_t threads_per_node; /* tuning knob: threads cooperating on one node row
+                               (power of two <= 256); 0 = automatic */
+} ots_solve_opts;
+
+/* Report of ots_sinkhorn_solve / ots_iterate. */
+typedef struct ots_solve_report {
+  int32_t iterations;      /* passes done by this call */
+  double src_residual;     /* ||U01 .* Psi_1 - R01||_1 / ||R01||_1, taken just before the
+                              last source update */
+  double cap_violation;    /* sum_t sum_i (P_t - d)_+ / ||R01||_1, taken just before each
+                              capacity update of the last pass */
+  double dual_objective;   /* dual objective of Theorem 3 (u = exp(-lambda/eps)) after the
+                              last pass, without the constant of the entropy term */
+  double seconds;          /* wall time of the call */
+  int32_t status;          /* same as the return value */
+} ots_solve_report;
+
+/* Fill opts with the defaults above. */
+ots_status ots_default_solve_opts(ots_solve_opts *opts);
+
+/* Validate and copy a problem to the device (Section 3.2 problem statement, eq.
+ * multicommodity; state graph of Sections 3.1 and 3.3).  On success *out owns all device
+ * memory of the problem; release it with ots_destroy_problem.  Also checks reachability of
+ * every sink from its commodity's sources within T-1 transitions (OTS_ERR_INFEASIBLE). */
+ots_status ots_create_problem(const ots_problem_desc *desc, ots_problem **out);
+
+/* Run Algorithm 2 (Section 4.3) until convergence: source update U01 <- R01 ./ Psi_1,
+ * forward sweep with the capacity updates u_t <- min(d ./ ((hatPsi_t .* Psi_t .* K_L)^T 1), 1),
+ * sink update U0T <- R0T ./ hatPsi_T, backward sweep (eq. psi_hat, eq. psi, Corollary 7).
+ * opts may be NULL (defaults); rep may be NULL.  Returns OTS_OK on convergence,
+ * OTS_ERR_NOT_CONVERGED / OTS_ERR_TIMEOUT otherwise (the duals are kept either way). */
+ots_status ots_sinkhorn_solve(ots_problem *p, const ots_solve_opts *opts, ots_solve_report *rep);
+
+/* Run exactly n passes of Algorithm 2 from the current duals (no convergence test); the
+ * measures of the last pass go to rep (may be NULL).  With reset = 1 the duals are first
+ * set to their initial values.  Used for benchmarking and iterate-by-iterate checks. */
+ots_status ots_iterate(ots_problem *p, int32_t n, int32_t reset, ots_solve_report *rep);
+
+/* Aggregate flows P_t(M) = sum_l P_{0,t}(M) (Corollary 7; eq. proj_0t for t = 1, T) of the
+ * current iterate, for t in [t_begin, t_end) with 1 <= t_begin < t_end <= T + 1.
+ * out: host buffer [(t_end - t_begin) x n_states], row-major, FP64.  The flow of state i
+ * at t is the amount on edge / wait loop i during the interval (t-1, t). */
+ots_status ots_get_flows(ots_problem *p, int32_t t_begin, int32_t t_end, double *out);
+
+/* Per-commodity flows P_{0,t}(M) (Theorem 6, eq. proj_0t) for t in [t_begin, t_end) and
+ * commodities [l_begin, l_end).  out: host [(t_end-t_begin) x (l_end-l_begin) x n_states]. */
+ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_end,
+                                   int32_t l_begin, int32_t l_end, double *out);
+
+/* Current duals in natural-log form (Theorem 3 convention u = exp(-lambda/eps), so
+ * lambda = -eps * log u).  log_u: host [(T-2) x n_states], rows t = 2..T-1;
+ * log_U01: host [n_sources] aligned with the descriptor's source triples;
+ * log_U0T: host [n_sinks] aligned with the sink triples.  Any pointer may be NULL. */
+ots_status ots_get_duals(ots_problem *p, double *log_u, double *log_U01, double *log_U0T);
+
+/* Set the duals (same layout as ots_get_duals), e.g. to resume from a checkpoint; the
+ * next solve or iterate call first recomputes the backward messages.  log_u entries must
+ * be <= 0. */
+ots_status ots_set_duals(ots_problem *p, const double *log_u, const double *log_U01,
+                         const double *log_U0T);
+
+/* Sizes and counters of a created problem. */
+typedef struct ots_problem_stats {
+  int32_t n_states;         /* states (edges plus wait loops) */
+  int32_t n_nodes;
+  int32_t T;
+  int32_t L;
+  int32_t padded_L;         /* row length of a device message panel (L rounded up) */
+  int32_t threads_per_node; /* threads cooperating on one node row */
+  int64_t device_bytes;     /* device memory held by the problem */
+  int64_t kernels_per_pass; /* kernels of one pass of Algorithm 2 */
+  int64_t kernels_launched; /* kernels of this library launched for the problem so far */
+  int64_t passes_total;     /* passes run so far */
+  int64_t h2d_bytes;        /* host-to-device bytes copied so far */
+  int64_t d2h_bytes;        /* device-to-host bytes copied so far */
+} ots_problem_stats;
+
+ots_status ots_problem_info(const ots_problem *p, ots_problem_stats *out);
+
+/* Device time in milliseconds of the phases of the most recent pass, from CUDA events
+ * recorded on the problem's stream: ms[0] source update, ms[1] forward sweep (T-2
+ * forward kernels), ms[2] sink update, ms[3] backward sweep (T-2 backward kernels).
+ * Synchronises the stream.  OTS_ERR_INVALID_ARG if no pass has run yet. */
+ots_status ots_last_pass_timing(ots_problem *p, double *ms);
+
+/* The cudaStream_t (as void*) on which all device work of the problem runs, so a caller can
+ * order its own work or record timing events around the solver's.  NULL if p is NULL. */
+void *ots_problem_stream(const ots_problem *p);
+
+/* Free all device and host memory of the problem (NULL is ignored). */
+void ots_destroy_problem(ots_problem *p);
+
+/* Static string naming a status code. */
+const char *ots_status_string(ots_status s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ots_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OTS_H */

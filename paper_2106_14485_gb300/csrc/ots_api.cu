@@ -1,0 +1,999 @@
+// ots_api.cu -- host side of the C ABI declared in include/ots.h.
+//
+// Builds the state graph of the road network (directed edges plus wait loops, Sections 3.1
+// and 3.3), its node-level CSR views (states entering / leaving each node), the boundary
+// triples of R01 and R0T, uploads everything into one device arena, captures one pass of
+// Algorithm 2 as a CUDA graph, and runs the passes until the convergence measures reach
+// the tolerance.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ots.h"
+#include "ots_device.cuh"
+
+namespace ots {
+cudaError_t launch_step(bool fwd, bool pc, int G, int C, const StepArgs &a, cudaStream_t s);
+int step_grid(int V, int G);
+cudaError_t launch_boundary(const BndArgs &b, cudaStream_t s);
+int boundary_grid(int n_seg);
+cudaError_t launch_pass_begin(DevStats *st, cudaStream_t s);
+cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, cudaStream_t s);
+cudaError_t launch_init_weights(int S, int T, const float *kl_hi, const float *kl_lo, double *logu, float *w_hi,
+                                float *w_lo, cudaStream_t s);
+cudaError_t launch_weights_from_logu(int S, int T, const float *kl_hi, const float *kl_lo, const double *logu,
+                                     float *w_hi, float *w_lo, cudaStream_t s);
+cudaError_t launch_fill_panel(size_t n, float *hi, __half *lo, cudaStream_t s);
+cudaError_t launch_commodity_flows(int S, int Lp, int l0, int l1, const int *tail, const int *head, const float *a_hi,
+                                   const __half *a_lo, const float *b_hi, const __half *b_lo, const float *kl_hi,
+                                   const float *kl_lo, const float *klc_hi, const __half *klc_lo, const double *logu_t,
+                                   double *out, cudaStream_t s);
+cudaError_t launch_boundary_flows(int n, int Lp, const int *tri_l, const int *tri_node_other, const double *tri_logU,
+                                  const float *msg_hi, const __half *msg_lo, double *out, cudaStream_t s);
+}  // namespace ots
+
+using namespace ots;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ots_status fail(ots_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define OTS_CUDA(expr)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(e_ == cudaErrorMemoryAllocation ? OTS_ERR_OOM : OTS_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+  } while (0)
+
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr double kInvLn2 = 1.44269504088896340736;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+void split_ff(double x, float &hi, float &lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// One side of the boundary (sources or sinks): unique (commodity, state) triples grouped in
+// segments of equal (node, commodity).
+struct Boundary {
+  int n = 0;                      // unique triples
+  int n_seg = 0;
+  std::vector<int> seg_ptr, seg_node, seg_l;
+  std::vector<int> tri_l, tri_state, tri_other;
+  std::vector<double> tri_R;
+  std::vector<int> input_to_tri;  // descriptor triple -> unique triple
+  // device
+  int *d_seg_ptr = nullptr, *d_seg_node = nullptr, *d_seg_l = nullptr, *d_tri_other = nullptr, *d_tri_l = nullptr;
+  double *d_tri_R = nullptr, *d_tri_logR = nullptr, *d_tri_logU = nullptr, *d_flow = nullptr;
+};
+
+}  // namespace
+
+struct ots_problem {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  ots_alloc_fn alloc = nullptr;
+  ots_free_fn free_fn = nullptr;
+  void *actx = nullptr;
+
+  int V = 0, E = 0, S = 0, L = 0, T = 0, G = 1, C = 1, Lp = 4;
+  double eps = 1.0, mass = 0.0;
+  bool pc = false;
+
+  std::vector<int> tail, head;
+  Boundary src, snk;
+
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+
+  int *d_in_ptr = nullptr, *d_in_state = nullptr, *d_in_nbr = nullptr;
+  int *d_out_ptr = nullptr, *d_out_state = nullptr, *d_out_nbr = nullptr;
+  int *d_tail = nullptr, *d_head = nullptr;
+  float *d_kl_hi = nullptr, *d_kl_lo = nullptr, *d_logd_hi = nullptr, *d_logd_lo = nullptr;
+  double *d_cap = nullptr;
+  float *d_klc_hi = nullptr;
+  __half *d_klc_lo = nullptr;
+  float *d_w_hi = nullptr, *d_w_lo = nullptr;  // [T+1][S]
+  double *d_logu = nullptr;                    // [T+1][S]
+  double *d_flow = nullptr;                    // [T+1][S]
+  float *d_a_hi[3] = {nullptr, nullptr, nullptr};
+  __half *d_a_lo[3] = {nullptr, nullptr, nullptr};
+  float *d_b_hi = nullptr;                     // [(T-1)][V][Lp], row t-2
+  __half *d_b_lo = nullptr;
+  DevStats *d_stats = nullptr;
+  PassReport *d_report = nullptr;
+  double *d_partials = nullptr;
+  unsigned int *d_counter = nullptr;
+  PassReport *h_report = nullptr;              // pinned
+
+  cudaGraphExec_t pass_exec = nullptr;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // phase marks of a pass
+  bool stale = true;                           // backward messages not consistent with duals
+  long long passes_total = 0;
+  long long kernels_launched = 0;
+  long long h2d_bytes = 0, d2h_bytes = 0;
+
+  size_t panel() const { return (size_t)V * Lp; }
+  float *a_hi(int t) { return t == 1 ? d_a_hi[0] : d_a_hi[1 + (t & 1)]; }
+  __half *a_lo(int t) { return t == 1 ? d_a_lo[0] : d_a_lo[1 + (t & 1)]; }
+  float *b_hi(int t) { return d_b_hi + (size_t)(t - 2) * panel(); }
+  __half *b_lo(int t) { return d_b_lo + (size_t)(t - 2) * panel(); }
+};
+
+namespace {
+
+void *dev_alloc(ots_problem *p, size_t bytes) {
+  if (p->alloc) return p->alloc(bytes, p->actx);
+  void *ptr = nullptr;
+  if (cudaMalloc(&ptr, bytes) != cudaSuccess) return nullptr;
+  return ptr;
+}
+
+void dev_free(ots_problem *p, void *ptr) {
+  if (!ptr) return;
+  if (p->free_fn) p->free_fn(ptr, p->actx);
+  else cudaFree(ptr);
+}
+
+// Thread mapping for L commodities: G threads per node (power of two <= 256), C chunks of 4.
+bool choose_mapping(int L, int want_G, int &G, int &C, int &Lp) {
+  int q = (L + 3) / 4;
+  if (want_G > 0) {
+    if ((want_G & (want_G - 1)) != 0 || want_G > 256) return false;
+    G = want_G;
+    C = (q + G - 1) / G;
+    if (G < 256 && C != 1) return false;
+  } else if (q <= 256) {
+    G = 1;
+    while (G < q) G <<= 1;
+    C = 1;
+  } else {
+    G = 256;
+    C = (q + 255) / 256;
+  }
+  if (C > 4 || (C == 3 && G != 256)) return false;
+  Lp = 4 * G * C;
+  return true;
+}
+
+StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
+  StepArgs a{};
+  a.V = p->V;
+  a.Lp = p->Lp;
+  if (fwd) {
+    a.ptr = p->d_in_ptr; a.state = p->d_in_state; a.nbr = p->d_in_nbr;
+    a.x_hi = p->a_hi(t - 1); a.x_lo = p->a_lo(t - 1);
+    a.y_hi = p->b_hi(t + 1); a.y_lo = p->b_lo(t + 1);
+    a.out_hi = p->a_hi(t); a.out_lo = p->a_lo(t);
+  } else {
+    a.ptr = p->d_out_ptr; a.state = p->d_out_state; a.nbr = p->d_out_nbr;
+    a.x_hi = p->b_hi(t + 1); a.x_lo = p->b_lo(t + 1);
+    a.out_hi = p->b_hi(t); a.out_lo = p->b_lo(t);
+  }
+  a.kl_hi = p->d_kl_hi; a.kl_lo = p->d_kl_lo;
+  a.klc_hi = p->d_klc_hi; a.klc_lo = p->d_klc_lo;
+  a.logd_hi = p->d_logd_hi; a.logd_lo = p->d_logd_lo;
+  a.cap = p->d_cap;
+  a.logu_t = p->d_logu + (size_t)t * p->S;
+  a.w_hi_t = p->d_w_hi + (size_t)t * p->S;
+  a.w_lo_t = p->d_w_lo + (size_t)t * p->S;
+  a.flow_t = p->d_flow + (size_t)t * p->S;
+  a.partials = p->d_partials;
+  a.counter = p->d_counter;
+  a.stats = p->d_stats;
+  a.mode = mode;
+  return a;
+}
+
+BndArgs bnd_args(ots_problem *p, bool source, int mode) {
+  Boundary &b = source ? p->src : p->snk;
+  BndArgs a{};
+  a.n_seg = b.n_seg;
+  a.seg_ptr = b.d_seg_ptr; a.seg_node = b.d_seg_node; a.seg_l = b.d_seg_l;
+  a.tri_node_other = b.d_tri_other;
+  a.tri_R = b.d_tri_R; a.tri_logR = b.d_tri_logR; a.tri_logU = b.d_tri_logU;
+  a.Lp = p->Lp;
+  if (source) {
+    a.msg_hi = p->b_hi(2); a.msg_lo = p->b_lo(2);
+    a.out_hi = p->a_hi(1); a.out_lo = p->a_lo(1);
+  } else {
+    a.msg_hi = p->a_hi(p->T - 1); a.msg_lo = p->a_lo(p->T - 1);
+    a.out_hi = p->b_hi(p->T); a.out_lo = p->b_lo(p->T);
+  }
+  a.partials = p->d_partials; a.counter = p->d_counter; a.stats = p->d_stats;
+  a.mode = mode;
+  a.is_source = source ? 1 : 0;
+  return a;
+}
+
+// Backward sweep of Algorithm 2 ("Compute Psi_t"), from the current duals.
+ots_status enqueue_backward_sweep(ots_problem *p) {
+  OTS_CUDA(launch_boundary(bnd_args(p, false, 1), p->stream));
+  for (int t = p->T - 1; t >= 2; --t)
+    OTS_CUDA(launch_step(false, p->pc, p->G, p->C, step_args(p, false, t, 0), p->stream));
+  p->kernels_launched += p->T - 1;
+  return OTS_OK;
+}
+
+long long kernels_per_pass(const ots_problem *p) { return 2LL * p->T; }
+
+// One pass of the while loop of Algorithm 2 (enqueued directly or captured into a graph),
+// with phase events around the source update, the forward sweep, the sink update and the
+// backward sweep.
+ots_status enqueue_pass(ots_problem *p, bool capture) {
+  // inside a graph the marks become external event-record nodes, usable for timing
+  const unsigned flags = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
+  OTS_CUDA(launch_pass_begin(p->d_stats, p->stream));
+  OTS_CUDA(cudaEventRecordWithFlags(p->ev[0], p->stream, flags));
+  OTS_CUDA(launch_boundary(bnd_args(p, true, 0), p->stream));                 // U01, hatPsi_2
+  OTS_CUDA(cudaEventRecordWithFlags(p->ev[1], p->stream, flags));
+  for (int t = 2; t <= p->T - 1; ++t)                                          // u_t, hatPsi_{t+1}
+    OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 0), p->stream));
+  OTS_CUDA(cudaEventRecordWithFlags(p->ev[2], p->stream, flags));
+  OTS_CUDA(launch_boundary(bnd_args(p, false, 0), p->stream));                // U0T, Psi_{T-1}
+  OTS_CUDA(cudaEventRecordWithFlags(p->ev[3], p->stream, flags));
+  for (int t = p->T - 1; t >= 2; --t)                                          // Psi_{t-1}
+    OTS_CUDA(launch_step(false, p->pc, p->G, p->C, step_args(p, false, t, 0), p->stream));
+  OTS_CUDA(cudaEventRecordWithFlags(p->ev[4], p->stream, flags));
+  OTS_CUDA(launch_pass_end(p->d_stats, p->d_report, p->mass, p->eps, p->stream));
+  return OTS_OK;
+}
+
+ots_status build_pass_graph(ots_problem *p) {
+  if (p->pass_exec) return OTS_OK;
+  cudaGraph_t g = nullptr;
+  OTS_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+  ots_status st = enqueue_pass(p, true);
+  cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+  if (st != OTS_OK) { if (g) cudaGraphDestroy(g); return st; }
+  if (e != cudaSuccess) return fail(OTS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&p->pass_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { p->pass_exec = nullptr; return fail(OTS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+  return OTS_OK;
+}
+
+// Reset the duals to the initialisation of Algorithm 2 (u_t = 1, U01 = U0T = 1 on the
+// supports) and recompute the backward messages.
+ots_status reset_duals(ots_problem *p) {
+  p->kernels_launched += 2;
+  OTS_CUDA(launch_init_weights(p->S, p->T, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo, p->d_logu,
+                               p->d_w_hi, p->d_w_lo, p->stream));
+  if (p->src.n) OTS_CUDA(cudaMemsetAsync(p->src.d_tri_logU, 0, sizeof(double) * p->src.n, p->stream));
+  if (p->snk.n) OTS_CUDA(cudaMemsetAsync(p->snk.d_tri_logU, 0, sizeof(double) * p->snk.n, p->stream));
+  OTS_CUDA(cudaMemsetAsync(p->d_report, 0, sizeof(PassReport), p->stream));
+  OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
+  ots_status st = enqueue_backward_sweep(p);
+  if (st) return st;
+  p->stale = false;
+  return OTS_OK;
+}
+
+ots_status refresh_if_stale(ots_problem *p) {
+  if (!p->stale) return OTS_OK;
+  p->kernels_launched += 2;
+  OTS_CUDA(launch_weights_from_logu(p->S, p->T, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo, p->d_logu,
+                                    p->d_w_hi, p->d_w_lo, p->stream));
+  OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
+  ots_status st = enqueue_backward_sweep(p);
+  if (st) return st;
+  p->stale = false;
+  return OTS_OK;
+}
+
+ots_status run_passes(ots_problem *p, int n, bool use_graph) {
+  if (use_graph) {
+    ots_status st = build_pass_graph(p);
+    if (st) return st;
+    for (int k = 0; k < n; ++k) OTS_CUDA(cudaGraphLaunch(p->pass_exec, p->stream));
+  } else {
+    for (int k = 0; k < n; ++k) {
+      ots_status st = enqueue_pass(p, false);
+      if (st) return st;
+    }
+  }
+  p->passes_total += n;
+  p->kernels_launched += (long long)n * kernels_per_pass(p);
+  return OTS_OK;
+}
+
+ots_status read_report(ots_problem *p, ots_solve_report *rep) {
+  OTS_CUDA(cudaMemcpyAsync(p->h_report, p->d_report, sizeof(PassReport), cudaMemcpyDeviceToHost, p->stream));
+  p->d2h_bytes += sizeof(PassReport);
+  OTS_CUDA(cudaStreamSynchronize(p->stream));
+  rep->src_residual = p->h_report->src_resid_rel;
+  rep->cap_violation = p->h_report->cap_viol_rel;
+  rep->dual_objective = p->h_report->dual_objective;
+  if (p->h_report->bad > 0) return fail(OTS_ERR_INFEASIBLE, "a source or sink message vanished (infeasible instance)");
+  if (std::isnan(rep->src_residual) || std::isnan(rep->cap_violation) || std::isnan(rep->dual_objective))
+    return fail(OTS_ERR_NUMERIC, "NaN in the convergence measures");
+  return OTS_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Necessary feasibility condition: every sink state is reached by a source state of the same
+// commodity, and every source reaches a sink, in exactly T-1 transitions.  With wait loops a
+// walk of length k <= T-1 can be padded to T-1, so the test is on hop distances: state j is
+// reachable from state i after T-1 transitions iff 1 + dist(head(i), tail(j)) <= T-1 (or
+// i == j needs a loop to stay; covered by the same rule when loops exist).
+bool feasible(ots_problem *p, const std::vector<int> &eptr, const std::vector<int> &enbr, std::string &why) {
+  std::map<int, std::vector<int>> cache;
+  auto dist_from = [&](int s) -> const std::vector<int> & {
+    auto it = cache.find(s);
+    if (it != cache.end()) return it->second;
+    std::vector<int> d(p->V, -1);
+    std::vector<int> q;
+    q.reserve(p->V);
+    d[s] = 0;
+    q.push_back(s);
+    for (size_t h = 0; h < q.size(); ++h) {
+      int u = q[h];
+      for (int k = eptr[u]; k < eptr[u + 1]; ++k) {
+        int w = enbr[k];
+        if (d[w] < 0) { d[w] = d[u] + 1; q.push_back(w); }
+      }
+    }
+    return cache.emplace(s, std::move(d)).first->second;
+  };
+  // group triples by commodity
+  std::vector<std::vector<int>> src_by_l(p->L), snk_by_l(p->L);
+  for (int q = 0; q < p->src.n; ++q) src_by_l[p->src.tri_l[q]].push_back(q);
+  for (int q = 0; q < p->snk.n; ++q) snk_by_l[p->snk.tri_l[q]].push_back(q);
+  for (int l = 0; l < p->L; ++l) {
+    std::vector<char> snk_hit(snk_by_l[l].size(), 0);
+    for (int qs : src_by_l[l]) {
+      const std::vector<int> &d = dist_from(p->head[p->src.tri_state[qs]]);
+      bool any = false;
+      for (size_t k = 0; k < snk_by_l[l].size(); ++k) {
+        int j = p->snk.tri_state[snk_by_l[l][k]];
+        int dd = d[p->tail[j]];
+        if (dd >= 0 && 1 + dd <= p->T - 1) { any = true; snk_hit[k] = 1; }
+      }
+      if (!any) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "commodity %d: source state %d reaches no sink within T-1 transitions", l,
+                 p->src.tri_state[qs]);
+        why = buf;
+        return false;
+      }
+    }
+    for (size_t k = 0; k < snk_hit.size(); ++k) {
+      if (!snk_hit[k]) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "commodity %d: sink state %d is reached by no source within T-1 transitions", l,
+                 p->snk.tri_state[snk_by_l[l][k]]);
+        why = buf;
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+ots_status build_boundary(ots_problem *p, Boundary &b, int n, const int32_t *comm, const int32_t *state,
+                          const double *mass, bool source) {
+  std::map<std::pair<int, int>, int> uniq;  // (l, state) -> unique index
+  std::vector<std::pair<int, int>> keys;
+  std::vector<double> R;
+  b.input_to_tri.resize(n);
+  for (int q = 0; q < n; ++q) {
+    if (comm[q] < 0 || comm[q] >= p->L) return fail(OTS_ERR_INVALID_ARG, "triple %d: commodity %d out of range", q, comm[q]);
+    if (state[q] < 0 || state[q] >= p->S) return fail(OTS_ERR_INVALID_ARG, "triple %d: state %d out of range", q, state[q]);
+    if (!(mass[q] > 0.0) || !std::isfinite(mass[q]))
+      return fail(OTS_ERR_INVALID_ARG, "triple %d: mass must be positive and finite", q);
+    auto key = std::make_pair((int)comm[q], (int)state[q]);
+    auto it = uniq.find(key);
+    if (it == uniq.end()) {
+      uniq[key] = (int)keys.size();
+      b.input_to_tri[q] = (int)keys.size();
+      keys.push_back(key);
+      R.push_back(mass[q]);
+    } else {
+      b.input_to_tri[q] = it->second;
+      R[it->second] += mass[q];
+    }
+  }
+  // order unique triples by (segment node, commodity, state)
+  const int nu = (int)keys.size();
+  std::vector<int> order(nu);
+  for (int k = 0; k < nu; ++k) order[k] = k;
+  auto seg_node_of = [&](int k) { return source ? p->head[keys[k].second] : p->tail[keys[k].second]; };
+  std::sort(order.begin(), order.end(), [&](int a, int c) {
+    int na = seg_node_of(a), nc = seg_node_of(c);
+    if (na != nc) return na < nc;
+    if (keys[a].first != keys[c].first) return keys[a].first < keys[c].first;
+    return keys[a].second < keys[c].second;
+  });
+  std::vector<int> rank(nu);
+  for (int k = 0; k < nu; ++k) rank[order[k]] = k;
+  for (int q = 0; q < n; ++q) b.input_to_tri[q] = rank[b.input_to_tri[q]];
+  b.n = nu;
+  b.tri_l.resize(nu); b.tri_state.resize(nu); b.tri_other.resize(nu); b.tri_R.resize(nu);
+  b.seg_ptr.clear(); b.seg_node.clear(); b.seg_l.clear();
+  for (int k = 0; k < nu; ++k) {
+    int u = order[k];
+    b.tri_l[k] = keys[u].first;
+    b.tri_state[k] = keys[u].second;
+    // message row read at the boundary: Psi_1 = B_2[head(i)] for sources, hatPsi_T = A_{T-1}[tail(j)] for sinks
+    b.tri_other[k] = source ? p->head[keys[u].second] : p->tail[keys[u].second];
+    b.tri_R[k] = R[u];
+    int node = seg_node_of(u);
+    if (k == 0 || node != b.seg_node.back() || keys[u].first != b.seg_l.back()) {
+      b.seg_ptr.push_back(k);
+      b.seg_node.push_back(node);
+      b.seg_l.push_back(keys[u].first);
+    }
+  }
+  b.seg_ptr.push_back(nu);
+  b.n_seg = (int)b.seg_node.size();
+  return OTS_OK;
+}
+
+// Arena carving helper.
+struct Carver {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t count) {
+    size_t o = align_up(off, 256);
+    off = o + align_up(count * sizeof(T), 256);
+    return o;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *ots_status_string(ots_status s) {
+  switch (s) {
+    case OTS_OK: return "OTS_OK";
+    case OTS_ERR_INVALID_ARG: return "OTS_ERR_INVALID_ARG";
+    case OTS_ERR_INFEASIBLE: return "OTS_ERR_INFEASIBLE";
+    case OTS_ERR_NOT_CONVERGED: return "OTS_ERR_NOT_CONVERGED";
+    case OTS_ERR_TIMEOUT: return "OTS_ERR_TIMEOUT";
+    case OTS_ERR_OOM: return "OTS_ERR_OOM";
+    case OTS_ERR_CUDA: return "OTS_ERR_CUDA";
+    case OTS_ERR_NUMERIC: return "OTS_ERR_NUMERIC";
+  }
+  return "OTS_ERR_UNKNOWN";
+}
+
+const char *ots_last_error(void) { return g_last_error.c_str(); }
+
+ots_status ots_default_solve_opts(ots_solve_opts *o) {
+  if (!o) return fail(OTS_ERR_INVALID_ARG, "opts is NULL");
+  o->tol = 1e-6;
+  o->max_iters = 100000;
+  o->check_every = 10;
+  o->timeout_ms = 0.0;
+  o->warm_start = 0;
+  o->use_graph = 1;
+  o->threads_per_node = 0;
+  return OTS_OK;
+}
+
+void ots_destroy_problem(ots_problem *p) {
+  if (!p) return;
+  DeviceGuard guard(p->dev);
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->pass_exec) cudaGraphExecDestroy(p->pass_exec);
+  for (int k = 0; k < 5; ++k)
+    if (p->ev[k]) cudaEventDestroy(p->ev[k]);
+  if (p->arena) dev_free(p, p->arena);
+  if (p->h_report) cudaFreeHost(p->h_report);
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  delete p;
+}
+
+ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
+  g_last_error.clear();
+  if (!d || !out) return fail(OTS_ERR_INVALID_ARG, "desc or out is NULL");
+  *out = nullptr;
+  if (d->n_nodes < 1 || d->n_edges < 0) return fail(OTS_ERR_INVALID_ARG, "n_nodes must be >= 1 and n_edges >= 0");
+  if (d->n_edges > 0 && (!d->edge_src || !d->edge_dst)) return fail(OTS_ERR_INVALID_ARG, "edge_src / edge_dst missing");
+  if (d->T < 3) return fail(OTS_ERR_INVALID_ARG, "T must be >= 3 (Algorithm 2 needs hatPsi_2 and Psi_{T-1})");
+  if (d->L < 1 || d->L > 4096) return fail(OTS_ERR_INVALID_ARG, "L must be in [1, 4096]");
+  if (!(d->eps > 0.0) || !std::isfinite(d->eps)) return fail(OTS_ERR_INVALID_ARG, "eps must be > 0");
+  if ((d->alloc == nullptr) != (d->free_fn == nullptr)) return fail(OTS_ERR_INVALID_ARG, "alloc and free_fn go together");
+  if (d->n_sources < 1 || d->n_sinks < 1) return fail(OTS_ERR_INVALID_ARG, "need at least one source and one sink");
+  if (!d->src_commodity || !d->src_state || !d->src_mass || !d->snk_commodity || !d->snk_state || !d->snk_mass)
+    return fail(OTS_ERR_INVALID_ARG, "source / sink arrays missing");
+
+  ots_problem *p = new (std::nothrow) ots_problem();
+  if (!p) return fail(OTS_ERR_OOM, "host allocation failed");
+  p->dev = d->device;
+  p->alloc = d->alloc;
+  p->free_fn = d->free_fn;
+  p->actx = d->alloc_ctx;
+  p->V = d->n_nodes;
+  p->E = d->n_edges;
+  p->S = d->n_edges + (d->add_wait_loops ? d->n_nodes : 0);
+  p->L = d->L;
+  p->T = d->T;
+  p->eps = d->eps;
+  p->pc = d->commodity_cost != nullptr;
+  if (p->S < 1) { delete p; return fail(OTS_ERR_INVALID_ARG, "no states"); }
+  if (!choose_mapping(p->L, 0, p->G, p->C, p->Lp)) { delete p; return fail(OTS_ERR_INVALID_ARG, "unsupported L"); }
+
+  auto bail = [&](ots_status s) { ots_destroy_problem(p); return s; };
+
+  // ---- state graph (Sections 3.1, 3.3) ----
+  p->tail.resize(p->S);
+  p->head.resize(p->S);
+  for (int e = 0; e < p->E; ++e) {
+    if (d->edge_src[e] < 0 || d->edge_src[e] >= p->V || d->edge_dst[e] < 0 || d->edge_dst[e] >= p->V)
+      return bail(fail(OTS_ERR_INVALID_ARG, "edge %d: node index out of range", e));
+    p->tail[e] = d->edge_src[e];
+    p->head[e] = d->edge_dst[e];
+  }
+  if (d->add_wait_loops)
+    for (int v = 0; v < p->V; ++v) { p->tail[p->E + v] = v; p->head[p->E + v] = v; }
+
+  std::vector<int> in_ptr(p->V + 1, 0), out_ptr(p->V + 1, 0);
+  for (int s = 0; s < p->S; ++s) { in_ptr[p->head[s] + 1]++; out_ptr[p->tail[s] + 1]++; }
+  for (int v = 0; v < p->V; ++v) { in_ptr[v + 1] += in_ptr[v]; out_ptr[v + 1] += out_ptr[v]; }
+  std::vector<int> in_state(p->S), in_nbr(p->S), out_state(p->S), out_nbr(p->S);
+  {
+    std::vector<int> fi(in_ptr.begin(), in_ptr.end() - 1), fo(out_ptr.begin(), out_ptr.end() - 1);
+    for (int s = 0; s < p->S; ++s) {
+      int k = fi[p->head[s]]++;
+      in_state[k] = s; in_nbr[k] = p->tail[s];
+      k = fo[p->tail[s]]++;
+      out_state[k] = s; out_nbr[k] = p->head[s];
+    }
+  }
+  // node adjacency for the feasibility BFS (edges with positive capacity)
+  std::vector<int> eptr(p->V + 1, 0), enbr;
+  {
+    std::vector<std::vector<int>> adj(p->V);
+    for (int e = 0; e < p->E; ++e) {
+      double cap = d->edge_capacity ? d->edge_capacity[e] : INFINITY;
+      if (cap > 0.0 && p->tail[e] != p->head[e]) adj[p->tail[e]].push_back(p->head[e]);
+    }
+    for (int v = 0; v < p->V; ++v) { eptr[v + 1] = eptr[v] + (int)adj[v].size(); enbr.insert(enbr.end(), adj[v].begin(), adj[v].end()); }
+  }
+
+  // ---- per-state data (costs, capacities) in log2 units ----
+  std::vector<float> kl_hi(p->S), kl_lo(p->S), logd_hi(p->S), logd_lo(p->S);
+  std::vector<double> cap(p->S);
+  for (int s = 0; s < p->S; ++s) {
+    double c = 0.0, dd = INFINITY;
+    if (s < p->E) {
+      if (d->edge_cost) c = d->edge_cost[s];
+      if (d->edge_capacity) dd = d->edge_capacity[s];
+    } else {
+      int v = s - p->E;
+      if (d->wait_cost) c = d->wait_cost[v];
+      if (d->wait_capacity) dd = d->wait_capacity[v];
+    }
+    if (!std::isfinite(c)) return bail(fail(OTS_ERR_INVALID_ARG, "state %d: cost must be finite", s));
+    if (std::isnan(dd) || dd < 0.0) return bail(fail(OTS_ERR_INVALID_ARG, "state %d: capacity must be >= 0", s));
+    split_ff(-c / d->eps * kInvLn2, kl_hi[s], kl_lo[s]);
+    cap[s] = dd;
+    if (dd == 0.0) { logd_hi[s] = kNeg; logd_lo[s] = 0.f; }
+    else if (std::isinf(dd)) { logd_hi[s] = 0.f; logd_lo[s] = 0.f; }
+    else split_ff(std::log2(dd), logd_hi[s], logd_lo[s]);
+  }
+  std::vector<float> klc_hi;
+  std::vector<__half> klc_lo;
+  if (p->pc) {
+    klc_hi.assign((size_t)p->S * p->Lp, kNeg);
+    klc_lo.assign((size_t)p->S * p->Lp, __float2half(0.f));
+    for (int l = 0; l < p->L; ++l)
+      for (int s = 0; s < p->S; ++s) {
+        double c = d->commodity_cost[(size_t)l * p->S + s];
+        if (!std::isfinite(c)) return bail(fail(OTS_ERR_INVALID_ARG, "commodity_cost must be finite"));
+        float h, lo;
+        split_ff(-c / d->eps * kInvLn2, h, lo);
+        klc_hi[(size_t)s * p->Lp + l] = h;
+        klc_lo[(size_t)s * p->Lp + l] = __float2half_rn(lo);
+      }
+  }
+
+  // ---- boundary triples ----
+  ots_status st = build_boundary(p, p->src, d->n_sources, d->src_commodity, d->src_state, d->src_mass, true);
+  if (st) return bail(st);
+  st = build_boundary(p, p->snk, d->n_sinks, d->snk_commodity, d->snk_state, d->snk_mass, false);
+  if (st) return bail(st);
+  {
+    std::vector<double> ms(p->L, 0.0), mz(p->L, 0.0);
+    for (int q = 0; q < p->src.n; ++q) ms[p->src.tri_l[q]] += p->src.tri_R[q];
+    for (int q = 0; q < p->snk.n; ++q) mz[p->snk.tri_l[q]] += p->snk.tri_R[q];
+    p->mass = 0.0;
+    for (int l = 0; l < p->L; ++l) {
+      if (ms[l] <= 0.0 || mz[l] <= 0.0)
+        return bail(fail(OTS_ERR_INVALID_ARG, "commodity %d has no source or no sink", l));
+      if (std::fabs(ms[l] - mz[l]) > 1e-9 * std::max(ms[l], mz[l]))
+        return bail(fail(OTS_ERR_INVALID_ARG, "commodity %d: source mass %.17g != sink mass %.17g", l, ms[l], mz[l]));
+      p->mass += ms[l];
+    }
+  }
+  {
+    std::string why;
+    if (!feasible(p, eptr, enbr, why)) return bail(fail(OTS_ERR_INFEASIBLE, "%s", why.c_str()));
+  }
+
+  // ---- device ----
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return bail(fail(OTS_ERR_CUDA, "no CUDA device"));
+  if (p->dev < 0 || p->dev >= ndev) return bail(fail(OTS_ERR_INVALID_ARG, "device %d out of range", p->dev));
+  DeviceGuard guard(p->dev);
+  if (d->stream) {
+    p->stream = (cudaStream_t)d->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(fail(OTS_ERR_CUDA, "stream creation failed"));
+    p->own_stream = true;
+  }
+  if (cudaMallocHost(&p->h_report, sizeof(PassReport)) != cudaSuccess) return bail(fail(OTS_ERR_OOM, "pinned alloc failed"));
+  for (int k = 0; k < 5; ++k)
+    if (cudaEventCreate(&p->ev[k]) != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "event creation failed"));
+
+  const size_t S = p->S, V = p->V, T = p->T, panel = p->panel();
+  const int max_grid = std::max(std::max(step_grid(p->V, p->G), boundary_grid(p->src.n_seg)),
+                                std::max(boundary_grid(p->snk.n_seg), 1));
+  Carver cv;
+  size_t o_in_ptr = cv.take<int>(V + 1), o_in_state = cv.take<int>(S), o_in_nbr = cv.take<int>(S);
+  size_t o_out_ptr = cv.take<int>(V + 1), o_out_state = cv.take<int>(S), o_out_nbr = cv.take<int>(S);
+  size_t o_tail = cv.take<int>(S), o_head = cv.take<int>(S);
+  size_t o_kl_hi = cv.take<float>(S), o_kl_lo = cv.take<float>(S), o_ld_hi = cv.take<float>(S), o_ld_lo = cv.take<float>(S);
+  size_t o_cap = cv.take<double>(S);
+  size_t o_klc_hi = p->pc ? cv.take<float>(S * p->Lp) : 0, o_klc_lo = p->pc ? cv.take<__half>(S * p->Lp) : 0;
+  size_t o_w_hi = cv.take<float>((T + 1) * S), o_w_lo = cv.take<float>((T + 1) * S);
+  size_t o_logu = cv.take<double>((T + 1) * S), o_flow = cv.take<double>((T + 1) * S);
+  size_t o_a_hi[3], o_a_lo[3];
+  for (int k = 0; k < 3; ++k) { o_a_hi[k] = cv.take<float>(panel); o_a_lo[k] = cv.take<__half>(panel); }
+  size_t o_b_hi = cv.take<float>((T - 1) * panel), o_b_lo = cv.take<__half>((T - 1) * panel);
+  size_t o_stats = cv.take<DevStats>(1), o_report = cv.take<PassReport>(1);
+  size_t o_partials = cv.take<double>(2 * (size_t)max_grid), o_counter = cv.take<unsigned int>(4);
+  struct BOff { size_t seg_ptr, seg_node, seg_l, other, l, R, logR, logU, flow; } bo[2];
+  Boundary *sides[2] = {&p->src, &p->snk};
+  for (int k = 0; k < 2; ++k) {
+    Boundary &b = *sides[k];
+    bo[k].seg_ptr = cv.take<int>(b.n_seg + 1); bo[k].seg_node = cv.take<int>(b.n_seg); bo[k].seg_l = cv.take<int>(b.n_seg);
+    bo[k].other = cv.take<int>(b.n); bo[k].l = cv.take<int>(b.n);
+    bo[k].R = cv.take<double>(b.n); bo[k].logR = cv.take<double>(b.n); bo[k].logU = cv.take<double>(b.n);
+    bo[k].flow = cv.take<double>(b.n);
+  }
+  p->arena_bytes = cv.off;
+  p->arena = dev_alloc(p, p->arena_bytes);
+  if (!p->arena) return bail(fail(OTS_ERR_OOM, "device allocation of %zu bytes failed", p->arena_bytes));
+  char *base = (char *)p->arena;
+  auto at = [&](size_t off) { return (void *)(base + off); };
+  p->d_in_ptr = (int *)at(o_in_ptr); p->d_in_state = (int *)at(o_in_state); p->d_in_nbr = (int *)at(o_in_nbr);
+  p->d_out_ptr = (int *)at(o_out_ptr); p->d_out_state = (int *)at(o_out_state); p->d_out_nbr = (int *)at(o_out_nbr);
+  p->d_tail = (int *)at(o_tail); p->d_head = (int *)at(o_head);
+  p->d_kl_hi = (float *)at(o_kl_hi); p->d_kl_lo = (float *)at(o_kl_lo);
+  p->d_logd_hi = (float *)at(o_ld_hi); p->d_logd_lo = (float *)at(o_ld_lo);
+  p->d_cap = (double *)at(o_cap);
+  if (p->pc) { p->d_klc_hi = (float *)at(o_klc_hi); p->d_klc_lo = (__half *)at(o_klc_lo); }
+  p->d_w_hi = (float *)at(o_w_hi); p->d_w_lo = (float *)at(o_w_lo);
+  p->d_logu = (double *)at(o_logu); p->d_flow = (double *)at(o_flow);
+  for (int k = 0; k < 3; ++k) { p->d_a_hi[k] = (float *)at(o_a_hi[k]); p->d_a_lo[k] = (__half *)at(o_a_lo[k]); }
+  p->d_b_hi = (float *)at(o_b_hi); p->d_b_lo = (__half *)at(o_b_lo);
+  p->d_stats = (DevStats *)at(o_stats); p->d_report = (PassReport *)at(o_report);
+  p->d_partials = (double *)at(o_partials); p->d_counter = (unsigned int *)at(o_counter);
+  for (int k = 0; k < 2; ++k) {
+    Boundary &b = *sides[k];
+    b.d_seg_ptr = (int *)at(bo[k].seg_ptr); b.d_seg_node = (int *)at(bo[k].seg_node); b.d_seg_l = (int *)at(bo[k].seg_l);
+    b.d_tri_other = (int *)at(bo[k].other); b.d_tri_l = (int *)at(bo[k].l);
+    b.d_tri_R = (double *)at(bo[k].R); b.d_tri_logR = (double *)at(bo[k].logR); b.d_tri_logU = (double *)at(bo[k].logU);
+    b.d_flow = (double *)at(bo[k].flow);
+  }
+
+  auto up = [&](void *dst, const void *srcp, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    p->h2d_bytes += (long long)bytes;
+    return cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyHostToDevice, p->stream);
+  };
+#define UP(dst, vec) \
+  if (up(dst, vec.data(), vec.size() * sizeof(vec[0])) != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "upload " #vec))
+  UP(p->d_in_ptr, in_ptr); UP(p->d_in_state, in_state); UP(p->d_in_nbr, in_nbr);
+  UP(p->d_out_ptr, out_ptr); UP(p->d_out_state, out_state); UP(p->d_out_nbr, out_nbr);
+  UP(p->d_tail, p->tail); UP(p->d_head, p->head);
+  UP(p->d_kl_hi, kl_hi); UP(p->d_kl_lo, kl_lo); UP(p->d_logd_hi, logd_hi); UP(p->d_logd_lo, logd_lo);
+  UP(p->d_cap, cap);
+  if (p->pc) { UP(p->d_klc_hi, klc_hi); UP(p->d_klc_lo, klc_lo); }
+  std::vector<std::vector<double>> logR(2);
+  for (int k = 0; k < 2; ++k) {
+    Boundary &b = *sides[k];
+    logR[k].resize(b.n);
+    for (int q = 0; q < b.n; ++q) logR[k][q] = std::log2(b.tri_R[q]);
+    UP(b.d_seg_ptr, b.seg_ptr); UP(b.d_seg_node, b.seg_node); UP(b.d_seg_l, b.seg_l);
+    UP(b.d_tri_other, b.tri_other); UP(b.d_tri_l, b.tri_l); UP(b.d_tri_R, b.tri_R); UP(b.d_tri_logR, logR[k]);
+  }
+#undef UP
+  if (cudaMemsetAsync(p->d_stats, 0, sizeof(DevStats), p->stream) != cudaSuccess ||
+      cudaMemsetAsync(p->d_counter, 0, 4 * sizeof(unsigned int), p->stream) != cudaSuccess ||
+      cudaMemsetAsync(p->d_flow, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess)
+    return bail(fail(OTS_ERR_CUDA, "memset failed"));
+  // logu rows outside 2..T-1 stay 0; W rows likewise unused
+  if (cudaMemsetAsync(p->d_logu, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess)
+    return bail(fail(OTS_ERR_CUDA, "memset failed"));
+  // boundary panels start at log 0 everywhere; only the support entries are rewritten
+  p->kernels_launched += 2;
+  if (launch_fill_panel(panel, p->a_hi(1), p->a_lo(1), p->stream) != cudaSuccess ||
+      launch_fill_panel(panel, p->b_hi(p->T), p->b_lo(p->T), p->stream) != cudaSuccess)
+    return bail(fail(OTS_ERR_CUDA, "panel fill failed"));
+  st = reset_duals(p);
+  if (st) return bail(st);
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "%s", cudaGetErrorString(cudaGetLastError())));
+  *out = p;
+  return OTS_OK;
+}
+
+ots_status ots_problem_info(const ots_problem *p, ots_problem_stats *o) {
+  if (!p || !o) return fail(OTS_ERR_INVALID_ARG, "NULL argument");
+  o->n_states = p->S;
+  o->n_nodes = p->V;
+  o->T = p->T;
+  o->L = p->L;
+  o->padded_L = p->Lp;
+  o->threads_per_node = p->G;
+  o->device_bytes = (int64_t)p->arena_bytes;
+  o->kernels_per_pass = kernels_per_pass(p);
+  o->kernels_launched = p->kernels_launched;
+  o->passes_total = p->passes_total;
+  o->h2d_bytes = p->h2d_bytes;
+  o->d2h_bytes = p->d2h_bytes;
+  return OTS_OK;
+}
+
+ots_status ots_last_pass_timing(ots_problem *p, double *ms) {
+  if (!p || !ms) return fail(OTS_ERR_INVALID_ARG, "NULL argument");
+  if (p->passes_total == 0) return fail(OTS_ERR_INVALID_ARG, "no pass has run");
+  DeviceGuard guard(p->dev);
+  OTS_CUDA(cudaStreamSynchronize(p->stream));
+  for (int k = 0; k < 4; ++k) {
+    float v = 0.f;
+    OTS_CUDA(cudaEventElapsedTime(&v, p->ev[k], p->ev[k + 1]));
+    ms[k] = v;
+  }
+  return OTS_OK;
+}
+
+ots_status ots_iterate(ots_problem *p, int32_t n, int32_t reset, ots_solve_report *rep) {
+  g_last_error.clear();
+  if (!p || n < 0) return fail(OTS_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard guard(p->dev);
+  auto t0 = std::chrono::steady_clock::now();
+  ots_status st = reset ? reset_duals(p) : refresh_if_stale(p);
+  if (st) return st;
+  st = run_passes(p, n, true);
+  if (st) return st;
+  ots_solve_report r{};
+  st = read_report(p, &r);
+  r.iterations = n;
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  r.status = st;
+  if (rep) *rep = r;
+  return st;
+}
+
+ots_status ots_sinkhorn_solve(ots_problem *p, const ots_solve_opts *opts, ots_solve_report *rep) {
+  g_last_error.clear();
+  if (!p) return fail(OTS_ERR_INVALID_ARG, "problem is NULL");
+  ots_solve_opts o;
+  ots_default_solve_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || o.max_iters < 1 || o.check_every < 1) return fail(OTS_ERR_INVALID_ARG, "bad solve options");
+  if (o.threads_per_node != 0) {
+    int G, C, Lp;
+    if (!choose_mapping(p->L, o.threads_per_node, G, C, Lp) || Lp != p->Lp)
+      return fail(OTS_ERR_INVALID_ARG, "threads_per_node %d is not usable with L = %d", o.threads_per_node, p->L);
+  }
+  DeviceGuard guard(p->dev);
+  auto t0 = std::chrono::steady_clock::now();
+  ots_status st = o.warm_start ? refresh_if_stale(p) : reset_duals(p);
+  if (st) return st;
+  ots_solve_report r{};
+  int done = 0;
+  st = OTS_ERR_NOT_CONVERGED;
+  while (done < o.max_iters) {
+    int k = std::min(o.check_every, o.max_iters - done);
+    ots_status e = run_passes(p, k, o.use_graph != 0);
+    if (e) return e;
+    done += k;
+    e = read_report(p, &r);
+    if (e) { st = e; break; }
+    if (r.src_residual <= o.tol && r.cap_violation <= o.tol) { st = OTS_OK; break; }
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (o.timeout_ms > 0 && ms > o.timeout_ms) { st = fail(OTS_ERR_TIMEOUT, "timeout after %d passes", done); break; }
+  }
+  if (st == OTS_ERR_NOT_CONVERGED) fail(st, "not converged after %d passes (src %.3e, cap %.3e)", done, r.src_residual, r.cap_violation);
+  r.iterations = done;
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  r.status = st;
+  if (rep) *rep = r;
+  return st;
+}
+
+// Flows pass: recompute the forward messages at the current duals, writing the aggregate
+// flows P_t for t = 2..T-1 (Corollary 7).
+static ots_status flows_pass(ots_problem *p) {
+  ots_status st = refresh_if_stale(p);
+  if (st) return st;
+  p->kernels_launched += 1 + (p->T - 2) + 2;
+  OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
+  for (int t = 2; t <= p->T - 1; ++t)
+    OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
+  OTS_CUDA(launch_boundary_flows(p->src.n, p->Lp, p->src.d_tri_l, p->src.d_tri_other, p->src.d_tri_logU, p->b_hi(2),
+                                 p->b_lo(2), p->src.d_flow, p->stream));
+  OTS_CUDA(launch_boundary_flows(p->snk.n, p->Lp, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
+                                 p->a_hi(p->T - 1), p->a_lo(p->T - 1), p->snk.d_flow, p->stream));
+  return OTS_OK;
+}
+
+ots_status ots_get_flows(ots_problem *p, int32_t t_begin, int32_t t_end, double *out) {
+  g_last_error.clear();
+  if (!p || !out) return fail(OTS_ERR_INVALID_ARG, "NULL argument");
+  if (t_begin < 1 || t_end > p->T + 1 || t_begin >= t_end) return fail(OTS_ERR_INVALID_ARG, "bad t range");
+  DeviceGuard guard(p->dev);
+  ots_status st = flows_pass(p);
+  if (st) return st;
+  const size_t S = p->S;
+  std::vector<double> sf(p->src.n), zf(p->snk.n);
+  for (int t = t_begin; t < t_end; ++t) {
+    double *row = out + (size_t)(t - t_begin) * S;
+    if (t >= 2 && t <= p->T - 1) {
+      OTS_CUDA(cudaMemcpyAsync(row, p->d_flow + (size_t)t * S, sizeof(double) * S, cudaMemcpyDeviceToHost, p->stream));
+      p->d2h_bytes += (long long)(sizeof(double) * S);
+    }
+  }
+  if (p->src.n) OTS_CUDA(cudaMemcpyAsync(sf.data(), p->src.d_flow, sizeof(double) * p->src.n, cudaMemcpyDeviceToHost, p->stream));
+  if (p->snk.n) OTS_CUDA(cudaMemcpyAsync(zf.data(), p->snk.d_flow, sizeof(double) * p->snk.n, cudaMemcpyDeviceToHost, p->stream));
+  p->d2h_bytes += (long long)(sizeof(double) * (p->src.n + p->snk.n));
+  OTS_CUDA(cudaStreamSynchronize(p->stream));
+  for (int t = t_begin; t < t_end; ++t) {
+    double *row = out + (size_t)(t - t_begin) * S;
+    if (t == 1 || t == p->T) {
+      std::fill(row, row + S, 0.0);
+      const Boundary &b = t == 1 ? p->src : p->snk;
+      const std::vector<double> &f = t == 1 ? sf : zf;
+      for (int q = 0; q < b.n; ++q) row[b.tri_state[q]] += f[q];
+    }
+  }
+  return OTS_OK;
+}
+
+ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_end, int32_t l_begin, int32_t l_end,
+                                   double *out) {
+  g_last_error.clear();
+  if (!p || !out) return fail(OTS_ERR_INVALID_ARG, "NULL argument");
+  if (t_begin < 1 || t_end > p->T + 1 || t_begin >= t_end) return fail(OTS_ERR_INVALID_ARG, "bad t range");
+  if (l_begin < 0 || l_end > p->L || l_begin >= l_end) return fail(OTS_ERR_INVALID_ARG, "bad commodity range");
+  DeviceGuard guard(p->dev);
+  ots_status st = refresh_if_stale(p);
+  if (st) return st;
+  const size_t S = p->S, nl = l_end - l_begin, blk = S * nl;
+  double *d_tmp = (double *)dev_alloc(p, sizeof(double) * blk);
+  if (!d_tmp) return fail(OTS_ERR_OOM, "device allocation failed");
+  std::vector<double> sf(p->src.n), zf(p->snk.n);
+  ots_status rc = OTS_OK;
+  auto check = [&](cudaError_t e) {
+    if (e != cudaSuccess && rc == OTS_OK) rc = fail(OTS_ERR_CUDA, "%s", cudaGetErrorString(e));
+  };
+  check(launch_boundary(bnd_args(p, true, 1), p->stream));
+  for (int t = 2; t <= p->T - 1 && rc == OTS_OK; ++t) {
+    if (t >= t_begin && t < t_end) {
+      // A_{t-1} is current here (written by the previous forward step of this pass)
+      check(launch_commodity_flows(p->S, p->Lp, l_begin, l_end, p->d_tail, p->d_head, p->a_hi(t - 1), p->a_lo(t - 1),
+                                   p->b_hi(t + 1), p->b_lo(t + 1), p->d_kl_hi, p->d_kl_lo, p->d_klc_hi, p->d_klc_lo,
+                                   p->d_logu + (size_t)t * S, d_tmp, p->stream));
+      check(cudaMemcpyAsync(out + (size_t)(t - t_begin) * blk, d_tmp, sizeof(double) * blk, cudaMemcpyDeviceToHost,
+                            p->stream));
+      check(cudaStreamSynchronize(p->stream));
+    }
+    check(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
+  }
+  check(launch_boundary_flows(p->src.n, p->Lp, p->src.d_tri_l, p->src.d_tri_other, p->src.d_tri_logU, p->b_hi(2),
+                              p->b_lo(2), p->src.d_flow, p->stream));
+  check(launch_boundary_flows(p->snk.n, p->Lp, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
+                              p->a_hi(p->T - 1), p->a_lo(p->T - 1), p->snk.d_flow, p->stream));
+  if (p->src.n) check(cudaMemcpyAsync(sf.data(), p->src.d_flow, sizeof(double) * p->src.n, cudaMemcpyDeviceToHost, p->stream));
+  if (p->snk.n) check(cudaMemcpyAsync(zf.data(), p->snk.d_flow, sizeof(double) * p->snk.n, cudaMemcpyDeviceToHost, p->stream));
+  check(cudaStreamSynchronize(p->stream));
+  dev_free(p, d_tmp);
+  if (rc) return rc;
+  for (int t : {1, p->T}) {
+    if (t < t_begin || t >= t_end) continue;
+    double *blkp = out + (size_t)(t - t_begin) * blk;
+    std::fill(blkp, blkp + blk, 0.0);
+    const Boundary &b = t == 1 ? p->src : p->snk;
+    const std::vector<double> &f = t == 1 ? sf : zf;
+    for (int q = 0; q < b.n; ++q) {
+      int l = b.tri_l[q];
+      if (l >= l_begin && l < l_end) blkp[(size_t)(l - l_begin) * S + b.tri_state[q]] += f[q];
+    }
+  }
+  return OTS_OK;
+}
+
+ots_status ots_get_duals(ots_problem *p, double *log_u, double *log_U01, double *log_U0T) {
+  g_last_error.clear();
+  if (!p) return fail(OTS_ERR_INVALID_ARG, "problem is NULL");
+  DeviceGuard guard(p->dev);
+  const size_t S = p->S;
+  std::vector<double> lu, su(p->src.n), zu(p->snk.n);
+  if (log_u) {
+    lu.resize((size_t)(p->T - 2) * S);
+    OTS_CUDA(cudaMemcpyAsync(lu.data(), p->d_logu + 2 * S, sizeof(double) * lu.size(), cudaMemcpyDeviceToHost, p->stream));
+  }
+  if (p->src.n) OTS_CUDA(cudaMemcpyAsync(su.data(), p->src.d_tri_logU, sizeof(double) * p->src.n, cudaMemcpyDeviceToHost, p->stream));
+  if (p->snk.n) OTS_CUDA(cudaMemcpyAsync(zu.data(), p->snk.d_tri_logU, sizeof(double) * p->snk.n, cudaMemcpyDeviceToHost, p->stream));
+  OTS_CUDA(cudaStreamSynchronize(p->stream));
+  if (log_u)
+    for (size_t k = 0; k < lu.size(); ++k) log_u[k] = lu[k] < -1e29 ? -INFINITY : lu[k] * kLn2;
+  if (log_U01)
+    for (size_t q = 0; q < p->src.input_to_tri.size(); ++q) log_U01[q] = su[p->src.input_to_tri[q]] * kLn2;
+  if (log_U0T)
+    for (size_t q = 0; q < p->snk.input_to_tri.size(); ++q) log_U0T[q] = zu[p->snk.input_to_tri[q]] * kLn2;
+  return OTS_OK;
+}
+
+ots_status ots_set_duals(ots_problem *p, const double *log_u, const double *log_U01, const double *log_U0T) {
+  g_last_error.clear();
+  if (!p || !log_u || !log_U01 || !log_U0T) return fail(OTS_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard guard(p->dev);
+  const size_t S = p->S;
+  std::vector<double> lu((size_t)(p->T - 2) * S), su(p->src.n, 0.0), zu(p->snk.n, 0.0);
+  for (size_t k = 0; k < lu.size(); ++k) {
+    if (std::isnan(log_u[k]) || log_u[k] > 0.0) return fail(OTS_ERR_INVALID_ARG, "log_u must be <= 0");
+    lu[k] = std::isinf(log_u[k]) ? -1e30 : log_u[k] * kInvLn2;
+  }
+  for (size_t q = 0; q < p->src.input_to_tri.size(); ++q) {
+    if (!std::isfinite(log_U01[q])) return fail(OTS_ERR_INVALID_ARG, "log_U01 must be finite");
+    su[p->src.input_to_tri[q]] = log_U01[q] * kInvLn2;
+  }
+  for (size_t q = 0; q < p->snk.input_to_tri.size(); ++q) {
+    if (!std::isfinite(log_U0T[q])) return fail(OTS_ERR_INVALID_ARG, "log_U0T must be finite");
+    zu[p->snk.input_to_tri[q]] = log_U0T[q] * kInvLn2;
+  }
+  OTS_CUDA(cudaMemcpyAsync(p->d_logu + 2 * S, lu.data(), sizeof(double) * lu.size(), cudaMemcpyHostToDevice, p->stream));
+  if (p->src.n) OTS_CUDA(cudaMemcpyAsync(p->src.d_tri_logU, su.data(), sizeof(double) * p->src.n, cudaMemcpyHostToDevice, p->stream));
+  if (p->snk.n) OTS_CUDA(cudaMemcpyAsync(p->snk.d_tri_logU, zu.data(), sizeof(double) * p->snk.n, cudaMemcpyHostToDevice, p->stream));
+  OTS_CUDA(cudaStreamSynchronize(p->stream));
+  p->stale = true;
+  return OTS_OK;
+}
+
+// Stream of the problem (for callers that time or order work around it).
+void *ots_problem_stream(const ots_problem *p) { return p ? (void *)p->stream : nullptr; }
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+"""Python binding of the C ABI in ``include/ots.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and does nothing but convert
+numpy arrays and option values into the C structures and back; every step of the solver
+runs in ``libots.so``.  The library must be built (``paper_2106_14485_gb300.build.build()``):
+there is no fallback, and a missing library raises at load time.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libots.so")
+
+OTS_OK, OTS_ERR_INVALID_ARG, OTS_ERR_INFEASIBLE, OTS_ERR_NOT_CONVERGED = 0, 1, 2, 3
+OTS_ERR_TIMEOUT, OTS_ERR_OOM, OTS_ERR_CUDA, OTS_ERR_NUMERIC = 4, 5, 6, 7
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_nodes", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+        ("edge_src", _i32p), ("edge_dst", _i32p), ("edge_cost", _f64p), ("edge_capacity", _f64p),
+        ("add_wait_loops", ctypes.c_int32),
+        ("wait_cost", _f64p), ("wait_capacity", _f64p), ("commodity_cost", _f64p),
+        ("T", ctypes.c_int32), ("L", ctypes.c_int32), ("eps", ctypes.c_double),
+        ("n_sources", ctypes.c_int32), ("src_commodity", _i32p), ("src_state", _i32p), ("src_mass", _f64p),
+        ("n_sinks", ctypes.c_int32), ("snk_commodity", _i32p), ("snk_state", _i32p), ("snk_mass", _f64p),
+        ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class ProblemStats(ctypes.Structure):
+    _fields_ = [("n_states", ctypes.c_int32), ("n_nodes", ctypes.c_int32), ("T", ctypes.c_int32),
+                ("L", ctypes.c_int32), ("padded_L", ctypes.c_int32), ("threads_per_node", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("kernels_per_pass", ctypes.c_int64),
+                ("kernels_launched", ctypes.c_int64), ("passes_total", ctypes.c_int64),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("timeout_ms", ctypes.c_double), ("warm_start", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("threads_per_node", ctypes.c_int32)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("src_residual", ctypes.c_double),
+                ("cap_violation", ctypes.c_double), ("dual_objective", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTED = ["ots_default_solve_opts", "ots_create_problem", "ots_sinkhorn_solve", "ots_iterate", "ots_get_flows",
+            "ots_get_commodity_flows", "ots_get_duals", "ots_set_duals", "ots_problem_info", "ots_last_pass_timing",
+            "ots_problem_stream", "ots_destroy_problem", "ots_status_string", "ots_last_error"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libots.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2106_14485_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.ots_default_solve_opts.argtypes = [ctypes.POINTER(SolveOpts)]
+    lib.ots_create_problem.argtypes = [ctypes.POINTER(ProblemDesc), ctypes.POINTER(P)]
+    lib.ots_sinkhorn_solve.argtypes = [P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)]
+    lib.ots_iterate.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(SolveReport)]
+    lib.ots_get_flows.argtypes = [P, ctypes.c_int32, ctypes.c_int32, _f64p]
+    lib.ots_get_commodity_flows.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f64p]
+    lib.ots_get_duals.argtypes = [P, _f64p, _f64p, _f64p]
+    lib.ots_set_duals.argtypes = [P, _f64p, _f64p, _f64p]
+    lib.ots_problem_info.argtypes = [P, ctypes.POINTER(ProblemStats)]
+    lib.ots_last_pass_timing.argtypes = [P, _f64p]
+    lib.ots_problem_stream.argtypes = [P]
+    lib.ots_problem_stream.restype = ctypes.c_void_p
+    lib.ots_destroy_problem.argtypes = [P]
+    lib.ots_destroy_problem.restype = None
+    lib.ots_status_string.argtypes = [ctypes.c_int]
+    lib.ots_status_string.restype = ctypes.c_char_p
+    lib.ots_last_error.argtypes = []
+    lib.ots_last_error.restype = ctypes.c_char_p
+    for name in ("ots_default_solve_opts", "ots_create_problem", "ots_sinkhorn_solve", "ots_iterate",
+                 "ots_get_flows", "ots_get_commodity_flows", "ots_get_duals", "ots_set_duals", "ots_problem_info",
+                 "ots_last_pass_timing"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class OTSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ots_status_string(code)}: {msg}")
+        self.code = code
+
+
+def _check(code: int) -> int:
+    if code != OTS_OK:
+        raise OTSError(code, load_library().ots_last_error().decode())
+    return code
+
+
+def ots_status_string(code: int) -> str:
+    return load_library().ots_status_string(int(code)).decode()
+
+
+def _ptr(a, ct):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+class Handle:
+    """Owns an ``ots_problem*`` plus the host arrays and callbacks it was created from."""
+
+    def __init__(self, ptr, keep, n_states, T, L, n_sources, n_sinks):
+        self.ptr = ptr
+        self._keep = keep
+        self.n_states, self.T, self.L = n_states, T, L
+        self.n_sources, self.n_sinks = n_sources, n_sinks
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                ots_destroy_problem(self)
+            except Exception:
+                pass
+
+
+def _torch_allocator(device: int):
+    import torch
+    live = {}
+
+    def alloc(nbytes, ctx):
+        try:
+            ptr = torch.cuda.caching_allocator_alloc(int(nbytes), device=device)
+        except Exception:
+            return None
+        live[ptr] = nbytes
+        return ptr
+
+    def free(ptr, ctx):
+        if ptr in live:
+            del live[ptr]
+            torch.cuda.caching_allocator_delete(ptr)
+
+    return ALLOC_FN(alloc), FREE_FN(free)
+
+
+def ots_create_problem(inst, device: int = 0, stream: int | None = None, allocator: str = "torch") -> Handle:
+    """Create a problem from an object with the attributes of ``instances.Instance``.
+
+    allocator: "torch" (PyTorch caching allocator) or "cuda" (cudaMalloc inside the library)."""
+    lib = load_library()
+    c = lambda x, dt: np.ascontiguousarray(x, dtype=dt)
+    arr = {
+        "edge_src": c(inst.edge_src, np.int32), "edge_dst": c(inst.edge_dst, np.int32),
+        "edge_cost": c(inst.edge_cost, np.float64), "edge_cap": c(inst.edge_cap, np.float64),
+        "wait_cost": c(inst.wait_cost, np.float64), "wait_cap": c(inst.wait_cap, np.float64),
+        "src_comm": c(inst.src_comm, np.int32), "src_state": c(inst.src_state, np.int32),
+        "src_mass": c(inst.src_mass, np.float64), "snk_comm": c(inst.snk_comm, np.int32),
+        "snk_state": c(inst.snk_state, np.int32), "snk_mass": c(inst.snk_mass, np.float64),
+    }
+    cc = getattr(inst, "commodity_cost", None)
+    if cc is not None:
+        arr["commodity_cost"] = c(cc, np.float64)
+    d = ProblemDesc()
+    d.n_nodes, d.n_edges = int(inst.n_nodes), int(len(arr["edge_src"]))
+    d.edge_src, d.edge_dst = _ptr(arr["edge_src"], ctypes.c_int32), _ptr(arr["edge_dst"], ctypes.c_int32)
+    d.edge_cost, d.edge_capacity = _ptr(arr["edge_cost"], ctypes.c_double), _ptr(arr["edge_cap"], ctypes.c_double)
+    d.add_wait_loops = 1
+    d.wait_cost, d.wait_capacity = _ptr(arr["wait_cost"], ctypes.c_double), _ptr(arr["wait_cap"], ctypes.c_double)
+    d.commodity_cost = _ptr(arr.get("commodity_cost"), ctypes.c_double)
+    d.T, d.L, d.eps = int(inst.T), int(inst.L), float(inst.eps)
+    d.n_sources = len(arr["src_comm"])
+    d.src_commodity, d.src_state = _ptr(arr["src_comm"], ctypes.c_int32), _ptr(arr["src_state"], ctypes.c_int32)
+    d.src_mass = _ptr(arr["src_mass"], ctypes.c_double)
+    d.n_sinks = len(arr["snk_comm"])
+    d.snk_commodity, d.snk_state = _ptr(arr["snk_comm"], ctypes.c_int32), _ptr(arr["snk_state"], ctypes.c_int32)
+    d.snk_mass = _ptr(arr["snk_mass"], ctypes.c_double)
+    d.device = int(device)
+    d.stream = stream
+    keep = [arr]
+    if allocator == "torch":
+        a, f = _torch_allocator(int(device))
+        d.alloc, d.free_fn = a, f
+        keep.append((a, f))
+    elif allocator != "cuda":
+        raise ValueError("allocator must be 'torch' or 'cuda'")
+    out = ctypes.c_void_p()
+    _check(lib.ots_create_problem(ctypes.byref(d), ctypes.byref(out)))
+    S = int(inst.n_nodes) + d.n_edges
+    return Handle(out, keep, S, d.T, d.L, d.n_sources, d.n_sinks)
+
+
+def ots_default_solve_opts() -> SolveOpts:
+    o = SolveOpts()
+    _check(load_library().ots_default_solve_opts(ctypes.byref(o)))
+    return o
+
+
+def ots_sinkhorn_solve(h: Handle, tol: float = 1e-6, max_iters: int = 100000, check_every: int = 10,
+                       timeout_ms: float = 0.0, warm_start: bool = False, use_graph: bool = True,
+                       threads_per_node: int = 0, raise_on_error: bool = True) -> dict:
+    o = ots_default_solve_opts()
+    o.tol, o.max_iters, o.check_every, o.timeout_ms = tol, max_iters, check_every, timeout_ms
+    o.warm_start, o.use_graph, o.threads_per_node = int(warm_start), int(use_graph), int(threads_per_node)
+    r = SolveReport()
+    code = load_library().ots_sinkhorn_solve(h.ptr, ctypes.byref(o), ctypes.byref(r))
+    if raise_on_error and code not in (OTS_OK,):
+        _check(code)
+    return r.as_dict()
+
+
+def ots_iterate(h: Handle, n: int, reset: bool = False) -> dict:
+    r = SolveReport()
+    _check(load_library().ots_iterate(h.ptr, int(n), int(reset), ctypes.byref(r)))
+    return r.as_dict()
+
+
+def ots_get_flows(h: Handle, t_begin: int = 1, t_end: int | None = None) -> np.ndarray:
+    t_end = h.T + 1 if t_end is None else t_end
+    out = np.empty((t_end - t_begin, h.n_states), np.float64)
+    _check(load_library().ots_get_flows(h.ptr, int(t_begin), int(t_end), _ptr(out, ctypes.c_double)))
+    return out
+
+
+def ots_get_commodity_flows(h: Handle, t_begin: int = 1, t_end: int | None = None, l_begin: int = 0,
+                            l_end: int | None = None) -> np.ndarray:
+    t_end = h.T + 1 if t_end is None else t_end
+    l_end = h.L if l_end is None else l_end
+    out = np.empty((t_end - t_begin, l_end - l_begin, h.n_states), np.float64)
+    _check(load_library().ots_get_commodity_flows(h.ptr, int(t_begin), int(t_end), int(l_begin), int(l_end),
+                                                  _ptr(out, ctypes.c_double)))
+    return out
+
+
+def ots_get_duals(h: Handle):
+    lu = np.empty((h.T - 2, h.n_states), np.float64)
+    u1 = np.empty(h.n_sources, np.float64)
+    uT = np.empty(h.n_sinks, np.float64)
+    _check(load_library().ots_get_duals(h.ptr, _ptr(lu, ctypes.c_double), _ptr(u1, ctypes.c_double),
+                                        _ptr(uT, ctypes.c_double)))
+    return lu, u1, uT
+
+
+def ots_set_duals(h: Handle, log_u, log_U01, log_U0T) -> None:
+    lu = np.ascontiguousarray(log_u, np.float64)
+    u1 = np.ascontiguousarray(log_U01, np.float64)
+    uT = np.ascontiguousarray(log_U0T, np.float64)
+    _check(load_library().ots_set_duals(h.ptr, _ptr(lu, ctypes.c_double), _ptr(u1, ctypes.c_double),
+                                        _ptr(uT, ctypes.c_double)))
+
+
+def ots_problem_info(h: Handle) -> dict:
+    st = ProblemStats()
+    _check(load_library().ots_problem_info(h.ptr, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+def ots_last_pass_timing(h: Handle) -> dict:
+    ms = np.zeros(4, np.float64)
+    _check(load_library().ots_last_pass_timing(h.ptr, _ptr(ms, ctypes.c_double)))
+    return {"source_ms": ms[0], "forward_ms": ms[1], "sink_ms": ms[2], "backward_ms": ms[3]}
+
+
+def ots_problem_stream(h: Handle) -> int:
+    return int(load_library().ots_problem_stream(h.ptr) or 0)
+
+
+def ots_destroy_problem(h: Handle) -> None:
+    if h.ptr:
+        load_library().ots_destroy_problem(h.ptr)
+        h.ptr = None

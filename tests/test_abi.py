@@ -1,0 +1,81 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads and exports every
+function that include/ots.h declares; the binding's structures match the header's layout."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ots.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ots_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("ots_create_problem", "ots_sinkhorn_solve", "ots_get_flows", "ots_get_duals",
+              "ots_destroy_problem", "ots_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2106_14485_gb300 import build, ots
+    build.build()
+    lib = ots.load_library()
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    assert set(declared_functions()) == set(ots.EXPORTED)
+
+
+def test_status_strings_need_no_gpu():
+    from paper_2106_14485_gb300 import ots
+    assert ots.ots_status_string(0) == "OTS_OK"
+    assert ots.ots_status_string(2) == "OTS_ERR_INFEASIBLE"
+    o = ots.ots_default_solve_opts()
+    assert o.tol == 1e-6 and o.max_iters == 100000 and o.check_every == 10 and o.use_graph == 1
+
+
+def test_struct_layout_matches_header():
+    """Compile a tiny C program against ots.h that prints sizeof/offsetof and compare."""
+    import subprocess
+    import tempfile
+    from paper_2106_14485_gb300 import ots
+    prog = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "ots.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(ots_problem_desc), offsetof(ots_problem_desc, eps),
+         offsetof(ots_problem_desc, stream), offsetof(ots_problem_desc, alloc_ctx));
+  printf("%zu %zu\n", sizeof(ots_solve_opts), offsetof(ots_solve_opts, threads_per_node));
+  printf("%zu %zu\n", sizeof(ots_solve_report), offsetof(ots_solve_report, status));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "p.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "p")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        out = subprocess.check_output([exe]).decode().split()
+    vals = list(map(int, out))
+    D, O, R = ots.ProblemDesc, ots.SolveOpts, ots.SolveReport
+    assert vals[0] == ctypes.sizeof(D) and vals[1] == D.eps.offset
+    assert vals[2] == D.stream.offset and vals[3] == D.alloc_ctx.offset
+    assert vals[4] == ctypes.sizeof(O) and vals[5] == O.threads_per_node.offset
+    assert vals[6] == ctypes.sizeof(R) and vals[7] == R.status.offset
+
+
+def test_oracle_is_not_imported_by_the_product():
+    """The product path never loads the oracle (it is test infrastructure)."""
+    pkg = os.path.join(ROOT, "paper_2106_14485_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", txt, flags=re.M), f
+                assert "libots_oracle" not in txt and "ots_oracle" not in txt, f
