@@ -106,37 +106,119 @@ __device__ void block_sum2_last(double v0, double v1, double *partials, unsigned
   }
 }
 
-// Group-wide (G threads) merge of log-sum-exp pairs.  For G <= 32 the group is a slice of a
-// warp; for G > 32 the block is one node and partials go through shared memory.
-template <int G>
-__device__ __forceinline__ void group_lse(float &m, float &s, float *sm_m, float *sm_s) {
+// Group-wide (G threads) reductions of KB values at once.  For G <= 32 the group is a slice
+// of one warp (shuffles only); for G > 32 the block is one node and the warps exchange their
+// partial results through shared memory (sm holds BS/32 x KB floats).
+template <int G, int KB, bool MAX>
+__device__ __forceinline__ void group_reduce(float (&x)[KB], float *sm) {
   if (G == 1) return;
-  if (G <= 32) {
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned base = lane & ~(unsigned)(G - 1);
-    const unsigned mask = (G >= 32) ? 0xffffffffu : (((1u << (G & 31)) - 1u) << base);
+  const unsigned lane = threadIdx.x & 31u;
+  constexpr int W = G < 32 ? G : 32;
+  const unsigned base = lane & ~(unsigned)(W - 1);
+  const unsigned mask = (W >= 32) ? 0xffffffffu : (((1u << (W & 31)) - 1u) << base);
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      float om = __shfl_xor_sync(mask, m, o, 32);
-      float os = __shfl_xor_sync(mask, s, o, 32);
-      lse_merge(m, s, om, os);
+  for (int o = W / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      const float y = __shfl_xor_sync(mask, x[k], o, 32);
+      x[k] = MAX ? fmaxf(x[k], y) : x[k] + y;
     }
-  } else {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      float om = __shfl_xor_sync(0xffffffffu, m, o);
-      float os = __shfl_xor_sync(0xffffffffu, s, o);
-      lse_merge(m, s, om, os);
-    }
-    const int wid = threadIdx.x >> 5;
-    __syncthreads();                       // previous readers of sm_* are done
-    if ((threadIdx.x & 31) == 0) { sm_m[wid] = m; sm_s[wid] = s; }
-    __syncthreads();
-    m = sm_m[0];
-    s = sm_s[0];
-#pragma unroll
-    for (int w = 1; w < G / 32; ++w) lse_merge(m, s, sm_m[w], sm_s[w]);
   }
+  if (G > 32) {
+    constexpr int NW = G / 32;
+    const int wid = threadIdx.x >> 5;
+    __syncthreads();                              // earlier readers of sm are done
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < KB; ++k) sm[k * NW + wid] = x[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      float r = sm[k * NW];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) r = MAX ? fmaxf(r, sm[k * NW + w]) : r + sm[k * NW + w];
+      x[k] = r;
+    }
+  }
+}
+
+// Gather the thread's slice of up to KB input rows (row index nbr[j0 + k]) and, with
+// per-commodity costs, fold log2 K_L[., state] into them.
+template <int G, int C, int KB, bool PC>
+__device__ __forceinline__ void gather_rows(const StepArgs &a, int j0, int nb, int g, int (&st)[KB],
+                                            float (&xh)[KB][C][4], float (&xl)[KB][C][4]) {
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    if (k < nb) {
+      st[k] = a.state[j0 + k];
+      const size_t row = (size_t)a.nbr[j0 + k] * a.Lp;
+#pragma unroll
+      for (int c = 0; c < C; ++c) load4(a.x_hi + row + 4 * (c * G + g), a.x_lo + row + 4 * (c * G + g), xh[k][c], xl[k][c]);
+    } else {
+      st[k] = 0;
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { xh[k][c][q] = kNeg; xl[k][c][q] = 0.f; }
+    }
+  }
+  if (PC) {
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      if (k < nb) {
+        const size_t row = (size_t)st[k] * a.Lp;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          float ch[4], cl[4];
+          load4(a.klc_hi + row + 4 * (c * G + g), a.klc_lo + row + 4 * (c * G + g), ch, cl);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float s, e;
+            two_sum(xh[k][c][q], ch[q], s, e);
+            xh[k][c][q] = s;
+            xl[k][c][q] += e + cl[q];
+          }
+        }
+      }
+    }
+  }
+}
+
+// Accumulate one batch of terms x[k] + w[k] into the running log-sum-exp (M, acc) of each
+// commodity: exact float-float terms, batch maximum first, one ex2 per term.
+template <int C, int KB>
+__device__ __forceinline__ void aggregate_batch(int nb, float (&xh)[KB][C][4], const float (&xl)[KB][C][4],
+                                                const float (&wh)[KB], const float (&wl)[KB], float (&M)[C][4],
+                                                float (&acc)[C][4]) {
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float sv[KB], ev[KB];
+      float m = 2.f * kNeg;
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        float s, e;
+        two_sum(xh[k][c][q], wh[k], s, e);
+        sv[k] = s;
+        ev[k] = e + (xl[k][c][q] + wl[k]);
+        if (k < nb) m = fmaxf(m, s);
+      }
+      if (m < kNegThresh) continue;               // nothing reachable in this batch
+      float sum = 0.f;
+#pragma unroll
+      for (int k = 0; k < KB; ++k)
+        if (k < nb && sv[k] > kNegThresh) sum += ex2((sv[k] - m) + ev[k]);
+      // merge (m, sum) into (M, acc)
+      const float Mo = M[c][q];
+      if (m > Mo) {
+        acc[c][q] = fmaf(acc[c][q], ex2(Mo - m), sum);
+        M[c][q] = m;
+      } else {
+        acc[c][q] = fmaf(sum, ex2(m - Mo), acc[c][q]);
+      }
+    }
 }
 
 }  // namespace
@@ -150,11 +232,14 @@ __device__ __forceinline__ void group_lse(float &m, float &s, float *sm_m, float
 template <int G>
 struct BlockOf { static constexpr int value = G > 32 ? G : kBlock; };
 
+constexpr int kBatch = 4;   // in-states gathered per batch
+
 template <int G, int C, bool PC>
-__global__ void __launch_bounds__(BlockOf<G>::value) k_forward(const StepArgs a) {
+__global__ void __launch_bounds__(BlockOf<G>::value, 2 * 256 / BlockOf<G>::value) k_forward(const StepArgs a) {
   constexpr int BS = BlockOf<G>::value;
   constexpr int NPB = BS / G;  // nodes per block (1 when G > 32)
-  __shared__ float sm_m[BS / 32 > 0 ? BS / 32 : 1], sm_s[BS / 32 > 0 ? BS / 32 : 1];
+  constexpr int KB = kBatch;
+  __shared__ float sm[(BS / 32 > 0 ? BS / 32 : 1) * KB];
   const int g = threadIdx.x % G;
   const int v = blockIdx.x * NPB + threadIdx.x / G;
   const bool active = v < a.V;
@@ -168,123 +253,112 @@ __global__ void __launch_bounds__(BlockOf<G>::value) k_forward(const StepArgs a)
 #pragma unroll
   for (int c = 0; c < C; ++c)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) { M[c][k] = 2.f * kNeg; acc[c][k] = 0.f; }
+    for (int q = 0; q < 4; ++q) { M[c][q] = 2.f * kNeg; acc[c][q] = 0.f; }
 
   double viol = 0.0, dual = 0.0;
   const int jb = active ? a.ptr[v] : 0;
   const int je = active ? a.ptr[v + 1] : 0;
-  // G > 32: the block is one node, trip counts are uniform across the block.
-  for (int jj = jb; jj < je; ++jj) {
-    const int st = a.state[jj];
-    const size_t rowy = (size_t)a.nbr[jj] * a.Lp;
-    float ah[C][4], al[C][4];
-#pragma unroll
-    for (int c = 0; c < C; ++c) load4(a.x_hi + rowy + 4 * (c * G + g), a.x_lo + rowy + 4 * (c * G + g), ah[c], al[c]);
-    float ch[C][4], cl[C][4];
-    if (PC) {
-      const size_t rows = (size_t)st * a.Lp;
-#pragma unroll
-      for (int c = 0; c < C; ++c) load4(a.klc_hi + rows + 4 * (c * G + g), a.klc_lo + rows + 4 * (c * G + g), ch[c], cl[c]);
-      // fold the per-commodity cost into the input once: A_{t-1}[y] + log2 K_L[., st]
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float s, e;
-          two_sum(ah[c][k], ch[c][k], s, e);
-          ah[c][k] = s;
-          al[c][k] += e + cl[c][k];
-        }
-    }
-    // (1) column log-sum-exp over commodities of A_{t-1}[y] (+ K_L) + B_{t+1}[v]
-    float pm = 2.f * kNeg, ps = 0.f;
-    {
-      float sv[C][4], ev[C][4];
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float s, e;
-          two_sum(ah[c][k], bh[c][k], s, e);
-          sv[c][k] = s;
-          ev[c][k] = e + (al[c][k] + bl[c][k]);
-          pm = fmaxf(pm, s);
-        }
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) ps += ex2((sv[c][k] - pm) + ev[c][k]);
-      // all of this thread's terms at log 0: the error parts carry unrelated finite values
-      // (two_sum(kNeg, x) = (kNeg, x)) and must not count
-      if (pm < kNegThresh) ps = 0.f;
-    }
-    group_lse<G>(pm, ps, sm_m, sm_s);
-    // col = log2 of the column sum (hatPsi_t .* Psi_t .* K_L)^T 1 at state st
-    float col_hi, col_lo;
-    lse_finish(pm, ps, col_hi, col_lo);
-    const float klh = PC ? 0.f : a.kl_hi[st], kll = PC ? 0.f : a.kl_lo[st];
-    if (!PC && col_hi > kNegThresh) {
-      float s, e;
-      two_sum(col_hi, klh, s, e);
-      col_hi = s;
-      col_lo += e + kll;
-    }
+  // G > 32: the block is one node, so trip counts are uniform across the block.
+  for (int j0 = jb; j0 < je; j0 += KB) {
+    const int nb = min(KB, je - j0);
+    int st[KB];
+    float xh[KB][C][4], xl[KB][C][4];
+    gather_rows<G, C, KB, PC>(a, j0, nb, g, st, xh, xl);
 
-    // (2) capacity update of state st (Algorithm 2), or flows of the current iterate
-    float w_hi, w_lo;
-    if (a.mode == 0) {
-      const double cap = a.cap[st];
-      float lu_hi = 0.f, lu_lo = 0.f;
-      if (isfinite(cap) && col_hi > kNegThresh) {
-        if (a.logd_hi[st] < kNegThresh) {
-          lu_hi = kNeg;                    // d = 0: the state is closed
-        } else {
-          // log2 u = min(log2 d - col, 0) in float-float
-          float s1, e1, s2, e2;
-          two_sum(a.logd_hi[st], -col_hi, s1, e1);
-          e1 += a.logd_lo[st] - col_lo;
-          two_sum(s1, e1, s2, e2);
-          if (s2 < 0.f) { lu_hi = s2; lu_lo = e2; }
-        }
-      }
-      if (lu_hi < kNegThresh) {
-        w_hi = kNeg; w_lo = 0.f;
-      } else {
-        two_sum(klh, lu_hi, w_hi, w_lo);
-        w_lo += kll + lu_lo;
-      }
-      if (g == 0) {
-        const double lu_old = a.logu_t[st];
-        if (col_hi > kNegThresh) {
-          const double p_old = exp2(lu_old + (double)col_hi + (double)col_lo);
-          if (p_old > cap) viol += p_old - cap;
-        }
-        if (col_hi != col_hi || col_lo != col_lo) viol = __longlong_as_double(0x7ff8000000000000LL);  // NaN: reported
-        const double lu_new = lu_hi < kNegThresh ? -1e30 : (double)lu_hi + (double)lu_lo;
-        if (isfinite(cap) && cap > 0.0) dual += cap * lu_new;
-        a.logu_t[st] = lu_new;
-        a.w_hi_t[st] = w_hi;
-        a.w_lo_t[st] = w_lo;
-      }
-    } else {
-      w_hi = a.w_hi_t[st];
-      w_lo = a.w_lo_t[st];
-      if (g == 0) {
-        a.flow_t[st] = col_hi > kNegThresh && w_hi > kNegThresh
-                           ? exp2(a.logu_t[st] + (double)col_hi + (double)col_lo) : 0.0;
-      }
+    // (1) column log-sum-exp over commodities of A_{t-1}[y] (+ K_L) + B_{t+1}[v], for each
+    //     in-state of the batch: group maximum of the rounded sums, then group sum.
+    float cm[KB], cs[KB];
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      float m = 2.f * kNeg;
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) m = fmaxf(m, __fadd_rn(xh[k][c][q], bh[c][q]));
+      cm[k] = m;
     }
+    group_reduce<G, KB, true>(cm, sm);
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      float sum = 0.f;
+      if (cm[k] > kNegThresh) {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float s, e;
+            two_sum(xh[k][c][q], bh[c][q], s, e);
+            if (s > kNegThresh) sum += ex2((s - cm[k]) + (e + (xl[k][c][q] + bl[c][q])));
+          }
+      }
+      cs[k] = sum;
+    }
+    group_reduce<G, KB, false>(cs, sm);
 
-    // (3) A_t[v] accumulates A_{t-1}[y] + W_t[st]   (online log-sum-exp over the in-states)
+    // (2) capacity update of each in-state (Algorithm 2), or flows of the current iterate
+    float wh[KB], wl[KB];
 #pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < KB; ++k) {
+      wh[k] = kNeg;
+      wl[k] = 0.f;
+      if (k >= nb) continue;
+      const int sk = st[k];
+      float col_hi, col_lo;
+      lse_finish(cm[k], cs[k], col_hi, col_lo);   // log2 of (hatPsi_t .* Psi_t (.* K_L))^T 1
+      const float klh = PC ? 0.f : a.kl_hi[sk], kll = PC ? 0.f : a.kl_lo[sk];
+      if (!PC && col_hi > kNegThresh) {
         float s, e;
-        two_sum(ah[c][k], w_hi, s, e);
-        e += al[c][k] + w_lo;
-        lse_push(M[c][k], acc[c][k], s, e);
+        two_sum(col_hi, klh, s, e);
+        col_hi = s;
+        col_lo += e + kll;
       }
+      if (a.mode == 0) {
+        const double cap = a.cap[sk];
+        float lu_hi = 0.f, lu_lo = 0.f;
+        if (isfinite(cap) && col_hi > kNegThresh) {
+          if (a.logd_hi[sk] < kNegThresh) {
+            lu_hi = kNeg;                            // d = 0: the state is closed
+          } else {
+            // log2 u = min(log2 d - col, 0) in float-float
+            float s1, e1, s2, e2;
+            two_sum(a.logd_hi[sk], -col_hi, s1, e1);
+            e1 += a.logd_lo[sk] - col_lo;
+            two_sum(s1, e1, s2, e2);
+            if (s2 < 0.f) { lu_hi = s2; lu_lo = e2; }
+          }
+        }
+        if (lu_hi > kNegThresh) {
+          two_sum(klh, lu_hi, wh[k], wl[k]);
+          wl[k] += kll + lu_lo;
+        }
+        if (g == 0) {
+          const double lu_old = a.logu_t[sk];
+          if (col_hi > kNegThresh && isfinite(cap)) {
+            // excess (P_t - d)_+ with the old u_t; exact FP64 only near or above capacity
+            const float q = (float)lu_old + col_hi - a.logd_hi[sk];
+            if (q > -1e-3f) {
+              const double p_old = exp2(lu_old + (double)col_hi + (double)col_lo);
+              if (p_old > cap) viol += p_old - cap;
+            }
+          }
+          if (col_hi != col_hi || col_lo != col_lo) viol = __longlong_as_double(0x7ff8000000000000LL);  // NaN
+          const double lu_new = lu_hi < kNegThresh ? -1e30 : (double)lu_hi + (double)lu_lo;
+          if (isfinite(cap) && cap > 0.0) dual += cap * lu_new;
+          a.logu_t[sk] = lu_new;
+          a.w_hi_t[sk] = wh[k];
+          a.w_lo_t[sk] = wl[k];
+        }
+      } else {
+        wh[k] = a.w_hi_t[sk];
+        wl[k] = a.w_lo_t[sk];
+        if (g == 0)
+          a.flow_t[sk] = col_hi > kNegThresh && wh[k] > kNegThresh
+                             ? exp2(a.logu_t[sk] + (double)col_hi + (double)col_lo) : 0.0;
+      }
+    }
+
+    // (3) A_t[v] accumulates A_{t-1}[y] + W_t[state] over the batch
+    aggregate_batch<C, KB>(nb, xh, xl, wh, wl, M, acc);
   }
 
   if (active) {
@@ -292,7 +366,7 @@ __global__ void __launch_bounds__(BlockOf<G>::value) k_forward(const StepArgs a)
     for (int c = 0; c < C; ++c) {
       float oh[4], ol[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) lse_finish(M[c][k], acc[c][k], oh[k], ol[k]);
+      for (int q = 0; q < 4; ++q) lse_finish(M[c][q], acc[c][q], oh[q], ol[q]);
       store4(a.out_hi + rowv + 4 * (c * G + g), a.out_lo + rowv + 4 * (c * G + g), oh, ol);
     }
   }
@@ -303,9 +377,10 @@ __global__ void __launch_bounds__(BlockOf<G>::value) k_forward(const StepArgs a)
 // backward step t (t = T-1..2): B_t[v] = LSE_{j: tail j = v} (B_{t+1}[head j] + W_t[j] (+ K_L))
 // ------------------------------------------------------------------------------------
 template <int G, int C, bool PC>
-__global__ void __launch_bounds__(BlockOf<G>::value) k_backward(const StepArgs a) {
+__global__ void __launch_bounds__(BlockOf<G>::value, 3 * 256 / BlockOf<G>::value) k_backward(const StepArgs a) {
   constexpr int BS = BlockOf<G>::value;
   constexpr int NPB = BS / G;
+  constexpr int KB = kBatch;
   const int g = threadIdx.x % G;
   const int v = blockIdx.x * NPB + threadIdx.x / G;
   if (v >= a.V) return;
@@ -313,46 +388,27 @@ __global__ void __launch_bounds__(BlockOf<G>::value) k_backward(const StepArgs a
 #pragma unroll
   for (int c = 0; c < C; ++c)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) { M[c][k] = 2.f * kNeg; acc[c][k] = 0.f; }
+    for (int q = 0; q < 4; ++q) { M[c][q] = 2.f * kNeg; acc[c][q] = 0.f; }
   const int jb = a.ptr[v], je = a.ptr[v + 1];
-  for (int jj = jb; jj < je; ++jj) {
-    const int st = a.state[jj];
-    const size_t rowx = (size_t)a.nbr[jj] * a.Lp;
-    const float w_hi = a.w_hi_t[st], w_lo = a.w_lo_t[st];
-    float xh[C][4], xl[C][4];
+  for (int j0 = jb; j0 < je; j0 += KB) {
+    const int nb = min(KB, je - j0);
+    int st[KB];
+    float xh[KB][C][4], xl[KB][C][4];
+    gather_rows<G, C, KB, PC>(a, j0, nb, g, st, xh, xl);
+    float wh[KB], wl[KB];
 #pragma unroll
-    for (int c = 0; c < C; ++c) load4(a.x_hi + rowx + 4 * (c * G + g), a.x_lo + rowx + 4 * (c * G + g), xh[c], xl[c]);
-    if (PC) {
-      const size_t rows = (size_t)st * a.Lp;
-      float ch[C][4], cl[C][4];
-#pragma unroll
-      for (int c = 0; c < C; ++c) load4(a.klc_hi + rows + 4 * (c * G + g), a.klc_lo + rows + 4 * (c * G + g), ch[c], cl[c]);
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float s, e;
-          two_sum(xh[c][k], ch[c][k], s, e);
-          xh[c][k] = s;
-          xl[c][k] += e + cl[c][k];
-        }
+    for (int k = 0; k < KB; ++k) {
+      wh[k] = k < nb ? a.w_hi_t[st[k]] : kNeg;
+      wl[k] = k < nb ? a.w_lo_t[st[k]] : 0.f;
     }
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        float s, e;
-        two_sum(xh[c][k], w_hi, s, e);
-        e += xl[c][k] + w_lo;
-        lse_push(M[c][k], acc[c][k], s, e);
-      }
+    aggregate_batch<C, KB>(nb, xh, xl, wh, wl, M, acc);
   }
   const size_t rowo = (size_t)v * a.Lp;
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     float oh[4], ol[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) lse_finish(M[c][k], acc[c][k], oh[k], ol[k]);
+    for (int q = 0; q < 4; ++q) lse_finish(M[c][q], acc[c][q], oh[q], ol[q]);
     store4(a.out_hi + rowo + 4 * (c * G + g), a.out_lo + rowo + 4 * (c * G + g), oh, ol);
   }
 }
