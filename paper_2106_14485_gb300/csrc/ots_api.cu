@@ -5,7 +5,6 @@
 // triples of R01 and R0T, uploads everything into one device arena, captures one pass of
 // Algorithm 2 as a CUDA graph, and runs the passes until the convergence measures reach
 // the tolerance.
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,17 +28,16 @@ cudaError_t launch_boundary(const BndArgs &b, cudaStream_t s);
 int boundary_grid(int n_seg);
 cudaError_t launch_pass_begin(DevStats *st, cudaStream_t s);
 cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, cudaStream_t s);
-cudaError_t launch_init_weights(int S, int T, const float *kl_hi, const float *kl_lo, double *logu, float *w_hi,
-                                float *w_lo, cudaStream_t s);
-cudaError_t launch_weights_from_logu(int S, int T, const float *kl_hi, const float *kl_lo, const double *logu,
-                                     float *w_hi, float *w_lo, cudaStream_t s);
-cudaError_t launch_fill_panel(size_t n, float *hi, __half *lo, cudaStream_t s);
-cudaError_t launch_commodity_flows(int S, int Lp, int l0, int l1, const int *tail, const int *head, const float *a_hi,
-                                   const __half *a_lo, const float *b_hi, const __half *b_lo, const float *kl_hi,
-                                   const float *kl_lo, const float *klc_hi, const __half *klc_lo, const double *logu_t,
-                                   double *out, cudaStream_t s);
-cudaError_t launch_boundary_flows(int n, int Lp, const int *tri_l, const int *tri_node_other, const double *tri_logU,
-                                  const float *msg_hi, const __half *msg_lo, double *out, cudaStream_t s);
+cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, double *logu,
+                           float *w_hi, float *w_lo, int reset, cudaStream_t s);
+cudaError_t launch_fill_panel(size_t n, float *hi, lo_t *lo, cudaStream_t s);
+cudaError_t launch_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
+                                   const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
+                                   const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
+                                   const double *logu_t, double *out, cudaStream_t s);
+cudaError_t launch_boundary_flows(int n, int Lp, QScale qs, const int *tri_l, const int *tri_node_other,
+                                  const double *tri_logU, const float *msg_hi, const lo_t *msg_lo, double *out,
+                                  cudaStream_t s);
 }  // namespace ots
 
 using namespace ots;
@@ -102,6 +100,7 @@ struct ots_problem {
 
   int V = 0, E = 0, S = 0, L = 0, T = 0, G = 1, C = 1, Lp = 4;
   double eps = 1.0, mass = 0.0;
+  QScale qs{};                                 // quantum of the message hi parts
   bool pc = false;
 
   std::vector<int> tail, head;
@@ -116,14 +115,14 @@ struct ots_problem {
   float *d_kl_hi = nullptr, *d_kl_lo = nullptr, *d_logd_hi = nullptr, *d_logd_lo = nullptr;
   double *d_cap = nullptr;
   float *d_klc_hi = nullptr;
-  __half *d_klc_lo = nullptr;
+  lo_t *d_klc_lo = nullptr;
   float *d_w_hi = nullptr, *d_w_lo = nullptr;  // [T+1][S]
   double *d_logu = nullptr;                    // [T+1][S]
   double *d_flow = nullptr;                    // [T+1][S]
   float *d_a_hi[3] = {nullptr, nullptr, nullptr};
-  __half *d_a_lo[3] = {nullptr, nullptr, nullptr};
+  lo_t *d_a_lo[3] = {nullptr, nullptr, nullptr};
   float *d_b_hi = nullptr;                     // [(T-1)][V][Lp], row t-2
-  __half *d_b_lo = nullptr;
+  lo_t *d_b_lo = nullptr;
   DevStats *d_stats = nullptr;
   PassReport *d_report = nullptr;
   double *d_partials = nullptr;
@@ -139,9 +138,9 @@ struct ots_problem {
 
   size_t panel() const { return (size_t)V * Lp; }
   float *a_hi(int t) { return t == 1 ? d_a_hi[0] : d_a_hi[1 + (t & 1)]; }
-  __half *a_lo(int t) { return t == 1 ? d_a_lo[0] : d_a_lo[1 + (t & 1)]; }
+  lo_t *a_lo(int t) { return t == 1 ? d_a_lo[0] : d_a_lo[1 + (t & 1)]; }
   float *b_hi(int t) { return d_b_hi + (size_t)(t - 2) * panel(); }
-  __half *b_lo(int t) { return d_b_lo + (size_t)(t - 2) * panel(); }
+  lo_t *b_lo(int t) { return d_b_lo + (size_t)(t - 2) * panel(); }
 };
 
 namespace {
@@ -184,6 +183,7 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   StepArgs a{};
   a.V = p->V;
   a.Lp = p->Lp;
+  a.qs = p->qs;
   if (fwd) {
     a.ptr = p->d_in_ptr; a.state = p->d_in_state; a.nbr = p->d_in_nbr;
     a.x_hi = p->a_hi(t - 1); a.x_lo = p->a_lo(t - 1);
@@ -213,6 +213,7 @@ BndArgs bnd_args(ots_problem *p, bool source, int mode) {
   Boundary &b = source ? p->src : p->snk;
   BndArgs a{};
   a.n_seg = b.n_seg;
+  a.qs = p->qs;
   a.seg_ptr = b.d_seg_ptr; a.seg_node = b.d_seg_node; a.seg_l = b.d_seg_l;
   a.tri_node_other = b.d_tri_other;
   a.tri_R = b.d_tri_R; a.tri_logR = b.d_tri_logR; a.tri_logU = b.d_tri_logU;
@@ -281,8 +282,8 @@ ots_status build_pass_graph(ots_problem *p) {
 // supports) and recompute the backward messages.
 ots_status reset_duals(ots_problem *p) {
   p->kernels_launched += 2;
-  OTS_CUDA(launch_init_weights(p->S, p->T, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo, p->d_logu,
-                               p->d_w_hi, p->d_w_lo, p->stream));
+  OTS_CUDA(launch_weights(p->S, p->T, p->qs, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo, p->d_logu,
+                          p->d_w_hi, p->d_w_lo, 1, p->stream));
   if (p->src.n) OTS_CUDA(cudaMemsetAsync(p->src.d_tri_logU, 0, sizeof(double) * p->src.n, p->stream));
   if (p->snk.n) OTS_CUDA(cudaMemsetAsync(p->snk.d_tri_logU, 0, sizeof(double) * p->snk.n, p->stream));
   OTS_CUDA(cudaMemsetAsync(p->d_report, 0, sizeof(PassReport), p->stream));
@@ -296,8 +297,8 @@ ots_status reset_duals(ots_problem *p) {
 ots_status refresh_if_stale(ots_problem *p) {
   if (!p->stale) return OTS_OK;
   p->kernels_launched += 2;
-  OTS_CUDA(launch_weights_from_logu(p->S, p->T, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo, p->d_logu,
-                                    p->d_w_hi, p->d_w_lo, p->stream));
+  OTS_CUDA(launch_weights(p->S, p->T, p->qs, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo, p->d_logu,
+                          p->d_w_hi, p->d_w_lo, 0, p->stream));
   OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
   ots_status st = enqueue_backward_sweep(p);
   if (st) return st;
@@ -610,19 +611,35 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
     else if (std::isinf(dd)) { logd_hi[s] = 0.f; logd_lo[s] = 0.f; }
     else split_ff(std::log2(dd), logd_hi[s], logd_lo[s]);
   }
+  // quantum of the hi parts: the magnitude of any message is bounded by about (T+1) times the
+  // largest per-interval cost in bits; q = 2^k with that bound below 2^24 q keeps hi sums exact
+  {
+    double cmax = 0.0;
+    for (int s = 0; s < p->S; ++s) cmax = std::max(cmax, std::fabs((double)kl_hi[s]));
+    if (d->commodity_cost)
+      for (size_t k = 0; k < (size_t)p->L * p->S; ++k) cmax = std::max(cmax, std::fabs(d->commodity_cost[k]) / d->eps * kInvLn2);
+    const double bound = (p->T + 1.0) * std::max(cmax, 1.0) + 256.0;
+    int k = (int)std::ceil(std::log2(bound)) - 23;
+    k = std::min(std::max(k, -40), -2);
+    p->qs.q = std::ldexp(1.0f, k);
+    p->qs.inv_q = std::ldexp(1.0f, -k);
+    p->qs.lo_unit = std::ldexp(1.0f, k - 16);
+    p->qs.lo_inv = std::ldexp(1.0f, 16 - k);
+  }
   std::vector<float> klc_hi;
-  std::vector<__half> klc_lo;
+  std::vector<lo_t> klc_lo;
   if (p->pc) {
     klc_hi.assign((size_t)p->S * p->Lp, kNeg);
-    klc_lo.assign((size_t)p->S * p->Lp, __float2half(0.f));
+    klc_lo.assign((size_t)p->S * p->Lp, kLoZero);
+    const double q = p->qs.q;
     for (int l = 0; l < p->L; ++l)
       for (int s = 0; s < p->S; ++s) {
         double c = d->commodity_cost[(size_t)l * p->S + s];
         if (!std::isfinite(c)) return bail(fail(OTS_ERR_INVALID_ARG, "commodity_cost must be finite"));
-        float h, lo;
-        split_ff(-c / d->eps * kInvLn2, h, lo);
-        klc_hi[(size_t)s * p->Lp + l] = h;
-        klc_lo[(size_t)s * p->Lp + l] = __float2half_rn(lo);
+        const double x = -c / d->eps * kInvLn2;
+        const double h = std::nearbyint(x / q) * q;
+        klc_hi[(size_t)s * p->Lp + l] = (float)h;
+        klc_lo[(size_t)s * p->Lp + l] = (lo_t)((int)std::nearbyint((x - h) * 65536.0 / q) + 32768);
       }
   }
 
@@ -674,12 +691,12 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   size_t o_tail = cv.take<int>(S), o_head = cv.take<int>(S);
   size_t o_kl_hi = cv.take<float>(S), o_kl_lo = cv.take<float>(S), o_ld_hi = cv.take<float>(S), o_ld_lo = cv.take<float>(S);
   size_t o_cap = cv.take<double>(S);
-  size_t o_klc_hi = p->pc ? cv.take<float>(S * p->Lp) : 0, o_klc_lo = p->pc ? cv.take<__half>(S * p->Lp) : 0;
+  size_t o_klc_hi = p->pc ? cv.take<float>(S * p->Lp) : 0, o_klc_lo = p->pc ? cv.take<lo_t>(S * p->Lp) : 0;
   size_t o_w_hi = cv.take<float>((T + 1) * S), o_w_lo = cv.take<float>((T + 1) * S);
   size_t o_logu = cv.take<double>((T + 1) * S), o_flow = cv.take<double>((T + 1) * S);
   size_t o_a_hi[3], o_a_lo[3];
-  for (int k = 0; k < 3; ++k) { o_a_hi[k] = cv.take<float>(panel); o_a_lo[k] = cv.take<__half>(panel); }
-  size_t o_b_hi = cv.take<float>((T - 1) * panel), o_b_lo = cv.take<__half>((T - 1) * panel);
+  for (int k = 0; k < 3; ++k) { o_a_hi[k] = cv.take<float>(panel); o_a_lo[k] = cv.take<lo_t>(panel); }
+  size_t o_b_hi = cv.take<float>((T - 1) * panel), o_b_lo = cv.take<lo_t>((T - 1) * panel);
   size_t o_stats = cv.take<DevStats>(1), o_report = cv.take<PassReport>(1);
   size_t o_partials = cv.take<double>(2 * (size_t)max_grid), o_counter = cv.take<unsigned int>(4);
   struct BOff { size_t seg_ptr, seg_node, seg_l, other, l, R, logR, logU, flow; } bo[2];
@@ -702,11 +719,11 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   p->d_kl_hi = (float *)at(o_kl_hi); p->d_kl_lo = (float *)at(o_kl_lo);
   p->d_logd_hi = (float *)at(o_ld_hi); p->d_logd_lo = (float *)at(o_ld_lo);
   p->d_cap = (double *)at(o_cap);
-  if (p->pc) { p->d_klc_hi = (float *)at(o_klc_hi); p->d_klc_lo = (__half *)at(o_klc_lo); }
+  if (p->pc) { p->d_klc_hi = (float *)at(o_klc_hi); p->d_klc_lo = (lo_t *)at(o_klc_lo); }
   p->d_w_hi = (float *)at(o_w_hi); p->d_w_lo = (float *)at(o_w_lo);
   p->d_logu = (double *)at(o_logu); p->d_flow = (double *)at(o_flow);
-  for (int k = 0; k < 3; ++k) { p->d_a_hi[k] = (float *)at(o_a_hi[k]); p->d_a_lo[k] = (__half *)at(o_a_lo[k]); }
-  p->d_b_hi = (float *)at(o_b_hi); p->d_b_lo = (__half *)at(o_b_lo);
+  for (int k = 0; k < 3; ++k) { p->d_a_hi[k] = (float *)at(o_a_hi[k]); p->d_a_lo[k] = (lo_t *)at(o_a_lo[k]); }
+  p->d_b_hi = (float *)at(o_b_hi); p->d_b_lo = (lo_t *)at(o_b_lo);
   p->d_stats = (DevStats *)at(o_stats); p->d_report = (PassReport *)at(o_report);
   p->d_partials = (double *)at(o_partials); p->d_counter = (unsigned int *)at(o_counter);
   for (int k = 0; k < 2; ++k) {
@@ -853,9 +870,9 @@ static ots_status flows_pass(ots_problem *p) {
   OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
   for (int t = 2; t <= p->T - 1; ++t)
     OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
-  OTS_CUDA(launch_boundary_flows(p->src.n, p->Lp, p->src.d_tri_l, p->src.d_tri_other, p->src.d_tri_logU, p->b_hi(2),
+  OTS_CUDA(launch_boundary_flows(p->src.n, p->Lp, p->qs, p->src.d_tri_l, p->src.d_tri_other, p->src.d_tri_logU, p->b_hi(2),
                                  p->b_lo(2), p->src.d_flow, p->stream));
-  OTS_CUDA(launch_boundary_flows(p->snk.n, p->Lp, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
+  OTS_CUDA(launch_boundary_flows(p->snk.n, p->Lp, p->qs, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
                                  p->a_hi(p->T - 1), p->a_lo(p->T - 1), p->snk.d_flow, p->stream));
   return OTS_OK;
 }
@@ -913,7 +930,7 @@ ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_en
   for (int t = 2; t <= p->T - 1 && rc == OTS_OK; ++t) {
     if (t >= t_begin && t < t_end) {
       // A_{t-1} is current here (written by the previous forward step of this pass)
-      check(launch_commodity_flows(p->S, p->Lp, l_begin, l_end, p->d_tail, p->d_head, p->a_hi(t - 1), p->a_lo(t - 1),
+      check(launch_commodity_flows(p->S, p->Lp, p->qs, l_begin, l_end, p->d_tail, p->d_head, p->a_hi(t - 1), p->a_lo(t - 1),
                                    p->b_hi(t + 1), p->b_lo(t + 1), p->d_kl_hi, p->d_kl_lo, p->d_klc_hi, p->d_klc_lo,
                                    p->d_logu + (size_t)t * S, d_tmp, p->stream));
       check(cudaMemcpyAsync(out + (size_t)(t - t_begin) * blk, d_tmp, sizeof(double) * blk, cudaMemcpyDeviceToHost,
@@ -922,9 +939,9 @@ ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_en
     }
     check(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
   }
-  check(launch_boundary_flows(p->src.n, p->Lp, p->src.d_tri_l, p->src.d_tri_other, p->src.d_tri_logU, p->b_hi(2),
+  check(launch_boundary_flows(p->src.n, p->Lp, p->qs, p->src.d_tri_l, p->src.d_tri_other, p->src.d_tri_logU, p->b_hi(2),
                               p->b_lo(2), p->src.d_flow, p->stream));
-  check(launch_boundary_flows(p->snk.n, p->Lp, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
+  check(launch_boundary_flows(p->snk.n, p->Lp, p->qs, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
                               p->a_hi(p->T - 1), p->a_lo(p->T - 1), p->snk.d_flow, p->stream));
   if (p->src.n) check(cudaMemcpyAsync(sf.data(), p->src.d_flow, sizeof(double) * p->src.n, cudaMemcpyDeviceToHost, p->stream));
   if (p->snk.n) check(cudaMemcpyAsync(zf.data(), p->snk.d_flow, sizeof(double) * p->snk.n, cudaMemcpyDeviceToHost, p->stream));

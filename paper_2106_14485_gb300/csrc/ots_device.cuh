@@ -2,17 +2,21 @@
 //
 // Representation.  Every message, dual and weight is a base-2 logarithm ("bits"): the
 // exponentials of Algorithm 2 become ex2 and the logarithms lg2 on the SFU.  A message
-// entry is stored as an unevaluated pair hi + lo with hi an FP32 value and lo an FP16
-// value, |lo| <= ulp(hi) / 2: about 35 significant bits in 6 bytes.  Plain FP32 logs
-// carry an absolute error of |x| * 2^-24, which at eps = 0.005 (|x| ~ 1e4 bits) is far
-// above the 1e-5 relative flow tolerance; the pair keeps the absolute error near 1e-7.
-// Arithmetic on pairs is float-float (two_sum), all in FP32 instructions.
+// entry x is stored in 6 bytes as x = hi + (lo - 32768) * q / 65536 with
+//   hi : FP32, an integer multiple of the per-problem quantum q = 2^k (k < 0),
+//   lo : uint16, the remainder in units of q / 65536 (|remainder| <= q / 2), biased by 32768
+//        so that OR-ing it into the mantissa of 2^23 yields the float 2^23 + lo exactly
+//        (decoding costs one logic instruction, no integer-to-float conversion).
+// Sums of two hi values are then exact in FP32 (while |sum| < 2^24 q), so the inner loops
+// need no compensated additions, and the stored value has an absolute resolution of
+// q / 2^17 regardless of its magnitude.  Plain FP32 logs would carry an absolute error of
+// |x| 2^-24, which at eps = 0.005 (|x| ~ 1e4 bits) is far above the 1e-5 relative flow
+// tolerance.  Per-state weights W = log2 K_L + log2 u keep hi on the same grid and a float lo.
 //
-// log 0 is represented by the finite sentinel kNeg (-1e30): no inf or NaN ever enters the
-// float-float operations (two_sum of infinities would produce NaN).
+// log 0 is represented by the finite sentinel kNeg (-1e30) with lo = 0; terms whose hi part is
+// below kNegThresh are skipped by every reduction.
 #pragma once
 
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,6 +25,18 @@ namespace ots {
 constexpr float kNeg = -1e30f;        // log2 0
 constexpr float kNegThresh = -1e29f;  // anything below is treated as log2 0
 constexpr int kBlock = 256;           // threads per block of the message kernels
+
+typedef uint16_t lo_t;
+constexpr float kLoBias = 8421376.0f;   // 2^23 + 32768: float(2^23 | lo) - kLoBias = signed remainder
+constexpr lo_t kLoZero = 32768;
+
+// The quantum of the hi parts and the unit of the lo parts (all powers of two).
+struct QScale {
+  float q;        // 2^k
+  float inv_q;    // 2^-k
+  float lo_unit;  // q / 65536
+  float lo_inv;   // 65536 / q
+};
 
 struct alignas(16) DevStats {
   double src_resid;   // sum |U01 .* Psi_1 - R01| (taken before the source update)
@@ -44,31 +60,32 @@ struct alignas(16) PassReport {
 };
 
 // Arguments of the node-level message kernels.
-//   forward  (fwd = true):  out[v] = LSE_{j in in(v)}  (x[tail j] + W_t[j])   and, per in-state
-//                           j, the capacity update from LSE_l(x[tail j] + y[v]) (Corollary 7)
-//   backward (fwd = false): out[v] = LSE_{j in out(v)} (x[head j] + W_t[j])
+//   forward:  out[v] = LSE_{j in in(v)}  (x[tail j] + W_t[j])   and, per in-state j, the
+//             capacity update from LSE_l(x[tail j] + y[v]) (Corollary 7)
+//   backward: out[v] = LSE_{j in out(v)} (x[head j] + W_t[j])
 struct StepArgs {
   int V;
   int Lp;                     // padded commodity count (row length of a panel)
+  QScale qs;
   const int *ptr;             // [V+1] CSR over nodes: in-states (fwd) / out-states (bwd)
   const int *state;           // state id of each listed state
   const int *nbr;             // tail (fwd) / head (bwd) node of each listed state
   const float *x_hi;          // input panel [V][Lp]
-  const __half *x_lo;
+  const lo_t *x_lo;
   const float *y_hi;          // fwd only: B_{t+1} panel [V][Lp]
-  const __half *y_lo;
+  const lo_t *y_lo;
   float *out_hi;              // output panel [V][Lp]
-  __half *out_lo;
-  const float *kl_hi;         // [S] log2 K_L (commodity-independent rows)
+  lo_t *out_lo;
+  const float *kl_hi;         // [S] log2 K_L (commodity-independent rows), float-float
   const float *kl_lo;
-  const float *klc_hi;        // [S][Lp] log2 K_L per commodity (nullptr if rank-1)
-  const __half *klc_lo;
+  const float *klc_hi;        // [S][Lp] log2 K_L per commodity, panel format (nullptr if rank-1)
+  const lo_t *klc_lo;
   const float *logd_hi;       // [S] log2 d (kNeg for d = 0)
   const float *logd_lo;
   const double *cap;          // [S] d (inf allowed)
   double *logu_t;             // [S] log2 u_t (row t)
-  float *w_hi_t;              // [S] W_t = log2 K_L + log2 u_t (row t)
-  float *w_lo_t;
+  float *w_hi_t;              // [S] W_t hi (on the q grid)
+  float *w_lo_t;              // [S] W_t lo
   double *flow_t;             // [S] aggregate P_t (flows mode)
   double *partials;           // [2 * gridDim.x] per-block partial sums
   unsigned int *counter;      // last-block counter
@@ -79,6 +96,7 @@ struct StepArgs {
 // Boundary kernels (sources, sinks): segments of (node, commodity) with their triples.
 struct BndArgs {
   int n_seg;
+  QScale qs;
   const int *seg_ptr;         // [n_seg+1] into the triple arrays
   const int *seg_node;        // node of the segment (head of the source state / tail of the sink state)
   const int *seg_l;           // commodity of the segment
@@ -89,9 +107,9 @@ struct BndArgs {
   double *tri_logU;           // log2 U (in/out)
   int Lp;
   const float *msg_hi;        // message panel read (B_2 for sources, A_{T-1} for sinks)
-  const __half *msg_lo;
+  const lo_t *msg_lo;
   float *out_hi;              // boundary panel written (A_1 for sources, B_T for sinks)
-  __half *out_lo;
+  lo_t *out_lo;
   double *partials;
   unsigned int *counter;
   DevStats *stats;
@@ -122,45 +140,44 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Merge two (max, scaled-sum) pairs of a log-sum-exp: value = m + log2(s).
-__device__ __forceinline__ void lse_merge(float &m, float &s, float om, float os) {
-  float d = m - om;
-  float f = ex2(-fabsf(d));
-  if (d >= 0.f) {
-    s = fmaf(os, f, s);
-  } else {
-    s = fmaf(s, f, os);
-    m = om;
-  }
+// Round to the q grid (exact scalings by powers of two).
+__device__ __forceinline__ float quant(float x, const QScale &s) {
+  return __fmul_rn(rintf(__fmul_rn(x, s.inv_q)), s.q);
 }
 
-// Online log-sum-exp accumulation of one float-float term (s, e) into (m, acc).  Terms at
-// log 0 are skipped: two_sum(kNeg, x) returns (kNeg, x), whose error part x must not reach
-// ex2 (it can overflow).
-__device__ __forceinline__ void lse_push(float &m, float &acc, float s, float e) {
-  if (s < kNegThresh) return;
-  if (s > m) {
-    acc = fmaf(acc, ex2(m - s), ex2(e));
-    m = s;
-  } else {
-    acc += ex2((s - m) + e);
-  }
+// Mantissa-injected float of a stored lo: 2^23 + lo (exact).
+__device__ __forceinline__ float lo_word0(uint32_t w) { return __uint_as_float((w & 0xffffu) | 0x4B000000u); }
+__device__ __forceinline__ float lo_word1(uint32_t w) { return __uint_as_float((w >> 16) | 0x4B000000u); }
+
+__device__ __forceinline__ lo_t lo_from_units(float li) {
+  li = fminf(fmaxf(li, -32767.f), 32767.f);
+  return (lo_t)((int)li + 32768);
 }
 
-// Finish a log-sum-exp: (m + log2(acc)) as a normalised float-float pair.
-__device__ __forceinline__ void lse_finish(float m, float acc, float &hi, float &lo) {
-  if (m < kNegThresh || !(acc > 0.f)) {
+// Stored form of the float-float value (h + l): hi on the q grid, lo in biased units.
+__device__ __forceinline__ void encode(float h, float l, const QScale &s, float &hi, lo_t &lo) {
+  if (h < kNegThresh) {
     hi = kNeg;
-    lo = 0.f;
+    lo = kLoZero;
     return;
   }
-  two_sum(m, lg2(acc), hi, lo);
+  const float hq = quant(__fadd_rn(h, l), s);
+  const float rem = __fadd_rn(__fsub_rn(h, hq), l);   // h - hq is exact
+  hi = hq;
+  lo = lo_from_units(rintf(__fmul_rn(rem, s.lo_inv)));
 }
 
-__device__ __forceinline__ void store_pair(float *hp, __half *lp, float hi, float lo) {
-  if (hi < kNegThresh) { hi = kNeg; lo = 0.f; }
-  *hp = hi;
-  *lp = __float2half_rn(lo);
+// log-sum-exp result m + log2(acc), m on the q grid, in stored form.
+__device__ __forceinline__ void lse_encode(float m, float acc, const QScale &s, float &hi, lo_t &lo) {
+  if (m < kNegThresh || !(acc > 0.f)) {
+    hi = kNeg;
+    lo = kLoZero;
+    return;
+  }
+  const float f = lg2(acc);
+  const float fq = quant(f, s);
+  hi = __fadd_rn(m, fq);                       // exact: both on the grid
+  lo = lo_from_units(rintf(__fmul_rn(__fsub_rn(f, fq), s.lo_inv)));
 }
 
 }  // namespace ots

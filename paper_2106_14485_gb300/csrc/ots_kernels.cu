@@ -17,12 +17,12 @@
 // which the forward kernel of node v evaluates for all its in-states before forming A_t[v].
 //
 // Thread mapping: G threads cooperate on one node row; thread g owns commodities
-// 4 (c G + g) + k, k < 4, c < C (float4 / 4 x half loads, coalesced along the row).
-// Column sums over commodities are warp-shuffle (and, for G > 32, shared-memory)
-// log-sum-exp reductions.  Everything is FP32 float-float; reductions that decide
-// convergence are FP64 and deterministic (per-block partials summed by the last block in
-// block order).
-#include <cuda_fp16.h>
+// 4 (c G + g) + k, k < 4, c < C (16-byte hi / 8-byte lo loads, coalesced along the row).
+// In-states are processed in batches of kBatch rows gathered up front.  Column sums over
+// commodities are two group reductions (maximum, then sum of ex2 terms): warp shuffles, and
+// one shared-memory exchange when G > 32.  For G >= 32 the capacity update of in-state k is
+// done by thread k of the group and broadcast.  Sums that decide convergence are FP64 and
+// deterministic (per-block partials, reduced by the last block in a fixed order).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -33,29 +33,25 @@ namespace ots {
 
 namespace {
 
-__device__ __forceinline__ void load4(const float *hp, const __half *lp, float h[4], float l[4]) {
-  float4 a = *reinterpret_cast<const float4 *>(hp);
-  uint2 b = *reinterpret_cast<const uint2 *>(lp);
+// 4 consecutive entries of a panel row: hi values and the packed biased lo words.
+__device__ __forceinline__ void load4(const float *hp, const lo_t *lp, float h[4], uint32_t w[2]) {
+  const float4 a = *reinterpret_cast<const float4 *>(hp);
+  const uint2 b = *reinterpret_cast<const uint2 *>(lp);
   h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w;
-  __half2 b0 = *reinterpret_cast<__half2 *>(&b.x);
-  __half2 b1 = *reinterpret_cast<__half2 *>(&b.y);
-  float2 f0 = __half22float2(b0), f1 = __half22float2(b1);
-  l[0] = f0.x; l[1] = f0.y; l[2] = f1.x; l[3] = f1.y;
+  w[0] = b.x;
+  w[1] = b.y;
 }
 
-__device__ __forceinline__ void store4(float *hp, __half *lp, const float h[4], const float l[4]) {
-  float hh[4], ll[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    hh[k] = h[k] < kNegThresh ? kNeg : h[k];
-    ll[k] = h[k] < kNegThresh ? 0.f : l[k];
-  }
-  *reinterpret_cast<float4 *>(hp) = make_float4(hh[0], hh[1], hh[2], hh[3]);
-  __half2 b0 = __floats2half2_rn(ll[0], ll[1]);
-  __half2 b1 = __floats2half2_rn(ll[2], ll[3]);
+// 2^23 + lo of entry q (0..3) of a packed pair of words.
+__device__ __forceinline__ float lo_inj(const uint32_t w[2], int q) {
+  return (q & 1) ? lo_word1(w[q >> 1]) : lo_word0(w[q >> 1]);
+}
+
+__device__ __forceinline__ void store4(float *hp, lo_t *lp, const float h[4], const lo_t l[4]) {
+  *reinterpret_cast<float4 *>(hp) = make_float4(h[0], h[1], h[2], h[3]);
   uint2 b;
-  b.x = *reinterpret_cast<unsigned int *>(&b0);
-  b.y = *reinterpret_cast<unsigned int *>(&b1);
+  b.x = (uint32_t)l[0] | ((uint32_t)l[1] << 16);
+  b.y = (uint32_t)l[2] | ((uint32_t)l[3] << 16);
   *reinterpret_cast<uint2 *>(lp) = b;
 }
 
@@ -108,7 +104,7 @@ __device__ void block_sum2_last(double v0, double v1, double *partials, unsigned
 
 // Group-wide (G threads) reductions of KB values at once.  For G <= 32 the group is a slice
 // of one warp (shuffles only); for G > 32 the block is one node and the warps exchange their
-// partial results through shared memory (sm holds BS/32 x KB floats).
+// partial results through shared memory (sm holds G/32 x KB floats).
 template <int G, int KB, bool MAX>
 __device__ __forceinline__ void group_reduce(float (&x)[KB], float *sm) {
   if (G == 1) return;
@@ -143,42 +139,55 @@ __device__ __forceinline__ void group_reduce(float (&x)[KB], float *sm) {
   }
 }
 
-// Gather the thread's slice of up to KB input rows (row index nbr[j0 + k]) and, with
-// per-commodity costs, fold log2 K_L[., state] into them.
+// Gather the thread's slice of up to KB input rows (row index nbr[j0 + k]).  With
+// per-commodity costs the row of log2 K_L[., state] (same stored format) is added: hi sums are
+// exact; the two remainders are added in signed units and re-biased (|sum| <= 2^16 units, one
+// more unit of rounding when the sum leaves the int16 range is avoided by carrying into hi).
 template <int G, int C, int KB, bool PC>
 __device__ __forceinline__ void gather_rows(const StepArgs &a, int j0, int nb, int g, int (&st)[KB],
-                                            float (&xh)[KB][C][4], float (&xl)[KB][C][4]) {
+                                            float (&xh)[KB][C][4], uint32_t (&xw)[KB][C][2]) {
 #pragma unroll
   for (int k = 0; k < KB; ++k) {
     if (k < nb) {
       st[k] = a.state[j0 + k];
       const size_t row = (size_t)a.nbr[j0 + k] * a.Lp;
 #pragma unroll
-      for (int c = 0; c < C; ++c) load4(a.x_hi + row + 4 * (c * G + g), a.x_lo + row + 4 * (c * G + g), xh[k][c], xl[k][c]);
+      for (int c = 0; c < C; ++c) load4(a.x_hi + row + 4 * (c * G + g), a.x_lo + row + 4 * (c * G + g), xh[k][c], xw[k][c]);
     } else {
       st[k] = 0;
 #pragma unroll
-      for (int c = 0; c < C; ++c)
+      for (int c = 0; c < C; ++c) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { xh[k][c][q] = kNeg; xl[k][c][q] = 0.f; }
+        for (int q = 0; q < 4; ++q) xh[k][c][q] = kNeg;
+        xw[k][c][0] = 0x80008000u;
+        xw[k][c][1] = 0x80008000u;
+      }
     }
   }
   if (PC) {
+    const float q = a.qs.q;
 #pragma unroll
     for (int k = 0; k < KB; ++k) {
       if (k < nb) {
         const size_t row = (size_t)st[k] * a.Lp;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          float ch[4], cl[4];
-          load4(a.klc_hi + row + 4 * (c * G + g), a.klc_lo + row + 4 * (c * G + g), ch, cl);
+          float ch[4];
+          uint32_t cw[2];
+          load4(a.klc_hi + row + 4 * (c * G + g), a.klc_lo + row + 4 * (c * G + g), ch, cw);
+          lo_t nl[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            float s, e;
-            two_sum(xh[k][c][q], ch[q], s, e);
-            xh[k][c][q] = s;
-            xl[k][c][q] += e + cl[q];
+          for (int qq = 0; qq < 4; ++qq) {
+            // signed remainders in units, exact
+            float u = (lo_inj(xw[k][c], qq) - kLoBias) + (lo_inj(cw, qq) - kLoBias);
+            float h = xh[k][c][qq] + ch[qq];
+            if (u > 32767.f) { u -= 65536.f; h += q; }
+            if (u < -32767.f) { u += 65536.f; h -= q; }
+            xh[k][c][qq] = h;
+            nl[qq] = (lo_t)((int)u + 32768);
           }
+          xw[k][c][0] = (uint32_t)nl[0] | ((uint32_t)nl[1] << 16);
+          xw[k][c][1] = (uint32_t)nl[2] | ((uint32_t)nl[3] << 16);
         }
       }
     }
@@ -186,31 +195,30 @@ __device__ __forceinline__ void gather_rows(const StepArgs &a, int j0, int nb, i
 }
 
 // Accumulate one batch of terms x[k] + w[k] into the running log-sum-exp (M, acc) of each
-// commodity: exact float-float terms, batch maximum first, one ex2 per term.
+// commodity: hi sums are exact, batch maximum first, one ex2 per term.  Absent or unreachable
+// terms have hi sums near -1e30 and vanish in ex2 without a branch.
 template <int C, int KB>
-__device__ __forceinline__ void aggregate_batch(int nb, float (&xh)[KB][C][4], const float (&xl)[KB][C][4],
-                                                const float (&wh)[KB], const float (&wl)[KB], float (&M)[C][4],
-                                                float (&acc)[C][4]) {
+__device__ __forceinline__ void aggregate_batch(const float (&xh)[KB][C][4], const uint32_t (&xw)[KB][C][2],
+                                                const float (&wh)[KB], const float (&wl)[KB], float lo_unit,
+                                                float (&M)[C][4], float (&acc)[C][4]) {
+  float wlb[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) wlb[k] = wl[k] - kLoBias * lo_unit;
 #pragma unroll
   for (int c = 0; c < C; ++c)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      float sv[KB], ev[KB];
+      float sv[KB];
       float m = 2.f * kNeg;
 #pragma unroll
       for (int k = 0; k < KB; ++k) {
-        float s, e;
-        two_sum(xh[k][c][q], wh[k], s, e);
-        sv[k] = s;
-        ev[k] = e + (xl[k][c][q] + wl[k]);
-        if (k < nb) m = fmaxf(m, s);
+        sv[k] = xh[k][c][q] + wh[k];
+        m = fmaxf(m, sv[k]);
       }
       if (m < kNegThresh) continue;               // nothing reachable in this batch
       float sum = 0.f;
 #pragma unroll
-      for (int k = 0; k < KB; ++k)
-        if (k < nb && sv[k] > kNegThresh) sum += ex2((sv[k] - m) + ev[k]);
-      // merge (m, sum) into (M, acc)
+      for (int k = 0; k < KB; ++k) sum += ex2(fmaf(lo_inj(xw[k][c], q), lo_unit, (sv[k] - m) + wlb[k]));
       const float Mo = M[c][q];
       if (m > Mo) {
         acc[c][q] = fmaf(acc[c][q], ex2(Mo - m), sum);
@@ -221,7 +229,98 @@ __device__ __forceinline__ void aggregate_batch(int nb, float (&xh)[KB][C][4], c
     }
 }
 
+// Merge two (max, scaled-sum) pairs of a log-sum-exp: value = m + log2(s).
+__device__ __forceinline__ void lse_merge(float &m, float &s, float om, float os) {
+  if (om > m) {
+    s = fmaf(s, ex2(m - om), os);
+    m = om;
+  } else {
+    s = fmaf(os, ex2(om - m), s);
+  }
+}
+
+// W = log2 K_L + log2 u as (hi on the q grid, float lo).
+__device__ __forceinline__ void make_w(float kl_hi, float kl_lo, float lu_hi, float lu_lo, const QScale &qs,
+                                       float &w_hi, float &w_lo) {
+  if (lu_hi < kNegThresh) {
+    w_hi = kNeg;
+    w_lo = 0.f;
+    return;
+  }
+  float s, e;
+  two_sum(kl_hi, lu_hi, s, e);
+  e += kl_lo + lu_lo;
+  w_hi = quant(s, qs);
+  w_lo = (s - w_hi) + e;
+}
+
+// Capacity update of one state from its column log-sum-exp (cm + log2 cs) (Algorithm 2,
+// Corollary 7): W_t for the aggregation and, when `write`, the stored log2 u_t, W_t, the
+// excess (P_t - d)_+ with the old u_t and the dual term d log2 u_t (Theorem 3).  In flows
+// mode (a.mode == 1) W_t is read back and, when `write`, P_t is stored.
+template <bool PC>
+__device__ __forceinline__ void update_state(const StepArgs &a, int sk, float cm, float cs, bool write, float &w_hi,
+                                             float &w_lo, double &viol, double &dual) {
+  float col_hi = kNeg, col_lo = 0.f;
+  if (cm > kNegThresh && cs > 0.f) two_sum(cm, lg2(cs), col_hi, col_lo);  // log2 (hatPsi .* Psi (.* K_L))^T 1
+  const float klh = PC ? 0.f : a.kl_hi[sk], kll = PC ? 0.f : a.kl_lo[sk];
+  if (!PC && col_hi > kNegThresh) {
+    float s, e;
+    two_sum(col_hi, klh, s, e);
+    col_hi = s;
+    col_lo += e + kll;
+  }
+  if (a.mode != 0) {
+    w_hi = a.w_hi_t[sk];
+    w_lo = a.w_lo_t[sk];
+    if (write)
+      a.flow_t[sk] = col_hi > kNegThresh && w_hi > kNegThresh
+                         ? exp2(a.logu_t[sk] + (double)col_hi + (double)col_lo) : 0.0;
+    return;
+  }
+  const double cap = a.cap[sk];
+  float lu_hi = 0.f, lu_lo = 0.f;
+  if (isfinite(cap) && col_hi > kNegThresh) {
+    if (a.logd_hi[sk] < kNegThresh) {
+      lu_hi = kNeg;                                // d = 0: the state is closed
+    } else {
+      // log2 u = min(log2 d - col, 0) in float-float
+      float s1, e1, s2, e2;
+      two_sum(a.logd_hi[sk], -col_hi, s1, e1);
+      e1 += a.logd_lo[sk] - col_lo;
+      two_sum(s1, e1, s2, e2);
+      if (s2 < 0.f) { lu_hi = s2; lu_lo = e2; }
+    }
+  }
+  make_w(klh, kll, lu_hi, lu_lo, a.qs, w_hi, w_lo);
+  if (!write) return;
+  const double lu_old = a.logu_t[sk];
+  if (col_hi > kNegThresh && isfinite(cap)) {
+    // excess with the old u_t; exact FP64 only near or above capacity
+    const float qv = (float)lu_old + col_hi - a.logd_hi[sk];
+    if (qv > -1e-3f) {
+      const double p_old = exp2(lu_old + (double)col_hi + (double)col_lo);
+      if (p_old > cap) viol += p_old - cap;
+    }
+  }
+  if (col_hi != col_hi || col_lo != col_lo) viol = __longlong_as_double(0x7ff8000000000000LL);  // NaN: reported
+  const double lu_new = lu_hi < kNegThresh ? -1e30 : (double)lu_hi + (double)lu_lo;
+  if (isfinite(cap) && cap > 0.0) dual += cap * lu_new;
+  a.logu_t[sk] = lu_new;
+  a.w_hi_t[sk] = w_hi;
+  a.w_lo_t[sk] = w_lo;
+}
+
 }  // namespace
+
+template <int G>
+struct BlockOf { static constexpr int value = G > 32 ? G : kBlock; };
+template <int G>
+struct MinBlocks { static constexpr int value = G > 32 ? 768 / G : 3; };
+template <int G>
+struct MinBlocksFwd { static constexpr int value = G > 32 ? 512 / G : 2; };
+
+constexpr int kBatch = 6;   // in-states gathered per batch (grid nodes have 5)
 
 // ------------------------------------------------------------------------------------
 // forward step t (t = 2..T-1): capacity update of every state entering v, then A_t[v]
@@ -229,25 +328,29 @@ __device__ __forceinline__ void aggregate_batch(int nb, float (&xh)[KB][C][4], c
 // W_t[j] is log2 K_L[j] + log2 u_t[j] when the rows of C_L are shared by all commodities,
 // and log2 u_t[j] alone when a per-commodity K_L panel (klc) is given.
 // ------------------------------------------------------------------------------------
-template <int G>
-struct BlockOf { static constexpr int value = G > 32 ? G : kBlock; };
-
-constexpr int kBatch = 4;   // in-states gathered per batch
-
 template <int G, int C, bool PC>
-__global__ void __launch_bounds__(BlockOf<G>::value, 2 * 256 / BlockOf<G>::value) k_forward(const StepArgs a) {
+__global__ void __launch_bounds__(BlockOf<G>::value, MinBlocksFwd<G>::value) k_forward(const StepArgs a) {
   constexpr int BS = BlockOf<G>::value;
   constexpr int NPB = BS / G;  // nodes per block (1 when G > 32)
   constexpr int KB = kBatch;
-  __shared__ float sm[(BS / 32 > 0 ? BS / 32 : 1) * KB];
+  constexpr int NW = G > 32 ? G / 32 : 1;
+  __shared__ float red[1];                   // unused: reductions above stay within a warp
+  __shared__ float xch[2 * 2 * KB * NW];     // per-warp (max, sum) pairs, two batch buffers
+  const float lo_unit = a.qs.lo_unit;
+  int batch = 0;
   const int g = threadIdx.x % G;
   const int v = blockIdx.x * NPB + threadIdx.x / G;
   const bool active = v < a.V;
   const size_t rowv = (size_t)(active ? v : 0) * a.Lp;
 
-  float bh[C][4], bl[C][4];
+  float bh[C][4], bl[C][4];   // B_{t+1}[v]: hi, signed remainder in units
 #pragma unroll
-  for (int c = 0; c < C; ++c) load4(a.y_hi + rowv + 4 * (c * G + g), a.y_lo + rowv + 4 * (c * G + g), bh[c], bl[c]);
+  for (int c = 0; c < C; ++c) {
+    uint32_t w[2];
+    load4(a.y_hi + rowv + 4 * (c * G + g), a.y_lo + rowv + 4 * (c * G + g), bh[c], w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bl[c][q] = lo_inj(w, q) - kLoBias;
+  }
 
   float M[C][4], acc[C][4];
 #pragma unroll
@@ -262,11 +365,13 @@ __global__ void __launch_bounds__(BlockOf<G>::value, 2 * 256 / BlockOf<G>::value
   for (int j0 = jb; j0 < je; j0 += KB) {
     const int nb = min(KB, je - j0);
     int st[KB];
-    float xh[KB][C][4], xl[KB][C][4];
-    gather_rows<G, C, KB, PC>(a, j0, nb, g, st, xh, xl);
+    float xh[KB][C][4];
+    uint32_t xw[KB][C][2];
+    gather_rows<G, C, KB, PC>(a, j0, nb, g, st, xh, xw);
 
-    // (1) column log-sum-exp over commodities of A_{t-1}[y] (+ K_L) + B_{t+1}[v], for each
-    //     in-state of the batch: group maximum of the rounded sums, then group sum.
+    // (1) column log-sum-exp over commodities of A_{t-1}[y] (+ K_L) + B_{t+1}[v] for every
+    //     in-state of the batch.  Per warp (or per group when G < 32): maximum, then sum of
+    //     ex2 terms, by shuffles; exact hi sums.
     float cm[KB], cs[KB];
 #pragma unroll
     for (int k = 0; k < KB; ++k) {
@@ -274,10 +379,10 @@ __global__ void __launch_bounds__(BlockOf<G>::value, 2 * 256 / BlockOf<G>::value
 #pragma unroll
       for (int c = 0; c < C; ++c)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) m = fmaxf(m, __fadd_rn(xh[k][c][q], bh[c][q]));
+        for (int q = 0; q < 4; ++q) m = fmaxf(m, xh[k][c][q] + bh[c][q]);
       cm[k] = m;
     }
-    group_reduce<G, KB, true>(cm, sm);
+    group_reduce<(G < 32 ? G : 32), KB, true>(cm, red);
 #pragma unroll
     for (int k = 0; k < KB; ++k) {
       float sum = 0.f;
@@ -286,87 +391,70 @@ __global__ void __launch_bounds__(BlockOf<G>::value, 2 * 256 / BlockOf<G>::value
         for (int c = 0; c < C; ++c)
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            float s, e;
-            two_sum(xh[k][c][q], bh[c][q], s, e);
-            if (s > kNegThresh) sum += ex2((s - cm[k]) + (e + (xl[k][c][q] + bl[c][q])));
+            const float s = xh[k][c][q] + bh[c][q];
+            const float e = (lo_inj(xw[k][c], q) - kLoBias) + bl[c][q];   // exact, in units
+            sum += ex2(fmaf(e, lo_unit, s - cm[k]));
           }
       }
       cs[k] = sum;
     }
-    group_reduce<G, KB, false>(cs, sm);
+    group_reduce<(G < 32 ? G : 32), KB, false>(cs, red);
 
-    // (2) capacity update of each in-state (Algorithm 2), or flows of the current iterate
+    // (2) capacity update of each in-state and the weights W_t of the batch
     float wh[KB], wl[KB];
+    if (G >= 32) {
+      // lane k of every warp merges the warps' (max, sum) pairs of in-state k (one shared
+      // memory exchange, double-buffered by batch parity) and derives W_t[state k]; warp 0
+      // stores the update and the FP64 sums.  W is then broadcast by shuffles.
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      float mk = cm[0], sk_ = cs[0];
+      int stk = st[0];
 #pragma unroll
-    for (int k = 0; k < KB; ++k) {
-      wh[k] = kNeg;
-      wl[k] = 0.f;
-      if (k >= nb) continue;
-      const int sk = st[k];
-      float col_hi, col_lo;
-      lse_finish(cm[k], cs[k], col_hi, col_lo);   // log2 of (hatPsi_t .* Psi_t (.* K_L))^T 1
-      const float klh = PC ? 0.f : a.kl_hi[sk], kll = PC ? 0.f : a.kl_lo[sk];
-      if (!PC && col_hi > kNegThresh) {
-        float s, e;
-        two_sum(col_hi, klh, s, e);
-        col_hi = s;
-        col_lo += e + kll;
+      for (int k = 1; k < KB; ++k)
+        if (k == lane) { mk = cm[k]; sk_ = cs[k]; stk = st[k]; }
+      if (G > 32) {
+        float *xb = xch + (batch & 1) * (2 * KB * NW);
+        if (lane < nb) { xb[(2 * lane) * NW + wid] = mk; xb[(2 * lane + 1) * NW + wid] = sk_; }
+        __syncthreads();
+        if (lane < nb) {
+          mk = xb[(2 * lane) * NW];
+          sk_ = xb[(2 * lane + 1) * NW];
+#pragma unroll
+          for (int w = 1; w < NW; ++w) lse_merge(mk, sk_, xb[(2 * lane) * NW + w], xb[(2 * lane + 1) * NW + w]);
+        }
       }
-      if (a.mode == 0) {
-        const double cap = a.cap[sk];
-        float lu_hi = 0.f, lu_lo = 0.f;
-        if (isfinite(cap) && col_hi > kNegThresh) {
-          if (a.logd_hi[sk] < kNegThresh) {
-            lu_hi = kNeg;                            // d = 0: the state is closed
-          } else {
-            // log2 u = min(log2 d - col, 0) in float-float
-            float s1, e1, s2, e2;
-            two_sum(a.logd_hi[sk], -col_hi, s1, e1);
-            e1 += a.logd_lo[sk] - col_lo;
-            two_sum(s1, e1, s2, e2);
-            if (s2 < 0.f) { lu_hi = s2; lu_lo = e2; }
-          }
-        }
-        if (lu_hi > kNegThresh) {
-          two_sum(klh, lu_hi, wh[k], wl[k]);
-          wl[k] += kll + lu_lo;
-        }
-        if (g == 0) {
-          const double lu_old = a.logu_t[sk];
-          if (col_hi > kNegThresh && isfinite(cap)) {
-            // excess (P_t - d)_+ with the old u_t; exact FP64 only near or above capacity
-            const float q = (float)lu_old + col_hi - a.logd_hi[sk];
-            if (q > -1e-3f) {
-              const double p_old = exp2(lu_old + (double)col_hi + (double)col_lo);
-              if (p_old > cap) viol += p_old - cap;
-            }
-          }
-          if (col_hi != col_hi || col_lo != col_lo) viol = __longlong_as_double(0x7ff8000000000000LL);  // NaN
-          const double lu_new = lu_hi < kNegThresh ? -1e30 : (double)lu_hi + (double)lu_lo;
-          if (isfinite(cap) && cap > 0.0) dual += cap * lu_new;
-          a.logu_t[sk] = lu_new;
-          a.w_hi_t[sk] = wh[k];
-          a.w_lo_t[sk] = wl[k];
-        }
-      } else {
-        wh[k] = a.w_hi_t[sk];
-        wl[k] = a.w_lo_t[sk];
-        if (g == 0)
-          a.flow_t[sk] = col_hi > kNegThresh && wh[k] > kNegThresh
-                             ? exp2(a.logu_t[sk] + (double)col_hi + (double)col_lo) : 0.0;
+      float mh = kNeg, ml = 0.f;
+      // G == 32: each warp is its own node and stores its own updates
+      if (lane < nb) update_state<PC>(a, stk, mk, sk_, G == 32 || wid == 0, mh, ml, viol, dual);
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        const float h = __shfl_sync(0xffffffffu, mh, k);
+        const float l = __shfl_sync(0xffffffffu, ml, k);
+        wh[k] = k < nb ? h : kNeg;
+        wl[k] = k < nb ? l : 0.f;
+      }
+    } else {
+      // small groups: every thread derives all updates; thread 0 of the group stores them
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        wh[k] = kNeg;
+        wl[k] = 0.f;
+        if (k < nb) update_state<PC>(a, st[k], cm[k], cs[k], g == 0, wh[k], wl[k], viol, dual);
       }
     }
+    ++batch;
 
     // (3) A_t[v] accumulates A_{t-1}[y] + W_t[state] over the batch
-    aggregate_batch<C, KB>(nb, xh, xl, wh, wl, M, acc);
+    aggregate_batch<C, KB>(xh, xw, wh, wl, lo_unit, M, acc);
   }
 
   if (active) {
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      float oh[4], ol[4];
+      float oh[4];
+      lo_t ol[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) lse_finish(M[c][q], acc[c][q], oh[q], ol[q]);
+      for (int q = 0; q < 4; ++q) lse_encode(M[c][q], acc[c][q], a.qs, oh[q], ol[q]);
       store4(a.out_hi + rowv + 4 * (c * G + g), a.out_lo + rowv + 4 * (c * G + g), oh, ol);
     }
   }
@@ -377,7 +465,7 @@ __global__ void __launch_bounds__(BlockOf<G>::value, 2 * 256 / BlockOf<G>::value
 // backward step t (t = T-1..2): B_t[v] = LSE_{j: tail j = v} (B_{t+1}[head j] + W_t[j] (+ K_L))
 // ------------------------------------------------------------------------------------
 template <int G, int C, bool PC>
-__global__ void __launch_bounds__(BlockOf<G>::value, 3 * 256 / BlockOf<G>::value) k_backward(const StepArgs a) {
+__global__ void __launch_bounds__(BlockOf<G>::value, MinBlocks<G>::value) k_backward(const StepArgs a) {
   constexpr int BS = BlockOf<G>::value;
   constexpr int NPB = BS / G;
   constexpr int KB = kBatch;
@@ -393,22 +481,24 @@ __global__ void __launch_bounds__(BlockOf<G>::value, 3 * 256 / BlockOf<G>::value
   for (int j0 = jb; j0 < je; j0 += KB) {
     const int nb = min(KB, je - j0);
     int st[KB];
-    float xh[KB][C][4], xl[KB][C][4];
-    gather_rows<G, C, KB, PC>(a, j0, nb, g, st, xh, xl);
+    float xh[KB][C][4];
+    uint32_t xw[KB][C][2];
+    gather_rows<G, C, KB, PC>(a, j0, nb, g, st, xh, xw);
     float wh[KB], wl[KB];
 #pragma unroll
     for (int k = 0; k < KB; ++k) {
       wh[k] = k < nb ? a.w_hi_t[st[k]] : kNeg;
       wl[k] = k < nb ? a.w_lo_t[st[k]] : 0.f;
     }
-    aggregate_batch<C, KB>(nb, xh, xl, wh, wl, M, acc);
+    aggregate_batch<C, KB>(xh, xw, wh, wl, a.qs.lo_unit, M, acc);
   }
   const size_t rowo = (size_t)v * a.Lp;
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    float oh[4], ol[4];
+    float oh[4];
+    lo_t ol[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) lse_finish(M[c][q], acc[c][q], oh[q], ol[q]);
+    for (int q = 0; q < 4; ++q) lse_encode(M[c][q], acc[c][q], a.qs, oh[q], ol[q]);
     store4(a.out_hi + rowo + 4 * (c * G + g), a.out_lo + rowo + 4 * (c * G + g), oh, ol);
   }
 }
@@ -416,17 +506,17 @@ __global__ void __launch_bounds__(BlockOf<G>::value, 3 * 256 / BlockOf<G>::value
 // ------------------------------------------------------------------------------------
 // boundary updates: U01 <- R01 ./ Psi_1 (sources), U0T <- R0T ./ hatPsi_T (sinks), and the
 // boundary panels A_1 = (U01 K) by tail node, B_T = (U0T K^T) by head node.
-// One thread per (node, commodity) segment of triples.
+// One thread per (node, commodity) segment of triples; FP64 throughout.
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_boundary(const BndArgs b) {
   const int sidx = blockIdx.x * blockDim.x + threadIdx.x;
   double r0 = 0.0, r1 = 0.0, r2 = 0.0;
   if (sidx < b.n_seg) {
     const int l = b.seg_l[sidx];
-    float m = 2.f * kNeg, acc = 0.f;
+    double m = -INFINITY;
     for (int q = b.seg_ptr[sidx]; q < b.seg_ptr[sidx + 1]; ++q) {
       const size_t idx = (size_t)b.tri_node_other[q] * b.Lp + l;
-      const double msg = (double)b.msg_hi[idx] + (double)__half2float(b.msg_lo[idx]);
+      const double msg = (double)b.msg_hi[idx] + ((double)b.msg_lo[idx] - 32768.0) * (double)b.qs.lo_unit;
       double lu = b.tri_logU[q];
       if (b.mode == 0) {
         if (b.is_source) r0 += fabs(exp2(lu + msg) - b.tri_R[q]);   // mismatch before the update
@@ -436,18 +526,20 @@ __global__ void __launch_bounds__(kBlock) k_boundary(const BndArgs b) {
         r1 += b.tri_R[q] * lu;                                       // <R, log2 U>
         if (!b.is_source) r0 += exp2(lu + msg);                      // <K, U> after the update
       }
-      // segment log-sum-exp of log2 U in float-float
-      const float hi = (float)lu;
-      const float lo = (float)(lu - (double)hi);
-      lse_push(m, acc, hi, lo);
+      m = fmax(m, lu);
     }
-    float oh, ol;
-    lse_finish(m, acc, oh, ol);
+    double sum = 0.0;
+    for (int q = b.seg_ptr[sidx]; q < b.seg_ptr[sidx + 1]; ++q) sum += exp2(b.tri_logU[q] - m);
+    const double r = m + log2(sum);
+    const float h = (float)r;
+    float oh;
+    lo_t ol;
+    encode(h, (float)(r - (double)h), b.qs, oh, ol);
     const size_t o = (size_t)b.seg_node[sidx] * b.Lp + l;
-    store_pair(b.out_hi + o, b.out_lo + o, oh, ol);
+    b.out_hi[o] = oh;
+    b.out_lo[o] = ol;
   }
   if (b.mode == 0) {
-    // three sums through two reductions: (r0, r1) then r2 folded into stats->bad
     if (b.is_source) {
       block_sum2_last(r0, r1, b.partials, b.counter, &b.stats->src_resid, &b.stats->dual_src, 1);
     } else {
@@ -474,71 +566,61 @@ __global__ void k_pass_end(const DevStats *st, PassReport *rep, double mass, dou
   rep->passes += 1;
 }
 
-// Initial duals: log2 u_t = 0 and W_t = log2 K_L for t = 2..T-1.
-__global__ void k_init_weights(int S, int T, const float *kl_hi, const float *kl_lo, double *logu,
-                               float *w_hi, float *w_lo) {
+// W_t = log2 K_L + log2 u_t for t = 2..T-1 from log2 u (set to 0 first when reset).
+__global__ void k_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, double *logu, float *w_hi,
+                          float *w_lo, int reset) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   for (int t = 2; t <= T - 1; ++t) {
-    logu[(size_t)t * S + s] = 0.0;
-    w_hi[(size_t)t * S + s] = kl_hi ? kl_hi[s] : 0.f;
-    w_lo[(size_t)t * S + s] = kl_lo ? kl_lo[s] : 0.f;
-  }
-}
-
-// W_t = log2 K_L + log2 u_t from given log2 u (after ots_set_duals).
-__global__ void k_weights_from_logu(int S, int T, const float *kl_hi, const float *kl_lo, const double *logu,
-                                    float *w_hi, float *w_lo) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= S) return;
-  for (int t = 2; t <= T - 1; ++t) {
+    if (reset) logu[(size_t)t * S + s] = 0.0;
     const double lu = logu[(size_t)t * S + s];
     float luh = (float)lu;
     float lul = (float)(lu - (double)luh);
-    if (lu < -1e29) { w_hi[(size_t)t * S + s] = kNeg; w_lo[(size_t)t * S + s] = 0.f; continue; }
+    if (lu < -1e29) { luh = kNeg; lul = 0.f; }
     float hi, lo;
-    two_sum(kl_hi ? kl_hi[s] : 0.f, luh, hi, lo);
-    lo += (kl_lo ? kl_lo[s] : 0.f) + lul;
+    make_w(kl_hi ? kl_hi[s] : 0.f, kl_lo ? kl_lo[s] : 0.f, luh, lul, qs, hi, lo);
     w_hi[(size_t)t * S + s] = hi;
     w_lo[(size_t)t * S + s] = lo;
   }
 }
 
-__global__ void k_fill_panel(size_t n, float *hi, __half *lo) {
+__global__ void k_fill_panel(size_t n, float *hi, lo_t *lo) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     hi[i] = kNeg;
-    lo[i] = __float2half_rn(0.f);
+    lo[i] = kLoZero;
   }
 }
 
 // Per-commodity flows P_{0,t}[l, j] = 2^(A_{t-1}[tail j][l] + B_{t+1}[head j][l] + log2 K_L + log2 u_t)
 // for commodities [l0, l1), all states j; out[(l - l0) * S + j].
-__global__ void k_commodity_flows(int S, int Lp, int l0, int l1, const int *tail, const int *head,
-                                  const float *a_hi, const __half *a_lo, const float *b_hi, const __half *b_lo,
-                                  const float *kl_hi, const float *kl_lo, const float *klc_hi, const __half *klc_lo,
+__global__ void k_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
+                                  const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
+                                  const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
                                   const double *logu_t, double *out) {
   const size_t n = (size_t)S * (l1 - l0);
+  const double unit = qs.lo_unit;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(i % S);
     const int l = l0 + (int)(i / S);
     const size_t ia = (size_t)tail[j] * Lp + l, ib = (size_t)head[j] * Lp + l;
     const float ah = a_hi[ia], bh = b_hi[ib];
-    if (ah < kNegThresh || bh < kNegThresh) { out[i] = 0.0; continue; }
-    double x = (double)ah + (double)__half2float(a_lo[ia]) + (double)bh + (double)__half2float(b_lo[ib]) + logu_t[j];
-    if (klc_hi) x += (double)klc_hi[(size_t)j * Lp + l] + (double)__half2float(klc_lo[(size_t)j * Lp + l]);
+    if (ah < kNegThresh || bh < kNegThresh || logu_t[j] < -1e29) { out[i] = 0.0; continue; }
+    double x = (double)ah + ((double)a_lo[ia] - 32768.0) * unit + (double)bh + ((double)b_lo[ib] - 32768.0) * unit +
+               logu_t[j];
+    if (klc_hi) x += (double)klc_hi[(size_t)j * Lp + l] + ((double)klc_lo[(size_t)j * Lp + l] - 32768.0) * unit;
     else x += (double)kl_hi[j] + (double)kl_lo[j];
     out[i] = exp2(x);
   }
 }
 
 // Boundary flows of one triple list: P = 2^(log2 U + msg) per triple (t = 1 or t = T).
-__global__ void k_boundary_flows(int n, int Lp, const int *tri_l, const int *tri_node_other, const double *tri_logU,
-                                 const float *msg_hi, const __half *msg_lo, double *out) {
+__global__ void k_boundary_flows(int n, int Lp, QScale qs, const int *tri_l, const int *tri_node_other,
+                                 const double *tri_logU, const float *msg_hi, const lo_t *msg_lo, double *out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const size_t idx = (size_t)tri_node_other[q] * Lp + tri_l[q];
   if (msg_hi[idx] < kNegThresh) { out[q] = 0.0; return; }
-  const double msg = (double)msg_hi[idx] + (double)__half2float(msg_lo[idx]);
+  const double msg = (double)msg_hi[idx] + ((double)msg_lo[idx] - 32768.0) * (double)qs.lo_unit;
   out[q] = exp2(tri_logU[q] + msg);
 }
 
@@ -593,19 +675,13 @@ cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, do
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_weights(int S, int T, const float *kl_hi, const float *kl_lo, double *logu, float *w_hi,
-                                float *w_lo, cudaStream_t s) {
-  k_init_weights<<<(S + 255) / 256, 256, 0, s>>>(S, T, kl_hi, kl_lo, logu, w_hi, w_lo);
+cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, double *logu,
+                           float *w_hi, float *w_lo, int reset, cudaStream_t s) {
+  k_weights<<<(S + 255) / 256, 256, 0, s>>>(S, T, qs, kl_hi, kl_lo, logu, w_hi, w_lo, reset);
   return cudaGetLastError();
 }
 
-cudaError_t launch_weights_from_logu(int S, int T, const float *kl_hi, const float *kl_lo, const double *logu,
-                                     float *w_hi, float *w_lo, cudaStream_t s) {
-  k_weights_from_logu<<<(S + 255) / 256, 256, 0, s>>>(S, T, kl_hi, kl_lo, logu, w_hi, w_lo);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fill_panel(size_t n, float *hi, __half *lo, cudaStream_t s) {
+cudaError_t launch_fill_panel(size_t n, float *hi, lo_t *lo, cudaStream_t s) {
   size_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks == 0) blocks = 1;
@@ -613,23 +689,24 @@ cudaError_t launch_fill_panel(size_t n, float *hi, __half *lo, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_commodity_flows(int S, int Lp, int l0, int l1, const int *tail, const int *head, const float *a_hi,
-                                   const __half *a_lo, const float *b_hi, const __half *b_lo, const float *kl_hi,
-                                   const float *kl_lo, const float *klc_hi, const __half *klc_lo, const double *logu_t,
-                                   double *out, cudaStream_t s) {
+cudaError_t launch_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
+                                   const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
+                                   const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
+                                   const double *logu_t, double *out, cudaStream_t s) {
   size_t n = (size_t)S * (l1 - l0);
   size_t blocks = (n + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   if (blocks == 0) blocks = 1;
-  k_commodity_flows<<<(unsigned)blocks, 256, 0, s>>>(S, Lp, l0, l1, tail, head, a_hi, a_lo, b_hi, b_lo, kl_hi, kl_lo,
-                                                     klc_hi, klc_lo, logu_t, out);
+  k_commodity_flows<<<(unsigned)blocks, 256, 0, s>>>(S, Lp, qs, l0, l1, tail, head, a_hi, a_lo, b_hi, b_lo, kl_hi,
+                                                     kl_lo, klc_hi, klc_lo, logu_t, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_boundary_flows(int n, int Lp, const int *tri_l, const int *tri_node_other, const double *tri_logU,
-                                  const float *msg_hi, const __half *msg_lo, double *out, cudaStream_t s) {
+cudaError_t launch_boundary_flows(int n, int Lp, QScale qs, const int *tri_l, const int *tri_node_other,
+                                  const double *tri_logU, const float *msg_hi, const lo_t *msg_lo, double *out,
+                                  cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_boundary_flows<<<(n + 255) / 256, 256, 0, s>>>(n, Lp, tri_l, tri_node_other, tri_logU, msg_hi, msg_lo, out);
+  k_boundary_flows<<<(n + 255) / 256, 256, 0, s>>>(n, Lp, qs, tri_l, tri_node_other, tri_logU, msg_hi, msg_lo, out);
   return cudaGetLastError();
 }
 
