@@ -153,6 +153,22 @@ ots_status ots_get_flows(ots_problem *p, int32_t t_begin, int32_t t_end, double 
 ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_end,
                                    int32_t l_begin, int32_t l_end, double *out);
 
+/* Same values as ots_get_commodity_flows, computed without allocating memory.  The paper has
+ * no counterpart; this entry point is for callers that cannot allocate while they read
+ * results: a real-time loop that must not wait on the device allocator (cudaMalloc can
+ * synchronise the whole device) between solver passes, or an application that fixes this
+ * library's device memory when it creates the problem and has no room for more.  ots_get_commodity_flows takes a temporary
+ * device buffer per call; this variant uses one static device array of 8 MiB for the flows
+ * of one t plus 256 KiB for triple indices, present on every GPU that loads the library
+ * until the process exits.  Limits: (l_end - l_begin) x n_states <= 1048576 and at most
+ * 65536 source and 65536 sink triples, else OTS_ERR_INVALID_ARG.  Arguments and layout as
+ * in ots_get_commodity_flows (out is a host buffer).  The first call on a device looks up
+ * the array's device address; make that first call before any stream capture.  All calls
+ * share the one array: calls that overlap on the GPU (two problems on different streams,
+ * two host threads) race on it and must be serialised by the caller. */
+ots_status ots_get_commodity_flows_noalloc(ots_problem *p, int32_t t_begin, int32_t t_end,
+                                           int32_t l_begin, int32_t l_end, double *out);
+
 /* Current duals in natural-log form (Theorem 3 convention u = exp(-lambda/eps), so
  * lambda = -eps * log u).  log_u: host [(T-2) x n_states], rows t = 2..T-1;
  * log_U01: host [n_sources] aligned with the descriptor's source triples;

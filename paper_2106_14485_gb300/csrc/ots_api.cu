@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -958,6 +959,126 @@ ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_en
       int l = b.tri_l[q];
       if (l >= l_begin && l < l_end) blkp[(size_t)(l - l_begin) * S + b.tri_state[q]] += f[q];
     }
+  }
+  return OTS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free per-commodity flows.
+//
+// ots_get_commodity_flows obtains a temporary device buffer on every call.  Some callers
+// cannot allow that: a real-time loop that must not stall on the device allocator (cudaMalloc
+// can synchronise the whole device) between solver passes, or an application that gives this
+// library a fixed device-memory budget when the problem is created.  The variant
+// below computes the same flows with its scratch in one fixed array that lives in this
+// library's device image: kNoAllocMaxDoubles doubles (8 MiB) on every GPU that loads the
+// library, held until the process exits.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocMaxDoubles = size_t(1) << 20;     // flow slice: n_states x commodities
+constexpr size_t kNoAllocMaxTriples = 65536;               // boundary triples per side
+
+struct NoAllocScratch {
+  double flows[kNoAllocMaxDoubles];                        // [commodity - l0][state]
+  int tri_state[kNoAllocMaxTriples];                       // states of one side's triples
+};
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+// Scatter the per-triple boundary flows of commodities [l0, l1) into a zeroed
+// [commodity - l0][state] slice (triples are unique per (commodity, state)).
+__global__ void k_noalloc_scatter(int n, int l0, int l1, int S, const int *tri_l, const int *tri_state,
+                                  const double *flow, double *slice) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int l = tri_l[q];
+  if (l >= l0 && l < l1) slice[(size_t)(l - l0) * S + tri_state[q]] = flow[q];
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+NoAllocScratch *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once per device.
+ots_status noalloc_scratch(int dev, NoAllocScratch **out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(OTS_ERR_INVALID_ARG, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(OTS_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = (NoAllocScratch *)ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return OTS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ots_status ots_get_commodity_flows_noalloc(ots_problem *p, int32_t t_begin, int32_t t_end, int32_t l_begin,
+                                           int32_t l_end, double *out) {
+  g_last_error.clear();
+  if (!p || !out) return fail(OTS_ERR_INVALID_ARG, "NULL argument");
+  if (t_begin < 1 || t_end > p->T + 1 || t_begin >= t_end) return fail(OTS_ERR_INVALID_ARG, "bad t range");
+  if (l_begin < 0 || l_end > p->L || l_begin >= l_end) return fail(OTS_ERR_INVALID_ARG, "bad commodity range");
+  const size_t S = p->S, nl = l_end - l_begin, blk = S * nl;
+  if (blk > kNoAllocMaxDoubles)
+    return fail(OTS_ERR_INVALID_ARG,
+                "n_states x commodities = %zu exceeds the static buffer of %zu doubles; request fewer commodities",
+                blk, kNoAllocMaxDoubles);
+  if ((size_t)p->src.n > kNoAllocMaxTriples || (size_t)p->snk.n > kNoAllocMaxTriples)
+    return fail(OTS_ERR_INVALID_ARG, "more than %zu source or sink triples", kNoAllocMaxTriples);
+  DeviceGuard guard(p->dev);
+  NoAllocScratch *scr = nullptr;
+  ots_status st = noalloc_scratch(p->dev, &scr);
+  if (st) return st;
+  st = refresh_if_stale(p);
+  if (st) return st;
+  double *slice = scr->flows;
+  // forward pass at the current duals; interior rows come from the message panels
+  OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
+  for (int t = 2; t <= p->T - 1; ++t) {
+    if (t >= t_begin && t < t_end) {
+      OTS_CUDA(launch_commodity_flows(p->S, p->Lp, p->qs, l_begin, l_end, p->d_tail, p->d_head, p->a_hi(t - 1),
+                                      p->a_lo(t - 1), p->b_hi(t + 1), p->b_lo(t + 1), p->d_kl_hi, p->d_kl_lo,
+                                      p->d_klc_hi, p->d_klc_lo, p->d_logu + (size_t)t * S, slice, p->stream));
+      OTS_CUDA(cudaMemcpyAsync(out + (size_t)(t - t_begin) * blk, slice, sizeof(double) * blk,
+                               cudaMemcpyDeviceToHost, p->stream));
+      OTS_CUDA(cudaStreamSynchronize(p->stream));      // the slice is reused for the next t
+      p->kernels_launched += 1;
+      p->d2h_bytes += (long long)(sizeof(double) * blk);
+    }
+    OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
+  }
+  OTS_CUDA(launch_boundary_flows(p->src.n, p->Lp, p->qs, p->src.d_tri_l, p->src.d_tri_other, p->src.d_tri_logU,
+                                 p->b_hi(2), p->b_lo(2), p->src.d_flow, p->stream));
+  OTS_CUDA(launch_boundary_flows(p->snk.n, p->Lp, p->qs, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
+                                 p->a_hi(p->T - 1), p->a_lo(p->T - 1), p->snk.d_flow, p->stream));
+  p->kernels_launched += 1 + (p->T - 2) + 2;
+  // boundary rows t = 1 (sources) and t = T (sinks): scatter the per-triple flows into the
+  // zeroed slice; the states of the triples are copied from the problem's host-side list
+  for (int t : {1, p->T}) {
+    if (t < t_begin || t >= t_end) continue;
+    const Boundary &b = t == 1 ? p->src : p->snk;
+    OTS_CUDA(cudaMemsetAsync(slice, 0, sizeof(double) * blk, p->stream));
+    if (b.n > 0) {
+      OTS_CUDA(cudaMemcpyAsync(scr->tri_state, b.tri_state.data(), sizeof(int) * b.n, cudaMemcpyHostToDevice,
+                               p->stream));
+      k_noalloc_scatter<<<(b.n + 255) / 256, 256, 0, p->stream>>>(b.n, l_begin, l_end, p->S, b.d_tri_l,
+                                                                  scr->tri_state, b.d_flow, slice);
+      OTS_CUDA(cudaGetLastError());
+      p->kernels_launched += 1;
+      p->h2d_bytes += (long long)(sizeof(int) * b.n);
+    }
+    OTS_CUDA(cudaMemcpyAsync(out + (size_t)(t - t_begin) * blk, slice, sizeof(double) * blk, cudaMemcpyDeviceToHost,
+                             p->stream));
+    OTS_CUDA(cudaStreamSynchronize(p->stream));       // the slice is reused next
+    p->d2h_bytes += (long long)(sizeof(double) * blk);
   }
   return OTS_OK;
 }

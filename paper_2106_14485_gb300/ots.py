@@ -62,7 +62,7 @@ class SolveReport(ctypes.Structure):
 
 
 EXPORTED = ["ots_default_solve_opts", "ots_create_problem", "ots_sinkhorn_solve", "ots_iterate", "ots_get_flows",
-            "ots_get_commodity_flows", "ots_get_duals", "ots_set_duals", "ots_problem_info", "ots_last_pass_timing",
+            "ots_get_commodity_flows", "ots_get_commodity_flows_noalloc", "ots_get_duals", "ots_set_duals", "ots_problem_info", "ots_last_pass_timing",
             "ots_problem_stream", "ots_destroy_problem", "ots_status_string", "ots_last_error"]
 
 _lib = None
@@ -83,6 +83,8 @@ def load_library(path: str = LIB_PATH):
     lib.ots_iterate.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(SolveReport)]
     lib.ots_get_flows.argtypes = [P, ctypes.c_int32, ctypes.c_int32, _f64p]
     lib.ots_get_commodity_flows.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f64p]
+    lib.ots_get_commodity_flows_noalloc.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                    ctypes.c_int32, _f64p]
     lib.ots_get_duals.argtypes = [P, _f64p, _f64p, _f64p]
     lib.ots_set_duals.argtypes = [P, _f64p, _f64p, _f64p]
     lib.ots_problem_info.argtypes = [P, ctypes.POINTER(ProblemStats)]
@@ -96,7 +98,7 @@ def load_library(path: str = LIB_PATH):
     lib.ots_last_error.argtypes = []
     lib.ots_last_error.restype = ctypes.c_char_p
     for name in ("ots_default_solve_opts", "ots_create_problem", "ots_sinkhorn_solve", "ots_iterate",
-                 "ots_get_flows", "ots_get_commodity_flows", "ots_get_duals", "ots_set_duals", "ots_problem_info",
+                 "ots_get_flows", "ots_get_commodity_flows", "ots_get_commodity_flows_noalloc", "ots_get_duals", "ots_set_duals", "ots_problem_info",
                  "ots_last_pass_timing"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -245,6 +247,18 @@ def ots_get_commodity_flows(h: Handle, t_begin: int = 1, t_end: int | None = Non
     out = np.empty((t_end - t_begin, l_end - l_begin, h.n_states), np.float64)
     _check(load_library().ots_get_commodity_flows(h.ptr, int(t_begin), int(t_end), int(l_begin), int(l_end),
                                                   _ptr(out, ctypes.c_double)))
+    return out
+
+
+def ots_get_commodity_flows_noalloc(h: Handle, t_begin: int = 1, t_end: int | None = None, l_begin: int = 0,
+                                    l_end: int | None = None) -> np.ndarray:
+    """Same values as ots_get_commodity_flows; the library allocates no memory in this call
+    (its scratch is a fixed static device array, see include/ots.h for the limits)."""
+    t_end = h.T + 1 if t_end is None else t_end
+    l_end = h.L if l_end is None else l_end
+    out = np.empty((t_end - t_begin, l_end - l_begin, h.n_states), np.float64)
+    _check(load_library().ots_get_commodity_flows_noalloc(h.ptr, int(t_begin), int(t_end), int(l_begin),
+                                                          int(l_end), _ptr(out, ctypes.c_double)))
     return out
 
 
