@@ -24,13 +24,15 @@
 
 namespace ots {
 cudaError_t launch_step(bool fwd, bool pc, int G, int C, const StepArgs &a, cudaStream_t s);
+cudaError_t prepare_step_kernels(int G, int C, bool pc, int V, int *grid_fwd, int *grid_bwd);
 int step_grid(int V, int G);
 cudaError_t launch_boundary(const BndArgs &b, cudaStream_t s);
 int boundary_grid(int n_seg);
 cudaError_t launch_pass_begin(DevStats *st, cudaStream_t s);
 cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, cudaStream_t s);
 cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, double *logu,
-                           float *w_hi, float *w_lo, int reset, cudaStream_t s);
+                           float *w_hi, float *w_lo, int reset, const int *st_inpos, const int *st_outpos,
+                           double *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s);
 cudaError_t launch_fill_panel(size_t n, float *hi, lo_t *lo, cudaStream_t s);
 cudaError_t launch_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
                                    const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
@@ -102,6 +104,7 @@ struct ots_problem {
   int V = 0, E = 0, S = 0, L = 0, T = 0, G = 1, C = 1, Lp = 4;
   double eps = 1.0, mass = 0.0;
   QScale qs{};                                 // quantum of the message hi parts
+  int pgrid_fwd = 0, pgrid_bwd = 0;            // grids of the pipelined persistent kernels (0 = not used)
   bool pc = false;
 
   std::vector<int> tail, head;
@@ -119,6 +122,12 @@ struct ots_problem {
   lo_t *d_klc_lo = nullptr;
   float *d_w_hi = nullptr, *d_w_lo = nullptr;  // [T+1][S]
   double *d_logu = nullptr;                    // [T+1][S]
+  // CSR-ordered copies used by the pipelined kernels
+  int *d_st_inpos = nullptr, *d_st_outpos = nullptr, *d_in_outpos = nullptr;
+  float *d_in_kl_hi = nullptr, *d_in_kl_lo = nullptr, *d_in_logd_hi = nullptr, *d_in_logd_lo = nullptr;
+  double *d_in_cap = nullptr;
+  double *d_logu_in = nullptr;                 // [T+1][S] by in-CSR position
+  float *d_wout_hi = nullptr, *d_wout_lo = nullptr;  // [T+1][S] by out-CSR position
   double *d_flow = nullptr;                    // [T+1][S]
   float *d_a_hi[3] = {nullptr, nullptr, nullptr};
   lo_t *d_a_lo[3] = {nullptr, nullptr, nullptr};
@@ -203,6 +212,14 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   a.w_hi_t = p->d_w_hi + (size_t)t * p->S;
   a.w_lo_t = p->d_w_lo + (size_t)t * p->S;
   a.flow_t = p->d_flow + (size_t)t * p->S;
+  a.persist_grid_fwd = p->pgrid_fwd;
+  a.persist_grid_bwd = p->pgrid_bwd;
+  a.in_kl_hi = p->d_in_kl_hi; a.in_kl_lo = p->d_in_kl_lo;
+  a.in_logd_hi = p->d_in_logd_hi; a.in_logd_lo = p->d_in_logd_lo;
+  a.in_cap = p->d_in_cap; a.in_outpos = p->d_in_outpos;
+  a.logu_in_t = p->d_logu_in + (size_t)t * p->S;
+  a.wout_hi_t = p->d_wout_hi + (size_t)t * p->S;
+  a.wout_lo_t = p->d_wout_lo + (size_t)t * p->S;
   a.partials = p->d_partials;
   a.counter = p->d_counter;
   a.stats = p->d_stats;
@@ -284,7 +301,8 @@ ots_status build_pass_graph(ots_problem *p) {
 ots_status reset_duals(ots_problem *p) {
   p->kernels_launched += 2;
   OTS_CUDA(launch_weights(p->S, p->T, p->qs, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo, p->d_logu,
-                          p->d_w_hi, p->d_w_lo, 1, p->stream));
+                          p->d_w_hi, p->d_w_lo, 1, p->d_st_inpos, p->d_st_outpos, p->d_logu_in, p->d_wout_hi,
+                          p->d_wout_lo, p->stream));
   if (p->src.n) OTS_CUDA(cudaMemsetAsync(p->src.d_tri_logU, 0, sizeof(double) * p->src.n, p->stream));
   if (p->snk.n) OTS_CUDA(cudaMemsetAsync(p->snk.d_tri_logU, 0, sizeof(double) * p->snk.n, p->stream));
   OTS_CUDA(cudaMemsetAsync(p->d_report, 0, sizeof(PassReport), p->stream));
@@ -299,7 +317,8 @@ ots_status refresh_if_stale(ots_problem *p) {
   if (!p->stale) return OTS_OK;
   p->kernels_launched += 2;
   OTS_CUDA(launch_weights(p->S, p->T, p->qs, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo, p->d_logu,
-                          p->d_w_hi, p->d_w_lo, 0, p->stream));
+                          p->d_w_hi, p->d_w_lo, 0, p->d_st_inpos, p->d_st_outpos, p->d_logu_in, p->d_wout_hi,
+                          p->d_wout_lo, p->stream));
   OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
   ots_status st = enqueue_backward_sweep(p);
   if (st) return st;
@@ -644,6 +663,19 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
       }
   }
 
+  // ---- CSR-ordered copies (positions of every state in the in / out lists) ----
+  std::vector<int> st_inpos(p->S), st_outpos(p->S), in_outpos(p->S);
+  for (int k = 0; k < p->S; ++k) { st_inpos[in_state[k]] = k; st_outpos[out_state[k]] = k; }
+  for (int k = 0; k < p->S; ++k) in_outpos[k] = st_outpos[in_state[k]];
+  std::vector<float> in_kl_hi(p->S), in_kl_lo(p->S), in_logd_hi(p->S), in_logd_lo(p->S);
+  std::vector<double> in_cap(p->S);
+  for (int k = 0; k < p->S; ++k) {
+    const int st = in_state[k];
+    in_kl_hi[k] = kl_hi[st]; in_kl_lo[k] = kl_lo[st];
+    in_logd_hi[k] = logd_hi[st]; in_logd_lo[k] = logd_lo[st];
+    in_cap[k] = cap[st];
+  }
+
   // ---- boundary triples ----
   ots_status st = build_boundary(p, p->src, d->n_sources, d->src_commodity, d->src_state, d->src_mass, true);
   if (st) return bail(st);
@@ -680,6 +712,10 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
     p->own_stream = true;
   }
   if (cudaMallocHost(&p->h_report, sizeof(PassReport)) != cudaSuccess) return bail(fail(OTS_ERR_OOM, "pinned alloc failed"));
+  {
+    cudaError_t e = prepare_step_kernels(p->G, p->C, p->pc, p->V, &p->pgrid_fwd, &p->pgrid_bwd);
+    if (e != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(e)));
+  }
   for (int k = 0; k < 5; ++k)
     if (cudaEventCreate(&p->ev[k]) != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "event creation failed"));
 
@@ -695,6 +731,11 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   size_t o_klc_hi = p->pc ? cv.take<float>(S * p->Lp) : 0, o_klc_lo = p->pc ? cv.take<lo_t>(S * p->Lp) : 0;
   size_t o_w_hi = cv.take<float>((T + 1) * S), o_w_lo = cv.take<float>((T + 1) * S);
   size_t o_logu = cv.take<double>((T + 1) * S), o_flow = cv.take<double>((T + 1) * S);
+  size_t o_st_inpos = cv.take<int>(S), o_st_outpos = cv.take<int>(S), o_in_outpos = cv.take<int>(S);
+  size_t o_in_kl_hi = cv.take<float>(S), o_in_kl_lo = cv.take<float>(S), o_in_ld_hi = cv.take<float>(S),
+         o_in_ld_lo = cv.take<float>(S), o_in_cap = cv.take<double>(S);
+  size_t o_logu_in = cv.take<double>((T + 1) * S), o_wout_hi = cv.take<float>((T + 1) * S),
+         o_wout_lo = cv.take<float>((T + 1) * S);
   size_t o_a_hi[3], o_a_lo[3];
   for (int k = 0; k < 3; ++k) { o_a_hi[k] = cv.take<float>(panel); o_a_lo[k] = cv.take<lo_t>(panel); }
   size_t o_b_hi = cv.take<float>((T - 1) * panel), o_b_lo = cv.take<lo_t>((T - 1) * panel);
@@ -723,6 +764,11 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   if (p->pc) { p->d_klc_hi = (float *)at(o_klc_hi); p->d_klc_lo = (lo_t *)at(o_klc_lo); }
   p->d_w_hi = (float *)at(o_w_hi); p->d_w_lo = (float *)at(o_w_lo);
   p->d_logu = (double *)at(o_logu); p->d_flow = (double *)at(o_flow);
+  p->d_st_inpos = (int *)at(o_st_inpos); p->d_st_outpos = (int *)at(o_st_outpos); p->d_in_outpos = (int *)at(o_in_outpos);
+  p->d_in_kl_hi = (float *)at(o_in_kl_hi); p->d_in_kl_lo = (float *)at(o_in_kl_lo);
+  p->d_in_logd_hi = (float *)at(o_in_ld_hi); p->d_in_logd_lo = (float *)at(o_in_ld_lo);
+  p->d_in_cap = (double *)at(o_in_cap);
+  p->d_logu_in = (double *)at(o_logu_in); p->d_wout_hi = (float *)at(o_wout_hi); p->d_wout_lo = (float *)at(o_wout_lo);
   for (int k = 0; k < 3; ++k) { p->d_a_hi[k] = (float *)at(o_a_hi[k]); p->d_a_lo[k] = (lo_t *)at(o_a_lo[k]); }
   p->d_b_hi = (float *)at(o_b_hi); p->d_b_lo = (lo_t *)at(o_b_lo);
   p->d_stats = (DevStats *)at(o_stats); p->d_report = (PassReport *)at(o_report);
@@ -747,6 +793,9 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   UP(p->d_tail, p->tail); UP(p->d_head, p->head);
   UP(p->d_kl_hi, kl_hi); UP(p->d_kl_lo, kl_lo); UP(p->d_logd_hi, logd_hi); UP(p->d_logd_lo, logd_lo);
   UP(p->d_cap, cap);
+  UP(p->d_st_inpos, st_inpos); UP(p->d_st_outpos, st_outpos); UP(p->d_in_outpos, in_outpos);
+  UP(p->d_in_kl_hi, in_kl_hi); UP(p->d_in_kl_lo, in_kl_lo); UP(p->d_in_logd_hi, in_logd_hi);
+  UP(p->d_in_logd_lo, in_logd_lo); UP(p->d_in_cap, in_cap);
   if (p->pc) { UP(p->d_klc_hi, klc_hi); UP(p->d_klc_lo, klc_lo); }
   std::vector<std::vector<double>> logR(2);
   for (int k = 0; k < 2; ++k) {
@@ -762,7 +811,8 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
       cudaMemsetAsync(p->d_flow, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess)
     return bail(fail(OTS_ERR_CUDA, "memset failed"));
   // logu rows outside 2..T-1 stay 0; W rows likewise unused
-  if (cudaMemsetAsync(p->d_logu, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess)
+  if (cudaMemsetAsync(p->d_logu, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess ||
+      cudaMemsetAsync(p->d_logu_in, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess)
     return bail(fail(OTS_ERR_CUDA, "memset failed"));
   // boundary panels start at log 0 everywhere; only the support entries are rewritten
   p->kernels_launched += 2;

@@ -91,6 +91,18 @@ struct StepArgs {
   unsigned int *counter;      // last-block counter
   DevStats *stats;
   int mode;                   // 0: Sinkhorn update, 1: flows only (no update)
+  int persist_grid_fwd;       // > 0: pipelined persistent forward kernel with this grid
+  int persist_grid_bwd;       // > 0: pipelined persistent backward kernel with this grid
+  // CSR-ordered copies for the pipelined kernels (one independent load per work item):
+  const float *in_kl_hi;      // [S] log2 K_L of the state at in-CSR position j
+  const float *in_kl_lo;
+  const float *in_logd_hi;    // [S] log2 d at in-CSR position j
+  const float *in_logd_lo;
+  const double *in_cap;       // [S] d at in-CSR position j
+  const int *in_outpos;       // [S] out-CSR position of the state at in-CSR position j
+  double *logu_in_t;          // [S] log2 u_t by in-CSR position
+  float *wout_hi_t;           // [S] W_t by out-CSR position
+  float *wout_lo_t;
 };
 
 // Boundary kernels (sources, sinks): segments of (node, commodity) with their triples.

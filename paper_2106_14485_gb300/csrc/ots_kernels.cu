@@ -77,7 +77,7 @@ __device__ __forceinline__ void block_sum2(double &v0, double &v1, double *s0, d
 // counter for the next kernel.
 __device__ void block_sum2_last(double v0, double v1, double *partials, unsigned int *counter,
                                 double *dst0, double *dst1, int assign) {
-  __shared__ double s0[kBlock / 32], s1[kBlock / 32];
+  __shared__ double s0[32], s1[32];   // one slot per warp of any block size up to 1024 threads
   __shared__ bool is_last;
   block_sum2(v0, v1, s0, s1);
   if (threadIdx.x == 0) {
@@ -568,7 +568,8 @@ __global__ void k_pass_end(const DevStats *st, PassReport *rep, double mass, dou
 
 // W_t = log2 K_L + log2 u_t for t = 2..T-1 from log2 u (set to 0 first when reset).
 __global__ void k_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, double *logu, float *w_hi,
-                          float *w_lo, int reset) {
+                          float *w_lo, int reset, const int *st_inpos, const int *st_outpos, double *logu_in,
+                          float *wout_hi, float *wout_lo) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   for (int t = 2; t <= T - 1; ++t) {
@@ -581,6 +582,9 @@ __global__ void k_weights(int S, int T, QScale qs, const float *kl_hi, const flo
     make_w(kl_hi ? kl_hi[s] : 0.f, kl_lo ? kl_lo[s] : 0.f, luh, lul, qs, hi, lo);
     w_hi[(size_t)t * S + s] = hi;
     w_lo[(size_t)t * S + s] = lo;
+    logu_in[(size_t)t * S + st_inpos[s]] = lu;
+    wout_hi[(size_t)t * S + st_outpos[s]] = hi;
+    wout_lo[(size_t)t * S + st_outpos[s]] = lo;
   }
 }
 
@@ -625,6 +629,518 @@ __global__ void k_boundary_flows(int n, int Lp, QScale qs, const int *tri_l, con
 }
 
 // ------------------------------------------------------------------------------------
+// Pipelined persistent variants for G >= 64 (one node row of Lp = 4 G commodities per
+// block iteration; rank-1 K_L).  A work item is a node and up to kBatchTma of its in-states
+// (forward) or out-states (backward).  The rows an item gathers are fetched with TMA bulk
+// copies (cp.async.bulk) into one of two shared-memory stages while the block computes on the
+// other; an mbarrier with an expected byte count signals each stage.  Waits are bounded: a
+// wait that gives up records an error in the pass statistics instead of hanging.
+// ------------------------------------------------------------------------------------
+constexpr int kBatchTma = 5;
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < (1u << 22); ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+struct TmaItem {
+  int v, j0, nb;
+};
+
+__device__ __forceinline__ bool item_first(const int *ptr, int V, int KB, TmaItem &it) {
+  it.v = blockIdx.x;
+  if (it.v >= V) return false;
+  it.j0 = ptr[it.v];
+  it.nb = min(KB, ptr[it.v + 1] - it.j0);
+  return true;
+}
+
+__device__ __forceinline__ bool item_next(const int *ptr, int V, int KB, TmaItem &it) {
+  const int je = ptr[it.v + 1];
+  if (it.j0 + it.nb < je) {
+    it.j0 += it.nb;
+    it.nb = min(KB, je - it.j0);
+    return true;
+  }
+  it.v += gridDim.x;
+  if (it.v >= V) return false;
+  it.j0 = ptr[it.v];
+  it.nb = min(KB, ptr[it.v + 1] - it.j0);
+  return true;
+}
+
+// Producer (one thread): the rows of `it` into stage (hi, lo): forward puts B_{t+1}[v] in row
+// 0 and A_{t-1}[tail j] in rows 1..nb; backward puts B_{t+1}[head j] in rows 0..nb-1.
+template <bool FWD, int Lp>
+__device__ __forceinline__ void tma_issue(const StepArgs &a, const TmaItem &it, float *hi, lo_t *lo, uint32_t bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads of the stage are done
+  const int nrows = (FWD ? 1 : 0) + it.nb;
+  mbar_expect_tx(bar, (uint32_t)(nrows * Lp * (int)(sizeof(float) + sizeof(lo_t))));
+  int r = 0;
+  if (FWD) {
+    bulk_g2s(smem_u32(hi), a.y_hi + (size_t)it.v * Lp, Lp * sizeof(float), bar);
+    bulk_g2s(smem_u32(lo), a.y_lo + (size_t)it.v * Lp, Lp * sizeof(lo_t), bar);
+    r = 1;
+  }
+  for (int k = 0; k < it.nb; ++k) {
+    const size_t row = (size_t)a.nbr[it.j0 + k] * Lp;
+    bulk_g2s(smem_u32(hi + (r + k) * Lp), a.x_hi + row, Lp * sizeof(float), bar);
+    bulk_g2s(smem_u32(lo + (r + k) * Lp), a.x_lo + row, Lp * sizeof(lo_t), bar);
+  }
+}
+
+// Thread g's 4 entries of a staged row.
+__device__ __forceinline__ void srow(const float *hi, const lo_t *lo, int g, float h[4], uint32_t w[2]) {
+  const float4 x = reinterpret_cast<const float4 *>(hi)[g];
+  const uint2 y = reinterpret_cast<const uint2 *>(lo)[g];
+  h[0] = x.x; h[1] = x.y; h[2] = x.z; h[3] = x.w;
+  w[0] = y.x;
+  w[1] = y.y;
+}
+
+}  // namespace
+
+constexpr int kStages = 3;   // shared-memory stages of the pipelined kernels
+
+// Per-stage metadata written by the producer warp: the work item and everything the consumers
+// would otherwise fetch with dependent global loads.
+struct FwdMeta {
+  int v, j0, nb, last, valid;
+  int st[kBatchTma], outpos[kBatchTma], nbr[kBatchTma];
+  float kl_hi[kBatchTma], kl_lo[kBatchTma], logd_hi[kBatchTma], logd_lo[kBatchTma];
+  float w_hi[kBatchTma], w_lo[kBatchTma];      // flows mode: the stored weights
+  double cap[kBatchTma], lu_old[kBatchTma];
+};
+
+struct BwdMeta {
+  int v, j0, nb, last, valid;
+  int nbr[kBatchTma];
+  float w_hi[kBatchTma], w_lo[kBatchTma];
+};
+
+namespace {
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Named barrier among the G consumer threads (the producer warp does not take part).
+template <int G>
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(G) : "memory");
+}
+
+// Capacity update of one in-state from its column log-sum-exp, with the per-state inputs
+// prefetched into the stage metadata (same arithmetic as update_state).
+__device__ __forceinline__ void update_meta(int mode, const QScale &qs, float cm, float cs, float klh, float kll,
+                                            float ldh, float ldl, double cap, double lu_old, float win_hi,
+                                            float win_lo, float &w_hi, float &w_lo, double &lu_new, double &flow,
+                                            double &viol, double &dual) {
+  float col_hi = kNeg, col_lo = 0.f;
+  if (cm > kNegThresh && cs > 0.f) two_sum(cm, lg2(cs), col_hi, col_lo);
+  if (col_hi > kNegThresh) {
+    float s, e;
+    two_sum(col_hi, klh, s, e);
+    col_hi = s;
+    col_lo += e + kll;
+  }
+  if (mode != 0) {
+    w_hi = win_hi;
+    w_lo = win_lo;
+    flow = col_hi > kNegThresh && w_hi > kNegThresh ? exp2(lu_old + (double)col_hi + (double)col_lo) : 0.0;
+    lu_new = lu_old;
+    return;
+  }
+  float lu_hi = 0.f, lu_lo = 0.f;
+  if (isfinite(cap) && col_hi > kNegThresh) {
+    if (ldh < kNegThresh) {
+      lu_hi = kNeg;
+    } else {
+      float s1, e1, s2, e2;
+      two_sum(ldh, -col_hi, s1, e1);
+      e1 += ldl - col_lo;
+      two_sum(s1, e1, s2, e2);
+      if (s2 < 0.f) { lu_hi = s2; lu_lo = e2; }
+    }
+  }
+  make_w(klh, kll, lu_hi, lu_lo, qs, w_hi, w_lo);
+  if (col_hi > kNegThresh && isfinite(cap)) {
+    const float qv = (float)lu_old + col_hi - ldh;
+    if (qv > -1e-3f) {
+      const double p_old = exp2(lu_old + (double)col_hi + (double)col_lo);
+      if (p_old > cap) viol += p_old - cap;
+    }
+  }
+  if (col_hi != col_hi || col_lo != col_lo) viol = __longlong_as_double(0x7ff8000000000000LL);
+  lu_new = lu_hi < kNegThresh ? -1e30 : (double)lu_hi + (double)lu_lo;
+  if (isfinite(cap) && cap > 0.0) dual += cap * lu_new;
+}
+
+// Per-lane metadata of one work item (lane k < nb holds in-state / out-state k).
+struct LaneMeta {
+  int nbr, st, outpos;
+  float kl_hi, kl_lo, logd_hi, logd_lo, w_hi, w_lo;
+  double cap, lu_old;
+};
+
+// One independent round of loads per item: everything is stored in CSR order.
+template <bool FWD>
+__device__ __forceinline__ LaneMeta load_lane_meta(const StepArgs &a, const TmaItem &it, bool have, int lane) {
+  LaneMeta r{};
+  if (have && lane < it.nb) {
+    const int j = it.j0 + lane;
+    r.nbr = a.nbr[j];
+    if (FWD) {
+      r.st = a.state[j];
+      r.outpos = a.in_outpos[j];
+      r.kl_hi = a.in_kl_hi[j];
+      r.kl_lo = a.in_kl_lo[j];
+      r.logd_hi = a.in_logd_hi[j];
+      r.logd_lo = a.in_logd_lo[j];
+      r.cap = a.in_cap[j];
+      r.lu_old = a.logu_in_t[j];
+    } else {
+      r.w_hi = a.wout_hi_t[j];
+      r.w_lo = a.wout_lo_t[j];
+    }
+  }
+  return r;
+}
+
+// Producer warp: metadata of item i (loaded one iteration ahead) into stage s, then the bulk
+// copies of its rows (lane 0).  An exhausted item list writes a stop record.
+template <bool FWD, int Lp, typename Meta>
+__device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, float *st_hi, lo_t *st_lo,
+                                              uint64_t *full, uint64_t *empty, int rows, bool &timed_out) {
+  constexpr int KB = kBatchTma;
+  constexpr int NS = kStages;
+  const int lane = threadIdx.x & 31;
+  TmaItem it;
+  bool have = item_first(a.ptr, a.V, KB, it);
+  LaneMeta lm = load_lane_meta<FWD>(a, it, have, lane);
+  for (int i = 0;; ++i) {
+    const int s = i % NS;
+    TmaItem nx = it;
+    const bool have_nx = have && item_next(a.ptr, a.V, KB, nx);
+    const LaneMeta lm_nx = load_lane_meta<FWD>(a, nx, have_nx, lane);   // in flight during the wait
+    if (FWD && a.mode != 0 && have && lane < it.nb) {      // flows mode: stored weights
+      lm.w_hi = a.wout_hi_t[lm.outpos];
+      lm.w_lo = a.wout_lo_t[lm.outpos];
+    }
+    int ok = 1;
+    if (i >= NS && lane == 0) ok = mbar_wait(smem_u32(&empty[s]), ((i / NS) - 1) & 1) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) { timed_out = true; return; }
+    Meta &m = meta[s];
+    if (have && lane < it.nb) {
+      m.nbr[lane] = lm.nbr;
+      if constexpr (FWD) {
+        m.st[lane] = lm.st; m.outpos[lane] = lm.outpos;
+        m.kl_hi[lane] = lm.kl_hi; m.kl_lo[lane] = lm.kl_lo;
+        m.logd_hi[lane] = lm.logd_hi; m.logd_lo[lane] = lm.logd_lo;
+        m.cap[lane] = lm.cap; m.lu_old[lane] = lm.lu_old;
+        m.w_hi[lane] = lm.w_hi; m.w_lo[lane] = lm.w_lo;
+      } else {
+        m.w_hi[lane] = lm.w_hi; m.w_lo[lane] = lm.w_lo;
+      }
+    }
+    if (lane == 0) {
+      m.valid = have ? 1 : 0;
+      if (have) {
+        m.v = it.v; m.j0 = it.j0; m.nb = it.nb;
+        m.last = (!have_nx || nx.v != it.v) ? 1 : 0;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const uint32_t bar = smem_u32(&full[s]);
+      if (!have) {
+        mbar_expect_tx(bar, 0);
+      } else {
+        float *hi = st_hi + s * rows * Lp;
+        lo_t *lo = st_lo + s * rows * Lp;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const int nrows = (FWD ? 1 : 0) + it.nb;
+        mbar_expect_tx(bar, (uint32_t)(nrows * Lp * (int)(sizeof(float) + sizeof(lo_t))));
+        int r = 0;
+        if (FWD) {
+          bulk_g2s(smem_u32(hi), a.y_hi + (size_t)it.v * Lp, Lp * sizeof(float), bar);
+          bulk_g2s(smem_u32(lo), a.y_lo + (size_t)it.v * Lp, Lp * sizeof(lo_t), bar);
+          r = 1;
+        }
+        for (int k = 0; k < it.nb; ++k) {
+          const size_t row = (size_t)m.nbr[k] * Lp;
+          bulk_g2s(smem_u32(hi + (r + k) * Lp), a.x_hi + row, Lp * sizeof(float), bar);
+          bulk_g2s(smem_u32(lo + (r + k) * Lp), a.x_lo + row, Lp * sizeof(lo_t), bar);
+        }
+      }
+    }
+    if (!have) return;
+    it = nx;
+    have = have_nx;
+    lm = lm_nx;
+  }
+}
+
+// Consumer aggregation of one staged item into the running (M, acc) of the thread's 4 entries.
+template <int KB>
+__device__ __forceinline__ void aggregate_staged(const float *hs, const lo_t *ls, int Lp, int g, int nb,
+                                                 const float (&wh)[KB], const float (&wlb)[KB], float lo_unit,
+                                                 float (&M)[4], float (&acc)[4]) {
+  float hk[KB][4];
+  uint32_t wk[KB][2];
+#pragma unroll
+  for (int k = 0; k < KB; ++k)
+    if (k < nb) srow(hs + k * Lp, ls + k * Lp, g, hk[k], wk[k]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float sv[KB];
+    float m = 2.f * kNeg;
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      sv[k] = k < nb ? hk[k][q] + wh[k] : 2.f * kNeg;
+      m = fmaxf(m, sv[k]);
+    }
+    if (m > kNegThresh) {
+      float sum = 0.f;
+#pragma unroll
+      for (int k = 0; k < KB; ++k)
+        if (k < nb) sum += ex2(fmaf(lo_inj(wk[k], q), lo_unit, (sv[k] - m) + wlb[k]));
+      const float Mo = M[q];
+      if (m > Mo) {
+        acc[q] = fmaf(acc[q], ex2(Mo - m), sum);
+        M[q] = m;
+      } else {
+        acc[q] = fmaf(sum, ex2(m - Mo), acc[q]);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// Forward step, warp-specialised: G consumer threads (one node row) + one producer warp.
+template <int G>
+__global__ void __launch_bounds__(G + 32) k_forward_tma(const StepArgs a) {
+  constexpr int Lp = 4 * G;
+  constexpr int KB = kBatchTma;
+  constexpr int ROWS = KB + 1;
+  constexpr int NW = G / 32;
+  constexpr int NS = kStages;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float *st_hi = reinterpret_cast<float *>(smem);                                    // [NS][ROWS][Lp]
+  lo_t *st_lo = reinterpret_cast<lo_t *>(smem + NS * ROWS * Lp * sizeof(float));    // [NS][ROWS][Lp]
+  __shared__ __align__(8) uint64_t full[NS], empty[NS];
+  __shared__ FwdMeta meta[NS];
+  __shared__ float xch[2][2 * KB * NW];
+  const int g = threadIdx.x, lane = g & 31, wid = g >> 5;
+  if (g == 0) {
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(smem_u32(&full[k]), 1);
+      mbar_init(smem_u32(&empty[k]), NW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  double viol = 0.0, dual = 0.0;
+  bool timed_out = false;
+  if (wid == NW) {
+    // ---------------- producer warp ----------------
+    producer_loop<true, Lp, FwdMeta>(a, meta, st_hi, st_lo, full, empty, ROWS, timed_out);
+  } else {
+    // ---------------- consumers ----------------
+    const float lo_unit = a.qs.lo_unit;
+    float M[4], acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { M[q] = 2.f * kNeg; acc[q] = 0.f; }
+    for (int i = 0;; ++i) {
+      const int s = i % NS;
+      if (!mbar_wait(smem_u32(&full[s]), (i / NS) & 1)) { timed_out = true; break; }
+      const FwdMeta &m = meta[s];
+      if (!m.valid) break;
+      const int nb = m.nb;
+      const float *hs = st_hi + s * ROWS * Lp;
+      const lo_t *ls = st_lo + s * ROWS * Lp;
+      float bh[4], blb[4];
+      {
+        uint32_t w[2];
+        srow(hs, ls, g, bh, w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) blb[q] = lo_inj(w, q) - 2.f * kLoBias;   // exact
+      }
+      // (1) column log-sum-exp per in-state: warp max, then warp sum of ex2 terms
+      float cm[KB], cs[KB];
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        float mm = 2.f * kNeg;
+        if (k < nb) {
+          const float4 x = reinterpret_cast<const float4 *>(hs + (1 + k) * Lp)[g];
+          mm = fmaxf(fmaxf(x.x + bh[0], x.y + bh[1]), fmaxf(x.z + bh[2], x.w + bh[3]));
+        }
+        cm[k] = mm;
+      }
+      group_reduce<32, KB, true>(cm, nullptr);
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        float sum = 0.f;
+        if (k < nb && cm[k] > kNegThresh) {
+          float h[4];
+          uint32_t w[2];
+          srow(hs + (1 + k) * Lp, ls + (1 + k) * Lp, g, h, w);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) sum += ex2(fmaf(lo_inj(w, q) + blb[q], lo_unit, (h[q] + bh[q]) - cm[k]));
+        }
+        cs[k] = sum;
+      }
+      group_reduce<32, KB, false>(cs, nullptr);
+      // (2) exchange the warps' pairs; lane k of every warp merges in-state k and derives W
+      float mk = cm[0], sk_ = cs[0];
+#pragma unroll
+      for (int k = 1; k < KB; ++k)
+        if (k == lane) { mk = cm[k]; sk_ = cs[k]; }
+      float *xb = xch[i & 1];
+      if (lane < nb) { xb[(2 * lane) * NW + wid] = mk; xb[(2 * lane + 1) * NW + wid] = sk_; }
+      consumers_sync<G>();
+      float mh = kNeg, ml = 0.f;
+      if (lane < nb) {
+        mk = xb[(2 * lane) * NW];
+        sk_ = xb[(2 * lane + 1) * NW];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) lse_merge(mk, sk_, xb[(2 * lane) * NW + w], xb[(2 * lane + 1) * NW + w]);
+        double lu_new = 0.0, flow = 0.0, v0 = 0.0, v1 = 0.0;
+        update_meta(a.mode, a.qs, mk, sk_, m.kl_hi[lane], m.kl_lo[lane], m.logd_hi[lane], m.logd_lo[lane],
+                    m.cap[lane], m.lu_old[lane], m.w_hi[lane], m.w_lo[lane], mh, ml, lu_new, flow, v0, v1);
+        if (wid == 0) {
+          const int st = m.st[lane];
+          if (a.mode == 0) {
+            viol += v0;
+            dual += v1;
+            a.logu_t[st] = lu_new;
+            a.logu_in_t[m.j0 + lane] = lu_new;
+            a.w_hi_t[st] = mh;
+            a.w_lo_t[st] = ml;
+            a.wout_hi_t[m.outpos[lane]] = mh;
+            a.wout_lo_t[m.outpos[lane]] = ml;
+          } else {
+            a.flow_t[st] = flow;
+          }
+        }
+      }
+      float wh[KB], wlb[KB];
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        wh[k] = __shfl_sync(0xffffffffu, mh, k);
+        wlb[k] = __shfl_sync(0xffffffffu, ml, k) - kLoBias * lo_unit;
+      }
+      // (3) A_t[v] accumulates A_{t-1}[y] + W_t[state] over the item's in-states
+      aggregate_staged<KB>(hs + Lp, ls + Lp, Lp, g, nb, wh, wlb, lo_unit, M, acc);
+      if (m.last) {
+        float oh[4];
+        lo_t ol[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          lse_encode(M[q], acc[q], a.qs, oh[q], ol[q]);
+          M[q] = 2.f * kNeg;
+          acc[q] = 0.f;
+        }
+        store4(a.out_hi + (size_t)m.v * Lp + 4 * g, a.out_lo + (size_t)m.v * Lp + 4 * g, oh, ol);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+    }
+  }
+  if (timed_out) atomicAdd(&a.stats->bad, 1e6);
+  block_sum2_last(viol, dual, a.partials, a.counter, &a.stats->cap_viol, &a.stats->dual_cap, 0);
+}
+
+// Backward step, warp-specialised like the forward step.
+template <int G>
+__global__ void __launch_bounds__(G + 32) k_backward_tma(const StepArgs a) {
+  constexpr int Lp = 4 * G;
+  constexpr int KB = kBatchTma;
+  constexpr int ROWS = KB;
+  constexpr int NW = G / 32;
+  constexpr int NS = kStages;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float *st_hi = reinterpret_cast<float *>(smem);
+  lo_t *st_lo = reinterpret_cast<lo_t *>(smem + NS * ROWS * Lp * sizeof(float));
+  __shared__ __align__(8) uint64_t full[NS], empty[NS];
+  __shared__ BwdMeta meta[NS];
+  const int g = threadIdx.x, lane = g & 31, wid = g >> 5;
+  if (g == 0) {
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(smem_u32(&full[k]), 1);
+      mbar_init(smem_u32(&empty[k]), NW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool timed_out = false;
+  if (wid == NW) {
+    producer_loop<false, Lp, BwdMeta>(a, meta, st_hi, st_lo, full, empty, ROWS, timed_out);
+  } else {
+    const float lo_unit = a.qs.lo_unit;
+    float M[4], acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { M[q] = 2.f * kNeg; acc[q] = 0.f; }
+    for (int i = 0;; ++i) {
+      const int s = i % NS;
+      if (!mbar_wait(smem_u32(&full[s]), (i / NS) & 1)) { timed_out = true; break; }
+      const BwdMeta &m = meta[s];
+      if (!m.valid) break;
+      const int nb = m.nb;
+      float wh[KB], wlb[KB];
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        wh[k] = k < nb ? m.w_hi[k] : kNeg;
+        wlb[k] = (k < nb ? m.w_lo[k] : 0.f) - kLoBias * lo_unit;
+      }
+      aggregate_staged<KB>(st_hi + s * ROWS * Lp, st_lo + s * ROWS * Lp, Lp, g, nb, wh, wlb, lo_unit, M, acc);
+      if (m.last) {
+        float oh[4];
+        lo_t ol[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          lse_encode(M[q], acc[q], a.qs, oh[q], ol[q]);
+          M[q] = 2.f * kNeg;
+          acc[q] = 0.f;
+        }
+        store4(a.out_hi + (size_t)m.v * Lp + 4 * g, a.out_lo + (size_t)m.v * Lp + 4 * g, oh, ol);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+    }
+  }
+  if (timed_out) atomicAdd(&a.stats->bad, 1e6);
+}
+
+// ------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------
 
@@ -650,7 +1166,57 @@ static cudaError_t launch_step_g(int G, int C, const StepArgs &a, cudaStream_t s
   return cudaErrorInvalidValue;
 }
 
+template <int G>
+static size_t tma_smem(bool fwd) {
+  return (size_t)kStages * (fwd ? kBatchTma + 1 : kBatchTma) * 4 * G * (sizeof(float) + sizeof(lo_t));
+}
+
+template <int G>
+static cudaError_t launch_tma_t(bool fwd, const StepArgs &a, int grid, cudaStream_t s) {
+  if (fwd) k_forward_tma<G><<<grid, G + 32, tma_smem<G>(true), s>>>(a);
+  else k_backward_tma<G><<<grid, G + 32, tma_smem<G>(false), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int G>
+static cudaError_t prepare_tma_t(int n_sm, int V, int *grid_fwd, int *grid_bwd) {
+  cudaError_t e = cudaFuncSetAttribute(k_forward_tma<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<G>(true));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_backward_tma<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<G>(false));
+  if (e != cudaSuccess) return e;
+  int bf = 0, bb = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_forward_tma<G>, G + 32, tma_smem<G>(true));
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_backward_tma<G>, G + 32, tma_smem<G>(false));
+  if (e != cudaSuccess) return e;
+  *grid_fwd = bf > 0 ? min(V, n_sm * bf) : 0;
+  *grid_bwd = bb > 0 ? min(V, n_sm * bb) : 0;
+  return cudaSuccess;
+}
+
+// Set up the pipelined persistent kernels for this problem (before any graph capture):
+// grid sizes 0 mean "use the register kernels".
+cudaError_t prepare_step_kernels(int G, int C, bool pc, int V, int *grid_fwd, int *grid_bwd) {
+  *grid_fwd = 0;
+  *grid_bwd = 0;
+  if (pc || C != 1 || (G != 64 && G != 128 && G != 256)) return cudaSuccess;
+  int dev = 0, n_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (G == 64) return prepare_tma_t<64>(n_sm, V, grid_fwd, grid_bwd);
+  if (G == 128) return prepare_tma_t<128>(n_sm, V, grid_fwd, grid_bwd);
+  return prepare_tma_t<256>(n_sm, V, grid_fwd, grid_bwd);
+}
+
 cudaError_t launch_step(bool fwd, bool pc, int G, int C, const StepArgs &a, cudaStream_t s) {
+  const int pgrid = fwd ? a.persist_grid_fwd : a.persist_grid_bwd;
+  if (pgrid > 0 && !pc && C == 1) {
+    if (G == 64) return launch_tma_t<64>(fwd, a, pgrid, s);
+    if (G == 128) return launch_tma_t<128>(fwd, a, pgrid, s);
+    if (G == 256) return launch_tma_t<256>(fwd, a, pgrid, s);
+  }
   if (fwd) return pc ? launch_step_g<true, true>(G, C, a, s) : launch_step_g<true, false>(G, C, a, s);
   return pc ? launch_step_g<false, true>(G, C, a, s) : launch_step_g<false, false>(G, C, a, s);
 }
@@ -676,8 +1242,10 @@ cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, do
 }
 
 cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, double *logu,
-                           float *w_hi, float *w_lo, int reset, cudaStream_t s) {
-  k_weights<<<(S + 255) / 256, 256, 0, s>>>(S, T, qs, kl_hi, kl_lo, logu, w_hi, w_lo, reset);
+                           float *w_hi, float *w_lo, int reset, const int *st_inpos, const int *st_outpos,
+                           double *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s) {
+  k_weights<<<(S + 255) / 256, 256, 0, s>>>(S, T, qs, kl_hi, kl_lo, logu, w_hi, w_lo, reset, st_inpos, st_outpos,
+                                            logu_in, wout_hi, wout_lo);
   return cudaGetLastError();
 }
 

@@ -61,10 +61,13 @@ def test_config1_converged(O, seed):
     O.ots_destroy_problem(h)
 
 
-@pytest.mark.parametrize("L,eps", [(9, 0.05), (37, 0.02), (64, 0.01)])
-def test_capacitated_converged(O, L, eps):
-    """Binding capacities, several commodities (ragged L: 9 -> 16, 37 -> 64 padded lanes)."""
-    inst = capped_rgg(seed=L, L=L, eps=eps, T=18)
+@pytest.mark.parametrize("L,eps,seed,lo,hi", [(9, 0.05, 9, 0.15, 0.4), (37, 0.02, 37, 0.15, 0.4),
+                                              (64, 0.01, 64, 0.15, 0.4), (200, 0.05, 7, 0.05, 0.15),
+                                              (500, 0.05, 7, 0.05, 0.15), (1000, 0.05, 7, 0.05, 0.15)])
+def test_capacitated_converged(O, L, eps, seed, lo, hi):
+    """Binding capacities, several commodities (ragged L: 9 -> 16, 37 -> 64, 200 -> 256,
+    500 -> 512 padded lanes; L >= 200 runs the pipelined persistent kernels)."""
+    inst = capped_rgg(seed=seed, L=L, eps=eps, T=18, lo=lo, hi=hi)
     o = Oracle(inst)
     ro = o.solve(max_iters=100000, tol=1e-11)
     assert ro["status"] == 0 and ro["cap_viol"] <= 1e-11
