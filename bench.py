@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="instances of the batched workload (uneven random geometric graphs); 0 = skip")
+    ap.add_argument("--batch-max-passes", type=int, default=3000)
     ap.add_argument("--horizon", type=int, default=100,
                     help="T of the traffic-scale grid (100 = the benchmark workload; smaller values only "
                          "for profiling captures that must stay within a few GB)")
@@ -235,6 +238,109 @@ def run_reference(args):
     return 0
 
 
+def pct(a, q):
+    return float(np.percentile(np.asarray(a), q)) if len(a) else None
+
+
+def bench_batch(args, ots, torch, local):
+    """Batched workload: args.batch uneven instances (n ~ U{50..2000} random geometric graphs of
+    mean degree 6, T ~ U{10..80}, L ~ U{1..128}, capacities U[0.2,1] * mass / 8, eps = 0.01)
+    solved to marginal error <= tol (a) in one batch (persistent tick kernel, captured graphs,
+    autotuned thread mapping) and (b) one instance at a time with ots_sinkhorn_solve (the
+    plain single-instance GPU solver, convergence tested after every pass).  Both arms start
+    from host arrays and end with the flows on the host."""
+    from paper_2106_14485_gb300 import instances
+    t0 = time.perf_counter()
+    insts = instances.config4(0, count=args.batch, workers=min(16, os.cpu_count() or 1))
+    gen_s = time.perf_counter() - t0
+    need = 0
+    for x in insts:
+        g = 1
+        while 4 * g < x.L:
+            g <<= 1
+        Lp = 4 * g
+        need += (x.T - 1) * x.n_nodes * Lp * 6 + 3 * x.n_nodes * Lp * 6 + (x.T + 1) * x.n_states * 24 + x.n_states * 64
+    free, _ = torch.cuda.mem_get_info(local)
+    pool = int(min(max(2 * need, 1 << 30), 0.6 * free))
+    b = ots.ots_batch_create(device=local, pool_bytes=pool, max_instances=max(args.batch, 1), ticks_per_launch=32)
+    tune_path = os.path.join(tempfile.gettempdir(), f"ots_batch_tune_dev{local}.json")
+    t0 = time.perf_counter()
+    ots.ots_batch_autotune(b, tune_path)
+    tune_s = time.perf_counter() - t0
+    mapping = {f"L<={4 << c}": ots.ots_batch_mapping(b, 4 << c) for c in range(7)}
+    # warm-up: a few instances through the whole batch path
+    for x in insts[:8]:
+        ots.ots_batch_add(b, x, tol=args.tol, max_iters=args.batch_max_passes)
+    ots.ots_batch_run(b)
+    for i in list(b.shapes):
+        ots.ots_batch_remove(b, i)
+    info0 = ots.ots_batch_info(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ids = [ots.ots_batch_add(b, x, tol=args.tol, max_iters=args.batch_max_passes) for x in insts]
+    t_add = time.perf_counter()
+    ots.ots_batch_run(b)
+    t_run = time.perf_counter()
+    flows_b, st_b = [], []
+    for i in ids:
+        st_b.append(ots.ots_batch_status(b, i))
+        flows_b.append(ots.ots_batch_get_flows(b, i) if st_b[-1]["status"] in (0, ots.OTS_ERR_NOT_CONVERGED) else None)
+    t_end = time.perf_counter()
+    info1 = ots.ots_batch_info(b)
+    lat_b = [s["seconds"] for s in st_b]
+    ots.ots_batch_destroy(b)
+
+    # plain single-instance solver, one instance at a time
+    lat_p, solve_p, flows_p, st_p = [], [], [], []
+    launches_p = 0
+    for x in insts[:4]:                      # warm-up
+        h = ots.ots_create_problem(x, device=local)
+        ots.ots_sinkhorn_solve(h, tol=args.tol, max_iters=args.batch_max_passes, check_every=1, raise_on_error=False)
+        ots.ots_destroy_problem(h)
+    torch.cuda.synchronize()
+    tp0 = time.perf_counter()
+    for x in insts:
+        ta = time.perf_counter()
+        h = ots.ots_create_problem(x, device=local)
+        tb = time.perf_counter()
+        r = ots.ots_sinkhorn_solve(h, tol=args.tol, max_iters=args.batch_max_passes, check_every=1,
+                                   raise_on_error=False)
+        tc = time.perf_counter()
+        F = ots.ots_get_flows(h) if r["status"] in (0, ots.OTS_ERR_NOT_CONVERGED) else None
+        launches_p += ots.ots_problem_info(h)["kernels_launched"]
+        ots.ots_destroy_problem(h)
+        lat_p.append(time.perf_counter() - ta)
+        solve_p.append(tc - tb)
+        flows_p.append(F)
+        st_p.append(r)
+    tp1 = time.perf_counter()
+    diffs = [float(np.abs(fb - fp).sum() / np.abs(fp).sum()) for fb, fp in zip(flows_b, flows_p)
+             if fb is not None and fp is not None]
+    n = len(insts)
+    conv_b = sum(1 for s in st_b if s["status"] == 0)
+    conv_p = sum(1 for s in st_p if s["status"] == 0)
+    upd = sum(s["iterations"] * x.n_updates_per_iteration() for s, x in zip(st_b, insts))
+    return {
+        "workload": f"{n} uneven instances: random geometric graphs n~U{{50..2000}} (mean degree 6), "
+                    f"T~U{{10..80}}, L~U{{1..128}}, capacities U[0.2,1]*mass/8, eps=0.01, tol={args.tol}",
+        "batched": {"solves_per_s": n / (t_end - t0), "solve_only_per_s": n / (t_run - t_add),
+                    "updates_per_s": upd / (t_run - t_add),
+                    "add_s": t_add - t0, "run_s": t_run - t_add, "flows_readback_s": t_end - t_run,
+                    "p50_ms": pct(lat_b, 50) * 1e3, "p99_ms": pct(lat_b, 99) * 1e3, "converged": conv_b,
+                    "passes_mean": float(np.mean([s["iterations"] for s in st_b])),
+                    "max_src_residual": max(s["src_residual"] for s in st_b),
+                    "max_cap_violation": max(s["cap_violation"] for s in st_b),
+                    "tick_launches": int(info1["ticks"] - info0["ticks"]),
+                    "graph_launches": int(info1["launches"] - info0["launches"]),
+                    "mapping": mapping, "autotune_s": tune_s},
+        "plain": {"solves_per_s": n / (tp1 - tp0), "solve_only_per_s": n / float(np.sum(solve_p)),
+                  "p50_ms": pct(lat_p, 50) * 1e3, "p99_ms": pct(lat_p, 99) * 1e3, "converged": conv_p,
+                  "kernel_launches": int(launches_p)},
+        "max_rel_flow_diff_batched_vs_plain": max(diffs) if diffs else None,
+        "generate_s": gen_s,
+    }
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -340,6 +446,8 @@ def run_ours(args):
                   "p99_ms": float(np.percentile(lat, 99) * 1e3), "final_src_residual": rs["src_residual"],
                   "final_cap_violation": rs["cap_violation"]}
 
+    batch = bench_batch(args, ots, torch, local) if args.batch > 0 else None
+
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -370,7 +478,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 float-float (fp32 hi + fp16 lo log2 messages), f64 reductions",
             "data": "synthetic", "config": workload_config(inst, args.tol),
-            "solves_per_s": solves,
+            "solves_per_s": solves, "batch": batch,
             "passes_timed": args.steps, "src_residual_after": final["src_residual"],
             "cap_violation_after": final["cap_violation"],
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches)}

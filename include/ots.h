@@ -53,7 +53,8 @@ typedef enum ots_status {
   OTS_ERR_TIMEOUT = 4,       /* timeout_ms elapsed before convergence */
   OTS_ERR_OOM = 5,           /* device or host allocation failed */
   OTS_ERR_CUDA = 6,          /* a CUDA runtime call failed (see ots_last_error) */
-  OTS_ERR_NUMERIC = 7        /* a NaN appeared in the convergence measures */
+  OTS_ERR_NUMERIC = 7,       /* a NaN appeared in the convergence measures */
+  OTS_PENDING = 8            /* batch / server: the instance has not finished yet */
 } ots_status;
 
 typedef struct ots_problem ots_problem;
@@ -208,6 +209,101 @@ ots_status ots_last_pass_timing(ots_problem *p, double *ms);
 /* The cudaStream_t (as void*) on which all device work of the problem runs, so a caller can
  * order its own work or record timing events around the solver's.  NULL if p is NULL. */
 void *ots_problem_stream(const ots_problem *p);
+
+/* ------------------------------------------------------------------------------------
+ * Batches: many independent instances resident on one device, advanced together.
+ *
+ * The paper solves one instance at a time; a batch is this library's way of running many
+ * small instances at once without one kernel launch per Sinkhorn step of each.  Every
+ * instance in a batch runs Algorithm 2 exactly as ots_sinkhorn_solve does (same updates,
+ * convergence measured after every pass), but all resident instances advance by one
+ * step per launch of one persistent kernel, each at its own position in its own step
+ * sequence, and launches are replayed from a captured CUDA graph.  When an instance has
+ * converged (or reached its pass limit) the batch also computes its flows; its slot can
+ * then be reused.  Results do not depend on which other instances share the batch.
+ *
+ * Limits of batched instances: L <= 256 commodities, commodity-independent costs
+ * (commodity_cost must be NULL), duals start from the initialisation of Algorithm 2
+ * (no warm start).  Device memory of the instances comes from one pool allocated at
+ * ots_batch_create (admission by memory: ots_batch_add returns OTS_ERR_OOM when the
+ * instance does not fit in what is free).
+ * ------------------------------------------------------------------------------------ */
+typedef struct ots_batch ots_batch;
+
+typedef struct ots_batch_desc {
+  int32_t device;
+  void *stream;              /* cudaStream_t for all work of the batch; NULL = own stream */
+  int64_t pool_bytes;        /* device memory for resident instances */
+  int32_t max_instances;     /* instances resident at once (slots) */
+  int32_t max_items;         /* work items per tick (0 = 1 << 20); an instance of V nodes
+                                with thread mapping G takes ceil(V G / 256) items */
+  int32_t ticks_per_launch;  /* steps per graph launch (0 = 32) */
+  ots_alloc_fn alloc;        /* optional allocator for the pool (both or neither) */
+  ots_free_fn free_fn;
+  void *alloc_ctx;
+} ots_batch_desc;
+
+/* Counters of a batch. */
+typedef struct ots_batch_stats {
+  int32_t resident;          /* instances holding a slot (running or finished, not removed) */
+  int32_t running;           /* instances still iterating */
+  int64_t pool_bytes;
+  int64_t pool_used;         /* bytes of the pool held by resident instances */
+  int64_t launches;          /* graph launches so far */
+  int64_t ticks;             /* tick kernels launched so far */
+  int64_t items;             /* items in the current tick list */
+  int64_t h2d_bytes;
+  int64_t d2h_bytes;
+} ots_batch_stats;
+
+/* Fill d with defaults: device 0, own stream, 4 GiB pool, 256 slots. */
+ots_status ots_default_batch_desc(ots_batch_desc *d);
+
+ots_status ots_batch_create(const ots_batch_desc *desc, ots_batch **out);
+
+/* Validate and copy an instance into the batch (same descriptor as ots_create_problem;
+ * its device, stream and allocator fields are ignored).  opts may be NULL: tol and
+ * max_iters (a pass limit) are used, the other fields are ignored.  The instance starts
+ * iterating with the next ots_batch_run.  *id identifies it until ots_batch_remove.
+ * OTS_ERR_OOM: no free slot or not enough free pool memory (nothing is kept). */
+ots_status ots_batch_add(ots_batch *b, const ots_problem_desc *desc, const ots_solve_opts *opts, int32_t *id);
+
+/* Advance the batch by up to max_launches graph launches, returning early once no
+ * instance is running; *n_running (may be NULL) receives the number still running. */
+ots_status ots_batch_run(ots_batch *b, int32_t max_launches, int32_t *n_running);
+
+/* OTS_PENDING while the instance runs; afterwards its final status (OTS_OK,
+ * OTS_ERR_NOT_CONVERGED, OTS_ERR_INFEASIBLE, OTS_ERR_NUMERIC, OTS_ERR_TIMEOUT) with the
+ * measures of its last pass in rep (may be NULL; seconds = time from add to the launch
+ * that finished it). */
+ots_status ots_batch_status(ots_batch *b, int32_t id, ots_solve_report *rep);
+
+/* Flows of a finished instance (OTS_OK or OTS_ERR_NOT_CONVERGED), computed by the batch at
+ * its final duals; same layout as ots_get_flows.  OTS_PENDING while it runs. */
+ots_status ots_batch_get_flows(ots_batch *b, int32_t id, int32_t t_begin, int32_t t_end, double *out);
+
+/* Duals of an instance, same layout as ots_get_duals (any pointer may be NULL). */
+ots_status ots_batch_get_duals(ots_batch *b, int32_t id, double *log_u, double *log_U01, double *log_U0T);
+
+/* Stop (if running) and release an instance: its slot and pool memory become free. */
+ots_status ots_batch_remove(ots_batch *b, int32_t id);
+
+ots_status ots_batch_info(const ots_batch *b, ots_batch_stats *out);
+
+/* Thread mapping used for instances with L commodities: G threads per node row (a power of
+ * two <= 32, 32 / G node rows per warp) and C = 1 or 2 chunks of 4 commodities per thread
+ * (panel width 4 G C >= L).  Without tuning: C = 1 up to L = 128, then C = 2. */
+ots_status ots_batch_mapping(const ots_batch *b, int32_t L, int32_t *G, int32_t *C);
+
+/* Autotuner: for every class of commodity counts (L up to 4, 8, 16, ..., 256) time the tick
+ * kernel with each admissible chunk count C in {1, 2} on a synthetic grid instance and
+ * keep the fastest per class.  With cache_path != NULL the table is read from that JSON
+ * file when it exists and was made on the same device model, else measured and written
+ * there.  Only affects instances added afterwards.  The batch must hold no instance. */
+ots_status ots_batch_autotune(ots_batch *b, const char *cache_path);
+
+/* Release everything of the batch (NULL is ignored). */
+void ots_batch_destroy(ots_batch *b);
 
 /* Free all device and host memory of the problem (NULL is ignored). */
 void ots_destroy_problem(ots_problem *p);

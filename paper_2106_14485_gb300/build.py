@@ -1,6 +1,6 @@
 """Build the sm_103a solver library ``libots.so`` in-tree with nvcc (no CMake, no torch).
 
-The two translation units are compiled in parallel and linked into one shared library
+The translation units are compiled in parallel and linked into one shared library
 exporting the C ABI of ``include/ots.h``.
 """
 from __future__ import annotations
@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libots.so")
-SOURCES = ["ots_api.cu", "ots_kernels.cu"]
+SOURCES = ["ots_api.cu", "ots_kernels.cu", "ots_batch.cu", "ots_batch_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
 

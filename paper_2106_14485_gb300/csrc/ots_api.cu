@@ -21,31 +21,12 @@
 
 #include "ots.h"
 #include "ots_device.cuh"
-
-namespace ots {
-cudaError_t launch_step(bool fwd, bool pc, int G, int C, const StepArgs &a, cudaStream_t s);
-cudaError_t prepare_step_kernels(int G, int C, bool pc, int V, int *grid_fwd, int *grid_bwd);
-int step_grid(int V, int G);
-cudaError_t launch_boundary(const BndArgs &b, cudaStream_t s);
-int boundary_grid(int n_seg);
-cudaError_t launch_pass_begin(DevStats *st, cudaStream_t s);
-cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, cudaStream_t s);
-cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, double *logu,
-                           float *w_hi, float *w_lo, int reset, const int *st_inpos, const int *st_outpos,
-                           double *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s);
-cudaError_t launch_fill_panel(size_t n, float *hi, lo_t *lo, cudaStream_t s);
-cudaError_t launch_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
-                                   const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
-                                   const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
-                                   const double *logu_t, double *out, cudaStream_t s);
-cudaError_t launch_boundary_flows(int n, int Lp, QScale qs, const int *tri_l, const int *tri_node_other,
-                                  const double *tri_logU, const float *msg_hi, const lo_t *msg_lo, double *out,
-                                  cudaStream_t s);
-}  // namespace ots
+#include "ots_internal.h"
 
 using namespace ots;
+using namespace ots_host;
 
-namespace {
+namespace ots_host {
 
 thread_local std::string g_last_error;
 
@@ -59,99 +40,9 @@ ots_status fail(ots_status s, const char *fmt, ...) {
   return s;
 }
 
-#define OTS_CUDA(expr)                                                                          \
-  do {                                                                                          \
-    cudaError_t e_ = (expr);                                                                    \
-    if (e_ != cudaSuccess)                                                                      \
-      return fail(e_ == cudaErrorMemoryAllocation ? OTS_ERR_OOM : OTS_ERR_CUDA, "%s: %s (%s:%d)", \
-                  #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
-  } while (0)
+void clear_error() { g_last_error.clear(); }
 
-constexpr double kLn2 = 0.69314718055994530942;
-constexpr double kInvLn2 = 1.44269504088896340736;
-
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-void split_ff(double x, float &hi, float &lo) {
-  hi = (float)x;
-  lo = (float)(x - (double)hi);
-}
-
-// One side of the boundary (sources or sinks): unique (commodity, state) triples grouped in
-// segments of equal (node, commodity).
-struct Boundary {
-  int n = 0;                      // unique triples
-  int n_seg = 0;
-  std::vector<int> seg_ptr, seg_node, seg_l;
-  std::vector<int> tri_l, tri_state, tri_other;
-  std::vector<double> tri_R;
-  std::vector<int> input_to_tri;  // descriptor triple -> unique triple
-  // device
-  int *d_seg_ptr = nullptr, *d_seg_node = nullptr, *d_seg_l = nullptr, *d_tri_other = nullptr, *d_tri_l = nullptr;
-  double *d_tri_R = nullptr, *d_tri_logR = nullptr, *d_tri_logU = nullptr, *d_flow = nullptr;
-};
-
-}  // namespace
-
-struct ots_problem {
-  int dev = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  ots_alloc_fn alloc = nullptr;
-  ots_free_fn free_fn = nullptr;
-  void *actx = nullptr;
-
-  int V = 0, E = 0, S = 0, L = 0, T = 0, G = 1, C = 1, Lp = 4;
-  double eps = 1.0, mass = 0.0;
-  QScale qs{};                                 // quantum of the message hi parts
-  int pgrid_fwd = 0, pgrid_bwd = 0;            // grids of the pipelined persistent kernels (0 = not used)
-  bool pc = false;
-
-  std::vector<int> tail, head;
-  Boundary src, snk;
-
-  void *arena = nullptr;
-  size_t arena_bytes = 0;
-
-  int *d_in_ptr = nullptr, *d_in_state = nullptr, *d_in_nbr = nullptr;
-  int *d_out_ptr = nullptr, *d_out_state = nullptr, *d_out_nbr = nullptr;
-  int *d_tail = nullptr, *d_head = nullptr;
-  float *d_kl_hi = nullptr, *d_kl_lo = nullptr, *d_logd_hi = nullptr, *d_logd_lo = nullptr;
-  double *d_cap = nullptr;
-  float *d_klc_hi = nullptr;
-  lo_t *d_klc_lo = nullptr;
-  float *d_w_hi = nullptr, *d_w_lo = nullptr;  // [T+1][S]
-  double *d_logu = nullptr;                    // [T+1][S]
-  // CSR-ordered copies used by the pipelined kernels
-  int *d_st_inpos = nullptr, *d_st_outpos = nullptr, *d_in_outpos = nullptr;
-  float *d_in_kl_hi = nullptr, *d_in_kl_lo = nullptr, *d_in_logd_hi = nullptr, *d_in_logd_lo = nullptr;
-  double *d_in_cap = nullptr;
-  double *d_logu_in = nullptr;                 // [T+1][S] by in-CSR position
-  float *d_wout_hi = nullptr, *d_wout_lo = nullptr;  // [T+1][S] by out-CSR position
-  double *d_flow = nullptr;                    // [T+1][S]
-  float *d_a_hi[3] = {nullptr, nullptr, nullptr};
-  lo_t *d_a_lo[3] = {nullptr, nullptr, nullptr};
-  float *d_b_hi = nullptr;                     // [(T-1)][V][Lp], row t-2
-  lo_t *d_b_lo = nullptr;
-  DevStats *d_stats = nullptr;
-  PassReport *d_report = nullptr;
-  double *d_partials = nullptr;
-  unsigned int *d_counter = nullptr;
-  PassReport *h_report = nullptr;              // pinned
-
-  cudaGraphExec_t pass_exec = nullptr;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // phase marks of a pass
-  bool stale = true;                           // backward messages not consistent with duals
-  long long passes_total = 0;
-  long long kernels_launched = 0;
-  long long h2d_bytes = 0, d2h_bytes = 0;
-
-  size_t panel() const { return (size_t)V * Lp; }
-  float *a_hi(int t) { return t == 1 ? d_a_hi[0] : d_a_hi[1 + (t & 1)]; }
-  lo_t *a_lo(int t) { return t == 1 ? d_a_lo[0] : d_a_lo[1 + (t & 1)]; }
-  float *b_hi(int t) { return d_b_hi + (size_t)(t - 2) * panel(); }
-  lo_t *b_lo(int t) { return d_b_lo + (size_t)(t - 2) * panel(); }
-};
+}  // namespace ots_host
 
 namespace {
 
@@ -355,18 +246,6 @@ ots_status read_report(ots_problem *p, ots_solve_report *rep) {
   return OTS_OK;
 }
 
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    cudaGetDevice(&prev);
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 // Necessary feasibility condition: every sink state is reached by a source state of the same
 // commodity, and every source reaches a sink, in exactly T-1 transitions.  With wait loops a
@@ -511,6 +390,7 @@ const char *ots_status_string(ots_status s) {
     case OTS_ERR_OOM: return "OTS_ERR_OOM";
     case OTS_ERR_CUDA: return "OTS_ERR_CUDA";
     case OTS_ERR_NUMERIC: return "OTS_ERR_NUMERIC";
+    case OTS_PENDING: return "OTS_PENDING";
   }
   return "OTS_ERR_UNKNOWN";
 }
@@ -532,7 +412,7 @@ ots_status ots_default_solve_opts(ots_solve_opts *o) {
 void ots_destroy_problem(ots_problem *p) {
   if (!p) return;
   DeviceGuard guard(p->dev);
-  if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->stream && !p->member) cudaStreamSynchronize(p->stream);   // a batch orders its own frees
   if (p->pass_exec) cudaGraphExecDestroy(p->pass_exec);
   for (int k = 0; k < 5; ++k)
     if (p->ev[k]) cudaEventDestroy(p->ev[k]);
@@ -544,6 +424,12 @@ void ots_destroy_problem(ots_problem *p) {
 
 ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   g_last_error.clear();
+  return create_problem_impl(d, CreateOpts{}, out);
+}
+
+}  // extern "C"
+
+ots_status ots_host::create_problem_impl(const ots_problem_desc *d, const CreateOpts &co, ots_problem **out) {
   if (!d || !out) return fail(OTS_ERR_INVALID_ARG, "desc or out is NULL");
   *out = nullptr;
   if (d->n_nodes < 1 || d->n_edges < 0) return fail(OTS_ERR_INVALID_ARG, "n_nodes must be >= 1 and n_edges >= 0");
@@ -569,8 +455,19 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   p->T = d->T;
   p->eps = d->eps;
   p->pc = d->commodity_cost != nullptr;
+  p->member = co.member;
   if (p->S < 1) { delete p; return fail(OTS_ERR_INVALID_ARG, "no states"); }
-  if (!choose_mapping(p->L, 0, p->G, p->C, p->Lp)) { delete p; return fail(OTS_ERR_INVALID_ARG, "unsupported L"); }
+  if (co.member) {
+    if (p->pc) { delete p; return fail(OTS_ERR_INVALID_ARG, "batched instances take commodity-independent costs"); }
+    if (!d->stream) { delete p; return fail(OTS_ERR_INVALID_ARG, "batch member without a stream"); }
+    p->G = co.G;
+    p->C = co.C;
+    p->Lp = 4 * co.G * co.C;
+    if (p->Lp < p->L) { delete p; return fail(OTS_ERR_INVALID_ARG, "mapping too narrow for L"); }
+  } else if (!choose_mapping(p->L, 0, p->G, p->C, p->Lp)) {
+    delete p;
+    return fail(OTS_ERR_INVALID_ARG, "unsupported L");
+  }
 
   auto bail = [&](ots_status s) { ots_destroy_problem(p); return s; };
 
@@ -711,13 +608,14 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
       return bail(fail(OTS_ERR_CUDA, "stream creation failed"));
     p->own_stream = true;
   }
-  if (cudaMallocHost(&p->h_report, sizeof(PassReport)) != cudaSuccess) return bail(fail(OTS_ERR_OOM, "pinned alloc failed"));
-  {
+  if (!p->member) {
+    if (cudaMallocHost(&p->h_report, sizeof(PassReport)) != cudaSuccess) return bail(fail(OTS_ERR_OOM, "pinned alloc failed"));
     cudaError_t e = prepare_step_kernels(p->G, p->C, p->pc, p->V, &p->pgrid_fwd, &p->pgrid_bwd);
     if (e != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(e)));
+    for (int k = 0; k < 5; ++k)
+      if (cudaEventCreate(&p->ev[k]) != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "event creation failed"));
   }
-  for (int k = 0; k < 5; ++k)
-    if (cudaEventCreate(&p->ev[k]) != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "event creation failed"));
+  const bool csr_copies = !p->member;   // in- / out-CSR-ordered copies of the per-state data
 
   const size_t S = p->S, V = p->V, T = p->T, panel = p->panel();
   const int max_grid = std::max(std::max(step_grid(p->V, p->G), boundary_grid(p->src.n_seg)),
@@ -731,16 +629,17 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   size_t o_klc_hi = p->pc ? cv.take<float>(S * p->Lp) : 0, o_klc_lo = p->pc ? cv.take<lo_t>(S * p->Lp) : 0;
   size_t o_w_hi = cv.take<float>((T + 1) * S), o_w_lo = cv.take<float>((T + 1) * S);
   size_t o_logu = cv.take<double>((T + 1) * S), o_flow = cv.take<double>((T + 1) * S);
-  size_t o_st_inpos = cv.take<int>(S), o_st_outpos = cv.take<int>(S), o_in_outpos = cv.take<int>(S);
-  size_t o_in_kl_hi = cv.take<float>(S), o_in_kl_lo = cv.take<float>(S), o_in_ld_hi = cv.take<float>(S),
-         o_in_ld_lo = cv.take<float>(S), o_in_cap = cv.take<double>(S);
-  size_t o_logu_in = cv.take<double>((T + 1) * S), o_wout_hi = cv.take<float>((T + 1) * S),
-         o_wout_lo = cv.take<float>((T + 1) * S);
+  const size_t Sc = csr_copies ? S : 0;
+  size_t o_st_inpos = cv.take<int>(Sc), o_st_outpos = cv.take<int>(Sc), o_in_outpos = cv.take<int>(Sc);
+  size_t o_in_kl_hi = cv.take<float>(Sc), o_in_kl_lo = cv.take<float>(Sc), o_in_ld_hi = cv.take<float>(Sc),
+         o_in_ld_lo = cv.take<float>(Sc), o_in_cap = cv.take<double>(Sc);
+  size_t o_logu_in = cv.take<double>((T + 1) * Sc), o_wout_hi = cv.take<float>((T + 1) * Sc),
+         o_wout_lo = cv.take<float>((T + 1) * Sc);
   size_t o_a_hi[3], o_a_lo[3];
   for (int k = 0; k < 3; ++k) { o_a_hi[k] = cv.take<float>(panel); o_a_lo[k] = cv.take<lo_t>(panel); }
   size_t o_b_hi = cv.take<float>((T - 1) * panel), o_b_lo = cv.take<lo_t>((T - 1) * panel);
   size_t o_stats = cv.take<DevStats>(1), o_report = cv.take<PassReport>(1);
-  size_t o_partials = cv.take<double>(2 * (size_t)max_grid), o_counter = cv.take<unsigned int>(4);
+  size_t o_partials = cv.take<double>(3 * (size_t)max_grid), o_counter = cv.take<unsigned int>(4);
   struct BOff { size_t seg_ptr, seg_node, seg_l, other, l, R, logR, logU, flow; } bo[2];
   Boundary *sides[2] = {&p->src, &p->snk};
   for (int k = 0; k < 2; ++k) {
@@ -764,11 +663,13 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   if (p->pc) { p->d_klc_hi = (float *)at(o_klc_hi); p->d_klc_lo = (lo_t *)at(o_klc_lo); }
   p->d_w_hi = (float *)at(o_w_hi); p->d_w_lo = (float *)at(o_w_lo);
   p->d_logu = (double *)at(o_logu); p->d_flow = (double *)at(o_flow);
-  p->d_st_inpos = (int *)at(o_st_inpos); p->d_st_outpos = (int *)at(o_st_outpos); p->d_in_outpos = (int *)at(o_in_outpos);
-  p->d_in_kl_hi = (float *)at(o_in_kl_hi); p->d_in_kl_lo = (float *)at(o_in_kl_lo);
-  p->d_in_logd_hi = (float *)at(o_in_ld_hi); p->d_in_logd_lo = (float *)at(o_in_ld_lo);
-  p->d_in_cap = (double *)at(o_in_cap);
-  p->d_logu_in = (double *)at(o_logu_in); p->d_wout_hi = (float *)at(o_wout_hi); p->d_wout_lo = (float *)at(o_wout_lo);
+  if (csr_copies) {
+    p->d_st_inpos = (int *)at(o_st_inpos); p->d_st_outpos = (int *)at(o_st_outpos); p->d_in_outpos = (int *)at(o_in_outpos);
+    p->d_in_kl_hi = (float *)at(o_in_kl_hi); p->d_in_kl_lo = (float *)at(o_in_kl_lo);
+    p->d_in_logd_hi = (float *)at(o_in_ld_hi); p->d_in_logd_lo = (float *)at(o_in_ld_lo);
+    p->d_in_cap = (double *)at(o_in_cap);
+    p->d_logu_in = (double *)at(o_logu_in); p->d_wout_hi = (float *)at(o_wout_hi); p->d_wout_lo = (float *)at(o_wout_lo);
+  }
   for (int k = 0; k < 3; ++k) { p->d_a_hi[k] = (float *)at(o_a_hi[k]); p->d_a_lo[k] = (lo_t *)at(o_a_lo[k]); }
   p->d_b_hi = (float *)at(o_b_hi); p->d_b_lo = (lo_t *)at(o_b_lo);
   p->d_stats = (DevStats *)at(o_stats); p->d_report = (PassReport *)at(o_report);
@@ -793,9 +694,11 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   UP(p->d_tail, p->tail); UP(p->d_head, p->head);
   UP(p->d_kl_hi, kl_hi); UP(p->d_kl_lo, kl_lo); UP(p->d_logd_hi, logd_hi); UP(p->d_logd_lo, logd_lo);
   UP(p->d_cap, cap);
-  UP(p->d_st_inpos, st_inpos); UP(p->d_st_outpos, st_outpos); UP(p->d_in_outpos, in_outpos);
-  UP(p->d_in_kl_hi, in_kl_hi); UP(p->d_in_kl_lo, in_kl_lo); UP(p->d_in_logd_hi, in_logd_hi);
-  UP(p->d_in_logd_lo, in_logd_lo); UP(p->d_in_cap, in_cap);
+  if (csr_copies) {
+    UP(p->d_st_inpos, st_inpos); UP(p->d_st_outpos, st_outpos); UP(p->d_in_outpos, in_outpos);
+    UP(p->d_in_kl_hi, in_kl_hi); UP(p->d_in_kl_lo, in_kl_lo); UP(p->d_in_logd_hi, in_logd_hi);
+    UP(p->d_in_logd_lo, in_logd_lo); UP(p->d_in_cap, in_cap);
+  }
   if (p->pc) { UP(p->d_klc_hi, klc_hi); UP(p->d_klc_lo, klc_lo); }
   std::vector<std::vector<double>> logR(2);
   for (int k = 0; k < 2; ++k) {
@@ -806,6 +709,11 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
     UP(b.d_tri_other, b.tri_other); UP(b.d_tri_l, b.tri_l); UP(b.d_tri_R, b.tri_R); UP(b.d_tri_logR, logR[k]);
   }
 #undef UP
+  if (p->member) {
+    // duals, panels and accumulators are initialised by the batched kernel's set-up step
+    *out = p;
+    return OTS_OK;
+  }
   if (cudaMemsetAsync(p->d_stats, 0, sizeof(DevStats), p->stream) != cudaSuccess ||
       cudaMemsetAsync(p->d_counter, 0, 4 * sizeof(unsigned int), p->stream) != cudaSuccess ||
       cudaMemsetAsync(p->d_flow, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess)
@@ -825,6 +733,8 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   *out = p;
   return OTS_OK;
 }
+
+extern "C" {
 
 ots_status ots_problem_info(const ots_problem *p, ots_problem_stats *o) {
   if (!p || !o) return fail(OTS_ERR_INVALID_ARG, "NULL argument");

@@ -1,0 +1,80 @@
+// ots_batch.cuh -- device-side description of a batch of independent instances.
+//
+// A batch keeps many instances of the multi-commodity problem resident at once and advances
+// all of them with one kernel launch per "tick": in every tick each running instance executes
+// the next step of its own sequence of Algorithm 2 steps (set-up, initial backward sweep,
+// then passes of source update, forward steps t = 2..T-1, sink update, backward steps
+// t = T-1..2, and after convergence one flows pass).  Instances therefore sit at different
+// steps and horizons in the same launch, and an instance that finishes frees its slot
+// without stopping the others.  The work of a tick is a list of items (slot, item index);
+// item k of an instance covers nodes [k npb, (k+1) npb) of its node panels, or a slice of its
+// states or boundary triples, depending on the step.
+#pragma once
+
+#include "ots_device.cuh"
+
+namespace ots {
+
+constexpr int kTickBlock = 256;   // threads per block of the batched kernel
+
+// slot states (BatchCtl::status)
+enum : int {
+  kSlotIdle = 0,
+  kSlotRunning = 1,        // Sinkhorn passes
+  kSlotFlows = 2,          // flows pass after the last Sinkhorn pass
+  kSlotConverged = 3,      // final: converged, flows ready
+  kSlotNotConverged = 4,   // final: max passes reached, flows of the last duals ready
+  kSlotInfeasible = 5,     // final: a source or sink message vanished
+  kSlotNumeric = 6,        // final: NaN in the convergence measures
+  kSlotStopped = 7         // final: stopped by the host (timeout)
+};
+
+struct BndSide {
+  int n_seg, n_tri;
+  const int *seg_ptr, *seg_node, *seg_l, *tri_other, *tri_l;
+  const double *tri_R, *tri_logR;
+  double *tri_logU, *tri_flow;
+};
+
+// Static description of one resident instance (written by the host at admission).
+struct BatchInst {
+  int V, S, T, Lp, G, C, n_items, npb;   // npb: nodes per item = kTickBlock / G
+  QScale qs;
+  double mass, eps, tol;
+  int max_passes, pad;
+  const int *in_ptr, *in_state, *in_nbr, *out_ptr, *out_state, *out_nbr;
+  const float *kl_hi, *kl_lo, *logd_hi, *logd_lo;
+  const double *cap;
+  double *logu;                  // [T+1][S] log2 u_t
+  float *w_hi, *w_lo;            // [T+1][S] W_t
+  double *flow;                  // [T+1][S] P_t
+  float *a0_hi, *a1_hi, *a2_hi;  // A_1, and A_t for even / odd t
+  lo_t *a0_lo, *a1_lo, *a2_lo;
+  float *b_hi;                   // [T-1][V][Lp], row t-2 holds B_t
+  lo_t *b_lo;
+  BndSide src, snk;
+  double *partials;              // [3 n_items] per-item partial sums of the current step
+};
+
+// Dynamic state of one slot (device-resident; the host reads a copy after every launch).
+struct alignas(16) BatchCtl {
+  int status;
+  int step;                      // position in the step sequence of the current status
+  int passes;                    // completed Sinkhorn passes
+  int final_status;              // status to enter after the flows pass
+  unsigned int counter;          // items of this instance finished in the current tick
+  int pad0;
+  long long ticks;               // ticks this instance has executed
+  DevStats stats;
+  PassReport report;
+};
+
+struct TickArgs {
+  const BatchInst *inst;         // [slots]
+  BatchCtl *ctl;                 // [slots]
+  const int2 *items;             // (slot, item index within the instance)
+  const int *n_items;            // device scalar: number of items in the list
+  unsigned int *fetch;           // [2]: item fetch counter, exited blocks
+};
+
+}  // namespace ots

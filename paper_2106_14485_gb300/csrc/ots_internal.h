@@ -1,0 +1,161 @@
+// ots_internal.h -- host-side internals shared by the translation units of the library:
+// the problem object behind the opaque ots_problem handle, error reporting, and the kernel
+// launchers.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "ots.h"
+#include "ots_device.cuh"
+
+namespace ots {
+cudaError_t launch_step(bool fwd, bool pc, int G, int C, const StepArgs &a, cudaStream_t s);
+cudaError_t prepare_step_kernels(int G, int C, bool pc, int V, int *grid_fwd, int *grid_bwd);
+int step_grid(int V, int G);
+cudaError_t launch_boundary(const BndArgs &b, cudaStream_t s);
+int boundary_grid(int n_seg);
+cudaError_t launch_pass_begin(DevStats *st, cudaStream_t s);
+cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, cudaStream_t s);
+cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, double *logu,
+                           float *w_hi, float *w_lo, int reset, const int *st_inpos, const int *st_outpos,
+                           double *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s);
+cudaError_t launch_fill_panel(size_t n, float *hi, lo_t *lo, cudaStream_t s);
+cudaError_t launch_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
+                                   const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
+                                   const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
+                                   const double *logu_t, double *out, cudaStream_t s);
+cudaError_t launch_boundary_flows(int n, int Lp, QScale qs, const int *tri_l, const int *tri_node_other,
+                                  const double *tri_logU, const float *msg_hi, const lo_t *msg_lo, double *out,
+                                  cudaStream_t s);
+}  // namespace ots
+
+namespace ots_host {
+
+// Records a formatted message for ots_last_error (per thread) and returns s.
+ots_status fail(ots_status s, const char *fmt, ...);
+void clear_error();
+
+#define OTS_CUDA(expr)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (expr);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return ::ots_host::fail(e_ == cudaErrorMemoryAllocation ? OTS_ERR_OOM : OTS_ERR_CUDA,     \
+                              "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr double kInvLn2 = 1.44269504088896340736;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline void split_ff(double x, float &hi, float &lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// One side of the boundary (sources or sinks): unique (commodity, state) triples grouped in
+// segments of equal (node, commodity).
+struct Boundary {
+  int n = 0;                      // unique triples
+  int n_seg = 0;
+  std::vector<int> seg_ptr, seg_node, seg_l;
+  std::vector<int> tri_l, tri_state, tri_other;
+  std::vector<double> tri_R;
+  std::vector<int> input_to_tri;  // descriptor triple -> unique triple
+  // device
+  int *d_seg_ptr = nullptr, *d_seg_node = nullptr, *d_seg_l = nullptr, *d_tri_other = nullptr, *d_tri_l = nullptr;
+  double *d_tri_R = nullptr, *d_tri_logR = nullptr, *d_tri_logU = nullptr, *d_flow = nullptr;
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Options of the internal constructor.  A batch member is an instance that lives in a batch
+// (ots_batch / ots_server): it uses the batch's stream and device pool, is initialised by
+// the batched kernel rather than here, and has the thread mapping the batch chose.
+struct CreateOpts {
+  bool member = false;
+  int G = 0, C = 0;          // forced mapping (member only): G threads per node, C chunks of 4
+};
+
+ots_status create_problem_impl(const ots_problem_desc *d, const CreateOpts &co, ots_problem **out);
+
+}  // namespace ots_host
+
+struct ots_problem {
+  using QScale = ots::QScale;
+  using lo_t = ots::lo_t;
+  using DevStats = ots::DevStats;
+  using PassReport = ots::PassReport;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  ots_alloc_fn alloc = nullptr;
+  ots_free_fn free_fn = nullptr;
+  void *actx = nullptr;
+
+  int V = 0, E = 0, S = 0, L = 0, T = 0, G = 1, C = 1, Lp = 4;
+  double eps = 1.0, mass = 0.0;
+  QScale qs{};                                 // quantum of the message hi parts
+  int pgrid_fwd = 0, pgrid_bwd = 0;            // grids of the pipelined persistent kernels (0 = not used)
+  bool pc = false;
+  bool member = false;                         // lives in a batch (see CreateOpts)
+
+  std::vector<int> tail, head;
+  ots_host::Boundary src, snk;
+
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+
+  int *d_in_ptr = nullptr, *d_in_state = nullptr, *d_in_nbr = nullptr;
+  int *d_out_ptr = nullptr, *d_out_state = nullptr, *d_out_nbr = nullptr;
+  int *d_tail = nullptr, *d_head = nullptr;
+  float *d_kl_hi = nullptr, *d_kl_lo = nullptr, *d_logd_hi = nullptr, *d_logd_lo = nullptr;
+  double *d_cap = nullptr;
+  float *d_klc_hi = nullptr;
+  lo_t *d_klc_lo = nullptr;
+  float *d_w_hi = nullptr, *d_w_lo = nullptr;  // [T+1][S]
+  double *d_logu = nullptr;                    // [T+1][S]
+  // CSR-ordered copies used by the pipelined kernels
+  int *d_st_inpos = nullptr, *d_st_outpos = nullptr, *d_in_outpos = nullptr;
+  float *d_in_kl_hi = nullptr, *d_in_kl_lo = nullptr, *d_in_logd_hi = nullptr, *d_in_logd_lo = nullptr;
+  double *d_in_cap = nullptr;
+  double *d_logu_in = nullptr;                 // [T+1][S] by in-CSR position
+  float *d_wout_hi = nullptr, *d_wout_lo = nullptr;  // [T+1][S] by out-CSR position
+  double *d_flow = nullptr;                    // [T+1][S]
+  float *d_a_hi[3] = {nullptr, nullptr, nullptr};
+  lo_t *d_a_lo[3] = {nullptr, nullptr, nullptr};
+  float *d_b_hi = nullptr;                     // [(T-1)][V][Lp], row t-2
+  lo_t *d_b_lo = nullptr;
+  DevStats *d_stats = nullptr;
+  PassReport *d_report = nullptr;
+  double *d_partials = nullptr;
+  unsigned int *d_counter = nullptr;
+  PassReport *h_report = nullptr;              // pinned
+
+  cudaGraphExec_t pass_exec = nullptr;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // phase marks of a pass
+  bool stale = true;                           // backward messages not consistent with duals
+  long long passes_total = 0;
+  long long kernels_launched = 0;
+  long long h2d_bytes = 0, d2h_bytes = 0;
+
+  size_t panel() const { return (size_t)V * Lp; }
+  float *a_hi(int t) { return t == 1 ? d_a_hi[0] : d_a_hi[1 + (t & 1)]; }
+  lo_t *a_lo(int t) { return t == 1 ? d_a_lo[0] : d_a_lo[1 + (t & 1)]; }
+  float *b_hi(int t) { return d_b_hi + (size_t)(t - 2) * panel(); }
+  lo_t *b_lo(int t) { return d_b_lo + (size_t)(t - 2) * panel(); }
+};

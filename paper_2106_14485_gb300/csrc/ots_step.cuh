@@ -1,0 +1,331 @@
+// ots_step.cuh -- device helpers shared by the per-instance and the batched message kernels:
+// packed panel loads and stores, deterministic block reductions, group reductions over the
+// commodities of a node row, the batched log-sum-exp accumulation of Theorem 6 and the
+// capacity update of Algorithm 2 (Corollary 7).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ots_device.cuh"
+
+namespace ots {
+namespace {
+
+// 4 consecutive entries of a panel row: hi values and the packed biased lo words.
+__device__ __forceinline__ void load4(const float *hp, const lo_t *lp, float h[4], uint32_t w[2]) {
+  const float4 a = *reinterpret_cast<const float4 *>(hp);
+  const uint2 b = *reinterpret_cast<const uint2 *>(lp);
+  h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w;
+  w[0] = b.x;
+  w[1] = b.y;
+}
+
+// 2^23 + lo of entry q (0..3) of a packed pair of words.
+__device__ __forceinline__ float lo_inj(const uint32_t w[2], int q) {
+  return (q & 1) ? lo_word1(w[q >> 1]) : lo_word0(w[q >> 1]);
+}
+
+__device__ __forceinline__ void store4(float *hp, lo_t *lp, const float h[4], const lo_t l[4]) {
+  *reinterpret_cast<float4 *>(hp) = make_float4(h[0], h[1], h[2], h[3]);
+  uint2 b;
+  b.x = (uint32_t)l[0] | ((uint32_t)l[1] << 16);
+  b.y = (uint32_t)l[2] | ((uint32_t)l[3] << 16);
+  *reinterpret_cast<uint2 *>(lp) = b;
+}
+
+// Sum of two doubles over the block (fixed order: warp shuffles, then warps in order).
+__device__ __forceinline__ void block_sum2(double &v0, double &v1, double *s0, double *s1) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+  }
+  __syncthreads();
+  if (lane == 0) { s0[wid] = v0; s1[wid] = v1; }
+  __syncthreads();
+  v0 = 0.0;
+  v1 = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { v0 += s0[w]; v1 += s1[w]; }
+}
+
+// Deterministic FP64 grid reduction of two values: every block writes its partial sums, the
+// last block to finish reduces all partials with a fixed assignment to threads and a fixed
+// tree, then adds the totals to dst0 / dst1 (or assigns, when assign != 0) and resets the
+// counter for the next kernel.
+__device__ void block_sum2_last(double v0, double v1, double *partials, unsigned int *counter,
+                                double *dst0, double *dst1, int assign) {
+  __shared__ double s0[32], s1[32];   // one slot per warp of any block size up to 1024 threads
+  __shared__ bool is_last;
+  block_sum2(v0, v1, s0, s1);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = v0;
+    partials[2 * blockIdx.x + 1] = v1;
+    __threadfence();
+    unsigned int prev = atomicAdd(counter, 1u);
+    is_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double a = 0.0, b = 0.0;
+  for (unsigned int k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+    a += __ldcg(partials + 2 * k);
+    b += __ldcg(partials + 2 * k + 1);
+  }
+  block_sum2(a, b, s0, s1);
+  if (threadIdx.x == 0) {
+    if (assign) { *dst0 = a; *dst1 = b; } else { *dst0 += a; *dst1 += b; }
+    *counter = 0u;
+  }
+}
+
+// Group-wide (G threads) reductions of KB values at once.  For G <= 32 the group is a slice
+// of one warp (shuffles only); for G > 32 the block is one node and the warps exchange their
+// partial results through shared memory (sm holds G/32 x KB floats).
+template <int G, int KB, bool MAX>
+__device__ __forceinline__ void group_reduce(float (&x)[KB], float *sm) {
+  if (G == 1) return;
+  const unsigned lane = threadIdx.x & 31u;
+  constexpr int W = G < 32 ? G : 32;
+  const unsigned base = lane & ~(unsigned)(W - 1);
+  const unsigned mask = (W >= 32) ? 0xffffffffu : (((1u << (W & 31)) - 1u) << base);
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      const float y = __shfl_xor_sync(mask, x[k], o, 32);
+      x[k] = MAX ? fmaxf(x[k], y) : x[k] + y;
+    }
+  }
+  if (G > 32) {
+    constexpr int NW = G / 32;
+    const int wid = threadIdx.x >> 5;
+    __syncthreads();                              // earlier readers of sm are done
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < KB; ++k) sm[k * NW + wid] = x[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      float r = sm[k * NW];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) r = MAX ? fmaxf(r, sm[k * NW + w]) : r + sm[k * NW + w];
+      x[k] = r;
+    }
+  }
+}
+
+// Gather the thread's slice of up to KB input rows (row index nbr[j0 + k]).  With
+// per-commodity costs the row of log2 K_L[., state] (same stored format) is added: hi sums are
+// exact; the two remainders are added in signed units and re-biased (|sum| <= 2^16 units, one
+// more unit of rounding when the sum leaves the int16 range is avoided by carrying into hi).
+template <int G, int C, int KB, bool PC>
+__device__ __forceinline__ void gather_rows(const StepArgs &a, int j0, int nb, int g, int (&st)[KB],
+                                            float (&xh)[KB][C][4], uint32_t (&xw)[KB][C][2]) {
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    if (k < nb) {
+      st[k] = a.state[j0 + k];
+      const size_t row = (size_t)a.nbr[j0 + k] * a.Lp;
+#pragma unroll
+      for (int c = 0; c < C; ++c) load4(a.x_hi + row + 4 * (c * G + g), a.x_lo + row + 4 * (c * G + g), xh[k][c], xw[k][c]);
+    } else {
+      st[k] = 0;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xh[k][c][q] = kNeg;
+        xw[k][c][0] = 0x80008000u;
+        xw[k][c][1] = 0x80008000u;
+      }
+    }
+  }
+  if (PC) {
+    const float q = a.qs.q;
+#pragma unroll
+    for (int k = 0; k < KB; ++k) {
+      if (k < nb) {
+        const size_t row = (size_t)st[k] * a.Lp;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          float ch[4];
+          uint32_t cw[2];
+          load4(a.klc_hi + row + 4 * (c * G + g), a.klc_lo + row + 4 * (c * G + g), ch, cw);
+          lo_t nl[4];
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            // signed remainders in units, exact
+            float u = (lo_inj(xw[k][c], qq) - kLoBias) + (lo_inj(cw, qq) - kLoBias);
+            float h = xh[k][c][qq] + ch[qq];
+            if (u > 32767.f) { u -= 65536.f; h += q; }
+            if (u < -32767.f) { u += 65536.f; h -= q; }
+            xh[k][c][qq] = h;
+            nl[qq] = (lo_t)((int)u + 32768);
+          }
+          xw[k][c][0] = (uint32_t)nl[0] | ((uint32_t)nl[1] << 16);
+          xw[k][c][1] = (uint32_t)nl[2] | ((uint32_t)nl[3] << 16);
+        }
+      }
+    }
+  }
+}
+
+// Accumulate one batch of terms x[k] + w[k] into the running log-sum-exp (M, acc) of each
+// commodity: hi sums are exact, batch maximum first, one ex2 per term.  Absent or unreachable
+// terms have hi sums near -1e30 and vanish in ex2 without a branch.
+template <int C, int KB>
+__device__ __forceinline__ void aggregate_batch(const float (&xh)[KB][C][4], const uint32_t (&xw)[KB][C][2],
+                                                const float (&wh)[KB], const float (&wl)[KB], float lo_unit,
+                                                float (&M)[C][4], float (&acc)[C][4]) {
+  float wlb[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) wlb[k] = wl[k] - kLoBias * lo_unit;
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float sv[KB];
+      float m = 2.f * kNeg;
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        sv[k] = xh[k][c][q] + wh[k];
+        m = fmaxf(m, sv[k]);
+      }
+      if (m < kNegThresh) continue;               // nothing reachable in this batch
+      float sum = 0.f;
+#pragma unroll
+      for (int k = 0; k < KB; ++k) sum += ex2(fmaf(lo_inj(xw[k][c], q), lo_unit, (sv[k] - m) + wlb[k]));
+      const float Mo = M[c][q];
+      if (m > Mo) {
+        acc[c][q] = fmaf(acc[c][q], ex2(Mo - m), sum);
+        M[c][q] = m;
+      } else {
+        acc[c][q] = fmaf(sum, ex2(m - Mo), acc[c][q]);
+      }
+    }
+}
+
+// Merge two (max, scaled-sum) pairs of a log-sum-exp: value = m + log2(s).
+__device__ __forceinline__ void lse_merge(float &m, float &s, float om, float os) {
+  if (om > m) {
+    s = fmaf(s, ex2(m - om), os);
+    m = om;
+  } else {
+    s = fmaf(os, ex2(om - m), s);
+  }
+}
+
+// W = log2 K_L + log2 u as (hi on the q grid, float lo).
+__device__ __forceinline__ void make_w(float kl_hi, float kl_lo, float lu_hi, float lu_lo, const QScale &qs,
+                                       float &w_hi, float &w_lo) {
+  if (lu_hi < kNegThresh) {
+    w_hi = kNeg;
+    w_lo = 0.f;
+    return;
+  }
+  float s, e;
+  two_sum(kl_hi, lu_hi, s, e);
+  e += kl_lo + lu_lo;
+  w_hi = quant(s, qs);
+  w_lo = (s - w_hi) + e;
+}
+
+// Capacity update of one state from its column log-sum-exp (cm + log2 cs) (Algorithm 2,
+// Corollary 7): W_t for the aggregation and, when `write`, the stored log2 u_t, W_t, the
+// excess (P_t - d)_+ with the old u_t and the dual term d log2 u_t (Theorem 3).  In flows
+// mode (a.mode == 1) W_t is read back and, when `write`, P_t is stored.
+template <bool PC>
+__device__ __forceinline__ void update_state(const StepArgs &a, int sk, float cm, float cs, bool write, float &w_hi,
+                                             float &w_lo, double &viol, double &dual) {
+  float col_hi = kNeg, col_lo = 0.f;
+  if (cm > kNegThresh && cs > 0.f) two_sum(cm, lg2(cs), col_hi, col_lo);  // log2 (hatPsi .* Psi (.* K_L))^T 1
+  const float klh = PC ? 0.f : a.kl_hi[sk], kll = PC ? 0.f : a.kl_lo[sk];
+  if (!PC && col_hi > kNegThresh) {
+    float s, e;
+    two_sum(col_hi, klh, s, e);
+    col_hi = s;
+    col_lo += e + kll;
+  }
+  if (a.mode != 0) {
+    w_hi = a.w_hi_t[sk];
+    w_lo = a.w_lo_t[sk];
+    if (write)
+      a.flow_t[sk] = col_hi > kNegThresh && w_hi > kNegThresh
+                         ? exp2(a.logu_t[sk] + (double)col_hi + (double)col_lo) : 0.0;
+    return;
+  }
+  const double cap = a.cap[sk];
+  float lu_hi = 0.f, lu_lo = 0.f;
+  if (isfinite(cap) && col_hi > kNegThresh) {
+    if (a.logd_hi[sk] < kNegThresh) {
+      lu_hi = kNeg;                                // d = 0: the state is closed
+    } else {
+      // log2 u = min(log2 d - col, 0) in float-float
+      float s1, e1, s2, e2;
+      two_sum(a.logd_hi[sk], -col_hi, s1, e1);
+      e1 += a.logd_lo[sk] - col_lo;
+      two_sum(s1, e1, s2, e2);
+      if (s2 < 0.f) { lu_hi = s2; lu_lo = e2; }
+    }
+  }
+  make_w(klh, kll, lu_hi, lu_lo, a.qs, w_hi, w_lo);
+  if (!write) return;
+  const double lu_old = a.logu_t[sk];
+  if (col_hi > kNegThresh && isfinite(cap)) {
+    // excess with the old u_t; exact FP64 only near or above capacity
+    const float qv = (float)lu_old + col_hi - a.logd_hi[sk];
+    if (qv > -1e-3f) {
+      const double p_old = exp2(lu_old + (double)col_hi + (double)col_lo);
+      if (p_old > cap) viol += p_old - cap;
+    }
+  }
+  if (col_hi != col_hi || col_lo != col_lo) viol = __longlong_as_double(0x7ff8000000000000LL);  // NaN: reported
+  const double lu_new = lu_hi < kNegThresh ? -1e30 : (double)lu_hi + (double)lu_lo;
+  if (isfinite(cap) && cap > 0.0) dual += cap * lu_new;
+  a.logu_t[sk] = lu_new;
+  a.w_hi_t[sk] = w_hi;
+  a.w_lo_t[sk] = w_lo;
+}
+
+// One (node, commodity) segment of boundary triples (Algorithm 2, source and sink updates):
+// in mode 0, U <- R ./ message (log2: log2 U = log2 R - msg) with the mismatch before the
+// update (sources: r0 += |U msg - R|), <R, log2 U> (r1), the mass <K, U> after a sink update
+// (r0) and a count of vanishing messages (r2); in both modes the segment's entry of the
+// boundary panel is rebuilt as log2 sum_q U_q.  FP64 throughout.
+__device__ __forceinline__ void boundary_segment(const BndArgs &b, int sidx, double &r0, double &r1, double &r2) {
+  const int l = b.seg_l[sidx];
+  const int q0 = b.seg_ptr[sidx], q1 = b.seg_ptr[sidx + 1];
+  double m = -INFINITY;
+  for (int q = q0; q < q1; ++q) {
+    double lu = b.tri_logU[q];
+    if (b.mode == 0) {
+      const size_t idx = (size_t)b.tri_node_other[q] * b.Lp + l;
+      const double msg = (double)b.msg_hi[idx] + ((double)b.msg_lo[idx] - 32768.0) * (double)b.qs.lo_unit;
+      if (b.is_source) r0 += fabs(exp2(lu + msg) - b.tri_R[q]);   // mismatch before the update
+      if (b.msg_hi[idx] < kNegThresh) r2 += 1.0;                   // vanishing message
+      lu = b.tri_logR[q] - msg;
+      b.tri_logU[q] = lu;
+      r1 += b.tri_R[q] * lu;                                       // <R, log2 U>
+      if (!b.is_source) r0 += exp2(lu + msg);                      // <K, U> after the update
+    }
+    m = fmax(m, lu);
+  }
+  double sum = 0.0;
+  for (int q = q0; q < q1; ++q) sum += exp2(b.tri_logU[q] - m);
+  const double r = m + log2(sum);
+  const float h = (float)r;
+  float oh;
+  lo_t ol;
+  encode(h, (float)(r - (double)h), b.qs, oh, ol);
+  const size_t o = (size_t)b.seg_node[sidx] * b.Lp + l;
+  b.out_hi[o] = oh;
+  b.out_lo[o] = ol;
+}
+
+}  // namespace
+
+}  // namespace ots

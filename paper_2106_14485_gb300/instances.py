@@ -122,59 +122,100 @@ def _connected(n: int, src: np.ndarray, dst: np.ndarray) -> bool:
     return bool(np.all(hop_distances(n, src, dst, 0) >= 0))
 
 
-def rgg_graph(n: int, mean_degree: float, rng: np.random.Generator, max_tries: int = 200):
-    """Random geometric graph in the unit square.
-
-    The radius is calibrated per draw so that the mean degree is exactly ``mean_degree``
-    (the ``n * mean_degree / 2`` shortest pairs become undirected edges); draws that are
-    not connected are rejected.  Nodes are renumbered along a coarse spatial sort so that
-    neighbouring nodes have nearby ids.
-    """
-    n_und = int(round(n * mean_degree / 2))
-    for _ in range(max_tries):
-        pos = rng.random((n, 2))
-        d = np.sqrt(((pos[:, None, :] - pos[None, :, :]) ** 2).sum(-1))
-        iu, ju = np.triu_indices(n, 1)
-        dist = d[iu, ju]
-        order = np.argsort(dist, kind="stable")[:n_und]
-        a, b = iu[order], ju[order]
-        src = np.concatenate([a, b]).astype(np.int32)
-        dst = np.concatenate([b, a]).astype(np.int32)
-        if _connected(n, src, dst):
-            # spatial renumbering: strips of width ~ radius, snake order inside
-            r = float(dist[order[-1]])
-            nstrip = max(1, int(1.0 / max(r, 1e-3)))
-            strip = np.minimum((pos[:, 1] * nstrip).astype(np.int64), nstrip - 1)
-            key = np.where(strip % 2 == 0, pos[:, 0], -pos[:, 0])
-            perm = np.lexsort((key, strip))          # new order -> old id
-            inv = np.empty(n, np.int64)
-            inv[perm] = np.arange(n)
-            src2, dst2 = inv[src].astype(np.int32), inv[dst].astype(np.int32)
-            eorder = np.lexsort((dst2, src2))
-            length = np.sqrt(((pos[src] - pos[dst]) ** 2).sum(-1))
-            return src2[eorder], dst2[eorder], pos[perm], length[eorder], r
-    raise RuntimeError("could not draw a connected random geometric graph")
-
-
-def hop_distances(n: int, src: np.ndarray, dst: np.ndarray, s: int) -> np.ndarray:
-    """BFS hop distance from node s (-1 = unreachable)."""
+def _components(n: int, src: np.ndarray, dst: np.ndarray) -> np.ndarray:
+    """Connected-component label of every node (undirected edge lists in both directions)."""
+    label = np.full(n, -1, np.int64)
     order = np.argsort(src, kind="stable")
     ptr = np.zeros(n + 1, np.int64)
     np.add.at(ptr, src.astype(np.int64) + 1, 1)
     ptr = np.cumsum(ptr)
     nbr = dst[order]
-    dist = np.full(n, -1, np.int64)
-    dist[s] = 0
-    frontier = [s]
-    while frontier:
-        nxt = []
-        for v in frontier:
+    c = 0
+    for s0 in range(n):
+        if label[s0] >= 0:
+            continue
+        label[s0] = c
+        stack = [s0]
+        while stack:
+            v = stack.pop()
             for w in nbr[ptr[v]:ptr[v + 1]]:
-                if dist[w] < 0:
-                    dist[w] = dist[v] + 1
-                    nxt.append(int(w))
-        frontier = nxt
-    return dist
+                if label[w] < 0:
+                    label[w] = c
+                    stack.append(int(w))
+        c += 1
+    return label
+
+
+def rgg_graph(n: int, mean_degree: float, rng: np.random.Generator, max_tries: int = 200,
+              connect: str = "reject"):
+    """Random geometric graph in the unit square.
+
+    The radius is calibrated per draw so that the mean degree is exactly ``mean_degree``
+    (the ``n * mean_degree / 2`` shortest pairs become undirected edges).  A draw that is not
+    connected is rejected (connect="reject"), or (connect="bridge", used where graphs of up
+    to thousands of nodes are drawn and almost never come out connected at this degree)
+    kept and made connected by repeatedly joining the smallest component to the rest with
+    its shortest edge, as a road network would be.  Nodes are renumbered along a coarse
+    spatial sort so that neighbouring nodes have nearby ids.
+    """
+    n_und = int(round(n * mean_degree / 2))
+    for _ in range(max_tries if connect == "reject" else 1):
+        pos = rng.random((n, 2))
+        d = np.sqrt(((pos[:, None, :] - pos[None, :, :]) ** 2).sum(-1))
+        iu, ju = np.triu_indices(n, 1)
+        dist = d[iu, ju]
+        # the n_und shortest pairs in ascending order (ties by pair index)
+        sel = np.argpartition(dist, n_und - 1)[:n_und] if n_und < dist.size else np.arange(dist.size)
+        order = sel[np.lexsort((sel, dist[sel]))]
+        a, b = iu[order], ju[order]
+        src = np.concatenate([a, b]).astype(np.int32)
+        dst = np.concatenate([b, a]).astype(np.int32)
+        r = float(dist[order[-1]])
+        if connect == "bridge":
+            label = _components(n, src, dst)
+            extra_a, extra_b = [], []
+            while label.max() > 0:
+                sizes = np.bincount(label)
+                small = int(np.argmin(sizes))
+                inside = np.flatnonzero(label == small)
+                outside = np.flatnonzero(label != small)
+                sub = d[np.ix_(inside, outside)]
+                k = int(np.argmin(sub))
+                u, w = int(inside[k // outside.size]), int(outside[k % outside.size])
+                extra_a.append(u)
+                extra_b.append(w)
+                label[label == small] = label[w]
+                _, label = np.unique(label, return_inverse=True)
+            if extra_a:
+                ea, eb = np.asarray(extra_a, np.int32), np.asarray(extra_b, np.int32)
+                src = np.concatenate([src, ea, eb]).astype(np.int32)
+                dst = np.concatenate([dst, eb, ea]).astype(np.int32)
+        elif not _connected(n, src, dst):
+            continue
+        # spatial renumbering: strips of width ~ radius, snake order inside
+        nstrip = max(1, int(1.0 / max(r, 1e-3)))
+        strip = np.minimum((pos[:, 1] * nstrip).astype(np.int64), nstrip - 1)
+        key = np.where(strip % 2 == 0, pos[:, 0], -pos[:, 0])
+        perm = np.lexsort((key, strip))          # new order -> old id
+        inv = np.empty(n, np.int64)
+        inv[perm] = np.arange(n)
+        src2, dst2 = inv[src].astype(np.int32), inv[dst].astype(np.int32)
+        eorder = np.lexsort((dst2, src2))
+        length = np.sqrt(((pos[src] - pos[dst]) ** 2).sum(-1))
+        return src2[eorder], dst2[eorder], pos[perm], length[eorder], r
+    raise RuntimeError("could not draw a connected random geometric graph")
+
+
+def hop_distances(n: int, src: np.ndarray, dst: np.ndarray, s: int) -> np.ndarray:
+    """BFS hop distance from node s (-1 = unreachable)."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import shortest_path
+    g = csr_matrix((np.ones(src.shape[0]), (src.astype(np.int64), dst.astype(np.int64))), shape=(n, n))
+    d = shortest_path(g, method="D", unweighted=True, indices=int(s))
+    out = np.full(n, -1, np.int64)
+    ok = np.isfinite(d)
+    out[ok] = d[ok].astype(np.int64)
+    return out
 
 
 def _od_pairs(n: int, src, dst, L: int, max_hops: int, rng, grid_cols: Optional[int] = None):
@@ -241,10 +282,11 @@ def config1(seed: int = 0, rows: int = 5, cols: int = 5, T: int = 10, eps: float
 
 def rgg_instance(seed: int = 0, n: int = 400, L: int = 64, T: int = 50, eps: float = 0.01,
                  mean_degree: float = 6.0, wait_cost: float = 0.05, cap_lo: float = 0.2,
-                 cap_hi: float = 1.0, cap_div: float = 8.0, name: Optional[str] = None):
+                 cap_hi: float = 1.0, cap_div: float = 8.0, name: Optional[str] = None,
+                 connect: str = "reject"):
     """Random geometric graph, Euclidean edge costs, single-node OD pairs per commodity."""
     rng = np.random.default_rng(seed)
-    src, dst, pos, length, r = rgg_graph(n, mean_degree, rng)
+    src, dst, pos, length, r = rgg_graph(n, mean_degree, rng, connect=connect)
     pairs = _od_pairs(n, src, dst, L, T - 2, rng)
     mass = rng.uniform(0.5, 2.0, L)
     cap = rng.uniform(cap_lo, cap_hi, src.shape[0]) * mass.sum() / cap_div
@@ -280,19 +322,31 @@ def config3(seed: int = 0):
     return grid_traffic_instance(seed=seed)
 
 
-def config4(seed: int = 0, count: int = 256):
-    """Batch of uneven instances: n~U{50..2000} RGG, T~U{10..80}, L~U{1..128}."""
+def _config4_member(args):
+    k, n, T, L, sub = args
+    inst = rgg_instance(seed=sub, n=n, L=L, T=T, eps=0.01, name=f"b{k}-rgg{n}-L{L}-T{T}", connect="bridge")
+    inst.meta.update({"config": 4, "batch_index": k})
+    return inst
+
+
+def config4(seed: int = 0, count: int = 256, workers: int = 1):
+    """Batch of uneven instances: n~U{50..2000} RGG (bridged to be connected), T~U{10..80},
+    L~U{1..128}.  The sizes and sub-seeds are drawn first, so `workers` > 1 (a spawn process
+    pool) gives the same instances."""
     rng = np.random.default_rng(seed)
-    out = []
+    specs = []
     for k in range(count):
         n = int(rng.integers(50, 2001))
         T = int(rng.integers(10, 81))
         L = int(rng.integers(1, 129))
         sub = int(rng.integers(2**31 - 1))
-        inst = rgg_instance(seed=sub, n=n, L=L, T=T, eps=0.01, name=f"b{k}-rgg{n}-L{L}-T{T}")
-        inst.meta.update({"config": 4, "batch_index": k})
-        out.append(inst)
-    return out
+        specs.append((k, n, T, L, sub))
+    if workers <= 1:
+        return [_config4_member(s) for s in specs]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_config4_member, specs, chunksize=4))
 
 
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4}

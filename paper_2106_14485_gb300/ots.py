@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libots.so")
 
 OTS_OK, OTS_ERR_INVALID_ARG, OTS_ERR_INFEASIBLE, OTS_ERR_NOT_CONVERGED = 0, 1, 2, 3
 OTS_ERR_TIMEOUT, OTS_ERR_OOM, OTS_ERR_CUDA, OTS_ERR_NUMERIC = 4, 5, 6, 7
+OTS_PENDING = 8
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _f64p = ctypes.POINTER(ctypes.c_double)
@@ -61,9 +62,25 @@ class SolveReport(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p), ("pool_bytes", ctypes.c_int64),
+                ("max_instances", ctypes.c_int32), ("max_items", ctypes.c_int32),
+                ("ticks_per_launch", ctypes.c_int32),
+                ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("resident", ctypes.c_int32), ("running", ctypes.c_int32), ("pool_bytes", ctypes.c_int64),
+                ("pool_used", ctypes.c_int64), ("launches", ctypes.c_int64), ("ticks", ctypes.c_int64),
+                ("items", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+
+
 EXPORTED = ["ots_default_solve_opts", "ots_create_problem", "ots_sinkhorn_solve", "ots_iterate", "ots_get_flows",
             "ots_get_commodity_flows", "ots_get_commodity_flows_noalloc", "ots_get_duals", "ots_set_duals", "ots_problem_info", "ots_last_pass_timing",
-            "ots_problem_stream", "ots_destroy_problem", "ots_status_string", "ots_last_error"]
+            "ots_problem_stream", "ots_destroy_problem", "ots_status_string", "ots_last_error",
+            "ots_default_batch_desc", "ots_batch_create", "ots_batch_add", "ots_batch_run", "ots_batch_status",
+            "ots_batch_get_flows", "ots_batch_get_duals", "ots_batch_remove", "ots_batch_info", "ots_batch_mapping",
+            "ots_batch_autotune", "ots_batch_destroy"]
 
 _lib = None
 
@@ -97,6 +114,23 @@ def load_library(path: str = LIB_PATH):
     lib.ots_status_string.restype = ctypes.c_char_p
     lib.ots_last_error.argtypes = []
     lib.ots_last_error.restype = ctypes.c_char_p
+    lib.ots_default_batch_desc.argtypes = [ctypes.POINTER(BatchDesc)]
+    lib.ots_batch_create.argtypes = [ctypes.POINTER(BatchDesc), ctypes.POINTER(P)]
+    lib.ots_batch_add.argtypes = [P, ctypes.POINTER(ProblemDesc), ctypes.POINTER(SolveOpts), _i32p]
+    lib.ots_batch_run.argtypes = [P, ctypes.c_int32, _i32p]
+    lib.ots_batch_status.argtypes = [P, ctypes.c_int32, ctypes.POINTER(SolveReport)]
+    lib.ots_batch_get_flows.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _f64p]
+    lib.ots_batch_get_duals.argtypes = [P, ctypes.c_int32, _f64p, _f64p, _f64p]
+    lib.ots_batch_remove.argtypes = [P, ctypes.c_int32]
+    lib.ots_batch_info.argtypes = [P, ctypes.POINTER(BatchStats)]
+    lib.ots_batch_mapping.argtypes = [P, ctypes.c_int32, _i32p, _i32p]
+    lib.ots_batch_autotune.argtypes = [P, ctypes.c_char_p]
+    lib.ots_batch_destroy.argtypes = [P]
+    lib.ots_batch_destroy.restype = None
+    for name in ("ots_default_batch_desc", "ots_batch_create", "ots_batch_add", "ots_batch_run", "ots_batch_status",
+                 "ots_batch_get_flows", "ots_batch_get_duals", "ots_batch_remove", "ots_batch_info",
+                 "ots_batch_mapping", "ots_batch_autotune"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("ots_default_solve_opts", "ots_create_problem", "ots_sinkhorn_solve", "ots_iterate",
                  "ots_get_flows", "ots_get_commodity_flows", "ots_get_commodity_flows_noalloc", "ots_get_duals", "ots_set_duals", "ots_problem_info",
                  "ots_last_pass_timing"):
@@ -162,11 +196,9 @@ def _torch_allocator(device: int):
     return ALLOC_FN(alloc), FREE_FN(free)
 
 
-def ots_create_problem(inst, device: int = 0, stream: int | None = None, allocator: str = "torch") -> Handle:
-    """Create a problem from an object with the attributes of ``instances.Instance``.
-
-    allocator: "torch" (PyTorch caching allocator) or "cuda" (cudaMalloc inside the library)."""
-    lib = load_library()
+def _problem_desc(inst, device: int = 0, stream: int | None = None):
+    """ots_problem_desc of an object with the attributes of ``instances.Instance`` plus the
+    host arrays it points into (keep them alive while the descriptor is used)."""
     c = lambda x, dt: np.ascontiguousarray(x, dtype=dt)
     arr = {
         "edge_src": c(inst.edge_src, np.int32), "edge_dst": c(inst.edge_dst, np.int32),
@@ -195,6 +227,15 @@ def ots_create_problem(inst, device: int = 0, stream: int | None = None, allocat
     d.snk_mass = _ptr(arr["snk_mass"], ctypes.c_double)
     d.device = int(device)
     d.stream = stream
+    return d, arr
+
+
+def ots_create_problem(inst, device: int = 0, stream: int | None = None, allocator: str = "torch") -> Handle:
+    """Create a problem from an object with the attributes of ``instances.Instance``.
+
+    allocator: "torch" (PyTorch caching allocator) or "cuda" (cudaMalloc inside the library)."""
+    lib = load_library()
+    d, arr = _problem_desc(inst, device, stream)
     keep = [arr]
     if allocator == "torch":
         a, f = _torch_allocator(int(device))
@@ -299,3 +340,119 @@ def ots_destroy_problem(h: Handle) -> None:
     if h.ptr:
         load_library().ots_destroy_problem(h.ptr)
         h.ptr = None
+
+
+# ---------------------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------------------
+class Batch:
+    """Owns an ``ots_batch*`` and the shapes of the instances added to it."""
+
+    def __init__(self, ptr, keep):
+        self.ptr = ptr
+        self._keep = keep
+        self.shapes = {}   # id -> (n_states, T, L, n_sources, n_sinks)
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                ots_batch_destroy(self)
+            except Exception:
+                pass
+
+
+def ots_batch_create(device: int = 0, pool_bytes: int = 4 << 30, max_instances: int = 256, max_items: int = 0,
+                     ticks_per_launch: int = 0, stream: int | None = None, allocator: str = "torch") -> Batch:
+    lib = load_library()
+    d = BatchDesc()
+    _check(lib.ots_default_batch_desc(ctypes.byref(d)))
+    d.device, d.stream, d.pool_bytes = int(device), stream, int(pool_bytes)
+    d.max_instances, d.max_items, d.ticks_per_launch = int(max_instances), int(max_items), int(ticks_per_launch)
+    keep = []
+    if allocator == "torch":
+        a, f = _torch_allocator(int(device))
+        d.alloc, d.free_fn = a, f
+        keep.append((a, f))
+    elif allocator != "cuda":
+        raise ValueError("allocator must be 'torch' or 'cuda'")
+    out = ctypes.c_void_p()
+    _check(lib.ots_batch_create(ctypes.byref(d), ctypes.byref(out)))
+    return Batch(out, keep)
+
+
+def ots_batch_add(b: Batch, inst, tol: float = 1e-6, max_iters: int = 100000, timeout_ms: float = 0.0,
+                  raise_on_error: bool = True):
+    """Add an instance; returns its id (or the status code when raise_on_error is False and the
+    call failed, e.g. OTS_ERR_OOM when the batch is full)."""
+    d, arr = _problem_desc(inst)
+    o = ots_default_solve_opts()
+    o.tol, o.max_iters, o.timeout_ms = tol, max_iters, timeout_ms
+    i = ctypes.c_int32(-1)
+    code = load_library().ots_batch_add(b.ptr, ctypes.byref(d), ctypes.byref(o), ctypes.byref(i))
+    if code != OTS_OK:
+        if raise_on_error:
+            _check(code)
+        return -code
+    b.shapes[i.value] = (int(inst.n_nodes) + d.n_edges, d.T, d.L, d.n_sources, d.n_sinks)
+    return i.value
+
+
+def ots_batch_run(b: Batch, max_launches: int = 1 << 30) -> int:
+    n = ctypes.c_int32(0)
+    _check(load_library().ots_batch_run(b.ptr, int(max_launches), ctypes.byref(n)))
+    return n.value
+
+
+def ots_batch_status(b: Batch, i: int) -> dict:
+    r = SolveReport()
+    code = load_library().ots_batch_status(b.ptr, int(i), ctypes.byref(r))
+    if code == OTS_ERR_INVALID_ARG:
+        _check(code)
+    out = r.as_dict()
+    out["status"] = code
+    return out
+
+
+def ots_batch_get_flows(b: Batch, i: int, t_begin: int = 1, t_end: int | None = None) -> np.ndarray:
+    S, T = b.shapes[i][0], b.shapes[i][1]
+    t_end = T + 1 if t_end is None else t_end
+    out = np.empty((t_end - t_begin, S), np.float64)
+    _check(load_library().ots_batch_get_flows(b.ptr, int(i), int(t_begin), int(t_end), _ptr(out, ctypes.c_double)))
+    return out
+
+
+def ots_batch_get_duals(b: Batch, i: int):
+    S, T, _, ns, nz = b.shapes[i]
+    lu = np.empty((T - 2, S), np.float64)
+    u1 = np.empty(ns, np.float64)
+    uT = np.empty(nz, np.float64)
+    _check(load_library().ots_batch_get_duals(b.ptr, int(i), _ptr(lu, ctypes.c_double), _ptr(u1, ctypes.c_double),
+                                              _ptr(uT, ctypes.c_double)))
+    return lu, u1, uT
+
+
+def ots_batch_remove(b: Batch, i: int) -> None:
+    _check(load_library().ots_batch_remove(b.ptr, int(i)))
+    b.shapes.pop(i, None)
+
+
+def ots_batch_info(b: Batch) -> dict:
+    st = BatchStats()
+    _check(load_library().ots_batch_info(b.ptr, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+def ots_batch_mapping(b: Batch, L: int):
+    g, c = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load_library().ots_batch_mapping(b.ptr, int(L), ctypes.byref(g), ctypes.byref(c)))
+    return g.value, c.value
+
+
+def ots_batch_autotune(b: Batch, cache_path: str | None = None) -> None:
+    _check(load_library().ots_batch_autotune(b.ptr, None if cache_path is None else cache_path.encode()))
+
+
+def ots_batch_destroy(b: Batch) -> None:
+    if b.ptr:
+        load_library().ots_batch_destroy(b.ptr)
+        b.ptr = None

@@ -35,6 +35,7 @@ def test_status_strings_need_no_gpu():
     from paper_2106_14485_gb300 import ots
     assert ots.ots_status_string(0) == "OTS_OK"
     assert ots.ots_status_string(2) == "OTS_ERR_INFEASIBLE"
+    assert ots.ots_status_string(ots.OTS_PENDING) == "OTS_PENDING"
     o = ots.ots_default_solve_opts()
     assert o.tol == 1e-6 and o.max_iters == 100000 and o.check_every == 10 and o.use_graph == 1
 
@@ -53,6 +54,10 @@ int main(void) {
          offsetof(ots_problem_desc, stream), offsetof(ots_problem_desc, alloc_ctx));
   printf("%zu %zu\n", sizeof(ots_solve_opts), offsetof(ots_solve_opts, threads_per_node));
   printf("%zu %zu\n", sizeof(ots_solve_report), offsetof(ots_solve_report, status));
+  printf("%zu %zu %zu\n", sizeof(ots_batch_desc), offsetof(ots_batch_desc, ticks_per_launch),
+         offsetof(ots_batch_desc, alloc_ctx));
+  printf("%zu %zu\n", sizeof(ots_batch_stats), offsetof(ots_batch_stats, d2h_bytes));
+  printf("%d\n", (int)OTS_PENDING);
   return 0;
 }
 '''
@@ -68,6 +73,10 @@ int main(void) {
     assert vals[2] == D.stream.offset and vals[3] == D.alloc_ctx.offset
     assert vals[4] == ctypes.sizeof(O) and vals[5] == O.threads_per_node.offset
     assert vals[6] == ctypes.sizeof(R) and vals[7] == R.status.offset
+    B, BS = ots.BatchDesc, ots.BatchStats
+    assert vals[8] == ctypes.sizeof(B) and vals[9] == B.ticks_per_launch.offset and vals[10] == B.alloc_ctx.offset
+    assert vals[11] == ctypes.sizeof(BS) and vals[12] == BS.d2h_bytes.offset
+    assert vals[13] == ots.OTS_PENDING
 
 
 def test_oracle_is_not_imported_by_the_product():
