@@ -56,6 +56,12 @@ def parse():
     ap.add_argument("--batch", type=int, default=256,
                     help="instances of the batched workload (uneven random geometric graphs); 0 = skip")
     ap.add_argument("--batch-max-passes", type=int, default=3000)
+    ap.add_argument("--serve-rates", type=str, default="50,200,1000",
+                    help="Poisson arrival rates (requests/s) of the serving workload; empty = skip")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate")
+    ap.add_argument("--serve-drain", type=float, default=5.0, help="extra time for open requests per rate")
+    ap.add_argument("--serve-large-passes", type=int, default=300,
+                    help="pass limit of the traffic-scale requests in the serving mix")
     ap.add_argument("--horizon", type=int, default=100,
                     help="T of the traffic-scale grid (100 = the benchmark workload; smaller values only "
                          "for profiling captures that must stay within a few GB)")
@@ -242,17 +248,13 @@ def pct(a, q):
     return float(np.percentile(np.asarray(a), q)) if len(a) else None
 
 
-def bench_batch(args, ots, torch, local):
+def bench_batch(args, ots, torch, local, insts, gen_s):
     """Batched workload: args.batch uneven instances (n ~ U{50..2000} random geometric graphs of
     mean degree 6, T ~ U{10..80}, L ~ U{1..128}, capacities U[0.2,1] * mass / 8, eps = 0.01)
     solved to marginal error <= tol (a) in one batch (persistent tick kernel, captured graphs,
     autotuned thread mapping) and (b) one instance at a time with ots_sinkhorn_solve (the
     plain single-instance GPU solver, convergence tested after every pass).  Both arms start
     from host arrays and end with the flows on the host."""
-    from paper_2106_14485_gb300 import instances
-    t0 = time.perf_counter()
-    insts = instances.config4(0, count=args.batch, workers=min(16, os.cpu_count() or 1))
-    gen_s = time.perf_counter() - t0
     need = 0
     for x in insts:
         g = 1
@@ -339,6 +341,72 @@ def bench_batch(args, ots, torch, local):
         "max_rel_flow_diff_batched_vs_plain": max(diffs) if diffs else None,
         "generate_s": gen_s,
     }
+
+
+def bench_serve(args, ots, torch, local, small, large):
+    """Serving workload: Poisson arrivals at each rate of a request mix drawn from the batched
+    workload's instances (95%) and traffic-scale instances (5%, pass limit
+    --serve-large-passes), each request solved to marginal error <= tol from host arrays to
+    flows on the host.  Served (a) by the continuous-batching server and (b) by the same server
+    in plain mode (one request at a time, single-instance solver).  Latency = submit -> result,
+    queueing included; requests still open after the window plus the drain time are counted
+    as open, not as latencies."""
+    rates = [float(r) for r in args.serve_rates.split(",") if r.strip()]
+    out = {"workload": f"Poisson arrivals; 95% drawn from the {len(small)} batched-workload instances, 5% "
+                       f"traffic-scale grid (n={large.n_nodes}, L={large.L}, T={large.T}, eps={large.eps}, "
+                       f"<= {args.serve_large_passes} passes); tol={args.tol}",
+           "window_s": args.serve_seconds, "drain_s": args.serve_drain, "rates": []}
+    for rate in rates:
+        rng = np.random.default_rng(int(rate))
+        n_req = max(1, int(rng.poisson(rate * args.serve_seconds)))
+        arrivals = np.sort(rng.uniform(0.0, args.serve_seconds, n_req))
+        kinds = rng.random(n_req) < 0.05
+        picks = rng.integers(0, len(small), n_req)
+        row = {"rate": rate, "requests": n_req, "large_requests": int(kinds.sum())}
+        for mode, name in ((0, "batched"), (1, "plain")):
+            srv = ots.ots_server_create(device=local, pool_bytes=int(0.5 * torch.cuda.mem_get_info(local)[0]),
+                                        max_instances=256, ticks_per_launch=8, builder_threads=4, mode=mode)
+            tickets = []
+            t0 = time.perf_counter()
+            for k in range(n_req):
+                now = time.perf_counter() - t0
+                if arrivals[k] > now:
+                    time.sleep(arrivals[k] - now)
+                if kinds[k]:
+                    tk = ots.ots_server_submit(srv, large, tol=args.tol, max_iters=args.serve_large_passes,
+                                               check_every=10)
+                else:
+                    tk = ots.ots_server_submit(srv, small[picks[k]], tol=args.tol, max_iters=args.batch_max_passes)
+                tickets.append((tk, bool(kinds[k])))
+            deadline = t0 + args.serve_seconds + args.serve_drain
+            for tk, _ in tickets:
+                left = (deadline - time.perf_counter()) * 1e3
+                if left <= 0:
+                    break
+                ots.ots_server_wait(srv, tk, left)
+            t_end = time.perf_counter()
+            lat = {False: [], True: []}
+            solved = {False: 0, True: 0}
+            open_ = {False: 0, True: 0}
+            for tk, big in tickets:
+                r = ots.ots_server_poll(srv, tk)
+                if r["status"] == ots.OTS_PENDING:
+                    open_[big] += 1
+                    continue
+                lat[big].append(ots.ots_server_timing(srv, tk)["total_ms"])
+                solved[big] += r["status"] == 0
+            info = ots.ots_server_info(srv)
+            ots.ots_server_destroy(srv)
+            span = t_end - t0
+            row[name] = {"solves_per_s": (solved[False] + solved[True]) / span,
+                         "small": {"p50_ms": pct(lat[False], 50), "p99_ms": pct(lat[False], 99),
+                                   "solved": solved[False], "open": open_[False]},
+                         "large": {"p50_ms": pct(lat[True], 50), "p99_ms": pct(lat[True], 99),
+                                   "solved": solved[True], "open": open_[True]},
+                         "p50_ms": pct(lat[False] + lat[True], 50), "p99_ms": pct(lat[False] + lat[True], 99),
+                         "span_s": span, "batch_launches": int(info["batch_launches"])}
+        out["rates"].append(row)
+    return out
 
 
 def run_ours(args):
@@ -446,7 +514,16 @@ def run_ours(args):
                   "p99_ms": float(np.percentile(lat, 99) * 1e3), "final_src_residual": rs["src_residual"],
                   "final_cap_violation": rs["cap_violation"]}
 
-    batch = bench_batch(args, ots, torch, local) if args.batch > 0 else None
+    batch = serve = None
+    if args.batch > 0 or args.serve_rates.strip():
+        from paper_2106_14485_gb300 import instances as _inst
+        tg = time.perf_counter()
+        c4 = _inst.config4(0, count=max(args.batch, 64), workers=min(16, os.cpu_count() or 1))
+        gen_s = time.perf_counter() - tg
+        if args.batch > 0:
+            batch = bench_batch(args, ots, torch, local, c4[:args.batch], gen_s)
+        if args.serve_rates.strip():
+            serve = bench_serve(args, ots, torch, local, c4, inst)
 
     if rank != 0:
         if pg is not None:
@@ -478,7 +555,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 float-float (fp32 hi + fp16 lo log2 messages), f64 reductions",
             "data": "synthetic", "config": workload_config(inst, args.tol),
-            "solves_per_s": solves, "batch": batch,
+            "solves_per_s": solves, "batch": batch, "serving": serve,
             "passes_timed": args.steps, "src_residual_after": final["src_residual"],
             "cap_violation_after": final["cap_violation"],
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches)}

@@ -305,6 +305,79 @@ ots_status ots_batch_autotune(ots_batch *b, const char *cache_path);
 /* Release everything of the batch (NULL is ignored). */
 void ots_batch_destroy(ots_batch *b);
 
+/* ------------------------------------------------------------------------------------
+ * Server: a request loop with continuous batching on one device.
+ *
+ * The paper has no counterpart; this is how the library serves a stream of routing solves
+ * of different sizes, horizons and commodity counts.  ots_server_submit copies a request
+ * and returns at once.  Builder threads build and upload each request into the batch's
+ * device pool as soon as it fits (admission by memory) and a slot is free; a driver thread
+ * admits built requests into the running batch between graph launches, so requests that
+ * arrive while others are on the GPU join them and their work overlaps; finished requests
+ * leave with their flows and free their slot and memory.  Requests the batch does not take
+ * (L > 256 or per-commodity costs) are solved one at a time by the single-instance solver on
+ * a stream of their own, next to the batch, with memory from the same pool.  Every result is
+ * the one the request gets alone (the batch computes each instance independently).
+ * With mode = 1 every request is instead solved to completion, in arrival order, by the
+ * single-instance solver: the one-at-a-time baseline behind the same interface.
+ * ------------------------------------------------------------------------------------ */
+typedef struct ots_server ots_server;
+
+typedef struct ots_server_desc {
+  ots_batch_desc batch;      /* device, stream, pool, slots, steps per launch of the batch */
+  int32_t builder_threads;   /* host threads building requests (0 = 2) */
+  int32_t max_queued;        /* open requests accepted at once (0 = unlimited); beyond it
+                                ots_server_submit returns OTS_ERR_OOM */
+  int32_t mode;              /* 0: continuous batching; 1: one request at a time */
+} ots_server_desc;
+
+typedef struct ots_server_stats {
+  int64_t submitted, completed, failed;
+  int32_t queued;            /* submitted, not yet built or admitted */
+  int32_t building;          /* being built by a builder thread */
+  int32_t resident;          /* in the batch */
+  int32_t large_running;     /* being solved by the single-instance lane */
+  int64_t pool_bytes, pool_used;
+  int64_t batch_launches, batch_ticks;
+} ots_server_stats;
+
+/* Defaults: ots_default_batch_desc with 8 steps per launch, 2 builder threads, mode 0. */
+ots_status ots_default_server_desc(ots_server_desc *d);
+
+/* Start the server's threads (and create its batch in mode 0). */
+ots_status ots_server_create(const ots_server_desc *desc, ots_server **out);
+
+/* Submit a request: the descriptor's host arrays are copied (device, stream and allocator
+ * fields are ignored); opts as for ots_batch_add (tol, max_iters, timeout_ms) or
+ * ots_sinkhorn_solve (large and plain requests).  *ticket names the request.  Validation
+ * errors of the instance surface as its final status. */
+ots_status ots_server_submit(ots_server *s, const ots_problem_desc *desc, const ots_solve_opts *opts,
+                             int64_t *ticket);
+
+/* OTS_PENDING while the request is open, then its final status; rep (may be NULL) gets the
+ * measures of its last pass, rep->seconds = time from submit to result. */
+ots_status ots_server_poll(ots_server *s, int64_t ticket, ots_solve_report *rep);
+
+/* Block until the request is finished (timeout_ms <= 0: no limit), then as ots_server_poll. */
+ots_status ots_server_wait(ots_server *s, int64_t ticket, double timeout_ms, ots_solve_report *rep);
+
+/* Flows of a finished request (OTS_OK or OTS_ERR_NOT_CONVERGED), same layout as ots_get_flows
+ * (copied from the host-side result; no device work). */
+ots_status ots_server_get_flows(ots_server *s, int64_t ticket, int32_t t_begin, int32_t t_end, double *out);
+
+/* Milliseconds of a finished request: ms[0] from submit to admission (queueing, building),
+ * ms[1] from admission to result, ms[2] from submit to result. */
+ots_status ots_server_timing(ots_server *s, int64_t ticket, double *ms);
+
+/* Drop a finished request's result. */
+ots_status ots_server_release(ots_server *s, int64_t ticket);
+
+ots_status ots_server_info(ots_server *s, ots_server_stats *out);
+
+/* Stop the threads (a single-instance solve in progress runs to its end first) and free
+ * everything; open requests are dropped. */
+void ots_server_destroy(ots_server *s);
+
 /* Free all device and host memory of the problem (NULL is ignored). */
 void ots_destroy_problem(ots_problem *p);
 

@@ -429,7 +429,9 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
 
 }  // extern "C"
 
-ots_status ots_host::create_problem_impl(const ots_problem_desc *d, const CreateOpts &co, ots_problem **out) {
+// Host part of the construction (no CUDA call): validation, state graph, per-state data,
+// boundary triples, feasibility; the arrays to upload stay in p->host.
+ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateOpts &co, ots_problem **out) {
   if (!d || !out) return fail(OTS_ERR_INVALID_ARG, "desc or out is NULL");
   *out = nullptr;
   if (d->n_nodes < 1 || d->n_edges < 0) return fail(OTS_ERR_INVALID_ARG, "n_nodes must be >= 1 and n_edges >= 0");
@@ -596,13 +598,70 @@ ots_status ots_host::create_problem_impl(const ots_problem_desc *d, const Create
     if (!feasible(p, eptr, enbr, why)) return bail(fail(OTS_ERR_INFEASIBLE, "%s", why.c_str()));
   }
 
-  // ---- device ----
+  p->stream = (cudaStream_t)d->stream;          // NULL: the device step creates one
+  p->host.reset(new (std::nothrow) HostArrays());
+  if (!p->host) return bail(fail(OTS_ERR_OOM, "host allocation failed"));
+  HostArrays &H = *p->host;
+  H.in_ptr = std::move(in_ptr);
+  H.out_ptr = std::move(out_ptr);
+  H.in_state = std::move(in_state);
+  H.in_nbr = std::move(in_nbr);
+  H.out_state = std::move(out_state);
+  H.out_nbr = std::move(out_nbr);
+  H.st_inpos = std::move(st_inpos);
+  H.st_outpos = std::move(st_outpos);
+  H.in_outpos = std::move(in_outpos);
+  H.kl_hi = std::move(kl_hi);
+  H.kl_lo = std::move(kl_lo);
+  H.logd_hi = std::move(logd_hi);
+  H.logd_lo = std::move(logd_lo);
+  H.in_kl_hi = std::move(in_kl_hi);
+  H.in_kl_lo = std::move(in_kl_lo);
+  H.in_logd_hi = std::move(in_logd_hi);
+  H.in_logd_lo = std::move(in_logd_lo);
+  H.klc_hi = std::move(klc_hi);
+  H.cap = std::move(cap);
+  H.in_cap = std::move(in_cap);
+  H.klc_lo = std::move(klc_lo);
+  *out = p;
+  return OTS_OK;
+}
+
+// Device part of the construction: stream, kernel set-up, one arena for all device arrays,
+// uploads of the host arrays kept by the host part (released at the end), initial duals.
+// On failure the caller destroys p.
+ots_status ots_host::build_problem_device(ots_problem *p) {
+  if (!p || !p->host) return fail(OTS_ERR_INVALID_ARG, "problem has no host arrays to upload");
+  HostArrays &H = *p->host;
+  auto &in_ptr = H.in_ptr;
+  auto &out_ptr = H.out_ptr;
+  auto &in_state = H.in_state;
+  auto &in_nbr = H.in_nbr;
+  auto &out_state = H.out_state;
+  auto &out_nbr = H.out_nbr;
+  auto &st_inpos = H.st_inpos;
+  auto &st_outpos = H.st_outpos;
+  auto &in_outpos = H.in_outpos;
+  auto &kl_hi = H.kl_hi;
+  auto &kl_lo = H.kl_lo;
+  auto &logd_hi = H.logd_hi;
+  auto &logd_lo = H.logd_lo;
+  auto &in_kl_hi = H.in_kl_hi;
+  auto &in_kl_lo = H.in_kl_lo;
+  auto &in_logd_hi = H.in_logd_hi;
+  auto &in_logd_lo = H.in_logd_lo;
+  auto &klc_hi = H.klc_hi;
+  auto &cap = H.cap;
+  auto &in_cap = H.in_cap;
+  auto &klc_lo = H.klc_lo;
+  auto bail = [&](ots_status s) { return s; };
+  ots_status st = OTS_OK;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return bail(fail(OTS_ERR_CUDA, "no CUDA device"));
   if (p->dev < 0 || p->dev >= ndev) return bail(fail(OTS_ERR_INVALID_ARG, "device %d out of range", p->dev));
   DeviceGuard guard(p->dev);
-  if (d->stream) {
-    p->stream = (cudaStream_t)d->stream;
+  if (p->stream) {
+    p->own_stream = false;
   } else {
     if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess)
       return bail(fail(OTS_ERR_CUDA, "stream creation failed"));
@@ -709,11 +768,8 @@ ots_status ots_host::create_problem_impl(const ots_problem_desc *d, const Create
     UP(b.d_tri_other, b.tri_other); UP(b.d_tri_l, b.tri_l); UP(b.d_tri_R, b.tri_R); UP(b.d_tri_logR, logR[k]);
   }
 #undef UP
-  if (p->member) {
-    // duals, panels and accumulators are initialised by the batched kernel's set-up step
-    *out = p;
-    return OTS_OK;
-  }
+  p->host.reset();                             // pageable copies have completed
+  if (p->member) return OTS_OK;  // duals, panels, accumulators: the batched kernel's set-up step
   if (cudaMemsetAsync(p->d_stats, 0, sizeof(DevStats), p->stream) != cudaSuccess ||
       cudaMemsetAsync(p->d_counter, 0, 4 * sizeof(unsigned int), p->stream) != cudaSuccess ||
       cudaMemsetAsync(p->d_flow, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess)
@@ -730,6 +786,18 @@ ots_status ots_host::create_problem_impl(const ots_problem_desc *d, const Create
   st = reset_duals(p);
   if (st) return bail(st);
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "%s", cudaGetErrorString(cudaGetLastError())));
+  return OTS_OK;
+}
+
+ots_status ots_host::create_problem_impl(const ots_problem_desc *d, const CreateOpts &co, ots_problem **out) {
+  ots_problem *p = nullptr;
+  ots_status st = build_problem_host(d, co, &p);
+  if (st) return st;
+  st = build_problem_device(p);
+  if (st) {
+    ots_destroy_problem(p);
+    return st;
+  }
   *out = p;
   return OTS_OK;
 }

@@ -164,7 +164,6 @@ struct ots_batch {
   BatchCtl *d_ctl = nullptr;
   int2 *d_items = nullptr;
   int *d_n_items = nullptr;
-  unsigned int *d_fetch = nullptr;
   BatchInst *h_inst = nullptr;       // pinned staging, one per slot
   BatchCtl *h_ctl_init = nullptr;    // pinned staging, one per slot
   BatchCtl *h_ctl = nullptr;         // pinned copy of d_ctl after every launch
@@ -189,7 +188,7 @@ void release_device(ots_batch *b) {
   if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
   for (auto &s : b->slots)
     if (s.p) { ots_destroy_problem(s.p); s.p = nullptr; }
-  void *dev_ptrs[] = {b->d_inst, b->d_ctl, b->d_items, b->d_n_items, b->d_fetch};
+  void *dev_ptrs[] = {b->d_inst, b->d_ctl, b->d_items, b->d_n_items};
   for (void *p : dev_ptrs)
     if (p) cudaFree(p);
   void *host_ptrs[] = {b->h_inst, b->h_ctl_init, b->h_ctl, b->h_items, b->h_n_items, b->h_stop};
@@ -209,7 +208,6 @@ ots_status capture_graph(ots_batch *b) {
   ta.ctl = b->d_ctl;
   ta.items = b->d_items;
   ta.n_items = b->d_n_items;
-  ta.fetch = b->d_fetch;
   cudaGraph_t g = nullptr;
   OTS_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
@@ -227,12 +225,42 @@ ots_status capture_graph(ots_batch *b) {
   return OTS_OK;
 }
 
-// Rebuild and upload the item list of the running instances (slot order, items in order).
+// Rounds per item for the current load: items of one round while the running instances
+// have few node rows in total (keeps every SM busy in the tail of a batch), up to 8 rounds
+// when they have many (fewer, longer items).
+int choose_rounds(const ots_batch *b) {
+  long long rows = 0;
+  for (int s = 0; s < b->max_slots; ++s) {
+    const Slot &sl = b->slots[s];
+    if (sl.state != SlotState::Running) continue;
+    const BatchInst &I = b->h_inst[s];
+    rows += (I.V + I.npb - 1) / I.npb;
+  }
+  const long long r = rows / (4LL * std::max(b->grid, 1));
+  return (int)std::max(1LL, std::min(8LL, r));
+}
+
+// Rebuild and upload the item list of the running instances (slot order, items in order),
+// after re-deriving the items of every running instance for the current rounds per item.
 ots_status upload_items(ots_batch *b) {
+  const int R = choose_rounds(b);
+  for (int s = 0; s < b->max_slots; ++s) {
+    Slot &sl = b->slots[s];
+    if (sl.state != SlotState::Running) continue;
+    BatchInst &I = b->h_inst[s];
+    if (I.rounds == R) continue;
+    I.rounds = R;
+    I.npi = R * I.npb;
+    I.n_items = (I.V + I.npi - 1) / I.npi;
+    sl.n_items = I.n_items;
+    OTS_CUDA(cudaMemcpyAsync(b->d_inst + s, &I, sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
+    b->h2d += (long long)sizeof(BatchInst);
+  }
   int n = 0;
   for (int s = 0; s < b->max_slots; ++s) {
     const Slot &sl = b->slots[s];
     if (sl.state != SlotState::Running) continue;
+    if (n + sl.n_items > b->max_items) return fail(OTS_ERR_OOM, "item list full (%d items)", b->max_items);
     for (int k = 0; k < sl.n_items; ++k) b->h_items[n++] = make_int2(s, k);
   }
   *b->h_n_items = n;
@@ -314,8 +342,7 @@ ots_status ots_batch_create(const ots_batch_desc *d, ots_batch **out) {
   if (cudaMalloc(&b->d_inst, sizeof(BatchInst) * ns) != cudaSuccess ||
       cudaMalloc(&b->d_ctl, sizeof(BatchCtl) * ns) != cudaSuccess ||
       cudaMalloc(&b->d_items, sizeof(int2) * ni) != cudaSuccess ||
-      cudaMalloc(&b->d_n_items, sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&b->d_fetch, 2 * sizeof(unsigned int)) != cudaSuccess)
+      cudaMalloc(&b->d_n_items, sizeof(int)) != cudaSuccess)
     return bail(fail(OTS_ERR_OOM, "batch tables"));
   if (cudaMallocHost(&b->h_inst, sizeof(BatchInst) * ns) != cudaSuccess ||
       cudaMallocHost(&b->h_ctl_init, sizeof(BatchCtl) * ns) != cudaSuccess ||
@@ -329,8 +356,7 @@ ots_status ots_batch_create(const ots_batch_desc *d, ots_batch **out) {
   std::memset(b->h_ctl, 0, sizeof(BatchCtl) * ns);
   if (cudaMemsetAsync(b->d_ctl, 0, sizeof(BatchCtl) * ns, b->stream) != cudaSuccess ||
       cudaMemsetAsync(b->d_inst, 0, sizeof(BatchInst) * ns, b->stream) != cudaSuccess ||
-      cudaMemsetAsync(b->d_n_items, 0, sizeof(int), b->stream) != cudaSuccess ||
-      cudaMemsetAsync(b->d_fetch, 0, 2 * sizeof(unsigned int), b->stream) != cudaSuccess)
+      cudaMemsetAsync(b->d_n_items, 0, sizeof(int), b->stream) != cudaSuccess)
     return bail(fail(OTS_ERR_CUDA, "batch table init"));
   if (batch_tick_grid(&b->grid) != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "tick kernel occupancy"));
   ots_status st = capture_graph(b);
@@ -361,25 +387,32 @@ ots_status ots_batch_add(ots_batch *b, const ots_problem_desc *desc, const ots_s
   clear_error();
   if (!b || !desc || !id) return fail(OTS_ERR_INVALID_ARG, "NULL argument");
   *id = -1;
-  ots_solve_opts o;
-  ots_default_solve_opts(&o);
-  if (opts) o = *opts;
-  if (!(o.tol > 0.0) || o.max_iters < 1) return fail(OTS_ERR_INVALID_ARG, "bad solve options");
-  if (desc->L < 1 || desc->L > 256) return fail(OTS_ERR_INVALID_ARG, "batched instances take 1 <= L <= 256");
-  int s = -1;
-  for (int k = 0; k < b->max_slots; ++k)
-    if (b->slots[k].state == SlotState::Free) { s = k; break; }
-  if (s < 0) return fail(OTS_ERR_OOM, "no free slot (%d resident)", b->max_slots);
+  if (batch_free_slots(b) == 0) return fail(OTS_ERR_OOM, "no free slot (%d resident)", b->max_slots);
   DeviceGuard guard(b->dev);
+  ots_problem *p = nullptr;
+  ots_status st = batch_prepare(b, desc, b->stream, &p);
+  if (st) return st;
+  st = batch_admit(b, p, opts, id);
+  if (st) ots_destroy_problem(p);
+  return st;
+}
+
+}  // extern "C"
+
+// Host build and upload of a batch member (its mapping from the batch's table, its memory
+// from the pool, uploads on `upload_stream`).  Touches no batch table, so builder threads may
+// call it while the driver thread runs the batch; the caller synchronises upload_stream
+// before batch_admit when it is not the batch stream.
+ots_status ots_host::batch_prepare(ots_batch *b, const ots_problem_desc *desc, cudaStream_t upload_stream,
+                                   ots_problem **out) {
+  *out = nullptr;
+  if (desc->L < 1 || desc->L > 256) return fail(OTS_ERR_INVALID_ARG, "batched instances take 1 <= L <= 256");
+  if (desc->commodity_cost) return fail(OTS_ERR_INVALID_ARG, "batched instances take commodity-independent costs");
   int G = 0, C = 0;
   ots_batch_mapping(b, desc->L, &G, &C);
-  const int npb = kTickBlock / G;
-  const int n_items = (desc->n_nodes + npb - 1) / npb;
-  if (b->n_items_list + n_items > b->max_items) return fail(OTS_ERR_OOM, "item list full (%d items)", b->max_items);
-
   ots_problem_desc d = *desc;
   d.device = b->dev;
-  d.stream = b->stream;
+  d.stream = upload_stream;
   d.alloc = pool_alloc_cb;
   d.free_fn = pool_free_cb;
   d.alloc_ctx = &b->pool;
@@ -390,11 +423,42 @@ ots_status ots_batch_add(ots_batch *b, const ots_problem_desc *desc, const ots_s
   ots_problem *p = nullptr;
   ots_status st = create_problem_impl(&d, co, &p);
   if (st) return st;
+  p->stream = b->stream;                       // all later work of the member is on the batch stream
+  *out = p;
+  return OTS_OK;
+}
+
+Pool *ots_host::batch_pool(ots_batch *b) { return &b->pool; }
+
+int ots_host::batch_free_slots(const ots_batch *b) {
+  int n = 0;
+  for (auto &s : b->slots) n += s.state == SlotState::Free;
+  return n;
+}
+
+// Put a prepared member into a free slot (driver thread only); the batch owns p afterwards.
+ots_status ots_host::batch_admit(ots_batch *b, ots_problem *p, const ots_solve_opts *opts, int32_t *id) {
+  ots_solve_opts o;
+  ots_default_solve_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || o.max_iters < 1) return fail(OTS_ERR_INVALID_ARG, "bad solve options");
+  int s = -1;
+  for (int k = 0; k < b->max_slots; ++k)
+    if (b->slots[k].state == SlotState::Free) { s = k; break; }
+  if (s < 0) return fail(OTS_ERR_OOM, "no free slot (%d resident)", b->max_slots);
+  const int G = p->G, C = p->C;
+  const int npb = kTickBlock / G;
+  // one round per item to start with; upload_items re-derives the rounds for the load
+  const int rounds = 1;
+  const int npi = npb;
+  const int n_items = (p->V + npi - 1) / npi;
+  if (b->n_items_list + n_items > b->max_items) return fail(OTS_ERR_OOM, "item list full (%d items)", b->max_items);
+  DeviceGuard guard(b->dev);
 
   BatchInst &I = b->h_inst[s];
   std::memset(&I, 0, sizeof(I));
   I.V = p->V; I.S = p->S; I.T = p->T; I.Lp = p->Lp; I.G = G; I.C = C;
-  I.n_items = n_items; I.npb = npb;
+  I.n_items = n_items; I.npb = npb; I.rounds = rounds; I.npi = npi;
   I.qs = p->qs;
   I.mass = p->mass; I.eps = p->eps; I.tol = o.tol;
   I.max_passes = o.max_iters;
@@ -412,12 +476,8 @@ ots_status ots_batch_add(ots_batch *b, const ots_problem_desc *desc, const ots_s
   BatchCtl &c = b->h_ctl_init[s];
   std::memset(&c, 0, sizeof(c));
   c.status = kSlotRunning;
-  cudaError_t e = cudaMemcpyAsync(b->d_inst + s, &I, sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_ctl + s, &c, sizeof(BatchCtl), cudaMemcpyHostToDevice, b->stream);
-  if (e != cudaSuccess) {
-    ots_destroy_problem(p);
-    return fail(OTS_ERR_CUDA, "slot upload: %s", cudaGetErrorString(e));
-  }
+  OTS_CUDA(cudaMemcpyAsync(b->d_inst + s, &I, sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
+  OTS_CUDA(cudaMemcpyAsync(b->d_ctl + s, &c, sizeof(BatchCtl), cudaMemcpyHostToDevice, b->stream));
   b->h2d += (long long)(sizeof(BatchInst) + sizeof(BatchCtl)) + p->h2d_bytes;
   Slot &sl = b->slots[s];
   sl = Slot{};
@@ -435,6 +495,8 @@ ots_status ots_batch_add(ots_batch *b, const ots_problem_desc *desc, const ots_s
   *id = sl.id;
   return OTS_OK;
 }
+
+extern "C" {
 
 ots_status ots_batch_run(ots_batch *b, int32_t max_launches, int32_t *n_running) {
   clear_error();
@@ -520,12 +582,12 @@ ots_status ots_batch_get_flows(ots_batch *b, int32_t id, int32_t t_begin, int32_
   DeviceGuard guard(b->dev);
   const size_t S = p->S;
   std::vector<double> sf(p->src.n), zf(p->snk.n);
-  for (int t = t_begin; t < t_end; ++t)
-    if (t >= 2 && t <= p->T - 1) {
-      OTS_CUDA(cudaMemcpyAsync(out + (size_t)(t - t_begin) * S, p->d_flow + (size_t)t * S, sizeof(double) * S,
-                               cudaMemcpyDeviceToHost, b->stream));
-      b->d2h += (long long)(sizeof(double) * S);
-    }
+  const int t0 = std::max(t_begin, 2), t1 = std::min(t_end, p->T);   // interior rows, one copy
+  if (t0 < t1) {
+    OTS_CUDA(cudaMemcpyAsync(out + (size_t)(t0 - t_begin) * S, p->d_flow + (size_t)t0 * S,
+                             sizeof(double) * S * (t1 - t0), cudaMemcpyDeviceToHost, b->stream));
+    b->d2h += (long long)(sizeof(double) * S * (t1 - t0));
+  }
   if (p->src.n) OTS_CUDA(cudaMemcpyAsync(sf.data(), p->src.d_flow, sizeof(double) * p->src.n, cudaMemcpyDeviceToHost, b->stream));
   if (p->snk.n) OTS_CUDA(cudaMemcpyAsync(zf.data(), p->snk.d_flow, sizeof(double) * p->snk.n, cudaMemcpyDeviceToHost, b->stream));
   b->d2h += (long long)(sizeof(double) * (p->src.n + p->snk.n));

@@ -7,7 +7,8 @@
 // t = T-1..2, and after convergence one flows pass).  Instances therefore sit at different
 // steps and horizons in the same launch, and an instance that finishes frees its slot
 // without stopping the others.  The work of a tick is a list of items (slot, item index);
-// item k of an instance covers nodes [k npb, (k+1) npb) of its node panels, or a slice of its
+// item k of an instance covers nodes [k npi, (k+1) npi) of its node panels (npi = rounds x
+// npb, one round being one node row per G-thread group of the block), or a slice of its
 // states or boundary triples, depending on the step.
 #pragma once
 
@@ -36,9 +37,11 @@ struct BndSide {
   double *tri_logU, *tri_flow;
 };
 
-// Static description of one resident instance (written by the host at admission).
-struct BatchInst {
-  int V, S, T, Lp, G, C, n_items, npb;   // npb: nodes per item = kTickBlock / G
+// Static description of one resident instance (written by the host at admission; copied
+// into shared memory by every item, 16 bytes per lane).
+struct alignas(16) BatchInst {
+  int V, S, T, Lp, G, C, n_items, npb;   // npb: nodes per round = kTickBlock / G
+  int rounds, npi, pad1, pad2;           // npi: nodes per item = rounds * npb
   QScale qs;
   double mass, eps, tol;
   int max_passes, pad;
@@ -69,12 +72,13 @@ struct alignas(16) BatchCtl {
   PassReport report;
 };
 
+static_assert(sizeof(BatchInst) % 16 == 0, "BatchInst is copied in 16-byte words");
+
 struct TickArgs {
   const BatchInst *inst;         // [slots]
   BatchCtl *ctl;                 // [slots]
   const int2 *items;             // (slot, item index within the instance)
   const int *n_items;            // device scalar: number of items in the list
-  unsigned int *fetch;           // [2]: item fetch counter, exited blocks
 };
 
 }  // namespace ots

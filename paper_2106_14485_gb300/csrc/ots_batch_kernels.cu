@@ -12,10 +12,12 @@
 // The message arithmetic is that of the per-instance kernels (node-level rows, quantised
 // hi/lo storage, batched log-sum-exp), with the thread mapping as a runtime parameter of the
 // instance: G threads per node (G <= 32, so a node row is a slice of one warp) and C = 1 or 2
-// chunks of 4 commodities per thread, panel width Lp = 4 G C.  Blocks are persistent and pull
-// items from the tick's list; the last item of an instance to finish reduces the items'
-// FP64 partial sums in a fixed order and advances the instance, so every result is
-// deterministic and independent of the other instances in the batch.
+// chunks of 4 commodities per thread, panel width Lp = 4 G C.  Blocks are persistent: block b
+// takes items b, b + grid, b + 2 grid, ... of the tick's list, and stages the next item's
+// header and instance description in shared memory while it works on the current one.  The
+// last item of an instance to finish reduces the items' FP64 partial sums in a fixed order
+// and advances the instance, so every result is deterministic and independent of the other
+// instances in the batch.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -167,14 +169,17 @@ __device__ __forceinline__ void group_reduce_rt(float (&x)[KB], int G, unsigned 
   }
 }
 
-// Forward step t for nodes [v0, v0 + kTickBlock / G): capacity update of each in-state j of
-// a node (thread j mod G of the node's group owns it) and A_t of the node.
+// Forward step t for the nodes [v0, v0 + kTickBlock / G) of one round: capacity update of
+// each in-state j of a node (thread j mod G of the node's group owns it) and A_t of the node.
+// [jb, je) is the node's in-state range (loaded by the caller one round ahead).  When the
+// group has at least KB threads, each owner loads its state's inputs together with the
+// gathered rows, so the update waits for no further load.
 template <int C>
-__device__ __forceinline__ void fwd_item(const StepArgs &a, int G, int v0, float2 (*s_w)[6], double &viol,
-                                         double &dual) {
+__device__ __forceinline__ void fwd_round(const StepArgs &a, int G, int v0, int jb, int je, float2 (*s_w)[6],
+                                          double &viol, double &dual) {
   constexpr int KB = KBOf<C>::value;
   const int g = threadIdx.x & (G - 1);
-  const int nib = threadIdx.x / G;                 // node within the item
+  const int nib = threadIdx.x / G;                 // node within the round
   const int v = v0 + nib;
   const bool active = v < a.V;
   const unsigned lane = threadIdx.x & 31u;
@@ -182,6 +187,7 @@ __device__ __forceinline__ void fwd_item(const StepArgs &a, int G, int v0, float
   const unsigned mask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << base);
   const float lo_unit = a.qs.lo_unit;
   const size_t rowv = (size_t)(active ? v : 0) * a.Lp;
+  const bool own1 = G >= KB;                       // at most one in-state per thread
 
   float bh[C][4], bl[C][4];
 #pragma unroll
@@ -197,14 +203,28 @@ __device__ __forceinline__ void fwd_item(const StepArgs &a, int G, int v0, float
 #pragma unroll
     for (int q = 0; q < 4; ++q) { M[c][q] = 2.f * kNeg; acc[c][q] = 0.f; }
 
-  const int jb = active ? a.ptr[v] : 0;
-  const int je = active ? a.ptr[v + 1] : 0;
+  if (!active) je = jb;
   for (int j0 = jb; j0 < je; j0 += KB) {           // uniform within the group
     const int nb = min(KB, je - j0);
     int st[KB];
     float xh[KB][C][4];
     uint32_t xw[KB][C][2];
     gather_rt<C, KB>(a, G, j0, nb, g, st, xh, xw);
+
+    // inputs of the owned in-state (one per thread when own1)
+    int sk = 0;
+    float klh = 0.f, kll = 0.f, ldh = 0.f, ldl = 0.f, wih = kNeg, wil = 0.f;
+    double capk = 0.0, luo = 0.0;
+    if (own1 && g < nb) {
+#pragma unroll
+      for (int k = 0; k < KB; ++k)
+        if (k == g) sk = st[k];
+      klh = a.kl_hi[sk]; kll = a.kl_lo[sk];
+      ldh = a.logd_hi[sk]; ldl = a.logd_lo[sk];
+      capk = a.cap[sk];
+      luo = a.logu_t[sk];
+      if (a.mode != 0) { wih = a.w_hi_t[sk]; wil = a.w_lo_t[sk]; }
+    }
 
     // column log-sum-exp over the commodities of A_{t-1}[tail j] + B_{t+1}[v] per in-state
     float cm[KB], cs[KB];
@@ -235,16 +255,36 @@ __device__ __forceinline__ void fwd_item(const StepArgs &a, int G, int v0, float
     }
     group_reduce_rt<KB, false>(cs, G, mask);
 
-    // capacity updates: in-state mk is updated by thread mk mod G; W goes through shared memory
-    for (int mk = g; mk < nb; mk += G) {
-      float m = cm[0], s = cs[0];
-      int sk = st[0];
+    // capacity updates; W goes to the group through shared memory
+    if (own1) {
+      if (g < nb) {
+        float m = cm[0], sm = cs[0];
 #pragma unroll
-      for (int k = 1; k < KB; ++k)
-        if (k == mk) { m = cm[k]; s = cs[k]; sk = st[k]; }
-      float h, l;
-      update_state<false>(a, sk, m, s, true, h, l, viol, dual);
-      s_w[nib][mk] = make_float2(h, l);
+        for (int k = 1; k < KB; ++k)
+          if (k == g) { m = cm[k]; sm = cs[k]; }
+        float h, l;
+        double lu_new = 0.0, flow = 0.0;
+        update_meta(a.mode, a.qs, m, sm, klh, kll, ldh, ldl, capk, luo, wih, wil, h, l, lu_new, flow, viol, dual);
+        if (a.mode == 0) {
+          a.logu_t[sk] = lu_new;
+          a.w_hi_t[sk] = h;
+          a.w_lo_t[sk] = l;
+        } else {
+          a.flow_t[sk] = flow;
+        }
+        s_w[nib][g] = make_float2(h, l);
+      }
+    } else {
+      for (int mk = g; mk < nb; mk += G) {
+        float m = cm[0], sm = cs[0];
+        int skk = st[0];
+#pragma unroll
+        for (int k = 1; k < KB; ++k)
+          if (k == mk) { m = cm[k]; sm = cs[k]; skk = st[k]; }
+        float h, l;
+        update_state<false>(a, skk, m, sm, true, h, l, viol, dual);
+        s_w[nib][mk] = make_float2(h, l);
+      }
     }
     __syncwarp(mask);
     float wh[KB], wl[KB];
@@ -269,9 +309,10 @@ __device__ __forceinline__ void fwd_item(const StepArgs &a, int G, int v0, float
   }
 }
 
-// Backward step t for nodes [v0, v0 + kTickBlock / G): B_t[v] over the out-states of v.
+// Backward step t for the nodes [v0, v0 + kTickBlock / G) of one round: B_t[v] over the
+// out-states of v.
 template <int C>
-__device__ __forceinline__ void bwd_item(const StepArgs &a, int G, int v0) {
+__device__ __forceinline__ void bwd_round(const StepArgs &a, int G, int v0, int jb, int je) {
   constexpr int KB = KBOf<C>::value;
   const int g = threadIdx.x & (G - 1);
   const int v = v0 + threadIdx.x / G;
@@ -281,7 +322,6 @@ __device__ __forceinline__ void bwd_item(const StepArgs &a, int G, int v0) {
   for (int c = 0; c < C; ++c)
 #pragma unroll
     for (int q = 0; q < 4; ++q) { M[c][q] = 2.f * kNeg; acc[c][q] = 0.f; }
-  const int jb = a.ptr[v], je = a.ptr[v + 1];
   for (int j0 = jb; j0 < je; j0 += KB) {
     const int nb = min(KB, je - j0);
     int st[KB];
@@ -313,7 +353,7 @@ __device__ void setup_item(const BatchInst &I, int k) {
   const size_t pan = panel_of(I);
   float *bt_hi = I.b_hi + (size_t)(I.T - 2) * pan;
   lo_t *bt_lo = I.b_lo + (size_t)(I.T - 2) * pan;
-  const int v0 = k * I.npb, v1 = min(I.V, v0 + I.npb);
+  const int v0 = k * I.npi, v1 = min(I.V, v0 + I.npi);
   for (size_t e = (size_t)v0 * I.Lp + threadIdx.x; e < (size_t)v1 * I.Lp; e += kTickBlock) {
     I.a0_hi[e] = kNeg;
     I.a0_lo[e] = kLoZero;
@@ -424,93 +464,130 @@ __device__ void finalise(const BatchInst &I, BatchCtl *c, const Phase &ph, doubl
   c->ticks += 1;
   c->step = step;
   c->status = status;
-  __threadfence();
+}
+
+// Fetch-and-add with release (orders this thread's earlier writes, here the item's partial
+// sums, before the increment) and acquire (the last item then sees every item's partials).
+__device__ __forceinline__ unsigned int atomic_add_acq_rel(unsigned int *p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Warp 0 stages the header (slot, item, status, step) and the instance description of
+// item `it` into shared memory; w is the item's (slot, index) on every lane.
+__device__ __forceinline__ void stage_item(const TickArgs &ta, int2 w, int *hdr, BatchInst *si) {
+  const int lane = threadIdx.x & 31;
+  constexpr int kWords = (int)(sizeof(BatchInst) / 16);
+  static_assert(kWords <= 32, "one 16-byte word per lane");
+  if (lane < kWords)
+    reinterpret_cast<int4 *>(si)[lane] = __ldg(reinterpret_cast<const int4 *>(ta.inst + w.x) + lane);
+  if (lane == 0) {
+    const BatchCtl *c = ta.ctl + w.x;
+    hdr[0] = w.x;
+    hdr[1] = w.y;
+    hdr[2] = c->status;
+    hdr[3] = c->step;
+  }
 }
 
 }  // namespace
 
 __global__ void __launch_bounds__(kTickBlock, 2) k_batch_tick(const TickArgs ta) {
-  __shared__ int s_item, s_status, s_step, s_last;
+  __shared__ BatchInst s_inst[2];                  // current and next item's instance
+  __shared__ int s_hdr[2][4];
+  __shared__ int s_last;
   __shared__ double s_red[3 * (kTickBlock / 32)];
   __shared__ float2 s_w[kTickBlock][6];            // W of the in-states of each node (fwd)
   const int n = *ta.n_items;
-  for (;;) {
-    __syncthreads();                               // readers of the previous item are done
-    if (threadIdx.x == 0) {
-      const int it = (int)atomicAdd(ta.fetch, 1u);
-      s_item = it;
-      if (it < n) {
-        const BatchCtl *c = ta.ctl + ta.items[it].x;
-        s_status = c->status;
-        s_step = c->step;
-      }
-    }
-    __syncthreads();
-    const int it = s_item;
-    if (it >= n) break;
-    const int status = s_status;
-    if (status != kSlotRunning && status != kSlotFlows) continue;
-    const int2 w = ta.items[it];
-    const int k = w.y;
-    const BatchInst &I = ta.inst[w.x];
-    BatchCtl *c = ta.ctl + w.x;
-    const Phase ph = decode_phase(status, s_step, I.T);
-    const int G = I.G, C = I.C;
-    const int v0 = k * I.npb;
-    double r0 = 0.0, r1 = 0.0, r2 = 0.0;
-    switch (ph.kind) {
-      case kPhSetup:
-        setup_item(I, k);
-        break;
-      case kPhInitBnd:
-        bnd_item(bnd_of(I, true, 1), k, I.n_items, r0, r1, r2);
-        bnd_item(bnd_of(I, false, 1), k, I.n_items, r0, r1, r2);
-        break;
-      case kPhSrc:
-        bnd_item(bnd_of(I, true, 0), k, I.n_items, r0, r1, r2);
-        break;
-      case kPhSnk:
-        bnd_item(bnd_of(I, false, 0), k, I.n_items, r0, r1, r2);
-        break;
-      case kPhFwd:
-      case kPhFlowFwd: {
-        const StepArgs a = step_of(I, true, ph.t, ph.kind == kPhFwd ? 0 : 1);
-        if (C == 1) fwd_item<1>(a, G, v0, s_w, r0, r1);
-        else fwd_item<2>(a, G, v0, s_w, r0, r1);
-        break;
-      }
-      case kPhBwd: {
-        const StepArgs a = step_of(I, false, ph.t, 0);
-        if (C == 1) bwd_item<1>(a, G, v0);
-        else bwd_item<2>(a, G, v0);
-        break;
-      }
-      case kPhFlowBnd:
-        flow_bnd_item(I, k);
-        break;
-      default:
-        break;
-    }
-    block_sum3(r0, r1, r2, s_red);
-    if (threadIdx.x == 0) {
-      I.partials[3 * k] = r0;
-      I.partials[3 * k + 1] = r1;
-      I.partials[3 * k + 2] = r2;
-      __threadfence();
-      const unsigned prev = atomicAdd(&c->counter, 1u);
-      s_last = prev == (unsigned)(I.n_items - 1);
-    }
-    __syncthreads();
-    if (s_last) finalise(I, c, ph, s_red);
+  int it = blockIdx.x;                             // items it, it + grid, it + 2 grid, ...
+  if (it >= n) return;
+  if (threadIdx.x < 32) {
+    int2 w = make_int2(0, 0);
+    if (threadIdx.x == 0) w = ta.items[it];
+    w.x = __shfl_sync(0xffffffffu, w.x, 0);
+    w.y = __shfl_sync(0xffffffffu, w.y, 0);
+    stage_item(ta, w, s_hdr[0], &s_inst[0]);
   }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(ta.fetch + 1, 1u);
-    if (prev == gridDim.x - 1) {                   // every block has left the item loop
-      ta.fetch[0] = 0u;
-      ta.fetch[1] = 0u;
-      __threadfence();
+  __syncthreads();
+  int buf = 0;
+  for (;;) {
+    const int nxt = it + gridDim.x;
+    int2 wn = make_int2(0, 0);
+    if (threadIdx.x == 0 && nxt < n) wn = ta.items[nxt];   // used after this item's work
+    const int slot = s_hdr[buf][0], k = s_hdr[buf][1], status = s_hdr[buf][2];
+    const BatchInst &I = s_inst[buf];
+    const bool running = status == kSlotRunning || status == kSlotFlows;
+    const Phase ph = decode_phase(status, s_hdr[buf][3], I.T);
+    BatchCtl *c = ta.ctl + slot;
+    if (running) {
+      const int G = I.G, C = I.C;
+      double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+      switch (ph.kind) {
+        case kPhSetup:
+          setup_item(I, k);
+          break;
+        case kPhInitBnd:
+          bnd_item(bnd_of(I, true, 1), k, I.n_items, r0, r1, r2);
+          bnd_item(bnd_of(I, false, 1), k, I.n_items, r0, r1, r2);
+          break;
+        case kPhSrc:
+          bnd_item(bnd_of(I, true, 0), k, I.n_items, r0, r1, r2);
+          break;
+        case kPhSnk:
+          bnd_item(bnd_of(I, false, 0), k, I.n_items, r0, r1, r2);
+          break;
+        case kPhFwd:
+        case kPhFlowFwd:
+        case kPhBwd: {
+          const bool fwd = ph.kind != kPhBwd;
+          const StepArgs a = step_of(I, fwd, ph.t, ph.kind == kPhFlowFwd ? 1 : 0);
+          const int v_end = min(I.V, (k + 1) * I.npi);
+          const int nib = threadIdx.x / G;
+          int v0 = k * I.npi;
+          int vv = min(v0 + nib, I.V - 1);
+          int jb = a.ptr[vv], je = a.ptr[vv + 1];
+          for (; v0 < v_end; v0 += I.npb) {
+            // CSR range of this thread's node in the next round, loaded ahead
+            const int vn = min(v0 + I.npb + nib, I.V - 1);
+            int jbn = 0, jen = 0;
+            if (v0 + I.npb < v_end) { jbn = a.ptr[vn]; jen = a.ptr[vn + 1]; }
+            if (fwd) {
+              if (C == 1) fwd_round<1>(a, G, v0, jb, je, s_w, r0, r1);
+              else fwd_round<2>(a, G, v0, jb, je, s_w, r0, r1);
+            } else {
+              if (C == 1) bwd_round<1>(a, G, v0, jb, je);
+              else bwd_round<2>(a, G, v0, jb, je);
+            }
+            jb = jbn;
+            je = jen;
+          }
+          break;
+        }
+        case kPhFlowBnd:
+          flow_bnd_item(I, k);
+          break;
+        default:
+          break;
+      }
+      block_sum3(r0, r1, r2, s_red);
+      if (threadIdx.x == 0) {
+        I.partials[3 * k] = r0;
+        I.partials[3 * k + 1] = r1;
+        I.partials[3 * k + 2] = r2;
+        s_last = atomic_add_acq_rel(&c->counter, 1u) == (unsigned)(I.n_items - 1);
+      }
     }
+    if (threadIdx.x < 32 && nxt < n) {
+      wn.x = __shfl_sync(0xffffffffu, wn.x, 0);
+      wn.y = __shfl_sync(0xffffffffu, wn.y, 0);
+      stage_item(ta, wn, s_hdr[buf ^ 1], &s_inst[buf ^ 1]);
+    }
+    __syncthreads();
+    if (running && s_last) finalise(I, c, ph, s_red);
+    if (nxt >= n) break;
+    it = nxt;
+    buf ^= 1;
   }
 }
 

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -91,7 +92,28 @@ struct CreateOpts {
   int G = 0, C = 0;          // forced mapping (member only): G threads per node, C chunks of 4
 };
 
+// Host arrays of a problem between its host build and its upload.
+struct HostArrays {
+  std::vector<int> in_ptr, out_ptr, in_state, in_nbr, out_state, out_nbr, st_inpos, st_outpos, in_outpos;
+  std::vector<float> kl_hi, kl_lo, logd_hi, logd_lo, in_kl_hi, in_kl_lo, in_logd_hi, in_logd_lo, klc_hi;
+  std::vector<double> cap, in_cap;
+  std::vector<ots::lo_t> klc_lo;
+};
+
+// create_problem_impl = build_problem_host (no CUDA call; may run on any thread) followed by
+// build_problem_device (allocation, uploads and initial duals on p->stream).
+ots_status build_problem_host(const ots_problem_desc *d, const CreateOpts &co, ots_problem **out);
+ots_status build_problem_device(ots_problem *p);
 ots_status create_problem_impl(const ots_problem_desc *d, const CreateOpts &co, ots_problem **out);
+
+// Batch internals used by the server (ots_batch.cu).
+struct Pool;
+Pool *batch_pool(ots_batch *b);
+void *pool_alloc_cb(size_t bytes, void *ctx);   // ots_alloc_fn / ots_free_fn over a Pool
+void pool_free_cb(void *p, void *ctx);
+ots_status batch_prepare(ots_batch *b, const ots_problem_desc *desc, cudaStream_t upload_stream, ots_problem **out);
+ots_status batch_admit(ots_batch *b, ots_problem *p, const ots_solve_opts *opts, int32_t *id);
+int batch_free_slots(const ots_batch *b);
 
 }  // namespace ots_host
 
@@ -113,6 +135,7 @@ struct ots_problem {
   int pgrid_fwd = 0, pgrid_bwd = 0;            // grids of the pipelined persistent kernels (0 = not used)
   bool pc = false;
   bool member = false;                         // lives in a batch (see CreateOpts)
+  std::unique_ptr<ots_host::HostArrays> host;  // between the host build and the upload
 
   std::vector<int> tail, head;
   ots_host::Boundary src, snk;

@@ -326,6 +326,53 @@ __device__ __forceinline__ void boundary_segment(const BndArgs &b, int sidx, dou
   b.out_lo[o] = ol;
 }
 
+// Capacity update of one in-state from its column log-sum-exp, with the per-state inputs
+// loaded ahead by the caller (same arithmetic as update_state): W_t of the state (win in
+// flows mode), the new log2 u_t, the flow P_t (flows mode), and the excess and dual terms.
+__device__ __forceinline__ void update_meta(int mode, const QScale &qs, float cm, float cs, float klh, float kll,
+                                            float ldh, float ldl, double cap, double lu_old, float win_hi,
+                                            float win_lo, float &w_hi, float &w_lo, double &lu_new, double &flow,
+                                            double &viol, double &dual) {
+  float col_hi = kNeg, col_lo = 0.f;
+  if (cm > kNegThresh && cs > 0.f) two_sum(cm, lg2(cs), col_hi, col_lo);
+  if (col_hi > kNegThresh) {
+    float s, e;
+    two_sum(col_hi, klh, s, e);
+    col_hi = s;
+    col_lo += e + kll;
+  }
+  if (mode != 0) {
+    w_hi = win_hi;
+    w_lo = win_lo;
+    flow = col_hi > kNegThresh && w_hi > kNegThresh ? exp2(lu_old + (double)col_hi + (double)col_lo) : 0.0;
+    lu_new = lu_old;
+    return;
+  }
+  float lu_hi = 0.f, lu_lo = 0.f;
+  if (isfinite(cap) && col_hi > kNegThresh) {
+    if (ldh < kNegThresh) {
+      lu_hi = kNeg;
+    } else {
+      float s1, e1, s2, e2;
+      two_sum(ldh, -col_hi, s1, e1);
+      e1 += ldl - col_lo;
+      two_sum(s1, e1, s2, e2);
+      if (s2 < 0.f) { lu_hi = s2; lu_lo = e2; }
+    }
+  }
+  make_w(klh, kll, lu_hi, lu_lo, qs, w_hi, w_lo);
+  if (col_hi > kNegThresh && isfinite(cap)) {
+    const float qv = (float)lu_old + col_hi - ldh;
+    if (qv > -1e-3f) {
+      const double p_old = exp2(lu_old + (double)col_hi + (double)col_lo);
+      if (p_old > cap) viol += p_old - cap;
+    }
+  }
+  if (col_hi != col_hi || col_lo != col_lo) viol = __longlong_as_double(0x7ff8000000000000LL);
+  lu_new = lu_hi < kNegThresh ? -1e30 : (double)lu_hi + (double)lu_lo;
+  if (isfinite(cap) && cap > 0.0) dual += cap * lu_new;
+}
+
 }  // namespace
 
 }  // namespace ots

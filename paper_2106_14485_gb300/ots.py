@@ -75,12 +75,26 @@ class BatchStats(ctypes.Structure):
                 ("items", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
 
 
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("batch", BatchDesc), ("builder_threads", ctypes.c_int32), ("max_queued", ctypes.c_int32),
+                ("mode", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("queued", ctypes.c_int32), ("building", ctypes.c_int32), ("resident", ctypes.c_int32),
+                ("large_running", ctypes.c_int32), ("pool_bytes", ctypes.c_int64), ("pool_used", ctypes.c_int64),
+                ("batch_launches", ctypes.c_int64), ("batch_ticks", ctypes.c_int64)]
+
+
 EXPORTED = ["ots_default_solve_opts", "ots_create_problem", "ots_sinkhorn_solve", "ots_iterate", "ots_get_flows",
             "ots_get_commodity_flows", "ots_get_commodity_flows_noalloc", "ots_get_duals", "ots_set_duals", "ots_problem_info", "ots_last_pass_timing",
             "ots_problem_stream", "ots_destroy_problem", "ots_status_string", "ots_last_error",
             "ots_default_batch_desc", "ots_batch_create", "ots_batch_add", "ots_batch_run", "ots_batch_status",
             "ots_batch_get_flows", "ots_batch_get_duals", "ots_batch_remove", "ots_batch_info", "ots_batch_mapping",
-            "ots_batch_autotune", "ots_batch_destroy"]
+            "ots_batch_autotune", "ots_batch_destroy",
+            "ots_default_server_desc", "ots_server_create", "ots_server_submit", "ots_server_poll", "ots_server_wait",
+            "ots_server_get_flows", "ots_server_timing", "ots_server_release", "ots_server_info", "ots_server_destroy"]
 
 _lib = None
 
@@ -127,6 +141,22 @@ def load_library(path: str = LIB_PATH):
     lib.ots_batch_autotune.argtypes = [P, ctypes.c_char_p]
     lib.ots_batch_destroy.argtypes = [P]
     lib.ots_batch_destroy.restype = None
+    lib.ots_default_server_desc.argtypes = [ctypes.POINTER(ServerDesc)]
+    lib.ots_server_create.argtypes = [ctypes.POINTER(ServerDesc), ctypes.POINTER(P)]
+    lib.ots_server_submit.argtypes = [P, ctypes.POINTER(ProblemDesc), ctypes.POINTER(SolveOpts),
+                                      ctypes.POINTER(ctypes.c_int64)]
+    lib.ots_server_poll.argtypes = [P, ctypes.c_int64, ctypes.POINTER(SolveReport)]
+    lib.ots_server_wait.argtypes = [P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(SolveReport)]
+    lib.ots_server_get_flows.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _f64p]
+    lib.ots_server_timing.argtypes = [P, ctypes.c_int64, _f64p]
+    lib.ots_server_release.argtypes = [P, ctypes.c_int64]
+    lib.ots_server_info.argtypes = [P, ctypes.POINTER(ServerStats)]
+    lib.ots_server_destroy.argtypes = [P]
+    lib.ots_server_destroy.restype = None
+    for name in ("ots_default_server_desc", "ots_server_create", "ots_server_submit", "ots_server_poll",
+                 "ots_server_wait", "ots_server_get_flows", "ots_server_timing", "ots_server_release",
+                 "ots_server_info"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("ots_default_batch_desc", "ots_batch_create", "ots_batch_add", "ots_batch_run", "ots_batch_status",
                  "ots_batch_get_flows", "ots_batch_get_duals", "ots_batch_remove", "ots_batch_info",
                  "ots_batch_mapping", "ots_batch_autotune"):
@@ -456,3 +486,104 @@ def ots_batch_destroy(b: Batch) -> None:
     if b.ptr:
         load_library().ots_batch_destroy(b.ptr)
         b.ptr = None
+
+
+# ---------------------------------------------------------------------------------------
+# server
+# ---------------------------------------------------------------------------------------
+class Server:
+    """Owns an ``ots_server*`` and the shapes of the requests submitted to it."""
+
+    def __init__(self, ptr, keep):
+        self.ptr = ptr
+        self._keep = keep
+        self.shapes = {}   # ticket -> (n_states, T)
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                ots_server_destroy(self)
+            except Exception:
+                pass
+
+
+def ots_server_create(device: int = 0, pool_bytes: int = 4 << 30, max_instances: int = 256, ticks_per_launch: int = 8,
+                      builder_threads: int = 2, max_queued: int = 0, mode: int = 0, allocator: str = "torch") -> Server:
+    """mode 0: continuous batching; mode 1: one request at a time with the single-instance solver."""
+    lib = load_library()
+    d = ServerDesc()
+    _check(lib.ots_default_server_desc(ctypes.byref(d)))
+    d.batch.device, d.batch.pool_bytes, d.batch.max_instances = int(device), int(pool_bytes), int(max_instances)
+    d.batch.ticks_per_launch = int(ticks_per_launch)
+    d.builder_threads, d.max_queued, d.mode = int(builder_threads), int(max_queued), int(mode)
+    keep = []
+    if allocator == "torch":
+        a, f = _torch_allocator(int(device))
+        d.batch.alloc, d.batch.free_fn = a, f
+        keep.append((a, f))
+    elif allocator != "cuda":
+        raise ValueError("allocator must be 'torch' or 'cuda'")
+    out = ctypes.c_void_p()
+    _check(lib.ots_server_create(ctypes.byref(d), ctypes.byref(out)))
+    return Server(out, keep)
+
+
+def ots_server_submit(s: Server, inst, tol: float = 1e-6, max_iters: int = 100000, timeout_ms: float = 0.0,
+                      check_every: int = 1) -> int:
+    d, arr = _problem_desc(inst)
+    o = ots_default_solve_opts()
+    o.tol, o.max_iters, o.timeout_ms, o.check_every = tol, max_iters, timeout_ms, check_every
+    t = ctypes.c_int64(0)
+    _check(load_library().ots_server_submit(s.ptr, ctypes.byref(d), ctypes.byref(o), ctypes.byref(t)))
+    s.shapes[t.value] = (int(inst.n_nodes) + d.n_edges, d.T)
+    return t.value
+
+
+def _report(code, r):
+    out = r.as_dict()
+    out["status"] = code
+    return out
+
+
+def ots_server_poll(s: Server, ticket: int) -> dict:
+    r = SolveReport()
+    code = load_library().ots_server_poll(s.ptr, int(ticket), ctypes.byref(r))
+    return _report(code, r)
+
+
+def ots_server_wait(s: Server, ticket: int, timeout_ms: float = 0.0) -> dict:
+    r = SolveReport()
+    code = load_library().ots_server_wait(s.ptr, int(ticket), float(timeout_ms), ctypes.byref(r))
+    return _report(code, r)
+
+
+def ots_server_get_flows(s: Server, ticket: int, t_begin: int = 1, t_end: int | None = None) -> np.ndarray:
+    S, T = s.shapes[ticket]
+    t_end = T + 1 if t_end is None else t_end
+    out = np.empty((t_end - t_begin, S), np.float64)
+    _check(load_library().ots_server_get_flows(s.ptr, int(ticket), int(t_begin), int(t_end),
+                                               _ptr(out, ctypes.c_double)))
+    return out
+
+
+def ots_server_timing(s: Server, ticket: int) -> dict:
+    ms = np.zeros(3, np.float64)
+    _check(load_library().ots_server_timing(s.ptr, int(ticket), _ptr(ms, ctypes.c_double)))
+    return {"wait_ms": ms[0], "run_ms": ms[1], "total_ms": ms[2]}
+
+
+def ots_server_release(s: Server, ticket: int) -> None:
+    _check(load_library().ots_server_release(s.ptr, int(ticket)))
+    s.shapes.pop(ticket, None)
+
+
+def ots_server_info(s: Server) -> dict:
+    st = ServerStats()
+    _check(load_library().ots_server_info(s.ptr, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+def ots_server_destroy(s: Server) -> None:
+    if s.ptr:
+        load_library().ots_server_destroy(s.ptr)
+        s.ptr = None

@@ -58,6 +58,9 @@ int main(void) {
          offsetof(ots_batch_desc, alloc_ctx));
   printf("%zu %zu\n", sizeof(ots_batch_stats), offsetof(ots_batch_stats, d2h_bytes));
   printf("%d\n", (int)OTS_PENDING);
+  printf("%zu %zu %zu\n", sizeof(ots_server_desc), offsetof(ots_server_desc, mode),
+         sizeof(ots_server_stats));
+  printf("%zu\n", offsetof(ots_server_stats, batch_ticks));
   return 0;
 }
 '''
@@ -77,6 +80,9 @@ int main(void) {
     assert vals[8] == ctypes.sizeof(B) and vals[9] == B.ticks_per_launch.offset and vals[10] == B.alloc_ctx.offset
     assert vals[11] == ctypes.sizeof(BS) and vals[12] == BS.d2h_bytes.offset
     assert vals[13] == ots.OTS_PENDING
+    SD, SS = ots.ServerDesc, ots.ServerStats
+    assert vals[14] == ctypes.sizeof(SD) and vals[15] == SD.mode.offset and vals[16] == ctypes.sizeof(SS)
+    assert vals[17] == SS.batch_ticks.offset
 
 
 def test_oracle_is_not_imported_by_the_product():
