@@ -364,7 +364,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 struct TmaItem {
   int v, j0, nb;
 };
-
 __device__ __forceinline__ bool item_first(const int *ptr, int V, int KB, TmaItem &it) {
   it.v = blockIdx.x;
   if (it.v >= V) return false;
@@ -372,7 +371,6 @@ __device__ __forceinline__ bool item_first(const int *ptr, int V, int KB, TmaIte
   it.nb = min(KB, ptr[it.v + 1] - it.j0);
   return true;
 }
-
 __device__ __forceinline__ bool item_next(const int *ptr, int V, int KB, TmaItem &it) {
   const int je = ptr[it.v + 1];
   if (it.j0 + it.nb < je) {
@@ -386,6 +384,7 @@ __device__ __forceinline__ bool item_next(const int *ptr, int V, int KB, TmaItem
   it.nb = min(KB, ptr[it.v + 1] - it.j0);
   return true;
 }
+
 
 // Producer (one thread): the rows of `it` into stage (hi, lo): forward puts B_{t+1}[v] in row
 // 0 and A_{t-1}[tail j] in rows 1..nb; backward puts B_{t+1}[head j] in rows 0..nb-1.
@@ -428,6 +427,7 @@ struct FwdMeta {
   float kl_hi[kBatchTma], kl_lo[kBatchTma], logd_hi[kBatchTma], logd_lo[kBatchTma];
   float w_hi[kBatchTma], w_lo[kBatchTma];      // flows mode: the stored weights
   double cap[kBatchTma], lu_old[kBatchTma];
+  int fin[kBatchTma];                           // capacity finite
 };
 
 struct BwdMeta {
@@ -511,6 +511,7 @@ __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, flo
         m.kl_hi[lane] = lm.kl_hi; m.kl_lo[lane] = lm.kl_lo;
         m.logd_hi[lane] = lm.logd_hi; m.logd_lo[lane] = lm.logd_lo;
         m.cap[lane] = lm.cap; m.lu_old[lane] = lm.lu_old;
+        m.fin[lane] = isfinite(lm.cap) ? 1 : 0;
         m.w_hi[lane] = lm.w_hi; m.w_lo[lane] = lm.w_lo;
       } else {
         m.w_hi[lane] = lm.w_hi; m.w_lo[lane] = lm.w_lo;
@@ -679,10 +680,14 @@ __global__ void __launch_bounds__(G + 32) k_forward_tma(const StepArgs a) {
         sk_ = xb[(2 * lane + 1) * NW];
 #pragma unroll
         for (int w = 1; w < NW; ++w) lse_merge(mk, sk_, xb[(2 * lane) * NW + w], xb[(2 * lane + 1) * NW + w]);
-        double lu_new = 0.0, flow = 0.0, v0 = 0.0, v1 = 0.0;
-        update_meta(a.mode, a.qs, mk, sk_, m.kl_hi[lane], m.kl_lo[lane], m.logd_hi[lane], m.logd_lo[lane],
-                    m.cap[lane], m.lu_old[lane], m.w_hi[lane], m.w_lo[lane], mh, ml, lu_new, flow, v0, v1);
+        // every warp derives W (FP32); warp 0 alone does the FP64 part and the stores
+        float col_hi, col_lo, lu_hi, lu_lo;
+        update_w(a.mode, a.qs, mk, sk_, m.kl_hi[lane], m.kl_lo[lane], m.logd_hi[lane], m.logd_lo[lane],
+                 m.fin[lane] != 0, m.w_hi[lane], m.w_lo[lane], mh, ml, col_hi, col_lo, lu_hi, lu_lo);
         if (wid == 0) {
+          double lu_new = 0.0, flow = 0.0, v0 = 0.0, v1 = 0.0;
+          update_stats(a.mode, col_hi, col_lo, lu_hi, lu_lo, m.logd_hi[lane], m.logd_lo[lane], mh, m.cap[lane],
+                       m.lu_old[lane], lu_new, flow, v0, v1);
           const int st = m.st[lane];
           if (a.mode == 0) {
             viol += v0;

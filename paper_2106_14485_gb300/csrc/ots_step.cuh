@@ -234,6 +234,36 @@ __device__ __forceinline__ void make_w(float kl_hi, float kl_lo, float lu_hi, fl
   w_lo = (s - w_hi) + e;
 }
 
+// Adds the capacity excess (P_old - d)_+ of one state to viol, where P_old = 2^(log2 u_old +
+// col) is the column sum under the old u_t and d = 2^(ldh + ldl) its capacity (finite; d = 0
+// is the sentinel ldh = log2 0).  The ratio P_old / d = 2^e is formed in FP64 (its terms
+// cancel) and only near or above capacity; for 0 < e <= 32 the excess d (2^e - 1) is
+// evaluated in FP32: exp2 for e > 0.5, else the Taylor series of exp(x) - 1 at x = e ln 2
+// (|x| <= 0.35, truncation below 2e-7 relative).
+__device__ __forceinline__ void add_excess(double cap, double lu_old, float col_hi, float col_lo, float ldh, float ldl,
+                                           double &viol) {
+  if (ldh < kNegThresh) {                         // d = 0: every unit of flow is excess
+    if (lu_old > -1e29) viol += exp2(lu_old + (double)col_hi + (double)col_lo);
+    return;
+  }
+  const float qv = (float)lu_old + col_hi - ldh;
+  if (!(qv > -1e-3f)) return;
+  const float e = (float)((lu_old - (double)ldh) + ((double)col_hi + (double)(col_lo - ldl)));
+  if (!(e > 0.f)) return;
+  if (e > 32.f) {                                 // far above capacity (first passes): FP64
+    viol += exp2(lu_old + (double)col_hi + (double)col_lo) - cap;
+    return;
+  }
+  float r;
+  if (e > 0.5f) {
+    r = ex2(e) - 1.f;
+  } else {
+    const float x = e * 0.69314718f;
+    r = x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 720.f, 1.f / 120.f), 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
+  }
+  viol += cap * (double)r;
+}
+
 // Capacity update of one state from its column log-sum-exp (cm + log2 cs) (Algorithm 2,
 // Corollary 7): W_t for the aggregation and, when `write`, the stored log2 u_t, W_t, the
 // excess (P_t - d)_+ with the old u_t and the dual term d log2 u_t (Theorem 3).  In flows
@@ -275,14 +305,7 @@ __device__ __forceinline__ void update_state(const StepArgs &a, int sk, float cm
   make_w(klh, kll, lu_hi, lu_lo, a.qs, w_hi, w_lo);
   if (!write) return;
   const double lu_old = a.logu_t[sk];
-  if (col_hi > kNegThresh && isfinite(cap)) {
-    // excess with the old u_t; exact FP64 only near or above capacity
-    const float qv = (float)lu_old + col_hi - a.logd_hi[sk];
-    if (qv > -1e-3f) {
-      const double p_old = exp2(lu_old + (double)col_hi + (double)col_lo);
-      if (p_old > cap) viol += p_old - cap;
-    }
-  }
+  if (col_hi > kNegThresh && isfinite(cap)) add_excess(cap, lu_old, col_hi, col_lo, a.logd_hi[sk], a.logd_lo[sk], viol);
   if (col_hi != col_hi || col_lo != col_lo) viol = __longlong_as_double(0x7ff8000000000000LL);  // NaN: reported
   const double lu_new = lu_hi < kNegThresh ? -1e30 : (double)lu_hi + (double)lu_lo;
   if (isfinite(cap) && cap > 0.0) dual += cap * lu_new;
@@ -326,14 +349,17 @@ __device__ __forceinline__ void boundary_segment(const BndArgs &b, int sidx, dou
   b.out_lo[o] = ol;
 }
 
-// Capacity update of one in-state from its column log-sum-exp, with the per-state inputs
-// loaded ahead by the caller (same arithmetic as update_state): W_t of the state (win in
-// flows mode), the new log2 u_t, the flow P_t (flows mode), and the excess and dual terms.
-__device__ __forceinline__ void update_meta(int mode, const QScale &qs, float cm, float cs, float klh, float kll,
-                                            float ldh, float ldl, double cap, double lu_old, float win_hi,
-                                            float win_lo, float &w_hi, float &w_lo, double &lu_new, double &flow,
-                                            double &viol, double &dual) {
-  float col_hi = kNeg, col_lo = 0.f;
+// Capacity update of one in-state from its column log-sum-exp (cm + log2 cs), FP32 part:
+// the column sum col = log2 (hatPsi_t .* Psi_t .* K_L)^T 1 as a float-float (col_hi, col_lo),
+// the new log2 u_t = min(log2 d - col, 0) as a float-float (lu_hi, lu_lo; cap_finite = 0 for
+// d = inf), and W_t = log2 K_L + log2 u_t (w_hi, w_lo).  In flows mode (mode != 0) W_t is the
+// stored win and u_t is not changed.
+__device__ __forceinline__ void update_w(int mode, const QScale &qs, float cm, float cs, float klh, float kll,
+                                         float ldh, float ldl, bool cap_finite, float win_hi, float win_lo,
+                                         float &w_hi, float &w_lo, float &col_hi, float &col_lo, float &lu_hi,
+                                         float &lu_lo) {
+  col_hi = kNeg;
+  col_lo = 0.f;
   if (cm > kNegThresh && cs > 0.f) two_sum(cm, lg2(cs), col_hi, col_lo);
   if (col_hi > kNegThresh) {
     float s, e;
@@ -341,15 +367,14 @@ __device__ __forceinline__ void update_meta(int mode, const QScale &qs, float cm
     col_hi = s;
     col_lo += e + kll;
   }
+  lu_hi = 0.f;
+  lu_lo = 0.f;
   if (mode != 0) {
     w_hi = win_hi;
     w_lo = win_lo;
-    flow = col_hi > kNegThresh && w_hi > kNegThresh ? exp2(lu_old + (double)col_hi + (double)col_lo) : 0.0;
-    lu_new = lu_old;
     return;
   }
-  float lu_hi = 0.f, lu_lo = 0.f;
-  if (isfinite(cap) && col_hi > kNegThresh) {
+  if (cap_finite && col_hi > kNegThresh) {
     if (ldh < kNegThresh) {
       lu_hi = kNeg;
     } else {
@@ -361,16 +386,35 @@ __device__ __forceinline__ void update_meta(int mode, const QScale &qs, float cm
     }
   }
   make_w(klh, kll, lu_hi, lu_lo, qs, w_hi, w_lo);
-  if (col_hi > kNegThresh && isfinite(cap)) {
-    const float qv = (float)lu_old + col_hi - ldh;
-    if (qv > -1e-3f) {
-      const double p_old = exp2(lu_old + (double)col_hi + (double)col_lo);
-      if (p_old > cap) viol += p_old - cap;
-    }
+}
+
+// FP64 part of the same update (one thread per state): the new log2 u_t, the flow P_t in
+// flows mode, the excess (P_t - d)_+ with the old u_t (exact FP64 only near or above
+// capacity) and the dual term d log2 u_t of Theorem 3.
+__device__ __forceinline__ void update_stats(int mode, float col_hi, float col_lo, float lu_hi, float lu_lo, float ldh,
+                                             float ldl, float w_hi, double cap, double lu_old, double &lu_new,
+                                             double &flow, double &viol, double &dual) {
+  if (mode != 0) {
+    flow = col_hi > kNegThresh && w_hi > kNegThresh ? exp2(lu_old + (double)col_hi + (double)col_lo) : 0.0;
+    lu_new = lu_old;
+    return;
   }
+  if (col_hi > kNegThresh && isfinite(cap)) add_excess(cap, lu_old, col_hi, col_lo, ldh, ldl, viol);
   if (col_hi != col_hi || col_lo != col_lo) viol = __longlong_as_double(0x7ff8000000000000LL);
   lu_new = lu_hi < kNegThresh ? -1e30 : (double)lu_hi + (double)lu_lo;
   if (isfinite(cap) && cap > 0.0) dual += cap * lu_new;
+}
+
+// Both parts at once (same arithmetic as update_state, with the per-state inputs loaded
+// ahead by the caller).
+__device__ __forceinline__ void update_meta(int mode, const QScale &qs, float cm, float cs, float klh, float kll,
+                                            float ldh, float ldl, double cap, double lu_old, float win_hi,
+                                            float win_lo, float &w_hi, float &w_lo, double &lu_new, double &flow,
+                                            double &viol, double &dual) {
+  float col_hi, col_lo, lu_hi, lu_lo;
+  update_w(mode, qs, cm, cs, klh, kll, ldh, ldl, isfinite(cap), win_hi, win_lo, w_hi, w_lo, col_hi, col_lo, lu_hi,
+           lu_lo);
+  update_stats(mode, col_hi, col_lo, lu_hi, lu_lo, ldh, ldl, w_hi, cap, lu_old, lu_new, flow, viol, dual);
 }
 
 }  // namespace
