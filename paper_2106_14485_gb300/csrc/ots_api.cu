@@ -99,7 +99,7 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   a.klc_hi = p->d_klc_hi; a.klc_lo = p->d_klc_lo;
   a.logd_hi = p->d_logd_hi; a.logd_lo = p->d_logd_lo;
   a.cap = p->d_cap;
-  a.logu_t = p->d_logu + (size_t)t * p->S;
+  a.lu_t = p->d_logu + (size_t)t * p->S;
   a.w_hi_t = p->d_w_hi + (size_t)t * p->S;
   a.w_lo_t = p->d_w_lo + (size_t)t * p->S;
   a.flow_t = p->d_flow + (size_t)t * p->S;
@@ -108,7 +108,7 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   a.in_kl_hi = p->d_in_kl_hi; a.in_kl_lo = p->d_in_kl_lo;
   a.in_logd_hi = p->d_in_logd_hi; a.in_logd_lo = p->d_in_logd_lo;
   a.in_cap = p->d_in_cap; a.in_outpos = p->d_in_outpos;
-  a.logu_in_t = p->d_logu_in + (size_t)t * p->S;
+  a.lu_in_t = p->d_logu_in + (size_t)t * p->S;
   a.wout_hi_t = p->d_wout_hi + (size_t)t * p->S;
   a.wout_lo_t = p->d_wout_lo + (size_t)t * p->S;
   a.partials = p->d_partials;
@@ -567,12 +567,18 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   for (int k = 0; k < p->S; ++k) { st_inpos[in_state[k]] = k; st_outpos[out_state[k]] = k; }
   for (int k = 0; k < p->S; ++k) in_outpos[k] = st_outpos[in_state[k]];
   std::vector<float> in_kl_hi(p->S), in_kl_lo(p->S), in_logd_hi(p->S), in_logd_lo(p->S);
-  std::vector<double> in_cap(p->S);
+  std::vector<float2> in_cap(p->S), cap2(p->S);
+  auto split_cap = [](double dd) {
+    if (!(dd < 3.0e38)) return make_float2(INFINITY, 0.f);        // no capacity (or beyond FP32)
+    const float h = (float)dd;
+    return make_float2(h, (float)(dd - (double)h));
+  };
+  for (int k = 0; k < p->S; ++k) cap2[k] = split_cap(cap[k]);
   for (int k = 0; k < p->S; ++k) {
     const int st = in_state[k];
     in_kl_hi[k] = kl_hi[st]; in_kl_lo[k] = kl_lo[st];
     in_logd_hi[k] = logd_hi[st]; in_logd_lo[k] = logd_lo[st];
-    in_cap[k] = cap[st];
+    in_cap[k] = cap2[st];
   }
 
   // ---- boundary triples ----
@@ -620,8 +626,8 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   H.in_logd_hi = std::move(in_logd_hi);
   H.in_logd_lo = std::move(in_logd_lo);
   H.klc_hi = std::move(klc_hi);
-  H.cap = std::move(cap);
   H.in_cap = std::move(in_cap);
+  H.cap = std::move(cap2);
   H.klc_lo = std::move(klc_lo);
   *out = p;
   return OTS_OK;
@@ -684,15 +690,15 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   size_t o_out_ptr = cv.take<int>(V + 1), o_out_state = cv.take<int>(S), o_out_nbr = cv.take<int>(S);
   size_t o_tail = cv.take<int>(S), o_head = cv.take<int>(S);
   size_t o_kl_hi = cv.take<float>(S), o_kl_lo = cv.take<float>(S), o_ld_hi = cv.take<float>(S), o_ld_lo = cv.take<float>(S);
-  size_t o_cap = cv.take<double>(S);
+  size_t o_cap = cv.take<float2>(S);
   size_t o_klc_hi = p->pc ? cv.take<float>(S * p->Lp) : 0, o_klc_lo = p->pc ? cv.take<lo_t>(S * p->Lp) : 0;
   size_t o_w_hi = cv.take<float>((T + 1) * S), o_w_lo = cv.take<float>((T + 1) * S);
-  size_t o_logu = cv.take<double>((T + 1) * S), o_flow = cv.take<double>((T + 1) * S);
+  size_t o_logu = cv.take<float2>((T + 1) * S), o_flow = cv.take<double>((T + 1) * S);
   const size_t Sc = csr_copies ? S : 0;
   size_t o_st_inpos = cv.take<int>(Sc), o_st_outpos = cv.take<int>(Sc), o_in_outpos = cv.take<int>(Sc);
   size_t o_in_kl_hi = cv.take<float>(Sc), o_in_kl_lo = cv.take<float>(Sc), o_in_ld_hi = cv.take<float>(Sc),
-         o_in_ld_lo = cv.take<float>(Sc), o_in_cap = cv.take<double>(Sc);
-  size_t o_logu_in = cv.take<double>((T + 1) * Sc), o_wout_hi = cv.take<float>((T + 1) * Sc),
+         o_in_ld_lo = cv.take<float>(Sc), o_in_cap = cv.take<float2>(Sc);
+  size_t o_logu_in = cv.take<float2>((T + 1) * Sc), o_wout_hi = cv.take<float>((T + 1) * Sc),
          o_wout_lo = cv.take<float>((T + 1) * Sc);
   size_t o_a_hi[3], o_a_lo[3];
   for (int k = 0; k < 3; ++k) { o_a_hi[k] = cv.take<float>(panel); o_a_lo[k] = cv.take<lo_t>(panel); }
@@ -718,16 +724,16 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   p->d_tail = (int *)at(o_tail); p->d_head = (int *)at(o_head);
   p->d_kl_hi = (float *)at(o_kl_hi); p->d_kl_lo = (float *)at(o_kl_lo);
   p->d_logd_hi = (float *)at(o_ld_hi); p->d_logd_lo = (float *)at(o_ld_lo);
-  p->d_cap = (double *)at(o_cap);
+  p->d_cap = (float2 *)at(o_cap);
   if (p->pc) { p->d_klc_hi = (float *)at(o_klc_hi); p->d_klc_lo = (lo_t *)at(o_klc_lo); }
   p->d_w_hi = (float *)at(o_w_hi); p->d_w_lo = (float *)at(o_w_lo);
-  p->d_logu = (double *)at(o_logu); p->d_flow = (double *)at(o_flow);
+  p->d_logu = (float2 *)at(o_logu); p->d_flow = (double *)at(o_flow);
   if (csr_copies) {
     p->d_st_inpos = (int *)at(o_st_inpos); p->d_st_outpos = (int *)at(o_st_outpos); p->d_in_outpos = (int *)at(o_in_outpos);
     p->d_in_kl_hi = (float *)at(o_in_kl_hi); p->d_in_kl_lo = (float *)at(o_in_kl_lo);
     p->d_in_logd_hi = (float *)at(o_in_ld_hi); p->d_in_logd_lo = (float *)at(o_in_ld_lo);
-    p->d_in_cap = (double *)at(o_in_cap);
-    p->d_logu_in = (double *)at(o_logu_in); p->d_wout_hi = (float *)at(o_wout_hi); p->d_wout_lo = (float *)at(o_wout_lo);
+    p->d_in_cap = (float2 *)at(o_in_cap);
+    p->d_logu_in = (float2 *)at(o_logu_in); p->d_wout_hi = (float *)at(o_wout_hi); p->d_wout_lo = (float *)at(o_wout_lo);
   }
   for (int k = 0; k < 3; ++k) { p->d_a_hi[k] = (float *)at(o_a_hi[k]); p->d_a_lo[k] = (lo_t *)at(o_a_lo[k]); }
   p->d_b_hi = (float *)at(o_b_hi); p->d_b_lo = (lo_t *)at(o_b_lo);
@@ -775,8 +781,8 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
       cudaMemsetAsync(p->d_flow, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess)
     return bail(fail(OTS_ERR_CUDA, "memset failed"));
   // logu rows outside 2..T-1 stay 0; W rows likewise unused
-  if (cudaMemsetAsync(p->d_logu, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess ||
-      cudaMemsetAsync(p->d_logu_in, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess)
+  if (cudaMemsetAsync(p->d_logu, 0, sizeof(float2) * (T + 1) * S, p->stream) != cudaSuccess ||
+      cudaMemsetAsync(p->d_logu_in, 0, sizeof(float2) * (T + 1) * S, p->stream) != cudaSuccess)
     return bail(fail(OTS_ERR_CUDA, "memset failed"));
   // boundary panels start at log 0 everywhere; only the support entries are rewritten
   p->kernels_launched += 2;
@@ -1116,16 +1122,18 @@ ots_status ots_get_duals(ots_problem *p, double *log_u, double *log_U01, double 
   if (!p) return fail(OTS_ERR_INVALID_ARG, "problem is NULL");
   DeviceGuard guard(p->dev);
   const size_t S = p->S;
-  std::vector<double> lu, su(p->src.n), zu(p->snk.n);
+  std::vector<float2> lu;
+  std::vector<double> su(p->src.n), zu(p->snk.n);
   if (log_u) {
     lu.resize((size_t)(p->T - 2) * S);
-    OTS_CUDA(cudaMemcpyAsync(lu.data(), p->d_logu + 2 * S, sizeof(double) * lu.size(), cudaMemcpyDeviceToHost, p->stream));
+    OTS_CUDA(cudaMemcpyAsync(lu.data(), p->d_logu + 2 * S, sizeof(float2) * lu.size(), cudaMemcpyDeviceToHost, p->stream));
   }
   if (p->src.n) OTS_CUDA(cudaMemcpyAsync(su.data(), p->src.d_tri_logU, sizeof(double) * p->src.n, cudaMemcpyDeviceToHost, p->stream));
   if (p->snk.n) OTS_CUDA(cudaMemcpyAsync(zu.data(), p->snk.d_tri_logU, sizeof(double) * p->snk.n, cudaMemcpyDeviceToHost, p->stream));
   OTS_CUDA(cudaStreamSynchronize(p->stream));
   if (log_u)
-    for (size_t k = 0; k < lu.size(); ++k) log_u[k] = lu[k] < -1e29 ? -INFINITY : lu[k] * kLn2;
+    for (size_t k = 0; k < lu.size(); ++k)
+      log_u[k] = lu[k].x < -1e29f ? -INFINITY : ((double)lu[k].x + (double)lu[k].y) * kLn2;
   if (log_U01)
     for (size_t q = 0; q < p->src.input_to_tri.size(); ++q) log_U01[q] = su[p->src.input_to_tri[q]] * kLn2;
   if (log_U0T)
@@ -1138,10 +1146,17 @@ ots_status ots_set_duals(ots_problem *p, const double *log_u, const double *log_
   if (!p || !log_u || !log_U01 || !log_U0T) return fail(OTS_ERR_INVALID_ARG, "NULL argument");
   DeviceGuard guard(p->dev);
   const size_t S = p->S;
-  std::vector<double> lu((size_t)(p->T - 2) * S), su(p->src.n, 0.0), zu(p->snk.n, 0.0);
+  std::vector<float2> lu((size_t)(p->T - 2) * S);
+  std::vector<double> su(p->src.n, 0.0), zu(p->snk.n, 0.0);
   for (size_t k = 0; k < lu.size(); ++k) {
     if (std::isnan(log_u[k]) || log_u[k] > 0.0) return fail(OTS_ERR_INVALID_ARG, "log_u must be <= 0");
-    lu[k] = std::isinf(log_u[k]) ? -1e30 : log_u[k] * kInvLn2;
+    if (std::isinf(log_u[k])) {
+      lu[k] = make_float2(kNeg, 0.f);
+    } else {
+      const double x = log_u[k] * kInvLn2;
+      const float h = (float)x;
+      lu[k] = make_float2(h, (float)(x - (double)h));
+    }
   }
   for (size_t q = 0; q < p->src.input_to_tri.size(); ++q) {
     if (!std::isfinite(log_U01[q])) return fail(OTS_ERR_INVALID_ARG, "log_U01 must be finite");
@@ -1151,7 +1166,7 @@ ots_status ots_set_duals(ots_problem *p, const double *log_u, const double *log_
     if (!std::isfinite(log_U0T[q])) return fail(OTS_ERR_INVALID_ARG, "log_U0T must be finite");
     zu[p->snk.input_to_tri[q]] = log_U0T[q] * kInvLn2;
   }
-  OTS_CUDA(cudaMemcpyAsync(p->d_logu + 2 * S, lu.data(), sizeof(double) * lu.size(), cudaMemcpyHostToDevice, p->stream));
+  OTS_CUDA(cudaMemcpyAsync(p->d_logu + 2 * S, lu.data(), sizeof(float2) * lu.size(), cudaMemcpyHostToDevice, p->stream));
   if (p->src.n) OTS_CUDA(cudaMemcpyAsync(p->src.d_tri_logU, su.data(), sizeof(double) * p->src.n, cudaMemcpyHostToDevice, p->stream));
   if (p->snk.n) OTS_CUDA(cudaMemcpyAsync(p->snk.d_tri_logU, zu.data(), sizeof(double) * p->snk.n, cudaMemcpyHostToDevice, p->stream));
   OTS_CUDA(cudaStreamSynchronize(p->stream));

@@ -466,7 +466,7 @@ ots_status ots_host::batch_admit(ots_batch *b, ots_problem *p, const ots_solve_o
   I.out_ptr = p->d_out_ptr; I.out_state = p->d_out_state; I.out_nbr = p->d_out_nbr;
   I.kl_hi = p->d_kl_hi; I.kl_lo = p->d_kl_lo; I.logd_hi = p->d_logd_hi; I.logd_lo = p->d_logd_lo;
   I.cap = p->d_cap;
-  I.logu = p->d_logu; I.w_hi = p->d_w_hi; I.w_lo = p->d_w_lo; I.flow = p->d_flow;
+  I.lu = p->d_logu; I.w_hi = p->d_w_hi; I.w_lo = p->d_w_lo; I.flow = p->d_flow;
   I.a0_hi = p->d_a_hi[0]; I.a1_hi = p->d_a_hi[1]; I.a2_hi = p->d_a_hi[2];
   I.a0_lo = p->d_a_lo[0]; I.a1_lo = p->d_a_lo[1]; I.a2_lo = p->d_a_lo[2];
   I.b_hi = p->d_b_hi; I.b_lo = p->d_b_lo;

@@ -47,8 +47,8 @@ struct alignas(16) BatchInst {
   int max_passes, pad;
   const int *in_ptr, *in_state, *in_nbr, *out_ptr, *out_state, *out_nbr;
   const float *kl_hi, *kl_lo, *logd_hi, *logd_lo;
-  const double *cap;
-  double *logu;                  // [T+1][S] log2 u_t
+  const float2 *cap;             // [S] d as a float-float
+  float2 *lu;                    // [T+1][S] log2 u_t as a float-float
   float *w_hi, *w_lo;            // [T+1][S] W_t
   double *flow;                  // [T+1][S] P_t
   float *a0_hi, *a1_hi, *a2_hi;  // A_1, and A_t for even / odd t

@@ -81,7 +81,7 @@ __device__ __forceinline__ StepArgs step_of(const BatchInst &I, bool fwd, int t,
   a.kl_hi = I.kl_hi; a.kl_lo = I.kl_lo;
   a.logd_hi = I.logd_hi; a.logd_lo = I.logd_lo;
   a.cap = I.cap;
-  a.logu_t = I.logu + (size_t)t * I.S;
+  a.lu_t = I.lu + (size_t)t * I.S;
   a.w_hi_t = I.w_hi + (size_t)t * I.S;
   a.w_lo_t = I.w_lo + (size_t)t * I.S;
   a.flow_t = I.flow + (size_t)t * I.S;
@@ -111,20 +111,21 @@ __device__ __forceinline__ BndArgs bnd_of(const BatchInst &I, bool source, int m
   return b;
 }
 
-// Sum of three doubles over the block, fixed order.
-__device__ __forceinline__ void block_sum3(double &v0, double &v1, double &v2, double *s) {
+// Sum of three float-floats over the block, fixed order.
+__device__ __forceinline__ void block_sum3(float2 &v0, float2 &v1, float2 &v2, float2 *s) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-    v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-  }
+  v0 = warp_sum_ff(v0);
+  v1 = warp_sum_ff(v1);
+  v2 = warp_sum_ff(v2);
   __syncthreads();
   if (lane == 0) { s[3 * wid] = v0; s[3 * wid + 1] = v1; s[3 * wid + 2] = v2; }
   __syncthreads();
-  v0 = 0.0; v1 = 0.0; v2 = 0.0;
-  for (int w = 0; w < kTickBlock / 32; ++w) { v0 += s[3 * w]; v1 += s[3 * w + 1]; v2 += s[3 * w + 2]; }
+  v0 = s[0]; v1 = s[1]; v2 = s[2];
+  for (int w = 1; w < kTickBlock / 32; ++w) {
+    ff_add(v0, s[3 * w].x, s[3 * w].y);
+    ff_add(v1, s[3 * w + 1].x, s[3 * w + 1].y);
+    ff_add(v2, s[3 * w + 2].x, s[3 * w + 2].y);
+  }
 }
 
 template <int C>
@@ -176,7 +177,7 @@ __device__ __forceinline__ void group_reduce_rt(float (&x)[KB], int G, unsigned 
 // gathered rows, so the update waits for no further load.
 template <int C>
 __device__ __forceinline__ void fwd_round(const StepArgs &a, int G, int v0, int jb, int je, float2 (*s_w)[6],
-                                          double &viol, double &dual) {
+                                          float &viol, float2 &dual) {
   constexpr int KB = KBOf<C>::value;
   const int g = threadIdx.x & (G - 1);
   const int nib = threadIdx.x / G;                 // node within the round
@@ -214,7 +215,7 @@ __device__ __forceinline__ void fwd_round(const StepArgs &a, int G, int v0, int 
     // inputs of the owned in-state (one per thread when own1)
     int sk = 0;
     float klh = 0.f, kll = 0.f, ldh = 0.f, ldl = 0.f, wih = kNeg, wil = 0.f;
-    double capk = 0.0, luo = 0.0;
+    float2 capk = make_float2(0.f, 0.f), luo = make_float2(0.f, 0.f);
     if (own1 && g < nb) {
 #pragma unroll
       for (int k = 0; k < KB; ++k)
@@ -222,7 +223,7 @@ __device__ __forceinline__ void fwd_round(const StepArgs &a, int G, int v0, int 
       klh = a.kl_hi[sk]; kll = a.kl_lo[sk];
       ldh = a.logd_hi[sk]; ldl = a.logd_lo[sk];
       capk = a.cap[sk];
-      luo = a.logu_t[sk];
+      luo = a.lu_t[sk];
       if (a.mode != 0) { wih = a.w_hi_t[sk]; wil = a.w_lo_t[sk]; }
     }
 
@@ -263,10 +264,11 @@ __device__ __forceinline__ void fwd_round(const StepArgs &a, int G, int v0, int 
         for (int k = 1; k < KB; ++k)
           if (k == g) { m = cm[k]; sm = cs[k]; }
         float h, l;
-        double lu_new = 0.0, flow = 0.0;
+        float2 lu_new;
+        double flow = 0.0;
         update_meta(a.mode, a.qs, m, sm, klh, kll, ldh, ldl, capk, luo, wih, wil, h, l, lu_new, flow, viol, dual);
         if (a.mode == 0) {
-          a.logu_t[sk] = lu_new;
+          a.lu_t[sk] = lu_new;
           a.w_hi_t[sk] = h;
           a.w_lo_t[sk] = l;
         } else {
@@ -365,7 +367,7 @@ __device__ void setup_item(const BatchInst &I, int k) {
     float wh, wl;
     make_w(I.kl_hi[s], I.kl_lo[s], 0.f, 0.f, I.qs, wh, wl);
     for (int t = 2; t <= I.T - 1; ++t) {
-      I.logu[(size_t)t * I.S + s] = 0.0;
+      I.lu[(size_t)t * I.S + s] = make_float2(0.f, 0.f);
       I.w_hi[(size_t)t * I.S + s] = wh;
       I.w_lo[(size_t)t * I.S + s] = wl;
     }
@@ -404,16 +406,20 @@ __device__ void flow_bnd_item(const BatchInst &I, int k) {
 
 // The last item of an instance in this tick: reduce the items' partials (fixed order),
 // fold them into the pass statistics, and advance the step sequence.
-__device__ void finalise(const BatchInst &I, BatchCtl *c, const Phase &ph, double *s_red) {
+__device__ void finalise(const BatchInst &I, BatchCtl *c, const Phase &ph, float2 *s_red) {
   __threadfence();
-  double a = 0.0, b = 0.0, d = 0.0;
+  float2 fa = make_float2(0.f, 0.f), fb = fa, fd = fa;
   for (int q = threadIdx.x; q < I.n_items; q += kTickBlock) {
-    a += __ldcg(I.partials + 3 * q);
-    b += __ldcg(I.partials + 3 * q + 1);
-    d += __ldcg(I.partials + 3 * q + 2);
+    const float2 x = to_ff(__ldcg(I.partials + 3 * q));
+    const float2 y = to_ff(__ldcg(I.partials + 3 * q + 1));
+    const float2 z = to_ff(__ldcg(I.partials + 3 * q + 2));
+    ff_add(fa, x.x, x.y);
+    ff_add(fb, y.x, y.y);
+    ff_add(fd, z.x, z.y);
   }
-  block_sum3(a, b, d, s_red);
+  block_sum3(fa, fb, fd, s_red);
   if (threadIdx.x != 0) return;
+  const double a = from_ff(fa), b = from_ff(fb), d = from_ff(fd);
   DevStats &st = c->stats;
   int status = c->status;
   int step = c->step + 1;
@@ -497,7 +503,7 @@ __global__ void __launch_bounds__(kTickBlock, 2) k_batch_tick(const TickArgs ta)
   __shared__ BatchInst s_inst[2];                  // current and next item's instance
   __shared__ int s_hdr[2][4];
   __shared__ int s_last;
-  __shared__ double s_red[3 * (kTickBlock / 32)];
+  __shared__ float2 s_red[3 * (kTickBlock / 32)];
   __shared__ float2 s_w[kTickBlock][6];            // W of the in-states of each node (fwd)
   const int n = *ta.n_items;
   int it = blockIdx.x;                             // items it, it + grid, it + 2 grid, ...
@@ -522,7 +528,9 @@ __global__ void __launch_bounds__(kTickBlock, 2) k_batch_tick(const TickArgs ta)
     BatchCtl *c = ta.ctl + slot;
     if (running) {
       const int G = I.G, C = I.C;
-      double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+      double r0 = 0.0, r1 = 0.0, r2 = 0.0;          // boundary steps (FP64)
+      float fviol = 0.f;                             // forward steps: excess, dual (float-float)
+      float2 fdual = make_float2(0.f, 0.f);
       switch (ph.kind) {
         case kPhSetup:
           setup_item(I, k);
@@ -553,8 +561,8 @@ __global__ void __launch_bounds__(kTickBlock, 2) k_batch_tick(const TickArgs ta)
             int jbn = 0, jen = 0;
             if (v0 + I.npb < v_end) { jbn = a.ptr[vn]; jen = a.ptr[vn + 1]; }
             if (fwd) {
-              if (C == 1) fwd_round<1>(a, G, v0, jb, je, s_w, r0, r1);
-              else fwd_round<2>(a, G, v0, jb, je, s_w, r0, r1);
+              if (C == 1) fwd_round<1>(a, G, v0, jb, je, s_w, fviol, fdual);
+              else fwd_round<2>(a, G, v0, jb, je, s_w, fviol, fdual);
             } else {
               if (C == 1) bwd_round<1>(a, G, v0, jb, je);
               else bwd_round<2>(a, G, v0, jb, je);
@@ -570,11 +578,15 @@ __global__ void __launch_bounds__(kTickBlock, 2) k_batch_tick(const TickArgs ta)
         default:
           break;
       }
-      block_sum3(r0, r1, r2, s_red);
+      const bool bnd = ph.kind == kPhSrc || ph.kind == kPhSnk || ph.kind == kPhInitBnd;
+      float2 p0 = bnd ? to_ff(r0) : make_float2(fviol, 0.f);
+      float2 p1 = bnd ? to_ff(r1) : fdual;
+      float2 p2 = bnd ? to_ff(r2) : make_float2(0.f, 0.f);
+      block_sum3(p0, p1, p2, s_red);
       if (threadIdx.x == 0) {
-        I.partials[3 * k] = r0;
-        I.partials[3 * k + 1] = r1;
-        I.partials[3 * k + 2] = r2;
+        I.partials[3 * k] = from_ff(p0);
+        I.partials[3 * k + 1] = from_ff(p1);
+        I.partials[3 * k + 2] = from_ff(p2);
         s_last = atomic_add_acq_rel(&c->counter, 1u) == (unsigned)(I.n_items - 1);
       }
     }

@@ -15,6 +15,11 @@
 //
 // log 0 is represented by the finite sentinel kNeg (-1e30) with lo = 0; terms whose hi part is
 // below kNegThresh are skipped by every reduction.
+//
+// Per-state duals log2 u_t and capacities d are float-float pairs (float2: value = x + y), and
+// per-thread sums that decide convergence are float-float too; FP64 appears only in the
+// per-block totals, the boundary updates and the flows.  (The FP64 pipe of this GPU issues a
+// warp instruction in tens of cycles, so FP64 on the per-state path dominated the step.)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -82,8 +87,8 @@ struct StepArgs {
   const lo_t *klc_lo;
   const float *logd_hi;       // [S] log2 d (kNeg for d = 0)
   const float *logd_lo;
-  const double *cap;          // [S] d (inf allowed)
-  double *logu_t;             // [S] log2 u_t (row t)
+  const float2 *cap;          // [S] d as a float-float (x = +inf for no capacity)
+  float2 *lu_t;               // [S] log2 u_t (row t) as a float-float; (kNeg, 0) for u = 0
   float *w_hi_t;              // [S] W_t hi (on the q grid)
   float *w_lo_t;              // [S] W_t lo
   double *flow_t;             // [S] aggregate P_t (flows mode)
@@ -98,9 +103,9 @@ struct StepArgs {
   const float *in_kl_lo;
   const float *in_logd_hi;    // [S] log2 d at in-CSR position j
   const float *in_logd_lo;
-  const double *in_cap;       // [S] d at in-CSR position j
+  const float2 *in_cap;       // [S] d at in-CSR position j
   const int *in_outpos;       // [S] out-CSR position of the state at in-CSR position j
-  double *logu_in_t;          // [S] log2 u_t by in-CSR position
+  float2 *lu_in_t;            // [S] log2 u_t by in-CSR position
   float *wout_hi_t;           // [S] W_t by out-CSR position
   float *wout_lo_t;
 };

@@ -20,14 +20,14 @@ cudaError_t launch_boundary(const BndArgs &b, cudaStream_t s);
 int boundary_grid(int n_seg);
 cudaError_t launch_pass_begin(DevStats *st, cudaStream_t s);
 cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, cudaStream_t s);
-cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, double *logu,
+cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, float2 *logu,
                            float *w_hi, float *w_lo, int reset, const int *st_inpos, const int *st_outpos,
-                           double *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s);
+                           float2 *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s);
 cudaError_t launch_fill_panel(size_t n, float *hi, lo_t *lo, cudaStream_t s);
 cudaError_t launch_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
                                    const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
                                    const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
-                                   const double *logu_t, double *out, cudaStream_t s);
+                                   const float2 *logu_t, double *out, cudaStream_t s);
 cudaError_t launch_boundary_flows(int n, int Lp, QScale qs, const int *tri_l, const int *tri_node_other,
                                   const double *tri_logU, const float *msg_hi, const lo_t *msg_lo, double *out,
                                   cudaStream_t s);
@@ -96,7 +96,7 @@ struct CreateOpts {
 struct HostArrays {
   std::vector<int> in_ptr, out_ptr, in_state, in_nbr, out_state, out_nbr, st_inpos, st_outpos, in_outpos;
   std::vector<float> kl_hi, kl_lo, logd_hi, logd_lo, in_kl_hi, in_kl_lo, in_logd_hi, in_logd_lo, klc_hi;
-  std::vector<double> cap, in_cap;
+  std::vector<float2> cap, in_cap;          // capacities as float-float pairs (x = inf: none)
   std::vector<ots::lo_t> klc_lo;
 };
 
@@ -147,16 +147,16 @@ struct ots_problem {
   int *d_out_ptr = nullptr, *d_out_state = nullptr, *d_out_nbr = nullptr;
   int *d_tail = nullptr, *d_head = nullptr;
   float *d_kl_hi = nullptr, *d_kl_lo = nullptr, *d_logd_hi = nullptr, *d_logd_lo = nullptr;
-  double *d_cap = nullptr;
+  float2 *d_cap = nullptr;                     // [S] float-float
   float *d_klc_hi = nullptr;
   lo_t *d_klc_lo = nullptr;
   float *d_w_hi = nullptr, *d_w_lo = nullptr;  // [T+1][S]
-  double *d_logu = nullptr;                    // [T+1][S]
+  float2 *d_logu = nullptr;                    // [T+1][S] log2 u_t, float-float
   // CSR-ordered copies used by the pipelined kernels
   int *d_st_inpos = nullptr, *d_st_outpos = nullptr, *d_in_outpos = nullptr;
   float *d_in_kl_hi = nullptr, *d_in_kl_lo = nullptr, *d_in_logd_hi = nullptr, *d_in_logd_lo = nullptr;
-  double *d_in_cap = nullptr;
-  double *d_logu_in = nullptr;                 // [T+1][S] by in-CSR position
+  float2 *d_in_cap = nullptr;
+  float2 *d_logu_in = nullptr;                 // [T+1][S] by in-CSR position
   float *d_wout_hi = nullptr, *d_wout_lo = nullptr;  // [T+1][S] by out-CSR position
   double *d_flow = nullptr;                    // [T+1][S]
   float *d_a_hi[3] = {nullptr, nullptr, nullptr};

@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(BlockOf<G>::value, MinBlocksFwd<G>::value) k_f
 #pragma unroll
     for (int q = 0; q < 4; ++q) { M[c][q] = 2.f * kNeg; acc[c][q] = 0.f; }
 
-  double viol = 0.0, dual = 0.0;
+  float viol = 0.f;
+  float2 dual = make_float2(0.f, 0.f);
   const int jb = active ? a.ptr[v] : 0;
   const int je = active ? a.ptr[v + 1] : 0;
   // G > 32: the block is one node, so trip counts are uniform across the block.
@@ -177,7 +178,8 @@ __global__ void __launch_bounds__(BlockOf<G>::value, MinBlocksFwd<G>::value) k_f
       store4(a.out_hi + rowv + 4 * (c * G + g), a.out_lo + rowv + 4 * (c * G + g), oh, ol);
     }
   }
-  if (a.mode == 0) block_sum2_last(viol, dual, a.partials, a.counter, &a.stats->cap_viol, &a.stats->dual_cap, 0);
+  if (a.mode == 0)
+    block_sum2_last(make_float2(viol, 0.f), dual, a.partials, a.counter, &a.stats->cap_viol, &a.stats->dual_cap, 0);
 }
 
 // ------------------------------------------------------------------------------------
@@ -233,9 +235,9 @@ __global__ void __launch_bounds__(kBlock) k_boundary(const BndArgs b) {
   if (sidx < b.n_seg) boundary_segment(b, sidx, r0, r1, r2);
   if (b.mode == 0) {
     if (b.is_source) {
-      block_sum2_last(r0, r1, b.partials, b.counter, &b.stats->src_resid, &b.stats->dual_src, 1);
+      block_sum2_last(to_ff(r0), to_ff(r1), b.partials, b.counter, &b.stats->src_resid, &b.stats->dual_src, 1);
     } else {
-      block_sum2_last(r0, r1, b.partials, b.counter, &b.stats->mass_snk, &b.stats->dual_snk, 1);
+      block_sum2_last(to_ff(r0), to_ff(r1), b.partials, b.counter, &b.stats->mass_snk, &b.stats->dual_snk, 1);
     }
     if (r2 > 0.0) atomicAdd(&b.stats->bad, r2);
   }
@@ -259,22 +261,20 @@ __global__ void k_pass_end(const DevStats *st, PassReport *rep, double mass, dou
 }
 
 // W_t = log2 K_L + log2 u_t for t = 2..T-1 from log2 u (set to 0 first when reset).
-__global__ void k_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, double *logu, float *w_hi,
-                          float *w_lo, int reset, const int *st_inpos, const int *st_outpos, double *logu_in,
+__global__ void k_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, float2 *lu2, float *w_hi,
+                          float *w_lo, int reset, const int *st_inpos, const int *st_outpos, float2 *lu2_in,
                           float *wout_hi, float *wout_lo) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= S) return;
   for (int t = 2; t <= T - 1; ++t) {
-    if (reset) logu[(size_t)t * S + s] = 0.0;
-    const double lu = logu[(size_t)t * S + s];
-    float luh = (float)lu;
-    float lul = (float)(lu - (double)luh);
-    if (lu < -1e29) { luh = kNeg; lul = 0.f; }
+    if (reset) lu2[(size_t)t * S + s] = make_float2(0.f, 0.f);
+    float2 lu = lu2[(size_t)t * S + s];
+    if (lu.x < kNegThresh) lu = make_float2(kNeg, 0.f);
     float hi, lo;
-    make_w(kl_hi ? kl_hi[s] : 0.f, kl_lo ? kl_lo[s] : 0.f, luh, lul, qs, hi, lo);
+    make_w(kl_hi ? kl_hi[s] : 0.f, kl_lo ? kl_lo[s] : 0.f, lu.x, lu.y, qs, hi, lo);
     w_hi[(size_t)t * S + s] = hi;
     w_lo[(size_t)t * S + s] = lo;
-    logu_in[(size_t)t * S + st_inpos[s]] = lu;
+    lu2_in[(size_t)t * S + st_inpos[s]] = lu;
     wout_hi[(size_t)t * S + st_outpos[s]] = hi;
     wout_lo[(size_t)t * S + st_outpos[s]] = lo;
   }
@@ -292,7 +292,7 @@ __global__ void k_fill_panel(size_t n, float *hi, lo_t *lo) {
 __global__ void k_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
                                   const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
                                   const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
-                                  const double *logu_t, double *out) {
+                                  const float2 *lu_t, double *out) {
   const size_t n = (size_t)S * (l1 - l0);
   const double unit = qs.lo_unit;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -300,9 +300,10 @@ __global__ void k_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, cons
     const int l = l0 + (int)(i / S);
     const size_t ia = (size_t)tail[j] * Lp + l, ib = (size_t)head[j] * Lp + l;
     const float ah = a_hi[ia], bh = b_hi[ib];
-    if (ah < kNegThresh || bh < kNegThresh || logu_t[j] < -1e29) { out[i] = 0.0; continue; }
+    const float2 lu = lu_t[j];
+    if (ah < kNegThresh || bh < kNegThresh || lu.x < kNegThresh) { out[i] = 0.0; continue; }
     double x = (double)ah + ((double)a_lo[ia] - 32768.0) * unit + (double)bh + ((double)b_lo[ib] - 32768.0) * unit +
-               logu_t[j];
+               (double)lu.x + (double)lu.y;
     if (klc_hi) x += (double)klc_hi[(size_t)j * Lp + l] + ((double)klc_lo[(size_t)j * Lp + l] - 32768.0) * unit;
     else x += (double)kl_hi[j] + (double)kl_lo[j];
     out[i] = exp2(x);
@@ -426,7 +427,7 @@ struct FwdMeta {
   int st[kBatchTma], outpos[kBatchTma], nbr[kBatchTma];
   float kl_hi[kBatchTma], kl_lo[kBatchTma], logd_hi[kBatchTma], logd_lo[kBatchTma];
   float w_hi[kBatchTma], w_lo[kBatchTma];      // flows mode: the stored weights
-  double cap[kBatchTma], lu_old[kBatchTma];
+  float2 cap[kBatchTma], lu_old[kBatchTma];
   int fin[kBatchTma];                           // capacity finite
 };
 
@@ -452,7 +453,7 @@ __device__ __forceinline__ void consumers_sync() {
 struct LaneMeta {
   int nbr, st, outpos;
   float kl_hi, kl_lo, logd_hi, logd_lo, w_hi, w_lo;
-  double cap, lu_old;
+  float2 cap, lu_old;
 };
 
 // One independent round of loads per item: everything is stored in CSR order.
@@ -470,7 +471,7 @@ __device__ __forceinline__ LaneMeta load_lane_meta(const StepArgs &a, const TmaI
       r.logd_hi = a.in_logd_hi[j];
       r.logd_lo = a.in_logd_lo[j];
       r.cap = a.in_cap[j];
-      r.lu_old = a.logu_in_t[j];
+      r.lu_old = a.lu_in_t[j];
     } else {
       r.w_hi = a.wout_hi_t[j];
       r.w_lo = a.wout_lo_t[j];
@@ -511,7 +512,7 @@ __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, flo
         m.kl_hi[lane] = lm.kl_hi; m.kl_lo[lane] = lm.kl_lo;
         m.logd_hi[lane] = lm.logd_hi; m.logd_lo[lane] = lm.logd_lo;
         m.cap[lane] = lm.cap; m.lu_old[lane] = lm.lu_old;
-        m.fin[lane] = isfinite(lm.cap) ? 1 : 0;
+        m.fin[lane] = lm.cap.x < INFINITY ? 1 : 0;
         m.w_hi[lane] = lm.w_hi; m.w_lo[lane] = lm.w_lo;
       } else {
         m.w_hi[lane] = lm.w_hi; m.w_lo[lane] = lm.w_lo;
@@ -615,7 +616,8 @@ __global__ void __launch_bounds__(G + 32) k_forward_tma(const StepArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  double viol = 0.0, dual = 0.0;
+  float viol = 0.f;
+  float2 dual = make_float2(0.f, 0.f);
   bool timed_out = false;
   if (wid == NW) {
     // ---------------- producer warp ----------------
@@ -685,15 +687,14 @@ __global__ void __launch_bounds__(G + 32) k_forward_tma(const StepArgs a) {
         update_w(a.mode, a.qs, mk, sk_, m.kl_hi[lane], m.kl_lo[lane], m.logd_hi[lane], m.logd_lo[lane],
                  m.fin[lane] != 0, m.w_hi[lane], m.w_lo[lane], mh, ml, col_hi, col_lo, lu_hi, lu_lo);
         if (wid == 0) {
-          double lu_new = 0.0, flow = 0.0, v0 = 0.0, v1 = 0.0;
+          float2 lu_new;
+          double flow = 0.0;
           update_stats(a.mode, col_hi, col_lo, lu_hi, lu_lo, m.logd_hi[lane], m.logd_lo[lane], mh, m.cap[lane],
-                       m.lu_old[lane], lu_new, flow, v0, v1);
+                       m.lu_old[lane], lu_new, flow, viol, dual);
           const int st = m.st[lane];
           if (a.mode == 0) {
-            viol += v0;
-            dual += v1;
-            a.logu_t[st] = lu_new;
-            a.logu_in_t[m.j0 + lane] = lu_new;
+            a.lu_t[st] = lu_new;
+            a.lu_in_t[m.j0 + lane] = lu_new;
             a.w_hi_t[st] = mh;
             a.w_lo_t[st] = ml;
             a.wout_hi_t[m.outpos[lane]] = mh;
@@ -727,7 +728,7 @@ __global__ void __launch_bounds__(G + 32) k_forward_tma(const StepArgs a) {
     }
   }
   if (timed_out) atomicAdd(&a.stats->bad, 1e6);
-  block_sum2_last(viol, dual, a.partials, a.counter, &a.stats->cap_viol, &a.stats->dual_cap, 0);
+  block_sum2_last(make_float2(viol, 0.f), dual, a.partials, a.counter, &a.stats->cap_viol, &a.stats->dual_cap, 0);
 }
 
 // Backward step, warp-specialised like the forward step.
@@ -892,9 +893,9 @@ cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, do
   return cudaGetLastError();
 }
 
-cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, double *logu,
+cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, float2 *logu,
                            float *w_hi, float *w_lo, int reset, const int *st_inpos, const int *st_outpos,
-                           double *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s) {
+                           float2 *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s) {
   k_weights<<<(S + 255) / 256, 256, 0, s>>>(S, T, qs, kl_hi, kl_lo, logu, w_hi, w_lo, reset, st_inpos, st_outpos,
                                             logu_in, wout_hi, wout_lo);
   return cudaGetLastError();
@@ -911,7 +912,7 @@ cudaError_t launch_fill_panel(size_t n, float *hi, lo_t *lo, cudaStream_t s) {
 cudaError_t launch_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
                                    const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
                                    const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
-                                   const double *logu_t, double *out, cudaStream_t s) {
+                                   const float2 *logu_t, double *out, cudaStream_t s) {
   size_t n = (size_t)S * (l1 - l0);
   size_t blocks = (n + 255) / 256;
   if (blocks > 8192) blocks = 8192;

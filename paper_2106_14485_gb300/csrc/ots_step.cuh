@@ -35,8 +35,61 @@ __device__ __forceinline__ void store4(float *hp, lo_t *lp, const float h[4], co
   *reinterpret_cast<uint2 *>(lp) = b;
 }
 
-// Sum of two doubles over the block (fixed order: warp shuffles, then warps in order).
-__device__ __forceinline__ void block_sum2(double &v0, double &v1, double *s0, double *s1) {
+// ---- float-float accumulation (value = x + y) ------------------------------------------------
+
+// a += (bh + bl), renormalised (the pair stays non-overlapping).
+__device__ __forceinline__ void ff_add(float2 &a, float bh, float bl) {
+  float s, e;
+  two_sum(a.x, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.y, bl));
+  const float h = __fadd_rn(s, e);
+  a.y = __fsub_rn(e, __fsub_rn(h, s));
+  a.x = h;
+}
+
+// acc += c * u for float-float c and u (exact product of the hi parts via fma).
+__device__ __forceinline__ void ff_mac(float2 &acc, float2 c, float2 u) {
+  const float p = __fmul_rn(c.x, u.x);
+  const float pe = fmaf(c.x, u.x, -p);
+  ff_add(acc, p, __fadd_rn(pe, __fadd_rn(__fmul_rn(c.x, u.y), __fmul_rn(c.y, u.x))));
+}
+
+__device__ __forceinline__ float2 to_ff(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+__device__ __forceinline__ double from_ff(float2 v) { return (double)v.x + (double)v.y; }
+
+// Butterfly sum of a float-float over the warp (fixed order; every lane ends with the total).
+__device__ __forceinline__ float2 warp_sum_ff(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, v.x, o);
+    const float l = __shfl_xor_sync(0xffffffffu, v.y, o);
+    ff_add(v, h, l);
+  }
+  return v;
+}
+
+// Sum of two float-floats over the block (fixed order: warp shuffles, then warps in order).
+__device__ __forceinline__ void block_sum2(float2 &v0, float2 &v1, float2 *s0, float2 *s1) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v0 = warp_sum_ff(v0);
+  v1 = warp_sum_ff(v1);
+  __syncthreads();
+  if (lane == 0) { s0[wid] = v0; s1[wid] = v1; }
+  __syncthreads();
+  v0 = s0[0];
+  v1 = s1[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+    ff_add(v0, s0[w].x, s0[w].y);
+    ff_add(v1, s1[w].x, s1[w].y);
+  }
+}
+
+// Sum of two doubles over the block (FP64; used once per launch, by the last block).
+__device__ __forceinline__ void block_sum2_f64(double &v0, double &v1, double *s0, double *s1) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -51,18 +104,19 @@ __device__ __forceinline__ void block_sum2(double &v0, double &v1, double *s0, d
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { v0 += s0[w]; v1 += s1[w]; }
 }
 
-// Deterministic FP64 grid reduction of two values: every block writes its partial sums, the
-// last block to finish reduces all partials with a fixed assignment to threads and a fixed
-// tree, then adds the totals to dst0 / dst1 (or assigns, when assign != 0) and resets the
-// counter for the next kernel.
-__device__ void block_sum2_last(double v0, double v1, double *partials, unsigned int *counter,
+// Deterministic grid reduction of two values: every block sums its threads' float-float
+// values and writes the block total as FP64; the last block to finish reduces all partials in
+// FP64 with a fixed assignment to threads and a fixed tree, then adds the totals to dst0 /
+// dst1 (or assigns, when assign != 0) and resets the counter for the next kernel.
+__device__ void block_sum2_last(float2 v0, float2 v1, double *partials, unsigned int *counter,
                                 double *dst0, double *dst1, int assign) {
-  __shared__ double s0[32], s1[32];   // one slot per warp of any block size up to 1024 threads
+  __shared__ float2 f0[32], f1[32];   // one slot per warp of any block size up to 1024 threads
+  __shared__ double s0[32], s1[32];
   __shared__ bool is_last;
-  block_sum2(v0, v1, s0, s1);
+  block_sum2(v0, v1, f0, f1);
   if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = v0;
-    partials[2 * blockIdx.x + 1] = v1;
+    partials[2 * blockIdx.x] = from_ff(v0);
+    partials[2 * blockIdx.x + 1] = from_ff(v1);
     __threadfence();
     unsigned int prev = atomicAdd(counter, 1u);
     is_last = (prev == gridDim.x - 1);
@@ -75,7 +129,7 @@ __device__ void block_sum2_last(double v0, double v1, double *partials, unsigned
     a += __ldcg(partials + 2 * k);
     b += __ldcg(partials + 2 * k + 1);
   }
-  block_sum2(a, b, s0, s1);
+  block_sum2_f64(a, b, s0, s1);
   if (threadIdx.x == 0) {
     if (assign) { *dst0 = a; *dst1 = b; } else { *dst0 += a; *dst1 += b; }
     *counter = 0u;
@@ -235,42 +289,42 @@ __device__ __forceinline__ void make_w(float kl_hi, float kl_lo, float lu_hi, fl
 }
 
 // Adds the capacity excess (P_old - d)_+ of one state to viol, where P_old = 2^(log2 u_old +
-// col) is the column sum under the old u_t and d = 2^(ldh + ldl) its capacity (finite; d = 0
-// is the sentinel ldh = log2 0).  The ratio P_old / d = 2^e is formed in FP64 (its terms
-// cancel) and only near or above capacity; for 0 < e <= 32 the excess d (2^e - 1) is
+// col) is the column sum under the old u_t and d = cap.x + cap.y its capacity (finite; d = 0
+// is the sentinel ldh = log2 0).  The exponent e of the ratio P_old / d = 2^e is formed in
+// float-float (its terms cancel), only near or above capacity; the excess d (2^e - 1) is
 // evaluated in FP32: exp2 for e > 0.5, else the Taylor series of exp(x) - 1 at x = e ln 2
 // (|x| <= 0.35, truncation below 2e-7 relative).
-__device__ __forceinline__ void add_excess(double cap, double lu_old, float col_hi, float col_lo, float ldh, float ldl,
-                                           double &viol) {
+__device__ __forceinline__ void add_excess(float2 cap, float2 lu_old, float col_hi, float col_lo, float ldh, float ldl,
+                                           float &viol) {
   if (ldh < kNegThresh) {                         // d = 0: every unit of flow is excess
-    if (lu_old > -1e29) viol += exp2(lu_old + (double)col_hi + (double)col_lo);
+    if (lu_old.x > kNegThresh) viol += ex2(fminf((lu_old.x + col_hi) + (lu_old.y + col_lo), 126.f));
     return;
   }
-  const float qv = (float)lu_old + col_hi - ldh;
+  const float qv = lu_old.x + col_hi - ldh;
   if (!(qv > -1e-3f)) return;
-  const float e = (float)((lu_old - (double)ldh) + ((double)col_hi + (double)(col_lo - ldl)));
+  float s1, e1, s2, e2;
+  two_sum(lu_old.x, -ldh, s1, e1);
+  two_sum(s1, col_hi, s2, e2);
+  const float e = __fadd_rn(s2, __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(lu_old.y, col_lo), -ldl)));
   if (!(e > 0.f)) return;
-  if (e > 32.f) {                                 // far above capacity (first passes): FP64
-    viol += exp2(lu_old + (double)col_hi + (double)col_lo) - cap;
-    return;
-  }
   float r;
   if (e > 0.5f) {
-    r = ex2(e) - 1.f;
+    r = ex2(fminf(e, 126.f)) - 1.f;
   } else {
     const float x = e * 0.69314718f;
     r = x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 720.f, 1.f / 120.f), 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
   }
-  viol += cap * (double)r;
+  viol += fminf(cap.x * r, 1e30f);                // huge excesses stay finite (reported, not NaN)
 }
 
 // Capacity update of one state from its column log-sum-exp (cm + log2 cs) (Algorithm 2,
 // Corollary 7): W_t for the aggregation and, when `write`, the stored log2 u_t, W_t, the
-// excess (P_t - d)_+ with the old u_t and the dual term d log2 u_t (Theorem 3).  In flows
-// mode (a.mode == 1) W_t is read back and, when `write`, P_t is stored.
+// excess (P_t - d)_+ with the old u_t (viol) and the dual term d log2 u_t (Theorem 3; dual,
+// float-float).  In flows mode (a.mode == 1) W_t is read back and, when `write`, P_t is
+// stored.
 template <bool PC>
 __device__ __forceinline__ void update_state(const StepArgs &a, int sk, float cm, float cs, bool write, float &w_hi,
-                                             float &w_lo, double &viol, double &dual) {
+                                             float &w_lo, float &viol, float2 &dual) {
   float col_hi = kNeg, col_lo = 0.f;
   if (cm > kNegThresh && cs > 0.f) two_sum(cm, lg2(cs), col_hi, col_lo);  // log2 (hatPsi .* Psi (.* K_L))^T 1
   const float klh = PC ? 0.f : a.kl_hi[sk], kll = PC ? 0.f : a.kl_lo[sk];
@@ -283,14 +337,17 @@ __device__ __forceinline__ void update_state(const StepArgs &a, int sk, float cm
   if (a.mode != 0) {
     w_hi = a.w_hi_t[sk];
     w_lo = a.w_lo_t[sk];
-    if (write)
+    if (write) {
+      const float2 lu = a.lu_t[sk];
       a.flow_t[sk] = col_hi > kNegThresh && w_hi > kNegThresh
-                         ? exp2(a.logu_t[sk] + (double)col_hi + (double)col_lo) : 0.0;
+                         ? exp2((double)lu.x + (double)lu.y + (double)col_hi + (double)col_lo) : 0.0;
+    }
     return;
   }
-  const double cap = a.cap[sk];
+  const float2 cap = a.cap[sk];
+  const bool fin = cap.x < INFINITY;
   float lu_hi = 0.f, lu_lo = 0.f;
-  if (isfinite(cap) && col_hi > kNegThresh) {
+  if (fin && col_hi > kNegThresh) {
     if (a.logd_hi[sk] < kNegThresh) {
       lu_hi = kNeg;                                // d = 0: the state is closed
     } else {
@@ -304,12 +361,12 @@ __device__ __forceinline__ void update_state(const StepArgs &a, int sk, float cm
   }
   make_w(klh, kll, lu_hi, lu_lo, a.qs, w_hi, w_lo);
   if (!write) return;
-  const double lu_old = a.logu_t[sk];
-  if (col_hi > kNegThresh && isfinite(cap)) add_excess(cap, lu_old, col_hi, col_lo, a.logd_hi[sk], a.logd_lo[sk], viol);
-  if (col_hi != col_hi || col_lo != col_lo) viol = __longlong_as_double(0x7ff8000000000000LL);  // NaN: reported
-  const double lu_new = lu_hi < kNegThresh ? -1e30 : (double)lu_hi + (double)lu_lo;
-  if (isfinite(cap) && cap > 0.0) dual += cap * lu_new;
-  a.logu_t[sk] = lu_new;
+  const float2 lu_old = a.lu_t[sk];
+  if (col_hi > kNegThresh && fin) add_excess(cap, lu_old, col_hi, col_lo, a.logd_hi[sk], a.logd_lo[sk], viol);
+  if (col_hi != col_hi || col_lo != col_lo) viol = __int_as_float(0x7fc00000);   // NaN: reported
+  const float2 lu_new = lu_hi < kNegThresh ? make_float2(kNeg, 0.f) : make_float2(lu_hi, lu_lo);
+  if (fin && cap.x > 0.f && lu_new.x > kNegThresh) ff_mac(dual, cap, lu_new);
+  a.lu_t[sk] = lu_new;
   a.w_hi_t[sk] = w_hi;
   a.w_lo_t[sk] = w_lo;
 }
@@ -388,31 +445,33 @@ __device__ __forceinline__ void update_w(int mode, const QScale &qs, float cm, f
   make_w(klh, kll, lu_hi, lu_lo, qs, w_hi, w_lo);
 }
 
-// FP64 part of the same update (one thread per state): the new log2 u_t, the flow P_t in
-// flows mode, the excess (P_t - d)_+ with the old u_t (exact FP64 only near or above
-// capacity) and the dual term d log2 u_t of Theorem 3.
+// Per-state part of the same update (one thread per state): the new log2 u_t, the flow P_t
+// in flows mode (FP64: once per solve), the excess (P_t - d)_+ with the old u_t (viol) and the
+// dual term d log2 u_t of Theorem 3 (dual, float-float).
 __device__ __forceinline__ void update_stats(int mode, float col_hi, float col_lo, float lu_hi, float lu_lo, float ldh,
-                                             float ldl, float w_hi, double cap, double lu_old, double &lu_new,
-                                             double &flow, double &viol, double &dual) {
+                                             float ldl, float w_hi, float2 cap, float2 lu_old, float2 &lu_new,
+                                             double &flow, float &viol, float2 &dual) {
   if (mode != 0) {
-    flow = col_hi > kNegThresh && w_hi > kNegThresh ? exp2(lu_old + (double)col_hi + (double)col_lo) : 0.0;
+    flow = col_hi > kNegThresh && w_hi > kNegThresh
+               ? exp2((double)lu_old.x + (double)lu_old.y + (double)col_hi + (double)col_lo) : 0.0;
     lu_new = lu_old;
     return;
   }
-  if (col_hi > kNegThresh && isfinite(cap)) add_excess(cap, lu_old, col_hi, col_lo, ldh, ldl, viol);
-  if (col_hi != col_hi || col_lo != col_lo) viol = __longlong_as_double(0x7ff8000000000000LL);
-  lu_new = lu_hi < kNegThresh ? -1e30 : (double)lu_hi + (double)lu_lo;
-  if (isfinite(cap) && cap > 0.0) dual += cap * lu_new;
+  const bool fin = cap.x < INFINITY;
+  if (col_hi > kNegThresh && fin) add_excess(cap, lu_old, col_hi, col_lo, ldh, ldl, viol);
+  if (col_hi != col_hi || col_lo != col_lo) viol = __int_as_float(0x7fc00000);
+  lu_new = lu_hi < kNegThresh ? make_float2(kNeg, 0.f) : make_float2(lu_hi, lu_lo);
+  if (fin && cap.x > 0.f && lu_new.x > kNegThresh) ff_mac(dual, cap, lu_new);
 }
 
 // Both parts at once (same arithmetic as update_state, with the per-state inputs loaded
 // ahead by the caller).
 __device__ __forceinline__ void update_meta(int mode, const QScale &qs, float cm, float cs, float klh, float kll,
-                                            float ldh, float ldl, double cap, double lu_old, float win_hi,
-                                            float win_lo, float &w_hi, float &w_lo, double &lu_new, double &flow,
-                                            double &viol, double &dual) {
+                                            float ldh, float ldl, float2 cap, float2 lu_old, float win_hi,
+                                            float win_lo, float &w_hi, float &w_lo, float2 &lu_new, double &flow,
+                                            float &viol, float2 &dual) {
   float col_hi, col_lo, lu_hi, lu_lo;
-  update_w(mode, qs, cm, cs, klh, kll, ldh, ldl, isfinite(cap), win_hi, win_lo, w_hi, w_lo, col_hi, col_lo, lu_hi,
+  update_w(mode, qs, cm, cs, klh, kll, ldh, ldl, cap.x < INFINITY, win_hi, win_lo, w_hi, w_lo, col_hi, col_lo, lu_hi,
            lu_lo);
   update_stats(mode, col_hi, col_lo, lu_hi, lu_lo, ldh, ldl, w_hi, cap, lu_old, lu_new, flow, viol, dual);
 }
