@@ -68,6 +68,19 @@ def parse():
     return ap.parse_args()
 
 
+def combine_ranks(pg, seconds, units, device):
+    """Whole-job figures of independent replicas: the slowest rank's time and the units all
+    ranks processed (max and sum all-reduces; pg = torch.distributed or None for one rank)."""
+    if pg is None:
+        return float(seconds), float(units)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(u, op=pg.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -454,14 +467,7 @@ def run_ours(args):
     barrier()
 
     updates = args.steps * upd_per_pass
-    if pg is not None:
-        t = torch.tensor([elapsed_ms, float(updates)], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        pg.all_reduce(mx[:1], op=pg.ReduceOp.MAX)
-        pg.all_reduce(t[1:], op=pg.ReduceOp.SUM)
-        elapsed_ms, updates_all = float(mx[0]), float(t[1])
-    else:
-        updates_all = float(updates)
+    elapsed_ms, updates_all = combine_ranks(pg, elapsed_ms, float(updates), "cuda")
     value = updates_all / (elapsed_ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers ----
@@ -477,13 +483,8 @@ def run_ours(args):
         ots.ots_destroy_problem(h_e)
         t_e = time.perf_counter() - t0
         assert F.shape[0] == inst.T
-        e2e_val = args.steps * upd_per_pass / t_e
-        if pg is not None:
-            t = torch.tensor([t_e, float(args.steps * upd_per_pass)], dtype=torch.float64, device="cuda")
-            mx = t.clone()
-            pg.all_reduce(mx[:1], op=pg.ReduceOp.MAX)
-            pg.all_reduce(t[1:], op=pg.ReduceOp.SUM)
-            e2e_val = float(t[1]) / float(mx[0])
+        t_all, u_all = combine_ranks(pg, t_e, float(args.steps * upd_per_pass), "cuda")
+        e2e_val = u_all / t_all
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(st["h2d_bytes"]) // args.steps,
                "d2h_bytes_per_step": int(st["d2h_bytes"]) // args.steps,
                "note": f"one call sequence of {args.steps} passes: create from host arrays, passes, flows to host, destroy"}
