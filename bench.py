@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=256,
                     help="instances of the batched workload (uneven random geometric graphs); 0 = skip")
     ap.add_argument("--batch-max-passes", type=int, default=3000)
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="profiling case only: the first N batched-workload instances, 3 graph launches of the "
+                         "tick kernel, then exit (for ncu captures of k_batch_tick)")
     ap.add_argument("--serve-rates", type=str, default="50,200,1000",
                     help="Poisson arrival rates (requests/s) of the serving workload; empty = skip")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate")
@@ -163,7 +166,7 @@ def peaks():
 def kernel_sources_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("ots_kernels.cu", "ots_device.cuh"):
+    for f in ("ots_kernels.cu", "ots_device.cuh", "ots_step.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2106_14485_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -566,8 +569,26 @@ def run_ours(args):
     return 0
 
 
+def profile_batch(args):
+    import torch
+    from paper_2106_14485_gb300 import build, instances, ots
+    build.build()
+    ots.load_library()
+    insts = instances.config4(0, count=args.profile_batch, workers=min(16, os.cpu_count() or 1))
+    b = ots.ots_batch_create(pool_bytes=6 << 30, max_instances=args.profile_batch, ticks_per_launch=32)
+    for x in insts:
+        ots.ots_batch_add(b, x, tol=args.tol, max_iters=args.batch_max_passes)
+    ots.ots_batch_run(b, 3)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "batch", "instances": len(insts), "info": ots.ots_batch_info(b)}), flush=True)
+    ots.ots_batch_destroy(b)
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_batch > 0:
+        return profile_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
