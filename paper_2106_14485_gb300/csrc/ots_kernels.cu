@@ -418,7 +418,13 @@ __device__ __forceinline__ void srow(const float *hi, const lo_t *lo, int g, flo
 
 }  // namespace
 
-constexpr int kStages = 3;   // shared-memory stages of the pipelined kernels
+// Shared-memory stages per block of the pipelined kernels.  The forward kernel runs three blocks
+// per SM with two stages each (more warps for its issue-bound consumers); the backward kernel,
+// bound by the bytes in flight, runs two blocks with three stages each.
+constexpr int kStagesFwd = 2;
+constexpr int kStagesBwd = 3;
+template <bool FWD>
+struct StagesOf { static constexpr int value = FWD ? kStagesFwd : kStagesBwd; };
 
 // Per-stage metadata written by the producer warp: the work item and everything the consumers
 // would otherwise fetch with dependent global loads.
@@ -486,7 +492,7 @@ template <bool FWD, int Lp, typename Meta>
 __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, float *st_hi, lo_t *st_lo,
                                               uint64_t *full, uint64_t *empty, int rows, bool &timed_out) {
   constexpr int KB = kBatchTma;
-  constexpr int NS = kStages;
+  constexpr int NS = StagesOf<FWD>::value;
   const int lane = threadIdx.x & 31;
   TmaItem it;
   bool have = item_first(a.ptr, a.V, KB, it);
@@ -595,12 +601,12 @@ __device__ __forceinline__ void aggregate_staged(const float *hs, const lo_t *ls
 
 // Forward step, warp-specialised: G consumer threads (one node row) + one producer warp.
 template <int G>
-__global__ void __launch_bounds__(G + 32) k_forward_tma(const StepArgs a) {
+__global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const StepArgs a) {
   constexpr int Lp = 4 * G;
   constexpr int KB = kBatchTma;
   constexpr int ROWS = KB + 1;
   constexpr int NW = G / 32;
-  constexpr int NS = kStages;
+  constexpr int NS = kStagesFwd;
   extern __shared__ __align__(128) unsigned char smem[];
   float *st_hi = reinterpret_cast<float *>(smem);                                    // [NS][ROWS][Lp]
   lo_t *st_lo = reinterpret_cast<lo_t *>(smem + NS * ROWS * Lp * sizeof(float));    // [NS][ROWS][Lp]
@@ -738,7 +744,7 @@ __global__ void __launch_bounds__(G + 32) k_backward_tma(const StepArgs a) {
   constexpr int KB = kBatchTma;
   constexpr int ROWS = KB;
   constexpr int NW = G / 32;
-  constexpr int NS = kStages;
+  constexpr int NS = kStagesBwd;
   extern __shared__ __align__(128) unsigned char smem[];
   float *st_hi = reinterpret_cast<float *>(smem);
   lo_t *st_lo = reinterpret_cast<lo_t *>(smem + NS * ROWS * Lp * sizeof(float));
@@ -820,7 +826,7 @@ static cudaError_t launch_step_g(int G, int C, const StepArgs &a, cudaStream_t s
 
 template <int G>
 static size_t tma_smem(bool fwd) {
-  return (size_t)kStages * (fwd ? kBatchTma + 1 : kBatchTma) * 4 * G * (sizeof(float) + sizeof(lo_t));
+  return (size_t)(fwd ? kStagesFwd : kStagesBwd) * (fwd ? kBatchTma + 1 : kBatchTma) * 4 * G * (sizeof(float) + sizeof(lo_t));
 }
 
 template <int G>
