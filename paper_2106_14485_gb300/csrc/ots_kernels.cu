@@ -422,7 +422,7 @@ __device__ __forceinline__ void srow(const float *hi, const lo_t *lo, int g, flo
 // per SM with two stages each (more warps for its issue-bound consumers); the backward kernel,
 // bound by the bytes in flight, runs two blocks with three stages each.
 constexpr int kStagesFwd = 2;
-constexpr int kStagesBwd = 3;
+constexpr int kStagesBwd = 2;
 template <bool FWD>
 struct StagesOf { static constexpr int value = FWD ? kStagesFwd : kStagesBwd; };
 
@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
 
 // Backward step, warp-specialised like the forward step.
 template <int G>
-__global__ void __launch_bounds__(G + 32) k_backward_tma(const StepArgs a) {
+__global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_backward_tma(const StepArgs a) {
   constexpr int Lp = 4 * G;
   constexpr int KB = kBatchTma;
   constexpr int ROWS = KB;
