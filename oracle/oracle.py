@@ -51,6 +51,8 @@ def _load():
                                ctypes.c_double, _f64p, ctypes.c_int, _f64p,
                                ctypes.c_int, _i32p, _i32p, _f64p, ctypes.c_int, _i32p, _i32p, _f64p]
     lib.orc_destroy.argtypes = [ctypes.c_void_p]
+    lib.orc_set_time_costs.argtypes = [ctypes.c_void_p, _f64p]
+    lib.orc_set_time_costs.restype = ctypes.c_int
     lib.orc_set_threads.argtypes = [ctypes.c_int]
     lib.orc_get_threads.restype = ctypes.c_int
     lib.orc_num_states.argtypes = [ctypes.c_void_p]
@@ -120,6 +122,13 @@ class Oracle:
         if not self.h:
             raise ValueError("oracle rejected the instance")
         self._lib = lib
+        ct = getattr(inst, "state_cost_t", None)
+        if ct is not None:                    # time-varying network: one C_L per interval t
+            ct = np.ascontiguousarray(ct, np.float64)
+            if ct.shape != (self.T - 2, self.S):
+                raise ValueError("state_cost_t must be (T-2) x n_states")
+            if lib.orc_set_time_costs(self.h, ct.reshape(-1)):
+                raise MemoryError("oracle: time-varying costs")
         lib.orc_init_duals(self.h)
 
     def __del__(self):

@@ -15,7 +15,8 @@
  *   states s = directed edges plus one wait loop per node (Section 3.3 vertex augmentation)
  *   K      : line graph, K_ij = 1 iff edge i leads to edge j (head(i) == tail(j)), else 0
  *            (Section 3.1, C_ij = 0 or infinity)
- *   K_L    : exp(-C_L / eps), L x S (Section 3.2, eq. K_multicommodity)
+ *   K_L    : exp(-C_L / eps), L x S (Section 3.2, eq. K_multicommodity); with time-varying
+ *            costs (a time-dependent network, Section 3.3) one K_L per interval t = 2..T-1
  *   d      : capacities per state (inf = none)
  *   R01,R0T: source / sink matrices L x S
  *   duals  : u_t (t = 2..T-1), U01, U0T  (eq. U_multicommodity); stored as logs
@@ -54,7 +55,8 @@ typedef struct orc {
   int *pred_idx;
   int64_t *succ_ptr;           /* [S+1]  succ(i) = { j : head(i) == tail(j) } */
   int *succ_idx;
-  double *logKL;               /* [L*S] */
+  double *logKL;               /* [L*S], or [(T+1)*L*S] (rows t = 2..T-1) when tv */
+  int tv;                      /* time-varying costs set by orc_set_time_costs */
   double *d;                   /* [S] */
   double *R01, *R0T;           /* [L*S] dense */
   double *logu;                /* [T*S], row t (1-based) used for t = 2..T-1 */
@@ -176,6 +178,28 @@ orc *orc_create(int V, int E, const int *esrc, const int *edst, int L, int T, do
   return o;
 }
 
+/* log K_L row of commodity l in interval t (t >= 2). */
+static const double *kl_row(const orc *o, int t, int l) {
+  return o->logKL + ((size_t)(o->tv ? t : 0) * o->L + l) * o->S;
+}
+
+/* Time-varying network (Section 3.3: C replaced by time-dependent C_t): per-interval state
+ * costs cost_t[(t-2)*S + s] for t = 2..T-1, the same for every commodity; +INFINITY closes
+ * state s during interval t.  Replaces the costs given at creation. */
+int orc_set_time_costs(orc *o, const double *cost_t) {
+  const int S = o->S, L = o->L, T = o->T;
+  double *k = (double *)malloc(sizeof(double) * (size_t)(T + 1) * L * S);
+  if (!k) return ORC_NOMEM;
+  for (size_t q = 0; q < (size_t)(T + 1) * L * S; ++q) k[q] = 0.0;
+  for (int t = 2; t <= T - 1; ++t)
+    for (int l = 0; l < L; ++l)
+      for (int s = 0; s < S; ++s) k[((size_t)t * L + l) * S + s] = -cost_t[(size_t)(t - 2) * S + s] / o->eps;
+  free(o->logKL);
+  o->logKL = k;
+  o->tv = 1;
+  return ORC_OK;
+}
+
 int orc_num_states(const orc *o) { return o->S; }
 int64_t orc_nnz(const orc *o) { return o->pred_ptr[o->S]; }
 
@@ -222,7 +246,7 @@ static void fwd_product(const orc *o, const double *x, int t, double *out, int l
   for (int l = l0; l < l1; ++l) {
     for (int j = 0; j < S; ++j) {
       const double *xl = x + (size_t)(l - l0) * S;
-      const double *kl = o->logKL + (size_t)l * S;
+      const double *kl = kl_row(o, t, l);
       double m = -INFINITY;
       for (int64_t k = o->pred_ptr[j]; k < o->pred_ptr[j + 1]; ++k) {
         int i = o->pred_idx[k];
@@ -253,7 +277,7 @@ static void bwd_product(const orc *o, const double *x, int t, double *out, int l
   for (int l = l0; l < l1; ++l) {
     for (int i = 0; i < S; ++i) {
       const double *xl = x + (size_t)(l - l0) * S;
-      const double *kl = o->logKL + (size_t)l * S;
+      const double *kl = kl_row(o, t, l);
       double m = -INFINITY;
       for (int64_t k = o->succ_ptr[i]; k < o->succ_ptr[i + 1]; ++k) {
         int j = o->succ_idx[k];
@@ -276,20 +300,20 @@ static void bwd_product(const orc *o, const double *x, int t, double *out, int l
 }
 
 /* log of the column sums of (hatPsi_t .* Psi_t .* K_L) over commodities: ls[i]. */
-static void col_lse(const orc *o, const double *ph, const double *ps, double *ls) {
+static void col_lse(const orc *o, int t, const double *ph, const double *ps, double *ls) {
   const int S = o->S, L = o->L;
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < S; ++i) {
     double m = -INFINITY;
     for (int l = 0; l < L; ++l) {
-      double v = ph[(size_t)l * S + i] + ps[(size_t)l * S + i] + o->logKL[(size_t)l * S + i];
+      double v = ph[(size_t)l * S + i] + ps[(size_t)l * S + i] + kl_row(o, t, l)[i];
       if (v > m) m = v;
     }
     double r = -INFINITY;
     if (m > -INFINITY) {
       double acc = 0.0;
       for (int l = 0; l < L; ++l)
-        acc += exp(ph[(size_t)l * S + i] + ps[(size_t)l * S + i] + o->logKL[(size_t)l * S + i] - m);
+        acc += exp(ph[(size_t)l * S + i] + ps[(size_t)l * S + i] + kl_row(o, t, l)[i] - m);
       r = m + log(acc);
     }
     ls[i] = r;
@@ -363,7 +387,7 @@ int orc_iteration(orc *o, double *src_resid, double *cap_viol, double *trace) {
   double viol = 0.0;
   for (int t = 2; t <= T - 1; ++t) {
     /* u_t <- min(d ./ ((hatPsi_t .* Psi_t .* K_L)^T 1), 1), excess (P_t - d)_+ taken before */
-    col_lse(o, ph, o->psi + (size_t)t * LS, ls);
+    col_lse(o, t, ph, o->psi + (size_t)t * LS, ls);
     double *lu = o->logu + (size_t)t * S;
     double mass_t = 0.0;
     for (int i = 0; i < S; ++i) {
@@ -472,7 +496,7 @@ int orc_projections(orc *o, int l0, int l1, double *out) {
       /* t = 2..T-1: hatPsi_t .* Psi_t .* K_L .* u_t */
       for (int t = 2; t <= T - 1; ++t)
         out[(size_t)(t - 1) * blk + q] = exp(h[(size_t)(t - 2) * blk + q] + b[(size_t)(t - 1) * blk + q] +
-                                             o->logKL[(size_t)l * S + s] + o->logu[(size_t)t * S + s]);
+                                             kl_row(o, t, l)[s] + o->logu[(size_t)t * S + s]);
       /* t = T: U0T .* hatPsi_T */
       out[(size_t)(T - 1) * blk + q] = exp(o->logU0T[(size_t)l * S + s] + h[(size_t)(T - 2) * blk + q]);
     }

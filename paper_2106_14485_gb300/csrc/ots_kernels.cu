@@ -330,6 +330,7 @@ __global__ void k_boundary_flows(int n, int Lp, QScale qs, const int *tri_l, con
 // wait that gives up records an error in the pass statistics instead of hanging.
 // ------------------------------------------------------------------------------------
 constexpr int kBatchTma = 5;
+constexpr int kBatchBwd = 5;      // out-states per work item of the backward kernel (<= kBatchTma)
 
 namespace {
 
@@ -491,7 +492,7 @@ __device__ __forceinline__ LaneMeta load_lane_meta(const StepArgs &a, const TmaI
 template <bool FWD, int Lp, typename Meta>
 __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, float *st_hi, lo_t *st_lo,
                                               uint64_t *full, uint64_t *empty, int rows, bool &timed_out) {
-  constexpr int KB = kBatchTma;
+  constexpr int KB = FWD ? kBatchTma : kBatchBwd;
   constexpr int NS = StagesOf<FWD>::value;
   const int lane = threadIdx.x & 31;
   TmaItem it;
@@ -741,7 +742,7 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
 template <int G>
 __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_backward_tma(const StepArgs a) {
   constexpr int Lp = 4 * G;
-  constexpr int KB = kBatchTma;
+  constexpr int KB = kBatchBwd;
   constexpr int ROWS = KB;
   constexpr int NW = G / 32;
   constexpr int NS = kStagesBwd;
@@ -826,7 +827,7 @@ static cudaError_t launch_step_g(int G, int C, const StepArgs &a, cudaStream_t s
 
 template <int G>
 static size_t tma_smem(bool fwd) {
-  return (size_t)(fwd ? kStagesFwd : kStagesBwd) * (fwd ? kBatchTma + 1 : kBatchTma) * 4 * G * (sizeof(float) + sizeof(lo_t));
+  return (size_t)(fwd ? kStagesFwd : kStagesBwd) * (fwd ? kBatchTma + 1 : kBatchBwd) * 4 * G * (sizeof(float) + sizeof(lo_t));
 }
 
 template <int G>

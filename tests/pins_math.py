@@ -50,6 +50,15 @@ def cost_matrix(inst) -> np.ndarray:
     return np.tile(c, (inst.L, 1))
 
 
+def cost_at(inst, t: int) -> np.ndarray:
+    """C_L in interval t (1-based, 2..T-1) as an L x S matrix: the per-interval costs of a
+    time-varying network when the instance has them (same for every commodity)."""
+    ct = getattr(inst, "state_cost_t", None)
+    if ct is not None:
+        return np.tile(np.asarray(ct[t - 2], np.float64), (inst.L, 1))
+    return cost_matrix(inst)
+
+
 def capacity(inst) -> np.ndarray:
     return np.concatenate([inst.edge_cap, inst.wait_cap]).astype(np.float64)
 
@@ -66,7 +75,6 @@ class Tensor:
         self.L, self.T, self.S = inst.L, inst.T, inst.n_edges + inst.n_nodes
         self.paths = all_paths(self.S, self.T)                     # [N, T]
         K = dense_K(inst)
-        KL = np.exp(-cost_matrix(inst) / inst.eps)                  # [L, S]
         p = self.paths
         kpath = np.ones(len(p))
         for t in range(self.T - 1):                                 # prod_{t=1}^{T-1} K_{i_t i_{t+1}}
@@ -74,9 +82,10 @@ class Tensor:
         keep = kpath > 0                                            # drop infeasible paths
         self.paths = p[keep]
         self.kpath = kpath[keep]
-        # prod_{t=2}^{T-1} (K_L)_{i_0 i_t}
+        # prod_{t=2}^{T-1} (K_L,t)_{i_0 i_t}  (K_L,t = K_L unless the costs vary with t)
         self.kl = np.ones((self.L, len(self.paths)))
         for t in range(1, self.T - 1):
+            KL = np.exp(-cost_at(inst, t + 1) / inst.eps)          # [L, S], 1-based time t + 1
             self.kl *= KL[:, self.paths[:, t]]
 
     def M(self, u, U01, U0T):

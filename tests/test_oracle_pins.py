@@ -240,3 +240,84 @@ def test_infeasible_sink_is_reported():
     o.backward_sweep()
     with pytest.raises(RuntimeError):
         o.iteration()
+
+
+# ---------------------------------------------------------------------------------------
+# time-varying network (Section 3.3: C replaced by time-dependent C_t)
+# ---------------------------------------------------------------------------------------
+
+def time_varying(inst, seed=0, closures=1):
+    """Per-interval state costs: the static costs scaled per (t, state) by U[0.5, 2], with
+    `closures` random moving edges closed (+inf) in one interval each."""
+    rng = np.random.default_rng(seed)
+    base = np.concatenate([inst.edge_cost, inst.wait_cost]).astype(np.float64)
+    ct = base[None, :] * rng.uniform(0.5, 2.0, (inst.T - 2, base.size))
+    for _ in range(closures):
+        ct[rng.integers(inst.T - 2), rng.integers(inst.n_edges)] = np.inf
+    inst.state_cost_t = ct
+    return inst
+
+
+@pytest.mark.parametrize("T", [4, 5])
+def test_time_varying_projections_match_brute_force(T):
+    inst = time_varying(tiny_instance(seed=20 + T, T=T, per_commodity=False), seed=T, closures=2)
+    o = Oracle(inst)
+    rng = np.random.default_rng(30 + T)
+    S, L = inst.n_states, inst.L
+    R01, R0T = PM.dense_marginals(inst)
+    logu = -rng.uniform(0, 2, (T - 2, S))
+    U01 = rng.uniform(-2, 2, (L, S))
+    U0T = rng.uniform(-2, 2, (L, S))
+    o.set_duals(logu, U01, U0T)
+    P = o.projections()
+    tz = PM.Tensor(inst)
+    u = np.ones((T + 1, S))
+    u[2:T] = np.exp(logu)
+    M = tz.M(u, np.where(R01 > 0, np.exp(U01), 0), np.where(R0T > 0, np.exp(U0T), 0))
+    for t in range(1, T + 1):
+        ref = tz.proj0t(M, t)
+        np.testing.assert_allclose(P[t - 1], ref, rtol=1e-12, atol=1e-14 * max(ref.max(), 1e-300))
+
+
+def test_time_varying_fixed_point_matches_tensor_sinkhorn():
+    inst = time_varying(tiny_instance(seed=7, T=5, L=2, cap_scale=0.8, eps=0.5, per_commodity=False), seed=3,
+                        closures=1)
+    o = Oracle(inst)
+    r = o.solve(max_iters=50000, tol=1e-13)
+    assert r["status"] == 0 and r["src_resid"] < 1e-12 and r["cap_viol"] < 1e-12
+    P = o.projections()
+    tz, M, _ = PM.tensor_sinkhorn(inst)
+    for t in range(1, inst.T + 1):
+        np.testing.assert_allclose(P[t - 1], tz.proj0t(M, t), rtol=1e-7, atol=1e-9)
+
+
+def test_time_constant_costs_and_per_interval_shifts():
+    """Costs that do not vary with t reproduce the static solution; adding a constant to every
+    state's cost in one interval multiplies every path by the same factor, so M_eps does not
+    change; a state closed in an interval carries no flow there."""
+    base = I.rgg_instance(seed=4, n=40, L=3, T=9, eps=0.05, cap_lo=0.3, cap_hi=1.0)
+    o0 = Oracle(base)
+    o0.solve(max_iters=100000, tol=1e-12)
+    F0 = o0.flows()
+    c = np.concatenate([base.edge_cost, base.wait_cost]).astype(np.float64)
+    inst = I.rgg_instance(seed=4, n=40, L=3, T=9, eps=0.05, cap_lo=0.3, cap_hi=1.0)
+    inst.state_cost_t = np.tile(c, (inst.T - 2, 1))
+    o1 = Oracle(inst)
+    o1.solve(max_iters=100000, tol=1e-12)
+    np.testing.assert_allclose(o1.flows(), F0, rtol=1e-10, atol=1e-12)
+    shift = np.linspace(-0.3, 0.7, inst.T - 2)[:, None]
+    inst.state_cost_t = np.tile(c, (inst.T - 2, 1)) + shift
+    o2 = Oracle(inst)
+    o2.solve(max_iters=100000, tol=1e-12)
+    np.testing.assert_allclose(o2.flows(), F0, rtol=1e-8, atol=1e-10)
+    # close the busiest moving edge in interval t = 4
+    ct = np.tile(c, (inst.T - 2, 1))
+    e = int(np.argmax(F0[3, :inst.n_edges]))
+    ct[4 - 2, e] = np.inf
+    inst.state_cost_t = ct
+    o3 = Oracle(inst)
+    r3 = o3.solve(max_iters=100000, tol=1e-12)
+    assert r3["status"] == 0
+    F3 = o3.flows()
+    assert F3[3, e] == 0.0 and F0[3, e] > 1e-3
+    assert abs(F3[0].sum() - F0[0].sum()) < 1e-9 * F0[0].sum()
