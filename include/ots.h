@@ -93,6 +93,12 @@ typedef struct ots_problem_desc {
   ots_alloc_fn alloc;            /* optional device allocator (both or neither) */
   ots_free_fn free_fn;
   void *alloc_ctx;
+  const double *state_cost_t;    /* optional [(T-2) x n_states] row-major: a time-varying
+                                    network (Section 3.3, C replaced by time-dependent C_t):
+                                    the cost of every state in interval t = 2..T-1, the same
+                                    for all commodities; +INFINITY closes a state during that
+                                    interval.  When given, edge_cost and wait_cost are not used;
+                                    not combinable with commodity_cost. */
 } ots_problem_desc;
 
 /* Options of ots_sinkhorn_solve. */

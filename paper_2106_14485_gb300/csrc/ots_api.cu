@@ -95,7 +95,8 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
     a.x_hi = p->b_hi(t + 1); a.x_lo = p->b_lo(t + 1);
     a.out_hi = p->b_hi(t); a.out_lo = p->b_lo(t);
   }
-  a.kl_hi = p->d_kl_hi; a.kl_lo = p->d_kl_lo;
+  const size_t klo = p->tv ? (size_t)t * p->S : 0;   // time-varying costs: row t
+  a.kl_hi = p->d_kl_hi + klo; a.kl_lo = p->d_kl_lo + klo;
   a.klc_hi = p->d_klc_hi; a.klc_lo = p->d_klc_lo;
   a.logd_hi = p->d_logd_hi; a.logd_lo = p->d_logd_lo;
   a.cap = p->d_cap;
@@ -105,7 +106,8 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   a.flow_t = p->d_flow + (size_t)t * p->S;
   a.persist_grid_fwd = p->pgrid_fwd;
   a.persist_grid_bwd = p->pgrid_bwd;
-  a.in_kl_hi = p->d_in_kl_hi; a.in_kl_lo = p->d_in_kl_lo;
+  a.in_kl_hi = p->d_in_kl_hi ? p->d_in_kl_hi + klo : nullptr;
+  a.in_kl_lo = p->d_in_kl_lo ? p->d_in_kl_lo + klo : nullptr;
   a.in_logd_hi = p->d_in_logd_hi; a.in_logd_lo = p->d_in_logd_lo;
   a.in_cap = p->d_in_cap; a.in_outpos = p->d_in_outpos;
   a.lu_in_t = p->d_logu_in + (size_t)t * p->S;
@@ -191,9 +193,9 @@ ots_status build_pass_graph(ots_problem *p) {
 // supports) and recompute the backward messages.
 ots_status reset_duals(ots_problem *p) {
   p->kernels_launched += 2;
-  OTS_CUDA(launch_weights(p->S, p->T, p->qs, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo, p->d_logu,
-                          p->d_w_hi, p->d_w_lo, 1, p->d_st_inpos, p->d_st_outpos, p->d_logu_in, p->d_wout_hi,
-                          p->d_wout_lo, p->stream));
+  OTS_CUDA(launch_weights(p->S, p->T, p->qs, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo,
+                          p->tv ? p->S : 0, p->d_logu, p->d_w_hi, p->d_w_lo, 1, p->d_st_inpos, p->d_st_outpos,
+                          p->d_logu_in, p->d_wout_hi, p->d_wout_lo, p->stream));
   if (p->src.n) OTS_CUDA(cudaMemsetAsync(p->src.d_tri_logU, 0, sizeof(double) * p->src.n, p->stream));
   if (p->snk.n) OTS_CUDA(cudaMemsetAsync(p->snk.d_tri_logU, 0, sizeof(double) * p->snk.n, p->stream));
   OTS_CUDA(cudaMemsetAsync(p->d_report, 0, sizeof(PassReport), p->stream));
@@ -207,9 +209,9 @@ ots_status reset_duals(ots_problem *p) {
 ots_status refresh_if_stale(ots_problem *p) {
   if (!p->stale) return OTS_OK;
   p->kernels_launched += 2;
-  OTS_CUDA(launch_weights(p->S, p->T, p->qs, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo, p->d_logu,
-                          p->d_w_hi, p->d_w_lo, 0, p->d_st_inpos, p->d_st_outpos, p->d_logu_in, p->d_wout_hi,
-                          p->d_wout_lo, p->stream));
+  OTS_CUDA(launch_weights(p->S, p->T, p->qs, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo,
+                          p->tv ? p->S : 0, p->d_logu, p->d_w_hi, p->d_w_lo, 0, p->d_st_inpos, p->d_st_outpos,
+                          p->d_logu_in, p->d_wout_hi, p->d_wout_lo, p->stream));
   OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
   ots_status st = enqueue_backward_sweep(p);
   if (st) return st;
@@ -510,8 +512,24 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   }
 
   // ---- per-state data (costs, capacities) in log2 units ----
-  std::vector<float> kl_hi(p->S), kl_lo(p->S), logd_hi(p->S), logd_lo(p->S);
+  p->tv = d->state_cost_t != nullptr;
+  if (p->tv && d->commodity_cost) return bail(fail(OTS_ERR_INVALID_ARG, "state_cost_t and commodity_cost do not combine"));
+  const size_t KR = p->tv ? (size_t)(p->T + 1) : 1;   // rows of log2 K_L (row t for interval t)
+  std::vector<float> kl_hi(KR * p->S, 0.f), kl_lo(KR * p->S, 0.f), logd_hi(p->S), logd_lo(p->S);
   std::vector<double> cap(p->S);
+  double cmax_tv = 0.0;
+  if (p->tv) {
+    for (int t = 2; t <= p->T - 1; ++t)
+      for (int s = 0; s < p->S; ++s) {
+        const double c = d->state_cost_t[(size_t)(t - 2) * p->S + s];
+        const size_t q = (size_t)t * p->S + s;
+        if (std::isnan(c) || c == -INFINITY)
+          return bail(fail(OTS_ERR_INVALID_ARG, "state_cost_t[%d][%d] must be finite or +inf", t - 2, s));
+        if (c == INFINITY) { kl_hi[q] = kNeg; kl_lo[q] = 0.f; continue; }   // closed in interval t
+        split_ff(-c / d->eps * kInvLn2, kl_hi[q], kl_lo[q]);
+        cmax_tv = std::max(cmax_tv, std::fabs(c) / d->eps * kInvLn2);
+      }
+  }
   for (int s = 0; s < p->S; ++s) {
     double c = 0.0, dd = INFINITY;
     if (s < p->E) {
@@ -522,9 +540,9 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
       if (d->wait_cost) c = d->wait_cost[v];
       if (d->wait_capacity) dd = d->wait_capacity[v];
     }
-    if (!std::isfinite(c)) return bail(fail(OTS_ERR_INVALID_ARG, "state %d: cost must be finite", s));
+    if (!p->tv && !std::isfinite(c)) return bail(fail(OTS_ERR_INVALID_ARG, "state %d: cost must be finite", s));
     if (std::isnan(dd) || dd < 0.0) return bail(fail(OTS_ERR_INVALID_ARG, "state %d: capacity must be >= 0", s));
-    split_ff(-c / d->eps * kInvLn2, kl_hi[s], kl_lo[s]);
+    if (!p->tv) split_ff(-c / d->eps * kInvLn2, kl_hi[s], kl_lo[s]);
     cap[s] = dd;
     if (dd == 0.0) { logd_hi[s] = kNeg; logd_lo[s] = 0.f; }
     else if (std::isinf(dd)) { logd_hi[s] = 0.f; logd_lo[s] = 0.f; }
@@ -533,8 +551,9 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   // quantum of the hi parts: the magnitude of any message is bounded by about (T+1) times the
   // largest per-interval cost in bits; q = 2^k with that bound below 2^24 q keeps hi sums exact
   {
-    double cmax = 0.0;
-    for (int s = 0; s < p->S; ++s) cmax = std::max(cmax, std::fabs((double)kl_hi[s]));
+    double cmax = cmax_tv;
+    if (!p->tv)
+      for (int s = 0; s < p->S; ++s) cmax = std::max(cmax, std::fabs((double)kl_hi[s]));
     if (d->commodity_cost)
       for (size_t k = 0; k < (size_t)p->L * p->S; ++k) cmax = std::max(cmax, std::fabs(d->commodity_cost[k]) / d->eps * kInvLn2);
     const double bound = (p->T + 1.0) * std::max(cmax, 1.0) + 256.0;
@@ -566,7 +585,7 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   std::vector<int> st_inpos(p->S), st_outpos(p->S), in_outpos(p->S);
   for (int k = 0; k < p->S; ++k) { st_inpos[in_state[k]] = k; st_outpos[out_state[k]] = k; }
   for (int k = 0; k < p->S; ++k) in_outpos[k] = st_outpos[in_state[k]];
-  std::vector<float> in_kl_hi(p->S), in_kl_lo(p->S), in_logd_hi(p->S), in_logd_lo(p->S);
+  std::vector<float> in_kl_hi(KR * p->S), in_kl_lo(KR * p->S), in_logd_hi(p->S), in_logd_lo(p->S);
   std::vector<float2> in_cap(p->S), cap2(p->S);
   auto split_cap = [](double dd) {
     if (!(dd < 3.0e38)) return make_float2(INFINITY, 0.f);        // no capacity (or beyond FP32)
@@ -576,7 +595,10 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   for (int k = 0; k < p->S; ++k) cap2[k] = split_cap(cap[k]);
   for (int k = 0; k < p->S; ++k) {
     const int st = in_state[k];
-    in_kl_hi[k] = kl_hi[st]; in_kl_lo[k] = kl_lo[st];
+    for (size_t r = 0; r < KR; ++r) {
+      in_kl_hi[r * p->S + k] = kl_hi[r * p->S + st];
+      in_kl_lo[r * p->S + k] = kl_lo[r * p->S + st];
+    }
     in_logd_hi[k] = logd_hi[st]; in_logd_lo[k] = logd_lo[st];
     in_cap[k] = cap2[st];
   }
@@ -689,14 +711,16 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   size_t o_in_ptr = cv.take<int>(V + 1), o_in_state = cv.take<int>(S), o_in_nbr = cv.take<int>(S);
   size_t o_out_ptr = cv.take<int>(V + 1), o_out_state = cv.take<int>(S), o_out_nbr = cv.take<int>(S);
   size_t o_tail = cv.take<int>(S), o_head = cv.take<int>(S);
-  size_t o_kl_hi = cv.take<float>(S), o_kl_lo = cv.take<float>(S), o_ld_hi = cv.take<float>(S), o_ld_lo = cv.take<float>(S);
+  const size_t KR = p->tv ? T + 1 : 1;
+  size_t o_kl_hi = cv.take<float>(KR * S), o_kl_lo = cv.take<float>(KR * S), o_ld_hi = cv.take<float>(S),
+         o_ld_lo = cv.take<float>(S);
   size_t o_cap = cv.take<float2>(S);
   size_t o_klc_hi = p->pc ? cv.take<float>(S * p->Lp) : 0, o_klc_lo = p->pc ? cv.take<lo_t>(S * p->Lp) : 0;
   size_t o_w_hi = cv.take<float>((T + 1) * S), o_w_lo = cv.take<float>((T + 1) * S);
   size_t o_logu = cv.take<float2>((T + 1) * S), o_flow = cv.take<double>((T + 1) * S);
   const size_t Sc = csr_copies ? S : 0;
   size_t o_st_inpos = cv.take<int>(Sc), o_st_outpos = cv.take<int>(Sc), o_in_outpos = cv.take<int>(Sc);
-  size_t o_in_kl_hi = cv.take<float>(Sc), o_in_kl_lo = cv.take<float>(Sc), o_in_ld_hi = cv.take<float>(Sc),
+  size_t o_in_kl_hi = cv.take<float>(KR * Sc), o_in_kl_lo = cv.take<float>(KR * Sc), o_in_ld_hi = cv.take<float>(Sc),
          o_in_ld_lo = cv.take<float>(Sc), o_in_cap = cv.take<float2>(Sc);
   size_t o_logu_in = cv.take<float2>((T + 1) * Sc), o_wout_hi = cv.take<float>((T + 1) * Sc),
          o_wout_lo = cv.take<float>((T + 1) * Sc);
@@ -966,7 +990,8 @@ ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_en
     if (t >= t_begin && t < t_end) {
       // A_{t-1} is current here (written by the previous forward step of this pass)
       check(launch_commodity_flows(p->S, p->Lp, p->qs, l_begin, l_end, p->d_tail, p->d_head, p->a_hi(t - 1), p->a_lo(t - 1),
-                                   p->b_hi(t + 1), p->b_lo(t + 1), p->d_kl_hi, p->d_kl_lo, p->d_klc_hi, p->d_klc_lo,
+                                   p->b_hi(t + 1), p->b_lo(t + 1), p->d_kl_hi + (p->tv ? t * S : 0),
+                                   p->d_kl_lo + (p->tv ? t * S : 0), p->d_klc_hi, p->d_klc_lo,
                                    p->d_logu + (size_t)t * S, d_tmp, p->stream));
       check(cudaMemcpyAsync(out + (size_t)(t - t_begin) * blk, d_tmp, sizeof(double) * blk, cudaMemcpyDeviceToHost,
                             p->stream));
@@ -1079,7 +1104,8 @@ ots_status ots_get_commodity_flows_noalloc(ots_problem *p, int32_t t_begin, int3
   for (int t = 2; t <= p->T - 1; ++t) {
     if (t >= t_begin && t < t_end) {
       OTS_CUDA(launch_commodity_flows(p->S, p->Lp, p->qs, l_begin, l_end, p->d_tail, p->d_head, p->a_hi(t - 1),
-                                      p->a_lo(t - 1), p->b_hi(t + 1), p->b_lo(t + 1), p->d_kl_hi, p->d_kl_lo,
+                                      p->a_lo(t - 1), p->b_hi(t + 1), p->b_lo(t + 1),
+                                      p->d_kl_hi + (p->tv ? t * S : 0), p->d_kl_lo + (p->tv ? t * S : 0),
                                       p->d_klc_hi, p->d_klc_lo, p->d_logu + (size_t)t * S, slice, p->stream));
       OTS_CUDA(cudaMemcpyAsync(out + (size_t)(t - t_begin) * blk, slice, sizeof(double) * blk,
                                cudaMemcpyDeviceToHost, p->stream));

@@ -44,7 +44,8 @@ struct alignas(16) BatchInst {
   int rounds, npi, pad1, pad2;           // npi: nodes per item = rounds * npb
   QScale qs;
   double mass, eps, tol;
-  int max_passes, pad;
+  int max_passes;
+  int kl_stride;                 // S when the costs vary with the interval t (row t of kl), else 0
   const int *in_ptr, *in_state, *in_nbr, *out_ptr, *out_state, *out_nbr;
   const float *kl_hi, *kl_lo, *logd_hi, *logd_lo;
   const float2 *cap;             // [S] d as a float-float

@@ -78,7 +78,7 @@ __device__ __forceinline__ StepArgs step_of(const BatchInst &I, bool fwd, int t,
     a.x_hi = I.b_hi + (size_t)(t - 1) * pan; a.x_lo = I.b_lo + (size_t)(t - 1) * pan;   // B_{t+1}
     a.out_hi = I.b_hi + (size_t)(t - 2) * pan; a.out_lo = I.b_lo + (size_t)(t - 2) * pan;
   }
-  a.kl_hi = I.kl_hi; a.kl_lo = I.kl_lo;
+  a.kl_hi = I.kl_hi + (size_t)t * I.kl_stride; a.kl_lo = I.kl_lo + (size_t)t * I.kl_stride;
   a.logd_hi = I.logd_hi; a.logd_lo = I.logd_lo;
   a.cap = I.cap;
   a.lu_t = I.lu + (size_t)t * I.S;
@@ -364,9 +364,10 @@ __device__ void setup_item(const BatchInst &I, int k) {
   }
   const int s0 = (int)((long long)k * I.S / I.n_items), s1 = (int)((long long)(k + 1) * I.S / I.n_items);
   for (int s = s0 + threadIdx.x; s < s1; s += kTickBlock) {
-    float wh, wl;
-    make_w(I.kl_hi[s], I.kl_lo[s], 0.f, 0.f, I.qs, wh, wl);
     for (int t = 2; t <= I.T - 1; ++t) {
+      const size_t kq = (size_t)t * I.kl_stride + s;
+      float wh, wl;
+      make_w(I.kl_hi[kq], I.kl_lo[kq], 0.f, 0.f, I.qs, wh, wl);
       I.lu[(size_t)t * I.S + s] = make_float2(0.f, 0.f);
       I.w_hi[(size_t)t * I.S + s] = wh;
       I.w_lo[(size_t)t * I.S + s] = wl;

@@ -20,7 +20,7 @@ cudaError_t launch_boundary(const BndArgs &b, cudaStream_t s);
 int boundary_grid(int n_seg);
 cudaError_t launch_pass_begin(DevStats *st, cudaStream_t s);
 cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, cudaStream_t s);
-cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, float2 *logu,
+cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, int kl_stride, float2 *logu,
                            float *w_hi, float *w_lo, int reset, const int *st_inpos, const int *st_outpos,
                            float2 *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s);
 cudaError_t launch_fill_panel(size_t n, float *hi, lo_t *lo, cudaStream_t s);
@@ -135,6 +135,7 @@ struct ots_problem {
   int pgrid_fwd = 0, pgrid_bwd = 0;            // grids of the pipelined persistent kernels (0 = not used)
   bool pc = false;
   bool member = false;                         // lives in a batch (see CreateOpts)
+  bool tv = false;                             // time-varying costs: K_L rows per interval t
   std::unique_ptr<ots_host::HostArrays> host;  // between the host build and the upload
 
   std::vector<int> tail, head;

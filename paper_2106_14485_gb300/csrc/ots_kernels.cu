@@ -261,7 +261,8 @@ __global__ void k_pass_end(const DevStats *st, PassReport *rep, double mass, dou
 }
 
 // W_t = log2 K_L + log2 u_t for t = 2..T-1 from log2 u (set to 0 first when reset).
-__global__ void k_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, float2 *lu2, float *w_hi,
+__global__ void k_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, int kl_stride, float2 *lu2,
+                          float *w_hi,
                           float *w_lo, int reset, const int *st_inpos, const int *st_outpos, float2 *lu2_in,
                           float *wout_hi, float *wout_lo) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -271,7 +272,8 @@ __global__ void k_weights(int S, int T, QScale qs, const float *kl_hi, const flo
     float2 lu = lu2[(size_t)t * S + s];
     if (lu.x < kNegThresh) lu = make_float2(kNeg, 0.f);
     float hi, lo;
-    make_w(kl_hi ? kl_hi[s] : 0.f, kl_lo ? kl_lo[s] : 0.f, lu.x, lu.y, qs, hi, lo);
+    const size_t kq = (size_t)t * kl_stride + s;   // kl_stride = S for time-varying costs, else 0
+    make_w(kl_hi ? kl_hi[kq] : 0.f, kl_lo ? kl_lo[kq] : 0.f, lu.x, lu.y, qs, hi, lo);
     w_hi[(size_t)t * S + s] = hi;
     w_lo[(size_t)t * S + s] = lo;
     lu2_in[(size_t)t * S + st_inpos[s]] = lu;
@@ -900,10 +902,10 @@ cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, do
   return cudaGetLastError();
 }
 
-cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, float2 *logu,
+cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, int kl_stride, float2 *logu,
                            float *w_hi, float *w_lo, int reset, const int *st_inpos, const int *st_outpos,
                            float2 *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s) {
-  k_weights<<<(S + 255) / 256, 256, 0, s>>>(S, T, qs, kl_hi, kl_lo, logu, w_hi, w_lo, reset, st_inpos, st_outpos,
+  k_weights<<<(S + 255) / 256, 256, 0, s>>>(S, T, qs, kl_hi, kl_lo, kl_stride, logu, w_hi, w_lo, reset, st_inpos, st_outpos,
                                             logu_in, wout_hi, wout_lo);
   return cudaGetLastError();
 }

@@ -276,7 +276,7 @@ __device__ __forceinline__ void lse_merge(float &m, float &s, float om, float os
 // W = log2 K_L + log2 u as (hi on the q grid, float lo).
 __device__ __forceinline__ void make_w(float kl_hi, float kl_lo, float lu_hi, float lu_lo, const QScale &qs,
                                        float &w_hi, float &w_lo) {
-  if (lu_hi < kNegThresh) {
+  if (lu_hi < kNegThresh || kl_hi < kNegThresh) {   // u = 0, or the state is closed in this interval
     w_hi = kNeg;
     w_lo = 0.f;
     return;

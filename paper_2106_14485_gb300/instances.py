@@ -50,6 +50,7 @@ class Instance:
     snk_mass: np.ndarray          # float64 [n_snk]
     pos: Optional[np.ndarray] = None              # [V, 2] node positions (not used by solvers)
     commodity_cost: Optional[np.ndarray] = None   # [L, S] per-commodity state costs
+    state_cost_t: Optional[np.ndarray] = None     # [T-2, S] per-interval state costs (t = 2..T-1)
     meta: dict = field(default_factory=dict)
 
     # ---- derived sizes / per-state views (data assembly only) ----
@@ -347,6 +348,19 @@ def config4(seed: int = 0, count: int = 256, workers: int = 1):
     import multiprocessing as mp
     with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(_config4_member, specs, chunksize=4))
+
+
+def with_time_varying_costs(inst, seed: int = 0, lo: float = 0.5, hi: float = 2.0, closures: int = 0):
+    """A time-varying network for an instance (Section 3.3, C_t): the per-interval cost of every
+    state is its static cost times U[lo, hi], drawn per (t, state) for t = 2..T-1, and
+    `closures` random moving edges are closed (+inf) during one random interval each."""
+    rng = np.random.default_rng(seed)
+    base = inst.state_cost()
+    ct = base[None, :] * rng.uniform(lo, hi, (inst.T - 2, base.size))
+    for _ in range(closures):
+        ct[rng.integers(inst.T - 2), rng.integers(inst.n_edges)] = np.inf
+    inst.state_cost_t = ct
+    return inst
 
 
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4}

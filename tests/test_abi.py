@@ -94,3 +94,20 @@ def test_oracle_is_not_imported_by_the_product():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, flags=re.M), f
                 assert "libots_oracle" not in txt and "ots_oracle" not in txt, f
+
+
+def test_time_varying_costs_are_validated_on_the_host():
+    """Rejected before any device work: wrong combination and invalid values."""
+    import numpy as np
+    from paper_2106_14485_gb300 import instances as I, ots
+    inst = I.rgg_instance(seed=3, n=30, L=2, T=6, eps=0.1)
+    inst.state_cost_t = np.ones((inst.T - 2, inst.n_states))
+    inst.commodity_cost = np.ones((inst.L, inst.n_states))
+    with pytest.raises(ots.OTSError) as e:
+        ots.ots_create_problem(inst, allocator="cuda")
+    assert e.value.code == ots.OTS_ERR_INVALID_ARG
+    inst.commodity_cost = None
+    inst.state_cost_t[1, 3] = np.nan
+    with pytest.raises(ots.OTSError) as e:
+        ots.ots_create_problem(inst, allocator="cuda")
+    assert e.value.code == ots.OTS_ERR_INVALID_ARG
