@@ -111,6 +111,7 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   a.in_logd_hi = p->d_in_logd_hi; a.in_logd_lo = p->d_in_logd_lo;
   a.in_cap = p->d_in_cap; a.in_outpos = p->d_in_outpos;
   a.lu_in_t = p->d_logu_in + (size_t)t * p->S;
+  a.cref_in_t = p->d_cref_in ? p->d_cref_in + (size_t)t * p->S : nullptr;
   a.wout_hi_t = p->d_wout_hi + (size_t)t * p->S;
   a.wout_lo_t = p->d_wout_lo + (size_t)t * p->S;
   a.partials = p->d_partials;
@@ -723,7 +724,7 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   size_t o_in_kl_hi = cv.take<float>(KR * Sc), o_in_kl_lo = cv.take<float>(KR * Sc), o_in_ld_hi = cv.take<float>(Sc),
          o_in_ld_lo = cv.take<float>(Sc), o_in_cap = cv.take<float2>(Sc);
   size_t o_logu_in = cv.take<float2>((T + 1) * Sc), o_wout_hi = cv.take<float>((T + 1) * Sc),
-         o_wout_lo = cv.take<float>((T + 1) * Sc);
+         o_wout_lo = cv.take<float>((T + 1) * Sc), o_cref_in = cv.take<float>((T + 1) * Sc);
   size_t o_a_hi[3], o_a_lo[3];
   for (int k = 0; k < 3; ++k) { o_a_hi[k] = cv.take<float>(panel); o_a_lo[k] = cv.take<lo_t>(panel); }
   size_t o_b_hi = cv.take<float>((T - 1) * panel), o_b_lo = cv.take<lo_t>((T - 1) * panel);
@@ -758,6 +759,7 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
     p->d_in_logd_hi = (float *)at(o_in_ld_hi); p->d_in_logd_lo = (float *)at(o_in_ld_lo);
     p->d_in_cap = (float2 *)at(o_in_cap);
     p->d_logu_in = (float2 *)at(o_logu_in); p->d_wout_hi = (float *)at(o_wout_hi); p->d_wout_lo = (float *)at(o_wout_lo);
+    p->d_cref_in = (float *)at(o_cref_in);
   }
   for (int k = 0; k < 3; ++k) { p->d_a_hi[k] = (float *)at(o_a_hi[k]); p->d_a_lo[k] = (lo_t *)at(o_a_lo[k]); }
   p->d_b_hi = (float *)at(o_b_hi); p->d_b_lo = (lo_t *)at(o_b_lo);
@@ -806,7 +808,8 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
     return bail(fail(OTS_ERR_CUDA, "memset failed"));
   // logu rows outside 2..T-1 stay 0; W rows likewise unused
   if (cudaMemsetAsync(p->d_logu, 0, sizeof(float2) * (T + 1) * S, p->stream) != cudaSuccess ||
-      cudaMemsetAsync(p->d_logu_in, 0, sizeof(float2) * (T + 1) * S, p->stream) != cudaSuccess)
+      cudaMemsetAsync(p->d_logu_in, 0, sizeof(float2) * (T + 1) * S, p->stream) != cudaSuccess ||
+      cudaMemsetAsync(p->d_cref_in, 0xff, sizeof(float) * (T + 1) * S, p->stream) != cudaSuccess)   // NaN: none yet
     return bail(fail(OTS_ERR_CUDA, "memset failed"));
   // boundary panels start at log 0 everywhere; only the support entries are rewritten
   p->kernels_launched += 2;

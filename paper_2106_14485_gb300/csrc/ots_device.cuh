@@ -108,6 +108,7 @@ struct StepArgs {
   float2 *lu_in_t;            // [S] log2 u_t by in-CSR position
   float *wout_hi_t;           // [S] W_t by out-CSR position
   float *wout_lo_t;
+  float *cref_in_t;           // [S] by in-CSR position: column maximum of an earlier pass (NaN: none)
 };
 
 // Boundary kernels (sources, sinks): segments of (node, commodity) with their triples.

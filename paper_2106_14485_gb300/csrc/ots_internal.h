@@ -158,6 +158,7 @@ struct ots_problem {
   float *d_in_kl_hi = nullptr, *d_in_kl_lo = nullptr, *d_in_logd_hi = nullptr, *d_in_logd_lo = nullptr;
   float2 *d_in_cap = nullptr;
   float2 *d_logu_in = nullptr;                 // [T+1][S] by in-CSR position
+  float *d_cref_in = nullptr;                  // [T+1][S] column references by in-CSR position
   float *d_wout_hi = nullptr, *d_wout_lo = nullptr;  // [T+1][S] by out-CSR position
   double *d_flow = nullptr;                    // [T+1][S]
   float *d_a_hi[3] = {nullptr, nullptr, nullptr};

@@ -438,6 +438,8 @@ struct FwdMeta {
   float w_hi[kBatchTma], w_lo[kBatchTma];      // flows mode: the stored weights
   float2 cap[kBatchTma], lu_old[kBatchTma];
   int fin[kBatchTma];                           // capacity finite
+  float cref[kBatchTma];                        // column references (0 for k >= nb)
+  int use_ref;                                  // every in-state of the item has a reference
 };
 
 struct BwdMeta {
@@ -461,7 +463,7 @@ __device__ __forceinline__ void consumers_sync() {
 // Per-lane metadata of one work item (lane k < nb holds in-state / out-state k).
 struct LaneMeta {
   int nbr, st, outpos;
-  float kl_hi, kl_lo, logd_hi, logd_lo, w_hi, w_lo;
+  float kl_hi, kl_lo, logd_hi, logd_lo, w_hi, w_lo, cref;
   float2 cap, lu_old;
 };
 
@@ -481,6 +483,7 @@ __device__ __forceinline__ LaneMeta load_lane_meta(const StepArgs &a, const TmaI
       r.logd_lo = a.in_logd_lo[j];
       r.cap = a.in_cap[j];
       r.lu_old = a.lu_in_t[j];
+      r.cref = a.cref_in_t[j];
     } else {
       r.w_hi = a.wout_hi_t[j];
       r.w_lo = a.wout_lo_t[j];
@@ -514,6 +517,8 @@ __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, flo
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (!ok) { timed_out = true; return; }
     Meta &m = meta[s];
+    int use_ref = 0;
+    if constexpr (FWD) use_ref = __all_sync(0xffffffffu, !(have && lane < it.nb) || lm.cref > kNegThresh) ? 1 : 0;
     if (have && lane < it.nb) {
       m.nbr[lane] = lm.nbr;
       if constexpr (FWD) {
@@ -523,12 +528,17 @@ __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, flo
         m.cap[lane] = lm.cap; m.lu_old[lane] = lm.lu_old;
         m.fin[lane] = lm.cap.x < INFINITY ? 1 : 0;
         m.w_hi[lane] = lm.w_hi; m.w_lo[lane] = lm.w_lo;
+        m.cref[lane] = lm.cref;
       } else {
         m.w_hi[lane] = lm.w_hi; m.w_lo[lane] = lm.w_lo;
       }
     }
+    if constexpr (FWD) {
+      if (have && lane >= it.nb && lane < KB) m.cref[lane] = 0.f;
+    }
     if (lane == 0) {
       m.valid = have ? 1 : 0;
+      if constexpr (FWD) m.use_ref = use_ref;
       if (have) {
         m.v = it.v; m.j0 = it.j0; m.nb = it.nb;
         m.last = (!have_nx || nx.v != it.v) ? 1 : 0;
@@ -566,37 +576,33 @@ __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, flo
 }
 
 // Consumer aggregation of one staged item into the running (M, acc) of the thread's 4 entries.
+// Branch-free: rows k >= nb hold finite stale data and carry wh[k] = log2 0, so their terms
+// vanish; a batch with nothing reachable leaves M below kNegThresh (encoded as log2 0).
 template <int KB>
-__device__ __forceinline__ void aggregate_staged(const float *hs, const lo_t *ls, int Lp, int g, int nb,
+__device__ __forceinline__ void aggregate_staged(const float *hs, const lo_t *ls, int Lp, int g,
                                                  const float (&wh)[KB], const float (&wlb)[KB], float lo_unit,
                                                  float (&M)[4], float (&acc)[4]) {
   float hk[KB][4];
   uint32_t wk[KB][2];
 #pragma unroll
-  for (int k = 0; k < KB; ++k)
-    if (k < nb) srow(hs + k * Lp, ls + k * Lp, g, hk[k], wk[k]);
+  for (int k = 0; k < KB; ++k) srow(hs + k * Lp, ls + k * Lp, g, hk[k], wk[k]);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     float sv[KB];
     float m = 2.f * kNeg;
 #pragma unroll
     for (int k = 0; k < KB; ++k) {
-      sv[k] = k < nb ? hk[k][q] + wh[k] : 2.f * kNeg;
+      sv[k] = hk[k][q] + wh[k];
       m = fmaxf(m, sv[k]);
     }
-    if (m > kNegThresh) {
-      float sum = 0.f;
+    float sum = 0.f;
 #pragma unroll
-      for (int k = 0; k < KB; ++k)
-        if (k < nb) sum += ex2(fmaf(lo_inj(wk[k], q), lo_unit, (sv[k] - m) + wlb[k]));
-      const float Mo = M[q];
-      if (m > Mo) {
-        acc[q] = fmaf(acc[q], ex2(Mo - m), sum);
-        M[q] = m;
-      } else {
-        acc[q] = fmaf(sum, ex2(m - Mo), acc[q]);
-      }
-    }
+    for (int k = 0; k < KB; ++k) sum += ex2(fmaf(lo_inj(wk[k], q), lo_unit, (sv[k] - m) + wlb[k]));
+    const float Mo = M[q];
+    const bool up = m > Mo;
+    const float e = ex2(-fabsf(Mo - m));
+    acc[q] = fmaf(up ? acc[q] : sum, e, up ? sum : acc[q]);
+    M[q] = fmaxf(Mo, m);
   }
 }
 
@@ -615,7 +621,7 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
   lo_t *st_lo = reinterpret_cast<lo_t *>(smem + NS * ROWS * Lp * sizeof(float));    // [NS][ROWS][Lp]
   __shared__ __align__(8) uint64_t full[NS], empty[NS];
   __shared__ FwdMeta meta[NS];
-  __shared__ float xch[2][2 * KB * NW];
+  __shared__ float xch[2][2 * KB * NW], xref[2][KB * NW];
   const int g = threadIdx.x, lane = g & 31, wid = g >> 5;
   if (g == 0) {
     for (int k = 0; k < NS; ++k) {
@@ -623,6 +629,12 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
       mbar_init(smem_u32(&empty[k]), NW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    // finite contents for the rows an item does not fill (the consumers read all KB rows)
+    float4 *z = reinterpret_cast<float4 *>(smem);
+    constexpr int n16 = (int)(NS * ROWS * Lp * (sizeof(float) + sizeof(lo_t)) / 16);
+    for (int k = g; k < n16; k += G + 32) z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
   float viol = 0.f;
@@ -652,45 +664,86 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
 #pragma unroll
         for (int q = 0; q < 4; ++q) blb[q] = lo_inj(w, q) - 2.f * kLoBias;   // exact
       }
-      // (1) column log-sum-exp per in-state: warp max, then warp sum of ex2 terms
-      float cm[KB], cs[KB];
+      // (1) column log-sum-exp per in-state, log2 sum_l 2^(A_{t-1}[tail, l] + B_{t+1}[v, l]).
+      // With a stored reference r (the column maximum of an earlier pass, on the q grid) the
+      // sum is taken as 2^r sum_l 2^(x_l - r): one warp sum per in-state and no maximum.  It
+      // is kept when the total lies in [2^-8, 2^12] (no overflow, nothing significant below
+      // the FP32 range, arguments of the dominant terms within a few tens of bits); otherwise,
+      // or without a reference, the maximum is taken first.  The decision is the same in every
+      // warp (identical sums in the same order), so the barriers match.
+      float mk = 0.f, sk_ = 0.f;
+      bool exact = m.use_ref == 0;
+      if (!exact) {
+        float cs[KB];
 #pragma unroll
-      for (int k = 0; k < KB; ++k) {
-        float mm = 2.f * kNeg;
-        if (k < nb) {
-          const float4 x = reinterpret_cast<const float4 *>(hs + (1 + k) * Lp)[g];
-          mm = fmaxf(fmaxf(x.x + bh[0], x.y + bh[1]), fmaxf(x.z + bh[2], x.w + bh[3]));
-        }
-        cm[k] = mm;
-      }
-      group_reduce<32, KB, true>(cm, nullptr);
-#pragma unroll
-      for (int k = 0; k < KB; ++k) {
-        float sum = 0.f;
-        if (k < nb && cm[k] > kNegThresh) {
+        for (int k = 0; k < KB; ++k) {
           float h[4];
           uint32_t w[2];
           srow(hs + (1 + k) * Lp, ls + (1 + k) * Lp, g, h, w);
+          const float r = m.cref[k];
+          float sum = 0.f;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) sum += ex2(fmaf(lo_inj(w, q) + blb[q], lo_unit, (h[q] + bh[q]) - r));
+          cs[k] = sum;
+        }
+        group_reduce<32, KB, false>(cs, nullptr);
+        sk_ = cs[0];
+#pragma unroll
+        for (int k = 1; k < KB; ++k)
+          if (k == lane) sk_ = cs[k];
+        float *xb = xref[i & 1];
+        if (lane < nb) xb[lane * NW + wid] = sk_;
+        consumers_sync<G>();
+        bool ok = true;
+        if (lane < nb) {
+          sk_ = xb[lane * NW];
+#pragma unroll
+          for (int w = 1; w < NW; ++w) sk_ += xb[lane * NW + w];
+          mk = m.cref[lane];
+          ok = sk_ >= 0x1p-8f && sk_ <= 0x1p12f;
+        }
+        exact = !__all_sync(0xffffffffu, ok);
+      }
+      if (exact) {
+        // warp max, then warp sum of ex2 terms (all KB rows, branch-free; the pairs of rows
+        // k >= nb are finite and never used)
+        float cm[KB], cs[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          const float4 x = reinterpret_cast<const float4 *>(hs + (1 + k) * Lp)[g];
+          cm[k] = fmaxf(fmaxf(x.x + bh[0], x.y + bh[1]), fmaxf(x.z + bh[2], x.w + bh[3]));
+        }
+        group_reduce<32, KB, true>(cm, nullptr);
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          float h[4];
+          uint32_t w[2];
+          srow(hs + (1 + k) * Lp, ls + (1 + k) * Lp, g, h, w);
+          float sum = 0.f;
 #pragma unroll
           for (int q = 0; q < 4; ++q) sum += ex2(fmaf(lo_inj(w, q) + blb[q], lo_unit, (h[q] + bh[q]) - cm[k]));
+          cs[k] = sum;
         }
-        cs[k] = sum;
-      }
-      group_reduce<32, KB, false>(cs, nullptr);
-      // (2) exchange the warps' pairs; lane k of every warp merges in-state k and derives W
-      float mk = cm[0], sk_ = cs[0];
+        group_reduce<32, KB, false>(cs, nullptr);
+        // exchange the warps' pairs; lane k of every warp merges in-state k
+        mk = cm[0];
+        sk_ = cs[0];
 #pragma unroll
-      for (int k = 1; k < KB; ++k)
-        if (k == lane) { mk = cm[k]; sk_ = cs[k]; }
-      float *xb = xch[i & 1];
-      if (lane < nb) { xb[(2 * lane) * NW + wid] = mk; xb[(2 * lane + 1) * NW + wid] = sk_; }
-      consumers_sync<G>();
+        for (int k = 1; k < KB; ++k)
+          if (k == lane) { mk = cm[k]; sk_ = cs[k]; }
+        float *xb = xch[i & 1];
+        if (lane < nb) { xb[(2 * lane) * NW + wid] = mk; xb[(2 * lane + 1) * NW + wid] = sk_; }
+        consumers_sync<G>();
+        if (lane < nb) {
+          mk = xb[(2 * lane) * NW];
+          sk_ = xb[(2 * lane + 1) * NW];
+#pragma unroll
+          for (int w = 1; w < NW; ++w) lse_merge(mk, sk_, xb[(2 * lane) * NW + w], xb[(2 * lane + 1) * NW + w]);
+        }
+      }
+      // (2) lane k of every warp derives W for in-state k
       float mh = kNeg, ml = 0.f;
       if (lane < nb) {
-        mk = xb[(2 * lane) * NW];
-        sk_ = xb[(2 * lane + 1) * NW];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) lse_merge(mk, sk_, xb[(2 * lane) * NW + w], xb[(2 * lane + 1) * NW + w]);
         // every warp derives W (FP32); warp 0 alone does the FP64 part and the stores
         float col_hi, col_lo, lu_hi, lu_lo;
         update_w(a.mode, a.qs, mk, sk_, m.kl_hi[lane], m.kl_lo[lane], m.logd_hi[lane], m.logd_lo[lane],
@@ -701,6 +754,7 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
           update_stats(a.mode, col_hi, col_lo, lu_hi, lu_lo, m.logd_hi[lane], m.logd_lo[lane], mh, m.cap[lane],
                        m.lu_old[lane], lu_new, flow, viol, dual);
           const int st = m.st[lane];
+          if (exact) a.cref_in_t[m.j0 + lane] = mk;    // the column maximum: next pass's reference
           if (a.mode == 0) {
             a.lu_t[st] = lu_new;
             a.lu_in_t[m.j0 + lane] = lu_new;
@@ -720,7 +774,7 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
         wlb[k] = __shfl_sync(0xffffffffu, ml, k) - kLoBias * lo_unit;
       }
       // (3) A_t[v] accumulates A_{t-1}[y] + W_t[state] over the item's in-states
-      aggregate_staged<KB>(hs + Lp, ls + Lp, Lp, g, nb, wh, wlb, lo_unit, M, acc);
+      aggregate_staged<KB>(hs + Lp, ls + Lp, Lp, g, wh, wlb, lo_unit, M, acc);
       if (m.last) {
         float oh[4];
         lo_t ol[4];
@@ -761,6 +815,12 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_backward_tma(const
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  {
+    // finite contents for the rows an item does not fill (the consumers read all KB rows)
+    float4 *z = reinterpret_cast<float4 *>(smem);
+    constexpr int n16 = (int)(NS * ROWS * Lp * (sizeof(float) + sizeof(lo_t)) / 16);
+    for (int k = g; k < n16; k += G + 32) z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   __syncthreads();
   bool timed_out = false;
   if (wid == NW) {
@@ -782,7 +842,7 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_backward_tma(const
         wh[k] = k < nb ? m.w_hi[k] : kNeg;
         wlb[k] = (k < nb ? m.w_lo[k] : 0.f) - kLoBias * lo_unit;
       }
-      aggregate_staged<KB>(st_hi + s * ROWS * Lp, st_lo + s * ROWS * Lp, Lp, g, nb, wh, wlb, lo_unit, M, acc);
+      aggregate_staged<KB>(st_hi + s * ROWS * Lp, st_lo + s * ROWS * Lp, Lp, g, wh, wlb, lo_unit, M, acc);
       if (m.last) {
         float oh[4];
         lo_t ol[4];
