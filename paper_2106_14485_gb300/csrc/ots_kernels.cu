@@ -424,6 +424,7 @@ __device__ __forceinline__ void srow(const float *hi, const lo_t *lo, int g, flo
 // Shared-memory stages per block of the pipelined kernels.  The forward kernel runs three blocks
 // per SM with two stages each (more warps for its issue-bound consumers); the backward kernel,
 // bound by the bytes in flight, runs two blocks with three stages each.
+constexpr int kTmaChunks256 = 2;   // chunks of 4 commodities per consumer thread for rows of 1024
 constexpr int kStagesFwd = 2;
 constexpr int kStagesBwd = 2;
 template <bool FWD>
@@ -581,7 +582,7 @@ __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, flo
 template <int KB>
 __device__ __forceinline__ void aggregate_staged(const float *hs, const lo_t *ls, int Lp, int g,
                                                  const float (&wh)[KB], const float (&wlb)[KB], float lo_unit,
-                                                 float (&M)[4], float (&acc)[4]) {
+                                                 float *M, float *acc) {
   float hk[KB][4];
   uint32_t wk[KB][2];
 #pragma unroll
@@ -608,10 +609,11 @@ __device__ __forceinline__ void aggregate_staged(const float *hs, const lo_t *ls
 
 }  // namespace
 
-// Forward step, warp-specialised: G consumer threads (one node row) + one producer warp.
-template <int G>
-__global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const StepArgs a) {
-  constexpr int Lp = 4 * G;
+// Forward step, warp-specialised: G consumer threads (one node row, CH chunks of 4 commodities
+// per thread: entries 4 (c G + g) .. + 3) + one producer warp.
+template <int G, int CH>
+__global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_forward_tma(const StepArgs a) {
+  constexpr int Lp = 4 * G * CH;
   constexpr int KB = kBatchTma;
   constexpr int ROWS = KB + 1;
   constexpr int NW = G / 32;
@@ -646,9 +648,11 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
   } else {
     // ---------------- consumers ----------------
     const float lo_unit = a.qs.lo_unit;
-    float M[4], acc[4];
+    float M[CH][4], acc[CH][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { M[q] = 2.f * kNeg; acc[q] = 0.f; }
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { M[c][q] = 2.f * kNeg; acc[c][q] = 0.f; }
     for (int i = 0;; ++i) {
       const int s = i % NS;
       if (!mbar_wait(smem_u32(&full[s]), (i / NS) & 1)) { timed_out = true; break; }
@@ -657,12 +661,13 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
       const int nb = m.nb;
       const float *hs = st_hi + s * ROWS * Lp;
       const lo_t *ls = st_lo + s * ROWS * Lp;
-      float bh[4], blb[4];
-      {
-        uint32_t w[2];
-        srow(hs, ls, g, bh, w);
+      float bh[CH][4], blb[CH][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) blb[q] = lo_inj(w, q) - 2.f * kLoBias;   // exact
+      for (int c = 0; c < CH; ++c) {
+        uint32_t w[2];
+        srow(hs, ls, c * G + g, bh[c], w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) blb[c][q] = lo_inj(w, q) - 2.f * kLoBias;   // exact
       }
       // (1) column log-sum-exp per in-state, log2 sum_l 2^(A_{t-1}[tail, l] + B_{t+1}[v, l]).
       // With a stored reference r (the column maximum of an earlier pass, on the q grid) the
@@ -677,13 +682,17 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
         float cs[KB];
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
-          float h[4];
-          uint32_t w[2];
-          srow(hs + (1 + k) * Lp, ls + (1 + k) * Lp, g, h, w);
           const float r = m.cref[k];
           float sum = 0.f;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) sum += ex2(fmaf(lo_inj(w, q) + blb[q], lo_unit, (h[q] + bh[q]) - r));
+          for (int c = 0; c < CH; ++c) {
+            float h[4];
+            uint32_t w[2];
+            srow(hs + (1 + k) * Lp, ls + (1 + k) * Lp, c * G + g, h, w);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              sum += ex2(fmaf(lo_inj(w, q) + blb[c][q], lo_unit, (h[q] + bh[c][q]) - r));
+          }
           cs[k] = sum;
         }
         group_reduce<32, KB, false>(cs, nullptr);
@@ -710,18 +719,27 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
         float cm[KB], cs[KB];
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
-          const float4 x = reinterpret_cast<const float4 *>(hs + (1 + k) * Lp)[g];
-          cm[k] = fmaxf(fmaxf(x.x + bh[0], x.y + bh[1]), fmaxf(x.z + bh[2], x.w + bh[3]));
+          float mm = 2.f * kNeg;
+#pragma unroll
+          for (int c = 0; c < CH; ++c) {
+            const float4 x = reinterpret_cast<const float4 *>(hs + (1 + k) * Lp)[c * G + g];
+            mm = fmaxf(mm, fmaxf(fmaxf(x.x + bh[c][0], x.y + bh[c][1]), fmaxf(x.z + bh[c][2], x.w + bh[c][3])));
+          }
+          cm[k] = mm;
         }
         group_reduce<32, KB, true>(cm, nullptr);
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
-          float h[4];
-          uint32_t w[2];
-          srow(hs + (1 + k) * Lp, ls + (1 + k) * Lp, g, h, w);
           float sum = 0.f;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) sum += ex2(fmaf(lo_inj(w, q) + blb[q], lo_unit, (h[q] + bh[q]) - cm[k]));
+          for (int c = 0; c < CH; ++c) {
+            float h[4];
+            uint32_t w[2];
+            srow(hs + (1 + k) * Lp, ls + (1 + k) * Lp, c * G + g, h, w);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              sum += ex2(fmaf(lo_inj(w, q) + blb[c][q], lo_unit, (h[q] + bh[c][q]) - cm[k]));
+          }
           cs[k] = sum;
         }
         group_reduce<32, KB, false>(cs, nullptr);
@@ -774,17 +792,23 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
         wlb[k] = __shfl_sync(0xffffffffu, ml, k) - kLoBias * lo_unit;
       }
       // (3) A_t[v] accumulates A_{t-1}[y] + W_t[state] over the item's in-states
-      aggregate_staged<KB>(hs + Lp, ls + Lp, Lp, g, wh, wlb, lo_unit, M, acc);
-      if (m.last) {
-        float oh[4];
-        lo_t ol[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          lse_encode(M[q], acc[q], a.qs, oh[q], ol[q]);
-          M[q] = 2.f * kNeg;
-          acc[q] = 0.f;
+      for (int c = 0; c < CH; ++c)
+        aggregate_staged<KB>(hs + Lp, ls + Lp, Lp, c * G + g, wh, wlb, lo_unit, M[c], acc[c]);
+      if (m.last) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          float oh[4];
+          lo_t ol[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            lse_encode(M[c][q], acc[c][q], a.qs, oh[q], ol[q]);
+            M[c][q] = 2.f * kNeg;
+            acc[c][q] = 0.f;
+          }
+          const size_t o = (size_t)m.v * Lp + 4 * (c * G + g);
+          store4(a.out_hi + o, a.out_lo + o, oh, ol);
         }
-        store4(a.out_hi + (size_t)m.v * Lp + 4 * g, a.out_lo + (size_t)m.v * Lp + 4 * g, oh, ol);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
@@ -795,9 +819,9 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_forward_tma(const 
 }
 
 // Backward step, warp-specialised like the forward step.
-template <int G>
-__global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_backward_tma(const StepArgs a) {
-  constexpr int Lp = 4 * G;
+template <int G, int CH>
+__global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_backward_tma(const StepArgs a) {
+  constexpr int Lp = 4 * G * CH;
   constexpr int KB = kBatchBwd;
   constexpr int ROWS = KB;
   constexpr int NW = G / 32;
@@ -827,9 +851,11 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_backward_tma(const
     producer_loop<false, Lp, BwdMeta>(a, meta, st_hi, st_lo, full, empty, ROWS, timed_out);
   } else {
     const float lo_unit = a.qs.lo_unit;
-    float M[4], acc[4];
+    float M[CH][4], acc[CH][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) { M[q] = 2.f * kNeg; acc[q] = 0.f; }
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { M[c][q] = 2.f * kNeg; acc[c][q] = 0.f; }
     for (int i = 0;; ++i) {
       const int s = i % NS;
       if (!mbar_wait(smem_u32(&full[s]), (i / NS) & 1)) { timed_out = true; break; }
@@ -842,17 +868,24 @@ __global__ void __launch_bounds__(G + 32, G == 256 ? 3 : 1) k_backward_tma(const
         wh[k] = k < nb ? m.w_hi[k] : kNeg;
         wlb[k] = (k < nb ? m.w_lo[k] : 0.f) - kLoBias * lo_unit;
       }
-      aggregate_staged<KB>(st_hi + s * ROWS * Lp, st_lo + s * ROWS * Lp, Lp, g, wh, wlb, lo_unit, M, acc);
-      if (m.last) {
-        float oh[4];
-        lo_t ol[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          lse_encode(M[q], acc[q], a.qs, oh[q], ol[q]);
-          M[q] = 2.f * kNeg;
-          acc[q] = 0.f;
+      for (int c = 0; c < CH; ++c)
+        aggregate_staged<KB>(st_hi + s * ROWS * Lp, st_lo + s * ROWS * Lp, Lp, c * G + g, wh, wlb, lo_unit, M[c],
+                             acc[c]);
+      if (m.last) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          float oh[4];
+          lo_t ol[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            lse_encode(M[c][q], acc[c][q], a.qs, oh[q], ol[q]);
+            M[c][q] = 2.f * kNeg;
+            acc[c][q] = 0.f;
+          }
+          const size_t o = (size_t)m.v * Lp + 4 * (c * G + g);
+          store4(a.out_hi + o, a.out_lo + o, oh, ol);
         }
-        store4(a.out_hi + (size_t)m.v * Lp + 4 * g, a.out_lo + (size_t)m.v * Lp + 4 * g, oh, ol);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
@@ -887,33 +920,40 @@ static cudaError_t launch_step_g(int G, int C, const StepArgs &a, cudaStream_t s
   return cudaErrorInvalidValue;
 }
 
-template <int G>
+template <int G, int CH>
 static size_t tma_smem(bool fwd) {
-  return (size_t)(fwd ? kStagesFwd : kStagesBwd) * (fwd ? kBatchTma + 1 : kBatchBwd) * 4 * G * (sizeof(float) + sizeof(lo_t));
+  return (size_t)(fwd ? kStagesFwd : kStagesBwd) * (fwd ? kBatchTma + 1 : kBatchBwd) * 4 * G * CH *
+         (sizeof(float) + sizeof(lo_t));
 }
 
-template <int G>
+template <int G, int CH>
 static cudaError_t launch_tma_t(bool fwd, const StepArgs &a, int grid, cudaStream_t s) {
-  if (fwd) k_forward_tma<G><<<grid, G + 32, tma_smem<G>(true), s>>>(a);
-  else k_backward_tma<G><<<grid, G + 32, tma_smem<G>(false), s>>>(a);
+  if (fwd) k_forward_tma<G, CH><<<grid, G + 32, tma_smem<G, CH>(true), s>>>(a);
+  else k_backward_tma<G, CH><<<grid, G + 32, tma_smem<G, CH>(false), s>>>(a);
   return cudaGetLastError();
 }
 
-template <int G>
+template <int G, int CH>
 static cudaError_t prepare_tma_t(int n_sm, int V, int *grid_fwd, int *grid_bwd) {
-  cudaError_t e = cudaFuncSetAttribute(k_forward_tma<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<G>(true));
+  cudaError_t e = cudaFuncSetAttribute(k_forward_tma<G, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tma_smem<G, CH>(true));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_backward_tma<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem<G>(false));
+  e = cudaFuncSetAttribute(k_backward_tma<G, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tma_smem<G, CH>(false));
   if (e != cudaSuccess) return e;
   int bf = 0, bb = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_forward_tma<G>, G + 32, tma_smem<G>(true));
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_forward_tma<G, CH>, G + 32, tma_smem<G, CH>(true));
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_backward_tma<G>, G + 32, tma_smem<G>(false));
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_backward_tma<G, CH>, G + 32, tma_smem<G, CH>(false));
   if (e != cudaSuccess) return e;
   *grid_fwd = bf > 0 ? min(V, n_sm * bf) : 0;
   *grid_bwd = bb > 0 ? min(V, n_sm * bb) : 0;
   return cudaSuccess;
 }
+
+// Consumer threads and chunks per thread of the pipelined kernels for a row of Lp = 4 G
+// commodities: rows of 1024 commodities run 128 threads with two chunks each.
+static int tma_chunks(int G) { return G == 256 ? kTmaChunks256 : 1; }
 
 // Set up the pipelined persistent kernels for this problem (before any graph capture):
 // grid sizes 0 mean "use the register kernels".
@@ -926,17 +966,18 @@ cudaError_t prepare_step_kernels(int G, int C, bool pc, int V, int *grid_fwd, in
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  if (G == 64) return prepare_tma_t<64>(n_sm, V, grid_fwd, grid_bwd);
-  if (G == 128) return prepare_tma_t<128>(n_sm, V, grid_fwd, grid_bwd);
-  return prepare_tma_t<256>(n_sm, V, grid_fwd, grid_bwd);
+  if (G == 64) return prepare_tma_t<64, 1>(n_sm, V, grid_fwd, grid_bwd);
+  if (G == 128) return prepare_tma_t<128, 1>(n_sm, V, grid_fwd, grid_bwd);
+  if (tma_chunks(256) == 2) return prepare_tma_t<128, 2>(n_sm, V, grid_fwd, grid_bwd);
+  return prepare_tma_t<256, 1>(n_sm, V, grid_fwd, grid_bwd);
 }
 
 cudaError_t launch_step(bool fwd, bool pc, int G, int C, const StepArgs &a, cudaStream_t s) {
   const int pgrid = fwd ? a.persist_grid_fwd : a.persist_grid_bwd;
   if (pgrid > 0 && !pc && C == 1) {
-    if (G == 64) return launch_tma_t<64>(fwd, a, pgrid, s);
-    if (G == 128) return launch_tma_t<128>(fwd, a, pgrid, s);
-    if (G == 256) return launch_tma_t<256>(fwd, a, pgrid, s);
+    if (G == 64) return launch_tma_t<64, 1>(fwd, a, pgrid, s);
+    if (G == 128) return launch_tma_t<128, 1>(fwd, a, pgrid, s);
+    if (G == 256) return tma_chunks(256) == 2 ? launch_tma_t<128, 2>(fwd, a, pgrid, s) : launch_tma_t<256, 1>(fwd, a, pgrid, s);
   }
   if (fwd) return pc ? launch_step_g<true, true>(G, C, a, s) : launch_step_g<true, false>(G, C, a, s);
   return pc ? launch_step_g<false, true>(G, C, a, s) : launch_step_g<false, false>(G, C, a, s);

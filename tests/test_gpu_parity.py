@@ -117,6 +117,20 @@ def test_wide_panel_more_than_1024_commodities(O):
     assert rel_l1(O.ots_get_flows(h), o.flows()) <= FLOW_TOL
 
 
+def test_pipelined_rows_of_1024_commodities(O):
+    """L = 1000 (rows of 1024, ragged tail): the pipelined kernels with two 4-commodity chunks
+    per consumer thread, against the oracle's fixed point."""
+    inst = I.rgg_instance(seed=5, n=48, L=1000, T=9, eps=0.08, cap_lo=0.3, cap_hi=1.0, cap_div=40.0)
+    o = Oracle(inst)
+    o.solve(max_iters=20000, tol=1e-10)
+    h = O.ots_create_problem(inst)
+    r = O.ots_sinkhorn_solve(h, tol=1e-7, max_iters=20000)
+    assert r["status"] == 0
+    assert rel_l1(O.ots_get_flows(h), o.flows()) <= FLOW_TOL
+    P = O.ots_get_commodity_flows(h, 1, inst.T + 1, 990, 1000)
+    assert rel_l1(P, o.projections(990, 1000)) <= FLOW_TOL
+
+
 # ---------------------------------------------------------------------------------------
 # iterate-by-iterate parity (same initialisation, same number of passes)
 # ---------------------------------------------------------------------------------------
