@@ -351,14 +351,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up.  Each try may suspend
+// the thread for up to 2 us (returning as soon as the phase completes), so a waiting warp
+// does not spin on the issue slots; 2^20 tries bound the wait to about two seconds.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 22); ++i) {
+  for (uint32_t i = 0; i < (1u << 20); ++i) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(2000u)
         : "memory");
     if (ok) return true;
   }
@@ -387,27 +389,6 @@ __device__ __forceinline__ bool item_next(const int *ptr, int V, int KB, TmaItem
   it.j0 = ptr[it.v];
   it.nb = min(KB, ptr[it.v + 1] - it.j0);
   return true;
-}
-
-
-// Producer (one thread): the rows of `it` into stage (hi, lo): forward puts B_{t+1}[v] in row
-// 0 and A_{t-1}[tail j] in rows 1..nb; backward puts B_{t+1}[head j] in rows 0..nb-1.
-template <bool FWD, int Lp>
-__device__ __forceinline__ void tma_issue(const StepArgs &a, const TmaItem &it, float *hi, lo_t *lo, uint32_t bar) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads of the stage are done
-  const int nrows = (FWD ? 1 : 0) + it.nb;
-  mbar_expect_tx(bar, (uint32_t)(nrows * Lp * (int)(sizeof(float) + sizeof(lo_t))));
-  int r = 0;
-  if (FWD) {
-    bulk_g2s(smem_u32(hi), a.y_hi + (size_t)it.v * Lp, Lp * sizeof(float), bar);
-    bulk_g2s(smem_u32(lo), a.y_lo + (size_t)it.v * Lp, Lp * sizeof(lo_t), bar);
-    r = 1;
-  }
-  for (int k = 0; k < it.nb; ++k) {
-    const size_t row = (size_t)a.nbr[it.j0 + k] * Lp;
-    bulk_g2s(smem_u32(hi + (r + k) * Lp), a.x_hi + row, Lp * sizeof(float), bar);
-    bulk_g2s(smem_u32(lo + (r + k) * Lp), a.x_lo + row, Lp * sizeof(lo_t), bar);
-  }
 }
 
 // Thread g's 4 entries of a staged row.
