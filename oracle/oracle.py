@@ -53,6 +53,8 @@ def _load():
     lib.orc_destroy.argtypes = [ctypes.c_void_p]
     lib.orc_set_time_costs.argtypes = [ctypes.c_void_p, _f64p]
     lib.orc_set_time_costs.restype = ctypes.c_int
+    lib.orc_set_time_capacities.argtypes = [ctypes.c_void_p, _f64p]
+    lib.orc_set_time_capacities.restype = ctypes.c_int
     lib.orc_set_threads.argtypes = [ctypes.c_int]
     lib.orc_get_threads.restype = ctypes.c_int
     lib.orc_num_states.argtypes = [ctypes.c_void_p]
@@ -129,6 +131,13 @@ class Oracle:
                 raise ValueError("state_cost_t must be (T-2) x n_states")
             if lib.orc_set_time_costs(self.h, ct.reshape(-1)):
                 raise MemoryError("oracle: time-varying costs")
+        dt = getattr(inst, "state_capacity_t", None)
+        if dt is not None:
+            dt = np.ascontiguousarray(dt, np.float64)
+            if dt.shape != (self.T - 2, self.S):
+                raise ValueError("state_capacity_t must be (T-2) x n_states")
+            if lib.orc_set_time_capacities(self.h, dt.reshape(-1)):
+                raise ValueError("oracle: per-interval capacities must be >= 0 (inf for none)")
         lib.orc_init_duals(self.h)
 
     def __del__(self):

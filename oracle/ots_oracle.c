@@ -58,6 +58,7 @@ typedef struct orc {
   double *logKL;               /* [L*S], or [(T+1)*L*S] (rows t = 2..T-1) when tv */
   int tv;                      /* time-varying costs set by orc_set_time_costs */
   double *d;                   /* [S] */
+  double *dt;                  /* [(T+1)*S] per-interval capacities (row t), or NULL */
   double *R01, *R0T;           /* [L*S] dense */
   double *logu;                /* [T*S], row t (1-based) used for t = 2..T-1 */
   double *logU01, *logU0T;     /* [L*S] */
@@ -90,7 +91,7 @@ int orc_get_threads(void) {
 void orc_destroy(orc *o) {
   if (!o) return;
   free(o->tail); free(o->head); free(o->pred_ptr); free(o->pred_idx);
-  free(o->succ_ptr); free(o->succ_idx); free(o->logKL); free(o->d);
+  free(o->succ_ptr); free(o->succ_idx); free(o->logKL); free(o->d); free(o->dt);
   free(o->R01); free(o->R0T); free(o->logu); free(o->logU01); free(o->logU0T);
   free(o->psi); free(o->ph_a); free(o->ph_b);
   free(o);
@@ -199,6 +200,27 @@ int orc_set_time_costs(orc *o, const double *cost_t) {
   o->tv = 1;
   return ORC_OK;
 }
+
+/* Per-interval capacities d_t (the problem statements of Section 3 give one capacity vector
+ * per interval t = 2..T-1): cap_t is [(T-2)*S], row t-2 for interval t, INFINITY for none. */
+int orc_set_time_capacities(orc *o, const double *cap_t) {
+  const int S = o->S, T = o->T;
+  double *d = (double *)malloc(sizeof(double) * (size_t)(T + 1) * S);
+  if (!d) return ORC_NOMEM;
+  for (size_t q = 0; q < (size_t)(T + 1) * S; ++q) d[q] = INFINITY;
+  for (int t = 2; t <= T - 1; ++t)
+    for (int s = 0; s < S; ++s) {
+      const double c = cap_t[(size_t)(t - 2) * S + s];
+      if (!(c >= 0)) { free(d); return ORC_BAD_ARG; }
+      d[(size_t)t * S + s] = c;
+    }
+  free(o->dt);
+  o->dt = d;
+  return ORC_OK;
+}
+
+/* capacity of state s in interval t */
+static double cap_at(const orc *o, int t, int s) { return o->dt ? o->dt[(size_t)t * o->S + s] : o->d[s]; }
 
 int orc_num_states(const orc *o) { return o->S; }
 int64_t orc_nnz(const orc *o) { return o->pred_ptr[o->S]; }
@@ -331,7 +353,7 @@ static double dual_linear_part(const orc *o) {
   for (size_t q = 0; q < LS; ++q) a += xlogy(o->R01[q], o->logU01[q]) + xlogy(o->R0T[q], o->logU0T[q]);
   for (int t = 2; t <= o->T - 1; ++t)
     for (int s = 0; s < o->S; ++s)
-      if (isfinite(o->d[s])) a += xlogy(o->d[s], o->logu[(size_t)t * o->S + s]);
+      if (isfinite(cap_at(o, t, s))) a += xlogy(cap_at(o, t, s), o->logu[(size_t)t * o->S + s]);
   return o->eps * a;
 }
 
@@ -392,9 +414,10 @@ int orc_iteration(orc *o, double *src_resid, double *cap_viol, double *trace) {
     double mass_t = 0.0;
     for (int i = 0; i < S; ++i) {
       if (ls[i] > -INFINITY) {
+        const double di = cap_at(o, t, i);
         double p_old = exp(lu[i] + ls[i]);
-        if (p_old > o->d[i]) viol += p_old - o->d[i];
-        lu[i] = isfinite(o->d[i]) ? fmin(log(o->d[i]) - ls[i], 0.0) : 0.0;
+        if (p_old > di) viol += p_old - di;
+        lu[i] = isfinite(di) ? fmin(log(di) - ls[i], 0.0) : 0.0;
         mass_t += exp(lu[i] + ls[i]);
       } else {
         lu[i] = 0.0;

@@ -51,6 +51,7 @@ class Instance:
     pos: Optional[np.ndarray] = None              # [V, 2] node positions (not used by solvers)
     commodity_cost: Optional[np.ndarray] = None   # [L, S] per-commodity state costs
     state_cost_t: Optional[np.ndarray] = None     # [T-2, S] per-interval state costs (t = 2..T-1)
+    state_capacity_t: Optional[np.ndarray] = None  # [T-2, S] per-interval capacities d_t (inf: none)
     meta: dict = field(default_factory=dict)
 
     # ---- derived sizes / per-state views (data assembly only) ----
@@ -360,6 +361,21 @@ def with_time_varying_costs(inst, seed: int = 0, lo: float = 0.5, hi: float = 2.
     for _ in range(closures):
         ct[rng.integers(inst.T - 2), rng.integers(inst.n_edges)] = np.inf
     inst.state_cost_t = ct
+    return inst
+
+
+def with_time_varying_capacities(inst, seed: int = 0, lo: float = 0.5, hi: float = 1.5, closures: int = 0):
+    """Per-interval capacities d_t (the capacity vectors of the problem statements, one per
+    interval t = 2..T-1): each finite capacity times U[lo, hi], drawn per (t, state), and
+    `closures` random moving edges given capacity 0 in one random interval each."""
+    rng = np.random.default_rng(seed)
+    base = np.concatenate([inst.edge_cap, inst.wait_cap]).astype(np.float64)
+    dt = np.tile(base, (inst.T - 2, 1))
+    fin = np.isfinite(dt)
+    dt[fin] *= rng.uniform(lo, hi, int(fin.sum()))
+    for _ in range(closures):
+        dt[rng.integers(inst.T - 2), rng.integers(inst.n_edges)] = 0.0
+    inst.state_capacity_t = dt
     return inst
 
 

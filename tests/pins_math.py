@@ -63,6 +63,15 @@ def capacity(inst) -> np.ndarray:
     return np.concatenate([inst.edge_cap, inst.wait_cap]).astype(np.float64)
 
 
+def capacity_at(inst, t: int) -> np.ndarray:
+    """d_t for interval t (1-based, 2..T-1): the per-interval capacities when the instance has
+    them, else the single capacity vector."""
+    dt = getattr(inst, "state_capacity_t", None)
+    if dt is not None:
+        return np.asarray(dt[t - 2], np.float64)
+    return capacity(inst)
+
+
 def all_paths(S: int, T: int) -> np.ndarray:
     return np.array(list(itertools.product(range(S), repeat=T)), dtype=np.int64)
 
@@ -115,7 +124,6 @@ def tensor_sinkhorn(inst, iters=20000, tol=1e-13, reverse=True):
     tz = Tensor(inst)
     L, S, T = tz.L, tz.S, tz.T
     R01, R0T = dense_marginals(inst)
-    d = capacity(inst)
     u = np.ones((T + 1, S))
     U01 = (R01 > 0).astype(float)
     U0T = (R0T > 0).astype(float)
@@ -128,14 +136,16 @@ def tensor_sinkhorn(inst, iters=20000, tol=1e-13, reverse=True):
         for t in order:
             M = tz.M(u, U01, U0T)
             Pt = tz.proj0t(M, t).sum(0)
+            dt = capacity_at(inst, t)
             with np.errstate(divide="ignore", invalid="ignore"):
-                upd = np.where(Pt > 0, u[t] * d / Pt, 1.0)
+                upd = np.where(Pt > 0, u[t] * dt / Pt, 1.0)
+            upd = np.where(dt == 0, 0.0, upd)                       # d = 0 closes the state
             u[t] = np.minimum(upd, 1.0)
         M = tz.M(u, U01, U0T)
         PT = tz.proj0t(M, T)
         U0T = np.where(R0T > 0, U0T * R0T / np.where(PT > 0, PT, 1), 0.0)
         M = tz.M(u, U01, U0T)
-        excess = sum(np.maximum(tz.proj0t(M, t).sum(0) - d, 0).sum() for t in range(2, T))
+        excess = sum(np.maximum(tz.proj0t(M, t).sum(0) - capacity_at(inst, t), 0).sum() for t in range(2, T))
         if err < tol and excess / R01.sum() < tol:
             break
     M = tz.M(u, U01, U0T)

@@ -321,3 +321,67 @@ def test_time_constant_costs_and_per_interval_shifts():
     F3 = o3.flows()
     assert F3[3, e] == 0.0 and F0[3, e] > 1e-3
     assert abs(F3[0].sum() - F0[0].sum()) < 1e-9 * F0[0].sum()
+
+
+# ---------------------------------------------------------------------------------------
+# per-interval capacities d_t (the capacity vectors of the problem statements, one per
+# interval t = 2..T-1; Algorithm 2 writes a single d)
+# ---------------------------------------------------------------------------------------
+
+def test_per_interval_capacities_fixed_point_matches_tensor_sinkhorn():
+    inst = tiny_instance(seed=9, T=5, L=2, cap_scale=0.9, eps=0.5, per_commodity=False)
+    rng = np.random.default_rng(2)
+    d = PM.capacity(inst)
+    dt = np.tile(d, (inst.T - 2, 1))
+    fin = np.isfinite(dt)
+    dt[fin] *= rng.uniform(0.4, 1.6, int(fin.sum()))
+    dt[1, 0] = 0.0                                      # edge 0 closed in interval t = 3
+    inst.state_capacity_t = dt
+    o = Oracle(inst)
+    r = o.solve(max_iters=50000, tol=1e-13)
+    assert r["status"] == 0 and r["src_resid"] < 1e-12 and r["cap_viol"] < 1e-12
+    P = o.projections()
+    tz, M, _ = PM.tensor_sinkhorn(inst)
+    for t in range(1, inst.T + 1):
+        np.testing.assert_allclose(P[t - 1], tz.proj0t(M, t), rtol=1e-7, atol=1e-9)
+    assert np.all(P[2, :, 0] == 0.0)
+
+
+def test_per_interval_capacities_kkt_and_reductions():
+    """At the fixed point P_t <= d_t, and a state's dual is active (u_t < 1) only where its
+    capacity binds (complementary slackness of Theorem 3); d_t equal for every t reproduces
+    the single-capacity solution and d_t = inf the uncapacitated one."""
+    base = I.rgg_instance(seed=4, n=40, L=3, T=9, eps=0.05, cap_lo=0.3, cap_hi=1.0)
+    o0 = Oracle(base)
+    o0.solve(max_iters=100000, tol=1e-12)
+    F0 = o0.flows()
+    inst = I.rgg_instance(seed=4, n=40, L=3, T=9, eps=0.05, cap_lo=0.3, cap_hi=1.0)
+    inst.state_capacity_t = np.tile(PM.capacity(inst), (inst.T - 2, 1))
+    o1 = Oracle(inst)
+    o1.solve(max_iters=100000, tol=1e-12)
+    np.testing.assert_allclose(o1.flows(), F0, rtol=1e-10, atol=1e-12)
+    free = I.rgg_instance(seed=4, n=40, L=3, T=9, eps=0.05, cap_lo=0.3, cap_hi=1.0)
+    free.edge_cap = np.full_like(free.edge_cap, np.inf)
+    of = Oracle(free)
+    of.solve(max_iters=100000, tol=1e-12)
+    inst.state_capacity_t = np.full((inst.T - 2, inst.n_states), np.inf)
+    o2 = Oracle(inst)
+    o2.solve(max_iters=100000, tol=1e-12)
+    np.testing.assert_allclose(o2.flows(), of.flows(), rtol=1e-10, atol=1e-12)
+    I.with_time_varying_capacities(inst, seed=5, lo=0.8, hi=1.5, closures=1)
+    o3 = Oracle(inst)
+    r3 = o3.solve(max_iters=200000, tol=1e-12)
+    assert r3["status"] == 0 and r3["cap_viol"] < 1e-12 and r3["iters"] < 200000
+    F3 = o3.flows()
+    logu, _, _ = o3.get_duals()
+    dt = inst.state_capacity_t
+    n_active = 0
+    for t in range(2, inst.T):
+        P, d, lu = F3[t - 1], dt[t - 2], logu[t - 2]
+        assert np.all(P <= d + 1e-8)                   # feasible up to the solve tolerance
+        act = lu < -1e-6
+        n_active += int(act.sum())
+        np.testing.assert_allclose(P[act], d[act], rtol=1e-6, atol=1e-8)
+    assert n_active > 0
+    zero = dt == 0.0
+    assert zero.any() and np.all(F3[1:-1][zero] == 0.0)
