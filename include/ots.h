@@ -99,6 +99,13 @@ typedef struct ots_problem_desc {
                                     for all commodities; +INFINITY closes a state during that
                                     interval.  When given, edge_cost and wait_cost are not used;
                                     not combinable with commodity_cost. */
+  const double *state_capacity_t; /* optional [(T-2) x n_states] row-major: per-interval
+                                    capacities d_t (the problem statements of Section 3 and
+                                    eq. multicommodity_reg bound P_t by d_t for t = 2..T-1):
+                                    row t-2 holds d_t, >= 0, +INFINITY for none, 0 closes the
+                                    state in that interval.  When given, edge_capacity and
+                                    wait_capacity are not used.  NaN or negative entries give
+                                    OTS_ERR_INVALID_ARG. */
 } ots_problem_desc;
 
 /* Options of ots_sinkhorn_solve. */

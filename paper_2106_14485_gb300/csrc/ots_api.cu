@@ -98,8 +98,9 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   const size_t klo = p->tv ? (size_t)t * p->S : 0;   // time-varying costs: row t
   a.kl_hi = p->d_kl_hi + klo; a.kl_lo = p->d_kl_lo + klo;
   a.klc_hi = p->d_klc_hi; a.klc_lo = p->d_klc_lo;
-  a.logd_hi = p->d_logd_hi; a.logd_lo = p->d_logd_lo;
-  a.cap = p->d_cap;
+  const size_t dlo = p->cv ? (size_t)t * p->S : 0;   // per-interval capacities: row t
+  a.logd_hi = p->d_logd_hi + dlo; a.logd_lo = p->d_logd_lo + dlo;
+  a.cap = p->d_cap + dlo;
   a.lu_t = p->d_logu + (size_t)t * p->S;
   a.w_hi_t = p->d_w_hi + (size_t)t * p->S;
   a.w_lo_t = p->d_w_lo + (size_t)t * p->S;
@@ -108,8 +109,10 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   a.persist_grid_bwd = p->pgrid_bwd;
   a.in_kl_hi = p->d_in_kl_hi ? p->d_in_kl_hi + klo : nullptr;
   a.in_kl_lo = p->d_in_kl_lo ? p->d_in_kl_lo + klo : nullptr;
-  a.in_logd_hi = p->d_in_logd_hi; a.in_logd_lo = p->d_in_logd_lo;
-  a.in_cap = p->d_in_cap; a.in_outpos = p->d_in_outpos;
+  a.in_logd_hi = p->d_in_logd_hi ? p->d_in_logd_hi + dlo : nullptr;
+  a.in_logd_lo = p->d_in_logd_lo ? p->d_in_logd_lo + dlo : nullptr;
+  a.in_cap = p->d_in_cap ? p->d_in_cap + dlo : nullptr;
+  a.in_outpos = p->d_in_outpos;
   a.lu_in_t = p->d_logu_in + (size_t)t * p->S;
   a.cref_in_t = p->d_cref_in ? p->d_cref_in + (size_t)t * p->S : nullptr;
   a.wout_hi_t = p->d_wout_hi + (size_t)t * p->S;
@@ -507,6 +510,10 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
     std::vector<std::vector<int>> adj(p->V);
     for (int e = 0; e < p->E; ++e) {
       double cap = d->edge_capacity ? d->edge_capacity[e] : INFINITY;
+      if (d->state_capacity_t) {   // usable if open in some interval
+        cap = 0.0;
+        for (int t = 2; t <= p->T - 1; ++t) cap = std::max(cap, d->state_capacity_t[(size_t)(t - 2) * (p->E + p->V) + e]);
+      }
       if (cap > 0.0 && p->tail[e] != p->head[e]) adj[p->tail[e]].push_back(p->head[e]);
     }
     for (int v = 0; v < p->V; ++v) { eptr[v + 1] = eptr[v] + (int)adj[v].size(); enbr.insert(enbr.end(), adj[v].begin(), adj[v].end()); }
@@ -516,8 +523,25 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   p->tv = d->state_cost_t != nullptr;
   if (p->tv && d->commodity_cost) return bail(fail(OTS_ERR_INVALID_ARG, "state_cost_t and commodity_cost do not combine"));
   const size_t KR = p->tv ? (size_t)(p->T + 1) : 1;   // rows of log2 K_L (row t for interval t)
-  std::vector<float> kl_hi(KR * p->S, 0.f), kl_lo(KR * p->S, 0.f), logd_hi(p->S), logd_lo(p->S);
-  std::vector<double> cap(p->S);
+  p->cv = d->state_capacity_t != nullptr;
+  const size_t DR = p->cv ? (size_t)(p->T + 1) : 1;   // rows of the capacities (row t for interval t)
+  std::vector<float> kl_hi(KR * p->S, 0.f), kl_lo(KR * p->S, 0.f), logd_hi(DR * p->S, 0.f), logd_lo(DR * p->S, 0.f);
+  std::vector<double> cap(DR * p->S, INFINITY);
+  auto set_cap = [&](size_t q, double dd) {
+    cap[q] = dd;
+    if (dd == 0.0) { logd_hi[q] = kNeg; logd_lo[q] = 0.f; }
+    else if (std::isinf(dd)) { logd_hi[q] = 0.f; logd_lo[q] = 0.f; }
+    else split_ff(std::log2(dd), logd_hi[q], logd_lo[q]);
+  };
+  if (p->cv) {
+    for (int t = 2; t <= p->T - 1; ++t)
+      for (int s = 0; s < p->S; ++s) {
+        const double dd = d->state_capacity_t[(size_t)(t - 2) * p->S + s];
+        if (std::isnan(dd) || dd < 0.0)
+          return bail(fail(OTS_ERR_INVALID_ARG, "state_capacity_t[%d][%d] must be >= 0 (inf for none)", t - 2, s));
+        set_cap((size_t)t * p->S + s, dd);
+      }
+  }
   double cmax_tv = 0.0;
   if (p->tv) {
     for (int t = 2; t <= p->T - 1; ++t)
@@ -544,10 +568,7 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
     if (!p->tv && !std::isfinite(c)) return bail(fail(OTS_ERR_INVALID_ARG, "state %d: cost must be finite", s));
     if (std::isnan(dd) || dd < 0.0) return bail(fail(OTS_ERR_INVALID_ARG, "state %d: capacity must be >= 0", s));
     if (!p->tv) split_ff(-c / d->eps * kInvLn2, kl_hi[s], kl_lo[s]);
-    cap[s] = dd;
-    if (dd == 0.0) { logd_hi[s] = kNeg; logd_lo[s] = 0.f; }
-    else if (std::isinf(dd)) { logd_hi[s] = 0.f; logd_lo[s] = 0.f; }
-    else split_ff(std::log2(dd), logd_hi[s], logd_lo[s]);
+    if (!p->cv) set_cap(s, dd);
   }
   // quantum of the hi parts: the magnitude of any message is bounded by about (T+1) times the
   // largest per-interval cost in bits; q = 2^k with that bound below 2^24 q keeps hi sums exact
@@ -586,22 +607,25 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   std::vector<int> st_inpos(p->S), st_outpos(p->S), in_outpos(p->S);
   for (int k = 0; k < p->S; ++k) { st_inpos[in_state[k]] = k; st_outpos[out_state[k]] = k; }
   for (int k = 0; k < p->S; ++k) in_outpos[k] = st_outpos[in_state[k]];
-  std::vector<float> in_kl_hi(KR * p->S), in_kl_lo(KR * p->S), in_logd_hi(p->S), in_logd_lo(p->S);
-  std::vector<float2> in_cap(p->S), cap2(p->S);
+  std::vector<float> in_kl_hi(KR * p->S), in_kl_lo(KR * p->S), in_logd_hi(DR * p->S), in_logd_lo(DR * p->S);
+  std::vector<float2> in_cap(DR * p->S), cap2(DR * p->S);
   auto split_cap = [](double dd) {
     if (!(dd < 3.0e38)) return make_float2(INFINITY, 0.f);        // no capacity (or beyond FP32)
     const float h = (float)dd;
     return make_float2(h, (float)(dd - (double)h));
   };
-  for (int k = 0; k < p->S; ++k) cap2[k] = split_cap(cap[k]);
+  for (size_t q = 0; q < DR * p->S; ++q) cap2[q] = split_cap(cap[q]);
   for (int k = 0; k < p->S; ++k) {
     const int st = in_state[k];
     for (size_t r = 0; r < KR; ++r) {
       in_kl_hi[r * p->S + k] = kl_hi[r * p->S + st];
       in_kl_lo[r * p->S + k] = kl_lo[r * p->S + st];
     }
-    in_logd_hi[k] = logd_hi[st]; in_logd_lo[k] = logd_lo[st];
-    in_cap[k] = cap2[st];
+    for (size_t r = 0; r < DR; ++r) {
+      in_logd_hi[r * p->S + k] = logd_hi[r * p->S + st];
+      in_logd_lo[r * p->S + k] = logd_lo[r * p->S + st];
+      in_cap[r * p->S + k] = cap2[r * p->S + st];
+    }
   }
 
   // ---- boundary triples ----
@@ -713,16 +737,17 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   size_t o_out_ptr = cv.take<int>(V + 1), o_out_state = cv.take<int>(S), o_out_nbr = cv.take<int>(S);
   size_t o_tail = cv.take<int>(S), o_head = cv.take<int>(S);
   const size_t KR = p->tv ? T + 1 : 1;
-  size_t o_kl_hi = cv.take<float>(KR * S), o_kl_lo = cv.take<float>(KR * S), o_ld_hi = cv.take<float>(S),
-         o_ld_lo = cv.take<float>(S);
-  size_t o_cap = cv.take<float2>(S);
+  const size_t DR = p->cv ? T + 1 : 1;
+  size_t o_kl_hi = cv.take<float>(KR * S), o_kl_lo = cv.take<float>(KR * S), o_ld_hi = cv.take<float>(DR * S),
+         o_ld_lo = cv.take<float>(DR * S);
+  size_t o_cap = cv.take<float2>(DR * S);
   size_t o_klc_hi = p->pc ? cv.take<float>(S * p->Lp) : 0, o_klc_lo = p->pc ? cv.take<lo_t>(S * p->Lp) : 0;
   size_t o_w_hi = cv.take<float>((T + 1) * S), o_w_lo = cv.take<float>((T + 1) * S);
   size_t o_logu = cv.take<float2>((T + 1) * S), o_flow = cv.take<double>((T + 1) * S);
   const size_t Sc = csr_copies ? S : 0;
   size_t o_st_inpos = cv.take<int>(Sc), o_st_outpos = cv.take<int>(Sc), o_in_outpos = cv.take<int>(Sc);
-  size_t o_in_kl_hi = cv.take<float>(KR * Sc), o_in_kl_lo = cv.take<float>(KR * Sc), o_in_ld_hi = cv.take<float>(Sc),
-         o_in_ld_lo = cv.take<float>(Sc), o_in_cap = cv.take<float2>(Sc);
+  size_t o_in_kl_hi = cv.take<float>(KR * Sc), o_in_kl_lo = cv.take<float>(KR * Sc),
+         o_in_ld_hi = cv.take<float>(DR * Sc), o_in_ld_lo = cv.take<float>(DR * Sc), o_in_cap = cv.take<float2>(DR * Sc);
   size_t o_logu_in = cv.take<float2>((T + 1) * Sc), o_wout_hi = cv.take<float>((T + 1) * Sc),
          o_wout_lo = cv.take<float>((T + 1) * Sc), o_cref_in = cv.take<float>((T + 1) * Sc);
   size_t o_a_hi[3], o_a_lo[3];

@@ -463,6 +463,7 @@ ots_status ots_host::batch_admit(ots_batch *b, ots_problem *p, const ots_solve_o
   I.mass = p->mass; I.eps = p->eps; I.tol = o.tol;
   I.max_passes = o.max_iters;
   I.kl_stride = p->tv ? p->S : 0;
+  I.cap_stride = p->cv ? p->S : 0;
   I.in_ptr = p->d_in_ptr; I.in_state = p->d_in_state; I.in_nbr = p->d_in_nbr;
   I.out_ptr = p->d_out_ptr; I.out_state = p->d_out_state; I.out_nbr = p->d_out_nbr;
   I.kl_hi = p->d_kl_hi; I.kl_lo = p->d_kl_lo; I.logd_hi = p->d_logd_hi; I.logd_lo = p->d_logd_lo;

@@ -46,6 +46,8 @@ struct alignas(16) BatchInst {
   double mass, eps, tol;
   int max_passes;
   int kl_stride;                 // S when the costs vary with the interval t (row t of kl), else 0
+  int cap_stride;                // S when the capacities vary with t (row t of logd, cap), else 0
+  int pad3, pad4, pad5;
   const int *in_ptr, *in_state, *in_nbr, *out_ptr, *out_state, *out_nbr;
   const float *kl_hi, *kl_lo, *logd_hi, *logd_lo;
   const float2 *cap;             // [S] d as a float-float

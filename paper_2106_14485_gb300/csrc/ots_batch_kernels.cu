@@ -79,8 +79,8 @@ __device__ __forceinline__ StepArgs step_of(const BatchInst &I, bool fwd, int t,
     a.out_hi = I.b_hi + (size_t)(t - 2) * pan; a.out_lo = I.b_lo + (size_t)(t - 2) * pan;
   }
   a.kl_hi = I.kl_hi + (size_t)t * I.kl_stride; a.kl_lo = I.kl_lo + (size_t)t * I.kl_stride;
-  a.logd_hi = I.logd_hi; a.logd_lo = I.logd_lo;
-  a.cap = I.cap;
+  a.logd_hi = I.logd_hi + (size_t)t * I.cap_stride; a.logd_lo = I.logd_lo + (size_t)t * I.cap_stride;
+  a.cap = I.cap + (size_t)t * I.cap_stride;
   a.lu_t = I.lu + (size_t)t * I.S;
   a.w_hi_t = I.w_hi + (size_t)t * I.S;
   a.w_lo_t = I.w_lo + (size_t)t * I.S;

@@ -136,6 +136,7 @@ struct ots_problem {
   bool pc = false;
   bool member = false;                         // lives in a batch (see CreateOpts)
   bool tv = false;                             // time-varying costs: K_L rows per interval t
+  bool cv = false;                             // per-interval capacities: d rows per interval t
   std::unique_ptr<ots_host::HostArrays> host;  // between the host build and the upload
 
   std::vector<int> tail, head;

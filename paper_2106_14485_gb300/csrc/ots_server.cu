@@ -49,7 +49,7 @@ struct Request {
   ots_problem_desc d{};
   ots_solve_opts o{};
   std::vector<int32_t> esrc, edst, sc, ss, zc, zs;
-  std::vector<double> ecost, ecap, wcost, wcap, ccost, sm, zm;
+  std::vector<double> ecost, ecap, wcost, wcap, ccost, cost_t, cap_t, sm, zm;
   int S = 0, T = 0;
   bool large = false;
   ots_problem *p = nullptr;                   // prepared batch member (between build and admit)
@@ -339,6 +339,8 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   copy_array(r->wcost, d->wait_cost, d->add_wait_loops ? V : 0);
   copy_array(r->wcap, d->wait_capacity, d->add_wait_loops ? V : 0);
   copy_array(r->ccost, d->commodity_cost, d->commodity_cost ? (size_t)d->L * S : 0);
+  copy_array(r->cost_t, d->state_cost_t, d->state_cost_t ? (size_t)(d->T - 2) * S : 0);
+  copy_array(r->cap_t, d->state_capacity_t, d->state_capacity_t ? (size_t)(d->T - 2) * S : 0);
   copy_array(r->sc, d->src_commodity, d->n_sources);
   copy_array(r->ss, d->src_state, d->n_sources);
   copy_array(r->sm, d->src_mass, d->n_sources);
@@ -353,6 +355,8 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   r->d.wait_cost = ptr_or_null(r->wcost);
   r->d.wait_capacity = ptr_or_null(r->wcap);
   r->d.commodity_cost = ptr_or_null(r->ccost);
+  r->d.state_cost_t = ptr_or_null(r->cost_t);
+  r->d.state_capacity_t = ptr_or_null(r->cap_t);
   r->d.src_commodity = ptr_or_null(r->sc);
   r->d.src_state = ptr_or_null(r->ss);
   r->d.src_mass = ptr_or_null(r->sm);

@@ -37,6 +37,7 @@ class ProblemDesc(ctypes.Structure):
         ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
         ("state_cost_t", _f64p),
+        ("state_capacity_t", _f64p),
     ]
 
 
@@ -245,6 +246,9 @@ def _problem_desc(inst, device: int = 0, stream: int | None = None):
     ct = getattr(inst, "state_cost_t", None)
     if ct is not None:
         arr["state_cost_t"] = c(ct, np.float64)
+    dt = getattr(inst, "state_capacity_t", None)
+    if dt is not None:
+        arr["state_capacity_t"] = c(dt, np.float64)
     d = ProblemDesc()
     d.n_nodes, d.n_edges = int(inst.n_nodes), int(len(arr["edge_src"]))
     d.edge_src, d.edge_dst = _ptr(arr["edge_src"], ctypes.c_int32), _ptr(arr["edge_dst"], ctypes.c_int32)
@@ -253,6 +257,7 @@ def _problem_desc(inst, device: int = 0, stream: int | None = None):
     d.wait_cost, d.wait_capacity = _ptr(arr["wait_cost"], ctypes.c_double), _ptr(arr["wait_cap"], ctypes.c_double)
     d.commodity_cost = _ptr(arr.get("commodity_cost"), ctypes.c_double)
     d.state_cost_t = _ptr(arr.get("state_cost_t"), ctypes.c_double)
+    d.state_capacity_t = _ptr(arr.get("state_capacity_t"), ctypes.c_double)
     d.T, d.L, d.eps = int(inst.T), int(inst.L), float(inst.eps)
     d.n_sources = len(arr["src_comm"])
     d.src_commodity, d.src_state = _ptr(arr["src_comm"], ctypes.c_int32), _ptr(arr["src_state"], ctypes.c_int32)

@@ -111,3 +111,18 @@ def test_time_varying_costs_are_validated_on_the_host():
     with pytest.raises(ots.OTSError) as e:
         ots.ots_create_problem(inst, allocator="cuda")
     assert e.value.code == ots.OTS_ERR_INVALID_ARG
+
+
+def test_per_interval_capacities_are_validated_on_the_host():
+    import numpy as np
+    from paper_2106_14485_gb300 import instances as I, ots
+    inst = I.rgg_instance(seed=3, n=30, L=2, T=6, eps=0.1)
+    inst.state_capacity_t = np.full((inst.T - 2, inst.n_states), np.inf)
+    inst.state_capacity_t[2, 5] = -1.0
+    with pytest.raises(ots.OTSError) as e:
+        ots.ots_create_problem(inst, allocator="cuda")
+    assert e.value.code == ots.OTS_ERR_INVALID_ARG
+    inst.state_capacity_t[2, 5] = np.nan
+    with pytest.raises(ots.OTSError) as e:
+        ots.ots_create_problem(inst, allocator="cuda")
+    assert e.value.code == ots.OTS_ERR_INVALID_ARG
