@@ -37,7 +37,9 @@
  *   - Zero column sum (state unreachable) gives u_t = 1; d = inf gives u_t = 1;
  *     R = 0 gives U = 0 (Theorem 4, eq. u_augment); 0 * inf = 0.
  *   - Convergence measures: relative L1 source mismatch taken just before the U01 update,
- *     and relative capacity excess sum_t sum_i (P_t - d)_+ taken just before each u_t update.
+ *     and the relative capacity residual sum_t sum_i |P_t after - P_t before| of each u_t
+ *     update: from the initialisation (u_t = 1) this is the capacity excess (P_t - d)_+; from
+ *     a warm start below the fixed point it also counts the flow a too small u_t withheld.
  */
 #include <math.h>
 #include <stdint.h>
@@ -380,6 +382,15 @@ int orc_backward_sweep(orc *o) {
  * for the current duals (orc_solve does this).  Outputs the two convergence measures and,
  * if trace != NULL, the dual objective after every block update (T entries: after U01,
  * after u_2 .. u_{T-1}, after U0T). */
+/* |P_new - P_old| of one capacity update, P = exp(log u + ls): the excess (P_old - d)_+ where
+ * u_t drops, the withheld flow where it rises (from a warm start below the fixed point). */
+static double flow_change(double lu_old, double lu_new, double ls) {
+  if (lu_old == -INFINITY && lu_new == -INFINITY) return 0.0;
+  if (lu_old == -INFINITY) return exp(lu_new + ls);
+  if (lu_new == -INFINITY) return exp(lu_old + ls);
+  return exp(lu_old + ls) * fabs(expm1(lu_new - lu_old));
+}
+
 int orc_iteration(orc *o, double *src_resid, double *cap_viol, double *trace) {
   if (!o->psi) return ORC_BAD_ARG;
   const int S = o->S, L = o->L, T = o->T;
@@ -415,9 +426,9 @@ int orc_iteration(orc *o, double *src_resid, double *cap_viol, double *trace) {
     for (int i = 0; i < S; ++i) {
       if (ls[i] > -INFINITY) {
         const double di = cap_at(o, t, i);
-        double p_old = exp(lu[i] + ls[i]);
-        if (p_old > di) viol += p_old - di;
+        const double lu_old = lu[i];
         lu[i] = isfinite(di) ? fmin(log(di) - ls[i], 0.0) : 0.0;
+        viol += flow_change(lu_old, lu[i], ls[i]);
         mass_t += exp(lu[i] + ls[i]);
       } else {
         lu[i] = 0.0;
