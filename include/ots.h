@@ -120,6 +120,15 @@ typedef struct ots_solve_opts {
   int32_t use_graph;     /* 1: run each pass as one captured CUDA graph (default 1) */
   int32_t threads_per_node; /* tuning knob: threads cooperating on one node row
                                (power of two <= 256); 0 = automatic */
+  int32_t eps_stages;    /* epsilon continuation: number of warm-start stages (default 3) */
+  double eps_start;      /* > eps: run the passes first at eps_start, eps_start (eps /
+                            eps_start)^(1/n), ... (n = eps_stages stages, each to
+                            eps_stage_tol), carrying the duals lambda = -eps ln u from stage
+                            to stage, then at the problem's eps to tol.  The fixed point at eps
+                            is unique, so the result is the same; the pass count usually drops.
+                            0 (default) = off.  Not with per-commodity costs
+                            (OTS_ERR_INVALID_ARG); the batched solver rejects it. */
+  double eps_stage_tol;  /* tolerance of the warm-start stages (default 1e-4) */
 } ots_solve_opts;
 
 /* Report of ots_sinkhorn_solve / ots_iterate. */

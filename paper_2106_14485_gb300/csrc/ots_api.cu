@@ -412,6 +412,9 @@ ots_status ots_default_solve_opts(ots_solve_opts *o) {
   o->warm_start = 0;
   o->use_graph = 1;
   o->threads_per_node = 0;
+  o->eps_stages = 0;
+  o->eps_start = 0.0;
+  o->eps_stage_tol = 0.0;
   return OTS_OK;
 }
 
@@ -526,6 +529,7 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   p->cv = d->state_capacity_t != nullptr;
   const size_t DR = p->cv ? (size_t)(p->T + 1) : 1;   // rows of the capacities (row t for interval t)
   std::vector<float> kl_hi(KR * p->S, 0.f), kl_lo(KR * p->S, 0.f), logd_hi(DR * p->S, 0.f), logd_lo(DR * p->S, 0.f);
+  p->cost_nat.assign(KR * p->S, 0.0);
   std::vector<double> cap(DR * p->S, INFINITY);
   auto set_cap = [&](size_t q, double dd) {
     cap[q] = dd;
@@ -550,6 +554,7 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
         const size_t q = (size_t)t * p->S + s;
         if (std::isnan(c) || c == -INFINITY)
           return bail(fail(OTS_ERR_INVALID_ARG, "state_cost_t[%d][%d] must be finite or +inf", t - 2, s));
+        p->cost_nat[q] = c;
         if (c == INFINITY) { kl_hi[q] = kNeg; kl_lo[q] = 0.f; continue; }   // closed in interval t
         split_ff(-c / d->eps * kInvLn2, kl_hi[q], kl_lo[q]);
         cmax_tv = std::max(cmax_tv, std::fabs(c) / d->eps * kInvLn2);
@@ -567,7 +572,10 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
     }
     if (!p->tv && !std::isfinite(c)) return bail(fail(OTS_ERR_INVALID_ARG, "state %d: cost must be finite", s));
     if (std::isnan(dd) || dd < 0.0) return bail(fail(OTS_ERR_INVALID_ARG, "state %d: capacity must be >= 0", s));
-    if (!p->tv) split_ff(-c / d->eps * kInvLn2, kl_hi[s], kl_lo[s]);
+    if (!p->tv) {
+      split_ff(-c / d->eps * kInvLn2, kl_hi[s], kl_lo[s]);
+      p->cost_nat[s] = c;
+    }
     if (!p->cv) set_cap(s, dd);
   }
   // quantum of the hi parts: the magnitude of any message is bounded by about (T+1) times the
@@ -606,6 +614,7 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   // ---- CSR-ordered copies (positions of every state in the in / out lists) ----
   std::vector<int> st_inpos(p->S), st_outpos(p->S), in_outpos(p->S);
   for (int k = 0; k < p->S; ++k) { st_inpos[in_state[k]] = k; st_outpos[out_state[k]] = k; }
+  p->in_state_h = in_state;
   for (int k = 0; k < p->S; ++k) in_outpos[k] = st_outpos[in_state[k]];
   std::vector<float> in_kl_hi(KR * p->S), in_kl_lo(KR * p->S), in_logd_hi(DR * p->S), in_logd_lo(DR * p->S);
   std::vector<float2> in_cap(DR * p->S), cap2(DR * p->S);
@@ -910,6 +919,54 @@ ots_status ots_iterate(ots_problem *p, int32_t n, int32_t reset, ots_solve_repor
   return st;
 }
 
+namespace {
+
+// Continuation in epsilon (warm starts at larger epsilon; the fixed point at the problem's own
+// epsilon is unique, so the final result does not depend on them): rebuild log2 K_L for
+// epsilon e, carry the duals over with lambda = -eps ln u held fixed, and mark the messages
+// stale.  The quantum of the hi parts, chosen for the smallest epsilon, stays valid.
+ots_status set_eps(ots_problem *p, double e) {
+  if (e == p->eps) return OTS_OK;
+  const size_t S = p->S, KR = p->tv ? (size_t)p->T + 1 : 1;
+  std::vector<float> kh(KR * S, 0.f), kl(KR * S, 0.f);
+  for (size_t q = 0; q < KR * S; ++q) {
+    const size_t t = q / S;
+    if (p->tv && (t < 2 || t > (size_t)p->T - 1)) continue;
+    const double c = p->cost_nat[q];
+    if (c == INFINITY) { kh[q] = kNeg; kl[q] = 0.f; }
+    else split_ff(-c / e * kInvLn2, kh[q], kl[q]);
+  }
+  OTS_CUDA(cudaMemcpyAsync(p->d_kl_hi, kh.data(), sizeof(float) * KR * S, cudaMemcpyHostToDevice, p->stream));
+  OTS_CUDA(cudaMemcpyAsync(p->d_kl_lo, kl.data(), sizeof(float) * KR * S, cudaMemcpyHostToDevice, p->stream));
+  std::vector<float> ih, il;
+  if (p->d_in_kl_hi) {
+    ih.resize(KR * S);
+    il.resize(KR * S);
+    for (size_t r = 0; r < KR; ++r)
+      for (size_t k = 0; k < S; ++k) {
+        ih[r * S + k] = kh[r * S + p->in_state_h[k]];
+        il[r * S + k] = kl[r * S + p->in_state_h[k]];
+      }
+    OTS_CUDA(cudaMemcpyAsync(p->d_in_kl_hi, ih.data(), sizeof(float) * KR * S, cudaMemcpyHostToDevice, p->stream));
+    OTS_CUDA(cudaMemcpyAsync(p->d_in_kl_lo, il.data(), sizeof(float) * KR * S, cudaMemcpyHostToDevice, p->stream));
+  }
+  const size_t n_lu = (size_t)(p->T + 1) * S;
+  OTS_CUDA(launch_scale_duals(p->d_logu, n_lu, p->d_logu_in, p->d_logu_in ? n_lu : 0, p->src.d_tri_logU, p->src.n,
+                              p->snk.d_tri_logU, p->snk.n, p->eps / e, p->stream));
+  if (p->d_cref_in) OTS_CUDA(cudaMemsetAsync(p->d_cref_in, 0xff, sizeof(float) * n_lu, p->stream));
+  p->kernels_launched += 1;
+  OTS_CUDA(cudaStreamSynchronize(p->stream));   // the host staging vectors go out of scope
+  p->eps = e;
+  if (p->pass_exec) {                            // epsilon is an argument of the pass graph
+    cudaGraphExecDestroy(p->pass_exec);
+    p->pass_exec = nullptr;
+  }
+  p->stale = true;
+  return OTS_OK;
+}
+
+}  // namespace
+
 ots_status ots_sinkhorn_solve(ots_problem *p, const ots_solve_opts *opts, ots_solve_report *rep) {
   g_last_error.clear();
   if (!p) return fail(OTS_ERR_INVALID_ARG, "problem is NULL");
@@ -922,12 +979,44 @@ ots_status ots_sinkhorn_solve(ots_problem *p, const ots_solve_opts *opts, ots_so
     if (!choose_mapping(p->L, o.threads_per_node, G, C, Lp) || Lp != p->Lp)
       return fail(OTS_ERR_INVALID_ARG, "threads_per_node %d is not usable with L = %d", o.threads_per_node, p->L);
   }
+  const bool anneal = o.eps_start > p->eps;
+  if (anneal && (p->pc || !std::isfinite(o.eps_start) || o.eps_stages < 0))
+    return fail(OTS_ERR_INVALID_ARG, "epsilon continuation needs commodity-independent costs and a finite eps_start");
   DeviceGuard guard(p->dev);
   auto t0 = std::chrono::steady_clock::now();
-  ots_status st = o.warm_start ? refresh_if_stale(p) : reset_duals(p);
-  if (st) return st;
+  const double target = p->eps;
+  ots_status st = anneal ? set_eps(p, o.eps_start) : OTS_OK;
+  if (!st) st = o.warm_start ? refresh_if_stale(p) : reset_duals(p);
+  if (st) { if (anneal) set_eps(p, target); return st; }
   ots_solve_report r{};
   int done = 0;
+  if (anneal) {
+    // stages eps_start * (eps / eps_start)^(k / n), k = 0..n-1, each to the stage tolerance,
+    // then the problem's own epsilon below
+    const int ns = o.eps_stages > 0 ? o.eps_stages : 3;
+    const double stol = o.eps_stage_tol > 0.0 ? o.eps_stage_tol : 1e-4;
+    for (int k = 0; k < ns && done < o.max_iters && !st; ++k) {
+      st = set_eps(p, o.eps_start * std::pow(target / o.eps_start, (double)k / ns));
+      if (!st) st = refresh_if_stale(p);
+      while (!st && done < o.max_iters) {
+        const int n = std::min(o.check_every, o.max_iters - done);
+        st = run_passes(p, n, o.use_graph != 0);
+        if (st) break;
+        done += n;
+        st = read_report(p, &r);
+        if (st || (r.src_residual <= stol && r.cap_violation <= stol)) break;
+      }
+    }
+    const ots_status back = set_eps(p, target);
+    if (!st) st = back;
+    if (!st) st = refresh_if_stale(p);
+    if (st) {
+      r.iterations = done;
+      r.status = st;
+      if (rep) *rep = r;
+      return st;
+    }
+  }
   st = OTS_ERR_NOT_CONVERGED;
   while (done < o.max_iters) {
     int k = std::min(o.check_every, o.max_iters - done);

@@ -387,6 +387,7 @@ ots_status ots_batch_add(ots_batch *b, const ots_problem_desc *desc, const ots_s
   clear_error();
   if (!b || !desc || !id) return fail(OTS_ERR_INVALID_ARG, "NULL argument");
   *id = -1;
+  if (opts && opts->eps_start > 0.0) return fail(OTS_ERR_INVALID_ARG, "the batched solver has no epsilon continuation");
   if (batch_free_slots(b) == 0) return fail(OTS_ERR_OOM, "no free slot (%d resident)", b->max_slots);
   DeviceGuard guard(b->dev);
   ots_problem *p = nullptr;

@@ -24,6 +24,8 @@ cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const fl
                            float *w_hi, float *w_lo, int reset, const int *st_inpos, const int *st_outpos,
                            float2 *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s);
 cudaError_t launch_fill_panel(size_t n, float *hi, lo_t *lo, cudaStream_t s);
+cudaError_t launch_scale_duals(float2 *lu, size_t n_lu, float2 *lu_in, size_t n_in, double *ua, int na, double *ub,
+                               int nb, double r, cudaStream_t s);
 cudaError_t launch_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
                                    const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
                                    const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
@@ -137,6 +139,8 @@ struct ots_problem {
   bool member = false;                         // lives in a batch (see CreateOpts)
   bool tv = false;                             // time-varying costs: K_L rows per interval t
   bool cv = false;                             // per-interval capacities: d rows per interval t
+  std::vector<double> cost_nat;                // state costs in natural units ([S], or [T+1][S] rows when tv)
+  std::vector<int> in_state_h;                 // in-CSR order of the states (host copy)
   std::unique_ptr<ots_host::HostArrays> host;  // between the host build and the upload
 
   std::vector<int> tail, head;

@@ -24,6 +24,7 @@
 // done by thread k of the group and broadcast.  Sums that decide convergence are FP64 and
 // deterministic (per-block partials, reduced by the last block in a fixed order).
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <math.h>
 #include <stdint.h>
 
@@ -989,6 +990,36 @@ cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const fl
                            float2 *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s) {
   k_weights<<<(S + 255) / 256, 256, 0, s>>>(S, T, qs, kl_hi, kl_lo, kl_stride, logu, w_hi, w_lo, reset, st_inpos, st_outpos,
                                             logu_in, wout_hi, wout_lo);
+  return cudaGetLastError();
+}
+
+// Continuation in epsilon: the duals lambda = -eps ln u are carried to a new epsilon, so
+// every log u (float-float) and log U (FP64) is multiplied by r = eps_old / eps_new; log 0
+// stays the sentinel.
+__global__ void k_scale_duals(float2 *lu, size_t n_lu, float2 *lu_in, size_t n_in, double *ua, int na, double *ub,
+                              int nb, double r) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_lu + n_in; i += stride) {
+    float2 *p = i < n_lu ? lu + i : lu_in + (i - n_lu);
+    const float2 x = *p;
+    if (x.x < kNegThresh) continue;
+    const double v = ((double)x.x + (double)x.y) * r;
+    const float h = (float)v;
+    *p = make_float2(h, (float)(v - (double)h));
+  }
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)na + nb; i += stride) {
+    double *p = i < (size_t)na ? ua + i : ub + (i - na);
+    if (isfinite(*p)) *p *= r;
+  }
+}
+
+cudaError_t launch_scale_duals(float2 *lu, size_t n_lu, float2 *lu_in, size_t n_in, double *ua, int na, double *ub,
+                               int nb, double r, cudaStream_t s) {
+  size_t n = std::max(n_lu + n_in, (size_t)na + nb);
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks == 0) blocks = 1;
+  k_scale_duals<<<(unsigned)blocks, 256, 0, s>>>(lu, n_lu, lu_in, n_in, ua, na, ub, nb, r);
   return cudaGetLastError();
 }
 

@@ -371,7 +371,7 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   if (o) r->o = *o;
   r->S = (int)S;
   r->T = d->T;
-  r->large = s->desc.mode == 1 || d->L > 256 || d->commodity_cost != nullptr;
+  r->large = s->desc.mode == 1 || d->L > 256 || d->commodity_cost != nullptr || (o && o->eps_start > 0.0);
   r->t_submit = Clock::now();
   std::unique_lock<std::mutex> lk(s->mu);
   if (s->desc.max_queued > 0) {

@@ -288,33 +288,35 @@ __device__ __forceinline__ void make_w(float kl_hi, float kl_lo, float lu_hi, fl
   w_lo = (s - w_hi) + e;
 }
 
-// Adds the capacity excess (P_old - d)_+ of one state to viol, where P_old = 2^(log2 u_old +
-// col) is the column sum under the old u_t and d = cap.x + cap.y its capacity (finite; d = 0
-// is the sentinel ldh = log2 0).  The exponent e of the ratio P_old / d = 2^e is formed in
-// float-float (its terms cancel), only near or above capacity; the excess d (2^e - 1) is
-// evaluated in FP32: exp2 for e > 0.5, else the Taylor series of exp(x) - 1 at x = e ln 2
-// (|x| <= 0.35, truncation below 2e-7 relative).
-__device__ __forceinline__ void add_excess(float2 cap, float2 lu_old, float col_hi, float col_lo, float ldh, float ldl,
-                                           float &viol) {
-  if (ldh < kNegThresh) {                         // d = 0: every unit of flow is excess
-    if (lu_old.x > kNegThresh) viol += ex2(fminf((lu_old.x + col_hi) + (lu_old.y + col_lo), 126.f));
+// Adds |P_new - P_old| of one state's capacity update to viol, where P = 2^(log2 u + col) is the
+// state's flow under the old and the new u_t: the excess (P_old - d)_+ where the update lowers
+// u_t, and the flow a too small u_t withheld where it raises u_t (a warm start can begin below
+// the fixed point, where the excess alone reads zero).  Evaluated as P_old |2^delta - 1| with
+// delta = log2 u_new - log2 u_old formed in float-float (its terms cancel near convergence);
+// 2^delta - 1 from exp2 for |delta| > 0.5, else from the Taylor series of exp(x) - 1 at
+// x = delta ln 2 (|x| <= 0.35, truncation below 2e-7 relative).  A state that closes or
+// reopens moves all of its flow.
+__device__ __forceinline__ void add_residual(float2 lu_old, float2 lu_new, float col_hi, float col_lo, float &viol) {
+  const bool c_old = lu_old.x < kNegThresh, c_new = lu_new.x < kNegThresh;
+  if (c_old && c_new) return;
+  if (c_old || c_new) {
+    const float2 lu = c_old ? lu_new : lu_old;
+    viol += ex2(fminf((lu.x + col_hi) + (lu.y + col_lo), 126.f));
     return;
   }
-  const float qv = lu_old.x + col_hi - ldh;
-  if (!(qv > -1e-3f)) return;
-  float s1, e1, s2, e2;
-  two_sum(lu_old.x, -ldh, s1, e1);
-  two_sum(s1, col_hi, s2, e2);
-  const float e = __fadd_rn(s2, __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(lu_old.y, col_lo), -ldl)));
-  if (!(e > 0.f)) return;
+  float s, e;
+  two_sum(lu_new.x, -lu_old.x, s, e);
+  const float dl = __fadd_rn(s, __fadd_rn(e, __fsub_rn(lu_new.y, lu_old.y)));
+  if (dl == 0.f) return;
   float r;
-  if (e > 0.5f) {
-    r = ex2(fminf(e, 126.f)) - 1.f;
+  if (fabsf(dl) > 0.5f) {
+    r = fabsf(ex2(fminf(dl, 126.f)) - 1.f);
   } else {
-    const float x = e * 0.69314718f;
-    r = x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 720.f, 1.f / 120.f), 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
+    const float x = dl * 0.69314718f;
+    r = fabsf(x * fmaf(x, fmaf(x, fmaf(x, fmaf(x, fmaf(x, 1.f / 720.f, 1.f / 120.f), 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f));
   }
-  viol += fminf(cap.x * r, 1e30f);                // huge excesses stay finite (reported, not NaN)
+  const float p_old = ex2(fminf((lu_old.x + col_hi) + (lu_old.y + col_lo), 126.f));
+  viol += fminf(p_old * r, 1e30f);                // huge residuals stay finite (reported, not NaN)
 }
 
 // Capacity update of one state from its column log-sum-exp (cm + log2 cs) (Algorithm 2,
@@ -362,9 +364,9 @@ __device__ __forceinline__ void update_state(const StepArgs &a, int sk, float cm
   make_w(klh, kll, lu_hi, lu_lo, a.qs, w_hi, w_lo);
   if (!write) return;
   const float2 lu_old = a.lu_t[sk];
-  if (col_hi > kNegThresh && fin) add_excess(cap, lu_old, col_hi, col_lo, a.logd_hi[sk], a.logd_lo[sk], viol);
-  if (col_hi != col_hi || col_lo != col_lo) viol = __int_as_float(0x7fc00000);   // NaN: reported
   const float2 lu_new = lu_hi < kNegThresh ? make_float2(kNeg, 0.f) : make_float2(lu_hi, lu_lo);
+  if (col_hi > kNegThresh && fin) add_residual(lu_old, lu_new, col_hi, col_lo, viol);
+  if (col_hi != col_hi || col_lo != col_lo) viol = __int_as_float(0x7fc00000);   // NaN: reported
   if (fin && cap.x > 0.f && lu_new.x > kNegThresh) ff_mac(dual, cap, lu_new);
   a.lu_t[sk] = lu_new;
   a.w_hi_t[sk] = w_hi;
@@ -458,9 +460,9 @@ __device__ __forceinline__ void update_stats(int mode, float col_hi, float col_l
     return;
   }
   const bool fin = cap.x < INFINITY;
-  if (col_hi > kNegThresh && fin) add_excess(cap, lu_old, col_hi, col_lo, ldh, ldl, viol);
-  if (col_hi != col_hi || col_lo != col_lo) viol = __int_as_float(0x7fc00000);
   lu_new = lu_hi < kNegThresh ? make_float2(kNeg, 0.f) : make_float2(lu_hi, lu_lo);
+  if (col_hi > kNegThresh && fin) add_residual(lu_old, lu_new, col_hi, col_lo, viol);
+  if (col_hi != col_hi || col_lo != col_lo) viol = __int_as_float(0x7fc00000);
   if (fin && cap.x > 0.f && lu_new.x > kNegThresh) ff_mac(dual, cap, lu_new);
 }
 

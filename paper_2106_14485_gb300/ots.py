@@ -52,7 +52,8 @@ class ProblemStats(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_double), ("warm_start", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("threads_per_node", ctypes.c_int32)]
+                ("threads_per_node", ctypes.c_int32), ("eps_stages", ctypes.c_int32),
+                ("eps_start", ctypes.c_double), ("eps_stage_tol", ctypes.c_double)]
 
 
 class SolveReport(ctypes.Structure):
@@ -297,10 +298,12 @@ def ots_default_solve_opts() -> SolveOpts:
 
 def ots_sinkhorn_solve(h: Handle, tol: float = 1e-6, max_iters: int = 100000, check_every: int = 10,
                        timeout_ms: float = 0.0, warm_start: bool = False, use_graph: bool = True,
-                       threads_per_node: int = 0, raise_on_error: bool = True) -> dict:
+                       threads_per_node: int = 0, raise_on_error: bool = True, eps_start: float = 0.0,
+                       eps_stages: int = 0, eps_stage_tol: float = 0.0) -> dict:
     o = ots_default_solve_opts()
     o.tol, o.max_iters, o.check_every, o.timeout_ms = tol, max_iters, check_every, timeout_ms
     o.warm_start, o.use_graph, o.threads_per_node = int(warm_start), int(use_graph), int(threads_per_node)
+    o.eps_start, o.eps_stages, o.eps_stage_tol = float(eps_start), int(eps_stages), float(eps_stage_tol)
     r = SolveReport()
     code = load_library().ots_sinkhorn_solve(h.ptr, ctypes.byref(o), ctypes.byref(r))
     if raise_on_error and code not in (OTS_OK,):
@@ -539,10 +542,11 @@ def ots_server_create(device: int = 0, pool_bytes: int = 4 << 30, max_instances:
 
 
 def ots_server_submit(s: Server, inst, tol: float = 1e-6, max_iters: int = 100000, timeout_ms: float = 0.0,
-                      check_every: int = 1) -> int:
+                      check_every: int = 1, eps_start: float = 0.0, eps_stages: int = 0) -> int:
     d, arr = _problem_desc(inst)
     o = ots_default_solve_opts()
     o.tol, o.max_iters, o.timeout_ms, o.check_every = tol, max_iters, timeout_ms, check_every
+    o.eps_start, o.eps_stages = float(eps_start), int(eps_stages)
     t = ctypes.c_int64(0)
     _check(load_library().ots_server_submit(s.ptr, ctypes.byref(d), ctypes.byref(o), ctypes.byref(t)))
     s.shapes[t.value] = (int(inst.n_nodes) + d.n_edges, d.T)
