@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--serve-drain", type=float, default=5.0, help="extra time for open requests per rate")
     ap.add_argument("--serve-large-passes", type=int, default=300,
                     help="pass limit of the traffic-scale requests in the serving mix")
+    ap.add_argument("--no-traffic-solve", action="store_true",
+                    help="skip the full solve of the traffic-scale workload (epsilon continuation)")
     ap.add_argument("--horizon", type=int, default=100,
                     help="T of the traffic-scale grid (100 = the benchmark workload; smaller values only "
                          "for profiling captures that must stay within a few GB)")
@@ -505,6 +507,23 @@ def run_ours(args):
                "d2h_bytes_per_step": int(st["d2h_bytes"]) // args.steps,
                "note": f"one call sequence of {args.steps} passes: create from host arrays, passes, flows to host, destroy"}
 
+    # ---- one full solve of the traffic-scale workload to tol, with epsilon continuation ----
+    traffic = None
+    if not args.no_traffic_solve:
+        h_t = ots.ots_create_problem(inst, device=local)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rt = ots.ots_sinkhorn_solve(h_t, tol=args.tol, max_iters=20000, eps_start=8 * inst.eps, eps_stages=3,
+                                    raise_on_error=False)
+        torch.cuda.synchronize()
+        t_t = time.perf_counter() - t0
+        ots.ots_destroy_problem(h_t)
+        traffic = {"workload": workload_config(inst, args.tol)["workload"],
+                   "continuation": f"eps {8 * inst.eps:g} -> {inst.eps:g} in 3 warm-start stages (stage tol 1e-4)",
+                   "status": rt["status"], "passes": rt["iterations"], "seconds": t_t,
+                   "solves_per_s": 1.0 / t_t if rt["status"] == 0 else 0.0,
+                   "final_src_residual": rt["src_residual"], "final_cap_violation": rt["cap_violation"]}
+
     # ---- full solves to marginal error <= tol on the random-geometric workload ----
     solves = None
     if args.solves > 0:
@@ -572,7 +591,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 float-float (fp32 hi + fp16 lo log2 messages), f64 reductions",
             "data": "synthetic", "config": workload_config(inst, args.tol),
-            "solves_per_s": solves, "batch": batch, "serving": serve,
+            "solves_per_s": solves, "traffic_solve": traffic, "batch": batch, "serving": serve,
             "passes_timed": args.steps, "src_residual_after": final["src_residual"],
             "cap_violation_after": final["cap_violation"],
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches)}
