@@ -282,6 +282,35 @@ def config1(seed: int = 0, rows: int = 5, cols: int = 5, T: int = 10, eps: float
         pos=pos, meta={"config": 1, "seed": seed})
 
 
+def single_commodity_instance(seed: int = 0, rows: int = 6, cols: int = 6, T: int = 12, eps: float = 0.3,
+                              n_src: int = 6, n_snk: int = 6, cap_scale: float = 0.08, per_interval: bool = True):
+    """The single-commodity problem (eq. singlecommodity_reg) as an instance with L = 1: a grid
+    with random move costs U[0.5, 1.5] and wait costs U[0, 0.3], initial and final distributions
+    mu_1, mu_T (Dirichlet(1)) over random states (edges and wait loops), and moving-edge
+    capacities cap_scale x U[0.5, 1.5] (per interval t = 2..T-1 when per_interval)."""
+    rng = np.random.default_rng(seed)
+    src, dst, pos = grid_graph(rows, cols)
+    n, E = rows * cols, src.shape[0]
+    S = n + E
+    s_states = np.sort(rng.choice(S, n_src, replace=False)).astype(np.int32)
+    z_states = np.sort(rng.choice(S, n_snk, replace=False)).astype(np.int32)
+    inst = Instance(
+        name=f"single{rows}x{cols}-T{T}", n_nodes=n, edge_src=src, edge_dst=dst,
+        edge_cost=rng.uniform(0.5, 1.5, E), edge_cap=np.full(E, np.inf),
+        wait_cost=rng.uniform(0.0, 0.3, n), wait_cap=np.full(n, np.inf),
+        L=1, T=T, eps=eps,
+        src_comm=np.zeros(n_src, np.int32), src_state=s_states, src_mass=rng.dirichlet(np.ones(n_src)),
+        snk_comm=np.zeros(n_snk, np.int32), snk_state=z_states, snk_mass=rng.dirichlet(np.ones(n_snk)),
+        pos=pos, meta={"seed": seed, "single_commodity": True})
+    cap = np.concatenate([cap_scale * rng.uniform(0.5, 1.5, E), np.full(n, np.inf)])
+    if per_interval:
+        inst.state_capacity_t = cap[None, :] * rng.uniform(0.7, 1.3, (T - 2, S))
+        inst.state_capacity_t[:, E:] = np.inf
+    else:
+        inst.edge_cap = cap[:E].copy()
+    return inst
+
+
 def rgg_instance(seed: int = 0, n: int = 400, L: int = 64, T: int = 50, eps: float = 0.01,
                  mean_degree: float = 6.0, wait_cost: float = 0.05, cap_lo: float = 0.2,
                  cap_hi: float = 1.0, cap_div: float = 8.0, name: Optional[str] = None,
