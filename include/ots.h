@@ -106,6 +106,13 @@ typedef struct ots_problem_desc {
                                     state in that interval.  When given, edge_capacity and
                                     wait_capacity are not used.  NaN or negative entries give
                                     OTS_ERR_INVALID_ARG. */
+  int32_t psi_stride;            /* k > 1: keep the backward messages Psi_t only for t = 2, T and
+                                    every k-th t below T, and recompute the others (k - 1 at a
+                                    time, from the kept one above) whenever a forward sweep needs
+                                    them: about T/k + k message panels instead of T - 1, for about
+                                    (k-1)/k more backward steps per pass; results are bitwise the
+                                    same.  0 or 1 = keep all (default).  Ignored in a batch.
+                                    Negative values give OTS_ERR_INVALID_ARG. */
 } ots_problem_desc;
 
 /* Options of ots_sinkhorn_solve. */

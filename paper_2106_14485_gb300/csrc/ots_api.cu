@@ -155,7 +155,22 @@ ots_status enqueue_backward_sweep(ots_problem *p) {
   return OTS_OK;
 }
 
-long long kernels_per_pass(const ots_problem *p) { return 2LL * p->T; }
+// With backward panels kept only every bk-th t, a forward step t whose B_{t+1} has no slot of
+// its own starts a segment: the panels up to the next kept one are recomputed by backward steps
+// from it, with the weights the last backward sweep used (the forward sweep has not updated
+// them yet), so they equal the panels that sweep computed.
+cudaError_t enqueue_segment(ots_problem *p, int t) {
+  if (p->bk <= 1 || p->b_stored(t + 1) || !p->b_stored(t)) return cudaSuccess;
+  int hi = t + 2;
+  while (!p->b_stored(hi)) ++hi;
+  for (int tt = hi - 1; tt >= t + 1; --tt) {
+    cudaError_t e = launch_step(false, p->pc, p->G, p->C, step_args(p, false, tt, 0), p->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+long long kernels_per_pass(const ots_problem *p) { return 2LL * p->T + p->b_recompute; }
 
 // One pass of the while loop of Algorithm 2 (enqueued directly or captured into a graph),
 // with phase events around the source update, the forward sweep, the sink update and the
@@ -167,8 +182,10 @@ ots_status enqueue_pass(ots_problem *p, bool capture) {
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[0], p->stream, flags));
   OTS_CUDA(launch_boundary(bnd_args(p, true, 0), p->stream));                 // U01, hatPsi_2
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[1], p->stream, flags));
-  for (int t = 2; t <= p->T - 1; ++t)                                          // u_t, hatPsi_{t+1}
+  for (int t = 2; t <= p->T - 1; ++t) {                                        // u_t, hatPsi_{t+1}
+    OTS_CUDA(enqueue_segment(p, t));
     OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 0), p->stream));
+  }
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[2], p->stream, flags));
   OTS_CUDA(launch_boundary(bnd_args(p, false, 0), p->stream));                // U0T, Psi_{T-1}
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[3], p->stream, flags));
@@ -468,6 +485,27 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   p->pc = d->commodity_cost != nullptr;
   p->member = co.member;
   if (p->S < 1) { delete p; return fail(OTS_ERR_INVALID_ARG, "no states"); }
+  if (d->psi_stride < 0) { delete p; return fail(OTS_ERR_INVALID_ARG, "psi_stride must be >= 0"); }
+  p->bk = co.member ? 1 : std::max(1, (int)d->psi_stride);
+  {
+    // slots of the backward panels: one per kept t, then k - 1 shared recompute slots (a
+    // t between two kept ones uses slot first_recompute + (next kept above t) - 1 - t)
+    p->bslot.assign((size_t)p->T + 1, 0);
+    int nk = 0;
+    for (int t = 2; t <= p->T; ++t)
+      if (p->b_stored(t)) p->bslot[t] = nk++;
+    int maxgap = 0;
+    p->b_recompute = 0;
+    for (int t = 2; t <= p->T; ++t) {
+      if (p->b_stored(t)) continue;
+      int hi = t + 1;
+      while (!p->b_stored(hi)) ++hi;
+      p->bslot[t] = nk + (hi - 1 - t);
+      maxgap = std::max(maxgap, hi - t);
+      ++p->b_recompute;
+    }
+    p->nbslots = nk + maxgap;
+  }
   if (co.member) {
     if (p->pc) { delete p; return fail(OTS_ERR_INVALID_ARG, "batched instances take commodity-independent costs"); }
     if (!d->stream) { delete p; return fail(OTS_ERR_INVALID_ARG, "batch member without a stream"); }
@@ -761,7 +799,7 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
          o_wout_lo = cv.take<float>((T + 1) * Sc), o_cref_in = cv.take<float>((T + 1) * Sc);
   size_t o_a_hi[3], o_a_lo[3];
   for (int k = 0; k < 3; ++k) { o_a_hi[k] = cv.take<float>(panel); o_a_lo[k] = cv.take<lo_t>(panel); }
-  size_t o_b_hi = cv.take<float>((T - 1) * panel), o_b_lo = cv.take<lo_t>((T - 1) * panel);
+  size_t o_b_hi = cv.take<float>((size_t)p->nbslots * panel), o_b_lo = cv.take<lo_t>((size_t)p->nbslots * panel);
   size_t o_stats = cv.take<DevStats>(1), o_report = cv.take<PassReport>(1);
   size_t o_partials = cv.take<double>(3 * (size_t)max_grid), o_counter = cv.take<unsigned int>(4);
   struct BOff { size_t seg_ptr, seg_node, seg_l, other, l, R, logR, logU, flow; } bo[2];
@@ -1042,10 +1080,12 @@ ots_status ots_sinkhorn_solve(ots_problem *p, const ots_solve_opts *opts, ots_so
 static ots_status flows_pass(ots_problem *p) {
   ots_status st = refresh_if_stale(p);
   if (st) return st;
-  p->kernels_launched += 1 + (p->T - 2) + 2;
+  p->kernels_launched += 1 + (p->T - 2) + 2 + p->b_recompute;
   OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
-  for (int t = 2; t <= p->T - 1; ++t)
+  for (int t = 2; t <= p->T - 1; ++t) {
+    OTS_CUDA(enqueue_segment(p, t));
     OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
+  }
   OTS_CUDA(launch_boundary_flows(p->src.n, p->Lp, p->qs, p->src.d_tri_l, p->src.d_tri_other, p->src.d_tri_logU, p->b_hi(2),
                                  p->b_lo(2), p->src.d_flow, p->stream));
   OTS_CUDA(launch_boundary_flows(p->snk.n, p->Lp, p->qs, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
@@ -1104,6 +1144,7 @@ ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_en
   };
   check(launch_boundary(bnd_args(p, true, 1), p->stream));
   for (int t = 2; t <= p->T - 1 && rc == OTS_OK; ++t) {
+    check(enqueue_segment(p, t));
     if (t >= t_begin && t < t_end) {
       // A_{t-1} is current here (written by the previous forward step of this pass)
       check(launch_commodity_flows(p->S, p->Lp, p->qs, l_begin, l_end, p->d_tail, p->d_head, p->a_hi(t - 1), p->a_lo(t - 1),
@@ -1219,6 +1260,7 @@ ots_status ots_get_commodity_flows_noalloc(ots_problem *p, int32_t t_begin, int3
   // forward pass at the current duals; interior rows come from the message panels
   OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
   for (int t = 2; t <= p->T - 1; ++t) {
+    OTS_CUDA(enqueue_segment(p, t));
     if (t >= t_begin && t < t_end) {
       OTS_CUDA(launch_commodity_flows(p->S, p->Lp, p->qs, l_begin, l_end, p->d_tail, p->d_head, p->a_hi(t - 1),
                                       p->a_lo(t - 1), p->b_hi(t + 1), p->b_lo(t + 1),
@@ -1236,7 +1278,7 @@ ots_status ots_get_commodity_flows_noalloc(ots_problem *p, int32_t t_begin, int3
                                  p->b_hi(2), p->b_lo(2), p->src.d_flow, p->stream));
   OTS_CUDA(launch_boundary_flows(p->snk.n, p->Lp, p->qs, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
                                  p->a_hi(p->T - 1), p->a_lo(p->T - 1), p->snk.d_flow, p->stream));
-  p->kernels_launched += 1 + (p->T - 2) + 2;
+  p->kernels_launched += 1 + (p->T - 2) + 2 + p->b_recompute;
   // boundary rows t = 1 (sources) and t = T (sinks): scatter the per-triple flows into the
   // zeroed slice; the states of the triples are copied from the problem's host-side list
   for (int t : {1, p->T}) {

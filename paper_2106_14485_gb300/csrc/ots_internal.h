@@ -168,7 +168,7 @@ struct ots_problem {
   double *d_flow = nullptr;                    // [T+1][S]
   float *d_a_hi[3] = {nullptr, nullptr, nullptr};
   lo_t *d_a_lo[3] = {nullptr, nullptr, nullptr};
-  float *d_b_hi = nullptr;                     // [(T-1)][V][Lp], row t-2
+  float *d_b_hi = nullptr;                     // [nbslots][V][Lp]
   lo_t *d_b_lo = nullptr;
   DevStats *d_stats = nullptr;
   PassReport *d_report = nullptr;
@@ -186,6 +186,13 @@ struct ots_problem {
   size_t panel() const { return (size_t)V * Lp; }
   float *a_hi(int t) { return t == 1 ? d_a_hi[0] : d_a_hi[1 + (t & 1)]; }
   lo_t *a_lo(int t) { return t == 1 ? d_a_lo[0] : d_a_lo[1 + (t & 1)]; }
-  float *b_hi(int t) { return d_b_hi + (size_t)(t - 2) * panel(); }
-  lo_t *b_lo(int t) { return d_b_lo + (size_t)(t - 2) * panel(); }
+  // backward panels: B_t lives in slot bslot[t]; with bk > 1 only t = 2, T and every bk-th t
+  // below T keep their own slot, the others share k - 1 recompute slots
+  int bk = 1;
+  int nbslots = 0;
+  int b_recompute = 0;                         // backward steps a forward sweep adds
+  std::vector<int> bslot;
+  bool b_stored(int t) const { return bk <= 1 || t == 2 || t == T || (T - t) % bk == 0; }
+  float *b_hi(int t) { return d_b_hi + (size_t)bslot[t] * panel(); }
+  lo_t *b_lo(int t) { return d_b_lo + (size_t)bslot[t] * panel(); }
 };

@@ -38,6 +38,7 @@ class ProblemDesc(ctypes.Structure):
         ("alloc", ALLOC_FN), ("free_fn", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
         ("state_cost_t", _f64p),
         ("state_capacity_t", _f64p),
+        ("psi_stride", ctypes.c_int32),
     ]
 
 
@@ -271,12 +272,15 @@ def _problem_desc(inst, device: int = 0, stream: int | None = None):
     return d, arr
 
 
-def ots_create_problem(inst, device: int = 0, stream: int | None = None, allocator: str = "torch") -> Handle:
+def ots_create_problem(inst, device: int = 0, stream: int | None = None, allocator: str = "torch",
+                       psi_stride: int = 0) -> Handle:
     """Create a problem from an object with the attributes of ``instances.Instance``.
 
-    allocator: "torch" (PyTorch caching allocator) or "cuda" (cudaMalloc inside the library)."""
+    allocator: "torch" (PyTorch caching allocator) or "cuda" (cudaMalloc inside the library);
+    psi_stride: keep the backward messages every psi_stride-th t only (0 = all)."""
     lib = load_library()
     d, arr = _problem_desc(inst, device, stream)
+    d.psi_stride = int(psi_stride)
     keep = [arr]
     if allocator == "torch":
         a, f = _torch_allocator(int(device))
