@@ -55,6 +55,8 @@ def _load():
     lib.orc_set_time_costs.restype = ctypes.c_int
     lib.orc_set_time_capacities.argtypes = [ctypes.c_void_p, _f64p]
     lib.orc_set_time_capacities.restype = ctypes.c_int
+    lib.orc_set_windows.argtypes = [ctypes.c_void_p, _i32p, _i32p]
+    lib.orc_set_windows.restype = ctypes.c_int
     lib.orc_set_threads.argtypes = [ctypes.c_int]
     lib.orc_get_threads.restype = ctypes.c_int
     lib.orc_num_states.argtypes = [ctypes.c_void_p]
@@ -138,6 +140,13 @@ class Oracle:
                 raise ValueError("state_capacity_t must be (T-2) x n_states")
             if lib.orc_set_time_capacities(self.h, dt.reshape(-1)):
                 raise ValueError("oracle: per-interval capacities must be >= 0 (inf for none)")
+        ta = getattr(inst, "commodity_t_in", None)
+        tb = getattr(inst, "commodity_t_out", None)
+        if ta is not None or tb is not None:
+            ta = np.ascontiguousarray(np.ones(self.L) if ta is None else ta, np.int32)
+            tb = np.ascontiguousarray(np.full(self.L, self.T) if tb is None else tb, np.int32)
+            if lib.orc_set_windows(self.h, ta, tb):
+                raise ValueError("oracle: commodity windows need 1 <= t_in < t_out <= T")
         lib.orc_init_duals(self.h)
 
     def __del__(self):

@@ -61,6 +61,7 @@ typedef struct orc {
   int tv;                      /* time-varying costs set by orc_set_time_costs */
   double *d;                   /* [S] */
   double *dt;                  /* [(T+1)*S] per-interval capacities (row t), or NULL */
+  int *ta, *tb;                /* [L] entry and exit time of each commodity, or NULL (1 and T) */
   double *R01, *R0T;           /* [L*S] dense */
   double *logu;                /* [T*S], row t (1-based) used for t = 2..T-1 */
   double *logU01, *logU0T;     /* [L*S] */
@@ -93,7 +94,7 @@ int orc_get_threads(void) {
 void orc_destroy(orc *o) {
   if (!o) return;
   free(o->tail); free(o->head); free(o->pred_ptr); free(o->pred_idx);
-  free(o->succ_ptr); free(o->succ_idx); free(o->logKL); free(o->d); free(o->dt);
+  free(o->succ_ptr); free(o->succ_idx); free(o->logKL); free(o->d); free(o->dt); free(o->ta); free(o->tb);
   free(o->R01); free(o->R0T); free(o->logu); free(o->logU01); free(o->logU0T);
   free(o->psi); free(o->ph_a); free(o->ph_b);
   free(o);
@@ -219,6 +220,30 @@ int orc_set_time_capacities(orc *o, const double *cap_t) {
   free(o->dt);
   o->dt = d;
   return ORC_OK;
+}
+
+/* Per-commodity entry and exit times (the multi-tensor scheme of the Remark after
+ * Algorithm 2, where commodities enter and leave at different times): commodity l has its
+ * source marginal at time a[l] and its sink marginal at b[l], 1 <= a[l] < b[l] <= T; it is
+ * absent before a[l] and after b[l] and counts in the capacity sums at a[l] < t < b[l]. */
+int orc_set_windows(orc *o, const int *a, const int *b) {
+  for (int l = 0; l < o->L; ++l)
+    if (a[l] < 1 || b[l] > o->T || a[l] >= b[l]) return ORC_BAD_ARG;
+  free(o->ta); free(o->tb);
+  o->ta = (int *)malloc(sizeof(int) * o->L);
+  o->tb = (int *)malloc(sizeof(int) * o->L);
+  if (!o->ta || !o->tb) return ORC_NOMEM;
+  memcpy(o->ta, a, sizeof(int) * o->L);
+  memcpy(o->tb, b, sizeof(int) * o->L);
+  return ORC_OK;
+}
+
+static int t_in(const orc *o, int l) { return o->ta ? o->ta[l] : 1; }
+static int t_out(const orc *o, int l) { return o->tb ? o->tb[l] : o->T; }
+
+/* commodity l's row of a message array is log 0 (the commodity is absent at that time) */
+static void set_absent(const orc *o, double *x, int l) {
+  for (int s = 0; s < o->S; ++s) x[(size_t)l * o->S + s] = -INFINITY;
 }
 
 /* capacity of state s in interval t */
@@ -373,15 +398,17 @@ int orc_backward_sweep(orc *o) {
   const int T = o->T;
   size_t LS = (size_t)o->L * o->S;
   bwd_product(o, o->logU0T, 0, o->psi + (size_t)(T - 1) * LS, 0, o->L);        /* Psi_{T-1} = U0T K^T */
-  for (int t = T - 1; t >= 2; --t)                                             /* Psi_{t-1} */
+  for (int l = 0; l < o->L; ++l)                   /* commodities that leave before T are absent */
+    if (t_out(o, l) != T) set_absent(o, o->psi + (size_t)(T - 1) * LS, l);
+  for (int t = T - 1; t >= 2; --t) {                                           /* Psi_{t-1} */
     bwd_product(o, o->psi + (size_t)t * LS, t, o->psi + (size_t)(t - 1) * LS, 0, o->L);
+    for (int l = 0; l < o->L; ++l)                 /* leaving at t: Psi_{t-1} = U0T K^T */
+      if (t_out(o, l) == t)
+        bwd_product(o, o->logU0T + (size_t)l * o->S, 0, o->psi + (size_t)(t - 1) * LS + (size_t)l * o->S, l, l + 1);
+  }
   return ORC_OK;
 }
 
-/* One pass of the while loop of Algorithm 2.  Requires orc_backward_sweep to have been run
- * for the current duals (orc_solve does this).  Outputs the two convergence measures and,
- * if trace != NULL, the dual objective after every block update (T entries: after U01,
- * after u_2 .. u_{T-1}, after U0T). */
 /* |P_new - P_old| of one capacity update, P = exp(log u + ls): the excess (P_old - d)_+ where
  * u_t drops, the withheld flow where it rises (from a warm start below the fixed point). */
 static double flow_change(double lu_old, double lu_new, double ls) {
@@ -391,30 +418,37 @@ static double flow_change(double lu_old, double lu_new, double ls) {
   return exp(lu_old + ls) * fabs(expm1(lu_new - lu_old));
 }
 
+/* One pass of the while loop of Algorithm 2.  Requires orc_backward_sweep to have been run
+ * for the current duals (orc_solve does this).  Outputs the two convergence measures and,
+ * if trace != NULL, the dual objective after every block update (T entries: after U01,
+ * after u_2 .. u_{T-1}, after U0T). */
 int orc_iteration(orc *o, double *src_resid, double *cap_viol, double *trace) {
   if (!o->psi) return ORC_BAD_ARG;
   const int S = o->S, L = o->L, T = o->T;
   size_t LS = (size_t)L * S;
-  const double *psi1 = o->psi + 1 * LS;
   int bad = 0;
 
-  /* U01 <- R01 ./ Psi_1, with the mismatch |U01 .* Psi_1 - R01| taken just before. */
+  /* U01 <- R01 ./ Psi_1 (Psi_a for a commodity entering at a), with the mismatch
+   * |U01 .* Psi_1 - R01| taken just before. */
   double resid = 0.0, mass_now = 0.0;
   for (size_t q = 0; q < LS; ++q) {
     if (o->R01[q] > 0) {
-      resid += fabs(exp(o->logU01[q] + psi1[q]) - o->R01[q]);
-      if (!(psi1[q] > -INFINITY)) bad = 1;
-      o->logU01[q] = log(o->R01[q]) - psi1[q];
-      mass_now += exp(o->logU01[q] + psi1[q]);
+      const double p1 = o->psi[(size_t)t_in(o, (int)(q / S)) * LS + q];
+      resid += fabs(exp(o->logU01[q] + p1) - o->R01[q]);
+      if (!(p1 > -INFINITY)) bad = 1;
+      o->logU01[q] = log(o->R01[q]) - p1;
+      mass_now += exp(o->logU01[q] + p1);
     }
   }
   if (bad) return ORC_INFEASIBLE;
   if (src_resid) *src_resid = resid / o->mass01;
   if (trace) trace[0] = -o->eps * mass_now + dual_linear_part(o);
 
-  /* hatPsi_2 <- U01 K */
+  /* hatPsi_2 <- U01 K (commodities entering later are absent) */
   double *ph = o->ph_a, *pn = o->ph_b;
   fwd_product(o, o->logU01, 0, ph, 0, L);
+  for (int l = 0; l < L; ++l)
+    if (t_in(o, l) != 1) set_absent(o, ph, l);
 
   double *ls = (double *)malloc(sizeof(double) * S);
   double viol = 0.0;
@@ -437,14 +471,26 @@ int orc_iteration(orc *o, double *src_resid, double *cap_viol, double *trace) {
     if (trace) trace[t - 1] = -o->eps * mass_t + dual_linear_part(o);
     /* hatPsi_{t+1} <- (hatPsi_t .* K_L) diag(u_t) K */
     fwd_product(o, ph, t, pn, 0, L);
+    for (int l = 0; l < L; ++l) {
+      if (t_in(o, l) == t)                         /* entering at t: hatPsi_{t+1} = U01 K */
+        fwd_product(o, o->logU01 + (size_t)l * S, 0, pn + (size_t)l * S, l, l + 1);
+      if (t_out(o, l) == t + 1 && t + 1 < T)       /* leaving at t+1 < T: U0T <- R0T ./ hatPsi_{t+1} */
+        for (int s = 0; s < S; ++s) {
+          const size_t q = (size_t)l * S + s;
+          if (o->R0T[q] > 0) {
+            if (!(pn[q] > -INFINITY)) bad = 1;
+            o->logU0T[q] = log(o->R0T[q]) - pn[q];
+          }
+        }
+    }
     double *tmp = ph; ph = pn; pn = tmp;
   }
   free(ls);
 
-  /* U0T <- R0T ./ hatPsi_T */
+  /* U0T <- R0T ./ hatPsi_T  (commodities leaving at T) */
   mass_now = 0.0;
   for (size_t q = 0; q < LS; ++q) {
-    if (o->R0T[q] > 0) {
+    if (o->R0T[q] > 0 && t_out(o, (int)(q / S)) == T) {
       if (!(ph[q] > -INFINITY)) bad = 1;
       o->logU0T[q] = log(o->R0T[q]) - ph[q];
       mass_now += exp(o->logU0T[q] + ph[q]);
@@ -464,7 +510,7 @@ double orc_dual_objective(orc *o) {
   size_t LS = (size_t)o->L * o->S;
   double mass_now = 0.0;
   for (size_t q = 0; q < LS; ++q)
-    if (o->R01[q] > 0) mass_now += exp(o->logU01[q] + o->psi[1 * LS + q]);
+    if (o->R01[q] > 0) mass_now += exp(o->logU01[q] + o->psi[(size_t)t_in(o, (int)(q / o->S)) * LS + q]);
   return -o->eps * mass_now + dual_linear_part(o);
 }
 
@@ -501,10 +547,24 @@ int orc_messages(orc *o, int l0, int l1, double *psihat, double *psi) {
   if (!h || !b) { free(h); free(b); return ORC_NOMEM; }
   /* forward: hatPsi_2 = U01 K, hatPsi_{t+1} = (hatPsi_t .* K_L) diag(u_t) K */
   fwd_product(o, o->logU01 + (size_t)l0 * S, 0, h, l0, l1);
-  for (int t = 2; t <= T - 1; ++t) fwd_product(o, h + (size_t)(t - 2) * blk, t, h + (size_t)(t - 1) * blk, l0, l1);
+  for (int l = l0; l < l1; ++l)
+    if (t_in(o, l) != 1) set_absent(o, h, l - l0);
+  for (int t = 2; t <= T - 1; ++t) {
+    fwd_product(o, h + (size_t)(t - 2) * blk, t, h + (size_t)(t - 1) * blk, l0, l1);
+    for (int l = l0; l < l1; ++l)                  /* entering at t: hatPsi_{t+1} = U01 K */
+      if (t_in(o, l) == t)
+        fwd_product(o, o->logU01 + (size_t)l * S, 0, h + (size_t)(t - 1) * blk + (size_t)(l - l0) * S, l, l + 1);
+  }
   /* backward: Psi_{T-1} = U0T K^T, Psi_{t-1} = (Psi_t .* K_L) diag(u_t) K^T  (row t-1 holds Psi_t) */
   bwd_product(o, o->logU0T + (size_t)l0 * S, 0, b + (size_t)(T - 2) * blk, l0, l1);
-  for (int t = T - 1; t >= 2; --t) bwd_product(o, b + (size_t)(t - 1) * blk, t, b + (size_t)(t - 2) * blk, l0, l1);
+  for (int l = l0; l < l1; ++l)
+    if (t_out(o, l) != T) set_absent(o, b + (size_t)(T - 2) * blk, l - l0);
+  for (int t = T - 1; t >= 2; --t) {
+    bwd_product(o, b + (size_t)(t - 1) * blk, t, b + (size_t)(t - 2) * blk, l0, l1);
+    for (int l = l0; l < l1; ++l)                  /* leaving at t: Psi_{t-1} = U0T K^T */
+      if (t_out(o, l) == t)
+        bwd_product(o, o->logU0T + (size_t)l * S, 0, b + (size_t)(t - 2) * blk + (size_t)(l - l0) * S, l, l + 1);
+  }
   if (psihat) memcpy(psihat, h, sizeof(double) * blk * (T - 1));
   if (psi) memcpy(psi, b, sizeof(double) * blk * (T - 1));
   free(h); free(b);
@@ -523,16 +583,18 @@ int orc_projections(orc *o, int l0, int l1, double *out) {
   int rc = orc_messages(o, l0, l1, h, b);
   if (rc) { free(h); free(b); return rc; }
   for (int l = l0; l < l1; ++l) {
+    const int a = t_in(o, l), z = t_out(o, l);
     for (int s = 0; s < S; ++s) {
       size_t q = (size_t)(l - l0) * S + s;
-      /* t = 1: U01 .* Psi_1 */
-      out[q] = exp(o->logU01[(size_t)l * S + s] + b[q]);
-      /* t = 2..T-1: hatPsi_t .* Psi_t .* K_L .* u_t */
-      for (int t = 2; t <= T - 1; ++t)
+      for (int t = 1; t <= T; ++t) out[(size_t)(t - 1) * blk + q] = 0.0;
+      /* t = a: U01 .* Psi_a  (row a-1 of b holds Psi_a) */
+      out[(size_t)(a - 1) * blk + q] = exp(o->logU01[(size_t)l * S + s] + b[(size_t)(a - 1) * blk + q]);
+      /* a < t < z: hatPsi_t .* Psi_t .* K_L .* u_t */
+      for (int t = a + 1; t <= z - 1; ++t)
         out[(size_t)(t - 1) * blk + q] = exp(h[(size_t)(t - 2) * blk + q] + b[(size_t)(t - 1) * blk + q] +
                                              kl_row(o, t, l)[s] + o->logu[(size_t)t * S + s]);
-      /* t = T: U0T .* hatPsi_T */
-      out[(size_t)(T - 1) * blk + q] = exp(o->logU0T[(size_t)l * S + s] + h[(size_t)(T - 2) * blk + q]);
+      /* t = z: U0T .* hatPsi_z  (row z-2 of h holds hatPsi_z) */
+      out[(size_t)(z - 1) * blk + q] = exp(o->logU0T[(size_t)l * S + s] + h[(size_t)(z - 2) * blk + q]);
     }
   }
   free(h); free(b);

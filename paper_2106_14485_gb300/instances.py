@@ -52,6 +52,8 @@ class Instance:
     commodity_cost: Optional[np.ndarray] = None   # [L, S] per-commodity state costs
     state_cost_t: Optional[np.ndarray] = None     # [T-2, S] per-interval state costs (t = 2..T-1)
     state_capacity_t: Optional[np.ndarray] = None  # [T-2, S] per-interval capacities d_t (inf: none)
+    commodity_t_in: Optional[np.ndarray] = None   # [L] entry time of each commodity (1..T-1)
+    commodity_t_out: Optional[np.ndarray] = None  # [L] exit time of each commodity (t_in+1..T)
     meta: dict = field(default_factory=dict)
 
     # ---- derived sizes / per-state views (data assembly only) ----
@@ -405,6 +407,17 @@ def with_time_varying_capacities(inst, seed: int = 0, lo: float = 0.5, hi: float
     for _ in range(closures):
         dt[rng.integers(inst.T - 2), rng.integers(inst.n_edges)] = 0.0
     inst.state_capacity_t = dt
+    return inst
+
+
+def with_commodity_windows(inst, seed: int = 0, min_len: int = 3):
+    """Entry and exit times per commodity (the multi-tensor scheme): t_in uniform on
+    1..T-min_len+1, then t_out uniform on t_in+min_len-1..T (at least min_len times)."""
+    rng = np.random.default_rng(seed)
+    a = rng.integers(1, inst.T - min_len + 2, inst.L)
+    b = np.array([rng.integers(x + min_len - 1, inst.T + 1) for x in a])
+    inst.commodity_t_in = a.astype(np.int32)
+    inst.commodity_t_out = b.astype(np.int32)
     return inst
 
 

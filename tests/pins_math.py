@@ -275,3 +275,65 @@ def lp_optimum(inst):
     res = linprog(c, A_ub=Aub, b_ub=bub if r else None, A_eq=Aeq, b_eq=beq, bounds=(0, None), method="highs")
     assert res.status == 0, res.message
     return float(res.fun)
+
+
+def window_tensor_sinkhorn(inst, iters=20000, tol=1e-13):
+    """Proposition 5 on the multi-tensor problem of the Remark after Algorithm 2, with each
+    commodity's tensor over its own times a_l..b_l (paths of length b_l - a_l + 1, K_L and the
+    shared u_t at its interior times) and the capacity sums over the commodities inside their
+    windows; full enumeration for tiny instances.  Returns a function P(l, t) -> [S] (zero
+    outside the window)."""
+    K = dense_K(inst)
+    L, T, S = inst.L, inst.T, inst.n_edges + inst.n_nodes
+    a = np.asarray(inst.commodity_t_in)
+    b = np.asarray(inst.commodity_t_out)
+    R01, R0T = dense_marginals(inst)
+    KL = np.exp(-cost_matrix(inst) / inst.eps)
+    paths, base = [], []
+    for l in range(L):
+        p = all_paths(S, int(b[l] - a[l] + 1))
+        w = np.ones(len(p))
+        for k in range(p.shape[1] - 1):
+            w *= K[p[:, k], p[:, k + 1]]
+        for k in range(1, p.shape[1] - 1):
+            w *= KL[l, p[:, k]]
+        keep = w > 0
+        paths.append(p[keep])
+        base.append(w[keep])
+    u = np.ones((T + 1, S))
+    U01 = (R01 > 0).astype(float)
+    U0T = (R0T > 0).astype(float)
+
+    def M(l):
+        p = paths[l]
+        w = base[l] * U01[l, p[:, 0]] * U0T[l, p[:, -1]]
+        for k in range(1, p.shape[1] - 1):
+            w = w * u[a[l] + k][p[:, k]]
+        return w
+
+    def proj(l, t):
+        if t < a[l] or t > b[l]:
+            return np.zeros(S)
+        return np.bincount(paths[l][:, t - a[l]], weights=M(l), minlength=S)
+
+    for _ in range(iters):
+        err = 0.0
+        for l in range(L):
+            P = proj(l, a[l])
+            err += np.abs(P - R01[l]).sum()
+            U01[l] = np.where(R01[l] > 0, U01[l] * R01[l] / np.where(P > 0, P, 1), 0.0)
+        excess = 0.0
+        for t in range(T - 1, 1, -1):
+            Pt = sum(proj(l, t) for l in range(L) if a[l] < t < b[l]) + np.zeros(S)
+            d = capacity_at(inst, t)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                upd = np.where(Pt > 0, u[t] * d / Pt, 1.0)
+            u_new = np.minimum(upd, 1.0)
+            excess += np.abs((u_new - u[t]) * np.where(u[t] > 0, Pt / np.where(u[t] > 0, u[t], 1), 0)).sum()
+            u[t] = u_new
+        for l in range(L):
+            P = proj(l, b[l])
+            U0T[l] = np.where(R0T[l] > 0, U0T[l] * R0T[l] / np.where(P > 0, P, 1), 0.0)
+        if err / R01.sum() < tol and excess / R01.sum() < tol:
+            break
+    return proj

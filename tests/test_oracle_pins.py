@@ -385,3 +385,44 @@ def test_per_interval_capacities_kkt_and_reductions():
     assert n_active > 0
     zero = dt == 0.0
     assert zero.any() and np.all(F3[1:-1][zero] == 0.0)
+
+
+# ---------------------------------------------------------------------------------------
+# per-commodity entry and exit times (the multi-tensor scheme of the Remark after Algorithm 2)
+# ---------------------------------------------------------------------------------------
+
+def test_windows_fixed_point_matches_the_multi_tensor_problem():
+    inst = tiny_instance(seed=11, T=6, L=3, cap_scale=0.8, eps=0.5, per_commodity=False)
+    inst.commodity_t_in = np.array([2, 1, 3], np.int32)
+    inst.commodity_t_out = np.array([6, 4, 6], np.int32)
+    o = Oracle(inst)
+    r = o.solve(max_iters=50000, tol=1e-13)
+    assert r["status"] == 0 and r["src_resid"] < 1e-12 and r["cap_viol"] < 1e-12
+    P = o.projections()
+    proj = PM.window_tensor_sinkhorn(inst)
+    for l in range(inst.L):
+        for t in range(1, inst.T + 1):
+            np.testing.assert_allclose(P[t - 1, l], proj(l, t), rtol=1e-7, atol=1e-9)
+    R01, R0T = PM.dense_marginals(inst)
+    for l in range(inst.L):                             # marginals at the commodity's own times
+        np.testing.assert_allclose(P[inst.commodity_t_in[l] - 1, l], R01[l], atol=1e-12)
+        np.testing.assert_allclose(P[inst.commodity_t_out[l] - 1, l], R0T[l], atol=1e-11)
+
+
+def test_windows_shifted_in_time_reproduce_the_shorter_horizon():
+    """All commodities present from t = 3 to t = 9 of a T = 11 horizon solve the T = 7 problem
+    (time-invariant costs and capacities), shifted by two intervals; nothing flows outside."""
+    short = I.rgg_instance(seed=4, n=40, L=3, T=7, eps=0.05, cap_lo=0.3, cap_hi=1.0)
+    o0 = Oracle(short)
+    o0.solve(max_iters=100000, tol=1e-12)
+    F0 = o0.flows()
+    long = I.rgg_instance(seed=4, n=40, L=3, T=7, eps=0.05, cap_lo=0.3, cap_hi=1.0)
+    long.T = 11
+    long.commodity_t_in = np.full(3, 3, np.int32)
+    long.commodity_t_out = np.full(3, 9, np.int32)
+    o1 = Oracle(long)
+    r = o1.solve(max_iters=100000, tol=1e-12)
+    assert r["status"] == 0
+    F1 = o1.flows()
+    np.testing.assert_allclose(F1[2:9], F0, rtol=1e-9, atol=1e-12)
+    assert np.all(F1[:2] == 0.0) and np.all(F1[9:] == 0.0)
