@@ -113,6 +113,15 @@ typedef struct ots_problem_desc {
                                     (k-1)/k more backward steps per pass; results are bitwise the
                                     same.  0 or 1 = keep all (default).  Ignored in a batch.
                                     Negative values give OTS_ERR_INVALID_ARG. */
+  const int32_t *commodity_t_in;  /* optional [L]: entry time a_l of each commodity (the
+                                    multi-tensor scheme of the Remark after Algorithm 2, where
+                                    commodities enter and leave at different times): its sources
+                                    are its marginal at a_l, its sinks its marginal at b_l
+                                    (commodity_t_out), 1 <= a_l < b_l <= T; it is absent outside
+                                    [a_l, b_l] and counts in the capacity sums at a_l < t < b_l.
+                                    NULL: a_l = 1.  Not with psi_stride > 1; the batched solver
+                                    rejects windows (the server solves them one at a time). */
+  const int32_t *commodity_t_out; /* optional [L]: exit time b_l; NULL: b_l = T */
 } ots_problem_desc;
 
 /* Options of ots_sinkhorn_solve. */
@@ -195,7 +204,8 @@ ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_en
  * in ots_get_commodity_flows (out is a host buffer).  The first call on a device looks up
  * the array's device address; make that first call before any stream capture.  All calls
  * share the one array: calls that overlap on the GPU (two problems on different streams,
- * two host threads) race on it and must be serialised by the caller. */
+ * two host threads) race on it and must be serialised by the caller.  Problems with commodity
+ * windows (commodity_t_in / commodity_t_out) give OTS_ERR_INVALID_ARG here. */
 ots_status ots_get_commodity_flows_noalloc(ots_problem *p, int32_t t_begin, int32_t t_end,
                                            int32_t l_begin, int32_t l_end, double *out);
 

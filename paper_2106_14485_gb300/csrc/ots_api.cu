@@ -124,33 +124,141 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   return a;
 }
 
-BndArgs bnd_args(ots_problem *p, bool source, int mode) {
+// Boundary kernel arguments for all segments of a side (g < 0), or for group g of a problem
+// with commodity windows: the segments whose commodities enter (sources) or leave (sinks) at
+// time t.  Sources read Psi_t = B_{t+1} and write hatPsi_{t+1} = A_t; sinks read hatPsi_t =
+// A_{t-1} and write Psi_{t-1} = B_t.  An update (mode 0) of a group that enters after t = 1
+// or leaves before T writes no panel: its rows are put into A_t / B_t when the sweep gets there
+// (mode 1).  Groups after the first add their measures to the pass totals.
+BndArgs bnd_args(ots_problem *p, bool source, int mode, int g) {
   Boundary &b = source ? p->src : p->snk;
+  int s0 = 0, s1 = b.n_seg, t = source ? 1 : p->T;
+  if (g >= 0) { s0 = b.grp_seg[g]; s1 = b.grp_seg[g + 1]; t = b.grp_t[g]; }
   BndArgs a{};
-  a.n_seg = b.n_seg;
+  a.n_seg = s1 - s0;
   a.qs = p->qs;
-  a.seg_ptr = b.d_seg_ptr; a.seg_node = b.d_seg_node; a.seg_l = b.d_seg_l;
+  a.seg_ptr = b.d_seg_ptr + s0; a.seg_node = b.d_seg_node + s0; a.seg_l = b.d_seg_l + s0;
   a.tri_node_other = b.d_tri_other;
   a.tri_R = b.d_tri_R; a.tri_logR = b.d_tri_logR; a.tri_logU = b.d_tri_logU;
   a.Lp = p->Lp;
   if (source) {
-    a.msg_hi = p->b_hi(2); a.msg_lo = p->b_lo(2);
-    a.out_hi = p->a_hi(1); a.out_lo = p->a_lo(1);
+    a.msg_hi = p->b_hi(t + 1); a.msg_lo = p->b_lo(t + 1);
+    if (mode == 1 || t == 1) { a.out_hi = p->a_hi(t); a.out_lo = p->a_lo(t); }
   } else {
-    a.msg_hi = p->a_hi(p->T - 1); a.msg_lo = p->a_lo(p->T - 1);
-    a.out_hi = p->b_hi(p->T); a.out_lo = p->b_lo(p->T);
+    a.msg_hi = p->a_hi(t - 1); a.msg_lo = p->a_lo(t - 1);
+    if (mode == 1 || t == p->T) { a.out_hi = p->b_hi(t); a.out_lo = p->b_lo(t); }
   }
   a.partials = p->d_partials; a.counter = p->d_counter; a.stats = p->d_stats;
   a.mode = mode;
   a.is_source = source ? 1 : 0;
+  a.accumulate = g > 0 ? 1 : 0;
   return a;
+}
+
+BndArgs bnd_args(ots_problem *p, bool source, int mode) { return bnd_args(p, source, mode, -1); }
+
+int n_groups(const Boundary &b) { return (int)b.grp_t.size(); }
+
+// Panels of the first sweep step: A_1 from the sources entering at t = 1 (all of them
+// without windows), B_T from the sinks leaving at T.
+cudaError_t launch_boundary_rebuild(ots_problem *p, bool source) {
+  if (!p->win) return launch_boundary(bnd_args(p, source, 1), p->stream);
+  const Boundary &b = source ? p->src : p->snk;
+  const int t0 = source ? 1 : p->T;
+  for (int g = 0; g < n_groups(b); ++g)
+    if (b.grp_t[g] == t0) return launch_boundary(bnd_args(p, source, 1, g), p->stream);
+  return cudaSuccess;
+}
+
+// Commodity windows, after forward step t (A_t written): rows of the commodities entering at t
+// into A_t; the update (or, in flows mode, the boundary flows) of the sinks leaving at t+1 < T,
+// which read A_t.
+cudaError_t after_forward_step(ots_problem *p, int t, bool flows) {
+  if (!p->win) return cudaSuccess;
+  for (int g = 0; g < n_groups(p->src); ++g)
+    if (p->src.grp_t[g] == t) {
+      cudaError_t e = launch_boundary(bnd_args(p, true, 1, g), p->stream);
+      if (e != cudaSuccess) return e;
+      p->kernels_launched += 1;
+    }
+  for (int g = 0; g < n_groups(p->snk); ++g)
+    if (p->snk.grp_t[g] == t + 1 && t + 1 < p->T) {
+      cudaError_t e;
+      if (!flows) {
+        e = launch_boundary(bnd_args(p, false, 0, g), p->stream);
+      } else {
+        const Boundary &b = p->snk;
+        const int q0 = b.seg_ptr[b.grp_seg[g]], q1 = b.seg_ptr[b.grp_seg[g + 1]];
+        e = launch_boundary_flows(q1 - q0, p->Lp, p->qs, b.d_tri_l + q0, b.d_tri_other + q0, b.d_tri_logU + q0,
+                                  p->a_hi(t), p->a_lo(t), b.d_flow + q0, p->stream);
+      }
+      if (e != cudaSuccess) return e;
+      p->kernels_launched += 1;
+    }
+  return cudaSuccess;
+}
+
+// Commodity windows, after backward step t (B_t written): rows of the commodities leaving at t.
+cudaError_t after_backward_step(ots_problem *p, int t) {
+  if (!p->win) return cudaSuccess;
+  for (int g = 0; g < n_groups(p->snk); ++g)
+    if (p->snk.grp_t[g] == t) {
+      cudaError_t e = launch_boundary(bnd_args(p, false, 1, g), p->stream);
+      if (e != cudaSuccess) return e;
+      p->kernels_launched += 1;
+    }
+  return cudaSuccess;
+}
+
+// Source update at the start of a pass (mode 0): every group reads its own Psi_t.
+cudaError_t launch_source_update(ots_problem *p) {
+  if (!p->win) return launch_boundary(bnd_args(p, true, 0), p->stream);
+  for (int g = 0; g < n_groups(p->src); ++g) {
+    cudaError_t e = launch_boundary(bnd_args(p, true, 0, g), p->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Sink update after the forward sweep (mode 0): the sinks leaving at T.
+cudaError_t launch_sink_update(ots_problem *p) {
+  if (!p->win) return launch_boundary(bnd_args(p, false, 0), p->stream);
+  for (int g = 0; g < n_groups(p->snk); ++g)
+    if (p->snk.grp_t[g] == p->T) return launch_boundary(bnd_args(p, false, 0, g), p->stream);
+  return cudaSuccess;
+}
+
+// Boundary flows of the sources (all groups; each reads its Psi_t) and of the sinks leaving at T.
+cudaError_t launch_boundary_flows_all(ots_problem *p) {
+  const Boundary &bs = p->src, &bz = p->snk;
+  for (int g = 0; g < std::max(1, n_groups(bs)); ++g) {
+    const int s0 = bs.grp_seg.empty() ? 0 : bs.grp_seg[g], s1 = bs.grp_seg.empty() ? bs.n_seg : bs.grp_seg[g + 1];
+    const int t = bs.grp_t.empty() ? 1 : bs.grp_t[g];
+    const int q0 = bs.seg_ptr.empty() ? 0 : bs.seg_ptr[s0], q1 = bs.seg_ptr.empty() ? 0 : bs.seg_ptr[s1];
+    cudaError_t e = launch_boundary_flows(q1 - q0, p->Lp, p->qs, bs.d_tri_l + q0, bs.d_tri_other + q0,
+                                          bs.d_tri_logU + q0, p->b_hi(t + 1), p->b_lo(t + 1), bs.d_flow + q0, p->stream);
+    if (e != cudaSuccess) return e;
+  }
+  for (int g = 0; g < std::max(1, n_groups(bz)); ++g) {
+    const int t = bz.grp_t.empty() ? p->T : bz.grp_t[g];
+    if (t != p->T) continue;                     // earlier exits: after_forward_step
+    const int s0 = bz.grp_seg.empty() ? 0 : bz.grp_seg[g], s1 = bz.grp_seg.empty() ? bz.n_seg : bz.grp_seg[g + 1];
+    const int q0 = bz.seg_ptr.empty() ? 0 : bz.seg_ptr[s0], q1 = bz.seg_ptr.empty() ? 0 : bz.seg_ptr[s1];
+    cudaError_t e = launch_boundary_flows(q1 - q0, p->Lp, p->qs, bz.d_tri_l + q0, bz.d_tri_other + q0,
+                                          bz.d_tri_logU + q0, p->a_hi(p->T - 1), p->a_lo(p->T - 1), bz.d_flow + q0,
+                                          p->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Backward sweep of Algorithm 2 ("Compute Psi_t"), from the current duals.
 ots_status enqueue_backward_sweep(ots_problem *p) {
-  OTS_CUDA(launch_boundary(bnd_args(p, false, 1), p->stream));
-  for (int t = p->T - 1; t >= 2; --t)
+  OTS_CUDA(launch_boundary_rebuild(p, false));
+  for (int t = p->T - 1; t >= 2; --t) {
     OTS_CUDA(launch_step(false, p->pc, p->G, p->C, step_args(p, false, t, 0), p->stream));
+    OTS_CUDA(after_backward_step(p, t));
+  }
   p->kernels_launched += p->T - 1;
   return OTS_OK;
 }
@@ -180,17 +288,20 @@ ots_status enqueue_pass(ots_problem *p, bool capture) {
   const unsigned flags = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
   OTS_CUDA(launch_pass_begin(p->d_stats, p->stream));
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[0], p->stream, flags));
-  OTS_CUDA(launch_boundary(bnd_args(p, true, 0), p->stream));                 // U01, hatPsi_2
+  OTS_CUDA(launch_source_update(p));                                           // U01, hatPsi_2
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[1], p->stream, flags));
   for (int t = 2; t <= p->T - 1; ++t) {                                        // u_t, hatPsi_{t+1}
     OTS_CUDA(enqueue_segment(p, t));
     OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 0), p->stream));
+    OTS_CUDA(after_forward_step(p, t, false));
   }
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[2], p->stream, flags));
-  OTS_CUDA(launch_boundary(bnd_args(p, false, 0), p->stream));                // U0T, Psi_{T-1}
+  OTS_CUDA(launch_sink_update(p));                                             // U0T, Psi_{T-1}
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[3], p->stream, flags));
-  for (int t = p->T - 1; t >= 2; --t)                                          // Psi_{t-1}
+  for (int t = p->T - 1; t >= 2; --t) {                                        // Psi_{t-1}
     OTS_CUDA(launch_step(false, p->pc, p->G, p->C, step_args(p, false, t, 0), p->stream));
+    OTS_CUDA(after_backward_step(p, t));
+  }
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[4], p->stream, flags));
   OTS_CUDA(launch_pass_end(p->d_stats, p->d_report, p->mass, p->eps, p->stream));
   return OTS_OK;
@@ -220,7 +331,7 @@ ots_status reset_duals(ots_problem *p) {
   if (p->src.n) OTS_CUDA(cudaMemsetAsync(p->src.d_tri_logU, 0, sizeof(double) * p->src.n, p->stream));
   if (p->snk.n) OTS_CUDA(cudaMemsetAsync(p->snk.d_tri_logU, 0, sizeof(double) * p->snk.n, p->stream));
   OTS_CUDA(cudaMemsetAsync(p->d_report, 0, sizeof(PassReport), p->stream));
-  OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
+  OTS_CUDA(launch_boundary_rebuild(p, true));
   ots_status st = enqueue_backward_sweep(p);
   if (st) return st;
   p->stale = false;
@@ -233,7 +344,7 @@ ots_status refresh_if_stale(ots_problem *p) {
   OTS_CUDA(launch_weights(p->S, p->T, p->qs, p->pc ? nullptr : p->d_kl_hi, p->pc ? nullptr : p->d_kl_lo,
                           p->tv ? p->S : 0, p->d_logu, p->d_w_hi, p->d_w_lo, 0, p->d_st_inpos, p->d_st_outpos,
                           p->d_logu_in, p->d_wout_hi, p->d_wout_lo, p->stream));
-  OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
+  OTS_CUDA(launch_boundary_rebuild(p, true));
   ots_status st = enqueue_backward_sweep(p);
   if (st) return st;
   p->stale = false;
@@ -306,11 +417,11 @@ bool feasible(ots_problem *p, const std::vector<int> &eptr, const std::vector<in
       for (size_t k = 0; k < snk_by_l[l].size(); ++k) {
         int j = p->snk.tri_state[snk_by_l[l][k]];
         int dd = d[p->tail[j]];
-        if (dd >= 0 && 1 + dd <= p->T - 1) { any = true; snk_hit[k] = 1; }
+        if (dd >= 0 && 1 + dd <= p->tb[l] - p->ta[l]) { any = true; snk_hit[k] = 1; }
       }
       if (!any) {
         char buf[160];
-        snprintf(buf, sizeof(buf), "commodity %d: source state %d reaches no sink within T-1 transitions", l,
+        snprintf(buf, sizeof(buf), "commodity %d: source state %d reaches no sink within t_out - t_in transitions", l,
                  p->src.tri_state[qs]);
         why = buf;
         return false;
@@ -319,7 +430,7 @@ bool feasible(ots_problem *p, const std::vector<int> &eptr, const std::vector<in
     for (size_t k = 0; k < snk_hit.size(); ++k) {
       if (!snk_hit[k]) {
         char buf[160];
-        snprintf(buf, sizeof(buf), "commodity %d: sink state %d is reached by no source within T-1 transitions", l,
+        snprintf(buf, sizeof(buf), "commodity %d: sink state %d is reached by no source within t_out - t_in transitions", l,
                  p->snk.tri_state[snk_by_l[l][k]]);
         why = buf;
         return false;
@@ -352,12 +463,16 @@ ots_status build_boundary(ots_problem *p, Boundary &b, int n, const int32_t *com
       R[it->second] += mass[q];
     }
   }
-  // order unique triples by (segment node, commodity, state)
+  // order unique triples by (time of the commodity, segment node, commodity, state); the time
+  // is the entry time for sources and the exit time for sinks (1 and T without windows)
   const int nu = (int)keys.size();
   std::vector<int> order(nu);
   for (int k = 0; k < nu; ++k) order[k] = k;
   auto seg_node_of = [&](int k) { return source ? p->head[keys[k].second] : p->tail[keys[k].second]; };
+  auto time_of = [&](int l) { return source ? p->ta[l] : p->tb[l]; };
   std::sort(order.begin(), order.end(), [&](int a, int c) {
+    const int ta = time_of(keys[a].first), tc = time_of(keys[c].first);
+    if (ta != tc) return ta < tc;
     int na = seg_node_of(a), nc = seg_node_of(c);
     if (na != nc) return na < nc;
     if (keys[a].first != keys[c].first) return keys[a].first < keys[c].first;
@@ -385,6 +500,16 @@ ots_status build_boundary(ots_problem *p, Boundary &b, int n, const int32_t *com
   }
   b.seg_ptr.push_back(nu);
   b.n_seg = (int)b.seg_node.size();
+  b.grp_t.clear();
+  b.grp_seg.clear();
+  for (int g = 0; g < b.n_seg; ++g) {
+    const int t = time_of(b.seg_l[g]);
+    if (b.grp_t.empty() || b.grp_t.back() != t) {
+      b.grp_t.push_back(t);
+      b.grp_seg.push_back(g);
+    }
+  }
+  b.grp_seg.push_back(b.n_seg);
   return OTS_OK;
 }
 
@@ -674,6 +799,19 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
       in_cap[r * p->S + k] = cap2[r * p->S + st];
     }
   }
+
+  // ---- commodity windows (entry / exit times) ----
+  p->ta.assign(p->L, 1);
+  p->tb.assign(p->L, p->T);
+  for (int l = 0; l < p->L; ++l) {
+    if (d->commodity_t_in) p->ta[l] = d->commodity_t_in[l];
+    if (d->commodity_t_out) p->tb[l] = d->commodity_t_out[l];
+    if (p->ta[l] < 1 || p->tb[l] > p->T || p->ta[l] >= p->tb[l])
+      return bail(fail(OTS_ERR_INVALID_ARG, "commodity %d: need 1 <= t_in < t_out <= T", l));
+    if (p->ta[l] != 1 || p->tb[l] != p->T) p->win = true;
+  }
+  if (p->win && p->member) return bail(fail(OTS_ERR_INVALID_ARG, "the batched solver takes no commodity windows"));
+  if (p->win && p->bk > 1) return bail(fail(OTS_ERR_INVALID_ARG, "commodity windows need psi_stride <= 1"));
 
   // ---- boundary triples ----
   ots_status st = build_boundary(p, p->src, d->n_sources, d->src_commodity, d->src_state, d->src_mass, true);
@@ -1081,15 +1219,13 @@ static ots_status flows_pass(ots_problem *p) {
   ots_status st = refresh_if_stale(p);
   if (st) return st;
   p->kernels_launched += 1 + (p->T - 2) + 2 + p->b_recompute;
-  OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
+  OTS_CUDA(launch_boundary_rebuild(p, true));
   for (int t = 2; t <= p->T - 1; ++t) {
     OTS_CUDA(enqueue_segment(p, t));
     OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
+    OTS_CUDA(after_forward_step(p, t, true));
   }
-  OTS_CUDA(launch_boundary_flows(p->src.n, p->Lp, p->qs, p->src.d_tri_l, p->src.d_tri_other, p->src.d_tri_logU, p->b_hi(2),
-                                 p->b_lo(2), p->src.d_flow, p->stream));
-  OTS_CUDA(launch_boundary_flows(p->snk.n, p->Lp, p->qs, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
-                                 p->a_hi(p->T - 1), p->a_lo(p->T - 1), p->snk.d_flow, p->stream));
+  OTS_CUDA(launch_boundary_flows_all(p));
   return OTS_OK;
 }
 
@@ -1113,13 +1249,16 @@ ots_status ots_get_flows(ots_problem *p, int32_t t_begin, int32_t t_end, double 
   if (p->snk.n) OTS_CUDA(cudaMemcpyAsync(zf.data(), p->snk.d_flow, sizeof(double) * p->snk.n, cudaMemcpyDeviceToHost, p->stream));
   p->d2h_bytes += (long long)(sizeof(double) * (p->src.n + p->snk.n));
   OTS_CUDA(cudaStreamSynchronize(p->stream));
-  for (int t = t_begin; t < t_end; ++t) {
-    double *row = out + (size_t)(t - t_begin) * S;
-    if (t == 1 || t == p->T) {
-      std::fill(row, row + S, 0.0);
-      const Boundary &b = t == 1 ? p->src : p->snk;
-      const std::vector<double> &f = t == 1 ? sf : zf;
-      for (int q = 0; q < b.n; ++q) row[b.tri_state[q]] += f[q];
+  // rows t = 1 and T hold only boundary flows; each source (sink) triple adds its flow at its
+  // commodity's entry (exit) time, where the interior rows leave that commodity out
+  for (int t = t_begin; t < t_end; ++t)
+    if (t == 1 || t == p->T) std::fill(out + (size_t)(t - t_begin) * S, out + (size_t)(t - t_begin + 1) * S, 0.0);
+  for (int side = 0; side < 2; ++side) {
+    const Boundary &b = side == 0 ? p->src : p->snk;
+    const std::vector<double> &f = side == 0 ? sf : zf;
+    for (int q = 0; q < b.n; ++q) {
+      const int t = side == 0 ? p->ta[b.tri_l[q]] : p->tb[b.tri_l[q]];
+      if (t >= t_begin && t < t_end) out[(size_t)(t - t_begin) * S + b.tri_state[q]] += f[q];
     }
   }
   return OTS_OK;
@@ -1142,7 +1281,7 @@ ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_en
   auto check = [&](cudaError_t e) {
     if (e != cudaSuccess && rc == OTS_OK) rc = fail(OTS_ERR_CUDA, "%s", cudaGetErrorString(e));
   };
-  check(launch_boundary(bnd_args(p, true, 1), p->stream));
+  check(launch_boundary_rebuild(p, true));
   for (int t = 2; t <= p->T - 1 && rc == OTS_OK; ++t) {
     check(enqueue_segment(p, t));
     if (t >= t_begin && t < t_end) {
@@ -1156,25 +1295,24 @@ ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_en
       check(cudaStreamSynchronize(p->stream));
     }
     check(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
+    check(after_forward_step(p, t, true));
   }
-  check(launch_boundary_flows(p->src.n, p->Lp, p->qs, p->src.d_tri_l, p->src.d_tri_other, p->src.d_tri_logU, p->b_hi(2),
-                              p->b_lo(2), p->src.d_flow, p->stream));
-  check(launch_boundary_flows(p->snk.n, p->Lp, p->qs, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
-                              p->a_hi(p->T - 1), p->a_lo(p->T - 1), p->snk.d_flow, p->stream));
+  check(launch_boundary_flows_all(p));
   if (p->src.n) check(cudaMemcpyAsync(sf.data(), p->src.d_flow, sizeof(double) * p->src.n, cudaMemcpyDeviceToHost, p->stream));
   if (p->snk.n) check(cudaMemcpyAsync(zf.data(), p->snk.d_flow, sizeof(double) * p->snk.n, cudaMemcpyDeviceToHost, p->stream));
   check(cudaStreamSynchronize(p->stream));
   dev_free(p, d_tmp);
   if (rc) return rc;
-  for (int t : {1, p->T}) {
-    if (t < t_begin || t >= t_end) continue;
-    double *blkp = out + (size_t)(t - t_begin) * blk;
-    std::fill(blkp, blkp + blk, 0.0);
-    const Boundary &b = t == 1 ? p->src : p->snk;
-    const std::vector<double> &f = t == 1 ? sf : zf;
+  for (int t : {1, p->T})
+    if (t >= t_begin && t < t_end) std::fill(out + (size_t)(t - t_begin) * blk, out + (size_t)(t - t_begin + 1) * blk, 0.0);
+  for (int side = 0; side < 2; ++side) {
+    const Boundary &b = side == 0 ? p->src : p->snk;
+    const std::vector<double> &f = side == 0 ? sf : zf;
     for (int q = 0; q < b.n; ++q) {
-      int l = b.tri_l[q];
-      if (l >= l_begin && l < l_end) blkp[(size_t)(l - l_begin) * S + b.tri_state[q]] += f[q];
+      const int l = b.tri_l[q];
+      const int t = side == 0 ? p->ta[l] : p->tb[l];
+      if (l >= l_begin && l < l_end && t >= t_begin && t < t_end)
+        out[(size_t)(t - t_begin) * blk + (size_t)(l - l_begin) * S + b.tri_state[q]] += f[q];
     }
   }
   return OTS_OK;
@@ -1250,6 +1388,7 @@ ots_status ots_get_commodity_flows_noalloc(ots_problem *p, int32_t t_begin, int3
                 blk, kNoAllocMaxDoubles);
   if ((size_t)p->src.n > kNoAllocMaxTriples || (size_t)p->snk.n > kNoAllocMaxTriples)
     return fail(OTS_ERR_INVALID_ARG, "more than %zu source or sink triples", kNoAllocMaxTriples);
+  if (p->win) return fail(OTS_ERR_INVALID_ARG, "commodity windows: use ots_get_commodity_flows");
   DeviceGuard guard(p->dev);
   NoAllocScratch *scr = nullptr;
   ots_status st = noalloc_scratch(p->dev, &scr);
@@ -1258,7 +1397,7 @@ ots_status ots_get_commodity_flows_noalloc(ots_problem *p, int32_t t_begin, int3
   if (st) return st;
   double *slice = scr->flows;
   // forward pass at the current duals; interior rows come from the message panels
-  OTS_CUDA(launch_boundary(bnd_args(p, true, 1), p->stream));
+  OTS_CUDA(launch_boundary_rebuild(p, true));
   for (int t = 2; t <= p->T - 1; ++t) {
     OTS_CUDA(enqueue_segment(p, t));
     if (t >= t_begin && t < t_end) {
@@ -1273,11 +1412,9 @@ ots_status ots_get_commodity_flows_noalloc(ots_problem *p, int32_t t_begin, int3
       p->d2h_bytes += (long long)(sizeof(double) * blk);
     }
     OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
+    OTS_CUDA(after_forward_step(p, t, true));
   }
-  OTS_CUDA(launch_boundary_flows(p->src.n, p->Lp, p->qs, p->src.d_tri_l, p->src.d_tri_other, p->src.d_tri_logU,
-                                 p->b_hi(2), p->b_lo(2), p->src.d_flow, p->stream));
-  OTS_CUDA(launch_boundary_flows(p->snk.n, p->Lp, p->qs, p->snk.d_tri_l, p->snk.d_tri_other, p->snk.d_tri_logU,
-                                 p->a_hi(p->T - 1), p->a_lo(p->T - 1), p->snk.d_flow, p->stream));
+  OTS_CUDA(launch_boundary_flows_all(p));
   p->kernels_launched += 1 + (p->T - 2) + 2 + p->b_recompute;
   // boundary rows t = 1 (sources) and t = T (sinks): scatter the per-triple flows into the
   // zeroed slice; the states of the triples are copied from the problem's host-side list

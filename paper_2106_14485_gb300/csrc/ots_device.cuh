@@ -126,13 +126,14 @@ struct BndArgs {
   int Lp;
   const float *msg_hi;        // message panel read (B_2 for sources, A_{T-1} for sinks)
   const lo_t *msg_lo;
-  float *out_hi;              // boundary panel written (A_1 for sources, B_T for sinks)
+  float *out_hi;              // boundary panel written (A_1 for sources, B_T for sinks); nullptr: none
   lo_t *out_lo;
   double *partials;
   unsigned int *counter;
   DevStats *stats;
   int mode;                   // 0: update U, 1: rebuild the panel from the current U only
   int is_source;
+  int accumulate;             // mode 0: add the measures to the pass totals instead of setting them
 };
 
 // ------------------------------------------------------------------------------------

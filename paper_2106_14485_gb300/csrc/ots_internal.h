@@ -68,6 +68,9 @@ struct Boundary {
   std::vector<int> tri_l, tri_state, tri_other;
   std::vector<double> tri_R;
   std::vector<int> input_to_tri;  // descriptor triple -> unique triple
+  // groups of segments with the same time (entry time of the commodity for sources, exit time
+  // for sinks), in increasing time: group g holds segments [grp_seg[g], grp_seg[g+1])
+  std::vector<int> grp_t, grp_seg;
   // device
   int *d_seg_ptr = nullptr, *d_seg_node = nullptr, *d_seg_l = nullptr, *d_tri_other = nullptr, *d_tri_l = nullptr;
   double *d_tri_R = nullptr, *d_tri_logR = nullptr, *d_tri_logU = nullptr, *d_flow = nullptr;
@@ -139,6 +142,8 @@ struct ots_problem {
   bool member = false;                         // lives in a batch (see CreateOpts)
   bool tv = false;                             // time-varying costs: K_L rows per interval t
   bool cv = false;                             // per-interval capacities: d rows per interval t
+  bool win = false;                            // commodities with their own entry / exit times
+  std::vector<int> ta, tb;                     // [L] entry and exit time of each commodity
   std::vector<double> cost_nat;                // state costs in natural units ([S], or [T+1][S] rows when tv)
   std::vector<int> in_state_h;                 // in-CSR order of the states (host copy)
   std::unique_ptr<ots_host::HostArrays> host;  // between the host build and the upload

@@ -235,10 +235,11 @@ __global__ void __launch_bounds__(kBlock) k_boundary(const BndArgs b) {
   double r0 = 0.0, r1 = 0.0, r2 = 0.0;
   if (sidx < b.n_seg) boundary_segment(b, sidx, r0, r1, r2);
   if (b.mode == 0) {
+    const int assign = b.accumulate ? 0 : 1;
     if (b.is_source) {
-      block_sum2_last(to_ff(r0), to_ff(r1), b.partials, b.counter, &b.stats->src_resid, &b.stats->dual_src, 1);
+      block_sum2_last(to_ff(r0), to_ff(r1), b.partials, b.counter, &b.stats->src_resid, &b.stats->dual_src, assign);
     } else {
-      block_sum2_last(to_ff(r0), to_ff(r1), b.partials, b.counter, &b.stats->mass_snk, &b.stats->dual_snk, 1);
+      block_sum2_last(to_ff(r0), to_ff(r1), b.partials, b.counter, &b.stats->mass_snk, &b.stats->dual_snk, assign);
     }
     if (r2 > 0.0) atomicAdd(&b.stats->bad, r2);
   }

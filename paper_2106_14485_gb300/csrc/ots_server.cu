@@ -48,7 +48,7 @@ struct Request {
   int64_t ticket = 0;
   ots_problem_desc d{};
   ots_solve_opts o{};
-  std::vector<int32_t> esrc, edst, sc, ss, zc, zs;
+  std::vector<int32_t> esrc, edst, sc, ss, zc, zs, win_in, win_out;
   std::vector<double> ecost, ecap, wcost, wcap, ccost, cost_t, cap_t, sm, zm;
   int S = 0, T = 0;
   bool large = false;
@@ -341,6 +341,8 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   copy_array(r->ccost, d->commodity_cost, d->commodity_cost ? (size_t)d->L * S : 0);
   copy_array(r->cost_t, d->state_cost_t, d->state_cost_t ? (size_t)(d->T - 2) * S : 0);
   copy_array(r->cap_t, d->state_capacity_t, d->state_capacity_t ? (size_t)(d->T - 2) * S : 0);
+  copy_array(r->win_in, d->commodity_t_in, d->commodity_t_in ? (size_t)d->L : 0);
+  copy_array(r->win_out, d->commodity_t_out, d->commodity_t_out ? (size_t)d->L : 0);
   copy_array(r->sc, d->src_commodity, d->n_sources);
   copy_array(r->ss, d->src_state, d->n_sources);
   copy_array(r->sm, d->src_mass, d->n_sources);
@@ -357,6 +359,8 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   r->d.commodity_cost = ptr_or_null(r->ccost);
   r->d.state_cost_t = ptr_or_null(r->cost_t);
   r->d.state_capacity_t = ptr_or_null(r->cap_t);
+  r->d.commodity_t_in = ptr_or_null(r->win_in);
+  r->d.commodity_t_out = ptr_or_null(r->win_out);
   r->d.src_commodity = ptr_or_null(r->sc);
   r->d.src_state = ptr_or_null(r->ss);
   r->d.src_mass = ptr_or_null(r->sm);
@@ -371,7 +375,8 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   if (o) r->o = *o;
   r->S = (int)S;
   r->T = d->T;
-  r->large = s->desc.mode == 1 || d->L > 256 || d->commodity_cost != nullptr || (o && o->eps_start > 0.0);
+  r->large = s->desc.mode == 1 || d->L > 256 || d->commodity_cost != nullptr || (o && o->eps_start > 0.0) ||
+             d->commodity_t_in != nullptr || d->commodity_t_out != nullptr;
   r->t_submit = Clock::now();
   std::unique_lock<std::mutex> lk(s->mu);
   if (s->desc.max_queued > 0) {

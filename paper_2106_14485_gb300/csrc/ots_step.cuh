@@ -398,6 +398,7 @@ __device__ __forceinline__ void boundary_segment(const BndArgs &b, int sidx, dou
   }
   double sum = 0.0;
   for (int q = q0; q < q1; ++q) sum += exp2(b.tri_logU[q] - m);
+  if (!b.out_hi) return;
   const double r = m + log2(sum);
   const float h = (float)r;
   float oh;

@@ -410,14 +410,29 @@ def with_time_varying_capacities(inst, seed: int = 0, lo: float = 0.5, hi: float
     return inst
 
 
-def with_commodity_windows(inst, seed: int = 0, min_len: int = 3):
-    """Entry and exit times per commodity (the multi-tensor scheme): t_in uniform on
-    1..T-min_len+1, then t_out uniform on t_in+min_len-1..T (at least min_len times)."""
+def with_commodity_windows(inst, seed: int = 0, slack: int = 1):
+    """Entry and exit times per commodity (the multi-tensor scheme of the Remark after
+    Algorithm 2) for an instance with one source and one sink node per commodity (on the wait
+    loops): a window needs at least hops + 1 transitions (hops = hop distance from the source
+    node to the sink node); with m = hops + 1 + slack (capped at T - 1), t_in is uniform on
+    1..T-m and t_out uniform on t_in+m..T."""
     rng = np.random.default_rng(seed)
-    a = rng.integers(1, inst.T - min_len + 2, inst.L)
-    b = np.array([rng.integers(x + min_len - 1, inst.T + 1) for x in a])
-    inst.commodity_t_in = a.astype(np.int32)
-    inst.commodity_t_out = b.astype(np.int32)
+    E = inst.n_edges
+    a = np.ones(inst.L, np.int32)
+    b = np.full(inst.L, inst.T, np.int32)
+    dist = {}
+    for k in range(len(inst.src_comm)):
+        l = int(inst.src_comm[k])
+        s_node = int(inst.src_state[k]) - E
+        z = [int(inst.snk_state[q]) - E for q in range(len(inst.snk_comm)) if inst.snk_comm[q] == l]
+        if s_node not in dist:
+            dist[s_node] = hop_distances(inst.n_nodes, inst.edge_src, inst.edge_dst, s_node)
+        hops = max(int(dist[s_node][zn]) for zn in z)
+        m = min(hops + 1 + slack, inst.T - 1)
+        a[l] = rng.integers(1, inst.T - m + 1)
+        b[l] = rng.integers(a[l] + m, inst.T + 1)
+    inst.commodity_t_in = a
+    inst.commodity_t_out = b
     return inst
 
 

@@ -39,6 +39,7 @@ class ProblemDesc(ctypes.Structure):
         ("state_cost_t", _f64p),
         ("state_capacity_t", _f64p),
         ("psi_stride", ctypes.c_int32),
+        ("commodity_t_in", _i32p), ("commodity_t_out", _i32p),
     ]
 
 
@@ -251,6 +252,10 @@ def _problem_desc(inst, device: int = 0, stream: int | None = None):
     dt = getattr(inst, "state_capacity_t", None)
     if dt is not None:
         arr["state_capacity_t"] = c(dt, np.float64)
+    for k in ("commodity_t_in", "commodity_t_out"):
+        w = getattr(inst, k, None)
+        if w is not None:
+            arr[k] = c(w, np.int32)
     d = ProblemDesc()
     d.n_nodes, d.n_edges = int(inst.n_nodes), int(len(arr["edge_src"]))
     d.edge_src, d.edge_dst = _ptr(arr["edge_src"], ctypes.c_int32), _ptr(arr["edge_dst"], ctypes.c_int32)
@@ -260,6 +265,8 @@ def _problem_desc(inst, device: int = 0, stream: int | None = None):
     d.commodity_cost = _ptr(arr.get("commodity_cost"), ctypes.c_double)
     d.state_cost_t = _ptr(arr.get("state_cost_t"), ctypes.c_double)
     d.state_capacity_t = _ptr(arr.get("state_capacity_t"), ctypes.c_double)
+    d.commodity_t_in = _ptr(arr.get("commodity_t_in"), ctypes.c_int32)
+    d.commodity_t_out = _ptr(arr.get("commodity_t_out"), ctypes.c_int32)
     d.T, d.L, d.eps = int(inst.T), int(inst.L), float(inst.eps)
     d.n_sources = len(arr["src_comm"])
     d.src_commodity, d.src_state = _ptr(arr["src_comm"], ctypes.c_int32), _ptr(arr["src_state"], ctypes.c_int32)

@@ -126,3 +126,18 @@ def test_per_interval_capacities_are_validated_on_the_host():
     with pytest.raises(ots.OTSError) as e:
         ots.ots_create_problem(inst, allocator="cuda")
     assert e.value.code == ots.OTS_ERR_INVALID_ARG
+
+
+def test_commodity_windows_are_validated_on_the_host():
+    import numpy as np
+    from paper_2106_14485_gb300 import instances as I, ots
+    inst = I.rgg_instance(seed=3, n=30, L=2, T=6, eps=0.1)
+    inst.commodity_t_in = np.array([1, 4], np.int32)
+    inst.commodity_t_out = np.array([6, 4], np.int32)          # t_out <= t_in
+    with pytest.raises(ots.OTSError) as e:
+        ots.ots_create_problem(inst, allocator="cuda")
+    assert e.value.code == ots.OTS_ERR_INVALID_ARG
+    inst.commodity_t_out = np.array([6, 6], np.int32)
+    with pytest.raises(ots.OTSError) as e:                      # windows need every Psi_t kept
+        ots.ots_create_problem(inst, allocator="cuda", psi_stride=3)
+    assert e.value.code == ots.OTS_ERR_INVALID_ARG
