@@ -57,6 +57,8 @@ def _load():
     lib.orc_set_time_capacities.restype = ctypes.c_int
     lib.orc_set_windows.argtypes = [ctypes.c_void_p, _i32p, _i32p]
     lib.orc_set_windows.restype = ctypes.c_int
+    lib.orc_set_commodity_capacities.argtypes = [ctypes.c_void_p, _f64p]
+    lib.orc_set_commodity_capacities.restype = ctypes.c_int
     lib.orc_set_threads.argtypes = [ctypes.c_int]
     lib.orc_get_threads.restype = ctypes.c_int
     lib.orc_num_states.argtypes = [ctypes.c_void_p]
@@ -147,6 +149,13 @@ class Oracle:
             tb = np.ascontiguousarray(np.full(self.L, self.T) if tb is None else tb, np.int32)
             if lib.orc_set_windows(self.h, ta, tb):
                 raise ValueError("oracle: commodity windows need 1 <= t_in < t_out <= T")
+        cd = getattr(inst, "commodity_capacity", None)
+        if cd is not None:
+            cd = np.ascontiguousarray(cd, np.float64)
+            if cd.shape != (self.L, self.S):
+                raise ValueError("commodity_capacity must be L x n_states")
+            if lib.orc_set_commodity_capacities(self.h, cd.reshape(-1)):
+                raise ValueError("oracle: commodity capacities must be >= 0 (inf for none)")
         lib.orc_init_duals(self.h)
 
     def __del__(self):

@@ -62,6 +62,8 @@ typedef struct orc {
   double *d;                   /* [S] */
   double *dt;                  /* [(T+1)*S] per-interval capacities (row t), or NULL */
   int *ta, *tb;                /* [L] entry and exit time of each commodity, or NULL (1 and T) */
+  double *logD;                /* [L*S] log of the commodity capacities D^(0,t), or NULL */
+  double *logUc;               /* [(T+1)*L*S] log U^(0,t), the duals of P_{0,t} <= D^(0,t) */
   double *R01, *R0T;           /* [L*S] dense */
   double *logu;                /* [T*S], row t (1-based) used for t = 2..T-1 */
   double *logU01, *logU0T;     /* [L*S] */
@@ -94,7 +96,7 @@ int orc_get_threads(void) {
 void orc_destroy(orc *o) {
   if (!o) return;
   free(o->tail); free(o->head); free(o->pred_ptr); free(o->pred_idx);
-  free(o->succ_ptr); free(o->succ_idx); free(o->logKL); free(o->d); free(o->dt); free(o->ta); free(o->tb);
+  free(o->succ_ptr); free(o->succ_idx); free(o->logKL); free(o->d); free(o->dt); free(o->ta); free(o->tb); free(o->logD); free(o->logUc);
   free(o->R01); free(o->R0T); free(o->logu); free(o->logU01); free(o->logU0T);
   free(o->psi); free(o->ph_a); free(o->ph_b);
   free(o);
@@ -238,6 +240,33 @@ int orc_set_windows(orc *o, const int *a, const int *b) {
   return ORC_OK;
 }
 
+/* Commodity-dependent capacities (Section 3.3): P_{0,t}(M) <= D^(0,t) for t = 2..T-1, with one
+ * D (L x S, INFINITY for none) for every t.  Each adds a dual U^(0,t) per (commodity, state)
+ * that multiplies K_L like u_t does; its Sinkhorn update (Proposition 5 with the commodity mode)
+ * follows the update of u_t in each forward step:
+ * U^(0,t) <- min(U^(0,t) .* D ./ P_{0,t}, 1). */
+int orc_set_commodity_capacities(orc *o, const double *D) {
+  const size_t LS = (size_t)o->L * o->S;
+  double *ld = (double *)malloc(sizeof(double) * LS);
+  double *lu = (double *)calloc((size_t)(o->T + 1) * LS, sizeof(double));
+  if (!ld || !lu) { free(ld); free(lu); return ORC_NOMEM; }
+  for (size_t q = 0; q < LS; ++q) {
+    if (!(D[q] >= 0)) { free(ld); free(lu); return ORC_BAD_ARG; }
+    ld[q] = log(D[q]);
+  }
+  free(o->logD); free(o->logUc);
+  o->logD = ld;
+  o->logUc = lu;
+  return ORC_OK;
+}
+
+/* log of the weight of state i for commodity l in interval t: log K_L (+ log U^(0,t)) */
+static double wlog(const orc *o, int t, int l, int i) {
+  double w = kl_row(o, t, l)[i];
+  if (o->logUc && t >= 2 && t <= o->T - 1) w += o->logUc[((size_t)t * o->L + l) * o->S + i];
+  return w;
+}
+
 static int t_in(const orc *o, int l) { return o->ta ? o->ta[l] : 1; }
 static int t_out(const orc *o, int l) { return o->tb ? o->tb[l] : o->T; }
 
@@ -259,6 +288,8 @@ int64_t orc_nnz(const orc *o) { return o->pred_ptr[o->S]; }
 void orc_init_duals(orc *o) {
   size_t LS = (size_t)o->L * o->S;
   for (size_t q = 0; q < (size_t)o->T * o->S; ++q) o->logu[q] = 0.0;
+  if (o->logUc)
+    for (size_t q = 0; q < (size_t)(o->T + 1) * o->L * o->S; ++q) o->logUc[q] = 0.0;
   for (size_t q = 0; q < LS; ++q) {
     o->logU01[q] = o->R01[q] > 0 ? 0.0 : -INFINITY;
     o->logU0T[q] = o->R0T[q] > 0 ? 0.0 : -INFINITY;
@@ -295,11 +326,10 @@ static void fwd_product(const orc *o, const double *x, int t, double *out, int l
   for (int l = l0; l < l1; ++l) {
     for (int j = 0; j < S; ++j) {
       const double *xl = x + (size_t)(l - l0) * S;
-      const double *kl = kl_row(o, t, l);
       double m = -INFINITY;
       for (int64_t k = o->pred_ptr[j]; k < o->pred_ptr[j + 1]; ++k) {
         int i = o->pred_idx[k];
-        double v = xl[i] + (lu ? kl[i] + lu[i] : 0.0);
+        double v = xl[i] + (lu ? wlog(o, t, l, i) + lu[i] : 0.0);
         if (v > m) m = v;
       }
       double r = -INFINITY;
@@ -307,7 +337,7 @@ static void fwd_product(const orc *o, const double *x, int t, double *out, int l
         double acc = 0.0;
         for (int64_t k = o->pred_ptr[j]; k < o->pred_ptr[j + 1]; ++k) {
           int i = o->pred_idx[k];
-          double v = xl[i] + (lu ? kl[i] + lu[i] : 0.0);
+          double v = xl[i] + (lu ? wlog(o, t, l, i) + lu[i] : 0.0);
           acc += exp(v - m);
         }
         r = m + log(acc);
@@ -326,11 +356,10 @@ static void bwd_product(const orc *o, const double *x, int t, double *out, int l
   for (int l = l0; l < l1; ++l) {
     for (int i = 0; i < S; ++i) {
       const double *xl = x + (size_t)(l - l0) * S;
-      const double *kl = kl_row(o, t, l);
       double m = -INFINITY;
       for (int64_t k = o->succ_ptr[i]; k < o->succ_ptr[i + 1]; ++k) {
         int j = o->succ_idx[k];
-        double v = xl[j] + (lu ? kl[j] + lu[j] : 0.0);
+        double v = xl[j] + (lu ? wlog(o, t, l, j) + lu[j] : 0.0);
         if (v > m) m = v;
       }
       double r = -INFINITY;
@@ -338,7 +367,7 @@ static void bwd_product(const orc *o, const double *x, int t, double *out, int l
         double acc = 0.0;
         for (int64_t k = o->succ_ptr[i]; k < o->succ_ptr[i + 1]; ++k) {
           int j = o->succ_idx[k];
-          double v = xl[j] + (lu ? kl[j] + lu[j] : 0.0);
+          double v = xl[j] + (lu ? wlog(o, t, l, j) + lu[j] : 0.0);
           acc += exp(v - m);
         }
         r = m + log(acc);
@@ -355,14 +384,14 @@ static void col_lse(const orc *o, int t, const double *ph, const double *ps, dou
   for (int i = 0; i < S; ++i) {
     double m = -INFINITY;
     for (int l = 0; l < L; ++l) {
-      double v = ph[(size_t)l * S + i] + ps[(size_t)l * S + i] + kl_row(o, t, l)[i];
+      double v = ph[(size_t)l * S + i] + ps[(size_t)l * S + i] + wlog(o, t, l, i);
       if (v > m) m = v;
     }
     double r = -INFINITY;
     if (m > -INFINITY) {
       double acc = 0.0;
       for (int l = 0; l < L; ++l)
-        acc += exp(ph[(size_t)l * S + i] + ps[(size_t)l * S + i] + kl_row(o, t, l)[i] - m);
+        acc += exp(ph[(size_t)l * S + i] + ps[(size_t)l * S + i] + wlog(o, t, l, i) - m);
       r = m + log(acc);
     }
     ls[i] = r;
@@ -381,6 +410,10 @@ static double dual_linear_part(const orc *o) {
   for (int t = 2; t <= o->T - 1; ++t)
     for (int s = 0; s < o->S; ++s)
       if (isfinite(cap_at(o, t, s))) a += xlogy(cap_at(o, t, s), o->logu[(size_t)t * o->S + s]);
+  if (o->logD)
+    for (int t = 2; t <= o->T - 1; ++t)
+      for (size_t q = 0; q < LS; ++q)
+        if (isfinite(o->logD[q])) a += xlogy(exp(o->logD[q]), o->logUc[(size_t)t * LS + q]);
   return o->eps * a;
 }
 
@@ -467,6 +500,19 @@ int orc_iteration(orc *o, double *src_resid, double *cap_viol, double *trace) {
       } else {
         lu[i] = 0.0;
       }
+    }
+    if (o->logD) {
+      /* U^(0,t) <- min(U^(0,t) .* D ./ P_{0,t}, 1), P_{0,t} under the new u_t */
+      double *lc = o->logUc + (size_t)t * LS;
+      for (int l = 0; l < L; ++l)
+        for (int i = 0; i < S; ++i) {
+          const size_t q = (size_t)l * S + i;
+          const double base = ph[q] + o->psi[(size_t)t * LS + q] + kl_row(o, t, l)[i] + lu[i];
+          if (!(base > -INFINITY)) { lc[q] = 0.0; continue; }
+          const double old = lc[q];
+          lc[q] = isfinite(o->logD[q]) ? fmin(o->logD[q] - base, 0.0) : 0.0;
+          viol += flow_change(old, lc[q], base);
+        }
     }
     if (trace) trace[t - 1] = -o->eps * mass_t + dual_linear_part(o);
     /* hatPsi_{t+1} <- (hatPsi_t .* K_L) diag(u_t) K */
@@ -592,7 +638,7 @@ int orc_projections(orc *o, int l0, int l1, double *out) {
       /* a < t < z: hatPsi_t .* Psi_t .* K_L .* u_t */
       for (int t = a + 1; t <= z - 1; ++t)
         out[(size_t)(t - 1) * blk + q] = exp(h[(size_t)(t - 2) * blk + q] + b[(size_t)(t - 1) * blk + q] +
-                                             kl_row(o, t, l)[s] + o->logu[(size_t)t * S + s]);
+                                             wlog(o, t, l, s) + o->logu[(size_t)t * S + s]);
       /* t = z: U0T .* hatPsi_z  (row z-2 of h holds hatPsi_z) */
       out[(size_t)(z - 1) * blk + q] = exp(o->logU0T[(size_t)l * S + s] + h[(size_t)(z - 2) * blk + q]);
     }

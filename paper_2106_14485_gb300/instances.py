@@ -54,6 +54,7 @@ class Instance:
     state_capacity_t: Optional[np.ndarray] = None  # [T-2, S] per-interval capacities d_t (inf: none)
     commodity_t_in: Optional[np.ndarray] = None   # [L] entry time of each commodity (1..T-1)
     commodity_t_out: Optional[np.ndarray] = None  # [L] exit time of each commodity (t_in+1..T)
+    commodity_capacity: Optional[np.ndarray] = None  # [L, S] D^(0,t), the same for every t (inf: none)
     meta: dict = field(default_factory=dict)
 
     # ---- derived sizes / per-state views (data assembly only) ----

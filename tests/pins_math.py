@@ -120,35 +120,53 @@ class Tensor:
 
 
 def tensor_sinkhorn(inst, iters=20000, tol=1e-13, reverse=True):
-    """Proposition 5 on the full tensor: U01, then u_t (reverse order by default), then U0T."""
+    """Proposition 5 on the full tensor: U01, then u_t (reverse order by default; each followed by
+    the commodity-capacity duals U^(0,t) when the instance has D), then U0T."""
     tz = Tensor(inst)
     L, S, T = tz.L, tz.S, tz.T
     R01, R0T = dense_marginals(inst)
+    D = getattr(inst, "commodity_capacity", None)
     u = np.ones((T + 1, S))
+    Uc = np.ones((T + 1, L, S))
     U01 = (R01 > 0).astype(float)
     U0T = (R0T > 0).astype(float)
     order = list(range(T - 1, 1, -1)) if reverse else list(range(2, T))
-    for k in range(iters):
+
+    def Mc():
         M = tz.M(u, U01, U0T)
+        if D is not None:
+            for t in range(2, T):
+                M = M * Uc[t][:, tz.paths[:, t - 1]]
+        return M
+
+    for k in range(iters):
+        M = Mc()
         P1 = tz.proj0t(M, 1)
         err = np.abs(P1 - R01).sum() / R01.sum()
         U01 = np.where(R01 > 0, U01 * R01 / np.where(P1 > 0, P1, 1), 0.0)
         for t in order:
-            M = tz.M(u, U01, U0T)
+            M = Mc()
             Pt = tz.proj0t(M, t).sum(0)
             dt = capacity_at(inst, t)
             with np.errstate(divide="ignore", invalid="ignore"):
                 upd = np.where(Pt > 0, u[t] * dt / Pt, 1.0)
             upd = np.where(dt == 0, 0.0, upd)                       # d = 0 closes the state
             u[t] = np.minimum(upd, 1.0)
-        M = tz.M(u, U01, U0T)
+            if D is not None:                                       # U^(0,t) <- min(U D ./ P_{0,t}, 1)
+                P0t = tz.proj0t(Mc(), t)
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    updc = np.where(P0t > 0, Uc[t] * D / P0t, 1.0)
+                Uc[t] = np.minimum(np.where(D == 0, 0.0, updc), 1.0)
+        M = Mc()
         PT = tz.proj0t(M, T)
         U0T = np.where(R0T > 0, U0T * R0T / np.where(PT > 0, PT, 1), 0.0)
-        M = tz.M(u, U01, U0T)
+        M = Mc()
         excess = sum(np.maximum(tz.proj0t(M, t).sum(0) - capacity_at(inst, t), 0).sum() for t in range(2, T))
+        if D is not None:
+            excess += sum(np.maximum(tz.proj0t(M, t) - D, 0).sum() for t in range(2, T))
         if err < tol and excess / R01.sum() < tol:
             break
-    M = tz.M(u, U01, U0T)
+    M = Mc()
     return tz, M, (u, U01, U0T)
 
 

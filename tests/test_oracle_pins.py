@@ -426,3 +426,48 @@ def test_windows_shifted_in_time_reproduce_the_shorter_horizon():
     F1 = o1.flows()
     np.testing.assert_allclose(F1[2:9], F0, rtol=1e-9, atol=1e-12)
     assert np.all(F1[:2] == 0.0) and np.all(F1[9:] == 0.0)
+
+
+# ---------------------------------------------------------------------------------------
+# commodity-dependent capacities D^(0,t) (Section 3.3), one D for every t
+# ---------------------------------------------------------------------------------------
+
+def test_commodity_capacities_fixed_point_matches_tensor_sinkhorn():
+    inst = tiny_instance(seed=7, T=5, L=2, cap_scale=1.2, eps=0.5, per_commodity=False)
+    rng = np.random.default_rng(4)
+    D = np.full((inst.L, inst.n_states), np.inf)
+    D[:, :inst.n_edges] = rng.uniform(0.08, 0.25, (inst.L, inst.n_edges))
+    inst.commodity_capacity = D
+    o = Oracle(inst)
+    r = o.solve(max_iters=50000, tol=1e-13)
+    assert r["status"] == 0 and r["iters"] < 50000 and r["cap_viol"] < 1e-12
+    P = o.projections()
+    tz, M, _ = PM.tensor_sinkhorn(inst, reverse=False)
+    for t in range(1, inst.T + 1):
+        np.testing.assert_allclose(P[t - 1], tz.proj0t(M, t), rtol=1e-7, atol=1e-9)
+    act = 0
+    for t in range(2, inst.T):                          # KKT of the commodity mode
+        assert np.all(P[t - 1] <= D + 1e-9)
+        act += int((np.abs(P[t - 1] - D) < 1e-7).sum())
+    assert act > 0
+
+
+def test_commodity_capacities_reductions():
+    """D = inf changes nothing; with one commodity, D = d repeats the aggregate constraint and
+    the fixed point is the one without D."""
+    base = I.rgg_instance(seed=4, n=40, L=3, T=9, eps=0.05, cap_lo=0.3, cap_hi=1.0)
+    o0 = Oracle(base)
+    o0.solve(max_iters=100000, tol=1e-12)
+    inst = I.rgg_instance(seed=4, n=40, L=3, T=9, eps=0.05, cap_lo=0.3, cap_hi=1.0)
+    inst.commodity_capacity = np.full((inst.L, inst.n_states), np.inf)
+    o1 = Oracle(inst)
+    o1.solve(max_iters=100000, tol=1e-12)
+    np.testing.assert_allclose(o1.flows(), o0.flows(), rtol=1e-12, atol=1e-14)
+    single = I.single_commodity_instance(seed=1, per_interval=False)
+    os_ = Oracle(single)
+    os_.solve(max_iters=100000, tol=1e-13)
+    single.commodity_capacity = PM.capacity(single)[None, :].copy()
+    od = Oracle(single)
+    r = od.solve(max_iters=100000, tol=1e-13)
+    assert r["status"] == 0 and r["iters"] < 100000
+    np.testing.assert_allclose(od.flows(), os_.flows(), rtol=1e-8, atol=1e-11)
