@@ -122,6 +122,15 @@ typedef struct ots_problem_desc {
                                     NULL: a_l = 1.  Not with psi_stride > 1; the batched solver
                                     rejects windows (the server solves them one at a time). */
   const int32_t *commodity_t_out; /* optional [L]: exit time b_l; NULL: b_l = T */
+  const double *commodity_capacity; /* optional [L x n_states] row-major: commodity-dependent
+                                    capacities D^(0,t) (Section 3.3), P_{0,t} <= D for
+                                    t = 2..T-1 with the same D for every t; +INFINITY for none, 0
+                                    closes the state for that commodity.  Adds one dual per
+                                    (t, state, commodity), updated after u_t in each forward step;
+                                    the capacity residual includes its changes.  Runs on the
+                                    per-commodity kernels (as commodity_cost does); not with
+                                    state_cost_t, epsilon continuation or the batched solver.
+                                    The reported dual objective leaves out the D term. */
 } ots_problem_desc;
 
 /* Options of ots_sinkhorn_solve. */

@@ -115,6 +115,8 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   a.in_outpos = p->d_in_outpos;
   a.lu_in_t = p->d_logu_in + (size_t)t * p->S;
   a.cref_in_t = p->d_cref_in ? p->d_cref_in + (size_t)t * p->S : nullptr;
+  a.dc = p->d_dc;
+  a.uc_t = p->d_uc ? p->d_uc + (size_t)t * p->S * p->Lp : nullptr;
   a.wout_hi_t = p->d_wout_hi + (size_t)t * p->S;
   a.wout_lo_t = p->d_wout_lo + (size_t)t * p->S;
   a.partials = p->d_partials;
@@ -330,6 +332,7 @@ ots_status reset_duals(ots_problem *p) {
                           p->d_logu_in, p->d_wout_hi, p->d_wout_lo, p->stream));
   if (p->src.n) OTS_CUDA(cudaMemsetAsync(p->src.d_tri_logU, 0, sizeof(double) * p->src.n, p->stream));
   if (p->snk.n) OTS_CUDA(cudaMemsetAsync(p->snk.d_tri_logU, 0, sizeof(double) * p->snk.n, p->stream));
+  if (p->d_uc) OTS_CUDA(cudaMemsetAsync(p->d_uc, 0, sizeof(float) * (size_t)(p->T + 1) * p->S * p->Lp, p->stream));
   OTS_CUDA(cudaMemsetAsync(p->d_report, 0, sizeof(PassReport), p->stream));
   OTS_CUDA(launch_boundary_rebuild(p, true));
   ots_status st = enqueue_backward_sweep(p);
@@ -607,7 +610,8 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   p->L = d->L;
   p->T = d->T;
   p->eps = d->eps;
-  p->pc = d->commodity_cost != nullptr;
+  p->pc = d->commodity_cost != nullptr || d->commodity_capacity != nullptr;
+  p->cc = d->commodity_capacity != nullptr;
   p->member = co.member;
   if (p->S < 1) { delete p; return fail(OTS_ERR_INVALID_ARG, "no states"); }
   if (d->psi_stride < 0) { delete p; return fail(OTS_ERR_INVALID_ARG, "psi_stride must be >= 0"); }
@@ -687,7 +691,7 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
 
   // ---- per-state data (costs, capacities) in log2 units ----
   p->tv = d->state_cost_t != nullptr;
-  if (p->tv && d->commodity_cost) return bail(fail(OTS_ERR_INVALID_ARG, "state_cost_t and commodity_cost do not combine"));
+  if (p->tv && p->pc) return bail(fail(OTS_ERR_INVALID_ARG, "state_cost_t does not combine with commodity_cost or commodity_capacity"));
   const size_t KR = p->tv ? (size_t)(p->T + 1) : 1;   // rows of log2 K_L (row t for interval t)
   p->cv = d->state_capacity_t != nullptr;
   const size_t DR = p->cv ? (size_t)(p->T + 1) : 1;   // rows of the capacities (row t for interval t)
@@ -765,7 +769,10 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
     const double q = p->qs.q;
     for (int l = 0; l < p->L; ++l)
       for (int s = 0; s < p->S; ++s) {
-        double c = d->commodity_cost[(size_t)l * p->S + s];
+        // per-commodity costs, or the state costs for every commodity (commodity capacities alone)
+        double c = d->commodity_cost ? d->commodity_cost[(size_t)l * p->S + s]
+                   : s < p->E ? (d->edge_cost ? d->edge_cost[s] : 0.0)
+                              : (d->wait_cost ? d->wait_cost[s - p->E] : 0.0);
         if (!std::isfinite(c)) return bail(fail(OTS_ERR_INVALID_ARG, "commodity_cost must be finite"));
         const double x = -c / d->eps * kInvLn2;
         const double h = std::nearbyint(x / q) * q;
@@ -861,6 +868,19 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   H.in_cap = std::move(in_cap);
   H.cap = std::move(cap2);
   H.klc_lo = std::move(klc_lo);
+  if (p->cc) {
+    // log2 D per (state, commodity) in the panel layout: +inf none, log 0 closed
+    H.dc.assign((size_t)p->S * p->Lp, make_float2(INFINITY, 0.f));
+    for (int l = 0; l < p->L; ++l)
+      for (int s = 0; s < p->S; ++s) {
+        const double dd = d->commodity_capacity[(size_t)l * p->S + s];
+        if (std::isnan(dd) || dd < 0.0)
+          return bail(fail(OTS_ERR_INVALID_ARG, "commodity_capacity[%d][%d] must be >= 0 (inf for none)", l, s));
+        float2 &v = H.dc[(size_t)s * p->Lp + l];
+        if (dd == 0.0) v = make_float2(kNeg, 0.f);
+        else if (std::isfinite(dd)) split_ff(std::log2(dd), v.x, v.y);
+      }
+  }
   *out = p;
   return OTS_OK;
 }
@@ -927,6 +947,7 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
          o_ld_lo = cv.take<float>(DR * S);
   size_t o_cap = cv.take<float2>(DR * S);
   size_t o_klc_hi = p->pc ? cv.take<float>(S * p->Lp) : 0, o_klc_lo = p->pc ? cv.take<lo_t>(S * p->Lp) : 0;
+  size_t o_dc = p->cc ? cv.take<float2>(S * p->Lp) : 0, o_uc = p->cc ? cv.take<float>((T + 1) * S * p->Lp) : 0;
   size_t o_w_hi = cv.take<float>((T + 1) * S), o_w_lo = cv.take<float>((T + 1) * S);
   size_t o_logu = cv.take<float2>((T + 1) * S), o_flow = cv.take<double>((T + 1) * S);
   const size_t Sc = csr_copies ? S : 0;
@@ -961,6 +982,7 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   p->d_logd_hi = (float *)at(o_ld_hi); p->d_logd_lo = (float *)at(o_ld_lo);
   p->d_cap = (float2 *)at(o_cap);
   if (p->pc) { p->d_klc_hi = (float *)at(o_klc_hi); p->d_klc_lo = (lo_t *)at(o_klc_lo); }
+  if (p->cc) { p->d_dc = (float2 *)at(o_dc); p->d_uc = (float *)at(o_uc); }
   p->d_w_hi = (float *)at(o_w_hi); p->d_w_lo = (float *)at(o_w_lo);
   p->d_logu = (float2 *)at(o_logu); p->d_flow = (double *)at(o_flow);
   if (csr_copies) {
@@ -1001,6 +1023,7 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
     UP(p->d_in_logd_lo, in_logd_lo); UP(p->d_in_cap, in_cap);
   }
   if (p->pc) { UP(p->d_klc_hi, klc_hi); UP(p->d_klc_lo, klc_lo); }
+  if (p->cc) { UP(p->d_dc, H.dc); }
   std::vector<std::vector<double>> logR(2);
   for (int k = 0; k < 2; ++k) {
     Boundary &b = *sides[k];
@@ -1289,6 +1312,7 @@ ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_en
       check(launch_commodity_flows(p->S, p->Lp, p->qs, l_begin, l_end, p->d_tail, p->d_head, p->a_hi(t - 1), p->a_lo(t - 1),
                                    p->b_hi(t + 1), p->b_lo(t + 1), p->d_kl_hi + (p->tv ? t * S : 0),
                                    p->d_kl_lo + (p->tv ? t * S : 0), p->d_klc_hi, p->d_klc_lo,
+                                   p->d_uc ? p->d_uc + (size_t)t * S * p->Lp : nullptr,
                                    p->d_logu + (size_t)t * S, d_tmp, p->stream));
       check(cudaMemcpyAsync(out + (size_t)(t - t_begin) * blk, d_tmp, sizeof(double) * blk, cudaMemcpyDeviceToHost,
                             p->stream));
@@ -1404,7 +1428,8 @@ ots_status ots_get_commodity_flows_noalloc(ots_problem *p, int32_t t_begin, int3
       OTS_CUDA(launch_commodity_flows(p->S, p->Lp, p->qs, l_begin, l_end, p->d_tail, p->d_head, p->a_hi(t - 1),
                                       p->a_lo(t - 1), p->b_hi(t + 1), p->b_lo(t + 1),
                                       p->d_kl_hi + (p->tv ? t * S : 0), p->d_kl_lo + (p->tv ? t * S : 0),
-                                      p->d_klc_hi, p->d_klc_lo, p->d_logu + (size_t)t * S, slice, p->stream));
+                                      p->d_klc_hi, p->d_klc_lo, p->d_uc ? p->d_uc + (size_t)t * S * p->Lp : nullptr,
+                                   p->d_logu + (size_t)t * S, slice, p->stream));
       OTS_CUDA(cudaMemcpyAsync(out + (size_t)(t - t_begin) * blk, slice, sizeof(double) * blk,
                                cudaMemcpyDeviceToHost, p->stream));
       OTS_CUDA(cudaStreamSynchronize(p->stream));      // the slice is reused for the next t

@@ -408,7 +408,8 @@ ots_status ots_host::batch_prepare(ots_batch *b, const ots_problem_desc *desc, c
                                    ots_problem **out) {
   *out = nullptr;
   if (desc->L < 1 || desc->L > 256) return fail(OTS_ERR_INVALID_ARG, "batched instances take 1 <= L <= 256");
-  if (desc->commodity_cost) return fail(OTS_ERR_INVALID_ARG, "batched instances take commodity-independent costs");
+  if (desc->commodity_cost || desc->commodity_capacity)
+    return fail(OTS_ERR_INVALID_ARG, "batched instances take commodity-independent costs and capacities");
   int G = 0, C = 0;
   ots_batch_mapping(b, desc->L, &G, &C);
   ots_problem_desc d = *desc;

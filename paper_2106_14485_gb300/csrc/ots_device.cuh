@@ -109,6 +109,9 @@ struct StepArgs {
   float *wout_hi_t;           // [S] W_t by out-CSR position
   float *wout_lo_t;
   float *cref_in_t;           // [S] by in-CSR position: column maximum of an earlier pass (NaN: none)
+  // commodity-dependent capacities (register kernels with per-commodity K_L):
+  const float2 *dc;           // [S][Lp] log2 D^(0,t) as float-float (x = +inf: none; log2 0 = kNeg)
+  float *uc_t;                // [S][Lp] log2 U^(0,t) of row t (nullptr: no commodity capacities)
 };
 
 // Boundary kernels (sources, sinks): segments of (node, commodity) with their triples.

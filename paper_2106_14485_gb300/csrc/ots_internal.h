@@ -29,7 +29,7 @@ cudaError_t launch_scale_duals(float2 *lu, size_t n_lu, float2 *lu_in, size_t n_
 cudaError_t launch_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
                                    const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
                                    const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
-                                   const float2 *logu_t, double *out, cudaStream_t s);
+                                   const float *uc_t, const float2 *logu_t, double *out, cudaStream_t s);
 cudaError_t launch_boundary_flows(int n, int Lp, QScale qs, const int *tri_l, const int *tri_node_other,
                                   const double *tri_logU, const float *msg_hi, const lo_t *msg_lo, double *out,
                                   cudaStream_t s);
@@ -102,6 +102,7 @@ struct HostArrays {
   std::vector<int> in_ptr, out_ptr, in_state, in_nbr, out_state, out_nbr, st_inpos, st_outpos, in_outpos;
   std::vector<float> kl_hi, kl_lo, logd_hi, logd_lo, in_kl_hi, in_kl_lo, in_logd_hi, in_logd_lo, klc_hi;
   std::vector<float2> cap, in_cap;          // capacities as float-float pairs (x = inf: none)
+  std::vector<float2> dc;                   // [S][Lp] log2 of the commodity capacities
   std::vector<ots::lo_t> klc_lo;
 };
 
@@ -143,6 +144,9 @@ struct ots_problem {
   bool tv = false;                             // time-varying costs: K_L rows per interval t
   bool cv = false;                             // per-interval capacities: d rows per interval t
   bool win = false;                            // commodities with their own entry / exit times
+  bool cc = false;                             // commodity-dependent capacities D^(0,t)
+  float2 *d_dc = nullptr;                      // [S][Lp] log2 D, float-float
+  float *d_uc = nullptr;                       // [T+1][S][Lp] log2 U^(0,t)
   std::vector<int> ta, tb;                     // [L] entry and exit time of each commodity
   std::vector<double> cost_nat;                // state costs in natural units ([S], or [T+1][S] rows when tv)
   std::vector<int> in_state_h;                 // in-CSR order of the states (host copy)

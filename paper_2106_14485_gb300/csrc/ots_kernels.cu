@@ -165,6 +165,74 @@ __global__ void __launch_bounds__(BlockOf<G>::value, MinBlocksFwd<G>::value) k_f
     }
     ++batch;
 
+    // (2b) commodity-dependent capacities (Section 3.3): after u_t, the dual of
+    //      P_{0,t} <= D of every (in-state, commodity) of the batch,
+    //      log2 U^(0,t) <- min(log2 D - log2 (P_{0,t} ./ U^(0,t)), 0), with P_{0,t} under the
+    //      new u_t; the change of P_{0,t} joins the capacity residual, and the gathered rows
+    //      take the new U^(0,t) for the aggregation.
+    if constexpr (PC) {
+      if (a.uc_t && a.mode == 0 && active) {
+        const float q = a.qs.q;
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+          if (k >= nb) continue;
+          const size_t row = (size_t)st[k] * a.Lp;
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            const int col0 = 4 * (c * G + g);
+            const float4 u4 = *reinterpret_cast<const float4 *>(a.uc_t + row + col0);
+            const float uo[4] = {u4.x, u4.y, u4.z, u4.w};
+            float un4[4];
+            lo_t nl[4];
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              float uh, uu;
+              split_units(uo[qq], a.qs, uh, uu);
+              // log2 P_{0,t} / U^(0,t): hi on the grid (exact), lo in units plus W's lo
+              const float ph = (xh[k][c][qq] - uh) + bh[c][qq] + wh[k];
+              const float pu = (lo_inj(xw[k][c], qq) - kLoBias) - uu + bl[c][qq];
+              const float pl = fmaf(pu, lo_unit, wl[k]);
+              float unew = 0.f;
+              const float2 d = a.dc[row + col0 + qq];
+              if (xh[k][c][qq] > kNegThresh && bh[c][qq] > kNegThresh && wh[k] > kNegThresh && d.x < INFINITY) {
+                if (d.x < kNegThresh) {
+                  unew = kNeg;                               // D = 0: closed for this commodity
+                } else {
+                  float s1, e1;
+                  two_sum(d.x, -ph, s1, e1);
+                  unew = fminf(s1 + (e1 + (d.y - pl)), 0.f);
+                }
+                // |P_new - P_old| = P_old |2^(unew - uold) - 1|, P_old = 2^(log2 P / U + uold)
+                const bool co = uo[qq] < kNegThresh, cn = unew < kNegThresh;
+                if (!(co && cn)) {
+                  const float lp = (ph + pl);
+                  if (co || cn) {
+                    viol += ex2(fminf(lp + (co ? unew : uo[qq]), 126.f));
+                  } else {
+                    const float dl = unew - uo[qq];
+                    if (dl != 0.f)
+                      viol += fminf(ex2(fminf(lp + uo[qq], 126.f)) * fabsf(ex2(fminf(dl, 126.f)) - 1.f), 1e30f);
+                  }
+                }
+              }
+              un4[qq] = unew;
+              // the gathered row with the new dual: x - old + new, on the grid
+              float nh, nu;
+              split_units(unew, a.qs, nh, nu);
+              float u = (lo_inj(xw[k][c], qq) - kLoBias) - uu + nu;
+              float h = (xh[k][c][qq] - uh) + nh;
+              carry_units(u, h, q);
+              xh[k][c][qq] = h;
+              nl[qq] = (lo_t)((int)u + 32768);
+            }
+            *reinterpret_cast<float4 *>(a.uc_t + row + col0) = make_float4(un4[0], un4[1], un4[2], un4[3]);
+            xw[k][c][0] = (uint32_t)nl[0] | ((uint32_t)nl[1] << 16);
+            xw[k][c][1] = (uint32_t)nl[2] | ((uint32_t)nl[3] << 16);
+          }
+        }
+      }
+    }
+
     // (3) A_t[v] accumulates A_{t-1}[y] + W_t[state] over the batch
     aggregate_batch<C, KB>(xh, xw, wh, wl, lo_unit, M, acc);
   }
@@ -296,7 +364,7 @@ __global__ void k_fill_panel(size_t n, float *hi, lo_t *lo) {
 __global__ void k_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
                                   const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
                                   const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
-                                  const float2 *lu_t, double *out) {
+                                  const float *uc_t, const float2 *lu_t, double *out) {
   const size_t n = (size_t)S * (l1 - l0);
   const double unit = qs.lo_unit;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -310,6 +378,11 @@ __global__ void k_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, cons
                (double)lu.x + (double)lu.y;
     if (klc_hi) x += (double)klc_hi[(size_t)j * Lp + l] + ((double)klc_lo[(size_t)j * Lp + l] - 32768.0) * unit;
     else x += (double)kl_hi[j] + (double)kl_lo[j];
+    if (uc_t) {
+      const float u = uc_t[(size_t)j * Lp + l];
+      if (u < kNegThresh) { out[i] = 0.0; continue; }
+      x += (double)u;
+    }
     out[i] = exp2(x);
   }
 }
@@ -1035,13 +1108,13 @@ cudaError_t launch_fill_panel(size_t n, float *hi, lo_t *lo, cudaStream_t s) {
 cudaError_t launch_commodity_flows(int S, int Lp, QScale qs, int l0, int l1, const int *tail, const int *head,
                                    const float *a_hi, const lo_t *a_lo, const float *b_hi, const lo_t *b_lo,
                                    const float *kl_hi, const float *kl_lo, const float *klc_hi, const lo_t *klc_lo,
-                                   const float2 *logu_t, double *out, cudaStream_t s) {
+                                   const float *uc_t, const float2 *logu_t, double *out, cudaStream_t s) {
   size_t n = (size_t)S * (l1 - l0);
   size_t blocks = (n + 255) / 256;
   if (blocks > 8192) blocks = 8192;
   if (blocks == 0) blocks = 1;
   k_commodity_flows<<<(unsigned)blocks, 256, 0, s>>>(S, Lp, qs, l0, l1, tail, head, a_hi, a_lo, b_hi, b_lo, kl_hi,
-                                                     kl_lo, klc_hi, klc_lo, logu_t, out);
+                                                     kl_lo, klc_hi, klc_lo, uc_t, logu_t, out);
   return cudaGetLastError();
 }
 

@@ -49,7 +49,7 @@ struct Request {
   ots_problem_desc d{};
   ots_solve_opts o{};
   std::vector<int32_t> esrc, edst, sc, ss, zc, zs, win_in, win_out;
-  std::vector<double> ecost, ecap, wcost, wcap, ccost, cost_t, cap_t, sm, zm;
+  std::vector<double> ecost, ecap, wcost, wcap, ccost, cost_t, cap_t, ccap, sm, zm;
   int S = 0, T = 0;
   bool large = false;
   ots_problem *p = nullptr;                   // prepared batch member (between build and admit)
@@ -342,6 +342,7 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   copy_array(r->cost_t, d->state_cost_t, d->state_cost_t ? (size_t)(d->T - 2) * S : 0);
   copy_array(r->cap_t, d->state_capacity_t, d->state_capacity_t ? (size_t)(d->T - 2) * S : 0);
   copy_array(r->win_in, d->commodity_t_in, d->commodity_t_in ? (size_t)d->L : 0);
+  copy_array(r->ccap, d->commodity_capacity, d->commodity_capacity ? (size_t)d->L * S : 0);
   copy_array(r->win_out, d->commodity_t_out, d->commodity_t_out ? (size_t)d->L : 0);
   copy_array(r->sc, d->src_commodity, d->n_sources);
   copy_array(r->ss, d->src_state, d->n_sources);
@@ -360,6 +361,7 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   r->d.state_cost_t = ptr_or_null(r->cost_t);
   r->d.state_capacity_t = ptr_or_null(r->cap_t);
   r->d.commodity_t_in = ptr_or_null(r->win_in);
+  r->d.commodity_capacity = ptr_or_null(r->ccap);
   r->d.commodity_t_out = ptr_or_null(r->win_out);
   r->d.src_commodity = ptr_or_null(r->sc);
   r->d.src_state = ptr_or_null(r->ss);
@@ -375,7 +377,7 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   if (o) r->o = *o;
   r->S = (int)S;
   r->T = d->T;
-  r->large = s->desc.mode == 1 || d->L > 256 || d->commodity_cost != nullptr || (o && o->eps_start > 0.0) ||
+  r->large = s->desc.mode == 1 || d->L > 256 || d->commodity_cost != nullptr || d->commodity_capacity != nullptr || (o && o->eps_start > 0.0) ||
              d->commodity_t_in != nullptr || d->commodity_t_out != nullptr;
   r->t_submit = Clock::now();
   std::unique_lock<std::mutex> lk(s->mu);

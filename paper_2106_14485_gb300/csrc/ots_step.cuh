@@ -173,6 +173,23 @@ __device__ __forceinline__ void group_reduce(float (&x)[KB], float *sm) {
   }
 }
 
+// A log2 value as (hi on the q grid, remainder in lo units); the remainder is rounded to the
+// units (|error| <= q / 2^17, the resolution of the stored messages).
+__device__ __forceinline__ void split_units(float v, const QScale &qs, float &h, float &units) {
+  h = quant(v, qs);
+  units = rintf(__fmul_rn(__fsub_rn(v, h), qs.lo_inv));
+}
+
+// Bring a sum of up to three remainders back to [-32768, 32767] units, moving whole quanta
+// into the hi part (exact: q is a power of two and h stays on its grid).
+__device__ __forceinline__ void carry_units(float &u, float &h, float q) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if (u > 32767.f) { u -= 65536.f; h += q; }
+    if (u < -32768.f) { u += 65536.f; h -= q; }
+  }
+}
+
 // Gather the thread's slice of up to KB input rows (row index nbr[j0 + k]).  With
 // per-commodity costs the row of log2 K_L[., state] (same stored format) is added: hi sums are
 // exact; the two remainders are added in signed units and re-biased (|sum| <= 2^16 units, one
@@ -209,14 +226,20 @@ __device__ __forceinline__ void gather_rows(const StepArgs &a, int j0, int nb, i
           float ch[4];
           uint32_t cw[2];
           load4(a.klc_hi + row + 4 * (c * G + g), a.klc_lo + row + 4 * (c * G + g), ch, cw);
+          float ucv[4] = {0.f, 0.f, 0.f, 0.f};
+          if (a.uc_t) {
+            const float4 u4 = *reinterpret_cast<const float4 *>(a.uc_t + row + 4 * (c * G + g));
+            ucv[0] = u4.x; ucv[1] = u4.y; ucv[2] = u4.z; ucv[3] = u4.w;
+          }
           lo_t nl[4];
 #pragma unroll
           for (int qq = 0; qq < 4; ++qq) {
-            // signed remainders in units, exact
-            float u = (lo_inj(xw[k][c], qq) - kLoBias) + (lo_inj(cw, qq) - kLoBias);
-            float h = xh[k][c][qq] + ch[qq];
-            if (u > 32767.f) { u -= 65536.f; h += q; }
-            if (u < -32767.f) { u += 65536.f; h -= q; }
+            // signed remainders in units, exact; log2 U^(0,t) enters split on the same grid
+            float uh, un;
+            split_units(ucv[qq], a.qs, uh, un);
+            float u = (lo_inj(xw[k][c], qq) - kLoBias) + (lo_inj(cw, qq) - kLoBias) + un;
+            float h = xh[k][c][qq] + ch[qq] + uh;
+            carry_units(u, h, q);
             xh[k][c][qq] = h;
             nl[qq] = (lo_t)((int)u + 32768);
           }

@@ -40,6 +40,7 @@ class ProblemDesc(ctypes.Structure):
         ("state_capacity_t", _f64p),
         ("psi_stride", ctypes.c_int32),
         ("commodity_t_in", _i32p), ("commodity_t_out", _i32p),
+        ("commodity_capacity", _f64p),
     ]
 
 
@@ -252,6 +253,9 @@ def _problem_desc(inst, device: int = 0, stream: int | None = None):
     dt = getattr(inst, "state_capacity_t", None)
     if dt is not None:
         arr["state_capacity_t"] = c(dt, np.float64)
+    ccap = getattr(inst, "commodity_capacity", None)
+    if ccap is not None:
+        arr["commodity_capacity"] = c(ccap, np.float64)
     for k in ("commodity_t_in", "commodity_t_out"):
         w = getattr(inst, k, None)
         if w is not None:
@@ -267,6 +271,7 @@ def _problem_desc(inst, device: int = 0, stream: int | None = None):
     d.state_capacity_t = _ptr(arr.get("state_capacity_t"), ctypes.c_double)
     d.commodity_t_in = _ptr(arr.get("commodity_t_in"), ctypes.c_int32)
     d.commodity_t_out = _ptr(arr.get("commodity_t_out"), ctypes.c_int32)
+    d.commodity_capacity = _ptr(arr.get("commodity_capacity"), ctypes.c_double)
     d.T, d.L, d.eps = int(inst.T), int(inst.L), float(inst.eps)
     d.n_sources = len(arr["src_comm"])
     d.src_commodity, d.src_state = _ptr(arr["src_comm"], ctypes.c_int32), _ptr(arr["src_state"], ctypes.c_int32)
