@@ -96,7 +96,7 @@ def dist_env():
 def workload(seed: int, T: int = 100):
     from paper_2106_14485_gb300 import instances
     if T == 100:
-        return instances.config3(seed)
+        return instances.traffic_grid(seed)
     return instances.grid_traffic_instance(seed=seed, T=T)
 
 
@@ -528,7 +528,7 @@ def run_ours(args):
     solves = None
     if args.solves > 0:
         from paper_2106_14485_gb300 import instances
-        rg = instances.config2(rank)
+        rg = instances.rgg400(rank)
         hs = ots.ots_create_problem(rg, device=local)
         for _ in range(3):
             ots.ots_sinkhorn_solve(hs, tol=args.tol)
@@ -554,7 +554,7 @@ def run_ours(args):
     if args.batch > 0 or args.serve_rates.strip():
         from paper_2106_14485_gb300 import instances as _inst
         tg = time.perf_counter()
-        c4 = _inst.config4(0, count=max(args.batch, 64), workers=min(16, os.cpu_count() or 1))
+        c4 = _inst.uneven_rgg_batch(0, count=max(args.batch, 64), workers=min(16, os.cpu_count() or 1))
         gen_s = time.perf_counter() - tg
         if args.batch > 0:
             batch = bench_batch(args, ots, torch, local, c4[:args.batch], gen_s)
@@ -606,7 +606,7 @@ def profile_batch(args):
     from paper_2106_14485_gb300 import build, instances, ots
     build.build()
     ots.load_library()
-    insts = instances.config4(0, count=args.profile_batch, workers=min(16, os.cpu_count() or 1))
+    insts = instances.uneven_rgg_batch(0, count=args.profile_batch, workers=min(16, os.cpu_count() or 1))
     b = ots.ots_batch_create(pool_bytes=6 << 30, max_instances=args.profile_batch, ticks_per_launch=32)
     for x in insts:
         ots.ots_batch_add(b, x, tol=args.tol, max_iters=args.batch_max_passes)

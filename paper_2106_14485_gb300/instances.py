@@ -19,7 +19,7 @@ Conventions (shared by every consumer, restated in ``include/ots.h``):
   ``R^(0,1)`` and ``R^(0,T)`` of Section 3.2.  All sources and sinks sit on wait-loop
   states of nodes.
 
-Workload recipes follow the five configurations of the benchmark (see ``CONFIGS``).
+Workload recipes of the benchmark (see ``WORKLOADS``).
 """
 from __future__ import annotations
 
@@ -263,7 +263,7 @@ def _single_pair_instance(name, n, src, dst, edge_cost, edge_cap, wait_cost, L, 
 # workload recipes
 # ----------------------------------------------------------------------------------
 
-def config1(seed: int = 0, rows: int = 5, cols: int = 5, T: int = 10, eps: float = 0.05,
+def grid_single_commodity(seed: int = 0, rows: int = 5, cols: int = 5, T: int = 10, eps: float = 0.05,
             move_cost: float = 1.0, wait_cost: float = 0.1, n_src: int = 3, n_snk: int = 3):
     """Single commodity on a grid: Dirichlet(1) sources and sinks over 3 nodes each."""
     rng = np.random.default_rng(seed)
@@ -282,7 +282,7 @@ def config1(seed: int = 0, rows: int = 5, cols: int = 5, T: int = 10, eps: float
         src_mass=s_mass.astype(np.float64),
         snk_comm=np.zeros(n_snk, np.int32), snk_state=(E + z_nodes).astype(np.int32),
         snk_mass=z_mass.astype(np.float64),
-        pos=pos, meta={"config": 1, "seed": seed})
+        pos=pos, meta={"workload": "grid5x5", "seed": seed})
 
 
 def single_commodity_instance(seed: int = 0, rows: int = 6, cols: int = 6, T: int = 12, eps: float = 0.3,
@@ -326,10 +326,10 @@ def rgg_instance(seed: int = 0, n: int = 400, L: int = 64, T: int = 50, eps: flo
     cap = rng.uniform(cap_lo, cap_hi, src.shape[0]) * mass.sum() / cap_div
     return _single_pair_instance(name or f"rgg{n}-L{L}-T{T}", n, src, dst, length, cap,
                                  wait_cost, L, T, eps, pairs, mass, pos,
-                                 {"config": 2, "seed": seed, "radius": r})
+                                 {"workload": "rgg", "seed": seed, "radius": r})
 
 
-def config2(seed: int = 0):
+def rgg400(seed: int = 0):
     """Multi-commodity with capacities on a random geometric graph (n=400, L=64, T=50)."""
     return rgg_instance(seed=seed, n=400, L=64, T=50, eps=0.01)
 
@@ -348,22 +348,22 @@ def grid_traffic_instance(seed: int = 0, rows: int = 100, cols: int = 100, L: in
     mass = rng.uniform(0.1, 1.0, L)
     return _single_pair_instance(name or f"grid{rows}x{cols}-L{L}-T{T}", rows * cols, src, dst,
                                  cost, cap, wait_cost, L, T, eps, pairs, mass, pos,
-                                 {"config": 3, "seed": seed})
+                                 {"workload": "traffic_grid", "seed": seed})
 
 
-def config3(seed: int = 0):
+def traffic_grid(seed: int = 0):
     """Traffic-scale: 100x100 grid, L=1024 OD commodities, T=100, eps=0.005."""
     return grid_traffic_instance(seed=seed)
 
 
-def _config4_member(args):
+def _uneven_rgg_member(args):
     k, n, T, L, sub = args
     inst = rgg_instance(seed=sub, n=n, L=L, T=T, eps=0.01, name=f"b{k}-rgg{n}-L{L}-T{T}", connect="bridge")
-    inst.meta.update({"config": 4, "batch_index": k})
+    inst.meta.update({"workload": "uneven_rgg_batch", "batch_index": k})
     return inst
 
 
-def config4(seed: int = 0, count: int = 256, workers: int = 1):
+def uneven_rgg_batch(seed: int = 0, count: int = 256, workers: int = 1):
     """Batch of uneven instances: n~U{50..2000} RGG (bridged to be connected), T~U{10..80},
     L~U{1..128}.  The sizes and sub-seeds are drawn first, so `workers` > 1 (a spawn process
     pool) gives the same instances."""
@@ -376,11 +376,11 @@ def config4(seed: int = 0, count: int = 256, workers: int = 1):
         sub = int(rng.integers(2**31 - 1))
         specs.append((k, n, T, L, sub))
     if workers <= 1:
-        return [_config4_member(s) for s in specs]
+        return [_uneven_rgg_member(s) for s in specs]
     import concurrent.futures as cf
     import multiprocessing as mp
     with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
-        return list(ex.map(_config4_member, specs, chunksize=4))
+        return list(ex.map(_uneven_rgg_member, specs, chunksize=4))
 
 
 def with_time_varying_costs(inst, seed: int = 0, lo: float = 0.5, hi: float = 2.0, closures: int = 0):
@@ -437,4 +437,5 @@ def with_commodity_windows(inst, seed: int = 0, slack: int = 1):
     return inst
 
 
-CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4}
+WORKLOADS = {"grid5x5": grid_single_commodity, "rgg400": rgg400, "traffic_grid": traffic_grid,
+             "uneven_rgg_batch": uneven_rgg_batch}

@@ -36,7 +36,7 @@ def rel_l1(a, b):
 def mixed_instances():
     """Uneven sizes, horizons and commodity counts covering every thread mapping of the
     batch kernel (G = 1..32 with C = 1, and C = 2 for L > 128), binding capacities."""
-    out = [I.config1(0), I.config1(1)]
+    out = [I.grid_single_commodity(0), I.grid_single_commodity(1)]
     shapes = [(30, 1, 7, 100), (45, 3, 9, 200), (60, 7, 12, 102), (50, 13, 10, 103), (40, 30, 8, 202),
               (70, 61, 11, 105), (36, 120, 9, 106), (32, 200, 8, 107)]
     for n, L, T, seed in shapes:     # seeds whose capacities admit a feasible flow
@@ -155,7 +155,7 @@ def test_capacity_infeasible_instance_stops_at_pass_limit(O):
     """Capacities that admit no feasible flow: the batch stops at the pass limit with
     OTS_ERR_NOT_CONVERGED (as ots_sinkhorn_solve does) while a feasible neighbour converges."""
     bad = I.rgg_instance(seed=17, n=40, L=5, T=12, eps=0.05, cap_lo=0.01, cap_hi=0.02)
-    good = I.config1(2)
+    good = I.grid_single_commodity(2)
     b = O.ots_batch_create(pool_bytes=256 << 20, max_instances=4)
     ib = O.ots_batch_add(b, bad, tol=1e-7, max_iters=300)
     ig = O.ots_batch_add(b, good, tol=1e-8, max_iters=100000)

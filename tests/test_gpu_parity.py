@@ -48,8 +48,8 @@ def capped_rgg(seed=4, n=60, L=9, T=16, eps=0.05, lo=0.15, hi=0.4):
 # ---------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_config1_converged(O, seed):
-    inst = I.config1(seed)
+def test_grid5x5_converged(O, seed):
+    inst = I.grid_single_commodity(seed)
     o = Oracle(inst)
     ro = o.solve(max_iters=200000, tol=1e-12)
     assert ro["status"] == 0
@@ -135,8 +135,8 @@ def test_pipelined_rows_of_1024_commodities(O):
 # iterate-by-iterate parity (same initialisation, same number of passes)
 # ---------------------------------------------------------------------------------------
 
-def test_config2_iterates_and_converged(O):
-    inst = I.config2(0)
+def test_rgg400_iterates_and_converged(O):
+    inst = I.rgg400(0)
     o = Oracle(inst)
     o.backward_sweep()
     h = O.ots_create_problem(inst)
@@ -180,8 +180,8 @@ def test_dual_objective_matches_and_increases(O):
 # traffic-scale workload (100x100 grid, L = 1024, T = 100): sampled outputs and properties
 # ---------------------------------------------------------------------------------------
 
-def test_config3_sampled_commodities_and_properties(O):
-    inst = I.config3(0)
+def test_traffic_grid_sampled_commodities_and_properties(O):
+    inst = I.traffic_grid(0)
     h = O.ots_create_problem(inst)
     O.ots_iterate(h, 2, reset=True)
     lu, U01, U0T = O.ots_get_duals(h)
@@ -242,7 +242,7 @@ def test_duplicate_triples_and_closed_states(O):
 
 
 def test_invalid_and_infeasible_inputs(O):
-    inst = I.config1(0)
+    inst = I.grid_single_commodity(0)
     bad = I.Instance(**{**inst.__dict__})
     bad.eps = -1.0
     with pytest.raises(O.OTSError) as e:
@@ -253,7 +253,7 @@ def test_invalid_and_infeasible_inputs(O):
     with pytest.raises(O.OTSError) as e:
         O.ots_create_problem(bad)
     assert e.value.code == O.OTS_ERR_INVALID_ARG
-    far = I.config1(0, T=3)
+    far = I.grid_single_commodity(0, T=3)
     far.src_state = np.array([far.n_edges + 0], np.int32); far.src_mass = np.array([1.0]); far.src_comm = np.zeros(1, np.int32)
     far.snk_state = np.array([far.n_edges + 24], np.int32); far.snk_mass = np.array([1.0]); far.snk_comm = np.zeros(1, np.int32)
     with pytest.raises(O.OTSError) as e:

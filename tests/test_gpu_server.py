@@ -127,13 +127,13 @@ def test_plain_mode_and_failures(O):
         assert O.ots_server_wait(plain, a, 60000)["status"] == 0
         assert O.ots_server_wait(batched, b, 60000)["status"] == 0
         assert rel_l1(O.ots_server_get_flows(batched, b), O.ots_server_get_flows(plain, a)) <= 1e-6
-    bad = I.config1(0)
+    bad = I.grid_single_commodity(0)
     bad.snk_mass = bad.snk_mass * 2.0                      # unbalanced masses
     t = O.ots_server_submit(batched, bad)
     assert O.ots_server_wait(batched, t, 60000)["status"] == O.OTS_ERR_INVALID_ARG
     t = O.ots_server_submit(plain, bad)
     assert O.ots_server_wait(plain, t, 60000)["status"] == O.OTS_ERR_INVALID_ARG
-    far = I.config1(0, T=3)                                # sinks out of reach in T-1 steps
+    far = I.grid_single_commodity(0, T=3)                                # sinks out of reach in T-1 steps
     t = O.ots_server_submit(batched, far)
     assert O.ots_server_wait(batched, t, 60000)["status"] == O.OTS_ERR_INFEASIBLE
     O.ots_server_destroy(plain)

@@ -46,7 +46,7 @@ def tiny_instance(seed=0, rows=2, cols=2, L=2, T=4, eps=0.7, cap_scale=None, per
 
 
 def test_line_graph_matches_definition():
-    for inst in (tiny_instance(), I.config1(0), I.rgg_instance(seed=3, n=60, L=4, T=12)):
+    for inst in (tiny_instance(), I.grid_single_commodity(0), I.rgg_instance(seed=3, n=60, L=4, T=12)):
         o = Oracle(inst)
         assert o.nnz == int(PM.dense_K(inst).sum())
         assert o.nnz == inst.nnz_line_graph()
@@ -112,10 +112,10 @@ def test_bridge_closed_form_one_iteration():
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_config1_two_marginal_reduction(seed):
-    """Config-1 workload (multi-source, single commodity, no capacities) equals textbook
+def test_grid5x5_two_marginal_reduction(seed):
+    """The 5x5-grid workload (multi-source, single commodity, no capacities) equals textbook
     two-marginal Sinkhorn on K_eff = K (diag(k) K)^(T-2)."""
-    inst = I.config1(seed)
+    inst = I.grid_single_commodity(seed)
     o = Oracle(inst)
     r = o.solve(max_iters=100000, tol=1e-13)
     assert r["status"] == 0 and r["src_resid"] < 1e-12
@@ -231,7 +231,7 @@ def test_degenerate_source_equals_sink_and_T3():
 
 def test_infeasible_sink_is_reported():
     """A sink that no source reaches within T-1 transitions makes Psi_1 vanish on the source."""
-    inst = I.config1(0, T=3)
+    inst = I.grid_single_commodity(0, T=3)
     far = inst.n_edges + 24
     near = inst.n_edges + 0
     inst.src_state = np.array([near], np.int32); inst.src_mass = np.array([1.0]); inst.src_comm = np.zeros(1, np.int32)
