@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--batch", type=int, default=256,
                     help="instances of the batched workload (uneven random geometric graphs); 0 = skip")
     ap.add_argument("--batch-max-passes", type=int, default=3000)
+    ap.add_argument("--batch-eps-factor", type=float, default=0.0,
+                    help="epsilon continuation of the batched and serving workloads: start at this multiple of "
+                         "each instance's epsilon (halved per stage); 0 = off (default: on these instances it "
+                         "costs passes).  The one-at-a-time arm uses the same")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="profiling case only: the first N batched-workload instances, 3 graph launches of the "
                          "tick kernel, then exit (for ncu captures of k_batch_tick)")
@@ -266,6 +270,14 @@ def pct(a, q):
     return float(np.percentile(np.asarray(a), q)) if len(a) else None
 
 
+def plain_continuation(args, x):
+    """The same epsilon stages for the one-at-a-time arm as the batch runs (eps halved per stage)."""
+    if args.batch_eps_factor <= 1.0:
+        return {}
+    k = max(1, int(round(np.log2(args.batch_eps_factor))))
+    return {"eps_start": float(2 ** k) * x.eps, "eps_stages": k}
+
+
 def bench_batch(args, ots, torch, local, insts, gen_s):
     """Batched workload: args.batch uneven instances (n ~ U{50..2000} random geometric graphs of
     mean degree 6, T ~ U{10..80}, L ~ U{1..128}, capacities U[0.2,1] * mass / 8, eps = 0.01)
@@ -290,14 +302,15 @@ def bench_batch(args, ots, torch, local, insts, gen_s):
     mapping = {f"L<={4 << c}": ots.ots_batch_mapping(b, 4 << c) for c in range(7)}
     # warm-up: a few instances through the whole batch path
     for x in insts[:8]:
-        ots.ots_batch_add(b, x, tol=args.tol, max_iters=args.batch_max_passes)
+        ots.ots_batch_add(b, x, tol=args.tol, max_iters=args.batch_max_passes, eps_start=args.batch_eps_factor * x.eps if args.batch_eps_factor > 1 else 0.0)
     ots.ots_batch_run(b)
     for i in list(b.shapes):
         ots.ots_batch_remove(b, i)
     info0 = ots.ots_batch_info(b)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ids = [ots.ots_batch_add(b, x, tol=args.tol, max_iters=args.batch_max_passes) for x in insts]
+    ids = [ots.ots_batch_add(b, x, tol=args.tol, max_iters=args.batch_max_passes, eps_start=args.batch_eps_factor * x.eps if args.batch_eps_factor > 1 else 0.0)
+           for x in insts]
     t_add = time.perf_counter()
     ots.ots_batch_run(b)
     t_run = time.perf_counter()
@@ -315,7 +328,8 @@ def bench_batch(args, ots, torch, local, insts, gen_s):
     launches_p = 0
     for x in insts[:4]:                      # warm-up
         h = ots.ots_create_problem(x, device=local)
-        ots.ots_sinkhorn_solve(h, tol=args.tol, max_iters=args.batch_max_passes, check_every=1, raise_on_error=False)
+        ots.ots_sinkhorn_solve(h, tol=args.tol, max_iters=args.batch_max_passes, check_every=1, raise_on_error=False,
+                               **plain_continuation(args, x))
         ots.ots_destroy_problem(h)
     torch.cuda.synchronize()
     tp0 = time.perf_counter()
@@ -323,7 +337,7 @@ def bench_batch(args, ots, torch, local, insts, gen_s):
         ta = time.perf_counter()
         h = ots.ots_create_problem(x, device=local)
         tb = time.perf_counter()
-        r = ots.ots_sinkhorn_solve(h, tol=args.tol, max_iters=args.batch_max_passes, check_every=1,
+        r = ots.ots_sinkhorn_solve(h, tol=args.tol, max_iters=args.batch_max_passes, check_every=1, **plain_continuation(args, x),
                                    raise_on_error=False)
         tc = time.perf_counter()
         F = ots.ots_get_flows(h) if r["status"] in (0, ots.OTS_ERR_NOT_CONVERGED) else None
@@ -400,7 +414,8 @@ def bench_serve(args, ots, torch, local, small, large):
                     tk = ots.ots_server_submit(srv, large, tol=args.tol, max_iters=args.serve_large_passes,
                                                check_every=10)
                 else:
-                    tk = ots.ots_server_submit(srv, small[picks[k]], tol=args.tol, max_iters=args.batch_max_passes)
+                    tk = ots.ots_server_submit(srv, small[picks[k]], tol=args.tol, max_iters=args.batch_max_passes,
+                                               eps_start=args.batch_eps_factor * small[picks[k]].eps if args.batch_eps_factor > 1 else 0.0)
                 tickets.append((tk, bool(kinds[k])))
             deadline = t0 + args.serve_seconds + args.serve_drain
             for tk, _ in tickets:
@@ -609,7 +624,7 @@ def profile_batch(args):
     insts = instances.uneven_rgg_batch(0, count=args.profile_batch, workers=min(16, os.cpu_count() or 1))
     b = ots.ots_batch_create(pool_bytes=6 << 30, max_instances=args.profile_batch, ticks_per_launch=32)
     for x in insts:
-        ots.ots_batch_add(b, x, tol=args.tol, max_iters=args.batch_max_passes)
+        ots.ots_batch_add(b, x, tol=args.tol, max_iters=args.batch_max_passes, eps_start=args.batch_eps_factor * x.eps if args.batch_eps_factor > 1 else 0.0)
     ots.ots_batch_run(b, 3)
     torch.cuda.synchronize()
     print(json.dumps({"profile": "batch", "instances": len(insts), "info": ots.ots_batch_info(b)}), flush=True)

@@ -152,7 +152,9 @@ typedef struct ots_solve_opts {
                             to stage, then at the problem's eps to tol.  The fixed point at eps
                             is unique, so the result is the same; the pass count usually drops.
                             0 (default) = off.  Not with per-commodity costs
-                            (OTS_ERR_INVALID_ARG); the batched solver rejects it. */
+                            (OTS_ERR_INVALID_ARG).  The batched solver halves epsilon per
+                            stage: stages at eps 2^k, ..., 2 eps, eps with
+                            k = round(log2(eps_start / eps)) (eps_stages is not used there). */
   double eps_stage_tol;  /* tolerance of the warm-start stages (default 1e-4) */
 } ots_solve_opts;
 

@@ -387,7 +387,6 @@ ots_status ots_batch_add(ots_batch *b, const ots_problem_desc *desc, const ots_s
   clear_error();
   if (!b || !desc || !id) return fail(OTS_ERR_INVALID_ARG, "NULL argument");
   *id = -1;
-  if (opts && opts->eps_start > 0.0) return fail(OTS_ERR_INVALID_ARG, "the batched solver has no epsilon continuation");
   if (batch_free_slots(b) == 0) return fail(OTS_ERR_OOM, "no free slot (%d resident)", b->max_slots);
   DeviceGuard guard(b->dev);
   ots_problem *p = nullptr;
@@ -463,6 +462,7 @@ ots_status ots_host::batch_admit(ots_batch *b, ots_problem *p, const ots_solve_o
   I.n_items = n_items; I.npb = npb; I.rounds = rounds; I.npi = npi;
   I.qs = p->qs;
   I.mass = p->mass; I.eps = p->eps; I.tol = o.tol;
+  I.stage_tol = o.eps_stage_tol > 0.0 ? o.eps_stage_tol : 1e-4;
   I.max_passes = o.max_iters;
   I.kl_stride = p->tv ? p->S : 0;
   I.cap_stride = p->cv ? p->S : 0;
@@ -480,6 +480,9 @@ ots_status ots_host::batch_admit(ots_batch *b, ots_problem *p, const ots_solve_o
   BatchCtl &c = b->h_ctl_init[s];
   std::memset(&c, 0, sizeof(c));
   c.status = kSlotRunning;
+  // epsilon continuation in the batch: stages at eps 2^k, ..., 2 eps, eps (k from eps_start / eps)
+  if (o.eps_start > p->eps && std::isfinite(o.eps_start))
+    c.shift = std::min(16, std::max(1, (int)std::lround(std::log2(o.eps_start / p->eps))));
   OTS_CUDA(cudaMemcpyAsync(b->d_inst + s, &I, sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
   OTS_CUDA(cudaMemcpyAsync(b->d_ctl + s, &c, sizeof(BatchCtl), cudaMemcpyHostToDevice, b->stream));
   b->h2d += (long long)(sizeof(BatchInst) + sizeof(BatchCtl)) + p->h2d_bytes;

@@ -29,6 +29,11 @@ enum : int {
   kSlotNumeric = 6,        // final: NaN in the convergence measures
   kSlotStopped = 7         // final: stopped by the host (timeout)
 };
+// Epsilon continuation: an instance admitted with shift k > 0 runs its passes at eps 2^k until
+// the stage tolerance, then at eps 2^(k-1), ..., and at eps to its tolerance.  Halving epsilon
+// doubles log2 K_L's divisor and every log dual exactly (powers of two), so a stage change is a
+// set-up step that doubles the duals and rebuilds W, the boundary panels and the backward
+// messages, with the pass count carried on.
 
 struct BndSide {
   int n_seg, n_tri;
@@ -44,10 +49,11 @@ struct alignas(16) BatchInst {
   int rounds, npi, pad1, pad2;           // npi: nodes per item = rounds * npb
   QScale qs;
   double mass, eps, tol;
+  double stage_tol;              // tolerance of the warm-start stages (epsilon continuation)
   int max_passes;
   int kl_stride;                 // S when the costs vary with the interval t (row t of kl), else 0
   int cap_stride;                // S when the capacities vary with t (row t of logd, cap), else 0
-  int pad3, pad4, pad5;
+  int pad3;
   const int *in_ptr, *in_state, *in_nbr, *out_ptr, *out_state, *out_nbr;
   const float *kl_hi, *kl_lo, *logd_hi, *logd_lo;
   const float2 *cap;             // [S] d as a float-float
@@ -69,7 +75,7 @@ struct alignas(16) BatchCtl {
   int passes;                    // completed Sinkhorn passes
   int final_status;              // status to enter after the flows pass
   unsigned int counter;          // items of this instance finished in the current tick
-  int pad0;
+  int shift;                     // epsilon continuation: this stage runs at eps 2^shift
   long long ticks;               // ticks this instance has executed
   DevStats stats;
   PassReport report;

@@ -62,8 +62,9 @@ __device__ __forceinline__ lo_t *a_lo_of(const BatchInst &I, int t) {
 }
 __device__ __forceinline__ size_t panel_of(const BatchInst &I) { return (size_t)I.V * I.Lp; }
 
-__device__ __forceinline__ StepArgs step_of(const BatchInst &I, bool fwd, int t, int mode) {
+__device__ __forceinline__ StepArgs step_of(const BatchInst &I, bool fwd, int t, int mode, int shift) {
   StepArgs a{};
+  a.kl_shift = shift;
   a.V = I.V;
   a.Lp = I.Lp;
   a.qs = I.qs;
@@ -220,7 +221,7 @@ __device__ __forceinline__ void fwd_round(const StepArgs &a, int G, int v0, int 
 #pragma unroll
       for (int k = 0; k < KB; ++k)
         if (k == g) sk = st[k];
-      klh = a.kl_hi[sk]; kll = a.kl_lo[sk];
+      klh = ldexpf(a.kl_hi[sk], -a.kl_shift); kll = ldexpf(a.kl_lo[sk], -a.kl_shift);
       ldh = a.logd_hi[sk]; ldl = a.logd_lo[sk];
       capk = a.cap[sk];
       luo = a.lu_t[sk];
@@ -351,7 +352,7 @@ __device__ __forceinline__ void bwd_round(const StepArgs &a, int G, int v0, int 
 
 // Set-up slice k: boundary panels A_1, B_T at log 0 for the item's nodes; u_t = 1 and
 // W_t = log2 K_L for its share of the states; U01 = U0T = 1 for its share of the triples.
-__device__ void setup_item(const BatchInst &I, int k) {
+__device__ void setup_item(const BatchInst &I, int k, int shift, bool restage) {
   const size_t pan = panel_of(I);
   float *bt_hi = I.b_hi + (size_t)(I.T - 2) * pan;
   lo_t *bt_lo = I.b_lo + (size_t)(I.T - 2) * pan;
@@ -367,8 +368,13 @@ __device__ void setup_item(const BatchInst &I, int k) {
     for (int t = 2; t <= I.T - 1; ++t) {
       const size_t kq = (size_t)t * I.kl_stride + s;
       float wh, wl;
-      make_w(I.kl_hi[kq], I.kl_lo[kq], 0.f, 0.f, I.qs, wh, wl);
-      I.lu[(size_t)t * I.S + s] = make_float2(0.f, 0.f);
+      float2 lu = make_float2(0.f, 0.f);
+      if (restage) {                               // epsilon halved: log u doubles (exact)
+        lu = I.lu[(size_t)t * I.S + s];
+        lu = lu.x < kNegThresh ? make_float2(kNeg, 0.f) : make_float2(2.f * lu.x, 2.f * lu.y);
+      }
+      make_w(ldexpf(I.kl_hi[kq], -shift), ldexpf(I.kl_lo[kq], -shift), lu.x, lu.y, I.qs, wh, wl);
+      I.lu[(size_t)t * I.S + s] = lu;
       I.w_hi[(size_t)t * I.S + s] = wh;
       I.w_lo[(size_t)t * I.S + s] = wl;
     }
@@ -378,7 +384,8 @@ __device__ void setup_item(const BatchInst &I, int k) {
   for (int h = 0; h < 2; ++h) {
     const int n = sides[h]->n_tri;
     const int q0 = (int)((long long)k * n / I.n_items), q1 = (int)((long long)(k + 1) * n / I.n_items);
-    for (int q = q0 + threadIdx.x; q < q1; q += kTickBlock) sides[h]->tri_logU[q] = 0.0;
+    for (int q = q0 + threadIdx.x; q < q1; q += kTickBlock)
+      sides[h]->tri_logU[q] = restage ? 2.0 * sides[h]->tri_logU[q] : 0.0;
   }
 }
 
@@ -448,14 +455,23 @@ __device__ void finalise(const BatchInst &I, BatchCtl *c, const Phase &ph, float
     PassReport &r = c->report;
     r.src_resid_rel = st.src_resid / I.mass;
     r.cap_viol_rel = st.cap_viol / I.mass;
-    r.dual_objective = -I.eps * st.mass_snk + I.eps * 0.69314718055994530942 * (st.dual_src + st.dual_snk + st.dual_cap);
+    const double eps_now = ldexp(I.eps, c->shift);
+    r.dual_objective = -eps_now * st.mass_snk + eps_now * 0.69314718055994530942 * (st.dual_src + st.dual_snk + st.dual_cap);
     r.bad = st.bad;
     r.passes = passes;
+    const double tol_now = c->shift > 0 ? I.stage_tol : I.tol;
     if (st.bad > 0.0) {
       status = kSlotInfeasible;
     } else if (isnan(r.src_resid_rel) || isnan(r.cap_viol_rel) || isnan(r.dual_objective)) {
       status = kSlotNumeric;
-    } else if (r.src_resid_rel <= I.tol && r.cap_viol_rel <= I.tol) {
+    } else if (c->shift > 0 && passes < I.max_passes) {
+      if (r.src_resid_rel <= tol_now && r.cap_viol_rel <= tol_now) {
+        c->shift -= 1;                              // next stage: epsilon halved, set-up rescales
+        step = 0;
+      } else {
+        step = I.T;                                 // next pass of this stage
+      }
+    } else if (c->shift == 0 && r.src_resid_rel <= tol_now && r.cap_viol_rel <= tol_now) {
       status = kSlotFlows;
       c->final_status = kSlotConverged;
       step = 0;
@@ -495,6 +511,8 @@ __device__ __forceinline__ void stage_item(const TickArgs &ta, int2 w, int *hdr,
     hdr[1] = w.y;
     hdr[2] = c->status;
     hdr[3] = c->step;
+    hdr[4] = c->shift;
+    hdr[5] = c->passes;
   }
 }
 
@@ -502,7 +520,7 @@ __device__ __forceinline__ void stage_item(const TickArgs &ta, int2 w, int *hdr,
 
 __global__ void __launch_bounds__(kTickBlock, 2) k_batch_tick(const TickArgs ta) {
   __shared__ BatchInst s_inst[2];                  // current and next item's instance
-  __shared__ int s_hdr[2][4];
+  __shared__ int s_hdr[2][8];
   __shared__ int s_last;
   __shared__ float2 s_red[3 * (kTickBlock / 32)];
   __shared__ float2 s_w[kTickBlock][6];            // W of the in-states of each node (fwd)
@@ -523,6 +541,7 @@ __global__ void __launch_bounds__(kTickBlock, 2) k_batch_tick(const TickArgs ta)
     int2 wn = make_int2(0, 0);
     if (threadIdx.x == 0 && nxt < n) wn = ta.items[nxt];   // used after this item's work
     const int slot = s_hdr[buf][0], k = s_hdr[buf][1], status = s_hdr[buf][2];
+    const int c_shift = s_hdr[buf][4], c_passes = s_hdr[buf][5];
     const BatchInst &I = s_inst[buf];
     const bool running = status == kSlotRunning || status == kSlotFlows;
     const Phase ph = decode_phase(status, s_hdr[buf][3], I.T);
@@ -534,7 +553,7 @@ __global__ void __launch_bounds__(kTickBlock, 2) k_batch_tick(const TickArgs ta)
       float2 fdual = make_float2(0.f, 0.f);
       switch (ph.kind) {
         case kPhSetup:
-          setup_item(I, k);
+          setup_item(I, k, c_shift, c_passes > 0);
           break;
         case kPhInitBnd:
           bnd_item(bnd_of(I, true, 1), k, I.n_items, r0, r1, r2);
@@ -550,7 +569,7 @@ __global__ void __launch_bounds__(kTickBlock, 2) k_batch_tick(const TickArgs ta)
         case kPhFlowFwd:
         case kPhBwd: {
           const bool fwd = ph.kind != kPhBwd;
-          const StepArgs a = step_of(I, fwd, ph.t, ph.kind == kPhFlowFwd ? 1 : 0);
+          const StepArgs a = step_of(I, fwd, ph.t, ph.kind == kPhFlowFwd ? 1 : 0, c_shift);
           const int v_end = min(I.V, (k + 1) * I.npi);
           const int nib = threadIdx.x / G;
           int v0 = k * I.npi;

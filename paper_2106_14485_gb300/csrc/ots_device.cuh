@@ -112,6 +112,7 @@ struct StepArgs {
   // commodity-dependent capacities (register kernels with per-commodity K_L):
   const float2 *dc;           // [S][Lp] log2 D^(0,t) as float-float (x = +inf: none; log2 0 = kNeg)
   float *uc_t;                // [S][Lp] log2 U^(0,t) of row t (nullptr: no commodity capacities)
+  int kl_shift;               // log2 K_L is read as kl * 2^-kl_shift (epsilon 2^kl_shift times larger)
 };
 
 // Boundary kernels (sources, sinks): segments of (node, commodity) with their triples.

@@ -377,7 +377,7 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   if (o) r->o = *o;
   r->S = (int)S;
   r->T = d->T;
-  r->large = s->desc.mode == 1 || d->L > 256 || d->commodity_cost != nullptr || d->commodity_capacity != nullptr || (o && o->eps_start > 0.0) ||
+  r->large = s->desc.mode == 1 || d->L > 256 || d->commodity_cost != nullptr || d->commodity_capacity != nullptr ||
              d->commodity_t_in != nullptr || d->commodity_t_out != nullptr;
   r->t_submit = Clock::now();
   std::unique_lock<std::mutex> lk(s->mu);

@@ -352,7 +352,7 @@ __device__ __forceinline__ void update_state(const StepArgs &a, int sk, float cm
                                              float &w_lo, float &viol, float2 &dual) {
   float col_hi = kNeg, col_lo = 0.f;
   if (cm > kNegThresh && cs > 0.f) two_sum(cm, lg2(cs), col_hi, col_lo);  // log2 (hatPsi .* Psi (.* K_L))^T 1
-  const float klh = PC ? 0.f : a.kl_hi[sk], kll = PC ? 0.f : a.kl_lo[sk];
+  const float klh = PC ? 0.f : ldexpf(a.kl_hi[sk], -a.kl_shift), kll = PC ? 0.f : ldexpf(a.kl_lo[sk], -a.kl_shift);
   if (!PC && col_hi > kNegThresh) {
     float s, e;
     two_sum(col_hi, klh, s, e);
@@ -410,7 +410,9 @@ __device__ __forceinline__ void boundary_segment(const BndArgs &b, int sidx, dou
     if (b.mode == 0) {
       const size_t idx = (size_t)b.tri_node_other[q] * b.Lp + l;
       const double msg = (double)b.msg_hi[idx] + ((double)b.msg_lo[idx] - 32768.0) * (double)b.qs.lo_unit;
-      if (b.is_source) r0 += fabs(exp2(lu + msg) - b.tri_R[q]);   // mismatch before the update
+      // mismatch before the update; a term is capped at 1e30 so that the far-from-feasible first
+      // passes (messages of 2^1000 and more at large epsilon) give a huge finite measure
+      if (b.is_source) r0 += fmin(fabs(exp2(fmin(lu + msg, 1000.0)) - b.tri_R[q]), 1e30);
       if (b.msg_hi[idx] < kNegThresh) r2 += 1.0;                   // vanishing message
       lu = b.tri_logR[q] - msg;
       b.tri_logU[q] = lu;

@@ -440,12 +440,13 @@ def ots_batch_create(device: int = 0, pool_bytes: int = 4 << 30, max_instances: 
 
 
 def ots_batch_add(b: Batch, inst, tol: float = 1e-6, max_iters: int = 100000, timeout_ms: float = 0.0,
-                  raise_on_error: bool = True):
+                  raise_on_error: bool = True, eps_start: float = 0.0, eps_stage_tol: float = 0.0):
     """Add an instance; returns its id (or the status code when raise_on_error is False and the
     call failed, e.g. OTS_ERR_OOM when the batch is full)."""
     d, arr = _problem_desc(inst)
     o = ots_default_solve_opts()
     o.tol, o.max_iters, o.timeout_ms = tol, max_iters, timeout_ms
+    o.eps_start, o.eps_stage_tol = float(eps_start), float(eps_stage_tol)
     i = ctypes.c_int32(-1)
     code = load_library().ots_batch_add(b.ptr, ctypes.byref(d), ctypes.byref(o), ctypes.byref(i))
     if code != OTS_OK:

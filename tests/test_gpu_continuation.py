@@ -50,16 +50,34 @@ def test_annealed_solve_reaches_the_oracle_fixed_point(O, L, tv, seed):
     O.ots_destroy_problem(h)
 
 
+def test_batched_continuation_reaches_the_oracle_fixed_point(O):
+    """The batch halves epsilon per stage (eps 8x -> eps); the instances next to it run without
+    continuation, and each result matches the oracle at its own epsilon."""
+    insts = [I.rgg_instance(seed=5, n=60, L=9, T=14, eps=0.02, cap_lo=0.3, cap_hi=1.0),
+             I.rgg_instance(seed=4, n=40, L=3, T=9, eps=0.05, cap_lo=0.3, cap_hi=1.0),
+             I.rgg_instance(seed=11, n=90, L=40, T=13, eps=0.03, cap_lo=0.3, cap_hi=1.0)]
+    refs = []
+    for x in insts:
+        o = Oracle(x)
+        ro = o.solve(max_iters=100000, tol=1e-12)
+        assert ro["status"] == 0 and ro["iters"] < 100000
+        refs.append(o.flows())
+    b = O.ots_batch_create(pool_bytes=256 << 20, max_instances=8)
+    ids = [O.ots_batch_add(b, insts[0], tol=1e-8, eps_start=8 * insts[0].eps),
+           O.ots_batch_add(b, insts[1], tol=1e-8),
+           O.ots_batch_add(b, insts[2], tol=1e-8, eps_start=4 * insts[2].eps)]
+    assert O.ots_batch_run(b) == 0
+    for i, ref in zip(ids, refs):
+        r = O.ots_batch_status(b, i)
+        assert r["status"] == 0
+        assert rel_l1(O.ots_batch_get_flows(b, i), ref) <= FLOW_TOL
+    O.ots_batch_destroy(b)
+
+
 def test_continuation_is_rejected_where_unsupported(O):
-    inst = I.rgg_instance(seed=4, n=40, L=3, T=9, eps=0.05, cap_lo=0.3, cap_hi=1.0)
-    b = O.ots_batch_create(pool_bytes=64 << 20, max_instances=2)
-    d, arr = O._problem_desc(inst)
+    import ctypes
     o = O.ots_default_solve_opts()
     o.eps_start = 0.2
-    import ctypes
-    i = ctypes.c_int32(-1)
-    assert O.load_library().ots_batch_add(b.ptr, ctypes.byref(d), ctypes.byref(o), ctypes.byref(i)) == O.OTS_ERR_INVALID_ARG
-    O.ots_batch_destroy(b)
     pc = I.rgg_instance(seed=4, n=40, L=3, T=9, eps=0.05, cap_lo=0.3, cap_hi=1.0)
     pc.commodity_cost = np.ones((pc.L, pc.n_states))
     h = O.ots_create_problem(pc)
