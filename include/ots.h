@@ -136,7 +136,7 @@ typedef struct ots_problem_desc {
 /* Options of ots_sinkhorn_solve. */
 typedef struct ots_solve_opts {
   double tol;            /* stop when the relative L1 source mismatch and the relative
-                            capacity excess are both <= tol (default 1e-6) */
+                            capacity residual are both <= tol (default 1e-6) */
   int32_t max_iters;     /* Sinkhorn passes (default 100000) */
   int32_t check_every;   /* passes between host reads of the measures (default 10) */
   double timeout_ms;     /* 0 = none */
@@ -163,8 +163,9 @@ typedef struct ots_solve_report {
   int32_t iterations;      /* passes done by this call */
   double src_residual;     /* ||U01 .* Psi_1 - R01||_1 / ||R01||_1, taken just before the
                               last source update */
-  double cap_violation;    /* sum_t sum_i (P_t - d)_+ / ||R01||_1, taken just before each
-                              capacity update of the last pass */
+  double cap_violation;    /* capacity residual of the last pass: sum_t sum_i |P_t after the
+                              capacity update u_t - P_t before it| / ||R01||_1 (from u_t = 1
+                              this is the excess sum (P_t - d)_+; at a fixed point it is 0) */
   double dual_objective;   /* dual objective of Theorem 3 (u = exp(-lambda/eps)) after the
                               last pass, without the constant of the entropy term */
   double seconds;          /* wall time of the call */

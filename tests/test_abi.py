@@ -141,3 +141,21 @@ def test_commodity_windows_are_validated_on_the_host():
     with pytest.raises(ots.OTSError) as e:                      # windows need every Psi_t kept
         ots.ots_create_problem(inst, allocator="cuda", psi_stride=3)
     assert e.value.code == ots.OTS_ERR_INVALID_ARG
+
+
+def build_c_example():
+    """Compile the plain-C example against include/ots.h and link it to libots.so."""
+    import subprocess
+    from paper_2106_14485_gb300 import build
+    lib = build.build()
+    pkg = os.path.dirname(lib)
+    exe = os.path.join(pkg, "_build", "solve_grid")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(pkg, "examples", "solve_grid.c"), "-o", exe, "-L", pkg, "-lots",
+                           "-Wl,-rpath," + pkg, "-lm"])
+    return exe
+
+
+def test_c_example_builds_against_the_header_and_the_library():
+    assert os.path.exists(build_c_example())

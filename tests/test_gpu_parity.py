@@ -296,3 +296,12 @@ def test_solver_without_graph_and_with_cuda_allocator(O):
     r2 = O.ots_sinkhorn_solve(h2, tol=1e-6)
     assert r1["iterations"] == r2["iterations"]
     assert np.array_equal(O.ots_get_flows(h1), O.ots_get_flows(h2))
+
+
+def test_plain_c_program_through_the_abi(O):
+    """The C example drives the library without Python: create, solve, flows, duals."""
+    import subprocess
+    from tests.test_abi import build_c_example
+    r = subprocess.run([build_c_example()], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "OTS_OK" in r.stdout
