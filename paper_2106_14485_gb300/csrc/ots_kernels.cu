@@ -443,10 +443,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 }
 
 struct TmaItem {
-  int v, j0, nb;
+  int v, j0, nb, first;
 };
 __device__ __forceinline__ bool item_first(const int *ptr, int V, int KB, TmaItem &it) {
   it.v = blockIdx.x;
+  it.first = 1;
   if (it.v >= V) return false;
   it.j0 = ptr[it.v];
   it.nb = min(KB, ptr[it.v + 1] - it.j0);
@@ -455,11 +456,13 @@ __device__ __forceinline__ bool item_first(const int *ptr, int V, int KB, TmaIte
 __device__ __forceinline__ bool item_next(const int *ptr, int V, int KB, TmaItem &it) {
   const int je = ptr[it.v + 1];
   if (it.j0 + it.nb < je) {
+    it.first = 0;
     it.j0 += it.nb;
     it.nb = min(KB, je - it.j0);
     return true;
   }
   it.v += gridDim.x;
+  it.first = 1;
   if (it.v >= V) return false;
   it.j0 = ptr[it.v];
   it.nb = min(KB, ptr[it.v + 1] - it.j0);
@@ -489,7 +492,7 @@ struct StagesOf { static constexpr int value = FWD ? kStagesFwd : kStagesBwd; };
 // Per-stage metadata written by the producer warp: the work item and everything the consumers
 // would otherwise fetch with dependent global loads.
 struct FwdMeta {
-  int v, j0, nb, last, valid;
+  int v, j0, nb, first, last, valid;
   int st[kBatchTma], outpos[kBatchTma], nbr[kBatchTma];
   float kl_hi[kBatchTma], kl_lo[kBatchTma], logd_hi[kBatchTma], logd_lo[kBatchTma];
   float w_hi[kBatchTma], w_lo[kBatchTma];      // flows mode: the stored weights
@@ -500,7 +503,7 @@ struct FwdMeta {
 };
 
 struct BwdMeta {
-  int v, j0, nb, last, valid;
+  int v, j0, nb, first, last, valid;
   int nbr[kBatchTma];
   float w_hi[kBatchTma], w_lo[kBatchTma];
 };
@@ -597,7 +600,7 @@ __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, flo
       m.valid = have ? 1 : 0;
       if constexpr (FWD) m.use_ref = use_ref;
       if (have) {
-        m.v = it.v; m.j0 = it.j0; m.nb = it.nb;
+        m.v = it.v; m.j0 = it.j0; m.nb = it.nb; m.first = it.first;
         m.last = (!have_nx || nx.v != it.v) ? 1 : 0;
       }
     }
@@ -632,13 +635,14 @@ __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, flo
   }
 }
 
-// Consumer aggregation of one staged item into the running (M, acc) of the thread's 4 entries.
+// Consumer aggregation of one staged item into the running (M, acc) of the thread's 4 entries
+// (first: the node's first item, which replaces them; uniform over the block).
 // Branch-free: rows k >= nb hold finite stale data and carry wh[k] = log2 0, so their terms
 // vanish; a batch with nothing reachable leaves M below kNegThresh (encoded as log2 0).
 template <int KB>
 __device__ __forceinline__ void aggregate_staged(const float *hs, const lo_t *ls, int Lp, int g,
                                                  const float (&wh)[KB], const float (&wlb)[KB], float lo_unit,
-                                                 float *M, float *acc) {
+                                                 bool first, float *M, float *acc) {
   float hk[KB][4];
   uint32_t wk[KB][2];
 #pragma unroll
@@ -655,11 +659,16 @@ __device__ __forceinline__ void aggregate_staged(const float *hs, const lo_t *ls
     float sum = 0.f;
 #pragma unroll
     for (int k = 0; k < KB; ++k) sum += ex2(fmaf(lo_inj(wk[k], q), lo_unit, (sv[k] - m) + wlb[k]));
-    const float Mo = M[q];
-    const bool up = m > Mo;
-    const float e = ex2(-fabsf(Mo - m));
-    acc[q] = fmaf(up ? acc[q] : sum, e, up ? sum : acc[q]);
-    M[q] = fmaxf(Mo, m);
+    if (first) {                      // the node's first item: nothing to merge with
+      acc[q] = sum;
+      M[q] = m;
+    } else {
+      const float Mo = M[q];
+      const bool up = m > Mo;
+      const float e = ex2(-fabsf(Mo - m));
+      acc[q] = fmaf(up ? acc[q] : sum, e, up ? sum : acc[q]);
+      M[q] = fmaxf(Mo, m);
+    }
   }
 }
 
@@ -850,7 +859,8 @@ __global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_forward_tma(c
       // (3) A_t[v] accumulates A_{t-1}[y] + W_t[state] over the item's in-states
 #pragma unroll
       for (int c = 0; c < CH; ++c)
-        aggregate_staged<KB>(hs + Lp, ls + Lp, Lp, c * G + g, wh, wlb, lo_unit, M[c], acc[c]);
+        // the generic merge on every item (a branch on the node's first item measured slower here)
+        aggregate_staged<KB>(hs + Lp, ls + Lp, Lp, c * G + g, wh, wlb, lo_unit, false, M[c], acc[c]);
       if (m.last) {
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
@@ -926,8 +936,8 @@ __global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_backward_tma(
       }
 #pragma unroll
       for (int c = 0; c < CH; ++c)
-        aggregate_staged<KB>(st_hi + s * ROWS * Lp, st_lo + s * ROWS * Lp, Lp, c * G + g, wh, wlb, lo_unit, M[c],
-                             acc[c]);
+        aggregate_staged<KB>(st_hi + s * ROWS * Lp, st_lo + s * ROWS * Lp, Lp, c * G + g, wh, wlb, lo_unit,
+                             m.first != 0, M[c], acc[c]);
       if (m.last) {
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
