@@ -1,9 +1,11 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (spec targets, FP32 float-float log-domain messages vs FP64 oracle):
+Tolerances (FP32 float-float log-domain messages against the FP64 oracle):
   relative L1 flow error  ||F - F*||_1 / ||F*||_1  <= 1e-5   over all (t, state) flows,
   marginal violation (source mismatch, capacity excess) <= 1e-6 at the GPU's stopping point.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -305,3 +307,19 @@ def test_plain_c_program_through_the_abi(O):
     r = subprocess.run([build_c_example()], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "OTS_OK" in r.stdout
+
+
+@pytest.mark.parametrize("name", ["grid5x5_seed0", "rgg30_L4_capped"])
+def test_stored_golden_flows(O, name):
+    """The GPU fixed point against the stored oracle values of tests/golden/ (no oracle run)."""
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_golden as G
+    inst = G.CASES[name][0]()
+    Fs, dual_s = G.load(name)
+    h = O.ots_create_problem(inst)
+    r = O.ots_sinkhorn_solve(h, tol=1e-8, max_iters=50000)
+    assert r["status"] == 0
+    assert rel_l1(O.ots_get_flows(h), Fs) <= FLOW_TOL
+    assert r["dual_objective"] == pytest.approx(dual_s, rel=1e-5)
+    O.ots_destroy_problem(h)
