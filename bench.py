@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="profiling case only: the first N batched-workload instances, 3 graph launches of the "
                          "tick kernel, then exit (for ncu captures of k_batch_tick)")
+    ap.add_argument("--profile-rgg", type=int, default=0,
+                    help="profiling case only: 3 untimed full solves of the n=400 random-geometric workload, then N "
+                         "solves between cudaProfilerStart/Stop (for ncu --profile-from-start off), then exit")
     ap.add_argument("--serve-rates", type=str, default="50,200,1000",
                     help="Poisson arrival rates (requests/s) of the serving workload; empty = skip")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window per rate")
@@ -632,10 +635,37 @@ def profile_batch(args):
     return 0
 
 
+def profile_rgg(args):
+    import torch
+    from paper_2106_14485_gb300 import build, instances, ots
+    build.build()
+    ots.load_library()
+    rg = instances.rgg400(0)
+    h = ots.ots_create_problem(rg)
+    for _ in range(3):
+        ots.ots_sinkhorn_solve(h, tol=args.tol)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    lat, passes = [], 0
+    for _ in range(args.profile_rgg):
+        t0 = time.perf_counter()
+        r = ots.ots_sinkhorn_solve(h, tol=args.tol, check_every=2)
+        lat.append(time.perf_counter() - t0)
+        passes += r["iterations"]
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile": "rgg400", "solves": len(lat), "passes": passes, "solve_ms": [x * 1e3 for x in lat],
+                      "pass_timing_ms": ots.ots_last_pass_timing(h)}), flush=True)
+    ots.ots_destroy_problem(h)
+    return 0
+
+
 def main():
     args = parse()
     if args.profile_batch > 0:
         return profile_batch(args)
+    if args.profile_rgg > 0:
+        return profile_rgg(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

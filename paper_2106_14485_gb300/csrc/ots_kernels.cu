@@ -154,6 +154,26 @@ __global__ void __launch_bounds__(BlockOf<G>::value, MinBlocksFwd<G>::value) k_f
         wh[k] = k < nb ? h : kNeg;
         wl[k] = k < nb ? l : 0.f;
       }
+    } else if (G >= KB) {
+      // groups of at least KB threads: thread k of the group updates in-state k (its loads of
+      // the per-state inputs run in parallel with the other threads') and W is broadcast
+      // within the group by shuffles
+      float mk = cm[0], sk_ = cs[0];
+      int stk = st[0];
+#pragma unroll
+      for (int k = 1; k < KB; ++k)
+        if (k == g) { mk = cm[k]; sk_ = cs[k]; stk = st[k]; }
+      float mh = kNeg, ml = 0.f;
+      if (g < nb) update_state<PC>(a, stk, mk, sk_, true, mh, ml, viol, dual);
+      // the group's lanes only: groups of one warp run different numbers of batches
+      const unsigned gmask = (G >= 32) ? 0xffffffffu : (((1u << (G & 31)) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+#pragma unroll
+      for (int k = 0; k < KB; ++k) {
+        const float h = __shfl_sync(gmask, mh, k, G);
+        const float l = __shfl_sync(gmask, ml, k, G);
+        wh[k] = k < nb ? h : kNeg;
+        wl[k] = k < nb ? l : 0.f;
+      }
     } else {
       // small groups: every thread derives all updates; thread 0 of the group stores them
 #pragma unroll
