@@ -20,8 +20,8 @@
 // 4 (c G + g) + k, k < 4, c < C (16-byte hi / 8-byte lo loads, coalesced along the row).
 // In-states are processed in batches of kBatch rows gathered up front.  Column sums over
 // commodities are two group reductions (maximum, then sum of ex2 terms): warp shuffles, and
-// one shared-memory exchange when G > 32.  For G >= 32 the capacity update of in-state k is
-// done by thread k of the group and broadcast.  Sums that decide convergence are FP64 and
+// one shared-memory exchange when G > 32.  For G >= kBatch the capacity update of in-state k
+// is done by thread k of the group and broadcast; smaller groups do all updates in every thread.  Sums that decide convergence are FP64 and
 // deterministic (per-block partials, reduced by the last block in a fixed order).
 #include <cuda_runtime.h>
 #include <algorithm>
