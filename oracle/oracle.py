@@ -58,6 +58,8 @@ def _load():
     lib.orc_set_windows.argtypes = [ctypes.c_void_p, _i32p, _i32p]
     lib.orc_set_windows.restype = ctypes.c_int
     lib.orc_set_commodity_capacities.argtypes = [ctypes.c_void_p, _f64p]
+    lib.orc_set_state_graph.argtypes = [ctypes.c_void_p, _i32p, _i32p, ctypes.c_void_p]
+    lib.orc_set_state_graph.restype = ctypes.c_int
     lib.orc_set_commodity_capacities.restype = ctypes.c_int
     lib.orc_set_threads.argtypes = [ctypes.c_int]
     lib.orc_get_threads.restype = ctypes.c_int
@@ -128,6 +130,17 @@ class Oracle:
         if not self.h:
             raise ValueError("oracle rejected the instance")
         self._lib = lib
+        st = getattr(inst, "state_tail", None)
+        if st is not None:                    # explicit state graph: storage states (Section 3.3)
+            tl = np.ascontiguousarray(st, np.int32)
+            hd = np.ascontiguousarray(inst.state_head, np.int32)
+            hl = getattr(inst, "state_hold", None)
+            hl = None if hl is None else np.ascontiguousarray(hl, np.int32)
+            if tl.shape != (self.S,) or hd.shape != (self.S,) or (hl is not None and hl.shape != (self.S,)):
+                raise ValueError("state_tail / state_head / state_hold must have n_states entries")
+            self._keep += [tl, hd, hl]
+            if lib.orc_set_state_graph(self.h, tl, hd, None if hl is None else hl.ctypes.data):
+                raise ValueError("oracle: state heads and tails must be -1 or a node")
         ct = getattr(inst, "state_cost_t", None)
         if ct is not None:                    # time-varying network: one C_L per interval t
             ct = np.ascontiguousarray(ct, np.float64)

@@ -12,9 +12,12 @@
  * step; no blocking, fusion or reordering beyond the order of Algorithm 2.
  *
  * Notation (Section 3.2 / Theorem 6):
- *   states s = directed edges plus one wait loop per node (Section 3.3 vertex augmentation)
+ *   states s = directed edges plus one wait loop per node (Section 3.3 vertex augmentation),
+ *            or an explicit list of states with a head and a tail node each (-1: none) and a
+ *            storage flag (orc_set_state_graph; Section 3.3 storage on edges and the
+ *            source / sink states of eq. cost_traffic_routing)
  *   K      : line graph, K_ij = 1 iff edge i leads to edge j (head(i) == tail(j)), else 0
- *            (Section 3.1, C_ij = 0 or infinity)
+ *            (Section 3.1, C_ij = 0 or infinity), plus K_ii = 1 for a storage state
  *   K_L    : exp(-C_L / eps), L x S (Section 3.2, eq. K_multicommodity); with time-varying
  *            costs (a time-dependent network, Section 3.3) one K_L per interval t = 2..T-1
  *   d      : capacities per state (inf = none)
@@ -102,6 +105,78 @@ void orc_destroy(orc *o) {
   free(o);
 }
 
+/* State-level CSR of K: K_ij = 1 iff head(i) == tail(j) (Section 3.1), plus K_jj = 1 for the
+ * states marked in hold (storage on a state, Section 3.3; already present when head == tail).
+ * A state whose head (tail) is -1 leads to (is reached from) no other state.  pred(j) lists the
+ * states i with K_ij = 1, succ(i) the states j with K_ij = 1, each in increasing state order. */
+static int build_csr(orc *o, const int *hold) {
+  const int S = o->S, V = o->V;
+  free(o->pred_ptr); free(o->pred_idx); free(o->succ_ptr); free(o->succ_idx);
+  o->pred_ptr = NULL; o->pred_idx = NULL; o->succ_ptr = NULL; o->succ_idx = NULL;
+  int64_t *in_cnt = (int64_t *)calloc((size_t)V + 1, sizeof(int64_t));
+  int64_t *out_cnt = (int64_t *)calloc((size_t)V + 1, sizeof(int64_t));
+  int *in_list = (int *)malloc(sizeof(int) * (size_t)S), *out_list = (int *)malloc(sizeof(int) * (size_t)S);
+  o->pred_ptr = (int64_t *)malloc(sizeof(int64_t) * ((size_t)S + 1));
+  o->succ_ptr = (int64_t *)malloc(sizeof(int64_t) * ((size_t)S + 1));
+  if (!in_cnt || !out_cnt || !in_list || !out_list || !o->pred_ptr || !o->succ_ptr) {
+    free(in_cnt); free(out_cnt); free(in_list); free(out_list);
+    return ORC_NOMEM;
+  }
+  /* per node v: the states entering v (head == v) and leaving v (tail == v), in state order */
+  for (int s = 0; s < S; ++s) {
+    if (o->head[s] >= 0) in_cnt[o->head[s] + 1]++;
+    if (o->tail[s] >= 0) out_cnt[o->tail[s] + 1]++;
+  }
+  for (int v = 0; v < V; ++v) { in_cnt[v + 1] += in_cnt[v]; out_cnt[v + 1] += out_cnt[v]; }
+  {
+    int64_t *in_fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(V > 0 ? V : 1));
+    int64_t *out_fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(V > 0 ? V : 1));
+    if (!in_fill || !out_fill) {
+      free(in_fill); free(out_fill); free(in_cnt); free(out_cnt); free(in_list); free(out_list);
+      return ORC_NOMEM;
+    }
+    for (int v = 0; v < V; ++v) { in_fill[v] = in_cnt[v]; out_fill[v] = out_cnt[v]; }
+    for (int s = 0; s < S; ++s) {
+      if (o->head[s] >= 0) in_list[in_fill[o->head[s]]++] = s;
+      if (o->tail[s] >= 0) out_list[out_fill[o->tail[s]]++] = s;
+    }
+    free(in_fill); free(out_fill);
+  }
+  /* a storage state adds itself unless head == tail already puts it there */
+#define EXTRA(s) ((hold && hold[s] && !(o->head[s] >= 0 && o->head[s] == o->tail[s])) ? 1 : 0)
+  o->pred_ptr[0] = 0; o->succ_ptr[0] = 0;
+  for (int s = 0; s < S; ++s) {
+    const int u = o->tail[s], w = o->head[s];
+    o->pred_ptr[s + 1] = o->pred_ptr[s] + (u >= 0 ? in_cnt[u + 1] - in_cnt[u] : 0) + EXTRA(s);
+    o->succ_ptr[s + 1] = o->succ_ptr[s] + (w >= 0 ? out_cnt[w + 1] - out_cnt[w] : 0) + EXTRA(s);
+  }
+  o->pred_idx = (int *)malloc(sizeof(int) * (size_t)(o->pred_ptr[S] > 0 ? o->pred_ptr[S] : 1));
+  o->succ_idx = (int *)malloc(sizeof(int) * (size_t)(o->succ_ptr[S] > 0 ? o->succ_ptr[S] : 1));
+  if (!o->pred_idx || !o->succ_idx) { free(in_cnt); free(out_cnt); free(in_list); free(out_list); return ORC_NOMEM; }
+  for (int s = 0; s < S; ++s) {
+    const int u = o->tail[s], w = o->head[s];
+    int64_t k = o->pred_ptr[s];
+    int placed = !EXTRA(s);
+    if (u >= 0)
+      for (int64_t q = in_cnt[u]; q < in_cnt[u + 1]; ++q) {
+        if (!placed && in_list[q] > s) { o->pred_idx[k++] = s; placed = 1; }
+        o->pred_idx[k++] = in_list[q];
+      }
+    if (!placed) o->pred_idx[k++] = s;
+    k = o->succ_ptr[s];
+    placed = !EXTRA(s);
+    if (w >= 0)
+      for (int64_t q = out_cnt[w]; q < out_cnt[w + 1]; ++q) {
+        if (!placed && out_list[q] > s) { o->succ_idx[k++] = s; placed = 1; }
+        o->succ_idx[k++] = out_list[q];
+      }
+    if (!placed) o->succ_idx[k++] = s;
+  }
+#undef EXTRA
+  free(in_cnt); free(out_cnt); free(in_list); free(out_list);
+  return ORC_OK;
+}
+
 /* Build the state graph and the dense problem data.
  * state_cost: C_L, either [S] (same for every commodity) or [L*S] when per_commodity != 0.
  * state_cap : [S], INFINITY for none.  Sources / sinks: (commodity, state, mass) triples,
@@ -122,35 +197,7 @@ orc *orc_create(int V, int E, const int *esrc, const int *edst, int L, int T, do
   for (int s = 0; s < S; ++s)
     if (o->tail[s] < 0 || o->tail[s] >= V || o->head[s] < 0 || o->head[s] >= V) { orc_destroy(o); return NULL; }
 
-  /* K_ij > 0 iff head(i) == tail(j): collect, per node v, the states entering v and the
-   * states leaving v; pred(j) = states entering tail(j), succ(i) = states leaving head(i). */
-  int64_t *in_cnt = (int64_t *)calloc((size_t)V + 1, sizeof(int64_t));
-  int64_t *out_cnt = (int64_t *)calloc((size_t)V + 1, sizeof(int64_t));
-  for (int s = 0; s < S; ++s) { in_cnt[o->head[s] + 1]++; out_cnt[o->tail[s] + 1]++; }
-  for (int v = 0; v < V; ++v) { in_cnt[v + 1] += in_cnt[v]; out_cnt[v + 1] += out_cnt[v]; }
-  int *in_list = (int *)malloc(sizeof(int) * S), *out_list = (int *)malloc(sizeof(int) * S);
-  int64_t *in_fill = (int64_t *)malloc(sizeof(int64_t) * V), *out_fill = (int64_t *)malloc(sizeof(int64_t) * V);
-  for (int v = 0; v < V; ++v) { in_fill[v] = in_cnt[v]; out_fill[v] = out_cnt[v]; }
-  for (int s = 0; s < S; ++s) { in_list[in_fill[o->head[s]]++] = s; out_list[out_fill[o->tail[s]]++] = s; }
-
-  o->pred_ptr = (int64_t *)malloc(sizeof(int64_t) * (S + 1));
-  o->succ_ptr = (int64_t *)malloc(sizeof(int64_t) * (S + 1));
-  o->pred_ptr[0] = 0; o->succ_ptr[0] = 0;
-  for (int s = 0; s < S; ++s) {
-    int u = o->tail[s], w = o->head[s];
-    o->pred_ptr[s + 1] = o->pred_ptr[s] + (in_cnt[u + 1] - in_cnt[u]);
-    o->succ_ptr[s + 1] = o->succ_ptr[s] + (out_cnt[w + 1] - out_cnt[w]);
-  }
-  o->pred_idx = (int *)malloc(sizeof(int) * (size_t)(o->pred_ptr[S] > 0 ? o->pred_ptr[S] : 1));
-  o->succ_idx = (int *)malloc(sizeof(int) * (size_t)(o->succ_ptr[S] > 0 ? o->succ_ptr[S] : 1));
-  for (int s = 0; s < S; ++s) {
-    int u = o->tail[s], w = o->head[s];
-    int64_t k = o->pred_ptr[s];
-    for (int64_t q = in_cnt[u]; q < in_cnt[u + 1]; ++q) o->pred_idx[k++] = in_list[q];
-    k = o->succ_ptr[s];
-    for (int64_t q = out_cnt[w]; q < out_cnt[w + 1]; ++q) o->succ_idx[k++] = out_list[q];
-  }
-  free(in_cnt); free(out_cnt); free(in_list); free(out_list); free(in_fill); free(out_fill);
+  if (build_csr(o, NULL)) { orc_destroy(o); return NULL; }
 
   size_t LS = (size_t)L * S;
   o->logKL = (double *)malloc(sizeof(double) * LS);
@@ -182,6 +229,17 @@ orc *orc_create(int V, int E, const int *esrc, const int *edst, int L, int T, do
     orc_destroy(o); return NULL;
   }
   return o;
+}
+
+/* Replace the state graph by explicit heads and tails (-1: none) and a storage flag per state
+ * (Section 3.3: storage on edges, and the source / sink states of eq. cost_traffic_routing, which
+ * nothing enters and nothing leaves).  hold may be NULL.  Call before orc_init_duals. */
+int orc_set_state_graph(orc *o, const int *tail, const int *head, const int *hold) {
+  for (int s = 0; s < o->S; ++s)
+    if (tail[s] < -1 || tail[s] >= o->V || head[s] < -1 || head[s] >= o->V) return ORC_BAD_ARG;
+  memcpy(o->tail, tail, sizeof(int) * (size_t)o->S);
+  memcpy(o->head, head, sizeof(int) * (size_t)o->S);
+  return build_csr(o, hold);
 }
 
 /* log K_L row of commodity l in interval t (t >= 2). */

@@ -55,6 +55,11 @@ class Instance:
     commodity_t_in: Optional[np.ndarray] = None   # [L] entry time of each commodity (1..T-1)
     commodity_t_out: Optional[np.ndarray] = None  # [L] exit time of each commodity (t_in+1..T)
     commodity_capacity: Optional[np.ndarray] = None  # [L, S] D^(0,t), the same for every t (inf: none)
+    # explicit state graph (Section 3.3 storage models), replacing edges + wait loops: tail and head
+    # node of every state (-1: none) and a storage flag (the state may follow itself)
+    state_tail: Optional[np.ndarray] = None       # int32 [S]
+    state_head: Optional[np.ndarray] = None       # int32 [S]
+    state_hold: Optional[np.ndarray] = None       # int32 [S], 1 = storage
     meta: dict = field(default_factory=dict)
 
     # ---- derived sizes / per-state views (data assembly only) ----
@@ -75,7 +80,10 @@ class Instance:
         return np.concatenate([self.edge_cap, self.wait_cap]).astype(np.float64)
 
     def state_tail_head(self):
-        """(tail, head) node of every state; a wait loop has tail == head."""
+        """(tail, head) node of every state; a wait loop has tail == head (-1: none, with an
+        explicit state graph)."""
+        if self.state_tail is not None:
+            return np.asarray(self.state_tail, np.int32), np.asarray(self.state_head, np.int32)
         loops = np.arange(self.n_nodes, dtype=np.int32)
         tail = np.concatenate([self.edge_src, loops]).astype(np.int32)
         head = np.concatenate([self.edge_dst, loops]).astype(np.int32)
@@ -90,17 +98,19 @@ class Instance:
         nnz(K) counts the transitions of the line graph with wait loops, i.e. the
         ordered state pairs (i, j) with head(i) == tail(j).
         """
-        tail, head = self.state_tail_head()
-        indeg = np.bincount(head, minlength=self.n_nodes).astype(np.int64)
-        outdeg = np.bincount(tail, minlength=self.n_nodes).astype(np.int64)
-        nnz = int(np.sum(indeg * outdeg))
-        return 2 * (self.T - 1) * nnz * self.L
+        return 2 * (self.T - 1) * self.nnz_line_graph() * self.L
 
     def nnz_line_graph(self) -> int:
+        """Ordered state pairs (i, j) with head(i) == tail(j), plus the storage states that do
+        not already follow themselves."""
         tail, head = self.state_tail_head()
-        indeg = np.bincount(head, minlength=self.n_nodes).astype(np.int64)
-        outdeg = np.bincount(tail, minlength=self.n_nodes).astype(np.int64)
-        return int(np.sum(indeg * outdeg))
+        indeg = np.bincount(head[head >= 0], minlength=self.n_nodes).astype(np.int64)
+        outdeg = np.bincount(tail[tail >= 0], minlength=self.n_nodes).astype(np.int64)
+        extra = 0
+        if self.state_hold is not None:
+            hold = np.asarray(self.state_hold) != 0
+            extra = int(np.sum(hold & ~((head >= 0) & (head == tail))))
+        return int(np.sum(indeg * outdeg)) + extra
 
 
 # ----------------------------------------------------------------------------------
@@ -434,6 +444,51 @@ def with_commodity_windows(inst, seed: int = 0, slack: int = 1):
         b[l] = rng.integers(a[l] + m, inst.T + 1)
     inst.commodity_t_in = a
     inst.commodity_t_out = b
+    return inst
+
+
+def traffic_routing_instance(seed: int = 0, rows: int = 4, cols: int = 4, L: int = 3, T: int = 8, eps: float = 0.1,
+                             cap_lo: float = 0.2, cap_hi: float = 0.6, edge_storage: bool = False):
+    """The traffic-routing state model of eq. cost_traffic_routing on a grid: states are the
+    directed streets plus, per commodity, a source state at its origin node (nothing enters it;
+    agents may stay) and a sink state at its destination node (nothing leaves it; agents stay).
+    The wait loops of the street nodes are closed (no storage at junctions).  With
+    edge_storage, agents may also stay on a street (storage on edges, Section 3.3; the street's
+    per-interval cost accumulates).  Layout: nodes 0..V-1 are the junctions, node V + 2 l the
+    source and node V + 2 l + 1 the sink of commodity l; state E + w is the state of node w."""
+    rng = np.random.default_rng(seed)
+    src, dst, pos = grid_graph(rows, cols)
+    V, E = rows * cols, src.shape[0]
+    Vx = V + 2 * L
+    od = []
+    while len(od) < L:
+        o, z = rng.choice(V, 2, replace=False)
+        h = int(hop_distances(V, src, dst, int(o))[int(z)])
+        if 1 <= h <= T - 2:
+            od.append((int(o), int(z)))
+    mass = rng.uniform(0.5, 1.5, L)
+    tail = np.concatenate([src, np.full(Vx, -1)]).astype(np.int32)
+    head = np.concatenate([dst, np.full(Vx, -1)]).astype(np.int32)
+    hold = np.zeros(E + Vx, np.int32)
+    if edge_storage:
+        hold[:E] = 1
+    for l, (o, z) in enumerate(od):
+        s_src, s_snk = E + V + 2 * l, E + V + 2 * l + 1
+        head[s_src] = o                   # a source leads onto the streets leaving its origin
+        tail[s_snk] = z                   # a sink is reached from the streets entering its destination
+        hold[s_src] = hold[s_snk] = 1
+    edge_cost = rng.uniform(0.5, 1.5, E)
+    edge_cap = rng.uniform(cap_lo, cap_hi, E) * mass.sum() / 4.0
+    inst = Instance(
+        name=f"traffic-routing{rows}x{cols}-L{L}-T{T}", n_nodes=Vx, edge_src=src, edge_dst=dst,
+        edge_cost=edge_cost, edge_cap=edge_cap, wait_cost=np.zeros(Vx), wait_cap=np.full(Vx, np.inf),
+        L=L, T=T, eps=eps,
+        src_comm=np.arange(L, dtype=np.int32), src_state=(E + V + 2 * np.arange(L)).astype(np.int32),
+        src_mass=mass.astype(np.float64),
+        snk_comm=np.arange(L, dtype=np.int32), snk_state=(E + V + 2 * np.arange(L) + 1).astype(np.int32),
+        snk_mass=mass.astype(np.float64),
+        pos=None, meta={"workload": "traffic_routing", "seed": seed, "od": od})
+    inst.state_tail, inst.state_head, inst.state_hold = tail, head, hold
     return inst
 
 

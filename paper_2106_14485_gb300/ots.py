@@ -235,6 +235,8 @@ def _torch_allocator(device: int):
 def _problem_desc(inst, device: int = 0, stream: int | None = None):
     """ots_problem_desc of an object with the attributes of ``instances.Instance`` plus the
     host arrays it points into (keep them alive while the descriptor is used)."""
+    if getattr(inst, "state_tail", None) is not None or getattr(inst, "state_hold", None) is not None:
+        raise ValueError("explicit state graphs (storage states) are not supported by the CUDA solver")
     c = lambda x, dt: np.ascontiguousarray(x, dtype=dt)
     arr = {
         "edge_src": c(inst.edge_src, np.int32), "edge_dst": c(inst.edge_dst, np.int32),

@@ -19,6 +19,8 @@ import numpy as np
 
 
 def tail_head(inst):
+    if getattr(inst, "state_tail", None) is not None:            # explicit state graph (-1: none)
+        return np.asarray(inst.state_tail), np.asarray(inst.state_head)
     V = inst.n_nodes
     tail = np.concatenate([np.asarray(inst.edge_src), np.arange(V)])
     head = np.concatenate([np.asarray(inst.edge_dst), np.arange(V)])
@@ -26,9 +28,14 @@ def tail_head(inst):
 
 
 def dense_K(inst) -> np.ndarray:
-    """K_ij = 1 if edge i leads to edge j (second vertex of i is the first vertex of j)."""
+    """K_ij = 1 if edge i leads to edge j (second vertex of i is the first vertex of j), and
+    K_ii = 1 for a state that may hold its flow (storage, Section 3.3)."""
     tail, head = tail_head(inst)
-    return (head[:, None] == tail[None, :]).astype(np.float64)
+    K = ((head[:, None] == tail[None, :]) & (head[:, None] >= 0)).astype(np.float64)
+    hold = getattr(inst, "state_hold", None)
+    if hold is not None:
+        K[np.arange(K.shape[0]), np.arange(K.shape[0])] = np.maximum(np.diag(K), np.asarray(hold, np.float64))
+    return K
 
 
 def dense_marginals(inst):
