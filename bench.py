@@ -607,7 +607,10 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 float-float (fp32 hi + fp16 lo log2 messages), f64 reductions",
+            "dtype": "f32",
+            "number_format": "log2 messages as an fp32 part on a power-of-two grid plus a 16-bit integer "
+                             "remainder (float-float arithmetic in f32); f64 convergence sums, boundary updates "
+                             "and flows",
             "data": "synthetic", "config": workload_config(inst, args.tol),
             "solves_per_s": solves, "traffic_solve": traffic, "batch": batch, "serving": serve,
             "passes_timed": args.steps, "src_residual_after": final["src_residual"],
