@@ -203,7 +203,7 @@ def measured_traffic(horizon: int):
 
 def forward_bytes_per_launch(info, inst):
     """Algorithmic bytes of one forward-step launch: read A_{t-1} and B_{t+1}, write A_t
-    (6 bytes per entry: fp32 hi + fp16 lo) for V x L node rows, plus the per-state vectors
+    (6 bytes per entry: fp32 hi + 16-bit remainder) for V x L node rows, plus the per-state vectors
     (cost, capacity, old/new duals, weights, CSR: 56 bytes per state) and the node CSR."""
     V, S, L = info["n_nodes"], info["n_states"], inst.L
     return 18 * V * L + 56 * S + 4 * (V + 1)
