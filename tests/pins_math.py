@@ -362,3 +362,15 @@ def window_tensor_sinkhorn(inst, iters=20000, tol=1e-13):
         if err / R01.sum() < tol and excess / R01.sum() < tol:
             break
     return proj
+
+
+def primal_objective(inst, tz, M) -> float:
+    """Entropic primal objective of eq. multicommodity_reg on the full tensor, without the constant
+    of the entropy term: sum over paths of M (path cost) + eps M (log M - 1), with the state
+    costs C_L applied at t = 2..T-1 (the transitions of K cost nothing)."""
+    cost = np.zeros((tz.L, len(tz.paths)))
+    for t in range(1, tz.T - 1):
+        C = cost_at(inst, t + 1)                                    # [L, S], 1-based time t + 1
+        cost += C[:, tz.paths[:, t]]
+    pos = M > 0
+    return float(np.sum(M * cost) + inst.eps * np.sum(M[pos] * (np.log(M[pos]) - 1.0)))

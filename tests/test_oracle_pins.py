@@ -471,3 +471,17 @@ def test_commodity_capacities_reductions():
     r = od.solve(max_iters=100000, tol=1e-13)
     assert r["status"] == 0 and r["iters"] < 100000
     np.testing.assert_allclose(od.flows(), os_.flows(), rtol=1e-8, atol=1e-11)
+
+
+@pytest.mark.parametrize("cap_scale", [None, 0.8])
+def test_dual_objective_equals_the_primal_at_the_optimum(cap_scale):
+    """Strong duality (Theorem 3): at the optimum the dual objective the oracle reports equals the
+    entropic primal objective evaluated directly on the optimal tensor (both without the constant
+    of the entropy term), with and without binding capacities."""
+    inst = tiny_instance(seed=7, T=5, L=2, cap_scale=cap_scale, eps=0.5)
+    o = Oracle(inst)
+    r = o.solve(max_iters=100000, tol=1e-13)
+    assert r["status"] == 0 and r["src_resid"] < 1e-12 and r["cap_viol"] < 1e-12
+    tz, M, _ = PM.tensor_sinkhorn(inst)
+    primal = PM.primal_objective(inst, tz, M)
+    assert o.dual_objective() == pytest.approx(primal, rel=1e-9, abs=1e-12)
