@@ -374,3 +374,35 @@ def primal_objective(inst, tz, M) -> float:
         cost += C[:, tz.paths[:, t]]
     pos = M > 0
     return float(np.sum(M * cost) + inst.eps * np.sum(M[pos] * (np.log(M[pos]) - 1.0)))
+
+
+def brute_messages(inst, u, U01, U0T):
+    """The messages of Theorem 6 by direct summation over partial paths (linear domain):
+    hatPsi_t[l, j] sums U01[l, i_1] prod_s K[i_s, i_{s+1}] prod_{s=2}^{t-1} K_L[l, i_s] u_s[i_s] over the
+    paths (i_1, ..., i_t = j), t = 2..T; Psi_t[l, i] sums prod_s K[i_s, i_{s+1}]
+    prod_{s=t+1}^{T-1} K_L[l, i_s] u_s[i_s] U0T[l, i_T] over the paths (i = i_t, ..., i_T), t = 1..T-1.
+    u is [T+1, S] (rows 2..T-1 used).  Returns (hat [T+1, L, S], psi [T+1, L, S]) by row t."""
+    K = dense_K(inst)
+    L, T, S = inst.L, inst.T, K.shape[0]
+    KL = {s: np.exp(-cost_at(inst, s) / inst.eps) for s in range(2, T)}
+    hat = np.zeros((T + 1, L, S))
+    psi = np.zeros((T + 1, L, S))
+    for t in range(2, T + 1):
+        for p in itertools.product(range(S), repeat=t):
+            k = np.prod([K[p[s], p[s + 1]] for s in range(t - 1)])
+            if k == 0:
+                continue
+            w = U01[:, p[0]] * k
+            for s in range(2, t):                                  # 1-based interval s at p[s - 1]
+                w = w * KL[s][:, p[s - 1]] * u[s][p[s - 1]]
+            hat[t, :, p[-1]] += w
+    for t in range(1, T):
+        for p in itertools.product(range(S), repeat=T - t + 1):
+            k = np.prod([K[p[s], p[s + 1]] for s in range(T - t)])
+            if k == 0:
+                continue
+            w = U0T[:, p[-1]] * k
+            for s in range(t + 1, T):
+                w = w * KL[s][:, p[s - t]] * u[s][p[s - t]]
+            psi[t, :, p[0]] += w
+    return hat, psi

@@ -72,9 +72,18 @@ def test_projections_match_brute_force(T):
     for t in range(1, T + 1):
         ref = tz.proj0t(M, t)
         np.testing.assert_allclose(P[t - 1], ref, rtol=1e-12, atol=1e-14 * ref.max())
-    # messages equal the brute-force partial sums of Theorem 6's proof at one state
+    # the messages equal the partial sums of Theorem 6 over partial paths
     h, b = o.messages()
     assert h.shape == (T - 1, L, S) and b.shape == (T - 1, L, S)
+    if T <= 4:
+        hat, psi = PM.brute_messages(inst, u, np.where(R01 > 0, np.exp(U01), 0), np.where(R0T > 0, np.exp(U0T), 0))
+        for t in range(2, T + 1):
+            ref = hat[t]
+            with np.errstate(divide="ignore"):
+                np.testing.assert_allclose(np.exp(h[t - 2]), ref, rtol=1e-12, atol=1e-14 * ref.max())
+        for t in range(1, T):
+            ref = psi[t]
+            np.testing.assert_allclose(np.exp(b[t - 1]), ref, rtol=1e-12, atol=1e-14 * ref.max())
 
 
 def test_fixed_point_matches_tensor_sinkhorn():
