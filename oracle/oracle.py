@@ -40,12 +40,15 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
-def _load():
+def _load(path: str | None = None):
+    """The oracle library (built on first use), or, for the tests that plant mistakes in copies of
+    the oracle, the library at path."""
     global _lib
-    if _lib is not None:
+    if path is None and _lib is not None:
         return _lib
-    build()
-    lib = ctypes.CDLL(_SO)
+    if path is None:
+        build()
+    lib = ctypes.CDLL(path or _SO)
     lib.orc_create.restype = ctypes.c_void_p
     lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.c_int, ctypes.c_int,
                                ctypes.c_double, _f64p, ctypes.c_int, _f64p,
@@ -86,7 +89,8 @@ def _load():
     lib.orc_projections.restype = ctypes.c_int
     lib.orc_sample_backward_products.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
     lib.orc_sample_backward_products.restype = ctypes.c_int
-    _lib = lib
+    if path is None:
+        _lib = lib
     return lib
 
 
@@ -108,8 +112,8 @@ def state_cost_matrix(inst) -> np.ndarray:
 class Oracle:
     """FP64 log-domain Algorithm 2 for one instance."""
 
-    def __init__(self, inst, threads: int | None = None):
-        lib = _load()
+    def __init__(self, inst, threads: int | None = None, lib_path: str | None = None):
+        lib = _load(lib_path)
         if threads:
             lib.orc_set_threads(int(threads))
         self.inst = inst
