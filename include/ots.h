@@ -181,6 +181,13 @@ ots_status ots_default_solve_opts(ots_solve_opts *opts);
  * every sink from its commodity's sources within T-1 transitions (OTS_ERR_INFEASIBLE). */
 ots_status ots_create_problem(const ots_problem_desc *desc, ots_problem **out);
 
+/* The host part of ots_create_problem alone: every check of the descriptor (arguments, state
+ * graph, costs, capacities, masses, windows) and the reachability test, with no device, stream
+ * or allocator call (desc->device, stream and allocator are not used).  OTS_OK when
+ * ots_create_problem would get past its host part; otherwise the same status and message
+ * (ots_last_error).  Runs on machines without a GPU. */
+ots_status ots_check_problem(const ots_problem_desc *desc);
+
 /* Run Algorithm 2 (Section 4.3) until convergence: source update U01 <- R01 ./ Psi_1,
  * forward sweep with the capacity updates u_t <- min(d ./ ((hatPsi_t .* Psi_t .* K_L)^T 1), 1),
  * sink update U0T <- R0T ./ hatPsi_T, backward sweep (eq. psi_hat, eq. psi, Corollary 7).

@@ -581,6 +581,15 @@ ots_status ots_create_problem(const ots_problem_desc *d, ots_problem **out) {
   return create_problem_impl(d, CreateOpts{}, out);
 }
 
+ots_status ots_check_problem(const ots_problem_desc *d) {
+  g_last_error.clear();
+  ots_problem *p = nullptr;
+  const ots_status st = build_problem_host(d, CreateOpts{}, &p);
+  if (st) return st;
+  delete p;   // the host part holds no device resource: no stream, arena, events or pinned memory yet
+  return OTS_OK;
+}
+
 }  // extern "C"
 
 // Host part of the construction (no CUDA call): validation, state graph, per-state data,

@@ -93,7 +93,7 @@ class ServerStats(ctypes.Structure):
                 ("batch_launches", ctypes.c_int64), ("batch_ticks", ctypes.c_int64)]
 
 
-EXPORTED = ["ots_default_solve_opts", "ots_create_problem", "ots_sinkhorn_solve", "ots_iterate", "ots_get_flows",
+EXPORTED = ["ots_default_solve_opts", "ots_create_problem", "ots_check_problem", "ots_sinkhorn_solve", "ots_iterate", "ots_get_flows",
             "ots_get_commodity_flows", "ots_get_commodity_flows_noalloc", "ots_get_duals", "ots_set_duals", "ots_problem_info", "ots_last_pass_timing",
             "ots_problem_stream", "ots_destroy_problem", "ots_status_string", "ots_last_error",
             "ots_default_batch_desc", "ots_batch_create", "ots_batch_add", "ots_batch_run", "ots_batch_status",
@@ -116,6 +116,7 @@ def load_library(path: str = LIB_PATH):
     P = ctypes.c_void_p
     lib.ots_default_solve_opts.argtypes = [ctypes.POINTER(SolveOpts)]
     lib.ots_create_problem.argtypes = [ctypes.POINTER(ProblemDesc), ctypes.POINTER(P)]
+    lib.ots_check_problem.argtypes = [ctypes.POINTER(ProblemDesc)]
     lib.ots_sinkhorn_solve.argtypes = [P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport)]
     lib.ots_iterate.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(SolveReport)]
     lib.ots_get_flows.argtypes = [P, ctypes.c_int32, ctypes.c_int32, _f64p]
@@ -306,6 +307,12 @@ def ots_create_problem(inst, device: int = 0, stream: int | None = None, allocat
     _check(lib.ots_create_problem(ctypes.byref(d), ctypes.byref(out)))
     S = int(inst.n_nodes) + d.n_edges
     return Handle(out, keep, S, d.T, d.L, d.n_sources, d.n_sinks)
+
+
+def ots_check_problem(inst) -> None:
+    """The host-side checks of ots_create_problem (no device needed); raises OTSError."""
+    d, arr = _problem_desc(inst, 0, None)
+    _check(load_library().ots_check_problem(ctypes.byref(d)))
 
 
 def ots_default_solve_opts() -> SolveOpts:

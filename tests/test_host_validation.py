@@ -64,6 +64,9 @@ def test_malformed_descriptor_is_rejected(O, mutate):
     with pytest.raises(O.OTSError) as e:
         O.ots_create_problem(inst, allocator="cuda")
     assert e.value.code == O.OTS_ERR_INVALID_ARG, e.value
+    with pytest.raises(O.OTSError) as e:                          # the same through the host-only check
+        O.ots_check_problem(inst)
+    assert e.value.code == O.OTS_ERR_INVALID_ARG, e.value
 
 
 def test_negative_psi_stride_is_rejected(O):
@@ -90,3 +93,39 @@ def test_error_message_names_the_problem(O):
     with pytest.raises(O.OTSError) as e:
         O.ots_create_problem(inst, allocator="cuda")
     assert "capacity" in str(e.value)
+
+
+def _valid_instances():
+    yield I.grid_single_commodity(0)
+    yield I.rgg400(0)
+    yield I.traffic_grid(0)                                       # the benchmark workload (host part only)
+    yield I.with_time_varying_costs(I.rgg_instance(seed=3, n=60, L=5, T=12, eps=0.05), seed=1, closures=3)
+    yield I.with_time_varying_capacities(I.rgg_instance(seed=3, n=60, L=5, T=12, eps=0.05), seed=1)
+    yield I.with_commodity_windows(I.rgg_instance(seed=3, n=60, L=5, T=14, eps=0.05), seed=2)
+    yield I.single_commodity_instance(0)
+    x = I.rgg_instance(seed=3, n=40, L=3, T=10, eps=0.05)
+    x.commodity_capacity = np.full((x.L, x.n_states), 0.5)
+    yield x
+
+
+def test_valid_instances_pass_the_host_checks(O):
+    """The host part of the construction (state graph, per-state data, boundary triples,
+    reachability) accepts every workload the tests and the benchmark use, without a device."""
+    for inst in _valid_instances():
+        O.ots_check_problem(inst)
+
+
+def test_host_check_reports_unreachable_sinks(O):
+    inst = I.grid_single_commodity(0, T=5)
+    E = inst.n_edges
+    inst.src_comm = np.zeros(1, np.int32); inst.src_state = np.array([E + 0], np.int32); inst.src_mass = np.array([1.0])
+    inst.snk_comm = np.zeros(1, np.int32); inst.snk_state = np.array([E + 24], np.int32); inst.snk_mass = np.array([1.0])
+    with pytest.raises(O.OTSError) as e:
+        O.ots_check_problem(inst)
+    assert e.value.code == O.OTS_ERR_INFEASIBLE
+    inst.T = 9            # wait loop, 8 streets, wait loop: 9 transitions, one more than T - 1 = 8
+    with pytest.raises(O.OTSError) as e:
+        O.ots_check_problem(inst)
+    assert e.value.code == O.OTS_ERR_INFEASIBLE
+    inst.T = 10
+    O.ots_check_problem(inst)
