@@ -129,3 +129,14 @@ def test_host_check_reports_unreachable_sinks(O):
     assert e.value.code == O.OTS_ERR_INFEASIBLE
     inst.T = 10
     O.ots_check_problem(inst)
+
+
+def test_commodity_count_limits(O):
+    """The ABI takes 1 <= L <= 4096 (at most 256 threads per node row with four chunks of four
+    commodities); the host part accepts both ends and rejects one more."""
+    for L in (1, 4096):
+        O.ots_check_problem(I.rgg_instance(seed=3, n=30, L=L, T=6, eps=0.1))
+    x = I.rgg_instance(seed=3, n=30, L=4097, T=6, eps=0.1)
+    with pytest.raises(O.OTSError) as e:
+        O.ots_check_problem(x)
+    assert e.value.code == O.OTS_ERR_INVALID_ARG
