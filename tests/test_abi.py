@@ -159,3 +159,46 @@ def build_c_example():
 
 def test_c_example_builds_against_the_header_and_the_library():
     assert os.path.exists(build_c_example())
+
+
+def test_c_program_checks_a_descriptor_without_a_gpu():
+    """A plain C caller validates descriptors through the ABI on a machine without a GPU: a 3-node
+    line with one commodity is accepted; an unreachable sink and a negative capacity are refused
+    with their status codes."""
+    import subprocess
+    import tempfile
+    from paper_2106_14485_gb300 import build
+    pkg = os.path.dirname(build.build())
+    prog = r'''
+#include <math.h>
+#include <stdio.h>
+#include "ots.h"
+int main(void) {
+  int32_t src[4] = {0, 1, 1, 2}, dst[4] = {1, 2, 0, 1};
+  double cost[4] = {1, 1, 1, 1}, cap[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+  int32_t comm[1] = {0}, s_state[1] = {4 + 0}, z_state[1] = {4 + 2};
+  double mass[1] = {1.0};
+  ots_problem_desc d = {0};
+  d.n_nodes = 3; d.n_edges = 4; d.edge_src = src; d.edge_dst = dst; d.edge_cost = cost; d.edge_capacity = cap;
+  d.add_wait_loops = 1; d.T = 4; d.L = 1; d.eps = 0.1;
+  d.n_sources = 1; d.src_commodity = comm; d.src_state = s_state; d.src_mass = mass;
+  d.n_sinks = 1; d.snk_commodity = comm; d.snk_state = z_state; d.snk_mass = mass;
+  printf("%d\n", (int)ots_check_problem(&d));
+  d.T = 3;                       /* wait loop, two streets, wait loop: three transitions > T - 1 */
+  printf("%d\n", (int)ots_check_problem(&d));
+  d.T = 4; cap[1] = -1.0;
+  printf("%d %s\n", (int)ots_check_problem(&d), ots_last_error());
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "check.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "check")
+        subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), c, "-o", exe,
+                               "-L", pkg, "-lots", "-Wl,-rpath," + pkg])
+        out = subprocess.check_output([exe]).decode().split("\n")
+    from paper_2106_14485_gb300 import ots
+    assert int(out[0]) == ots.OTS_OK
+    assert int(out[1]) == ots.OTS_ERR_INFEASIBLE
+    assert int(out[2].split()[0]) == ots.OTS_ERR_INVALID_ARG and "capacity" in out[2]
