@@ -406,3 +406,36 @@ def brute_messages(inst, u, U01, U0T):
                 w = w * KL[s][:, p[s - t]] * u[s][p[s - t]]
             psi[t, :, p[0]] += w
     return hat, psi
+
+
+def tensor_pass_with_measures(inst, tz, u, U01, U0T):
+    """One pass of Algorithm 2 done on the full tensor (Proposition 5's block updates in the
+    order U01, u_2 .. u_{T-1}, U0T), with the two convergence measures taken from the tensor's
+    projections: the relative L1 source mismatch ||P_{0,1} - R01||_1 / ||R01||_1 of the tensor
+    before the U01 update, and the relative capacity residual
+    sum_t sum_i |P_t(after the u_t update) - P_t(before it)| / ||R01||_1.
+
+    u is [T+1, S] (rows 2..T-1 used), U01 and U0T are L x S linear duals (0 off the supports).
+    Returns (mismatch, residual, u, U01, U0T) with the updated duals (new arrays)."""
+    R01, R0T = dense_marginals(inst)
+    T = tz.T
+    u, U01, U0T = u.copy(), U01.copy(), U0T.copy()
+    mass = R01.sum()
+    P1 = tz.proj0t(tz.M(u, U01, U0T), 1)
+    mismatch = np.abs(P1 - R01).sum() / mass
+    with np.errstate(divide="ignore", invalid="ignore"):
+        U01 = np.where(R01 > 0, U01 * R01 / np.where(P1 > 0, P1, 1.0), 0.0)
+    resid = 0.0
+    for t in range(2, T):
+        before = tz.proj0t(tz.M(u, U01, U0T), t).sum(0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            column = np.where(u[t] > 0, before / np.where(u[t] > 0, u[t], 1.0), 0.0)
+            d = capacity_at(inst, t)
+            new = np.where(column > 0, np.minimum(d / np.where(column > 0, column, 1.0), 1.0), 1.0)
+        u[t] = new
+        after = tz.proj0t(tz.M(u, U01, U0T), t).sum(0)
+        resid += np.abs(after - before).sum()
+    PT = tz.proj0t(tz.M(u, U01, U0T), T)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        U0T = np.where(R0T > 0, U0T * R0T / np.where(PT > 0, PT, 1.0), 0.0)
+    return mismatch, resid / mass, u, U01, U0T

@@ -1,9 +1,11 @@
 """The pins catch plausible mistakes in the oracle.  Each case compiles a copy of
 ``oracle/ots_oracle.c`` with one planted mistake (a dropped term, a wrong sign, a wrong index, a
-transposed operand), on the CPU, and checks that at least one of three fast pins rejects it:
-projections and messages against brute force at random duals (Theorem 6), the fixed point against
-Proposition 5 on the full tensor with binding capacities, and strong duality at the optimum
-(Theorem 3).  The unmodified oracle passes all three."""
+transposed operand, a convergence measure taken at the wrong moment or scaled wrongly), on the
+CPU, and checks that at least one of four fast pins rejects it: projections and messages against
+brute force at random duals (Theorem 6), the fixed point against Proposition 5 on the full tensor
+with binding capacities, strong duality at the optimum (Theorem 3), and the two convergence
+measures of a pass against the same pass done on the tensor.  The unmodified oracle passes all
+four."""
 import os
 import subprocess
 import tempfile
@@ -36,6 +38,20 @@ MUTANTS = {
         ("o->logU01[q] = log(o->R01[q]) - p1;", "o->logU01[q] = log(o->R01[q]) + p1;", 1)],
     "sink update with the wrong sign": [
         ("o->logU0T[q] = log(o->R0T[q]) - ph[q];", "o->logU0T[q] = log(o->R0T[q]) + ph[q];", 1)],
+    "source mismatch taken after the source update": [
+        ("resid += fabs(exp(o->logU01[q] + p1) - o->R01[q]);\n      if (!(p1 > -INFINITY)) bad = 1;\n"
+         "      o->logU01[q] = log(o->R01[q]) - p1;",
+         "if (!(p1 > -INFINITY)) bad = 1;\n      o->logU01[q] = log(o->R01[q]) - p1;\n"
+         "      resid += fabs(exp(o->logU01[q] + p1) - o->R01[q]);", 1)],
+    "source mismatch without the absolute value": [
+        ("resid += fabs(exp(o->logU01[q] + p1) - o->R01[q]);", "resid += exp(o->logU01[q] + p1) - o->R01[q];", 1)],
+    "capacity residual as the excess left after the update": [
+        ("viol += flow_change(lu_old, lu[i], ls[i]);", "viol += fmax(exp(lu[i] + ls[i]) - di, 0.0);", 1)],
+    "capacity residual counting only the duals that drop": [
+        ("return exp(lu_old + ls) * fabs(expm1(lu_new - lu_old));",
+         "return lu_new < lu_old ? exp(lu_old + ls) * fabs(expm1(lu_new - lu_old)) : 0.0;", 1)],
+    "capacity residual not relative to the source mass": [
+        ("if (cap_viol) *cap_viol = viol / o->mass01;", "if (cap_viol) *cap_viol = viol;", 1)],
     "dual objective without the capacity term": [
         ("if (isfinite(cap_at(o, t, s))) a += xlogy(cap_at(o, t, s), o->logu[(size_t)t * o->S + s]);",
          "if (isfinite(cap_at(o, t, s))) a += 0.0;", 1)],
@@ -123,7 +139,30 @@ def pin_strong_duality(lib):
     return bool(np.isclose(dual, PM.primal_objective(inst, tz, M), rtol=1e-8, atol=1e-12))
 
 
-PINS = (pin_projections, pin_fixed_point, pin_strong_duality)
+def pin_measures(lib):
+    """The two convergence measures and the duals of one pass against the same pass done on the
+    full tensor: two cold passes, then one pass from duals pulled below the fixed point."""
+    from tests.test_measure_pins import binding_instance, check_pass
+    try:
+        inst = binding_instance(5)
+        tz = _reference(inst)[0]
+        o = Oracle(inst, lib_path=lib)
+        o.backward_sweep()
+        check_pass(o, inst, tz)
+        check_pass(o, inst, tz)
+        _, o2, r = _solved(lib)
+        if r["status"] != 0:
+            return False
+        lu, a, b = o2.get_duals()
+        o3 = Oracle(inst, lib_path=lib)
+        o3.set_duals(lu - 0.5, a, b)
+        check_pass(o3, inst, tz)
+    except (AssertionError, RuntimeError, ValueError):
+        return False
+    return True
+
+
+PINS = (pin_projections, pin_fixed_point, pin_strong_duality, pin_measures)
 
 
 @pytest.fixture(scope="module")
@@ -141,7 +180,7 @@ def variants():
 
 
 def test_unmodified_oracle_passes_every_pin(variants):
-    assert [p(variants["control"]) for p in PINS] == [True, True, True]
+    assert [p(variants["control"]) for p in PINS] == [True, True, True, True]
 
 
 @pytest.mark.parametrize("name", list(MUTANTS))
