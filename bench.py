@@ -269,8 +269,92 @@ def run_reference(args):
     return 0
 
 
+ORACLE_BATCH_SAMPLE = 8
+TRAFFIC_SAMPLE = ((0, 4), (1020, 1024))      # commodity ranges the oracle evaluates on the traffic workload
+
+
+def oracle_sample_index(st):
+    """A seeded sample of converged instances of the batch for the oracle leg."""
+    ok = [k for k, s in enumerate(st) if s["status"] == 0]
+    if not ok:
+        return []
+    rng = np.random.default_rng(8)
+    return sorted(int(k) for k in rng.choice(ok, min(ORACLE_BATCH_SAMPLE, len(ok)), replace=False))
+
+
+def traffic_commodity_sample(ots, h, inst):
+    """GPU per-commodity flows of the sampled commodities, and the duals, kept for the oracle leg."""
+    ranges = [(a, b) for a, b in TRAFFIC_SAMPLE if b <= inst.L]
+    return {"inst": inst, "duals": ots.ots_get_duals(h), "ranges": ranges,
+            "cflows": [ots.ots_get_commodity_flows(h, 1, inst.T + 1, a, b) for a, b in ranges]}
+
+
+def oracle_check(item, optimum_tol=None):
+    """Oracle leg: the FP64 oracle loads the GPU's duals and evaluates Theorem 6 there.  Returns
+    the flow error of the GPU against it (relative L1 and the worst entry relative to
+    1e-5 F* + 1e-9 max F*) and the marginal violation the oracle measures at those duals (source
+    mismatch ||P_{0,1} - R01||_1 / ||R01||_1 and, with every commodity, capacity excess
+    sum_t (P_t - d)_+ / ||R01||_1).  With optimum_tol, the oracle also solves the instance from
+    its own initialisation to that tolerance and the GPU's flows are compared with that optimum."""
+    from oracle.oracle import Oracle
+    inst = item["inst"]
+    L, S, T = inst.L, inst.n_states, inst.T
+    lu, U01, U0T = item["duals"]
+    a = np.full((L, S), -np.inf)
+    b = np.full((L, S), -np.inf)
+    a[inst.src_comm, inst.src_state] = U01
+    b[inst.snk_comm, inst.snk_state] = U0T
+    R01 = np.zeros((L, S))
+    np.add.at(R01, (inst.src_comm, inst.src_state), inst.src_mass)
+    o = Oracle(inst)
+    o.set_duals(lu, a, b)
+    t0 = time.perf_counter()
+
+    def elem(F, Fref):
+        return float((np.abs(F - Fref) / (1e-5 * np.abs(Fref) + 1e-9 * np.abs(Fref).max())).max())
+
+    out = {}
+    if "ranges" in item:                       # sampled commodities of a large instance
+        num = den = mis = mass = worst = 0.0
+        for (l0, l1), P in zip(item["ranges"], item["cflows"]):
+            Pref = o.projections(l0, l1)
+            num += float(np.abs(P - Pref).sum())
+            den += float(np.abs(Pref).sum())
+            worst = max(worst, elem(P, Pref))
+            mis += float(np.abs(Pref[0] - R01[l0:l1]).sum())
+            mass += float(R01[l0:l1].sum())
+        out.update(commodities=[list(r) for r in item["ranges"]], commodity_flow_rel_l1=num / den,
+                   commodity_flow_elem_worst=worst, oracle_src_mismatch=mis / mass)
+    else:                                      # every commodity
+        Fref = np.zeros((T, S))
+        mis = 0.0
+        for l0 in range(0, L, 32):
+            l1 = min(L, l0 + 32)
+            Pref = o.projections(l0, l1)
+            Fref += Pref.sum(axis=1)
+            mis += float(np.abs(Pref[0] - R01[l0:l1]).sum())
+        d = np.concatenate([inst.edge_cap, inst.wait_cap]).astype(np.float64)
+        F = item["flows"]
+        out.update(flow_rel_l1=float(np.abs(F - Fref).sum() / np.abs(Fref).sum()), flow_elem_worst=elem(F, Fref),
+                   oracle_src_mismatch=mis / R01.sum(),
+                   oracle_cap_excess=float(sum(np.maximum(Fref[t - 1] - d, 0).sum() for t in range(2, T))) / R01.sum())
+        if optimum_tol is not None:
+            o2 = Oracle(inst)
+            r = o2.solve(max_iters=200000, tol=optimum_tol)
+            Fo = o2.flows()
+            out.update(optimum_tol=optimum_tol, optimum_passes=r["iters"],
+                       flow_rel_l1_vs_optimum=float(np.abs(F - Fo).sum() / np.abs(Fo).sum()),
+                       flow_elem_worst_vs_optimum=elem(F, Fo))
+    out["oracle_seconds"] = time.perf_counter() - t0
+    return out
+
+
 def pct(a, q):
     return float(np.percentile(np.asarray(a), q)) if len(a) else None
+
+
+def ms(x):
+    return None if x is None else 1e3 * x
 
 
 def plain_continuation(args, x):
@@ -322,6 +406,9 @@ def bench_batch(args, ots, torch, local, insts, gen_s):
         st_b.append(ots.ots_batch_status(b, i))
         flows_b.append(ots.ots_batch_get_flows(b, i) if st_b[-1]["status"] in (0, ots.OTS_ERR_NOT_CONVERGED) else None)
     t_end = time.perf_counter()
+    sample = oracle_sample_index(st_b)
+    samples = [{"inst": insts[k], "index": k, "flows": flows_b[k], "duals": ots.ots_batch_get_duals(b, ids[k])}
+               for k in sample]
     info1 = ots.ots_batch_info(b)
     lat_b = [s["seconds"] for s in st_b]
     ots.ots_batch_destroy(b)
@@ -356,30 +443,41 @@ def bench_batch(args, ots, torch, local, insts, gen_s):
     diffs = [float(np.abs(fb - fp).sum() / np.abs(fp).sum()) for fb, fp in zip(flows_b, flows_p)
              if fb is not None and fp is not None]
     n = len(insts)
-    conv_b = sum(1 for s in st_b if s["status"] == 0)
-    conv_p = sum(1 for s in st_p if s["status"] == 0)
+    ok_b = [s["status"] == 0 for s in st_b]
+    ok_p = [s["status"] == 0 for s in st_p]
+    conv_b, conv_p = sum(ok_b), sum(ok_p)
+    # latencies of converged solves only (the metric is solves at marginal error <= tol)
+    lat_b_ok = [v for v, ok in zip(lat_b, ok_b) if ok]
+    lat_p_sub_ok = [v for v, ok in zip(lat_p_sub, ok_p) if ok]
+    lat_p_ok = [v for v, ok in zip(lat_p, ok_p) if ok]
     upd = sum(s["iterations"] * x.n_updates_per_iteration() for s, x in zip(st_b, insts))
     return {
         "workload": f"{n} uneven instances: random geometric graphs n~U{{50..2000}} (mean degree 6), "
                     f"T~U{{10..80}}, L~U{{1..128}}, capacities U[0.2,1]*mass/8, eps=0.01, tol={args.tol}",
-        "batched": {"solves_per_s": n / (t_end - t0), "solve_only_per_s": n / (t_run - t_add),
-                    "updates_per_s": upd / (t_run - t_add),
+        "batched": {"solves_per_s": conv_b / (t_end - t0), "solve_only_per_s": conv_b / (t_run - t_add),
+                    "attempts_per_s": n / (t_end - t0), "updates_per_s": upd / (t_run - t_add),
                     "add_s": t_add - t0, "run_s": t_run - t_add, "flows_readback_s": t_end - t_run,
-                    "p50_ms": pct(lat_b, 50) * 1e3, "p99_ms": pct(lat_b, 99) * 1e3, "converged": conv_b,
+                    "p50_ms": ms(pct(lat_b_ok, 50)), "p99_ms": ms(pct(lat_b_ok, 99)),
+                    "all_attempts_p99_ms": ms(pct(lat_b, 99)), "converged": conv_b, "not_converged": n - conv_b,
                     "passes_mean": float(np.mean([s["iterations"] for s in st_b])),
                     "max_src_residual": max(s["src_residual"] for s in st_b),
                     "max_cap_violation": max(s["cap_violation"] for s in st_b),
                     "tick_launches": int(info1["ticks"] - info0["ticks"]),
                     "graph_launches": int(info1["launches"] - info0["launches"]),
                     "mapping": mapping, "autotune_s": tune_s},
-        "plain": {"solves_per_s": n / (tp1 - tp0), "solve_only_per_s": n / float(np.sum(solve_p)),
-                  "p50_ms": pct(lat_p_sub, 50) * 1e3, "p99_ms": pct(lat_p_sub, 99) * 1e3,
-                  "per_solve_p50_ms": pct(lat_p, 50) * 1e3, "per_solve_p99_ms": pct(lat_p, 99) * 1e3,
-                  "converged": conv_p, "kernel_launches": int(launches_p)},
-        "latency_note": "p50/p99 from submission of all instances at once (both arms); per_solve_* = one "
+        "plain": {"solves_per_s": conv_p / (tp1 - tp0), "solve_only_per_s": conv_p / float(np.sum(solve_p)),
+                  "attempts_per_s": n / (tp1 - tp0),
+                  "p50_ms": ms(pct(lat_p_sub_ok, 50)), "p99_ms": ms(pct(lat_p_sub_ok, 99)),
+                  "per_solve_p50_ms": ms(pct(lat_p_ok, 50)), "per_solve_p99_ms": ms(pct(lat_p_ok, 99)),
+                  "converged": conv_p, "not_converged": n - conv_p, "kernel_launches": int(launches_p)},
+        "latency_note": "solves_per_s and p50/p99 count converged solves only (marginal error <= tol); "
+                        "not_converged instances stopped at the pass limit (their capacities admit no feasible "
+                        "flow, or nearly none) and are reported apart; attempts_per_s counts every instance. "
+                        "p50/p99 from submission of all instances at once (both arms); per_solve_* = one "
                         "solve timed alone, without the wait for the instances before it",
         "max_rel_flow_diff_batched_vs_plain": max(diffs) if diffs else None,
         "generate_s": gen_s,
+        "_oracle_samples": samples,
     }
 
 
@@ -501,6 +599,7 @@ def run_ours(args):
     bwd_ms = [tm["backward_ms"] / (inst.T - 2)]
     final = r
     barrier()
+    checks = {"timed_passes": traffic_commodity_sample(ots, h, inst)} if rank == 0 else {}
 
     updates = args.steps * upd_per_pass
     elapsed_ms, updates_all = combine_ranks(pg, elapsed_ms, float(updates), "cuda")
@@ -535,6 +634,8 @@ def run_ours(args):
                                     raise_on_error=False)
         torch.cuda.synchronize()
         t_t = time.perf_counter() - t0
+        if rank == 0:
+            checks["traffic_solve"] = traffic_commodity_sample(ots, h_t, inst)
         ots.ots_destroy_problem(h_t)
         traffic = {"workload": workload_config(inst, args.tol)["workload"],
                    "continuation": f"eps {8 * inst.eps:g} -> {inst.eps:g} in 3 warm-start stages (stage tol 1e-4)",
@@ -558,6 +659,7 @@ def run_ours(args):
             rs = ots.ots_sinkhorn_solve(hs, tol=args.tol, check_every=2)
             lat.append(time.perf_counter() - t0)
             passes_s += rs["iterations"]
+        checks["rgg400"] = {"inst": rg, "duals": ots.ots_get_duals(hs), "flows": ots.ots_get_flows(hs)}
         ots.ots_destroy_problem(hs)
         lat = np.array(lat)
         solves = {"workload": f"random geometric graph n={rg.n_nodes}, L={rg.L}, T={rg.T}, eps={rg.eps}, "
@@ -601,8 +703,26 @@ def run_ours(args):
                          "frac": bb / (bwd_launch_ms * 1e-3) / 1e9 / hbm, "bytes_per_launch": bb,
                          "launch_ms": bwd_launch_ms}}
     cpu = None
+    oracle_error = None
+    samples = batch.pop("_oracle_samples", []) if batch else []
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(inst, args.cpu_seconds)
+        # oracle leg: the FP64 oracle evaluated at the GPU's results (duals and flows)
+        oracle_error = {"timed_passes": oracle_check(checks["timed_passes"])}
+        if traffic is not None:
+            traffic["oracle_error"] = oracle_error["traffic_solve"] = oracle_check(checks["traffic_solve"])
+        if solves is not None:
+            solves["oracle_error"] = oracle_error["rgg400_solves"] = oracle_check(checks["rgg400"], optimum_tol=1e-11)
+        if samples:
+            errs = [dict(oracle_check(x), index=x["index"], name=x["inst"].name) for x in samples]
+            batch["oracle_error"] = oracle_error["batch_sample"] = {
+                "instances": len(errs), "max_flow_rel_l1": max(e["flow_rel_l1"] for e in errs),
+                "max_flow_elem_worst": max(e["flow_elem_worst"] for e in errs),
+                "max_oracle_src_mismatch": max(e["oracle_src_mismatch"] for e in errs),
+                "max_oracle_cap_excess": max(e["oracle_cap_excess"] for e in errs), "per_instance": errs}
+        oracle_error["note"] = ("FP64 oracle at the GPU's duals: flow error of the GPU (relative L1; worst entry as "
+                                "|F-F*| / (1e-5 F* + 1e-9 max F*), <= 1 passes) and the marginal violation the oracle "
+                                "measures there; traffic workload on sampled commodities")
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -615,7 +735,7 @@ def run_ours(args):
             "solves_per_s": solves, "traffic_solve": traffic, "batch": batch, "serving": serve,
             "passes_timed": args.steps, "src_residual_after": final["src_residual"],
             "cap_violation_after": final["cap_violation"],
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches)}
+            "roofline": roof, "cpu_baseline": cpu, "oracle_error": oracle_error, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches)}
     print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

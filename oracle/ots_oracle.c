@@ -686,6 +686,7 @@ int orc_projections(orc *o, int l0, int l1, double *out) {
   if (!h || !b) { free(h); free(b); return ORC_NOMEM; }
   int rc = orc_messages(o, l0, l1, h, b);
   if (rc) { free(h); free(b); return rc; }
+#pragma omp parallel for schedule(static)
   for (int l = l0; l < l1; ++l) {
     const int a = t_in(o, l), z = t_out(o, l);
     for (int s = 0; s < S; ++s) {

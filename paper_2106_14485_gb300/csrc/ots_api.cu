@@ -784,9 +784,11 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
                               : (d->wait_cost ? d->wait_cost[s - p->E] : 0.0);
         if (!std::isfinite(c)) return bail(fail(OTS_ERR_INVALID_ARG, "commodity_cost must be finite"));
         const double x = -c / d->eps * kInvLn2;
-        const double h = std::nearbyint(x / q) * q;
+        double h = std::nearbyint(x / q) * q;
+        int units = (int)std::nearbyint((x - h) * 65536.0 / q);   // in [-32768, 32768]
+        if (units > 32767) { units -= 65536; h += q; }            // x - h = q/2 exactly
         klc_hi[(size_t)s * p->Lp + l] = (float)h;
-        klc_lo[(size_t)s * p->Lp + l] = (lo_t)((int)std::nearbyint((x - h) * 65536.0 / q) + 32768);
+        klc_lo[(size_t)s * p->Lp + l] = (lo_t)(units + 32768);
       }
   }
 

@@ -1,7 +1,7 @@
 // ots_device.cuh -- device-side types and helpers of the GB300 Sinkhorn solver.
 //
 // Representation.  Every message, dual and weight is a base-2 logarithm ("bits"): the
-// exponentials of Algorithm 2 become ex2 and the logarithms lg2 on the SFU.  A message
+// exponentials of Algorithm 2 become ex2 on the SFU and the logarithms log2f.  A message
 // entry x is stored in 6 bytes as x = hi + (lo - 32768) * q / 65536 with
 //   hi : FP32, an integer multiple of the per-problem quantum q = 2^k (k < 0),
 //   lo : uint16, the remainder in units of q / 65536 (|remainder| <= q / 2), biased by 32768
@@ -150,11 +150,12 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
-__device__ __forceinline__ float lg2(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
+// log2 for the one logarithm of every log-sum-exp output (and column sum).  The SFU's
+// lg2.approx errs by about +4e-8 on average for arguments in [1, 2), where these sums mostly
+// lie (the largest term contributes 1); a message passes through one such logarithm per time
+// step, so over a horizon of T steps the bias adds up to about T * 3e-8 of relative flow error,
+// the same sign at every step.  The libm-accurate log2f has no measurable mean error there.
+__device__ __forceinline__ float log2_unbiased(float x) { return log2f(x); }
 
 // Knuth's TwoSum: s + e == a + b exactly (round-to-nearest, no overflow).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -184,8 +185,20 @@ __device__ __forceinline__ void encode(float h, float l, const QScale &s, float 
     lo = kLoZero;
     return;
   }
-  const float hq = quant(__fadd_rn(h, l), s);
-  const float rem = __fadd_rn(__fsub_rn(h, hq), l);   // h - hq is exact
+  float hq = quant(__fadd_rn(h, l), s);
+  float rem = __fadd_rn(__fsub_rn(h, hq), l);         // h - hq is exact
+  // h + l rounded to FP32 is h itself when l is below half an ulp of h, and h can sit exactly
+  // halfway between two grid points: the grid point then chosen may be the far one for the
+  // value h + l, leaving |rem| up to q/2 + ulp(h)/2, past the 16-bit range.  Moving one whole
+  // quantum brings rem back to [-q/2, q/2] (both steps exact: q is a power of two, hq stays on
+  // the grid and rem - q is a difference of numbers within a factor of two).
+  if (rem > 0.5f * s.q) {
+    hq = __fadd_rn(hq, s.q);
+    rem = __fsub_rn(rem, s.q);
+  } else if (rem < -0.5f * s.q) {
+    hq = __fsub_rn(hq, s.q);
+    rem = __fadd_rn(rem, s.q);
+  }
   hi = hq;
   lo = lo_from_units(rintf(__fmul_rn(rem, s.lo_inv)));
 }
@@ -197,7 +210,7 @@ __device__ __forceinline__ void lse_encode(float m, float acc, const QScale &s, 
     lo = kLoZero;
     return;
   }
-  const float f = lg2(acc);
+  const float f = log2_unbiased(acc);
   const float fq = quant(f, s);
   hi = __fadd_rn(m, fq);                       // exact: both on the grid
   lo = lo_from_units(rintf(__fmul_rn(__fsub_rn(f, fq), s.lo_inv)));

@@ -351,7 +351,7 @@ template <bool PC>
 __device__ __forceinline__ void update_state(const StepArgs &a, int sk, float cm, float cs, bool write, float &w_hi,
                                              float &w_lo, float &viol, float2 &dual) {
   float col_hi = kNeg, col_lo = 0.f;
-  if (cm > kNegThresh && cs > 0.f) two_sum(cm, lg2(cs), col_hi, col_lo);  // log2 (hatPsi .* Psi (.* K_L))^T 1
+  if (cm > kNegThresh && cs > 0.f) two_sum(cm, log2_unbiased(cs), col_hi, col_lo);  // log2 (hatPsi .* Psi (.* K_L))^T 1
   const float klh = PC ? 0.f : ldexpf(a.kl_hi[sk], -a.kl_shift), kll = PC ? 0.f : ldexpf(a.kl_lo[sk], -a.kl_shift);
   if (!PC && col_hi > kNegThresh) {
     float s, e;
@@ -445,7 +445,7 @@ __device__ __forceinline__ void update_w(int mode, const QScale &qs, float cm, f
                                          float &lu_lo) {
   col_hi = kNeg;
   col_lo = 0.f;
-  if (cm > kNegThresh && cs > 0.f) two_sum(cm, lg2(cs), col_hi, col_lo);
+  if (cm > kNegThresh && cs > 0.f) two_sum(cm, log2_unbiased(cs), col_hi, col_lo);
   if (col_hi > kNegThresh) {
     float s, e;
     two_sum(col_hi, klh, s, e);

@@ -15,6 +15,7 @@ from paper_2106_14485_gb300 import instances as I
 pytestmark = pytest.mark.gpu
 
 FLOW_TOL = 1e-5
+ELEM_REL, ELEM_ABS = 1e-5, 1e-9     # entry-wise: |F - F*| <= ELEM_REL F* + ELEM_ABS max F*
 
 
 @pytest.fixture(scope="module")
@@ -30,6 +31,25 @@ def O():
 
 def rel_l1(a, b):
     return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+def assert_elementwise(F, Fref, what=""):
+    """Every entry within ELEM_REL of the oracle's, plus ELEM_ABS of the largest entry (so that
+    low-flow states cannot hide under an L1 norm dominated by the corridors); names the worst."""
+    r = np.abs(F - Fref) / (ELEM_REL * np.abs(Fref) + ELEM_ABS * np.abs(Fref).max())
+    k = int(np.argmax(r))
+    idx = np.unravel_index(k, r.shape)
+    assert r.flat[k] <= 1.0, f"{what}: worst entry {idx}: gpu {F[idx]!r} oracle {Fref[idx]!r} (ratio {r.flat[k]:.3g})"
+    return float(r.flat[k])
+
+
+def assert_duals_relative(lu, lu_ref, Fref, bound, what=""):
+    """log u is the relative error of u: compare it on the states that carry flow."""
+    carry = Fref[1:-1] > 1e-6 * Fref.max()
+    d = np.abs(lu - lu_ref)[carry]
+    k = int(np.argmax(d))
+    assert d[k] <= bound, f"{what}: log u differs by {d[k]:.3g} on a flow-carrying state (bound {bound})"
+    return float(d[k])
 
 
 def dense_duals(inst, U01, U0T):
@@ -59,7 +79,11 @@ def test_grid5x5_converged(O, seed):
     r = O.ots_sinkhorn_solve(h, tol=1e-8, max_iters=200000)
     assert r["src_residual"] <= 1e-8 and r["cap_violation"] <= 1e-8
     F = O.ots_get_flows(h)
-    assert rel_l1(F, o.flows()) <= FLOW_TOL
+    Fref = o.flows()
+    assert rel_l1(F, Fref) <= FLOW_TOL
+    assert_elementwise(F, Fref, "grid5x5")
+    lu, _, _ = O.ots_get_duals(h)
+    assert_duals_relative(lu, o.get_duals()[0], Fref, 1e-5, "grid5x5")
     O.ots_destroy_problem(h)
 
 
@@ -89,6 +113,21 @@ def test_capacitated_converged(O, L, eps, seed, lo, hi):
     P = O.ots_get_commodity_flows(h)
     Pref = o.projections()
     assert rel_l1(P, Pref) <= FLOW_TOL
+    # Entry by entry.  (1) Arithmetic: the oracle evaluates Theorem 6 at the GPU's own duals, so
+    # only the message arithmetic differs.  (2) The fixed point: at the stopping tolerance 1e-6 a
+    # low-flow entry can still be 2e-5 away from the optimum (convergence, not arithmetic), so the
+    # solve continues from its duals to 1e-8 first.
+    od = Oracle(inst)
+    od.set_duals(lu, *dense_duals(inst, U01, U0T))
+    e_ar = assert_elementwise(P, od.projections(), f"L={L} per commodity at the GPU's duals")
+    r8 = O.ots_sinkhorn_solve(h, tol=1e-8, max_iters=20000, warm_start=True)
+    assert r8["status"] == 0
+    F8, P8 = O.ots_get_flows(h), O.ots_get_commodity_flows(h)
+    e_agg = assert_elementwise(F8, Fref, f"L={L} aggregate")
+    e_com = assert_elementwise(P8, Pref, f"L={L} per commodity")
+    e_dual = assert_duals_relative(O.ots_get_duals(h)[0], logu_ref, Fref, 1e-5, f"L={L}")
+    print(f"capacitated L={L}: elementwise at duals {e_ar:.3g}, at 1e-8 {e_agg:.3g} / {e_com:.3g}, "
+          f"max dlog u {e_dual:.3g}")
     O.ots_destroy_problem(h)
 
 
@@ -128,9 +167,13 @@ def test_pipelined_rows_of_1024_commodities(O):
     h = O.ots_create_problem(inst)
     r = O.ots_sinkhorn_solve(h, tol=1e-7, max_iters=20000)
     assert r["status"] == 0
-    assert rel_l1(O.ots_get_flows(h), o.flows()) <= FLOW_TOL
+    F, Fref = O.ots_get_flows(h), o.flows()
+    assert rel_l1(F, Fref) <= FLOW_TOL
+    assert_elementwise(F, Fref, "L=1000 aggregate")
     P = O.ots_get_commodity_flows(h, 1, inst.T + 1, 990, 1000)
-    assert rel_l1(P, o.projections(990, 1000)) <= FLOW_TOL
+    Pref = o.projections(990, 1000)
+    assert rel_l1(P, Pref) <= FLOW_TOL
+    assert_elementwise(P, Pref, "L=1000 commodities 990..999")
 
 
 # ---------------------------------------------------------------------------------------
@@ -288,6 +331,37 @@ def test_checkpoint_resume_and_determinism(O):
     O.ots_set_duals(h4, *duals)
     O.ots_iterate(h4, 10, reset=False)
     assert rel_l1(O.ots_get_flows(h4), F20) <= 1e-6
+
+
+def test_flows_at_duals_loaded_from_the_oracle(O):
+    """Theorem 6 at duals the GPU did not produce: the oracle's iterate after three passes on a
+    traffic-like grid with binding capacities, loaded through ots_set_duals.  The boundary panels
+    are rebuilt from FP64 duals of ~1e4 bits; a remainder that once overflowed its 16-bit field
+    there (a float part exactly halfway between two grid points) cost whole commodities 1e-4 of
+    their flow at t >= 2.  Checked: every flow entry, every commodity's mass at every t, and a
+    shift of one commodity's U01 far below an FP32 ulp of log2 U01 moving its flows at every t."""
+    inst = I.grid_traffic_instance(seed=0, rows=30, cols=30, L=64, T=100, cap_lo=0.05, cap_hi=0.3)
+    o = Oracle(inst)
+    o.backward_sweep()
+    for _ in range(3):
+        o.iteration()
+    lu, a, b = o.get_duals()
+    U01, U0T = a[inst.src_comm, inst.src_state], b[inst.snk_comm, inst.snk_state]
+    h = O.ots_create_problem(inst)
+    O.ots_set_duals(h, lu, U01, U0T)
+    P, Pref = O.ots_get_commodity_flows(h), o.projections()
+    assert_elementwise(P, Pref, "per commodity at loaded duals")
+    np.testing.assert_allclose(P.sum(axis=2), Pref.sum(axis=2), rtol=1e-5)
+    m0 = P[1:3].sum(axis=2)                           # GPU masses at t = 2, 3 (read off A_1, A_2)
+    for l in range(inst.L):
+        k = int(np.where(inst.src_comm == l)[0][0])
+        for d in (1e-6, 3e-5):
+            U = U01.copy()
+            U[k] += d
+            O.ots_set_duals(h, lu, U, U0T)
+            m = O.ots_get_commodity_flows(h, 2, 4, l, l + 1).sum(axis=2)[:, 0]
+            np.testing.assert_allclose(np.log(m / m0[:, l]), d, atol=5e-7, err_msg=f"commodity {l}")
+    O.ots_destroy_problem(h)
 
 
 def test_solver_without_graph_and_with_cuda_allocator(O):
