@@ -74,6 +74,10 @@ def parse():
                     help="pass limit of the traffic-scale requests in the serving mix")
     ap.add_argument("--no-traffic-solve", action="store_true",
                     help="skip the full solve of the traffic-scale workload (epsilon continuation)")
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="with --impl reference: the oracle's update rate per pass on one core and on all cores "
+                         "for the four workloads, and its time to convergence on the grid and random-geometric "
+                         "workloads and on 8 sampled batch instances (host only, a few minutes)")
     ap.add_argument("--horizon", type=int, default=100,
                     help="T of the traffic-scale grid (100 = the benchmark workload; smaller values only "
                          "for profiling captures that must stay within a few GB)")
@@ -235,10 +239,81 @@ def cpu_baseline(inst, budget_s: float):
                       f"0..{l1 - 1} ({updates:.3e} updates, {dt:.1f} s, FP64 log domain)"}
 
 
+def oracle_timing(args):
+    """The FP64 oracle timed on the host: updates/s (2 (T-1) nnz(K) L per pass) on one core and
+    on every core, per workload, and time to marginal error <= tol from the initialisation on
+    the 5x5 grid, the n = 400 random geometric graph and 8 seeded samples of the batch (each
+    bounded to about a minute; a bound that ends the run first is reported as such).  The
+    traffic workload's pass is sampled (backward products on 16 commodities): a full pass takes
+    minutes on the host and convergence hours."""
+    from oracle.oracle import Oracle, get_threads, set_threads
+    from paper_2106_14485_gb300 import instances as I
+    cores = get_threads()
+    out = {"cores": cores, "per_pass": [], "to_convergence": []}
+
+    def pass_rate(inst, threads, passes=1):
+        set_threads(threads)
+        o = Oracle(inst)
+        o.backward_sweep()
+        t0 = time.perf_counter()
+        for _ in range(passes):
+            o.iteration()
+        dt = time.perf_counter() - t0
+        return passes * inst.n_updates_per_iteration() / dt, dt / passes
+
+    batch = I.uneven_rgg_batch(0, count=256, workers=min(16, os.cpu_count() or 1))
+    rng = np.random.default_rng(5)
+    sample = [batch[int(k)] for k in rng.choice(len(batch), 8, replace=False)]
+    for name, inst, passes in (("grid5x5 L=1 T=10", I.grid_single_commodity(0), 50), ("rgg400 L=64 T=50", I.rgg400(0), 2),
+                               ("batch sample (mean of 8)", None, 1)):
+        row = {"workload": name}
+        for threads, key in ((1, "one_core"), (cores, "all_cores")):
+            if inst is None:
+                rates = [pass_rate(x, threads)[0] for x in sample]
+                row[key + "_updates_per_s"] = float(np.mean(rates))
+            else:
+                row[key + "_updates_per_s"], row[key + "_s_per_pass"] = pass_rate(inst, threads, passes)
+        out["per_pass"].append(row)
+    traffic = workload(0, 100)
+    row = {"workload": "traffic grid100x100 L=1024 T=100 (sampled: backward products, 16 commodities)"}
+    for threads, key in ((1, "one_core"), (cores, "all_cores")):
+        set_threads(threads)
+        o = Oracle(traffic)
+        t0 = time.perf_counter()
+        o.sample_backward_products(3, 16)
+        dt = time.perf_counter() - t0
+        row[key + "_updates_per_s"] = 4 * o.nnz * 16 / dt
+        del o
+    out["per_pass"].append(row)
+    for name, inst in [("grid5x5 L=1 T=10", I.grid_single_commodity(0)), ("rgg400 L=64 T=50", I.rgg400(0))] + \
+                      [(x.name, x) for x in sample]:
+        # chunks of 20 passes, each continuing from the current duals, until tol or 60 s
+        threads = 1 if inst.n_updates_per_iteration() < 1e6 else cores   # tiny: threads only add overhead
+        set_threads(threads)
+        o = Oracle(inst)
+        passes, seconds, done, status = 0, 0.0, False, 0
+        while not done and seconds < 60.0:
+            r = o.solve(max_iters=20, tol=args.tol)
+            passes += r["iters"]
+            seconds += r["seconds"]
+            status = r["status"]
+            done = status == 0 and r["src_resid"] <= args.tol and r["cap_viol"] <= args.tol
+            if status != 0:
+                break
+        out["to_convergence"].append({"workload": name, "converged": bool(done), "passes": passes,
+                                      "seconds": seconds, "threads": threads, "status": status,
+                                      "bound": None if done else "60 s"})
+    set_threads(cores)
+    print(json.dumps({"impl": "reference", "oracle_timing": out}), flush=True)
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
+    if args.oracle_timing:
+        return oracle_timing(args)
     inst = workload(0, args.horizon)
     from oracle.oracle import Oracle, get_threads
     o = Oracle(inst)

@@ -54,7 +54,10 @@ typedef enum ots_status {
   OTS_ERR_OOM = 5,           /* device or host allocation failed */
   OTS_ERR_CUDA = 6,          /* a CUDA runtime call failed (see ots_last_error) */
   OTS_ERR_NUMERIC = 7,       /* a NaN appeared in the convergence measures */
-  OTS_PENDING = 8            /* batch / server: the instance has not finished yet */
+  OTS_PENDING = 8,           /* batch / server: the instance has not finished yet */
+  OTS_ERR_DEVICE_WAIT = 9    /* a bounded wait inside a pipelined step kernel gave up (its
+                                data did not arrive in time); the pass's results are invalid,
+                                the problem stays usable (reset the duals or load them again) */
 } ots_status;
 
 typedef struct ots_problem ots_problem;
@@ -239,6 +242,18 @@ ots_status ots_get_duals(ots_problem *p, double *log_u, double *log_U01, double 
  * be <= 0. */
 ots_status ots_set_duals(ots_problem *p, const double *log_u, const double *log_U01,
                          const double *log_U0T);
+
+/* Limit of the device-side waits of the pipelined step kernels (no counterpart in the paper:
+ * an execution safeguard).  Each wait on a shared-memory stage (an mbarrier) is tried at most
+ * `tries` times, each try suspending the waiting thread for up to 2 us; a wait that runs out
+ * makes the kernel finish its own work and return, and the pass reports OTS_ERR_DEVICE_WAIT.
+ * tries = 0 restores the default (2^20, about two seconds).  withhold_stage != 0 is a test
+ * switch: the consumers of every block never release their first stage, so the producer's
+ * next wait for it and the consumers' next wait for data run out; every copy that was
+ * started has been waited for by then, so none is left in flight.  Kernels that are not
+ * pipelined (narrow rows, per-commodity costs) have no such waits.  The next solve or
+ * iterate call rebuilds its pass graph.  OTS_ERR_INVALID_ARG for NULL or tries < 0. */
+ots_status ots_set_wait_limit(ots_problem *p, int32_t tries, int32_t withhold_stage);
 
 /* Sizes and counters of a created problem. */
 typedef struct ots_problem_stats {

@@ -123,6 +123,8 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   a.counter = p->d_counter;
   a.stats = p->d_stats;
   a.mode = mode;
+  a.wait_tries = p->wait_tries;
+  a.withhold_stage = p->withhold_stage;
   return a;
 }
 
@@ -377,6 +379,9 @@ ots_status read_report(ots_problem *p, ots_solve_report *rep) {
   rep->src_residual = p->h_report->src_resid_rel;
   rep->cap_violation = p->h_report->cap_viol_rel;
   rep->dual_objective = p->h_report->dual_objective;
+  // a wait that gave up adds 1e6 per thread, a vanishing boundary message 1 per triple
+  if (p->h_report->bad >= 1e6)
+    return fail(OTS_ERR_DEVICE_WAIT, "a bounded wait in a pipelined step kernel gave up (the pass is invalid)");
   if (p->h_report->bad > 0) return fail(OTS_ERR_INFEASIBLE, "a source or sink message vanished (infeasible instance)");
   if (std::isnan(rep->src_residual) || std::isnan(rep->cap_violation) || std::isnan(rep->dual_objective))
     return fail(OTS_ERR_NUMERIC, "NaN in the convergence measures");
@@ -542,6 +547,7 @@ const char *ots_status_string(ots_status s) {
     case OTS_ERR_CUDA: return "OTS_ERR_CUDA";
     case OTS_ERR_NUMERIC: return "OTS_ERR_NUMERIC";
     case OTS_PENDING: return "OTS_PENDING";
+    case OTS_ERR_DEVICE_WAIT: return "OTS_ERR_DEVICE_WAIT";
   }
   return "OTS_ERR_UNKNOWN";
 }
@@ -1529,6 +1535,18 @@ ots_status ots_set_duals(ots_problem *p, const double *log_u, const double *log_
   if (p->snk.n) OTS_CUDA(cudaMemcpyAsync(p->snk.d_tri_logU, zu.data(), sizeof(double) * p->snk.n, cudaMemcpyHostToDevice, p->stream));
   OTS_CUDA(cudaStreamSynchronize(p->stream));
   p->stale = true;
+  return OTS_OK;
+}
+
+ots_status ots_set_wait_limit(ots_problem *p, int32_t tries, int32_t withhold_stage) {
+  g_last_error.clear();
+  if (!p || tries < 0) return fail(OTS_ERR_INVALID_ARG, "NULL problem or negative tries");
+  p->wait_tries = tries == 0 ? (1u << 20) : (unsigned int)tries;
+  p->withhold_stage = withhold_stage != 0 ? 1 : 0;
+  if (p->pass_exec) {                               // the pass graph holds the old arguments
+    cudaGraphExecDestroy(p->pass_exec);
+    p->pass_exec = nullptr;
+  }
   return OTS_OK;
 }
 

@@ -113,6 +113,9 @@ struct StepArgs {
   const float2 *dc;           // [S][Lp] log2 D^(0,t) as float-float (x = +inf: none; log2 0 = kNeg)
   float *uc_t;                // [S][Lp] log2 U^(0,t) of row t (nullptr: no commodity capacities)
   int kl_shift;               // log2 K_L is read as kl * 2^-kl_shift (epsilon 2^kl_shift times larger)
+  unsigned int wait_tries;    // pipelined kernels: tries of each bounded mbarrier wait (each <= 2 us)
+  int withhold_stage;         // test switch: the consumers never release their first stage, so that the
+                              // bounded waits of the pipelined kernels run out (no copy stays in flight)
 };
 
 // Boundary kernels (sources, sinks): segments of (node, commodity) with their triples.

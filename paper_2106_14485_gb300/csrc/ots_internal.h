@@ -139,6 +139,8 @@ struct ots_problem {
   double eps = 1.0, mass = 0.0;
   QScale qs{};                                 // quantum of the message hi parts
   int pgrid_fwd = 0, pgrid_bwd = 0;            // grids of the pipelined persistent kernels (0 = not used)
+  unsigned int wait_tries = 1u << 20;          // tries of each bounded device wait (ots_set_wait_limit)
+  int withhold_stage = 0;                      // test switch of ots_set_wait_limit
   bool pc = false;
   bool member = false;                         // lives in a batch (see CreateOpts)
   bool tv = false;                             // time-varying costs: K_L rows per interval t

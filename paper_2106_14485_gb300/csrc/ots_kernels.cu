@@ -448,9 +448,9 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 
 // Bounded wait for phase `parity` of an mbarrier; false if it gave up.  Each try may suspend
 // the thread for up to 2 us (returning as soon as the phase completes), so a waiting warp
-// does not spin on the issue slots; 2^20 tries bound the wait to about two seconds.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < (1u << 20); ++i) {
+// does not spin on the issue slots; the default 2^20 tries bound the wait to about two seconds.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t tries) {
+  for (uint32_t i = 0; i < tries; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}\n"
@@ -593,7 +593,7 @@ __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, flo
       lm.w_lo = a.wout_lo_t[lm.outpos];
     }
     int ok = 1;
-    if (i >= NS && lane == 0) ok = mbar_wait(smem_u32(&empty[s]), ((i / NS) - 1) & 1) ? 1 : 0;
+    if (i >= NS && lane == 0) ok = mbar_wait(smem_u32(&empty[s]), ((i / NS) - 1) & 1, a.wait_tries) ? 1 : 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (!ok) { timed_out = true; return; }
     Meta &m = meta[s];
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_forward_tma(c
       for (int q = 0; q < 4; ++q) { M[c][q] = 2.f * kNeg; acc[c][q] = 0.f; }
     for (int i = 0;; ++i) {
       const int s = i % NS;
-      if (!mbar_wait(smem_u32(&full[s]), (i / NS) & 1)) { timed_out = true; break; }
+      if (!mbar_wait(smem_u32(&full[s]), (i / NS) & 1, a.wait_tries)) { timed_out = true; break; }
       const FwdMeta &m = meta[s];
       if (!m.valid) break;
       const int nb = m.nb;
@@ -897,7 +897,7 @@ __global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_forward_tma(c
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+      if (lane == 0 && !(a.withhold_stage && i == 0)) mbar_arrive(smem_u32(&empty[s]));
     }
   }
   if (timed_out) atomicAdd(&a.stats->bad, 1e6);
@@ -944,7 +944,7 @@ __global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_backward_tma(
       for (int q = 0; q < 4; ++q) { M[c][q] = 2.f * kNeg; acc[c][q] = 0.f; }
     for (int i = 0;; ++i) {
       const int s = i % NS;
-      if (!mbar_wait(smem_u32(&full[s]), (i / NS) & 1)) { timed_out = true; break; }
+      if (!mbar_wait(smem_u32(&full[s]), (i / NS) & 1, a.wait_tries)) { timed_out = true; break; }
       const BwdMeta &m = meta[s];
       if (!m.valid) break;
       const int nb = m.nb;
@@ -974,7 +974,7 @@ __global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_backward_tma(
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+      if (lane == 0 && !(a.withhold_stage && i == 0)) mbar_arrive(smem_u32(&empty[s]));
     }
   }
   if (timed_out) atomicAdd(&a.stats->bad, 1e6);

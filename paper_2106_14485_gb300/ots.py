@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libots.so")
 OTS_OK, OTS_ERR_INVALID_ARG, OTS_ERR_INFEASIBLE, OTS_ERR_NOT_CONVERGED = 0, 1, 2, 3
 OTS_ERR_TIMEOUT, OTS_ERR_OOM, OTS_ERR_CUDA, OTS_ERR_NUMERIC = 4, 5, 6, 7
 OTS_PENDING = 8
+OTS_ERR_DEVICE_WAIT = 9
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _f64p = ctypes.POINTER(ctypes.c_double)
@@ -95,7 +96,7 @@ class ServerStats(ctypes.Structure):
 
 EXPORTED = ["ots_default_solve_opts", "ots_create_problem", "ots_check_problem", "ots_sinkhorn_solve", "ots_iterate", "ots_get_flows",
             "ots_get_commodity_flows", "ots_get_commodity_flows_noalloc", "ots_get_duals", "ots_set_duals", "ots_problem_info", "ots_last_pass_timing",
-            "ots_problem_stream", "ots_destroy_problem", "ots_status_string", "ots_last_error",
+            "ots_set_wait_limit", "ots_problem_stream", "ots_destroy_problem", "ots_status_string", "ots_last_error",
             "ots_default_batch_desc", "ots_batch_create", "ots_batch_add", "ots_batch_run", "ots_batch_status",
             "ots_batch_get_flows", "ots_batch_get_duals", "ots_batch_remove", "ots_batch_info", "ots_batch_mapping",
             "ots_batch_autotune", "ots_batch_destroy",
@@ -125,6 +126,7 @@ def load_library(path: str = LIB_PATH):
                                                     ctypes.c_int32, _f64p]
     lib.ots_get_duals.argtypes = [P, _f64p, _f64p, _f64p]
     lib.ots_set_duals.argtypes = [P, _f64p, _f64p, _f64p]
+    lib.ots_set_wait_limit.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
     lib.ots_problem_info.argtypes = [P, ctypes.POINTER(ProblemStats)]
     lib.ots_last_pass_timing.argtypes = [P, _f64p]
     lib.ots_problem_stream.argtypes = [P]
@@ -170,7 +172,7 @@ def load_library(path: str = LIB_PATH):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("ots_default_solve_opts", "ots_create_problem", "ots_sinkhorn_solve", "ots_iterate",
                  "ots_get_flows", "ots_get_commodity_flows", "ots_get_commodity_flows_noalloc", "ots_get_duals", "ots_set_duals", "ots_problem_info",
-                 "ots_last_pass_timing"):
+                 "ots_last_pass_timing", "ots_set_wait_limit"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -386,6 +388,10 @@ def ots_set_duals(h: Handle, log_u, log_U01, log_U0T) -> None:
     uT = np.ascontiguousarray(log_U0T, np.float64)
     _check(load_library().ots_set_duals(h.ptr, _ptr(lu, ctypes.c_double), _ptr(u1, ctypes.c_double),
                                         _ptr(uT, ctypes.c_double)))
+
+
+def ots_set_wait_limit(h: Handle, tries: int = 0, withhold_stage: bool = False) -> None:
+    _check(load_library().ots_set_wait_limit(h.ptr, int(tries), int(bool(withhold_stage))))
 
 
 def ots_problem_info(h: Handle) -> dict:

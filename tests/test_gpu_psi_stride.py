@@ -54,3 +54,33 @@ def test_kept_every_k_solves_and_continues(O):
     assert np.array_equal(O.ots_get_commodity_flows_noalloc(h0), O.ots_get_commodity_flows_noalloc(h1))
     O.ots_destroy_problem(h0)
     O.ots_destroy_problem(h1)
+
+
+@pytest.mark.parametrize("L,k", [(9, 3), (300, 5)])
+def test_kept_every_k_against_the_oracle(O, L, k):
+    """Recomputed segments (stride k >= 3, horizon 24) against the FP64 oracle, not only against the
+    GPU's own full storage: iterates after 1 and 4 passes (flows and both measures) and the
+    converged flows, relative L1 <= 1e-5 and entry by entry."""
+    from oracle.oracle import Oracle
+    from tests.test_gpu_parity import assert_elementwise, rel_l1
+    inst = I.rgg_instance(seed=6, n=60, L=L, T=24, eps=0.03, cap_lo=0.3, cap_hi=1.0)
+    o = Oracle(inst)
+    o.backward_sweep()
+    h = O.ots_create_problem(inst, psi_stride=k)
+    done = 0
+    for target in (1, 4):
+        r = O.ots_iterate(h, target - done, reset=(done == 0))
+        for _ in range(target - done):
+            ro, co, _ = o.iteration()
+        done = target
+        assert rel_l1(O.ots_get_flows(h), o.flows()) <= 1e-5, target
+        assert abs(r["src_residual"] - ro) <= 1e-6 + 1e-4 * ro
+        assert abs(r["cap_violation"] - co) <= 1e-6 + 1e-4 * co
+    r = O.ots_sinkhorn_solve(h, tol=1e-8, max_iters=20000, warm_start=True)
+    assert r["status"] == 0
+    o2 = Oracle(inst)
+    assert o2.solve(max_iters=100000, tol=1e-11)["status"] == 0
+    F, Fref = O.ots_get_flows(h), o2.flows()
+    assert rel_l1(F, Fref) <= 1e-5
+    assert_elementwise(F, Fref, f"psi_stride {k}")
+    O.ots_destroy_problem(h)

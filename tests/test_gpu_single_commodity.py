@@ -3,7 +3,7 @@ node row), against the Algorithm 1 oracle: single-instance, batched and continua
 import numpy as np
 import pytest
 
-from oracle.single_commodity import algorithm1
+from oracle.single_commodity import cyclic_projections
 from paper_2106_14485_gb300 import instances as I
 from tests.test_single_commodity_pins import alg1_inputs
 
@@ -30,7 +30,7 @@ def rel_l1(a, b):
 @pytest.mark.parametrize("seed,rows,T", [(0, 6, 12), (1, 6, 12), (2, 16, 30)])
 def test_single_commodity_matches_algorithm1(O, seed, rows, T):
     inst = I.single_commodity_instance(seed=seed, rows=rows, cols=rows, T=T)
-    u, P, it, src, cap = algorithm1(*alg1_inputs(inst))
+    u, P, it, src, cap = cyclic_projections(*alg1_inputs(inst))
     assert src < 1e-12 and cap < 1e-12
     h = O.ots_create_problem(inst)
     r = O.ots_sinkhorn_solve(h, tol=1e-8, max_iters=100000)
@@ -44,7 +44,7 @@ def test_single_commodity_matches_algorithm1(O, seed, rows, T):
 
 def test_single_commodity_batched(O):
     insts = [I.single_commodity_instance(seed=s, rows=5 + s, cols=6, T=10 + s) for s in range(4)]
-    refs = [algorithm1(*alg1_inputs(x))[1][1:] for x in insts]
+    refs = [cyclic_projections(*alg1_inputs(x))[1][1:] for x in insts]
     b = O.ots_batch_create(pool_bytes=128 << 20, max_instances=8)
     ids = [O.ots_batch_add(b, x, tol=1e-8, max_iters=100000) for x in insts]
     assert O.ots_batch_run(b) == 0

@@ -60,3 +60,25 @@ def test_noalloc_rejects_requests_beyond_the_static_buffer(O):
     got = O.ots_get_commodity_flows_noalloc(h, 2, 3, 0, lmax)
     assert rel_l1(got, ref) <= 1e-12
     O.ots_destroy_problem(h)
+
+
+def test_noalloc_with_kept_panels_and_refusal_of_windows(O):
+    """Backward panels kept every 3rd t (the query recomputes the others segment by segment in
+    its problem's own memory): exactly the allocating query's values, which run the same
+    kernels.  Commodity windows are refused with OTS_ERR_INVALID_ARG before any device work."""
+    inst = I.rgg_instance(seed=14, n=60, L=8, T=16, eps=0.05, cap_lo=0.15, cap_hi=0.4)
+    h = O.ots_create_problem(inst, psi_stride=3)
+    O.ots_iterate(h, 5, reset=True)
+    for _ in range(2):
+        ref = O.ots_get_commodity_flows(h, 1, inst.T + 1, 1, 8)
+        got = O.ots_get_commodity_flows_noalloc(h, 1, inst.T + 1, 1, 8)
+        assert np.array_equal(got, ref)
+    O.ots_destroy_problem(h)
+    win = I.with_commodity_windows(I.rgg_instance(seed=5, n=60, L=9, T=14, eps=0.03, cap_lo=0.3, cap_hi=0.9),
+                                   seed=2, slack=2)
+    h = O.ots_create_problem(win)
+    O.ots_iterate(h, 1, reset=True)
+    with pytest.raises(O.OTSError) as e:
+        O.ots_get_commodity_flows_noalloc(h, 1, win.T + 1, 0, 2)
+    assert e.value.code == O.OTS_ERR_INVALID_ARG
+    O.ots_destroy_problem(h)
