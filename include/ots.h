@@ -134,6 +134,22 @@ typedef struct ots_problem_desc {
                                     per-commodity kernels (as commodity_cost does); not with
                                     state_cost_t, epsilon continuation or the batched solver.
                                     The reported dual objective leaves out the D term. */
+  const int32_t *state_tail;     /* optional [n_states]: an explicit state graph (Section 3.3:
+                                    storage on edges; the source and sink states of the
+                                    traffic-routing model, eq. cost_traffic_routing).  Tail node
+                                    of each state, -1 for none (no state leads into it); replaces
+                                    edge_src and the wait loops' nodes.  State j may follow state
+                                    i iff head(i) = tail(j) >= 0, or i = j when state_hold[i] = 1.
+                                    Given together with state_head. */
+  const int32_t *state_head;     /* optional [n_states]: head node of each state, -1 for none (it
+                                    leads to no state) */
+  const int32_t *state_hold;     /* optional [n_states] of 0 / 1: 1 = the state may follow itself
+                                    (storage; implied when head = tail >= 0, e.g. a wait loop).
+                                    Each such state with head != tail gets one message row of its
+                                    own.  Runs on the register kernels; not with per-commodity costs
+                                    or capacities, commodity windows, psi_stride > 1 or the batched
+                                    solver (OTS_ERR_INVALID_ARG).  Feasibility is checked on the
+                                    states (exact walks of T-1 transitions). */
 } ots_problem_desc;
 
 /* Options of ots_sinkhorn_solve. */

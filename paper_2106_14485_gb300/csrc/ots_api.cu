@@ -125,6 +125,7 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   a.mode = mode;
   a.wait_tries = p->wait_tries;
   a.withhold_stage = p->withhold_stage;
+  a.fixed_w = p->d_fixed_w;
   return a;
 }
 
@@ -139,6 +140,7 @@ BndArgs bnd_args(ots_problem *p, bool source, int mode, int g) {
   int s0 = 0, s1 = b.n_seg, t = source ? 1 : p->T;
   if (g >= 0) { s0 = b.grp_seg[g]; s1 = b.grp_seg[g + 1]; t = b.grp_t[g]; }
   BndArgs a{};
+  a.skip_node = p->null_row;                   // -1 unless the state graph is explicit
   a.n_seg = s1 - s0;
   a.qs = p->qs;
   a.seg_ptr = b.d_seg_ptr + s0; a.seg_node = b.d_seg_node + s0; a.seg_l = b.d_seg_l + s0;
@@ -163,10 +165,81 @@ BndArgs bnd_args(ots_problem *p, bool source, int mode) { return bnd_args(p, sou
 
 int n_groups(const Boundary &b) { return (int)b.grp_t.size(); }
 
+// ---- storage states of an explicit state graph (one row each, see StoreRowArgs) ----
+StoreRowArgs store_rows(ots_problem *p, bool fwd, int t, bool boundary) {
+  StoreRowArgs a{};
+  a.n = p->nstore; a.Lp = p->Lp; a.row0 = p->V; a.qs = p->qs;
+  a.state = p->d_store_state;
+  a.node = fwd ? p->d_store_tail : p->d_store_head;
+  a.p_hi = fwd ? p->a_hi(t) : p->b_hi(t);
+  a.p_lo = fwd ? p->a_lo(t) : p->b_lo(t);
+  if (!boundary) {
+    a.q_hi = fwd ? p->a_hi(t - 1) : p->b_hi(t + 1);
+    a.q_lo = fwd ? p->a_lo(t - 1) : p->b_lo(t + 1);
+    a.w_hi = p->d_w_hi + (size_t)t * p->S;
+    a.w_lo = p->d_w_lo + (size_t)t * p->S;
+  }
+  return a;
+}
+
+// The storage rows of A_1 (sources) or B_T (sinks) once its node rows are written: the row of the
+// state's tail (head), then (+) log2 U of the boundary triples on the state itself.
+cudaError_t store_boundary(ots_problem *p, bool source) {
+  if (!p->nstore) return cudaSuccess;
+  cudaError_t e = launch_store_rows(store_rows(p, source, source ? 1 : p->T, true), p->stream);
+  if (e != cudaSuccess) return e;
+  const int n = (int)(source ? p->sst_k.size() : p->zst_k.size());
+  if (n == 0) return cudaSuccess;
+  StoreTriArgs a{};
+  const int *d = source ? p->d_sst : p->d_zst;
+  a.n = n; a.Lp = p->Lp; a.row0 = p->V; a.qs = p->qs;
+  a.k = d; a.l = d + n; a.q = d + 2 * n;
+  a.tri_logU = (source ? p->src : p->snk).d_tri_logU;
+  a.p_hi = source ? p->a_hi(1) : p->b_hi(p->T);
+  a.p_lo = source ? p->a_lo(1) : p->b_lo(p->T);
+  return launch_store_triples(a, p->stream);
+}
+
+// Forward step t (mode 0: update, 1: flows): the storage states' own capacity update first (the
+// step reads their W_t back), then the node rows, then the storage rows of A_t.
+cudaError_t forward_step(ots_problem *p, int t, int mode) {
+  if (p->nstore) {
+    StepArgs a = step_args(p, true, t, mode);
+    a.fixed_w = nullptr;
+    StoreUpdArgs u{};
+    u.n = p->nstore; u.Lp = p->Lp; u.row0 = p->V; u.state = p->d_store_state;
+    u.x_hi = p->a_hi(t - 1); u.x_lo = p->a_lo(t - 1);
+    u.y_hi = p->b_hi(t + 1); u.y_lo = p->b_lo(t + 1);
+    cudaError_t e = launch_store_update(a, u, p->max_grid, p->stream);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, mode), p->stream);
+  if (e != cudaSuccess || !p->nstore) return e;
+  return launch_store_rows(store_rows(p, true, t, false), p->stream);
+}
+
+// Backward step t: the node rows of B_t, then its storage rows.
+cudaError_t backward_step(ots_problem *p, int t) {
+  cudaError_t e = launch_step(false, p->pc, p->G, p->C, step_args(p, false, t, 0), p->stream);
+  if (e != cudaSuccess || !p->nstore) return e;
+  return launch_store_rows(store_rows(p, false, t, false), p->stream);
+}
+
+// Kernels a storage state graph adds to a pass (update and rows per forward step, rows per
+// backward step, rows and triples at each boundary).
+long long store_kernels_per_pass(const ots_problem *p) {
+  if (!p->nstore) return 0;
+  return 3LL * (p->T - 2) + 2 + (p->sst_k.empty() ? 0 : 1) + (p->zst_k.empty() ? 0 : 1);
+}
+
 // Panels of the first sweep step: A_1 from the sources entering at t = 1 (all of them
 // without windows), B_T from the sinks leaving at T.
 cudaError_t launch_boundary_rebuild(ots_problem *p, bool source) {
-  if (!p->win) return launch_boundary(bnd_args(p, source, 1), p->stream);
+  if (!p->win) {
+    cudaError_t e = launch_boundary(bnd_args(p, source, 1), p->stream);
+    if (e != cudaSuccess) return e;
+    return store_boundary(p, source);
+  }
   const Boundary &b = source ? p->src : p->snk;
   const int t0 = source ? 1 : p->T;
   for (int g = 0; g < n_groups(b); ++g)
@@ -216,7 +289,11 @@ cudaError_t after_backward_step(ots_problem *p, int t) {
 
 // Source update at the start of a pass (mode 0): every group reads its own Psi_t.
 cudaError_t launch_source_update(ots_problem *p) {
-  if (!p->win) return launch_boundary(bnd_args(p, true, 0), p->stream);
+  if (!p->win) {
+    cudaError_t e = launch_boundary(bnd_args(p, true, 0), p->stream);
+    if (e != cudaSuccess) return e;
+    return store_boundary(p, true);
+  }
   for (int g = 0; g < n_groups(p->src); ++g) {
     cudaError_t e = launch_boundary(bnd_args(p, true, 0, g), p->stream);
     if (e != cudaSuccess) return e;
@@ -226,7 +303,11 @@ cudaError_t launch_source_update(ots_problem *p) {
 
 // Sink update after the forward sweep (mode 0): the sinks leaving at T.
 cudaError_t launch_sink_update(ots_problem *p) {
-  if (!p->win) return launch_boundary(bnd_args(p, false, 0), p->stream);
+  if (!p->win) {
+    cudaError_t e = launch_boundary(bnd_args(p, false, 0), p->stream);
+    if (e != cudaSuccess) return e;
+    return store_boundary(p, false);
+  }
   for (int g = 0; g < n_groups(p->snk); ++g)
     if (p->snk.grp_t[g] == p->T) return launch_boundary(bnd_args(p, false, 0, g), p->stream);
   return cudaSuccess;
@@ -260,7 +341,7 @@ cudaError_t launch_boundary_flows_all(ots_problem *p) {
 ots_status enqueue_backward_sweep(ots_problem *p) {
   OTS_CUDA(launch_boundary_rebuild(p, false));
   for (int t = p->T - 1; t >= 2; --t) {
-    OTS_CUDA(launch_step(false, p->pc, p->G, p->C, step_args(p, false, t, 0), p->stream));
+    OTS_CUDA(backward_step(p, t));
     OTS_CUDA(after_backward_step(p, t));
   }
   p->kernels_launched += p->T - 1;
@@ -282,7 +363,7 @@ cudaError_t enqueue_segment(ots_problem *p, int t) {
   return cudaSuccess;
 }
 
-long long kernels_per_pass(const ots_problem *p) { return 2LL * p->T + p->b_recompute; }
+long long kernels_per_pass(const ots_problem *p) { return 2LL * p->T + p->b_recompute + store_kernels_per_pass(p); }
 
 // One pass of the while loop of Algorithm 2 (enqueued directly or captured into a graph),
 // with phase events around the source update, the forward sweep, the sink update and the
@@ -296,14 +377,14 @@ ots_status enqueue_pass(ots_problem *p, bool capture) {
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[1], p->stream, flags));
   for (int t = 2; t <= p->T - 1; ++t) {                                        // u_t, hatPsi_{t+1}
     OTS_CUDA(enqueue_segment(p, t));
-    OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 0), p->stream));
+    OTS_CUDA(forward_step(p, t, 0));
     OTS_CUDA(after_forward_step(p, t, false));
   }
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[2], p->stream, flags));
   OTS_CUDA(launch_sink_update(p));                                             // U0T, Psi_{T-1}
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[3], p->stream, flags));
   for (int t = p->T - 1; t >= 2; --t) {                                        // Psi_{t-1}
-    OTS_CUDA(launch_step(false, p->pc, p->G, p->C, step_args(p, false, t, 0), p->stream));
+    OTS_CUDA(backward_step(p, t));
     OTS_CUDA(after_backward_step(p, t));
   }
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[4], p->stream, flags));
@@ -335,6 +416,10 @@ ots_status reset_duals(ots_problem *p) {
   if (p->src.n) OTS_CUDA(cudaMemsetAsync(p->src.d_tri_logU, 0, sizeof(double) * p->src.n, p->stream));
   if (p->snk.n) OTS_CUDA(cudaMemsetAsync(p->snk.d_tri_logU, 0, sizeof(double) * p->snk.n, p->stream));
   if (p->d_uc) OTS_CUDA(cudaMemsetAsync(p->d_uc, 0, sizeof(float) * (size_t)(p->T + 1) * p->S * p->Lp, p->stream));
+  // column references of the pipelined forward step are dropped too (NaN: none), so that a
+  // reset problem repeats a fresh one bit for bit whatever ran on it before
+  if (p->d_cref_in)
+    OTS_CUDA(cudaMemsetAsync(p->d_cref_in, 0xff, sizeof(float) * (size_t)(p->T + 1) * p->S, p->stream));
   OTS_CUDA(cudaMemsetAsync(p->d_report, 0, sizeof(PassReport), p->stream));
   OTS_CUDA(launch_boundary_rebuild(p, true));
   ots_status st = enqueue_backward_sweep(p);
@@ -448,6 +533,68 @@ bool feasible(ots_problem *p, const std::vector<int> &eptr, const std::vector<in
   return true;
 }
 
+// Explicit state graphs (storage states, states without a tail or head): the same necessary
+// condition on exact walks, without the hop-distance shortcut (waiting is possible only where
+// a state may follow itself).  Layered reachability over the states: after a state s comes every
+// state j with tail(j) = head(s) >= 0, and s itself when it may follow itself (a storage flag, or
+// head(s) = tail(s)); a state with capacity 0 in every interval is closed in the interior layers.
+bool feasible_states(ots_problem *p, const std::vector<int> &hold, const std::vector<double> &cap, std::string &why) {
+  const int S = p->S, T = p->T;
+  std::vector<char> open(S, 0);
+  for (int s = 0; s < S; ++s) {
+    if (!p->cv) open[s] = cap[s] > 0.0;
+    else
+      for (int t = 2; t <= T - 1; ++t) open[s] |= cap[(size_t)t * S + s] > 0.0;
+  }
+  std::vector<std::vector<int>> leaving(p->V);
+  for (int s = 0; s < S; ++s)
+    if (p->tail[s] >= 0) leaving[p->tail[s]].push_back(s);
+  auto reach = [&](int s0) {                      // states reachable from s0 in exactly T-1 steps
+    std::vector<char> cur(S, 0), nxt(S, 0);
+    cur[s0] = 1;
+    for (int step = 1; step <= T - 1; ++step) {
+      std::fill(nxt.begin(), nxt.end(), 0);
+      const bool last = step == T - 1;
+      for (int s = 0; s < S; ++s) {
+        if (!cur[s]) continue;
+        if ((hold[s] || (p->head[s] >= 0 && p->head[s] == p->tail[s])) && (last || open[s])) nxt[s] = 1;
+        if (p->head[s] >= 0)
+          for (int j : leaving[p->head[s]])
+            if (last || open[j]) nxt[j] = 1;
+      }
+      cur.swap(nxt);
+    }
+    return cur;
+  };
+  std::vector<std::vector<int>> src_by_l(p->L), snk_by_l(p->L);
+  for (int q = 0; q < p->src.n; ++q) src_by_l[p->src.tri_l[q]].push_back(q);
+  for (int q = 0; q < p->snk.n; ++q) snk_by_l[p->snk.tri_l[q]].push_back(q);
+  char buf[160];
+  for (int l = 0; l < p->L; ++l) {
+    std::vector<char> hit(snk_by_l[l].size(), 0);
+    for (int qs : src_by_l[l]) {
+      const std::vector<char> r = reach(p->src.tri_state[qs]);
+      bool any = false;
+      for (size_t k = 0; k < snk_by_l[l].size(); ++k)
+        if (r[p->snk.tri_state[snk_by_l[l][k]]]) { any = true; hit[k] = 1; }
+      if (!any) {
+        snprintf(buf, sizeof(buf), "commodity %d: source state %d reaches no sink in T-1 transitions", l,
+                 p->src.tri_state[qs]);
+        why = buf;
+        return false;
+      }
+    }
+    for (size_t k = 0; k < hit.size(); ++k)
+      if (!hit[k]) {
+        snprintf(buf, sizeof(buf), "commodity %d: sink state %d is reached by no source in T-1 transitions", l,
+                 p->snk.tri_state[snk_by_l[l][k]]);
+        why = buf;
+        return false;
+      }
+  }
+  return true;
+}
+
 ots_status build_boundary(ots_problem *p, Boundary &b, int n, const int32_t *comm, const int32_t *state,
                           const double *mass, bool source) {
   std::map<std::pair<int, int>, int> uniq;  // (l, state) -> unique index
@@ -476,7 +623,10 @@ ots_status build_boundary(ots_problem *p, Boundary &b, int n, const int32_t *com
   const int nu = (int)keys.size();
   std::vector<int> order(nu);
   for (int k = 0; k < nu; ++k) order[k] = k;
-  auto seg_node_of = [&](int k) { return source ? p->head[keys[k].second] : p->tail[keys[k].second]; };
+  auto seg_node_of = [&](int k) {   // the node row the boundary panel entry goes to (log-0 row: none)
+    const int v = source ? p->head[keys[k].second] : p->tail[keys[k].second];
+    return v >= 0 ? v : p->null_row;
+  };
   auto time_of = [&](int l) { return source ? p->ta[l] : p->tb[l]; };
   std::sort(order.begin(), order.end(), [&](int a, int c) {
     const int ta = time_of(keys[a].first), tc = time_of(keys[c].first);
@@ -496,8 +646,9 @@ ots_status build_boundary(ots_problem *p, Boundary &b, int n, const int32_t *com
     int u = order[k];
     b.tri_l[k] = keys[u].first;
     b.tri_state[k] = keys[u].second;
-    // message row read at the boundary: Psi_1 = B_2[head(i)] for sources, hatPsi_T = A_{T-1}[tail(j)] for sinks
-    b.tri_other[k] = source ? p->head[keys[u].second] : p->tail[keys[u].second];
+    // message row read at the boundary: Psi_1 = B_2[head(i)] for sources, hatPsi_T = A_{T-1}[tail(j)]
+    // for sinks (a storage state's own row, or the log-0 row without head / tail)
+    b.tri_other[k] = source ? p->brow[keys[u].second] : p->frow[keys[u].second];
     b.tri_R[k] = R[u];
     int node = seg_node_of(u);
     if (k == 0 || node != b.seg_node.back() || keys[u].first != b.seg_l.back()) {
@@ -620,6 +771,7 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   p->free_fn = d->free_fn;
   p->actx = d->alloc_ctx;
   p->V = d->n_nodes;
+  p->rows = p->V;
   p->E = d->n_edges;
   p->S = d->n_edges + (d->add_wait_loops ? d->n_nodes : 0);
   p->L = d->L;
@@ -676,17 +828,68 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   if (d->add_wait_loops)
     for (int v = 0; v < p->V; ++v) { p->tail[p->E + v] = v; p->head[p->E + v] = v; }
 
+  // ---- explicit state graph (Section 3.3: storage on edges, the traffic-routing model) ----
+  std::vector<int> hold(p->S, 0);
+  if (d->state_tail || d->state_head || d->state_hold) {
+    if (!d->state_tail || !d->state_head) return bail(fail(OTS_ERR_INVALID_ARG, "state_tail and state_head go together"));
+    for (int s = 0; s < p->S; ++s) {
+      const int tl = d->state_tail[s], hd = d->state_head[s], h = d->state_hold ? d->state_hold[s] : 0;
+      if (tl < -1 || tl >= p->V || hd < -1 || hd >= p->V)
+        return bail(fail(OTS_ERR_INVALID_ARG, "state %d: tail / head must be -1 or a node", s));
+      if (h != 0 && h != 1) return bail(fail(OTS_ERR_INVALID_ARG, "state %d: state_hold must be 0 or 1", s));
+      p->tail[s] = tl;
+      p->head[s] = hd;
+      hold[s] = h;
+    }
+    p->xgraph = true;
+  }
+  if (p->xgraph) {
+    if (co.member) return bail(fail(OTS_ERR_INVALID_ARG, "the batched solver takes no explicit state graph"));
+    if (p->pc) return bail(fail(OTS_ERR_INVALID_ARG, "an explicit state graph does not combine with per-commodity costs or capacities"));
+    if (p->bk > 1) return bail(fail(OTS_ERR_INVALID_ARG, "an explicit state graph needs psi_stride <= 1"));
+    if (d->commodity_t_in || d->commodity_t_out)
+      return bail(fail(OTS_ERR_INVALID_ARG, "an explicit state graph does not combine with commodity windows"));
+    // a state that may follow itself other than through its own node needs a row of its own
+    for (int s = 0; s < p->S; ++s)
+      if (hold[s] && !(p->head[s] >= 0 && p->head[s] == p->tail[s])) {
+        p->store_state.push_back(s);
+        p->store_tail.push_back(p->tail[s]);
+        p->store_head.push_back(p->head[s]);
+      }
+    p->nstore = (int)p->store_state.size();
+    p->null_row = p->V + p->nstore;
+    p->rows = p->V + p->nstore + 1;
+  }
+  // message rows gathered for each state: its tail's (forward) / head's (backward) node row, its
+  // own row when it is a storage state, the log-0 row when it has no tail / head
+  p->frow.resize(p->S);
+  p->brow.resize(p->S);
+  {
+    std::vector<int> sidx(p->S, -1);
+    for (int k = 0; k < p->nstore; ++k) sidx[p->store_state[k]] = k;
+    for (int s = 0; s < p->S; ++s) {
+      p->frow[s] = sidx[s] >= 0 ? p->V + sidx[s] : (p->tail[s] >= 0 ? p->tail[s] : p->null_row);
+      p->brow[s] = sidx[s] >= 0 ? p->V + sidx[s] : (p->head[s] >= 0 ? p->head[s] : p->null_row);
+    }
+  }
+
   std::vector<int> in_ptr(p->V + 1, 0), out_ptr(p->V + 1, 0);
-  for (int s = 0; s < p->S; ++s) { in_ptr[p->head[s] + 1]++; out_ptr[p->tail[s] + 1]++; }
+  for (int s = 0; s < p->S; ++s) {
+    if (p->head[s] >= 0) in_ptr[p->head[s] + 1]++;
+    if (p->tail[s] >= 0) out_ptr[p->tail[s] + 1]++;
+  }
   for (int v = 0; v < p->V; ++v) { in_ptr[v + 1] += in_ptr[v]; out_ptr[v + 1] += out_ptr[v]; }
+  // in_state / out_state list every state once: the node lists first, then (explicit graphs)
+  // the states with no head / tail, which no node gathers
   std::vector<int> in_state(p->S), in_nbr(p->S), out_state(p->S), out_nbr(p->S);
   {
     std::vector<int> fi(in_ptr.begin(), in_ptr.end() - 1), fo(out_ptr.begin(), out_ptr.end() - 1);
+    int xi = in_ptr[p->V], xo = out_ptr[p->V];
     for (int s = 0; s < p->S; ++s) {
-      int k = fi[p->head[s]]++;
-      in_state[k] = s; in_nbr[k] = p->tail[s];
-      k = fo[p->tail[s]]++;
-      out_state[k] = s; out_nbr[k] = p->head[s];
+      int k = p->head[s] >= 0 ? fi[p->head[s]]++ : xi++;
+      in_state[k] = s; in_nbr[k] = p->frow[s];
+      k = p->tail[s] >= 0 ? fo[p->tail[s]]++ : xo++;
+      out_state[k] = s; out_nbr[k] = p->brow[s];
     }
   }
   // node adjacency for the feasibility BFS (edges with positive capacity)
@@ -699,7 +902,7 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
         cap = 0.0;
         for (int t = 2; t <= p->T - 1; ++t) cap = std::max(cap, d->state_capacity_t[(size_t)(t - 2) * (p->E + p->V) + e]);
       }
-      if (cap > 0.0 && p->tail[e] != p->head[e]) adj[p->tail[e]].push_back(p->head[e]);
+      if (cap > 0.0 && p->tail[e] >= 0 && p->head[e] >= 0 && p->tail[e] != p->head[e]) adj[p->tail[e]].push_back(p->head[e]);
     }
     for (int v = 0; v < p->V; ++v) { eptr[v + 1] = eptr[v] + (int)adj[v].size(); enbr.insert(enbr.end(), adj[v].begin(), adj[v].end()); }
   }
@@ -842,6 +1045,18 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   if (st) return bail(st);
   st = build_boundary(p, p->snk, d->n_sinks, d->snk_commodity, d->snk_state, d->snk_mass, false);
   if (st) return bail(st);
+  if (p->nstore) {                               // boundary triples on storage states
+    std::vector<int> sidx(p->S, -1);
+    for (int k = 0; k < p->nstore; ++k) sidx[p->store_state[k]] = k;
+    for (int q = 0; q < p->src.n; ++q)
+      if (sidx[p->src.tri_state[q]] >= 0) {
+        p->sst_k.push_back(sidx[p->src.tri_state[q]]); p->sst_l.push_back(p->src.tri_l[q]); p->sst_q.push_back(q);
+      }
+    for (int q = 0; q < p->snk.n; ++q)
+      if (sidx[p->snk.tri_state[q]] >= 0) {
+        p->zst_k.push_back(sidx[p->snk.tri_state[q]]); p->zst_l.push_back(p->snk.tri_l[q]); p->zst_q.push_back(q);
+      }
+  }
   {
     std::vector<double> ms(p->L, 0.0), mz(p->L, 0.0);
     for (int q = 0; q < p->src.n; ++q) ms[p->src.tri_l[q]] += p->src.tri_R[q];
@@ -857,7 +1072,8 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
   }
   {
     std::string why;
-    if (!feasible(p, eptr, enbr, why)) return bail(fail(OTS_ERR_INFEASIBLE, "%s", why.c_str()));
+    if (p->xgraph ? !feasible_states(p, hold, cap, why) : !feasible(p, eptr, enbr, why))
+      return bail(fail(OTS_ERR_INFEASIBLE, "%s", why.c_str()));
   }
 
   p->stream = (cudaStream_t)d->stream;          // NULL: the device step creates one
@@ -946,6 +1162,7 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
     if (cudaMallocHost(&p->h_report, sizeof(PassReport)) != cudaSuccess) return bail(fail(OTS_ERR_OOM, "pinned alloc failed"));
     cudaError_t e = prepare_step_kernels(p->G, p->C, p->pc, p->V, &p->pgrid_fwd, &p->pgrid_bwd);
     if (e != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(e)));
+    if (p->xgraph) p->pgrid_fwd = p->pgrid_bwd = 0;   // explicit graphs run on the register kernels
     for (int k = 0; k < 5; ++k)
       if (cudaEventCreate(&p->ev[k]) != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "event creation failed"));
   }
@@ -954,6 +1171,7 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   const size_t S = p->S, V = p->V, T = p->T, panel = p->panel();
   const int max_grid = std::max(std::max(step_grid(p->V, p->G), boundary_grid(p->src.n_seg)),
                                 std::max(boundary_grid(p->snk.n_seg), 1));
+  p->max_grid = max_grid;
   Carver cv;
   size_t o_in_ptr = cv.take<int>(V + 1), o_in_state = cv.take<int>(S), o_in_nbr = cv.take<int>(S);
   size_t o_out_ptr = cv.take<int>(V + 1), o_out_state = cv.take<int>(S), o_out_nbr = cv.take<int>(S);
@@ -976,6 +1194,9 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   size_t o_a_hi[3], o_a_lo[3];
   for (int k = 0; k < 3; ++k) { o_a_hi[k] = cv.take<float>(panel); o_a_lo[k] = cv.take<lo_t>(panel); }
   size_t o_b_hi = cv.take<float>((size_t)p->nbslots * panel), o_b_lo = cv.take<lo_t>((size_t)p->nbslots * panel);
+  const size_t NS = p->nstore;
+  size_t o_store = cv.take<int>(3 * NS), o_fixed = cv.take<unsigned char>(NS ? S : 0);
+  size_t o_sst = cv.take<int>(3 * p->sst_k.size()), o_zst = cv.take<int>(3 * p->zst_k.size());
   size_t o_stats = cv.take<DevStats>(1), o_report = cv.take<PassReport>(1);
   size_t o_partials = cv.take<double>(3 * (size_t)max_grid), o_counter = cv.take<unsigned int>(4);
   struct BOff { size_t seg_ptr, seg_node, seg_l, other, l, R, logR, logU, flow; } bo[2];
@@ -1012,6 +1233,14 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   }
   for (int k = 0; k < 3; ++k) { p->d_a_hi[k] = (float *)at(o_a_hi[k]); p->d_a_lo[k] = (lo_t *)at(o_a_lo[k]); }
   p->d_b_hi = (float *)at(o_b_hi); p->d_b_lo = (lo_t *)at(o_b_lo);
+  if (NS) {
+    p->d_store_state = (int *)at(o_store);
+    p->d_store_tail = p->d_store_state + NS;
+    p->d_store_head = p->d_store_state + 2 * NS;
+    p->d_fixed_w = (unsigned char *)at(o_fixed);
+    if (!p->sst_k.empty()) p->d_sst = (int *)at(o_sst);
+    if (!p->zst_k.empty()) p->d_zst = (int *)at(o_zst);
+  }
   p->d_stats = (DevStats *)at(o_stats); p->d_report = (PassReport *)at(o_report);
   p->d_partials = (double *)at(o_partials); p->d_counter = (unsigned int *)at(o_counter);
   for (int k = 0; k < 2; ++k) {
@@ -1031,7 +1260,23 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   if (up(dst, vec.data(), vec.size() * sizeof(vec[0])) != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "upload " #vec))
   UP(p->d_in_ptr, in_ptr); UP(p->d_in_state, in_state); UP(p->d_in_nbr, in_nbr);
   UP(p->d_out_ptr, out_ptr); UP(p->d_out_state, out_state); UP(p->d_out_nbr, out_nbr);
-  UP(p->d_tail, p->tail); UP(p->d_head, p->head);
+  UP(p->d_tail, p->frow); UP(p->d_head, p->brow);     // rows gathered for each state (flow queries)
+  std::vector<int> stv, sst, zst;                      // kept until the end: the copies are asynchronous
+  std::vector<unsigned char> fixed;
+  if (NS) {
+    stv = p->store_state;
+    stv.insert(stv.end(), p->store_tail.begin(), p->store_tail.end());
+    stv.insert(stv.end(), p->store_head.begin(), p->store_head.end());
+    fixed.assign(S, 0);
+    for (int s : p->store_state) fixed[s] = 1;
+    sst = p->sst_k;
+    zst = p->zst_k;
+    sst.insert(sst.end(), p->sst_l.begin(), p->sst_l.end()); sst.insert(sst.end(), p->sst_q.begin(), p->sst_q.end());
+    zst.insert(zst.end(), p->zst_l.begin(), p->zst_l.end()); zst.insert(zst.end(), p->zst_q.begin(), p->zst_q.end());
+    UP(p->d_store_state, stv); UP(p->d_fixed_w, fixed);
+    if (p->d_sst) UP(p->d_sst, sst);
+    if (p->d_zst) UP(p->d_zst, zst);
+  }
   UP(p->d_kl_hi, kl_hi); UP(p->d_kl_lo, kl_lo); UP(p->d_logd_hi, logd_hi); UP(p->d_logd_lo, logd_lo);
   UP(p->d_cap, cap);
   if (csr_copies) {
@@ -1066,6 +1311,14 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   if (launch_fill_panel(panel, p->a_hi(1), p->a_lo(1), p->stream) != cudaSuccess ||
       launch_fill_panel(panel, p->b_hi(p->T), p->b_lo(p->T), p->stream) != cudaSuccess)
     return bail(fail(OTS_ERR_CUDA, "panel fill failed"));
+  if (p->xgraph) {
+    // every panel: the log-0 row is never written, and storage rows are read before their first write
+    bool ok = true;
+    for (int k = 0; k < 3; ++k) ok &= launch_fill_panel(panel, p->d_a_hi[k], p->d_a_lo[k], p->stream) == cudaSuccess;
+    ok &= launch_fill_panel((size_t)p->nbslots * panel, p->d_b_hi, p->d_b_lo, p->stream) == cudaSuccess;
+    if (!ok) return bail(fail(OTS_ERR_CUDA, "panel fill failed"));
+    p->kernels_launched += 4;
+  }
   st = reset_duals(p);
   if (st) return bail(st);
   if (cudaStreamSynchronize(p->stream) != cudaSuccess) return bail(fail(OTS_ERR_CUDA, "%s", cudaGetErrorString(cudaGetLastError())));
@@ -1262,7 +1515,7 @@ static ots_status flows_pass(ots_problem *p) {
   OTS_CUDA(launch_boundary_rebuild(p, true));
   for (int t = 2; t <= p->T - 1; ++t) {
     OTS_CUDA(enqueue_segment(p, t));
-    OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
+    OTS_CUDA(forward_step(p, t, 1));
     OTS_CUDA(after_forward_step(p, t, true));
   }
   OTS_CUDA(launch_boundary_flows_all(p));
@@ -1335,7 +1588,7 @@ ots_status ots_get_commodity_flows(ots_problem *p, int32_t t_begin, int32_t t_en
                             p->stream));
       check(cudaStreamSynchronize(p->stream));
     }
-    check(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
+    check(forward_step(p, t, 1));
     check(after_forward_step(p, t, true));
   }
   check(launch_boundary_flows_all(p));
@@ -1453,7 +1706,7 @@ ots_status ots_get_commodity_flows_noalloc(ots_problem *p, int32_t t_begin, int3
       p->kernels_launched += 1;
       p->d2h_bytes += (long long)(sizeof(double) * blk);
     }
-    OTS_CUDA(launch_step(true, p->pc, p->G, p->C, step_args(p, true, t, 1), p->stream));
+    OTS_CUDA(forward_step(p, t, 1));
     OTS_CUDA(after_forward_step(p, t, true));
   }
   OTS_CUDA(launch_boundary_flows_all(p));

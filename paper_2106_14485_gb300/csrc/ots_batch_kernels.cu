@@ -93,6 +93,7 @@ __device__ __forceinline__ StepArgs step_of(const BatchInst &I, bool fwd, int t,
 __device__ __forceinline__ BndArgs bnd_of(const BatchInst &I, bool source, int mode) {
   const BndSide &s = source ? I.src : I.snk;
   BndArgs b{};
+  b.skip_node = -1;
   b.n_seg = s.n_seg;
   b.qs = I.qs;
   b.seg_ptr = s.seg_ptr; b.seg_node = s.seg_node; b.seg_l = s.seg_l;

@@ -113,9 +113,48 @@ struct StepArgs {
   const float2 *dc;           // [S][Lp] log2 D^(0,t) as float-float (x = +inf: none; log2 0 = kNeg)
   float *uc_t;                // [S][Lp] log2 U^(0,t) of row t (nullptr: no commodity capacities)
   int kl_shift;               // log2 K_L is read as kl * 2^-kl_shift (epsilon 2^kl_shift times larger)
+  const unsigned char *fixed_w; // [S] or nullptr: 1 = a storage state, whose capacity update ran before this
+                              // step (its W_t is read back here, nothing about it is stored)
   unsigned int wait_tries;    // pipelined kernels: tries of each bounded mbarrier wait (each <= 2 us)
   int withhold_stage;         // test switch: the consumers never release their first stage, so that the
                               // bounded waits of the pipelined kernels run out (no copy stays in flight)
+};
+
+// Storage states (a state that may follow itself, K_ss = 1: storage on an edge, the source and
+// sink states of the traffic-routing model; Section 3.3).  K = B_in B_out + D with D diagonal
+// over those states, so a storage state k (state s) owns message row row0 + k of every panel:
+//   forward:  A_t[row0 + k] = hatPsi_{t+1}[s] = A_t[tail s] (+) (A_{t-1}[row0 + k] + W_t[s])
+//   backward: B_t[row0 + k] = Psi_{t-1}[s]    = B_t[head s] (+) (B_{t+1}[row0 + k] + W_t[s])
+// ((+): log-sum-exp; a missing tail or head contributes log 0).
+struct StoreRowArgs {
+  int n, Lp, row0;            // storage states, row length, first storage row (= number of nodes)
+  QScale qs;
+  const int *state;           // [n] state index
+  const int *node;            // [n] tail (forward) or head (backward) node, -1 for none
+  float *p_hi;                // panel of this step: node rows read, storage rows written
+  lo_t *p_lo;
+  const float *q_hi;          // panel of the step before (nullptr at a boundary: copy only)
+  const lo_t *q_lo;
+  const float *w_hi, *w_lo;   // W of this step by state
+};
+
+// Boundary terms of storage states: row row0 + k[i] of commodity l[i] takes (+) log2 U of triple q[i].
+struct StoreTriArgs {
+  int n, Lp, row0;
+  QScale qs;
+  const int *k, *l, *q;
+  const double *tri_logU;
+  float *p_hi;
+  lo_t *p_lo;
+};
+
+// Capacity update of the storage states before forward step t: their column sums read the
+// storage rows of A_{t-1} (x) and B_{t+1} (y).
+struct StoreUpdArgs {
+  int n, Lp, row0;
+  const int *state;
+  const float *x_hi, *y_hi;
+  const lo_t *x_lo, *y_lo;
 };
 
 // Boundary kernels (sources, sinks): segments of (node, commodity) with their triples.
@@ -139,6 +178,8 @@ struct BndArgs {
   unsigned int *counter;
   DevStats *stats;
   int mode;                   // 0: update U, 1: rebuild the panel from the current U only
+  int skip_node;              // segments of this node write no panel entry (a boundary state
+                              // without a head (sources) or tail (sinks); -1: none)
   int is_source;
   int accumulate;             // mode 0: add the measures to the pass totals instead of setting them
 };

@@ -17,6 +17,9 @@ cudaError_t launch_step(bool fwd, bool pc, int G, int C, const StepArgs &a, cuda
 cudaError_t prepare_step_kernels(int G, int C, bool pc, int V, int *grid_fwd, int *grid_bwd);
 int step_grid(int V, int G);
 cudaError_t launch_boundary(const BndArgs &b, cudaStream_t s);
+cudaError_t launch_store_rows(const StoreRowArgs &a, cudaStream_t s);
+cudaError_t launch_store_triples(const StoreTriArgs &a, cudaStream_t s);
+cudaError_t launch_store_update(const StepArgs &a, const StoreUpdArgs &u, int max_grid, cudaStream_t s);
 int boundary_grid(int n_seg);
 cudaError_t launch_pass_begin(DevStats *st, cudaStream_t s);
 cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, cudaStream_t s);
@@ -139,6 +142,7 @@ struct ots_problem {
   double eps = 1.0, mass = 0.0;
   QScale qs{};                                 // quantum of the message hi parts
   int pgrid_fwd = 0, pgrid_bwd = 0;            // grids of the pipelined persistent kernels (0 = not used)
+  int max_grid = 1;                            // blocks the per-block partial sums hold
   unsigned int wait_tries = 1u << 20;          // tries of each bounded device wait (ots_set_wait_limit)
   int withhold_stage = 0;                      // test switch of ots_set_wait_limit
   bool pc = false;
@@ -154,8 +158,17 @@ struct ots_problem {
   std::vector<int> in_state_h;                 // in-CSR order of the states (host copy)
   std::unique_ptr<ots_host::HostArrays> host;  // between the host build and the upload
 
-  std::vector<int> tail, head;
+  std::vector<int> tail, head;                 // -1: none (explicit state graphs)
   ots_host::Boundary src, snk;
+  // Explicit state graph (Section 3.3): storage state k owns row V + k of every panel, and row
+  // null_row = V + nstore stays log 0 (the row a state without a tail / head gathers).
+  bool xgraph = false;
+  int nstore = 0, null_row = -1, rows = 0;     // rows per panel: V, or V + nstore + 1
+  std::vector<int> store_state, store_tail, store_head, frow, brow;
+  std::vector<int> sst_k, sst_l, sst_q, zst_k, zst_l, zst_q;   // storage triples of sources / sinks
+  int *d_store_state = nullptr, *d_store_tail = nullptr, *d_store_head = nullptr;
+  int *d_sst = nullptr, *d_zst = nullptr;      // [3][n] (k, l, triple) of the storage triples
+  unsigned char *d_fixed_w = nullptr;          // [S] 1 = storage state
 
   void *arena = nullptr;
   size_t arena_bytes = 0;
@@ -194,7 +207,7 @@ struct ots_problem {
   long long kernels_launched = 0;
   long long h2d_bytes = 0, d2h_bytes = 0;
 
-  size_t panel() const { return (size_t)V * Lp; }
+  size_t panel() const { return (size_t)rows * Lp; }
   float *a_hi(int t) { return t == 1 ? d_a_hi[0] : d_a_hi[1 + (t & 1)]; }
   lo_t *a_lo(int t) { return t == 1 ? d_a_lo[0] : d_a_lo[1 + (t & 1)]; }
   // backward panels: B_t lives in slot bslot[t]; with bk > 1 only t = 2, T and every bk-th t

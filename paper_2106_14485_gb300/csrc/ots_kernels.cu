@@ -333,6 +333,122 @@ __global__ void __launch_bounds__(kBlock) k_boundary(const BndArgs b) {
   }
 }
 
+// ------------------------------------------------------------------------------------
+// Storage states (the rows of StoreRowArgs): after each step, and at the boundaries.
+// One thread per (storage state, 4 commodities); same arithmetic as the node rows (exact hi
+// sums on the q grid, one ex2 per term).
+// ------------------------------------------------------------------------------------
+__global__ void k_store_rows(const StoreRowArgs a) {
+  const int n4 = a.Lp / 4;
+  const size_t total = (size_t)a.n * n4;
+  const float lo_unit = a.qs.lo_unit;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(i / n4), c = (int)(i % n4);
+    const int v = a.node[k];
+    float h1[4];
+    uint32_t w1[2] = {0x80008000u, 0x80008000u};
+    if (v >= 0) {
+      load4(a.p_hi + (size_t)v * a.Lp + 4 * c, a.p_lo + (size_t)v * a.Lp + 4 * c, h1, w1);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) h1[q] = kNeg;
+    }
+    float oh[4];
+    lo_t ol[4];
+    if (!a.q_hi) {                                   // boundary: the node row's value
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        oh[q] = h1[q];
+        ol[q] = (lo_t)((w1[q >> 1] >> (16 * (q & 1))) & 0xffffu);
+      }
+    } else {
+      const int st = a.state[k];
+      const float wh = a.w_hi[st], wlb = a.w_lo[st] - kLoBias * lo_unit, nlb = -kLoBias * lo_unit;
+      const size_t r = (size_t)(a.row0 + k) * a.Lp + 4 * c;
+      float h2[4];
+      uint32_t w2[2];
+      load4(a.q_hi + r, a.q_lo + r, h2, w2);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float s1 = h1[q], s2 = h2[q] + wh;     // exact (q grid); a closed self term is log 0
+        const float m = fmaxf(s1, s2);
+        float acc = 0.f;
+        if (m > kNegThresh)
+          acc = ex2(fmaf(lo_inj(w1, q), lo_unit, (s1 - m) + nlb)) + ex2(fmaf(lo_inj(w2, q), lo_unit, (s2 - m) + wlb));
+        lse_encode(m, acc, a.qs, oh[q], ol[q]);
+      }
+    }
+    const size_t o = (size_t)(a.row0 + k) * a.Lp + 4 * c;
+    store4(a.p_hi + o, a.p_lo + o, oh, ol);
+  }
+}
+
+// Boundary terms of storage states: (+) log2 U of their own triples, in FP64 (as the node rows'
+// boundary entries); the (row, commodity) pairs are distinct, so no two threads share an entry.
+__global__ void k_store_triples(const StoreTriArgs a) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+    const size_t idx = (size_t)(a.row0 + a.k[i]) * a.Lp + a.l[i];
+    const double cur = a.p_hi[idx] < kNegThresh ? -INFINITY
+                                                 : (double)a.p_hi[idx] + ((double)a.p_lo[idx] - 32768.0) * (double)a.qs.lo_unit;
+    const double u = a.tri_logU[a.q[i]];
+    const double m = fmax(cur, u);
+    const double r = m + log2(exp2(cur - m) + exp2(u - m));
+    const float h = (float)r;
+    float oh;
+    lo_t ol;
+    encode(h, (float)(r - (double)h), a.qs, oh, ol);
+    a.p_hi[idx] = oh;
+    a.p_lo[idx] = ol;
+  }
+}
+
+// Capacity update of the storage states before forward step t (Corollary 7 with their own
+// message rows): one warp per state, the column log-sum-exp over commodities of
+// A_{t-1}[row0 + k] + B_{t+1}[row0 + k], then the same update as every other state (a.fixed_w is
+// not set here).  The FP64 sums join the pass totals.
+__global__ void __launch_bounds__(256) k_store_update(const StepArgs a, const StoreUpdArgs u) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  float viol = 0.f;
+  float2 dual = make_float2(0.f, 0.f);
+  const int n4 = u.Lp / 4;
+  for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < u.n; k += warps) {
+    const size_t r = (size_t)(u.row0 + k) * u.Lp;
+    float cm = 2.f * kNeg;
+    for (int c = lane; c < n4; c += 32) {
+      float hx[4], hy[4];
+      uint32_t wx[2], wy[2];
+      load4(u.x_hi + r + 4 * c, u.x_lo + r + 4 * c, hx, wx);
+      load4(u.y_hi + r + 4 * c, u.y_lo + r + 4 * c, hy, wy);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cm = fmaxf(cm, hx[q] + hy[q]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+    float cs = 0.f;
+    if (cm > kNegThresh) {
+      for (int c = lane; c < n4; c += 32) {
+        float hx[4], hy[4];
+        uint32_t wx[2], wy[2];
+        load4(u.x_hi + r + 4 * c, u.x_lo + r + 4 * c, hx, wx);
+        load4(u.y_hi + r + 4 * c, u.y_lo + r + 4 * c, hy, wy);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float bl = lo_inj(wy, q) - 2.f * kLoBias;                     // exact
+          cs += ex2(fmaf(lo_inj(wx, q) + bl, a.qs.lo_unit, (hx[q] + hy[q]) - cm));
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+    if (lane == 0) {
+      float wh, wl;
+      update_state<false>(a, u.state[k], cm, cs, true, wh, wl, viol, dual);
+    }
+  }
+  block_sum2_last(make_float2(viol, 0.f), dual, a.partials, a.counter, &a.stats->cap_viol, &a.stats->dual_cap, 0);
+}
+
 // Start of a pass: clear the accumulators the forward sweep adds into.
 __global__ void k_pass_begin(DevStats *st) {
   st->cap_viol = 0.0;
@@ -1074,6 +1190,26 @@ int step_grid(int V, int G) { const int npb = nodes_per_block(G); return (V + np
 cudaError_t launch_boundary(const BndArgs &b, cudaStream_t s) {
   const int grid = (b.n_seg + kBlock - 1) / kBlock;
   k_boundary<<<grid > 0 ? grid : 1, kBlock, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_rows(const StoreRowArgs &a, cudaStream_t s) {
+  const size_t total = (size_t)a.n * (a.Lp / 4);
+  const int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
+  k_store_rows<<<grid > 0 ? grid : 1, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_triples(const StoreTriArgs &a, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  k_store_triples<<<(a.n + 255) / 256, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_update(const StepArgs &a, const StoreUpdArgs &u, int max_grid, cudaStream_t s) {
+  int grid = (u.n + 7) / 8;                       // 8 warps per block, one state per warp
+  grid = std::max(1, std::min(grid, max_grid));   // the partial sums hold max_grid blocks
+  k_store_update<<<grid, 256, 0, s>>>(a, u);
   return cudaGetLastError();
 }
 

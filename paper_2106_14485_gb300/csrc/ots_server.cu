@@ -48,7 +48,7 @@ struct Request {
   int64_t ticket = 0;
   ots_problem_desc d{};
   ots_solve_opts o{};
-  std::vector<int32_t> esrc, edst, sc, ss, zc, zs, win_in, win_out;
+  std::vector<int32_t> esrc, edst, sc, ss, zc, zs, win_in, win_out, st_tail, st_head, st_hold;
   std::vector<double> ecost, ecap, wcost, wcap, ccost, cost_t, cap_t, ccap, sm, zm;
   int S = 0, T = 0;
   bool large = false;
@@ -344,6 +344,9 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   copy_array(r->win_in, d->commodity_t_in, d->commodity_t_in ? (size_t)d->L : 0);
   copy_array(r->ccap, d->commodity_capacity, d->commodity_capacity ? (size_t)d->L * S : 0);
   copy_array(r->win_out, d->commodity_t_out, d->commodity_t_out ? (size_t)d->L : 0);
+  copy_array(r->st_tail, d->state_tail, d->state_tail ? S : 0);
+  copy_array(r->st_head, d->state_head, d->state_head ? S : 0);
+  copy_array(r->st_hold, d->state_hold, d->state_hold ? S : 0);
   copy_array(r->sc, d->src_commodity, d->n_sources);
   copy_array(r->ss, d->src_state, d->n_sources);
   copy_array(r->sm, d->src_mass, d->n_sources);
@@ -363,6 +366,9 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   r->d.commodity_t_in = ptr_or_null(r->win_in);
   r->d.commodity_capacity = ptr_or_null(r->ccap);
   r->d.commodity_t_out = ptr_or_null(r->win_out);
+  r->d.state_tail = ptr_or_null(r->st_tail);
+  r->d.state_head = ptr_or_null(r->st_head);
+  r->d.state_hold = ptr_or_null(r->st_hold);
   r->d.src_commodity = ptr_or_null(r->sc);
   r->d.src_state = ptr_or_null(r->ss);
   r->d.src_mass = ptr_or_null(r->sm);
@@ -378,7 +384,8 @@ ots_status ots_server_submit(ots_server *s, const ots_problem_desc *d, const ots
   r->S = (int)S;
   r->T = d->T;
   r->large = s->desc.mode == 1 || d->L > 256 || d->commodity_cost != nullptr || d->commodity_capacity != nullptr ||
-             d->commodity_t_in != nullptr || d->commodity_t_out != nullptr;
+             d->commodity_t_in != nullptr || d->commodity_t_out != nullptr || d->state_tail != nullptr ||
+             d->state_head != nullptr || d->state_hold != nullptr;
   r->t_submit = Clock::now();
   std::unique_lock<std::mutex> lk(s->mu);
   if (s->desc.max_queued > 0) {

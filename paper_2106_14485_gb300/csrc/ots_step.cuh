@@ -350,6 +350,11 @@ __device__ __forceinline__ void add_residual(float2 lu_old, float2 lu_new, float
 template <bool PC>
 __device__ __forceinline__ void update_state(const StepArgs &a, int sk, float cm, float cs, bool write, float &w_hi,
                                              float &w_lo, float &viol, float2 &dual) {
+  if (a.fixed_w && a.fixed_w[sk]) {              // a storage state: updated by its own kernel
+    w_hi = a.w_hi_t[sk];
+    w_lo = a.w_lo_t[sk];
+    return;
+  }
   float col_hi = kNeg, col_lo = 0.f;
   if (cm > kNegThresh && cs > 0.f) two_sum(cm, log2_unbiased(cs), col_hi, col_lo);  // log2 (hatPsi .* Psi (.* K_L))^T 1
   const float klh = PC ? 0.f : ldexpf(a.kl_hi[sk], -a.kl_shift), kll = PC ? 0.f : ldexpf(a.kl_lo[sk], -a.kl_shift);
@@ -423,7 +428,7 @@ __device__ __forceinline__ void boundary_segment(const BndArgs &b, int sidx, dou
   }
   double sum = 0.0;
   for (int q = q0; q < q1; ++q) sum += exp2(b.tri_logU[q] - m);
-  if (!b.out_hi) return;
+  if (!b.out_hi || b.seg_node[sidx] == b.skip_node) return;
   const double r = m + log2(sum);
   const float h = (float)r;
   float oh;

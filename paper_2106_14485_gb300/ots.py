@@ -42,6 +42,7 @@ class ProblemDesc(ctypes.Structure):
         ("psi_stride", ctypes.c_int32),
         ("commodity_t_in", _i32p), ("commodity_t_out", _i32p),
         ("commodity_capacity", _f64p),
+        ("state_tail", _i32p), ("state_head", _i32p), ("state_hold", _i32p),
     ]
 
 
@@ -238,8 +239,6 @@ def _torch_allocator(device: int):
 def _problem_desc(inst, device: int = 0, stream: int | None = None):
     """ots_problem_desc of an object with the attributes of ``instances.Instance`` plus the
     host arrays it points into (keep them alive while the descriptor is used)."""
-    if getattr(inst, "state_tail", None) is not None or getattr(inst, "state_hold", None) is not None:
-        raise ValueError("explicit state graphs (storage states) are not supported by the CUDA solver")
     c = lambda x, dt: np.ascontiguousarray(x, dtype=dt)
     arr = {
         "edge_src": c(inst.edge_src, np.int32), "edge_dst": c(inst.edge_dst, np.int32),
@@ -261,7 +260,7 @@ def _problem_desc(inst, device: int = 0, stream: int | None = None):
     ccap = getattr(inst, "commodity_capacity", None)
     if ccap is not None:
         arr["commodity_capacity"] = c(ccap, np.float64)
-    for k in ("commodity_t_in", "commodity_t_out"):
+    for k in ("commodity_t_in", "commodity_t_out", "state_tail", "state_head", "state_hold"):
         w = getattr(inst, k, None)
         if w is not None:
             arr[k] = c(w, np.int32)
@@ -277,6 +276,9 @@ def _problem_desc(inst, device: int = 0, stream: int | None = None):
     d.commodity_t_in = _ptr(arr.get("commodity_t_in"), ctypes.c_int32)
     d.commodity_t_out = _ptr(arr.get("commodity_t_out"), ctypes.c_int32)
     d.commodity_capacity = _ptr(arr.get("commodity_capacity"), ctypes.c_double)
+    d.state_tail = _ptr(arr.get("state_tail"), ctypes.c_int32)
+    d.state_head = _ptr(arr.get("state_head"), ctypes.c_int32)
+    d.state_hold = _ptr(arr.get("state_hold"), ctypes.c_int32)
     d.T, d.L, d.eps = int(inst.T), int(inst.L), float(inst.eps)
     d.n_sources = len(arr["src_comm"])
     d.src_commodity, d.src_state = _ptr(arr["src_comm"], ctypes.c_int32), _ptr(arr["src_state"], ctypes.c_int32)

@@ -140,3 +140,30 @@ def test_commodity_count_limits(O):
     with pytest.raises(O.OTSError) as e:
         O.ots_check_problem(x)
     assert e.value.code == O.OTS_ERR_INVALID_ARG
+
+
+def test_explicit_state_graph_is_validated_on_the_host():
+    """ots_check_problem on explicit state graphs (no device): the traffic-routing model passes;
+    a tail out of range or a storage flag other than 0 / 1 is an invalid argument; a sink that
+    no exact walk of T-1 transitions reaches is infeasible."""
+    from paper_2106_14485_gb300 import ots
+    ots.load_library()
+    good = I.traffic_routing_instance(seed=1, rows=4, cols=4, L=3, T=9, eps=0.1)
+    ots.ots_check_problem(good)
+    bad = I.traffic_routing_instance(seed=1, rows=4, cols=4, L=3, T=9, eps=0.1)
+    bad.state_tail = bad.state_tail.copy()
+    bad.state_tail[0] = bad.n_nodes
+    with pytest.raises(ots.OTSError) as e:
+        ots.ots_check_problem(bad)
+    assert e.value.code == ots.OTS_ERR_INVALID_ARG
+    bad = I.traffic_routing_instance(seed=1, rows=4, cols=4, L=3, T=9, eps=0.1)
+    bad.state_hold = bad.state_hold.copy()
+    bad.state_hold[0] = 2
+    with pytest.raises(ots.OTSError) as e:
+        ots.ots_check_problem(bad)
+    assert e.value.code == ots.OTS_ERR_INVALID_ARG
+    short = I.traffic_routing_instance(seed=1, rows=4, cols=4, L=3, T=9, eps=0.1)
+    short.T = 3                                    # two transitions cannot cross the grid
+    with pytest.raises(ots.OTSError) as e:
+        ots.ots_check_problem(short)
+    assert e.value.code == ots.OTS_ERR_INFEASIBLE

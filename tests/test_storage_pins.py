@@ -3,7 +3,8 @@ may follow themselves): storage on edges and the traffic-routing model of eq.
 cost_traffic_routing, in which nothing enters a source and nothing leaves a sink.  Pinned against
 brute force over the full tensor with K built from the definition (tests/pins_math.py), the
 fixed point of Proposition 5 on that tensor, and the properties the model fixes.  The CUDA solver
-does not take these models (its binding refuses them)."""
+takes these models through the explicit state graph of its descriptor; its parity with this oracle
+is tested on the GPU (tests/test_gpu_storage.py)."""
 import numpy as np
 import pytest
 
@@ -106,7 +107,13 @@ def test_storage_on_a_wait_loop_changes_nothing():
         assert np.array_equal(o.flows(), F0)
 
 
-def test_cuda_binding_refuses_explicit_state_graphs():
+def test_cuda_binding_passes_the_state_graph_through():
+    """The binding hands tail, head and storage flag of every state to the library, whose host
+    checks accept the model (the device path is checked against the oracle on the GPU)."""
     from paper_2106_14485_gb300 import ots
-    with pytest.raises(ValueError):
-        ots._problem_desc(tiny())
+    inst = tiny()
+    d, arr = ots._problem_desc(inst)
+    assert np.array_equal(arr["state_tail"], inst.state_tail) and np.array_equal(arr["state_head"], inst.state_head)
+    assert np.array_equal(arr["state_hold"], inst.state_hold)
+    ots.load_library()
+    ots.ots_check_problem(inst)
