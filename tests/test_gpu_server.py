@@ -46,14 +46,23 @@ def test_alone_and_in_the_mix_give_the_same_result(O):
     r0 = O.ots_server_wait(s, t0, 60000)
     F0 = O.ots_server_get_flows(s, t0)
     assert r0["status"] == 0
-    # now the same request arrives in the middle of a stream
+    # now the same request arrives in the middle of a stream, behind a request whose capacities
+    # admit no feasible flow (it runs to its pass limit, so it is resident while the target runs)
+    from tests.test_gpu_parity import capped_rgg
+    blocker = O.ots_server_submit(s, capped_rgg(seed=17, L=5, T=12), tol=1e-9, max_iters=4000)
     tickets = [O.ots_server_submit(s, x, tol=1e-7) for x in others[:4]]
     time.sleep(0.002)
     t1 = O.ots_server_submit(s, target, tol=1e-7)
     tickets += [O.ots_server_submit(s, x, tol=1e-7) for x in others[4:]]
+    most = 0
+    while O.ots_server_poll(s, t1)["status"] == O.OTS_PENDING:
+        most = max(most, O.ots_server_info(s)["resident"])
+        time.sleep(0.0005)
     r1 = O.ots_server_wait(s, t1, 60000)
+    assert most >= 2, "the target never shared the GPU with another request"
     for t in tickets:
         assert O.ots_server_wait(s, t, 60000)["status"] == 0
+    assert O.ots_server_wait(s, blocker, 60000)["status"] == O.OTS_ERR_NOT_CONVERGED
     F1 = O.ots_server_get_flows(s, t1)
     assert r1["status"] == 0 and r1["iterations"] == r0["iterations"]
     assert np.array_equal(F0, F1)
@@ -65,7 +74,7 @@ def test_alone_and_in_the_mix_give_the_same_result(O):
         ox.solve(max_iters=200000, tol=1e-12)
         assert rel_l1(O.ots_server_get_flows(s, t), ox.flows()) <= FLOW_TOL
     info = O.ots_server_info(s)
-    assert info["completed"] == 2 + len(others) and info["failed"] == 0 and info["resident"] == 0
+    assert info["completed"] + info["failed"] == 3 + len(others) and info["failed"] <= 1 and info["resident"] == 0
     O.ots_server_destroy(s)
 
 
