@@ -126,6 +126,7 @@ StepArgs step_args(ots_problem *p, bool fwd, int t, int mode) {
   a.wait_tries = p->wait_tries;
   a.withhold_stage = p->withhold_stage;
   a.fixed_w = p->d_fixed_w;
+  a.slot = fwd && p->d_slots ? p->d_slots + (size_t)t * 2 * p->max_grid : nullptr;
   return a;
 }
 
@@ -363,7 +364,9 @@ cudaError_t enqueue_segment(ots_problem *p, int t) {
   return cudaSuccess;
 }
 
-long long kernels_per_pass(const ots_problem *p) { return 2LL * p->T + p->b_recompute + store_kernels_per_pass(p); }
+long long kernels_per_pass(const ots_problem *p) {
+  return 2LL * p->T + p->b_recompute + store_kernels_per_pass(p) + (p->d_slots ? 1 : 0);
+}
 
 // One pass of the while loop of Algorithm 2 (enqueued directly or captured into a graph),
 // with phase events around the source update, the forward sweep, the sink update and the
@@ -388,7 +391,8 @@ ots_status enqueue_pass(ots_problem *p, bool capture) {
     OTS_CUDA(after_backward_step(p, t));
   }
   OTS_CUDA(cudaEventRecordWithFlags(p->ev[4], p->stream, flags));
-  OTS_CUDA(launch_pass_end(p->d_stats, p->d_report, p->mass, p->eps, p->stream));
+  OTS_CUDA(launch_pass_end(p->d_stats, p->d_report, p->mass, p->eps, p->d_slots, 2 * p->max_grid, p->max_grid, p->T,
+                           p->d_step_tot, p->stream));
   return OTS_OK;
 }
 
@@ -1199,6 +1203,8 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   size_t o_sst = cv.take<int>(3 * p->sst_k.size()), o_zst = cv.take<int>(3 * p->zst_k.size());
   size_t o_stats = cv.take<DevStats>(1), o_report = cv.take<PassReport>(1);
   size_t o_partials = cv.take<double>(3 * (size_t)max_grid), o_counter = cv.take<unsigned int>(4);
+  const size_t n_slots = p->member ? 0 : (T + 1) * 2 * (size_t)max_grid;
+  size_t o_slots = cv.take<double>(n_slots), o_step_tot = cv.take<double>(p->member ? 0 : 2 * (T + 1));
   struct BOff { size_t seg_ptr, seg_node, seg_l, other, l, R, logR, logU, flow; } bo[2];
   Boundary *sides[2] = {&p->src, &p->snk};
   for (int k = 0; k < 2; ++k) {
@@ -1243,6 +1249,7 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
   }
   p->d_stats = (DevStats *)at(o_stats); p->d_report = (PassReport *)at(o_report);
   p->d_partials = (double *)at(o_partials); p->d_counter = (unsigned int *)at(o_counter);
+  if (n_slots) { p->d_slots = (double *)at(o_slots); p->d_step_tot = (double *)at(o_step_tot); }
   for (int k = 0; k < 2; ++k) {
     Boundary &b = *sides[k];
     b.d_seg_ptr = (int *)at(bo[k].seg_ptr); b.d_seg_node = (int *)at(bo[k].seg_node); b.d_seg_l = (int *)at(bo[k].seg_l);
@@ -1297,6 +1304,9 @@ ots_status ots_host::build_problem_device(ots_problem *p) {
 #undef UP
   p->host.reset();                             // pageable copies have completed
   if (p->member) return OTS_OK;  // duals, panels, accumulators: the batched kernel's set-up step
+  // slots of blocks that never run stay 0, so the pass end may add all max_grid of them
+  if (n_slots && cudaMemsetAsync(p->d_slots, 0, sizeof(double) * n_slots, p->stream) != cudaSuccess)
+    return bail(fail(OTS_ERR_CUDA, "memset failed"));
   if (cudaMemsetAsync(p->d_stats, 0, sizeof(DevStats), p->stream) != cudaSuccess ||
       cudaMemsetAsync(p->d_counter, 0, 4 * sizeof(unsigned int), p->stream) != cudaSuccess ||
       cudaMemsetAsync(p->d_flow, 0, sizeof(double) * (T + 1) * S, p->stream) != cudaSuccess)

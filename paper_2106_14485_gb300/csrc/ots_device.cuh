@@ -113,6 +113,8 @@ struct StepArgs {
   const float2 *dc;           // [S][Lp] log2 D^(0,t) as float-float (x = +inf: none; log2 0 = kNeg)
   float *uc_t;                // [S][Lp] log2 U^(0,t) of row t (nullptr: no commodity capacities)
   int kl_shift;               // log2 K_L is read as kl * 2^-kl_shift (epsilon 2^kl_shift times larger)
+  double *slot;               // [2 * blocks] or nullptr: each block's FP64 sums of this step, added up at
+                              // the end of the pass (nullptr: a last-block reduction into stats)
   const unsigned char *fixed_w; // [S] or nullptr: 1 = a storage state, whose capacity update ran before this
                               // step (its W_t is read back here, nothing about it is stored)
   unsigned int wait_tries;    // pipelined kernels: tries of each bounded mbarrier wait (each <= 2 us)

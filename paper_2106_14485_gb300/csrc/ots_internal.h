@@ -22,7 +22,8 @@ cudaError_t launch_store_triples(const StoreTriArgs &a, cudaStream_t s);
 cudaError_t launch_store_update(const StepArgs &a, const StoreUpdArgs &u, int max_grid, cudaStream_t s);
 int boundary_grid(int n_seg);
 cudaError_t launch_pass_begin(DevStats *st, cudaStream_t s);
-cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, cudaStream_t s);
+cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, const double *slots,
+                            int stride, int nblk, int T, double *tot, cudaStream_t s);
 cudaError_t launch_weights(int S, int T, QScale qs, const float *kl_hi, const float *kl_lo, int kl_stride, float2 *logu,
                            float *w_hi, float *w_lo, int reset, const int *st_inpos, const int *st_outpos,
                            float2 *logu_in, float *wout_hi, float *wout_lo, cudaStream_t s);
@@ -197,6 +198,8 @@ struct ots_problem {
   DevStats *d_stats = nullptr;
   PassReport *d_report = nullptr;
   double *d_partials = nullptr;
+  double *d_slots = nullptr;                   // [T+1][2 max_grid] per-block sums of each forward step
+  double *d_step_tot = nullptr;                // [T+1][2] their totals per step
   unsigned int *d_counter = nullptr;
   PassReport *h_report = nullptr;              // pinned
 

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(BlockOf<G>::value, MinBlocksFwd<G>::value) k_f
     }
   }
   if (a.mode == 0)
-    block_sum2_last(make_float2(viol, 0.f), dual, a.partials, a.counter, &a.stats->cap_viol, &a.stats->dual_cap, 0);
+    step_sums(a.slot, make_float2(viol, 0.f), dual, a.partials, a.counter, &a.stats->cap_viol, &a.stats->dual_cap);
 }
 
 // ------------------------------------------------------------------------------------
@@ -456,12 +456,31 @@ __global__ void k_pass_begin(DevStats *st) {
   st->bad = 0.0;
 }
 
+// End of a pass, first part: block t adds the per-block sums the forward step t left in its slot
+// (fixed assignment of blocks to threads, fixed tree), giving one pair of totals per step.
+__global__ void k_step_totals(const double *slots, int stride, int nblk, int T, double *tot) {
+  __shared__ double s0[32], s1[32];
+  const int t = blockIdx.x;
+  double v0 = 0.0, v1 = 0.0;
+  if (t >= 2 && t <= T - 1)
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+      v0 += slots[(size_t)t * stride + 2 * b];
+      v1 += slots[(size_t)t * stride + 2 * b + 1];
+    }
+  block_sum2_f64(v0, v1, s0, s1);
+  if (threadIdx.x == 0) { tot[2 * t] = v0; tot[2 * t + 1] = v1; }
+}
+
 // End of a pass: relative measures and the dual objective of Theorem 3 in natural units:
 //   -eps <K,U> + eps ln2 (<R01, log2 U01> + <R0T, log2 U0T> + sum_t <d, log2 u_t>).
-__global__ void k_pass_end(const DevStats *st, PassReport *rep, double mass, double eps) {
+// The forward steps' sums come from tot (steps 2..T-1, added in order; nullptr: already in st).
+__global__ void k_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, const double *tot, int T) {
+  double cap = st->cap_viol, dcap = st->dual_cap;
+  if (tot)
+    for (int t = 2; t <= T - 1; ++t) { cap += tot[2 * t]; dcap += tot[2 * t + 1]; }
   rep->src_resid_rel = st->src_resid / mass;
-  rep->cap_viol_rel = st->cap_viol / mass;
-  rep->dual_objective = -eps * st->mass_snk + eps * 0.69314718055994530942 * (st->dual_src + st->dual_snk + st->dual_cap);
+  rep->cap_viol_rel = cap / mass;
+  rep->dual_objective = -eps * st->mass_snk + eps * 0.69314718055994530942 * (st->dual_src + st->dual_snk + dcap);
   rep->bad = st->bad;
   rep->passes += 1;
 }
@@ -1017,7 +1036,7 @@ __global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_forward_tma(c
     }
   }
   if (timed_out) atomicAdd(&a.stats->bad, 1e6);
-  block_sum2_last(make_float2(viol, 0.f), dual, a.partials, a.counter, &a.stats->cap_viol, &a.stats->dual_cap, 0);
+  step_sums(a.slot, make_float2(viol, 0.f), dual, a.partials, a.counter, &a.stats->cap_viol, &a.stats->dual_cap);
 }
 
 // Backward step, warp-specialised like the forward step.
@@ -1220,8 +1239,14 @@ cudaError_t launch_pass_begin(DevStats *st, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, cudaStream_t s) {
-  k_pass_end<<<1, 1, 0, s>>>(st, rep, mass, eps);
+cudaError_t launch_pass_end(const DevStats *st, PassReport *rep, double mass, double eps, const double *slots,
+                            int stride, int nblk, int T, double *tot, cudaStream_t s) {
+  if (slots) {
+    k_step_totals<<<T, 256, 0, s>>>(slots, stride, nblk, T, tot);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_pass_end<<<1, 1, 0, s>>>(st, rep, mass, eps, slots ? tot : nullptr, T);
   return cudaGetLastError();
 }
 

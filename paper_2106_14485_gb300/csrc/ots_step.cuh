@@ -104,6 +104,12 @@ __device__ __forceinline__ void block_sum2_f64(double &v0, double &v1, double *s
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { v0 += s0[w]; v1 += s1[w]; }
 }
 
+// The FP64 sums (capacity residual, dual term) of a step: with a slot, every block writes its two
+// totals there and the pass-end kernels add the slots of all steps in a fixed order (no grid-wide
+// reduction at the end of each step); without one, the last block adds them to the pass statistics.
+__device__ __forceinline__ void step_sums(double *slot, float2 v0, float2 v1, double *partials, unsigned int *counter,
+                                          double *dst0, double *dst1);
+
 // Deterministic grid reduction of two values: every block sums its threads' float-float
 // values and writes the block total as FP64; the last block to finish reduces all partials in
 // FP64 with a fixed assignment to threads and a fixed tree, then adds the totals to dst0 /
@@ -133,6 +139,20 @@ __device__ void block_sum2_last(float2 v0, float2 v1, double *partials, unsigned
   if (threadIdx.x == 0) {
     if (assign) { *dst0 = a; *dst1 = b; } else { *dst0 += a; *dst1 += b; }
     *counter = 0u;
+  }
+}
+
+__device__ __forceinline__ void step_sums(double *slot, float2 v0, float2 v1, double *partials, unsigned int *counter,
+                                          double *dst0, double *dst1) {
+  if (!slot) {
+    block_sum2_last(v0, v1, partials, counter, dst0, dst1, 0);
+    return;
+  }
+  __shared__ float2 g0[32], g1[32];
+  block_sum2(v0, v1, g0, g1);
+  if (threadIdx.x == 0) {
+    slot[2 * blockIdx.x] = from_ff(v0);
+    slot[2 * blockIdx.x + 1] = from_ff(v1);
   }
 }
 
