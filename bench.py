@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=256,
                     help="instances of the batched workload (uneven random geometric graphs); 0 = skip")
     ap.add_argument("--batch-max-passes", type=int, default=3000)
+    ap.add_argument("--single-batch", type=int, default=64,
+                    help="members of the single-commodity workload (linear-domain path); 0 = skip the single-commodity legs")
+    ap.add_argument("--single-reps", type=int, default=5, help="timed repetitions of the 5x5 grid solves")
     ap.add_argument("--batch-eps-factor", type=float, default=0.0,
                     help="epsilon continuation of the batched and serving workloads: start at this multiple of "
                          "each instance's epsilon (halved per stage); 0 = off (default: on these instances it "
@@ -566,6 +569,119 @@ def bench_batch(args, ots, torch, local, insts, gen_s):
     }
 
 
+def bench_single(args, ots, torch, local):
+    """Single-commodity workloads (L = 1) through the linear-domain path against the log-domain
+    path.  (a) The 5x5 grid (25 nodes, T = 10, eps = 0.05): full solves to tol, one problem;
+    pass throughput of both paths.  (b) Members with the uneven batch's sizes (n~U{50..2000}
+    random geometric graphs, T~U{10..80}, L = 1, eps = 0.01, capacities U[0.2,1]*mass/2), from host
+    arrays to flows on the host: every member in one linear-domain launch (one thread block each),
+    the batched log-domain solver, and the plain one-at-a-time log-domain solver."""
+    from paper_2106_14485_gb300 import instances as I
+    out = {}
+    g = I.grid_single_commodity(0)
+    h = ots.ots_create_problem(g, device=local)
+    upd = g.n_updates_per_iteration()
+    ots.ots_sinkhorn_solve(h, tol=args.tol, max_iters=100000)
+    ots.ots_linear_solve(h, tol=args.tol, max_iters=100000)
+    reps = args.single_reps
+
+    def timed(f):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rs = [f() for _ in range(reps)]
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps, rs[-1]
+
+    t_log, r_log = timed(lambda: ots.ots_sinkhorn_solve(h, tol=args.tol, max_iters=100000))
+    t_lin, r_lin = timed(lambda: ots.ots_linear_solve(h, tol=args.tol, max_iters=100000))
+    n_it = 2000
+    t_plog, _ = timed(lambda: ots.ots_iterate(h, n_it, reset=True))
+    t_plin, r_plin = timed(lambda: ots.ots_linear_iterate(h, n_it, reset=True))
+    lin_duals = ots.ots_get_duals(h)
+    lin_flows = ots.ots_get_flows(h)
+    ots.ots_linear_solve(h, tol=args.tol, max_iters=100000)
+    item = {"inst": g, "duals": ots.ots_get_duals(h), "flows": ots.ots_get_flows(h)}
+    ots.ots_destroy_problem(h)
+    out["grid5x5"] = {
+        "workload": "5x5 grid, L=1, T=10, eps=0.05, move cost 1, wait cost 0.1, Dirichlet(1) marginals over 3 nodes",
+        "linear": {"solves_per_s": 1.0 / t_lin, "ms_per_solve": 1e3 * t_lin, "passes": r_lin["iterations"],
+                   "linear_stats": r_lin["linear"], "pass_updates_per_s": n_it * upd / t_plin,
+                   "us_per_pass": 1e6 * t_plin / n_it},
+        "log_domain": {"solves_per_s": 1.0 / t_log, "ms_per_solve": 1e3 * t_log, "passes": r_log["iterations"],
+                       "pass_updates_per_s": n_it * upd / t_plog, "us_per_pass": 1e6 * t_plog / n_it},
+        "speedup_solves": t_log / t_lin, "speedup_passes": t_plog / t_plin}
+    out["_oracle_items"] = [dict(item, name="grid5x5")]
+    del lin_duals, lin_flows
+
+    # (b) many single-commodity members
+    tg = time.perf_counter()
+    members = I.uneven_single_batch(0, count=args.single_batch, workers=min(16, os.cpu_count() or 1))
+    gen_s = time.perf_counter() - tg
+    n = len(members)
+    mp = args.batch_max_passes
+    for x in members[:2]:                           # warm-up of every arm
+        hx = ots.ots_create_problem(x, device=local)
+        ots.ots_linear_solve(hx, tol=args.tol, max_iters=mp, raise_on_error=False)
+        ots.ots_sinkhorn_solve(hx, tol=args.tol, max_iters=mp, check_every=1, raise_on_error=False)
+        ots.ots_destroy_problem(hx)
+    # linear-domain, one launch for all members
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs = [ots.ots_create_problem(x, device=local) for x in members]
+    t1 = time.perf_counter()
+    reps_l, st_l = ots.ots_linear_solve_many(hs, tol=args.tol, max_iters=mp, raise_on_error=False)
+    t2 = time.perf_counter()
+    flows_l = [ots.ots_get_flows(hx) for hx in hs]
+    t3 = time.perf_counter()
+    ok_l = [r["status"] == 0 for r in reps_l]
+    samp = [k for k in oracle_sample_index(reps_l)][:4]
+    out["_oracle_items"] += [{"inst": members[k], "duals": ots.ots_get_duals(hs[k]), "flows": flows_l[k],
+                              "name": members[k].name} for k in samp]
+    upd_l = sum(r["iterations"] * x.n_updates_per_iteration() for r, x in zip(reps_l, members))
+    for hx in hs:
+        ots.ots_destroy_problem(hx)
+    # batched log-domain solver
+    need = sum((x.T + 2) * x.n_nodes * 4 * 6 + (x.T + 1) * x.n_states * 24 + x.n_states * 64 for x in members)
+    free, _ = torch.cuda.mem_get_info(local)
+    b = ots.ots_batch_create(device=local, pool_bytes=int(min(max(2 * need, 1 << 30), 0.6 * free)),
+                             max_instances=n, ticks_per_launch=32)
+    torch.cuda.synchronize()
+    tb0 = time.perf_counter()
+    ids = [ots.ots_batch_add(b, x, tol=args.tol, max_iters=mp) for x in members]
+    ots.ots_batch_run(b)
+    st_b = [ots.ots_batch_status(b, i) for i in ids]
+    flows_b = [ots.ots_batch_get_flows(b, i) for i in ids]
+    tb1 = time.perf_counter()
+    ots.ots_batch_destroy(b)
+    ok_b = [r["status"] == 0 for r in st_b]
+    # plain one at a time
+    torch.cuda.synchronize()
+    tp0 = time.perf_counter()
+    st_p, flows_p = [], []
+    for x in members:
+        hx = ots.ots_create_problem(x, device=local)
+        st_p.append(ots.ots_sinkhorn_solve(hx, tol=args.tol, max_iters=mp, check_every=1, raise_on_error=False))
+        flows_p.append(ots.ots_get_flows(hx))
+        ots.ots_destroy_problem(hx)
+    tp1 = time.perf_counter()
+    ok_p = [r["status"] == 0 for r in st_p]
+    diffs = [float(np.abs(a - c).sum() / np.abs(c).sum()) for a, c, u, v in zip(flows_l, flows_p, ok_l, ok_p) if u and v]
+    out["uneven_single"] = {
+        "workload": f"{n} members: random geometric graphs n~U{{50..2000}} (mean degree 6, bridged), T~U{{10..80}}, "
+                    f"L=1, capacities U[0.2,1]*mass/2, eps=0.01, tol={args.tol}, pass limit {mp}",
+        "linear_many": {"solves_per_s": sum(ok_l) / (t3 - t0), "converged": sum(ok_l), "create_s": t1 - t0,
+                        "solve_s": t2 - t1, "flows_s": t3 - t2, "updates_per_s": upd_l / (t2 - t1),
+                        "linear_stats": st_l, "passes_mean": float(np.mean([r["iterations"] for r in reps_l]))},
+        "batched_log": {"solves_per_s": sum(ok_b) / (tb1 - tb0), "converged": sum(ok_b), "seconds": tb1 - tb0},
+        "plain_log": {"solves_per_s": sum(ok_p) / (tp1 - tp0), "converged": sum(ok_p), "seconds": tp1 - tp0},
+        "max_rel_flow_diff_linear_vs_plain": max(diffs) if diffs else None,
+        "generate_s": gen_s,
+        "note": "solves_per_s counts converged members (marginal error <= tol) over the whole call sequence "
+                "(create from host arrays, solve, flows to host); the linear arm confirms each member with "
+                "log-domain passes at tol"}
+    return out
+
+
 def bench_serve(args, ots, torch, local, small, large):
     """Serving workload: Poisson arrivals at each rate of a request mix drawn from the batched
     workload's instances (95%) and traffic-scale instances (5%, pass limit
@@ -774,6 +890,10 @@ def run_ours(args):
         if args.serve_rates.strip():
             serve = bench_serve(args, ots, torch, local, c4, inst)
 
+    single = None
+    if args.single_batch > 0:
+        single = bench_single(args, ots, torch, local)
+
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -798,6 +918,7 @@ def run_ours(args):
     cpu = None
     oracle_error = None
     samples = batch.pop("_oracle_samples", []) if batch else []
+    single_items = single.pop("_oracle_items", []) if single else []
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(inst, args.cpu_seconds)
         # oracle leg: the FP64 oracle evaluated at the GPU's results (duals and flows)
@@ -813,6 +934,9 @@ def run_ours(args):
                 "max_flow_elem_worst": max(e["flow_elem_worst"] for e in errs),
                 "max_oracle_src_mismatch": max(e["oracle_src_mismatch"] for e in errs),
                 "max_oracle_cap_excess": max(e["oracle_cap_excess"] for e in errs), "per_instance": errs}
+        if single is not None:
+            errs = [dict(oracle_check(x), name=x["name"]) for x in single_items]
+            single["oracle_error"] = oracle_error["single_commodity"] = errs
         oracle_error["note"] = ("FP64 oracle at the GPU's duals: flow error of the GPU (relative L1; worst entry as "
                                 "|F-F*| / (1e-5 F* + 1e-9 max F*), <= 1 passes) and the marginal violation the oracle "
                                 "measures there; traffic workload on sampled commodities")
@@ -826,6 +950,7 @@ def run_ours(args):
                              "and flows",
             "data": "synthetic", "config": workload_config(inst, args.tol),
             "solves_per_s": solves, "traffic_solve": traffic, "batch": batch, "serving": serve,
+            "single_commodity": single,
             "passes_timed": args.steps, "src_residual_after": final["src_residual"],
             "cap_violation_after": final["cap_violation"],
             "roofline": roof, "cpu_baseline": cpu, "oracle_error": oracle_error, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches)}

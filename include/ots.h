@@ -271,6 +271,53 @@ ots_status ots_set_duals(ots_problem *p, const double *log_u, const double *log_
  * iterate call rebuilds its pass graph.  OTS_ERR_INVALID_ARG for NULL or tries < 0. */
 ots_status ots_set_wait_limit(ots_problem *p, int32_t tries, int32_t withhold_stage);
 
+/* Counters of the linear-domain path (ots_linear_iterate, ots_linear_solve[_many]); summed over
+ * the problems of one call. */
+typedef struct ots_linear_stats {
+  int32_t linear_passes;   /* passes run in scaled FP32 linear arithmetic */
+  int32_t log_passes;      /* passes thrown away and run again in FP32 log arithmetic because a
+                              scaled message or dual left [2^-60, 2^60] */
+  int32_t rescalings;      /* sweeps that re-took the per-node scales from the messages */
+  int32_t confirm_passes;  /* log-domain passes of the confirmation (ots_linear_solve[_many]) */
+  double kernel_ms;        /* device time of the linear-domain kernel launches */
+} ots_linear_stats;
+
+/* Single-commodity problems (L = 1: eq. singlecommodity_reg, Algorithm 1 of Section 4.2, which is
+ * Algorithm 2 with one commodity) with FP32 messages in the linear domain: no exponential per
+ * term, a multiply-add per state and interval in each sweep, and a divide per capacitated state
+ * in the capacity update.  Every message keeps a power-of-two scale per node and interval and
+ * every dual u_t(i) an integer exponent, re-taken from the messages by a sweep in log arithmetic
+ * whenever a scaled value drifts out of [2^-30, 2^30]; a pass whose values leave [2^-60, 2^60]
+ * is run again in log arithmetic.  So the iteration is Algorithm 2's at any epsilon; the linear
+ * form pays off while rescalings are rare (epsilon not far below the cost differences that the
+ * duals move by per pass).  One thread block runs whole passes of one problem (two message rows
+ * of n_nodes floats in shared memory: n_nodes <= 16384).  Applies to problems with L = 1, state
+ * costs (also per interval) and capacities (also per interval); explicit state graphs, commodity
+ * windows, per-commodity costs or capacities and batch members give OTS_ERR_INVALID_ARG.
+ * The problem's device memory grows by about 36 bytes per state and interval on first use.
+ *
+ * ots_linear_iterate: exactly n linear-domain passes from the current duals (reset = 1: from the
+ * initial duals); rep gets the measures of the last pass (dual_objective = NaN).  The duals are
+ * written back to the problem (ots_get_duals, ots_get_flows read them).
+ *
+ * ots_linear_solve: linear-domain passes until the measures are <= tol (or max_iters passes),
+ * then log-domain passes of ots_sinkhorn_solve from those duals until a pass has measures <= tol
+ * (normally one): the reported measures and the flows are the log-domain path's.  opts as for
+ * ots_sinkhorn_solve (warm_start, tol, max_iters, check_every for the confirmation, timeout_ms
+ * between launches); epsilon continuation gives OTS_ERR_INVALID_ARG.  rep, stats may be NULL.
+ *
+ * ots_linear_solve_many: the same for n independent problems in one launch (one thread block
+ * each, so a whole set of small problems fills the GPU); all on one device, the launch on ps[0]'s
+ * stream after the other problems' streams have been synchronised.  reps: [n] or NULL.  Returns
+ * OTS_OK if every problem converged, else the first failing status (per-problem statuses in
+ * reps[i].status). */
+ots_status ots_linear_iterate(ots_problem *p, int32_t n, int32_t reset, ots_solve_report *rep,
+                              ots_linear_stats *stats);
+ots_status ots_linear_solve(ots_problem *p, const ots_solve_opts *opts, ots_solve_report *rep,
+                            ots_linear_stats *stats);
+ots_status ots_linear_solve_many(ots_problem *const *ps, int32_t n, const ots_solve_opts *opts,
+                                 ots_solve_report *reps, ots_linear_stats *stats);
+
 /* Sizes and counters of a created problem. */
 typedef struct ots_problem_stats {
   int32_t n_states;         /* states (edges plus wait loops) */

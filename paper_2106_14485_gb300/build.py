@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libots.so")
-SOURCES = ["ots_api.cu", "ots_kernels.cu", "ots_batch.cu", "ots_batch_kernels.cu", "ots_server.cu"]
+SOURCES = ["ots_api.cu", "ots_kernels.cu", "ots_batch.cu", "ots_batch_kernels.cu", "ots_server.cu", "ots_linear.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
 

@@ -42,22 +42,26 @@ ots_status fail(ots_status s, const char *fmt, ...) {
 
 void clear_error() { g_last_error.clear(); }
 
-}  // namespace ots_host
-
-namespace {
-
-void *dev_alloc(ots_problem *p, size_t bytes) {
+void *problem_alloc(ots_problem *p, size_t bytes) {
   if (p->alloc) return p->alloc(bytes, p->actx);
   void *ptr = nullptr;
   if (cudaMalloc(&ptr, bytes) != cudaSuccess) return nullptr;
   return ptr;
 }
 
-void dev_free(ots_problem *p, void *ptr) {
+void problem_free(ots_problem *p, void *ptr) {
   if (!ptr) return;
   if (p->free_fn) p->free_fn(ptr, p->actx);
   else cudaFree(ptr);
 }
+
+}  // namespace ots_host
+
+namespace {
+
+void *dev_alloc(ots_problem *p, size_t bytes) { return problem_alloc(p, bytes); }
+
+void dev_free(ots_problem *p, void *ptr) { problem_free(p, ptr); }
 
 // Thread mapping for L commodities: G threads per node (power of two <= 256), C chunks of 4.
 bool choose_mapping(int L, int want_G, int &G, int &C, int &Lp) {
@@ -731,6 +735,7 @@ void ots_destroy_problem(ots_problem *p) {
   if (p->pass_exec) cudaGraphExecDestroy(p->pass_exec);
   for (int k = 0; k < 5; ++k)
     if (p->ev[k]) cudaEventDestroy(p->ev[k]);
+  linear_release(p);
   if (p->arena) dev_free(p, p->arena);
   if (p->h_report) cudaFreeHost(p->h_report);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
@@ -967,6 +972,7 @@ ots_status ots_host::build_problem_host(const ots_problem_desc *d, const CreateO
     }
     if (!p->cv) set_cap(s, dd);
   }
+  p->cap_nat = cap;
   // quantum of the hi parts: the magnitude of any message is bounded by about (T+1) times the
   // largest per-interval cost in bits; q = 2^k with that bound below 2^24 q keeps hi sums exact
   {
@@ -1515,6 +1521,152 @@ ots_status ots_sinkhorn_solve(ots_problem *p, const ots_solve_opts *opts, ots_so
   if (rep) *rep = r;
   return st;
 }
+
+namespace {
+
+constexpr int kLinearChunk = 2000;   // passes per launch of the linear-domain kernel
+
+void add_stats(ots_linear_stats *st, const LinReport &r, double ms) {
+  if (!st) return;
+  st->linear_passes += r.passes - r.log_passes;
+  st->log_passes += r.log_passes;
+  st->rescalings += r.rescalings;
+  st->kernel_ms += ms;
+}
+
+// Linear-domain passes on n problems until each is converged (tol) or has run max_passes, in
+// launches of kLinearChunk passes.  done[i]: passes run on problem i.
+ots_status linear_phase(ots_problem *const *ps, int n, int max_passes, double tol, int init, double timeout_ms,
+                        std::chrono::steady_clock::time_point t0, std::vector<int> &done, ots_linear_stats *stats) {
+  done.assign(n, 0);
+  int ran = 0;
+  for (bool first = true; ran < max_passes; first = false) {
+    const int chunk = std::min(kLinearChunk, max_passes - ran);
+    double ms = 0.0;
+    ots_status st = linear_run(ps, n, chunk, tol, first ? init : 0, &ms);
+    if (st) return st;
+    bool open = false;
+    for (int i = 0; i < n; ++i) {
+      const LinReport &r = linear_report(ps[i]);
+      done[i] += r.passes;
+      add_stats(stats, r, i == 0 ? ms : 0.0);
+      if (r.status == OTS_OK && !r.converged && r.passes > 0) open = true;
+    }
+    ran += chunk;
+    if (!open) break;
+    const double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_ms > 0 && el > timeout_ms) break;
+  }
+  return OTS_OK;
+}
+
+// Log-domain passes from the duals the linear phase left, until the measures of a pass are
+// <= tol: the result and its measures are those of the log-domain path.
+ots_status confirm(ots_problem *p, const ots_solve_opts &o, int budget, ots_solve_report &r, int &passes) {
+  passes = 0;
+  ots_status st = refresh_if_stale(p);
+  if (st) return st;
+  int k = 1;
+  while (true) {
+    st = run_passes(p, k, o.use_graph != 0);
+    if (st) return st;
+    passes += k;
+    st = read_report(p, &r);
+    if (st) return st;
+    if (r.src_residual <= o.tol && r.cap_violation <= o.tol) return OTS_OK;
+    if (passes >= budget) return fail(OTS_ERR_NOT_CONVERGED, "not converged (src %.3e, cap %.3e)", r.src_residual, r.cap_violation);
+    k = std::min(std::min(2 * k, o.check_every), budget - passes);   // 1, 2, 4, ... up to check_every
+  }
+}
+
+ots_status linear_opts(const ots_solve_opts *opts, ots_solve_opts &o) {
+  ots_default_solve_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || o.max_iters < 1 || o.check_every < 1) return fail(OTS_ERR_INVALID_ARG, "bad solve options");
+  if (o.eps_start > 0.0) return fail(OTS_ERR_INVALID_ARG, "epsilon continuation is not part of the linear-domain path");
+  return OTS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ots_status ots_linear_iterate(ots_problem *p, int32_t n, int32_t reset, ots_solve_report *rep, ots_linear_stats *stats) {
+  g_last_error.clear();
+  if (!p || n < 0) return fail(OTS_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard guard(p->dev);
+  if (stats) *stats = ots_linear_stats{};
+  auto t0 = std::chrono::steady_clock::now();
+  ots_status st = linear_prepare(p);
+  if (st) return st;
+  std::vector<int> done;
+  st = linear_phase(&p, 1, n, -1.0, reset ? 1 : 2, 0.0, t0, done, stats);
+  if (st) return st;
+  const LinReport &lr = linear_report(p);
+  ots_solve_report r{};
+  r.iterations = done[0];
+  r.src_residual = lr.src;
+  r.cap_violation = lr.cap;
+  r.dual_objective = NAN;
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  r.status = n > 0 ? lr.status : OTS_OK;
+  if (r.status) fail((ots_status)r.status, "linear-domain pass failed (status %d)", r.status);
+  if (rep) *rep = r;
+  return (ots_status)r.status;
+}
+
+ots_status ots_linear_solve_many(ots_problem *const *ps, int32_t n, const ots_solve_opts *opts, ots_solve_report *reps,
+                                 ots_linear_stats *stats) {
+  g_last_error.clear();
+  if (!ps || n < 1) return fail(OTS_ERR_INVALID_ARG, "bad arguments");
+  for (int i = 0; i < n; ++i) {
+    if (!ps[i]) return fail(OTS_ERR_INVALID_ARG, "problem %d is NULL", i);
+    if (ps[i]->dev != ps[0]->dev) return fail(OTS_ERR_INVALID_ARG, "problems on different devices");
+    for (int j = 0; j < i; ++j)
+      if (ps[j] == ps[i]) return fail(OTS_ERR_INVALID_ARG, "problem %d appears twice", i);
+  }
+  ots_solve_opts o;
+  ots_status st = linear_opts(opts, o);
+  if (st) return st;
+  DeviceGuard guard(ps[0]->dev);
+  if (stats) *stats = ots_linear_stats{};
+  auto t0 = std::chrono::steady_clock::now();
+  for (int i = 0; i < n; ++i) {
+    st = linear_prepare(ps[i]);
+    if (st) return fail(st, "problem %d: %s", i, ots_last_error());
+  }
+  std::vector<int> done;
+  st = linear_phase(ps, n, o.max_iters, o.tol, o.warm_start ? 2 : 1, o.timeout_ms, t0, done, stats);
+  if (st) return st;
+  ots_status worst = OTS_OK;
+  for (int i = 0; i < n; ++i) {
+    ots_solve_report r{};
+    const LinReport &lr = linear_report(ps[i]);
+    int cp = 0;
+    ots_status si = (ots_status)lr.status;
+    if (!si) {
+      DeviceGuard g(ps[i]->dev);
+      si = confirm(ps[i], o, std::max(1, o.max_iters - done[i]), r, cp);
+    } else {
+      r.src_residual = lr.src;
+      r.cap_violation = lr.cap;
+    }
+    if (stats) stats->confirm_passes += cp;
+    r.iterations = done[i] + cp;
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    r.status = si;
+    if (reps) reps[i] = r;
+    if (si && !worst) worst = si;
+  }
+  if (worst) fail(worst, "%s", n > 1 ? "not every problem was solved (see the per-problem reports)" : ots_last_error());
+  return worst;
+}
+
+ots_status ots_linear_solve(ots_problem *p, const ots_solve_opts *opts, ots_solve_report *rep, ots_linear_stats *stats) {
+  return ots_linear_solve_many(&p, 1, opts, rep, stats);
+}
+
+}  // extern "C"
 
 // Flows pass: recompute the forward messages at the current duals, writing the aggregate
 // flows P_t for t = 2..T-1 (Corollary 7).

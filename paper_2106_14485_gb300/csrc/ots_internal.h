@@ -39,7 +39,22 @@ cudaError_t launch_boundary_flows(int n, int Lp, QScale qs, const int *tri_l, co
                                   cudaStream_t s);
 }  // namespace ots
 
+namespace ots {
+// Result of the last launch of the linear-domain kernel on a problem (ots_linear.cu).
+struct LinReport {
+  int passes;       // passes of the launch
+  int log_passes;   // of which redone in log arithmetic
+  int rescalings;   // scale sweeps of the launch
+  int status;       // ots_status
+  int converged;    // measures <= tol after the last pass
+  int pad;
+  double src, cap;  // measures of the last pass (relative)
+};
+}  // namespace ots
+
 namespace ots_host {
+
+struct LinearData;   // device arrays of the linear-domain path (ots_linear.cu)
 
 // Records a formatted message for ots_last_error (per thread) and returns s.
 ots_status fail(ots_status s, const char *fmt, ...);
@@ -116,6 +131,21 @@ ots_status build_problem_host(const ots_problem_desc *d, const CreateOpts &co, o
 ots_status build_problem_device(ots_problem *p);
 ots_status create_problem_impl(const ots_problem_desc *d, const CreateOpts &co, ots_problem **out);
 
+// Device memory through the problem's allocator (ots_api.cu).
+void *problem_alloc(ots_problem *p, size_t bytes);
+void problem_free(ots_problem *p, void *ptr);
+
+// Linear-domain path for L = 1 (ots_linear.cu).  linear_prepare builds the problem's arrays once
+// (OTS_ERR_INVALID_ARG where the path does not apply); linear_run runs up to max_passes passes on
+// each of the n problems in one launch (one thread block each; all on one device, launched on
+// ps[0]'s stream), stopping each at tol (tol < 0: never).  init: 1 = from the initial duals,
+// 2 = from the problem's duals, 0 = continue the previous launch.  The duals are written back
+// to each problem (which is then marked stale); per-problem results in linear_report.
+ots_status linear_prepare(ots_problem *p);
+ots_status linear_run(ots_problem *const *ps, int n, int max_passes, double tol, int init, double *kernel_ms);
+const ots::LinReport &linear_report(const ots_problem *p);
+void linear_release(ots_problem *p);
+
 // Batch internals used by the server (ots_batch.cu).
 struct Pool;
 Pool *batch_pool(ots_batch *b);
@@ -156,6 +186,8 @@ struct ots_problem {
   float *d_uc = nullptr;                       // [T+1][S][Lp] log2 U^(0,t)
   std::vector<int> ta, tb;                     // [L] entry and exit time of each commodity
   std::vector<double> cost_nat;                // state costs in natural units ([S], or [T+1][S] rows when tv)
+  std::vector<double> cap_nat;                 // capacities ([S], or [T+1][S] rows when cv; inf: none)
+  ots_host::LinearData *lin = nullptr;         // linear-domain path (L = 1), built on first use
   std::vector<int> in_state_h;                 // in-CSR order of the states (host copy)
   std::unique_ptr<ots_host::HostArrays> host;  // between the host build and the upload
 

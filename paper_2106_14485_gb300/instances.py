@@ -393,6 +393,29 @@ def uneven_rgg_batch(seed: int = 0, count: int = 256, workers: int = 1):
         return list(ex.map(_uneven_rgg_member, specs, chunksize=4))
 
 
+def _uneven_single_member(args):
+    k, n, T, sub = args
+    inst = rgg_instance(seed=sub, n=n, L=1, T=T, eps=0.01, cap_div=2.0, name=f"s{k}-rgg{n}-L1-T{T}", connect="bridge")
+    inst.meta.update({"workload": "uneven_single_batch", "batch_index": k})
+    return inst
+
+
+def uneven_single_batch(seed: int = 0, count: int = 64, workers: int = 1):
+    """Single-commodity members with the sizes of the uneven batch: n~U{50..2000} RGG (bridged),
+    T~U{10..80}, L = 1, eps = 0.01, one OD pair of mass U[0.5, 2].  Capacities U[0.2,1] * mass / 2:
+    with one commodity, mass / 8 is below the cut the commodity has to cross and most instances
+    would admit no feasible flow; mass / 2 binds on the busiest edges and leaves most feasible."""
+    rng = np.random.default_rng(seed)
+    specs = [(k, int(rng.integers(50, 2001)), int(rng.integers(10, 81)), int(rng.integers(2**31 - 1)))
+             for k in range(count)]
+    if workers <= 1:
+        return [_uneven_single_member(s) for s in specs]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_uneven_single_member, specs, chunksize=4))
+
+
 def with_time_varying_costs(inst, seed: int = 0, lo: float = 0.5, hi: float = 2.0, closures: int = 0):
     """A time-varying network for an instance (Section 3.3, C_t): the per-interval cost of every
     state is its static cost times U[lo, hi], drawn per (t, state) for t = 2..T-1, and

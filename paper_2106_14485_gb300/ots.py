@@ -70,6 +70,14 @@ class SolveReport(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class LinearStats(ctypes.Structure):
+    _fields_ = [("linear_passes", ctypes.c_int32), ("log_passes", ctypes.c_int32), ("rescalings", ctypes.c_int32),
+                ("confirm_passes", ctypes.c_int32), ("kernel_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class BatchDesc(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p), ("pool_bytes", ctypes.c_int64),
                 ("max_instances", ctypes.c_int32), ("max_items", ctypes.c_int32),
@@ -97,7 +105,7 @@ class ServerStats(ctypes.Structure):
 
 EXPORTED = ["ots_default_solve_opts", "ots_create_problem", "ots_check_problem", "ots_sinkhorn_solve", "ots_iterate", "ots_get_flows",
             "ots_get_commodity_flows", "ots_get_commodity_flows_noalloc", "ots_get_duals", "ots_set_duals", "ots_problem_info", "ots_last_pass_timing",
-            "ots_set_wait_limit", "ots_problem_stream", "ots_destroy_problem", "ots_status_string", "ots_last_error",
+            "ots_set_wait_limit", "ots_linear_iterate", "ots_linear_solve", "ots_linear_solve_many", "ots_problem_stream", "ots_destroy_problem", "ots_status_string", "ots_last_error",
             "ots_default_batch_desc", "ots_batch_create", "ots_batch_add", "ots_batch_run", "ots_batch_status",
             "ots_batch_get_flows", "ots_batch_get_duals", "ots_batch_remove", "ots_batch_info", "ots_batch_mapping",
             "ots_batch_autotune", "ots_batch_destroy",
@@ -128,6 +136,12 @@ def load_library(path: str = LIB_PATH):
     lib.ots_get_duals.argtypes = [P, _f64p, _f64p, _f64p]
     lib.ots_set_duals.argtypes = [P, _f64p, _f64p, _f64p]
     lib.ots_set_wait_limit.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+    lib.ots_linear_iterate.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(SolveReport),
+                                       ctypes.POINTER(LinearStats)]
+    lib.ots_linear_solve.argtypes = [P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveReport),
+                                     ctypes.POINTER(LinearStats)]
+    lib.ots_linear_solve_many.argtypes = [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(SolveOpts),
+                                          ctypes.POINTER(SolveReport), ctypes.POINTER(LinearStats)]
     lib.ots_problem_info.argtypes = [P, ctypes.POINTER(ProblemStats)]
     lib.ots_last_pass_timing.argtypes = [P, _f64p]
     lib.ots_problem_stream.argtypes = [P]
@@ -344,6 +358,47 @@ def ots_iterate(h: Handle, n: int, reset: bool = False) -> dict:
     r = SolveReport()
     _check(load_library().ots_iterate(h.ptr, int(n), int(reset), ctypes.byref(r)))
     return r.as_dict()
+
+
+def _solve_opts(tol, max_iters, check_every, timeout_ms, warm_start, use_graph):
+    o = ots_default_solve_opts()
+    o.tol, o.max_iters, o.check_every, o.timeout_ms = tol, max_iters, check_every, timeout_ms
+    o.warm_start, o.use_graph = int(warm_start), int(use_graph)
+    return o
+
+
+def ots_linear_iterate(h: Handle, n: int, reset: bool = False) -> dict:
+    """n linear-domain passes (L = 1); the report of the last pass plus the pass counters."""
+    r, st = SolveReport(), LinearStats()
+    _check(load_library().ots_linear_iterate(h.ptr, int(n), int(reset), ctypes.byref(r), ctypes.byref(st)))
+    return dict(r.as_dict(), linear=st.as_dict())
+
+
+def ots_linear_solve(h: Handle, tol: float = 1e-6, max_iters: int = 100000, check_every: int = 10,
+                     timeout_ms: float = 0.0, warm_start: bool = False, use_graph: bool = True,
+                     raise_on_error: bool = True) -> dict:
+    """Linear-domain passes to tol, confirmed by log-domain passes (L = 1)."""
+    o = _solve_opts(tol, max_iters, check_every, timeout_ms, warm_start, use_graph)
+    r, st = SolveReport(), LinearStats()
+    code = load_library().ots_linear_solve(h.ptr, ctypes.byref(o), ctypes.byref(r), ctypes.byref(st))
+    if raise_on_error:
+        _check(code)
+    return dict(r.as_dict(), linear=st.as_dict())
+
+
+def ots_linear_solve_many(hs, tol: float = 1e-6, max_iters: int = 100000, check_every: int = 10,
+                          timeout_ms: float = 0.0, warm_start: bool = False, use_graph: bool = True,
+                          raise_on_error: bool = True):
+    """The same for several L = 1 problems in one launch; returns (per-problem reports, counters)."""
+    o = _solve_opts(tol, max_iters, check_every, timeout_ms, warm_start, use_graph)
+    n = len(hs)
+    arr = (ctypes.c_void_p * n)(*[h.ptr for h in hs])
+    reps = (SolveReport * n)()
+    st = LinearStats()
+    code = load_library().ots_linear_solve_many(arr, n, ctypes.byref(o), reps, ctypes.byref(st))
+    if raise_on_error and code != OTS_OK:
+        _check(code)
+    return [r.as_dict() for r in reps], st.as_dict()
 
 
 def ots_get_flows(h: Handle, t_begin: int = 1, t_end: int | None = None) -> np.ndarray:
