@@ -45,24 +45,64 @@ namespace ots {
 struct LinArgs {
   int V, S, T, krs, drs;             // krs / drs: row strides of kappa / logd (S if per interval, else 0)
   int n_src, n_snk, n_sseg, n_zseg;
-  double mass;                       // sum of R01
-  const int *in_ptr, *in_tail, *in_head, *in_state;   // in-CSR by head node (entry k = state in_state[k])
-  const int *out_ptr, *out_tail, *out_head, *out_to_in;  // out-CSR by tail node
+  int mode;                          // arrays in shared memory: 0 none, 1 index arrays, 2 all (see lin_layout)
+  float mass;                        // sum of R01
+  const int *in_ptr, *in_tail, *in_head, *in_state, *in_to_out;   // in-CSR by head node (entry k = state in_state[k])
+  const int *out_ptr, *out_tail, *out_head, *out_to_in;           // out-CSR by tail node
   const float2 *kappa;               // [rows][S] log2 K of in-entry k (float-float); x = -inf: closed
   const float2 *logd;                // [rows][S] log2 d of in-entry k; x = +inf: no capacity, -inf: d = 0
-  float *Gf, *Gb, *Dc, *Fc;          // [(T+1) S]: Gf, Dc, Fc by in-entry, Gb by out-entry
+  float *Gf, *Gb, *Dc, *Fc;          // [(T+1) S] by in-entry
   int *nu;                           // [(T+1) S] by in-entry
   float *w[2];                       // [(T+1) S] by in-entry: w_t (two buffers: current, next)
+  float *gbw;                        // [(T+1) S] by out-entry: Gb_t w_t of the state
   float *alpha, *beta, *bm;          // [(T+1) V]: scales and the scaled backward messages
   const int *sseg_node, *sseg_ptr, *zseg_node, *zseg_ptr;   // boundary entries grouped by node
-  const double *src_R, *src_logR, *snk_R, *snk_logR;       // per entry, log2
-  double *lU01[2], *lU0T[2];         // per entry, log2 (two buffers)
+  const float *src_R, *snk_R;        // per entry
+  const float2 *src_logR, *snk_logR; // per entry, log2 R (float-float)
+  float2 *lU01[2], *lU0T[2];         // per entry, log2 U01 / U0T (float-float, two buffers)
   const int *src_tri, *snk_tri;      // entry -> boundary triple of the problem
   float2 *p_logu;                    // problem's log2 u_t [(T+1) S] by state (float-float)
   double *p_src_logU, *p_snk_logU;   // problem's log2 U01 / U0T per triple
   LinReport *rep;
-  int cur, need, done, pad;          // state kept between launches
+  int cur, done;                     // state kept between launches
 };
+
+// Shared-memory layout of one problem (offsets in 4-byte words, 16-byte aligned): always the two
+// message rows and one value per entry (the per-entry terms of a step before the node sums);
+// mode >= 1 adds the index arrays, mode 2 every per-(t, entry) and per-(t, node) array.
+struct LinLayout {
+  size_t rows, c, in_ptr, out_ptr, in_tail, in_head, in_to_out, out_head;
+  size_t Gf, Gb, Dc, Fc, nu, w0, w1, gbw, bm, alpha, beta, words;
+};
+
+__host__ __device__ inline size_t lin_take(size_t &o, size_t n) {
+  const size_t r = o;
+  o += (n + 3) & ~(size_t)3;
+  return r;
+}
+
+__host__ __device__ inline LinLayout lin_layout(int V, int S, int T, int mode) {
+  LinLayout L{};
+  size_t o = 0;
+  L.rows = lin_take(o, 2 * (size_t)V);
+  L.c = lin_take(o, (size_t)S);
+  if (mode >= 1) {
+    L.in_ptr = lin_take(o, (size_t)V + 1);
+    L.out_ptr = lin_take(o, (size_t)V + 1);
+    L.in_tail = lin_take(o, (size_t)S);
+    L.in_head = lin_take(o, (size_t)S);
+    L.in_to_out = lin_take(o, (size_t)S);
+    L.out_head = lin_take(o, (size_t)S);
+  }
+  if (mode >= 2) {
+    const size_t TS = (size_t)(T + 1) * S, TV = (size_t)(T + 1) * V;
+    L.Gf = lin_take(o, TS); L.Gb = lin_take(o, TS); L.Dc = lin_take(o, TS); L.Fc = lin_take(o, TS);
+    L.nu = lin_take(o, TS); L.w0 = lin_take(o, TS); L.w1 = lin_take(o, TS); L.gbw = lin_take(o, TS);
+    L.bm = lin_take(o, TV); L.alpha = lin_take(o, TV); L.beta = lin_take(o, TV);
+  }
+  L.words = o;
+  return L;
+}
 
 namespace {
 
@@ -70,6 +110,73 @@ constexpr int kLinThreads = 512;
 constexpr float kLost = 0x1p60f, kDrift = 0x1p30f;
 constexpr float kLn2f = 0.693147180559945309f;
 constexpr float kNegLog = -1e30f;    // log 0 in the problem's float-float duals
+
+// Where the working arrays of a problem live for one launch (shared or global memory).
+struct Ptrs {
+  const int *in_ptr, *out_ptr, *in_tail, *in_head, *in_to_out, *out_head;
+  float *Gf, *Gb, *Dc, *Fc, *w[2], *gbw, *bm, *alpha, *beta, *rows, *c;
+  int *nu;
+};
+
+__device__ Ptrs make_ptrs(const LinArgs &a, float *dyn) {
+  const LinLayout L = lin_layout(a.V, a.S, a.T, a.mode);
+  Ptrs P;
+  P.rows = dyn + L.rows;
+  P.c = dyn + L.c;
+  if (a.mode >= 1) {
+    P.in_ptr = (const int *)(dyn + L.in_ptr); P.out_ptr = (const int *)(dyn + L.out_ptr);
+    P.in_tail = (const int *)(dyn + L.in_tail); P.in_head = (const int *)(dyn + L.in_head);
+    P.in_to_out = (const int *)(dyn + L.in_to_out); P.out_head = (const int *)(dyn + L.out_head);
+  } else {
+    P.in_ptr = a.in_ptr; P.out_ptr = a.out_ptr; P.in_tail = a.in_tail; P.in_head = a.in_head;
+    P.in_to_out = a.in_to_out; P.out_head = a.out_head;
+  }
+  if (a.mode >= 2) {
+    P.Gf = dyn + L.Gf; P.Gb = dyn + L.Gb; P.Dc = dyn + L.Dc; P.Fc = dyn + L.Fc; P.nu = (int *)(dyn + L.nu);
+    P.w[0] = dyn + L.w0; P.w[1] = dyn + L.w1; P.gbw = dyn + L.gbw; P.bm = dyn + L.bm;
+    P.alpha = dyn + L.alpha; P.beta = dyn + L.beta;
+  } else {
+    P.Gf = a.Gf; P.Gb = a.Gb; P.Dc = a.Dc; P.Fc = a.Fc; P.nu = a.nu; P.w[0] = a.w[0]; P.w[1] = a.w[1];
+    P.gbw = a.gbw; P.bm = a.bm; P.alpha = a.alpha; P.beta = a.beta;
+  }
+  return P;
+}
+
+__device__ void copy_words(void *dst, const void *src, size_t n) {
+  const int *s = (const int *)src;
+  int *d = (int *)dst;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
+}
+
+// Index arrays (mode >= 1) and the duals' working copies (mode 2) into shared memory.
+__device__ void stage_in(const LinArgs &a, const Ptrs &P, bool duals) {
+  const int V = a.V, S = a.S;
+  if (a.mode >= 1) {
+    copy_words((void *)P.in_ptr, a.in_ptr, V + 1);
+    copy_words((void *)P.out_ptr, a.out_ptr, V + 1);
+    copy_words((void *)P.in_tail, a.in_tail, S);
+    copy_words((void *)P.in_head, a.in_head, S);
+    copy_words((void *)P.in_to_out, a.in_to_out, S);
+    copy_words((void *)P.out_head, a.out_head, S);
+  }
+  if (a.mode >= 2 && duals) {
+    const size_t TS = (size_t)(a.T + 1) * S;
+    copy_words(P.w[0], a.w[0], TS);
+    copy_words(P.w[1], a.w[1], TS);
+    copy_words(P.nu, a.nu, TS);
+  }
+  __syncthreads();
+}
+
+// The duals' working copies back to global memory (mode 2), for the next launch.
+__device__ void stage_out(const LinArgs &a, const Ptrs &P) {
+  if (a.mode >= 2) {
+    const size_t TS = (size_t)(a.T + 1) * a.S;
+    copy_words(a.w[0], P.w[0], TS);
+    copy_words(a.w[1], P.w[1], TS);
+    copy_words(a.nu, P.nu, TS);
+  }
+}
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = __fadd_rn(a, b);
@@ -95,6 +202,29 @@ __device__ __forceinline__ FF ff_add(FF a, float2 b) {
   return r;
 }
 
+// a + b for float-float values, renormalised (the boundary duals and the measures)
+__device__ __forceinline__ FF ff_sum(FF a, FF b) {
+  FF r;
+  float e;
+  two_sum(a.h, b.h, r.h, e);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  two_sum(r.h, e, r.h, r.l);
+  return r;
+}
+
+__device__ __forceinline__ FF ff_of(float2 x) { return FF{x.x, x.y}; }
+__device__ __forceinline__ float2 f2_of(FF x) { return make_float2(x.h, x.l); }
+__device__ __forceinline__ FF ff_neg(FF x) { return FF{-x.h, -x.l}; }
+
+// log2 x of a positive float as float-float: the exponent exactly, log2f of the mantissa in [1/2, 1)
+__device__ __forceinline__ FF ff_log2(float x) {
+  int e;
+  const float m = frexpf(x, &e);
+  FF r;
+  two_sum((float)e, log2f(m), r.h, r.l);
+  return r;
+}
+
 // 2^(h + l + n) for a float-float exponent (h, l) (|l| small) and an integer n: the integer part of
 // h is applied exactly by ldexpf, the rest by exp2f on [-1/2, 1/2] and a first-order term in l.
 __device__ __forceinline__ float exp2_ff(FF e, int n) {
@@ -106,14 +236,18 @@ __device__ __forceinline__ float exp2_ff(FF e, int n) {
   return ldexpf(z, k);
 }
 
-// Block reductions in a fixed order (all threads get the result).
-__device__ double block_sum(double v, double *red) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// Block reductions in a fixed order (all threads get the result).  Sums are float-float: FP64 on
+// this part issues a warp instruction every 16 cycles, too slow for per-pass reductions.
+__device__ FF block_sum(FF v, float2 *red) {
+  for (int o = 16; o; o >>= 1) {
+    const FF w{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+    v = ff_sum(v, w);
+  }
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f2_of(v);
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  FF s{0.f, 0.f};
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s = ff_sum(s, ff_of(red[i]));
   return s;
 }
 
@@ -138,45 +272,60 @@ struct Range {
   }
 };
 
+// |P_new - P_old| of one capacity update with P = 2^(log2 u + ls) (FP32 terms).
+__device__ __forceinline__ float flow_change(float lo, float ln, float ls) {
+  if (lo == -INFINITY && ln == -INFINITY) return 0.f;
+  if (lo == -INFINITY) return exp2f(ln + ls);
+  if (ln == -INFINITY) return exp2f(lo + ls);
+  return exp2f(lo + ls) * fabsf(exp2f(ln - lo) - 1.f);
+}
+
+__device__ __forceinline__ double dbl(float2 x) { return (double)x.x + (double)x.y; }
+__device__ __forceinline__ float2 split(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
 // Scale sweep (update = false) or a whole pass of Algorithm 2 in FP32 log arithmetic
 // (update = true): alpha_t, beta_t become the base-2 logarithms of the messages.  With updates,
 // the new duals go to the next buffers (w[nxt], lU01/lU0T[nxt], nu in place) and the measures
 // to *mism, *resid; returns an ots_status (OTS_ERR_INFEASIBLE if a boundary state has no path).
-__device__ int log_sweep(const LinArgs &a, int cur, bool update, float *rows, double *mism_out, double *res_out,
-                         double *red) {
+__device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, FF *mism_out, FF *res_out,
+                         float2 *red) {
   const int V = a.V, S = a.S, T = a.T, nxt = cur ^ 1;
-  float *rp = rows, *rc = rows + V;
+  float *rp = P.rows, *rc = P.rows + V;
   int bad = 0;
-  double mism = 0.0, res = 0.0;
+  FF mism{0.f, 0.f}, res{0.f, 0.f};
   // beta_T[v] = log2 sum_{sink j, tail j = v} U0T(j)
   for (int v = threadIdx.x; v < V; v += blockDim.x) rp[v] = -INFINITY;
   __syncthreads();
   for (int s = threadIdx.x; s < a.n_zseg; s += blockDim.x) {
+    // (this sweep runs once per rescaling: FP64 for the few boundary entries)
     double m = -INFINITY;
-    for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) m = fmax(m, a.lU0T[cur][e]);
+    for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) m = fmax(m, dbl(a.lU0T[cur][e]));
     double acc = 0.0;
-    for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) acc += exp2(a.lU0T[cur][e] - m);
+    for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) acc += exp2(dbl(a.lU0T[cur][e]) - m);
     rp[a.zseg_node[s]] = (float)(m + log2(acc));
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < V; v += blockDim.x) a.beta[(size_t)T * V + v] = rp[v];
+  for (int v = threadIdx.x; v < V; v += blockDim.x) P.beta[(size_t)T * V + v] = rp[v];
   // beta_t[v] = log2 sum_{tail j = v} 2^(beta_{t+1}[head j] + log2 K(j) + log2 u_t(j)),  t = T-1..2
   for (int t = T - 1; t >= 2; --t) {
     for (int v = threadIdx.x; v < V; v += blockDim.x) {
       float m = -INFINITY, sum = 0.f;
-      for (int k = a.out_ptr[v]; k < a.out_ptr[v + 1]; ++k) {
+      for (int k = P.out_ptr[v]; k < P.out_ptr[v + 1]; ++k) {
         const int ki = a.out_to_in[k];
         const size_t q = (size_t)t * S + ki;
         const float2 kap = a.kappa[(size_t)t * a.krs + ki];
-        const float wv = a.w[cur][q];
-        const float lu = wv > 0.f ? (float)a.nu[q] + log2f(wv) : -INFINITY;
-        const float x = rp[a.out_head[k]] + kap.x + lu;
+        const float wv = P.w[cur][q];
+        const float lu = wv > 0.f ? (float)P.nu[q] + log2f(wv) : -INFINITY;
+        const float x = rp[P.out_head[k]] + kap.x + lu;
         if (x > m) { sum = sum * exp2f(m - x) + 1.f; m = x; }
         else if (x > -INFINITY) sum += exp2f(x - m);
       }
       const float r = m > -INFINITY ? m + log2f(sum) : -INFINITY;
       rc[v] = r;
-      a.beta[(size_t)t * V + v] = r;
+      P.beta[(size_t)t * V + v] = r;
     }
     __syncthreads();
     float *tmp = rp; rp = rc; rc = tmp;
@@ -188,52 +337,49 @@ __device__ int log_sweep(const LinArgs &a, int cur, bool update, float *rows, do
   for (int s = threadIdx.x; s < a.n_sseg; s += blockDim.x) {
     const int v = a.sseg_node[s];
     if (update) {
-      const double p1 = (double)a.beta[(size_t)2 * V + v];
+      const double p1 = (double)P.beta[(size_t)2 * V + v];
       for (int e = a.sseg_ptr[s]; e < a.sseg_ptr[s + 1]; ++e) {
         if (!(p1 > -INFINITY)) { bad = 1; a.lU01[nxt][e] = a.lU01[cur][e]; continue; }
-        const double ln = a.src_logR[e] - p1;
-        mism += a.src_R[e] * fabs(exp2(a.lU01[cur][e] - ln) - 1.0);
-        a.lU01[nxt][e] = ln;
+        const double ln = dbl(a.src_logR[e]) - p1;
+        mism = ff_add(mism, (float)(a.src_R[e] * fabs(exp2(dbl(a.lU01[cur][e]) - ln) - 1.0)));
+        a.lU01[nxt][e] = split(ln);
       }
     }
     double m = -INFINITY;
-    for (int e = a.sseg_ptr[s]; e < a.sseg_ptr[s + 1]; ++e) m = fmax(m, a.lU01[su][e]);
+    for (int e = a.sseg_ptr[s]; e < a.sseg_ptr[s + 1]; ++e) m = fmax(m, dbl(a.lU01[su][e]));
     double acc = 0.0;
-    for (int e = a.sseg_ptr[s]; e < a.sseg_ptr[s + 1]; ++e) acc += exp2(a.lU01[su][e] - m);
+    for (int e = a.sseg_ptr[s]; e < a.sseg_ptr[s + 1]; ++e) acc += exp2(dbl(a.lU01[su][e]) - m);
     rc[v] = (float)(m + log2(acc));
   }
   __syncthreads();
   { float *tmp = rp; rp = rc; rc = tmp; }
-  for (int v = threadIdx.x; v < V; v += blockDim.x) a.alpha[(size_t)V + v] = rp[v];
+  for (int v = threadIdx.x; v < V; v += blockDim.x) P.alpha[(size_t)V + v] = rp[v];
   // forward: capacity update of u_t (update) and alpha_t[v] = log2 sum_{head i = v} 2^(alpha_{t-1}[tail i]
   // + log2 K(i) + log2 u_t(i)),  t = 2..T-1
   for (int t = 2; t <= T - 1; ++t) {
+    float rsum = 0.f;
     for (int v = threadIdx.x; v < V; v += blockDim.x) {
-      const float bb = a.beta[(size_t)(t + 1) * V + v];
+      const float bb = P.beta[(size_t)(t + 1) * V + v];
       float m = -INFINITY, sum = 0.f;
-      for (int k = a.in_ptr[v]; k < a.in_ptr[v + 1]; ++k) {
+      for (int k = P.in_ptr[v]; k < P.in_ptr[v + 1]; ++k) {
         const size_t q = (size_t)t * S + k;
-        const float al = rp[a.in_tail[k]];
+        const float al = rp[P.in_tail[k]];
         const float2 kap = a.kappa[(size_t)t * a.krs + k];
         const float2 ld = a.logd[(size_t)t * a.drs + k];
         float lu = 0.f;
         if (ld.x != INFINITY) {
-          const float wv = a.w[cur][q];
-          const float lo = wv > 0.f ? (float)a.nu[q] + log2f(wv) : -INFINITY;
+          const float wv = P.w[cur][q];
+          const float lo = wv > 0.f ? (float)P.nu[q] + log2f(wv) : -INFINITY;
           lu = lo;
           if (update) {
             const float ls = al + bb + kap.x;
             float ln = 0.f;
             if (ls > -INFINITY) {
               ln = ld.x == -INFINITY ? -INFINITY : fminf(ld.x - ls, 0.f);
-              // |P_new - P_old| with P = 2^(log2 u + ls)
-              if (lo == -INFINITY && ln == -INFINITY) {}
-              else if (lo == -INFINITY) res += exp2((double)ln + ls);
-              else if (ln == -INFINITY) res += exp2((double)lo + ls);
-              else res += exp2((double)lo + ls) * fabs(exp2((double)ln - lo) - 1.0);
+              rsum += flow_change(lo, ln, ls);
             }
-            if (ln == -INFINITY) { a.w[nxt][q] = 0.f; a.nu[q] = 0; }
-            else { const float n = floorf(ln); a.w[nxt][q] = exp2f(ln - n); a.nu[q] = (int)n; }
+            if (ln == -INFINITY) { P.w[nxt][q] = 0.f; P.nu[q] = 0; }
+            else { const float n = floorf(ln); P.w[nxt][q] = exp2f(ln - n); P.nu[q] = (int)n; }
             lu = ln;
           }
         }
@@ -243,8 +389,9 @@ __device__ int log_sweep(const LinArgs &a, int cur, bool update, float *rows, do
       }
       const float r = m > -INFINITY ? m + log2f(sum) : -INFINITY;
       rc[v] = r;
-      a.alpha[(size_t)t * V + v] = r;
+      P.alpha[(size_t)t * V + v] = r;
     }
+    res = ff_add(res, rsum);
     __syncthreads();
     float *tmp = rp; rp = rc; rc = tmp;
   }
@@ -254,55 +401,51 @@ __device__ int log_sweep(const LinArgs &a, int cur, bool update, float *rows, do
       const double p = (double)rp[a.zseg_node[s]];
       for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) {
         if (!(p > -INFINITY)) { bad = 1; a.lU0T[nxt][e] = a.lU0T[cur][e]; continue; }
-        a.lU0T[nxt][e] = a.snk_logR[e] - p;
+        a.lU0T[nxt][e] = split(dbl(a.snk_logR[e]) - p);
       }
     }
   }
   __syncthreads();
-  const double ms = block_sum(mism, red);
-  const double rs = block_sum(res, red);
-  const double bd = block_sum((double)bad, red);
+  const FF ms = block_sum(mism, red);
+  const FF rs = block_sum(res, red);
+  const FF bd = block_sum(FF{(float)bad, 0.f}, red);
   if (mism_out) *mism_out = ms;
   if (res_out) *res_out = rs;
-  return bd > 0.0 ? OTS_ERR_INFEASIBLE : OTS_OK;
+  return bd.h > 0.f ? OTS_ERR_INFEASIBLE : OTS_OK;
 }
 
 // Scale fold: w_t(i) = m 2^e with m in [1/2, 1) -> w = m, nu += e (exact).  Then the per-state
-// factors Gf, Gb, Dc, Fc from the current scales alpha, beta, nu.
-__device__ void rebuild(const LinArgs &a, int cur) {
+// factors Gf, Gb, Dc, Fc and the backward weights gbw = Gb w from the current scales.
+__device__ void rebuild(const LinArgs &a, const Ptrs &P, int cur) {
   const int V = a.V, S = a.S, T = a.T;
   const int n = (T - 2) * S;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int t = 2 + idx / S, k = idx - (t - 2) * S;
     const size_t q = (size_t)t * S + k;
-    const float2 ld = a.logd[(size_t)t * a.drs + k];
-    if (ld.x != INFINITY) {
-      const float wv = a.w[cur][q];
-      if (wv > 0.f) {
-        int e;
-        const float m = frexpf(wv, &e);
-        a.w[cur][q] = m;
-        a.nu[q] += e;
-      }
-    }
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const int t = 2 + idx / S, k = idx - (t - 2) * S;
-    const size_t q = (size_t)t * S + k;
     const float2 kap = a.kappa[(size_t)t * a.krs + k];
     const float2 ld = a.logd[(size_t)t * a.drs + k];
-    const float al0 = a.alpha[(size_t)(t - 1) * V + a.in_tail[k]];
-    const float al1 = a.alpha[(size_t)t * V + a.in_head[k]];
-    const float be1 = a.beta[(size_t)(t + 1) * V + a.in_head[k]];
-    const int nu = a.nu[q];
+    const int y = P.in_tail[k], v = P.in_head[k];
+    float wv = P.w[cur][q];
+    int nu = P.nu[q];
+    if (ld.x != INFINITY && wv > 0.f) {
+      int e;
+      wv = frexpf(wv, &e);
+      nu += e;
+      P.w[cur][q] = wv;
+      P.nu[q] = nu;
+    }
+    const float al0 = P.alpha[(size_t)(t - 1) * V + y], al1 = P.alpha[(size_t)t * V + v];
+    const float be1 = P.beta[(size_t)(t + 1) * V + v], be0 = P.beta[(size_t)t * V + y];
     const bool open = kap.x > -INFINITY;
-    float gf = 0.f;
+    float gf = 0.f, gb = 0.f;
     if (open && al0 > -INFINITY && al1 > -INFINITY) gf = exp2_ff(ff_add(ff_add(FF{al0, 0.f}, -al1), kap), nu);
-    a.Gf[q] = gf;
+    if (open && be1 > -INFINITY && be0 > -INFINITY) gb = exp2_ff(ff_add(ff_add(FF{be1, 0.f}, -be0), kap), nu);
+    P.Gf[q] = gf;
+    P.Gb[q] = gb;
+    P.gbw[(size_t)t * S + P.in_to_out[k]] = gb * wv;
     if (ld.x == INFINITY) {
-      a.Dc[q] = INFINITY;   // no capacity: w stays 1
-      a.Fc[q] = 0.f;
+      P.Dc[q] = INFINITY;   // no capacity: w stays 1
+      P.Fc[q] = 0.f;
     } else {
       float fc = 0.f, dc = FLT_MAX;
       if (open && al0 > -INFINITY && be1 > -INFINITY) {
@@ -315,144 +458,175 @@ __device__ void rebuild(const LinArgs &a, int cur) {
           dc = fminf(exp2_ff(g, -nu), FLT_MAX);
         }
       }
-      a.Fc[q] = fc;
-      a.Dc[q] = dc;
+      P.Fc[q] = fc;
+      P.Dc[q] = dc;
     }
-  }
-  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const int t = 2 + idx / S, k = idx - (t - 2) * S;
-    const int ki = a.out_to_in[k];
-    const float2 kap = a.kappa[(size_t)t * a.krs + ki];
-    const float b1 = a.beta[(size_t)(t + 1) * V + a.out_head[k]];
-    const float b0 = a.beta[(size_t)t * V + a.out_tail[k]];
-    float gb = 0.f;
-    if (kap.x > -INFINITY && b1 > -INFINITY && b0 > -INFINITY)
-      gb = exp2_ff(ff_add(ff_add(FF{b1, 0.f}, -b0), kap), a.nu[(size_t)t * S + ki]);
-    a.Gb[(size_t)t * S + k] = gb;
   }
   __syncthreads();
 }
 
-// One pass of Algorithm 2 on the scaled quantities; new duals to the next buffers.  Returns
-// 1 if a scaled value left [2^-60, 2^60] (the pass must be redone), sets *drift if one left
-// [2^-30, 2^30], and the measures (unnormalised) in *mism, *resid.
-__device__ int linear_pass(const LinArgs &a, int cur, float *rows, double *mism_out, double *res_out, int *drift,
-                           double *red, float *redf) {
+// One pass of Algorithm 2 on the scaled quantities; new duals to the next buffers.  Each step
+// has two phases: one thread per state entry computes its term (independent loads, several
+// entries' loads issued before any is used), then one thread per node adds the terms of its
+// entries in a fixed order.  Returns 1 if a scaled value left [2^-60, 2^60] (the pass must be
+// redone), sets *drift if one left [2^-30, 2^30], and the measures (unnormalised) in *mism,
+// *resid.  The boundary duals are float-float base-2 logarithms (about 48 bits).
+constexpr int kBatch = 4;   // entries per thread whose loads are in flight together
+
+__device__ int linear_pass(const LinArgs &a, const Ptrs &P, int cur, FF *mism_out, FF *res_out, int *drift,
+                           float2 *red, float *redf) {
   const int V = a.V, S = a.S, T = a.T, nxt = cur ^ 1;
-  float *rp = rows, *rc = rows + V;
+  float *rp = P.rows, *rc = P.rows + V, *c = P.c;
+  const int nt = blockDim.x;
   Range rg;
   int lost = 0;
-  double mism = 0.0, res = 0.0;
+  FF mism{0.f, 0.f}, res{0.f, 0.f};
   // b_T[v] = sum_{sink j, tail j = v} U0T(j) 2^-beta_T[v]
-  for (int v = threadIdx.x; v < V; v += blockDim.x) rp[v] = 0.f;
+  for (int v = threadIdx.x; v < V; v += nt) rp[v] = 0.f;
   __syncthreads();
-  for (int s = threadIdx.x; s < a.n_zseg; s += blockDim.x) {
+  for (int s = threadIdx.x; s < a.n_zseg; s += nt) {
     const int v = a.zseg_node[s];
-    const double sc = (double)a.beta[(size_t)T * V + v];
-    double acc = 0.0;
-    for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) acc += exp2(a.lU0T[cur][e] - sc);
-    const float f = (float)acc;
-    rg.see(f);
-    rp[v] = f;
+    const float sc = P.beta[(size_t)T * V + v];
+    float acc = 0.f;
+    for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) acc += exp2_ff(ff_add(ff_of(a.lU0T[cur][e]), -sc), 0);
+    rg.see(acc);
+    rp[v] = acc;
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < V; v += blockDim.x) a.bm[(size_t)T * V + v] = rp[v];
-  // backward sweep, t = T-1..2
+  for (int v = threadIdx.x; v < V; v += nt) P.bm[(size_t)T * V + v] = rp[v];
+  // backward sweep, t = T-1..2: term of out-entry j = b_{t+1}[head j] Gb_t(j) w_t(j)
   for (int t = T - 1; t >= 2; --t) {
-    const float *Gb = a.Gb + (size_t)t * S;
-    const float *wt = a.w[cur] + (size_t)t * S;
-    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+    const float *gw = P.gbw + (size_t)t * S;
+    for (int k0 = threadIdx.x; k0 < S; k0 += kBatch * nt) {
+      int hd[kBatch];
+      float g[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = k0 + j * nt;
+        hd[j] = k < S ? P.out_head[k] : 0;
+        g[j] = k < S ? gw[k] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = k0 + j * nt;
+        if (k < S) c[k] = rp[hd[j]] * g[j];
+      }
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += nt) {
       float acc = 0.f;
-      for (int k = a.out_ptr[v]; k < a.out_ptr[v + 1]; ++k)
-        acc = fmaf(rp[a.out_head[k]], Gb[k] * wt[a.out_to_in[k]], acc);
+      for (int k = P.out_ptr[v]; k < P.out_ptr[v + 1]; ++k) acc += c[k];
       rg.see(acc);
       rc[v] = acc;
-      a.bm[(size_t)t * V + v] = acc;
+      P.bm[(size_t)t * V + v] = acc;
     }
     __syncthreads();
     float *tmp = rp; rp = rc; rc = tmp;
   }
   // rp = b_2.  Source update U01 <- R01 / Psi_1 (mismatch taken before), then
   // a_1[v] = sum_{source i, head i = v} U01(i) 2^-alpha_1[v]
-  for (int v = threadIdx.x; v < V; v += blockDim.x) rc[v] = 0.f;
+  for (int v = threadIdx.x; v < V; v += nt) rc[v] = 0.f;
   __syncthreads();
-  for (int s = threadIdx.x; s < a.n_sseg; s += blockDim.x) {
+  for (int s = threadIdx.x; s < a.n_sseg; s += nt) {
     const int v = a.sseg_node[s];
     const float bb = rp[v];
-    const double p1 = (double)a.beta[(size_t)2 * V + v] + (bb > 0.f ? log2((double)bb) : 0.0);
-    const double sc = (double)a.alpha[(size_t)V + v];
-    double acc = 0.0;
+    const FF p1 = bb > 0.f ? ff_add(ff_log2(bb), P.beta[(size_t)2 * V + v]) : FF{0.f, 0.f};
+    const float sc = P.alpha[(size_t)V + v];
+    float acc = 0.f;
     for (int e = a.sseg_ptr[s]; e < a.sseg_ptr[s + 1]; ++e) {
-      double ln = a.lU01[cur][e];
+      const FF lo = ff_of(a.lU01[cur][e]);
+      FF ln = lo;
       if (bb > 0.f) {
-        ln = a.src_logR[e] - p1;
-        mism += a.src_R[e] * fabs(exp2(a.lU01[cur][e] - ln) - 1.0);
+        ln = ff_sum(ff_of(a.src_logR[e]), ff_neg(p1));
+        const FF d = ff_sum(lo, ff_neg(ln));
+        mism = ff_add(mism, a.src_R[e] * fabsf(expm1f((d.h + d.l) * kLn2f)));
       } else {
         lost = 1;
       }
-      a.lU01[nxt][e] = ln;
-      acc += exp2(ln - sc);
+      a.lU01[nxt][e] = f2_of(ln);
+      acc += exp2_ff(ff_add(ln, -sc), 0);
     }
-    const float f = (float)acc;
-    rg.see(f);
-    rc[v] = f;
+    rg.see(acc);
+    rc[v] = acc;
   }
   __syncthreads();
   { float *tmp = rp; rp = rc; rc = tmp; }
-  // forward sweep with the capacity updates, t = 2..T-1
+  // forward sweep with the capacity updates, t = 2..T-1: term of in-entry i =
+  // a_{t-1}[tail i] Gf_t(i) w_t(i), w_t(i) updated first where the state has a capacity
   for (int t = 2; t <= T - 1; ++t) {
     const size_t o = (size_t)t * S;
-    const float *bn = a.bm + (size_t)(t + 1) * V;
-    float rsum = 0.f;
-    for (int v = threadIdx.x; v < V; v += blockDim.x) {
-      const float bb = bn[v];
-      float acc = 0.f;
-      for (int k = a.in_ptr[v]; k < a.in_ptr[v + 1]; ++k) {
-        const float a0 = rp[a.in_tail[k]];
-        float g = a.Gf[o + k];
-        const float dc = a.Dc[o + k];
-        if (dc != INFINITY) {
-          const float x = a0 * bb;
-          const float uc = ldexpf(1.f, -a.nu[o + k]);
-          const float un = x > 0.f ? fminf(__fdiv_rn(dc, x), uc) : uc;
-          rsum += fabsf(un - a.w[cur][o + k]) * fminf(x * a.Fc[o + k], FLT_MAX);
-          a.w[nxt][o + k] = un;
+    const float *bn = P.bm + (size_t)(t + 1) * V;
+    FF rsum{0.f, 0.f};
+    for (int k0 = threadIdx.x; k0 < S; k0 += kBatch * nt) {
+      int ti[kBatch], hi[kBatch], nu[kBatch];
+      float gf[kBatch], dc[kBatch], wo[kBatch], fc[kBatch], gb[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = k0 + j * nt;
+        const bool in = k < S;
+        ti[j] = in ? P.in_tail[k] : 0;
+        hi[j] = in ? P.in_head[k] : 0;
+        gf[j] = in ? P.Gf[o + k] : 0.f;
+        dc[j] = in ? P.Dc[o + k] : INFINITY;
+        nu[j] = in ? P.nu[o + k] : 0;
+        wo[j] = in ? P.w[cur][o + k] : 0.f;
+        fc[j] = in ? P.Fc[o + k] : 0.f;
+        gb[j] = in ? P.Gb[o + k] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = k0 + j * nt;
+        if (k >= S) continue;
+        const float a0 = rp[ti[j]];
+        float g = gf[j];
+        if (dc[j] != INFINITY) {
+          const float x = a0 * bn[hi[j]];
+          const float uc = ldexpf(1.f, -nu[j]);
+          const float un = x > 0.f ? fminf(__fdiv_rn(dc[j], x), uc) : uc;
+          rsum = ff_add(rsum, fabsf(un - wo[j]) * fminf(x * fc[j], FLT_MAX));
+          P.w[nxt][o + k] = un;
+          P.gbw[o + P.in_to_out[k]] = gb[j] * un;
           if (un > 0.f) rg.lo = fminf(rg.lo, un);   // u_t must not drop out of the FP32 range
           g *= un;
         }
-        acc = fmaf(a0, g, acc);
+        c[k] = a0 * g;
       }
+    }
+    res = ff_sum(res, rsum);
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += nt) {
+      float acc = 0.f;
+      for (int k = P.in_ptr[v]; k < P.in_ptr[v + 1]; ++k) acc += c[k];
       rg.see(acc);
       rc[v] = acc;
     }
-    res += (double)rsum;
     __syncthreads();
     float *tmp = rp; rp = rc; rc = tmp;
   }
   // rp = a_{T-1}.  Sink update U0T <- R0T / hatPsi_T
-  for (int s = threadIdx.x; s < a.n_zseg; s += blockDim.x) {
+  for (int s = threadIdx.x; s < a.n_zseg; s += nt) {
     const int v = a.zseg_node[s];
     const float aa = rp[v];
-    const double p = (double)a.alpha[(size_t)(T - 1) * V + v] + (aa > 0.f ? log2((double)aa) : 0.0);
+    const FF p = aa > 0.f ? ff_add(ff_log2(aa), P.alpha[(size_t)(T - 1) * V + v]) : FF{0.f, 0.f};
     for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) {
-      if (aa > 0.f) a.lU0T[nxt][e] = a.snk_logR[e] - p;
+      if (aa > 0.f) a.lU0T[nxt][e] = f2_of(ff_sum(ff_of(a.snk_logR[e]), ff_neg(p)));
       else { a.lU0T[nxt][e] = a.lU0T[cur][e]; lost = 1; }
     }
   }
   __syncthreads();
   *mism_out = block_sum(mism, red);
   *res_out = block_sum(res, red);
-  const double nlost = block_sum((double)(lost | (rg.bad ? 1 : 0)), red);
+  const FF nlost = block_sum(FF{(float)(lost | (rg.bad ? 1 : 0)), 0.f}, red);
   const float hi = block_max(rg.hi, redf);
   const float inv_lo = block_max(rg.lo > 0.f ? 1.f / rg.lo : 0.f, redf);
   *drift = (hi > kDrift || inv_lo > kDrift) ? 1 : 0;
-  return (nlost > 0.0 || hi > kLost || inv_lo > kLost) ? 1 : 0;
+  return (nlost.h > 0.f || hi > kLost || inv_lo > kLost) ? 1 : 0;
 }
 
 // Duals in from the problem (init = 2), or the initialisation of Algorithm 2 (init = 1:
 // u_t = 1, U01 = U0T = 1 on the supports).  States without a capacity at t keep w = 1, nu = 0 in
 // both buffers.
-__device__ void load_duals(const LinArgs &a, int cur, int init) {
+__device__ void load_duals(const LinArgs &a, const Ptrs &P, int cur, int init) {
   const int S = a.S, T = a.T, n = (T - 2) * S;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int t = 2 + idx / S, k = idx - (t - 2) * S;
@@ -469,17 +643,19 @@ __device__ void load_duals(const LinArgs &a, int cur, int init) {
         nu = (int)n0;
       }
     }
-    a.w[cur][q] = wv;
-    a.nu[q] = nu;
-    if (ld.x == INFINITY) a.w[cur ^ 1][q] = 1.f;
+    P.w[cur][q] = wv;
+    P.nu[q] = nu;
+    if (ld.x == INFINITY) P.w[cur ^ 1][q] = 1.f;
   }
-  for (int e = threadIdx.x; e < a.n_src; e += blockDim.x) a.lU01[cur][e] = init == 2 ? a.p_src_logU[a.src_tri[e]] : 0.0;
-  for (int e = threadIdx.x; e < a.n_snk; e += blockDim.x) a.lU0T[cur][e] = init == 2 ? a.p_snk_logU[a.snk_tri[e]] : 0.0;
+  for (int e = threadIdx.x; e < a.n_src; e += blockDim.x)
+    a.lU01[cur][e] = init == 2 ? split(a.p_src_logU[a.src_tri[e]]) : make_float2(0.f, 0.f);
+  for (int e = threadIdx.x; e < a.n_snk; e += blockDim.x)
+    a.lU0T[cur][e] = init == 2 ? split(a.p_snk_logU[a.snk_tri[e]]) : make_float2(0.f, 0.f);
   __syncthreads();
 }
 
 // Duals out to the problem: log2 u_t = nu + log2 w as a float-float pair; U01, U0T per triple.
-__device__ void store_duals(const LinArgs &a, int cur) {
+__device__ void store_duals(const LinArgs &a, const Ptrs &P, int cur) {
   const int S = a.S, T = a.T, n = (T - 2) * S;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int t = 2 + idx / S, k = idx - (t - 2) * S;
@@ -487,10 +663,10 @@ __device__ void store_duals(const LinArgs &a, int cur) {
     const float2 ld = a.logd[(size_t)t * a.drs + k];
     float2 lu = make_float2(0.f, 0.f);
     if (ld.x != INFINITY) {
-      const float wv = a.w[cur][q];
+      const float wv = P.w[cur][q];
       if (wv > 0.f) {
         float h, l;
-        two_sum((float)a.nu[q], log2f(wv), h, l);
+        two_sum((float)P.nu[q], log2f(wv), h, l);
         lu = make_float2(h, l);
       } else {
         lu = make_float2(kNegLog, 0.f);
@@ -498,21 +674,23 @@ __device__ void store_duals(const LinArgs &a, int cur) {
     }
     a.p_logu[(size_t)t * S + a.in_state[k]] = lu;
   }
-  for (int e = threadIdx.x; e < a.n_src; e += blockDim.x) a.p_src_logU[a.src_tri[e]] = a.lU01[cur][e];
-  for (int e = threadIdx.x; e < a.n_snk; e += blockDim.x) a.p_snk_logU[a.snk_tri[e]] = a.lU0T[cur][e];
+  for (int e = threadIdx.x; e < a.n_src; e += blockDim.x) a.p_src_logU[a.src_tri[e]] = dbl(a.lU01[cur][e]);
+  for (int e = threadIdx.x; e < a.n_snk; e += blockDim.x) a.p_snk_logU[a.snk_tri[e]] = dbl(a.lU0T[cur][e]);
 }
 
 struct LinShared {
   LinArgs a;
-  double red[32];
+  Ptrs P;
+  float2 red[32];
   float redf[32];
 };
 
 // Up to max_passes passes on problem blockIdx.x, stopping at tol (tol < 0: never).  init: 0 =
-// continue (state kept in the argument block), 1 = initial duals, 2 = the problem's duals.
+// continue the previous launch, 1 = initial duals, 2 = the problem's duals.  Every launch starts
+// with a scale sweep (it does not change the iterate).
 __global__ void __launch_bounds__(kLinThreads) k_linear(LinArgs *const *args, int max_passes, double tol, int init) {
   __shared__ LinShared sh;
-  extern __shared__ float rows[];   // [2][V]
+  extern __shared__ __align__(16) float dyn[];
   LinArgs *g = args[blockIdx.x];
   if (threadIdx.x == 0) sh.a = *g;
   __syncthreads();
@@ -521,48 +699,53 @@ __global__ void __launch_bounds__(kLinThreads) k_linear(LinArgs *const *args, in
     if (threadIdx.x == 0) { a.rep->passes = 0; a.rep->log_passes = 0; a.rep->rescalings = 0; }
     return;
   }
-  int cur = a.cur, need = init ? 1 : a.need;
-  if (init) load_duals(a, cur, init);
+  if (threadIdx.x == 0) sh.P = make_ptrs(a, dyn);
+  __syncthreads();
+  const Ptrs &P = sh.P;
+  stage_in(a, P, init == 0);
+  int cur = a.cur, need = 1;
+  if (init) load_duals(a, P, cur, init);
   int passes = 0, log_passes = 0, rescalings = 0, status = OTS_OK, converged = 0;
-  double src = 0.0, cap = 0.0;
+  const float tolf = (float)tol;
+  FF mism{0.f, 0.f}, res{0.f, 0.f};
   while (passes < max_passes) {
     if (need) {
-      status = log_sweep(a, cur, false, rows, nullptr, nullptr, sh.red);
+      status = log_sweep(a, P, cur, false, nullptr, nullptr, sh.red);
       if (status) break;
-      rebuild(a, cur);
+      rebuild(a, P, cur);
       ++rescalings;
       need = 0;
     }
-    double mism, res;
     int drift = 0;
-    const int lost = linear_pass(a, cur, rows, &mism, &res, &drift, sh.red, sh.redf);
+    const int lost = linear_pass(a, P, cur, &mism, &res, &drift, sh.red, sh.redf);
     if (lost) {
       // thrown away: the same pass again in log arithmetic, from the same duals
-      status = log_sweep(a, cur, true, rows, &mism, &res, sh.red);
+      status = log_sweep(a, P, cur, true, &mism, &res, sh.red);
       cur ^= 1;
       ++log_passes;
       if (status) { ++passes; break; }
-      rebuild(a, cur);
+      rebuild(a, P, cur);
       ++rescalings;
     } else {
       cur ^= 1;
       need = drift;
     }
     ++passes;
-    src = mism / a.mass;
-    cap = res / a.mass;
-    if (!(src == src) || !(cap == cap)) { status = OTS_ERR_NUMERIC; break; }
-    if (!lost && src <= tol && cap <= tol) { converged = 1; break; }
+    const float srcf = (mism.h + mism.l) / a.mass, capf = (res.h + res.l) / a.mass;
+    if (!(srcf == srcf) || !(capf == capf)) { status = OTS_ERR_NUMERIC; break; }
+    if (!lost && srcf <= tolf && capf <= tolf) { converged = 1; break; }
   }
   __syncthreads();
-  store_duals(a, cur);
+  store_duals(a, P, cur);
+  stage_out(a, P);
   if (threadIdx.x == 0) {
     g->cur = cur;
-    g->need = need;
     g->done = converged || status != OTS_OK;
     LinReport r;
     r.passes = passes; r.log_passes = log_passes; r.rescalings = rescalings; r.status = status;
-    r.converged = converged; r.pad = 0; r.src = src; r.cap = cap;
+    r.converged = converged; r.pad = 0;
+    r.src = ((double)mism.h + (double)mism.l) / a.mass;
+    r.cap = ((double)res.h + (double)res.l) / a.mass;
     *a.rep = r;
   }
 }
@@ -589,6 +772,10 @@ struct LinearData {
 
 namespace {
 
+constexpr size_t kLinSmemAll = 96 * 1024;     // whole problem in shared memory up to this size
+constexpr size_t kLinSmemIndex = 96 * 1024;   // index arrays too up to this size
+constexpr int kLinSmemMax = 200 * 1024;       // two message rows + per-entry terms must fit
+
 struct Bump {
   size_t off = 0;
   size_t take(size_t bytes) {
@@ -613,11 +800,10 @@ ots_status linear_prepare(ots_problem *p) {
     return fail(OTS_ERR_INVALID_ARG, "the linear-domain path takes the node-level state graph with state costs and "
                                      "capacities only (no explicit state graph, windows or per-commodity data)");
   if (p->member) return fail(OTS_ERR_INVALID_ARG, "problem belongs to a batch");
-  if (p->V > 16384) return fail(OTS_ERR_INVALID_ARG, "the linear-domain path holds two message rows of %d nodes in shared memory (at most 16384)", p->V);
   const int V = p->V, S = p->S, T = p->T;
   // in-CSR by head node, out-CSR by tail node
   std::vector<int> in_ptr(V + 1, 0), out_ptr(V + 1, 0), in_state(S), in_tail(S), in_head(S), pos_in(S);
-  std::vector<int> out_tail(S), out_head(S), out_to_in(S);
+  std::vector<int> out_tail(S), out_head(S), out_to_in(S), in_to_out(S);
   for (int s = 0; s < S; ++s) { ++in_ptr[p->head[s] + 1]; ++out_ptr[p->tail[s] + 1]; }
   for (int v = 0; v < V; ++v) { in_ptr[v + 1] += in_ptr[v]; out_ptr[v + 1] += out_ptr[v]; }
   {
@@ -628,7 +814,7 @@ ots_status linear_prepare(ots_problem *p) {
     }
     for (int s = 0; s < S; ++s) {
       const int k = fo[p->tail[s]]++;
-      out_tail[k] = p->tail[s]; out_head[k] = p->head[s]; out_to_in[k] = pos_in[s];
+      out_tail[k] = p->tail[s]; out_head[k] = p->head[s]; out_to_in[k] = pos_in[s]; in_to_out[pos_in[s]] = k;
     }
   }
   // log2 K and log2 d per in-entry (rows t when they vary with t)
@@ -650,7 +836,8 @@ ots_status linear_prepare(ots_problem *p) {
   // boundary entries grouped by node (head of a source state, tail of a sink state)
   struct Side {
     std::vector<int> seg_node, seg_ptr, tri;
-    std::vector<double> R, logR;
+    std::vector<float> R;
+    std::vector<float2> logR;
   } side[2];
   double mass = 0.0;
   for (int b = 0; b < 2; ++b) {
@@ -664,8 +851,10 @@ ots_status linear_prepare(ots_problem *p) {
       const int q = order[i];
       if (i == 0 || node(q) != node(order[i - 1])) { sd.seg_node.push_back(node(q)); sd.seg_ptr.push_back(i); }
       sd.tri.push_back(q);
-      sd.R.push_back(bd.tri_R[q]);
-      sd.logR.push_back(std::log2(bd.tri_R[q]));
+      sd.R.push_back((float)bd.tri_R[q]);
+      float2 lr;
+      split_log2(std::log2(bd.tri_R[q]), lr);
+      sd.logR.push_back(lr);
       if (b == 0) mass += bd.tri_R[q];
     }
     sd.seg_ptr.push_back(bd.n);
@@ -677,13 +866,14 @@ ots_status linear_prepare(ots_problem *p) {
   const int nss = (int)side[0].seg_node.size(), nzs = (int)side[1].seg_node.size();
   const size_t o_in_ptr = m.take(4 * (V + 1)), o_in_tail = m.take(4 * S), o_in_head = m.take(4 * S),
                o_in_state = m.take(4 * S), o_out_ptr = m.take(4 * (V + 1)), o_out_tail = m.take(4 * S),
-               o_out_head = m.take(4 * S), o_out_to_in = m.take(4 * S), o_kappa = m.take(8 * kappa.size()),
+               o_out_head = m.take(4 * S), o_out_to_in = m.take(4 * S), o_in_to_out = m.take(4 * S),
+               o_gbw = m.take(4 * TS), o_kappa = m.take(8 * kappa.size()),
                o_logd = m.take(8 * logd.size()), o_gf = m.take(4 * TS), o_gb = m.take(4 * TS), o_dc = m.take(4 * TS),
                o_fc = m.take(4 * TS), o_nu = m.take(4 * TS), o_w0 = m.take(4 * TS), o_w1 = m.take(4 * TS),
                o_alpha = m.take(4 * TV), o_beta = m.take(4 * TV), o_bm = m.take(4 * TV),
                o_ssn = m.take(4 * std::max(nss, 1)), o_ssp = m.take(4 * (nss + 1)), o_zsn = m.take(4 * std::max(nzs, 1)),
-               o_zsp = m.take(4 * (nzs + 1)), o_sR = m.take(8 * std::max(ns, 1)), o_slR = m.take(8 * std::max(ns, 1)),
-               o_zR = m.take(8 * std::max(nz, 1)), o_zlR = m.take(8 * std::max(nz, 1)), o_u01a = m.take(8 * std::max(ns, 1)),
+               o_zsp = m.take(4 * (nzs + 1)), o_sR = m.take(4 * std::max(ns, 1)), o_slR = m.take(8 * std::max(ns, 1)),
+               o_zR = m.take(4 * std::max(nz, 1)), o_zlR = m.take(8 * std::max(nz, 1)), o_u01a = m.take(8 * std::max(ns, 1)),
                o_u01b = m.take(8 * std::max(ns, 1)), o_u0ta = m.take(8 * std::max(nz, 1)), o_u0tb = m.take(8 * std::max(nz, 1)),
                o_stri = m.take(4 * std::max(ns, 1)), o_ztri = m.take(4 * std::max(nz, 1)), o_args = m.take(sizeof(LinArgs)),
                o_argp = m.take(sizeof(LinArgs *)), o_rep = m.take(sizeof(LinReport));
@@ -698,25 +888,36 @@ ots_status linear_prepare(ots_problem *p) {
   auto at = [&](size_t o) { return (void *)(base + o); };
   LinArgs &h = L->h;
   h.V = V; h.S = S; h.T = T; h.krs = p->tv ? S : 0; h.drs = p->cv ? S : 0;
-  h.n_src = ns; h.n_snk = nz; h.n_sseg = nss; h.n_zseg = nzs; h.mass = mass;
+  h.n_src = ns; h.n_snk = nz; h.n_sseg = nss; h.n_zseg = nzs; h.mass = (float)mass;
   h.in_ptr = (int *)at(o_in_ptr); h.in_tail = (int *)at(o_in_tail); h.in_head = (int *)at(o_in_head);
   h.in_state = (int *)at(o_in_state); h.out_ptr = (int *)at(o_out_ptr); h.out_tail = (int *)at(o_out_tail);
-  h.out_head = (int *)at(o_out_head); h.out_to_in = (int *)at(o_out_to_in);
+  h.out_head = (int *)at(o_out_head); h.out_to_in = (int *)at(o_out_to_in); h.in_to_out = (int *)at(o_in_to_out);
+  h.gbw = (float *)at(o_gbw);
   h.kappa = (float2 *)at(o_kappa); h.logd = (float2 *)at(o_logd);
   h.Gf = (float *)at(o_gf); h.Gb = (float *)at(o_gb); h.Dc = (float *)at(o_dc); h.Fc = (float *)at(o_fc);
   h.nu = (int *)at(o_nu); h.w[0] = (float *)at(o_w0); h.w[1] = (float *)at(o_w1);
   h.alpha = (float *)at(o_alpha); h.beta = (float *)at(o_beta); h.bm = (float *)at(o_bm);
   h.sseg_node = (int *)at(o_ssn); h.sseg_ptr = (int *)at(o_ssp); h.zseg_node = (int *)at(o_zsn); h.zseg_ptr = (int *)at(o_zsp);
-  h.src_R = (double *)at(o_sR); h.src_logR = (double *)at(o_slR); h.snk_R = (double *)at(o_zR); h.snk_logR = (double *)at(o_zlR);
-  h.lU01[0] = (double *)at(o_u01a); h.lU01[1] = (double *)at(o_u01b); h.lU0T[0] = (double *)at(o_u0ta); h.lU0T[1] = (double *)at(o_u0tb);
+  h.src_R = (float *)at(o_sR); h.src_logR = (float2 *)at(o_slR); h.snk_R = (float *)at(o_zR); h.snk_logR = (float2 *)at(o_zlR);
+  h.lU01[0] = (float2 *)at(o_u01a); h.lU01[1] = (float2 *)at(o_u01b); h.lU0T[0] = (float2 *)at(o_u0ta); h.lU0T[1] = (float2 *)at(o_u0tb);
   h.src_tri = (int *)at(o_stri); h.snk_tri = (int *)at(o_ztri);
   h.p_logu = p->d_logu; h.p_src_logU = p->src.d_tri_logU; h.p_snk_logU = p->snk.d_tri_logU;
   L->d_rep = (LinReport *)at(o_rep);
   h.rep = L->d_rep;
-  h.cur = 0; h.need = 1; h.done = 0; h.pad = 0;
+  h.cur = 0; h.done = 0;
   L->d_args = (LinArgs *)at(o_args);
   L->d_argp = (LinArgs **)at(o_argp);
-  L->smem = 2 * V * (int)sizeof(float);
+  // shared-memory mode: everything when it fits in kLinSmemAll, else the index arrays when they
+  // fit in kLinSmemIndex, else only the two message rows and the per-entry terms
+  h.mode = 0;
+  if (lin_layout(V, S, T, 2).words * 4 <= kLinSmemAll) h.mode = 2;
+  else if (lin_layout(V, S, T, 1).words * 4 <= kLinSmemIndex) h.mode = 1;
+  L->smem = (int)(lin_layout(V, S, T, h.mode).words * 4);
+  if (L->smem > kLinSmemMax) {
+    cudaFreeHost(L->h_rep);
+    problem_free(p, L->arena);
+    return fail(OTS_ERR_INVALID_ARG, "the linear-domain path needs %d bytes of shared memory (at most %d)", L->smem, kLinSmemMax);
+  }
   LinArgs *argp = L->d_args;
   cudaStream_t s = p->stream;
   size_t up = 0;
@@ -733,15 +934,16 @@ ots_status linear_prepare(ots_problem *p) {
   if (!e) e = put(o_out_tail, out_tail.data(), 4 * S);
   if (!e) e = put(o_out_head, out_head.data(), 4 * S);
   if (!e) e = put(o_out_to_in, out_to_in.data(), 4 * S);
+  if (!e) e = put(o_in_to_out, in_to_out.data(), 4 * S);
   if (!e) e = put(o_kappa, kappa.data(), 8 * kappa.size());
   if (!e) e = put(o_logd, logd.data(), 8 * logd.size());
   if (!e) e = put(o_ssn, side[0].seg_node.data(), 4 * nss);
   if (!e) e = put(o_ssp, side[0].seg_ptr.data(), 4 * (nss + 1));
   if (!e) e = put(o_zsn, side[1].seg_node.data(), 4 * nzs);
   if (!e) e = put(o_zsp, side[1].seg_ptr.data(), 4 * (nzs + 1));
-  if (!e) e = put(o_sR, side[0].R.data(), 8 * ns);
+  if (!e) e = put(o_sR, side[0].R.data(), 4 * ns);
   if (!e) e = put(o_slR, side[0].logR.data(), 8 * ns);
-  if (!e) e = put(o_zR, side[1].R.data(), 8 * nz);
+  if (!e) e = put(o_zR, side[1].R.data(), 4 * nz);
   if (!e) e = put(o_zlR, side[1].logR.data(), 8 * nz);
   if (!e) e = put(o_stri, side[0].tri.data(), 4 * ns);
   if (!e) e = put(o_ztri, side[1].tri.data(), 4 * nz);
@@ -769,8 +971,14 @@ void linear_release(ots_problem *p) {
 }
 
 ots_status linear_run(ots_problem *const *ps, int n, int max_passes, double tol, int init, double *kernel_ms) {
-  int smem = 0;
-  for (int i = 0; i < n; ++i) smem = std::max(smem, ps[i]->lin->smem);
+  int smem = 0, smax = 0;
+  for (int i = 0; i < n; ++i) {
+    smem = std::max(smem, ps[i]->lin->smem);
+    smax = std::max(smax, ps[i]->S);
+  }
+  // threads per block: enough for one state entry each up to kLinThreads (small problems take
+  // fewer warps, so their barriers are cheaper)
+  const int threads = std::min(kLinThreads, std::max(64, (smax + 31) / 32 * 32));
   if (smem > 48 * 1024)
     OTS_CUDA(cudaFuncSetAttribute(k_linear, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   cudaStream_t s = ps[0]->stream;
@@ -787,7 +995,7 @@ ots_status linear_run(ots_problem *const *ps, int n, int max_passes, double tol,
   OTS_CUDA(cudaEventCreate(&e0));
   OTS_CUDA(cudaEventCreate(&e1));
   OTS_CUDA(cudaEventRecord(e0, s));
-  k_linear<<<n, kLinThreads, smem, s>>>(argp, max_passes, tol, init);
+  k_linear<<<n, threads, smem, s>>>(argp, max_passes, tol, init);
   cudaError_t le = cudaGetLastError();
   OTS_CUDA(cudaEventRecord(e1, s));
   for (int i = 0; i < n; ++i)
