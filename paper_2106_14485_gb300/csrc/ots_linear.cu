@@ -107,6 +107,7 @@ __host__ __device__ inline LinLayout lin_layout(int V, int S, int T, int mode) {
 namespace {
 
 constexpr int kLinThreads = 512;
+constexpr int kBatch = 4;   // state entries per thread whose loads are in flight together
 constexpr float kLost = 0x1p60f, kDrift = 0x1p30f;
 constexpr float kLn2f = 0.693147180559945309f;
 constexpr float kNegLog = -1e30f;    // log 0 in the problem's float-float duals
@@ -286,20 +287,37 @@ __device__ __forceinline__ float2 split(double x) {
   return make_float2(h, (float)(x - (double)h));
 }
 
+// log2 of the sum of 2^c[k] over k in [k0, k1) (two passes over shared memory; log 0 = -inf)
+__device__ __forceinline__ float lse_range(const float *c, int k0, int k1) {
+  float m = -INFINITY;
+  for (int k = k0; k < k1; ++k) m = fmaxf(m, c[k]);
+  if (!(m > -INFINITY)) return -INFINITY;
+  float sum = 0.f;
+  for (int k = k0; k < k1; ++k) sum += exp2f(c[k] - m);
+  return m + log2f(sum);
+}
+
+// log2 u_t of an entry from its stored pair (w, nu): 0 without a capacity, -inf for u = 0
+__device__ __forceinline__ float log2_u(float2 ld, float wv, int nu) {
+  if (ld.x == INFINITY) return 0.f;
+  return wv > 0.f ? (float)nu + log2f(wv) : -INFINITY;
+}
+
 // Scale sweep (update = false) or a whole pass of Algorithm 2 in FP32 log arithmetic
 // (update = true): alpha_t, beta_t become the base-2 logarithms of the messages.  With updates,
 // the new duals go to the next buffers (w[nxt], lU01/lU0T[nxt], nu in place) and the measures
 // to *mism, *resid; returns an ots_status (OTS_ERR_INFEASIBLE if a boundary state has no path).
+// Same two phases per step as the linear pass (per-entry terms, then per-node log-sum-exp).
 __device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, FF *mism_out, FF *res_out,
                          float2 *red) {
-  const int V = a.V, S = a.S, T = a.T, nxt = cur ^ 1;
-  float *rp = P.rows, *rc = P.rows + V;
+  const int V = a.V, S = a.S, T = a.T, nxt = cur ^ 1, nt = blockDim.x;
+  float *rp = P.rows, *rc = P.rows + V, *c = P.c;
   int bad = 0;
   FF mism{0.f, 0.f}, res{0.f, 0.f};
   // beta_T[v] = log2 sum_{sink j, tail j = v} U0T(j)
-  for (int v = threadIdx.x; v < V; v += blockDim.x) rp[v] = -INFINITY;
+  for (int v = threadIdx.x; v < V; v += nt) rp[v] = -INFINITY;
   __syncthreads();
-  for (int s = threadIdx.x; s < a.n_zseg; s += blockDim.x) {
+  for (int s = threadIdx.x; s < a.n_zseg; s += nt) {
     // (this sweep runs once per rescaling: FP64 for the few boundary entries)
     double m = -INFINITY;
     for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) m = fmax(m, dbl(a.lU0T[cur][e]));
@@ -308,22 +326,37 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, 
     rp[a.zseg_node[s]] = (float)(m + log2(acc));
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < V; v += blockDim.x) P.beta[(size_t)T * V + v] = rp[v];
+  for (int v = threadIdx.x; v < V; v += nt) P.beta[(size_t)T * V + v] = rp[v];
   // beta_t[v] = log2 sum_{tail j = v} 2^(beta_{t+1}[head j] + log2 K(j) + log2 u_t(j)),  t = T-1..2
   for (int t = T - 1; t >= 2; --t) {
-    for (int v = threadIdx.x; v < V; v += blockDim.x) {
-      float m = -INFINITY, sum = 0.f;
-      for (int k = P.out_ptr[v]; k < P.out_ptr[v + 1]; ++k) {
-        const int ki = a.out_to_in[k];
-        const size_t q = (size_t)t * S + ki;
-        const float2 kap = a.kappa[(size_t)t * a.krs + ki];
-        const float wv = P.w[cur][q];
-        const float lu = wv > 0.f ? (float)P.nu[q] + log2f(wv) : -INFINITY;
-        const float x = rp[P.out_head[k]] + kap.x + lu;
-        if (x > m) { sum = sum * exp2f(m - x) + 1.f; m = x; }
-        else if (x > -INFINITY) sum += exp2f(x - m);
+    for (int k0 = threadIdx.x; k0 < S; k0 += kBatch * nt) {
+      int hd[kBatch], ki[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = k0 + j * nt;
+        hd[j] = k < S ? P.out_head[k] : 0;
+        ki[j] = k < S ? a.out_to_in[k] : 0;
       }
-      const float r = m > -INFINITY ? m + log2f(sum) : -INFINITY;
+      float2 kap[kBatch], ld[kBatch];
+      float wv[kBatch];
+      int nu[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const size_t q = (size_t)t * S + ki[j];
+        kap[j] = a.kappa[(size_t)t * a.krs + ki[j]];
+        ld[j] = a.logd[(size_t)t * a.drs + ki[j]];
+        wv[j] = P.w[cur][q];
+        nu[j] = P.nu[q];
+      }
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = k0 + j * nt;
+        if (k < S) c[k] = rp[hd[j]] + kap[j].x + log2_u(ld[j], wv[j], nu[j]);
+      }
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += nt) {
+      const float r = lse_range(c, P.out_ptr[v], P.out_ptr[v + 1]);
       rc[v] = r;
       P.beta[(size_t)t * V + v] = r;
     }
@@ -332,9 +365,9 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, 
   }
   // source update U01 <- R01 / Psi_1, then alpha_1[v] = log2 sum_{source i, head i = v} U01(i)
   const int su = update ? nxt : cur;
-  for (int v = threadIdx.x; v < V; v += blockDim.x) rc[v] = -INFINITY;
+  for (int v = threadIdx.x; v < V; v += nt) rc[v] = -INFINITY;
   __syncthreads();
-  for (int s = threadIdx.x; s < a.n_sseg; s += blockDim.x) {
+  for (int s = threadIdx.x; s < a.n_sseg; s += nt) {
     const int v = a.sseg_node[s];
     if (update) {
       const double p1 = (double)P.beta[(size_t)2 * V + v];
@@ -353,51 +386,60 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, 
   }
   __syncthreads();
   { float *tmp = rp; rp = rc; rc = tmp; }
-  for (int v = threadIdx.x; v < V; v += blockDim.x) P.alpha[(size_t)V + v] = rp[v];
+  for (int v = threadIdx.x; v < V; v += nt) P.alpha[(size_t)V + v] = rp[v];
   // forward: capacity update of u_t (update) and alpha_t[v] = log2 sum_{head i = v} 2^(alpha_{t-1}[tail i]
   // + log2 K(i) + log2 u_t(i)),  t = 2..T-1
   for (int t = 2; t <= T - 1; ++t) {
+    const size_t o = (size_t)t * S;
     float rsum = 0.f;
-    for (int v = threadIdx.x; v < V; v += blockDim.x) {
-      const float bb = P.beta[(size_t)(t + 1) * V + v];
-      float m = -INFINITY, sum = 0.f;
-      for (int k = P.in_ptr[v]; k < P.in_ptr[v + 1]; ++k) {
-        const size_t q = (size_t)t * S + k;
-        const float al = rp[P.in_tail[k]];
-        const float2 kap = a.kappa[(size_t)t * a.krs + k];
-        const float2 ld = a.logd[(size_t)t * a.drs + k];
-        float lu = 0.f;
-        if (ld.x != INFINITY) {
-          const float wv = P.w[cur][q];
-          const float lo = wv > 0.f ? (float)P.nu[q] + log2f(wv) : -INFINITY;
-          lu = lo;
-          if (update) {
-            const float ls = al + bb + kap.x;
-            float ln = 0.f;
-            if (ls > -INFINITY) {
-              ln = ld.x == -INFINITY ? -INFINITY : fminf(ld.x - ls, 0.f);
-              rsum += flow_change(lo, ln, ls);
-            }
-            if (ln == -INFINITY) { P.w[nxt][q] = 0.f; P.nu[q] = 0; }
-            else { const float n = floorf(ln); P.w[nxt][q] = exp2f(ln - n); P.nu[q] = (int)n; }
-            lu = ln;
-          }
-        }
-        const float x = al + kap.x + lu;
-        if (x > m) { sum = sum * exp2f(m - x) + 1.f; m = x; }
-        else if (x > -INFINITY) sum += exp2f(x - m);
+    for (int k0 = threadIdx.x; k0 < S; k0 += kBatch * nt) {
+      int ti[kBatch], hi[kBatch], nu[kBatch];
+      float2 kap[kBatch], ld[kBatch];
+      float wv[kBatch];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = k0 + j * nt;
+        const bool in = k < S;
+        ti[j] = in ? P.in_tail[k] : 0;
+        hi[j] = in ? P.in_head[k] : 0;
+        kap[j] = in ? a.kappa[(size_t)t * a.krs + k] : make_float2(-INFINITY, 0.f);
+        ld[j] = in ? a.logd[(size_t)t * a.drs + k] : make_float2(INFINITY, 0.f);
+        wv[j] = in ? P.w[cur][o + k] : 1.f;
+        nu[j] = in ? P.nu[o + k] : 0;
       }
-      const float r = m > -INFINITY ? m + log2f(sum) : -INFINITY;
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int k = k0 + j * nt;
+        if (k >= S) continue;
+        const float al = rp[ti[j]];
+        float lu = log2_u(ld[j], wv[j], nu[j]);
+        if (update && ld[j].x != INFINITY) {
+          const float ls = al + P.beta[(size_t)(t + 1) * V + hi[j]] + kap[j].x;
+          float ln = 0.f;
+          if (ls > -INFINITY) {
+            ln = ld[j].x == -INFINITY ? -INFINITY : fminf(ld[j].x - ls, 0.f);
+            rsum += flow_change(lu, ln, ls);
+          }
+          if (ln == -INFINITY) { P.w[nxt][o + k] = 0.f; P.nu[o + k] = 0; }
+          else { const float n = floorf(ln); P.w[nxt][o + k] = exp2f(ln - n); P.nu[o + k] = (int)n; }
+          lu = ln;
+        }
+        c[k] = al + kap[j].x + lu;
+      }
+    }
+    res = ff_add(res, rsum);
+    __syncthreads();
+    for (int v = threadIdx.x; v < V; v += nt) {
+      const float r = lse_range(c, P.in_ptr[v], P.in_ptr[v + 1]);
       rc[v] = r;
       P.alpha[(size_t)t * V + v] = r;
     }
-    res = ff_add(res, rsum);
     __syncthreads();
     float *tmp = rp; rp = rc; rc = tmp;
   }
   // sink update U0T <- R0T / hatPsi_T
   if (update) {
-    for (int s = threadIdx.x; s < a.n_zseg; s += blockDim.x) {
+    for (int s = threadIdx.x; s < a.n_zseg; s += nt) {
       const double p = (double)rp[a.zseg_node[s]];
       for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) {
         if (!(p > -INFINITY)) { bad = 1; a.lU0T[nxt][e] = a.lU0T[cur][e]; continue; }
@@ -471,7 +513,6 @@ __device__ void rebuild(const LinArgs &a, const Ptrs &P, int cur) {
 // entries in a fixed order.  Returns 1 if a scaled value left [2^-60, 2^60] (the pass must be
 // redone), sets *drift if one left [2^-30, 2^30], and the measures (unnormalised) in *mism,
 // *resid.  The boundary duals are float-float base-2 logarithms (about 48 bits).
-constexpr int kBatch = 4;   // entries per thread whose loads are in flight together
 
 __device__ int linear_pass(const LinArgs &a, const Ptrs &P, int cur, FF *mism_out, FF *res_out, int *drift,
                            float2 *red, float *redf) {
@@ -708,27 +749,43 @@ __global__ void __launch_bounds__(kLinThreads) k_linear(LinArgs *const *args, in
   int passes = 0, log_passes = 0, rescalings = 0, status = OTS_OK, converged = 0;
   const float tolf = (float)tol;
   FF mism{0.f, 0.f}, res{0.f, 0.f};
+  int log_run = 0, backoff = 1;    // passes still to run in log arithmetic after a thrown-away pass
   while (passes < max_passes) {
-    if (need) {
-      status = log_sweep(a, P, cur, false, nullptr, nullptr, sh.red);
-      if (status) break;
-      rebuild(a, P, cur);
-      ++rescalings;
-      need = 0;
-    }
-    int drift = 0;
-    const int lost = linear_pass(a, P, cur, &mism, &res, &drift, sh.red, sh.redf);
-    if (lost) {
-      // thrown away: the same pass again in log arithmetic, from the same duals
+    int lost = 0;
+    if (log_run > 0) {
+      // a problem whose duals keep leaving the range (e.g. they diverge, with no feasible flow)
+      // runs in log arithmetic for a while before the linear form is tried again
       status = log_sweep(a, P, cur, true, &mism, &res, sh.red);
       cur ^= 1;
       ++log_passes;
+      lost = 1;
       if (status) { ++passes; break; }
-      rebuild(a, P, cur);
-      ++rescalings;
+      if (--log_run == 0) { rebuild(a, P, cur); ++rescalings; }
     } else {
-      cur ^= 1;
-      need = drift;
+      if (need) {
+        status = log_sweep(a, P, cur, false, nullptr, nullptr, sh.red);
+        if (status) break;
+        rebuild(a, P, cur);
+        ++rescalings;
+        need = 0;
+      }
+      int drift = 0;
+      lost = linear_pass(a, P, cur, &mism, &res, &drift, sh.red, sh.redf);
+      if (lost) {
+        // thrown away: the same pass again in log arithmetic, from the same duals; the next
+        // 1, 2, 4, ... 64 passes too while the linear form keeps failing
+        status = log_sweep(a, P, cur, true, &mism, &res, sh.red);
+        cur ^= 1;
+        ++log_passes;
+        if (status) { ++passes; break; }
+        log_run = backoff - 1;
+        backoff = min(2 * backoff, 64);
+        if (log_run == 0) { rebuild(a, P, cur); ++rescalings; }
+      } else {
+        cur ^= 1;
+        need = drift;
+        backoff = 1;
+      }
     }
     ++passes;
     const float srcf = (mism.h + mism.l) / a.mass, capf = (res.h + res.l) / a.mass;
