@@ -63,6 +63,8 @@ struct LinArgs {
   const int *src_tri, *snk_tri;      // entry -> boundary triple of the problem
   float2 *p_logu;                    // problem's log2 u_t [(T+1) S] by state (float-float)
   double *p_src_logU, *p_snk_logU;   // problem's log2 U01 / U0T per triple
+  float *arow;                       // [2 V] step rows of a problem on a cluster (read across its blocks)
+  float2 *cred;                      // [4][16] cluster reduction slots
   LinReport *rep;
   int cur, done;                     // state kept between launches
 };
@@ -262,6 +264,107 @@ __device__ float block_max(float v, float *red) {
   return s;
 }
 
+// The part of a problem one block owns: a node range, the state entries of those nodes (in-CSR
+// range for the forward step, out-CSR range for the backward step) and the boundary segments of
+// those nodes.  A problem on one block owns everything; on a cluster of R blocks the node ranges
+// split the in-entries evenly.
+struct Part {
+  int rank, R;
+  int v0, v1, in0, in1, out0, out1, s0, s1, z0, z1;
+  int slot;                          // next reduction slot (cluster)
+};
+
+__device__ int first_node_at(const int *ptr, int V, int target) {   // smallest v with ptr[v] >= target
+  int lo = 0, hi = V;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (ptr[mid] < target) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ int first_seg_at(const int *node, int n, int v) {        // first segment whose node >= v
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (node[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ Part make_part(const LinArgs &a, int rank, int R) {
+  Part p;
+  p.rank = rank;
+  p.R = R;
+  p.slot = 0;
+  const long long S = a.S;
+  p.v0 = rank == 0 ? 0 : first_node_at(a.in_ptr, a.V, (int)(S * rank / R));
+  p.v1 = rank == R - 1 ? a.V : first_node_at(a.in_ptr, a.V, (int)(S * (rank + 1) / R));
+  p.in0 = a.in_ptr[p.v0];
+  p.in1 = a.in_ptr[p.v1];
+  p.out0 = a.out_ptr[p.v0];
+  p.out1 = a.out_ptr[p.v1];
+  p.s0 = first_seg_at(a.sseg_node, a.n_sseg, p.v0);
+  p.s1 = first_seg_at(a.sseg_node, a.n_sseg, p.v1);
+  p.z0 = first_seg_at(a.zseg_node, a.n_zseg, p.v0);
+  p.z1 = first_seg_at(a.zseg_node, a.n_zseg, p.v1);
+  return p;
+}
+
+// Barrier between the steps: the block, or every block of the cluster (release / acquire at
+// cluster scope, so the rows one block wrote are seen by the others).
+template <bool CL>
+__device__ __forceinline__ void step_sync() {
+  if constexpr (CL) {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+  } else {
+    __syncthreads();
+  }
+}
+
+// Load of a value another block of the cluster may have written (L2, not a stale L1 line).
+template <bool CL, typename X>
+__device__ __forceinline__ X ldx(const X *p) {
+  if constexpr (CL) return __ldcg(p);
+  else return *p;
+}
+
+// Sum / maximum over the whole problem: the block's value, then (cluster) every block adds the R
+// block values in rank order from a slot in global memory, so every block gets the same result.
+template <bool CL>
+__device__ FF part_sum(FF v, float2 *red, float2 *cred, Part &pt) {
+  const FF b = block_sum(v, red);
+  if constexpr (!CL) {
+    return b;
+  } else {
+    float2 *sl = cred + (pt.slot & 3) * 16;
+    ++pt.slot;
+    if (threadIdx.x == 0) sl[pt.rank] = f2_of(b);
+    step_sync<true>();
+    FF s{0.f, 0.f};
+    for (int r = 0; r < pt.R; ++r) s = ff_sum(s, ff_of(__ldcg(sl + r)));
+    return s;
+  }
+}
+
+template <bool CL>
+__device__ float part_max(float v, float *redf, float2 *cred, Part &pt) {
+  const float b = block_max(v, redf);
+  if constexpr (!CL) {
+    return b;
+  } else {
+    float2 *sl = cred + (pt.slot & 3) * 16;
+    ++pt.slot;
+    if (threadIdx.x == 0) sl[pt.rank] = make_float2(b, 0.f);
+    step_sync<true>();
+    float s = 0.f;
+    for (int r = 0; r < pt.R; ++r) s = fmaxf(s, __ldcg(sl + r).x);
+    return s;
+  }
+}
+
 // Range of the scaled values a pass produced (non-zero ones; any non-finite value counts as
 // out of range).
 struct Range {
@@ -308,16 +411,17 @@ __device__ __forceinline__ float log2_u(float2 ld, float wv, int nu) {
 // the new duals go to the next buffers (w[nxt], lU01/lU0T[nxt], nu in place) and the measures
 // to *mism, *resid; returns an ots_status (OTS_ERR_INFEASIBLE if a boundary state has no path).
 // Same two phases per step as the linear pass (per-entry terms, then per-node log-sum-exp).
-__device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, FF *mism_out, FF *res_out,
+template <bool CL>
+__device__ int log_sweep(const LinArgs &a, const Ptrs &P, Part &pt, int cur, bool update, FF *mism_out, FF *res_out,
                          float2 *red) {
   const int V = a.V, S = a.S, T = a.T, nxt = cur ^ 1, nt = blockDim.x;
   float *rp = P.rows, *rc = P.rows + V, *c = P.c;
   int bad = 0;
   FF mism{0.f, 0.f}, res{0.f, 0.f};
   // beta_T[v] = log2 sum_{sink j, tail j = v} U0T(j)
-  for (int v = threadIdx.x; v < V; v += nt) rp[v] = -INFINITY;
+  for (int v = pt.v0 + threadIdx.x; v < pt.v1; v += nt) rp[v] = -INFINITY;
   __syncthreads();
-  for (int s = threadIdx.x; s < a.n_zseg; s += nt) {
+  for (int s = pt.z0 + threadIdx.x; s < pt.z1; s += nt) {
     // (this sweep runs once per rescaling: FP64 for the few boundary entries)
     double m = -INFINITY;
     for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) m = fmax(m, dbl(a.lU0T[cur][e]));
@@ -326,16 +430,17 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, 
     rp[a.zseg_node[s]] = (float)(m + log2(acc));
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < V; v += nt) P.beta[(size_t)T * V + v] = rp[v];
+  for (int v = pt.v0 + threadIdx.x; v < pt.v1; v += nt) P.beta[(size_t)T * V + v] = rp[v];
+  step_sync<CL>();
   // beta_t[v] = log2 sum_{tail j = v} 2^(beta_{t+1}[head j] + log2 K(j) + log2 u_t(j)),  t = T-1..2
   for (int t = T - 1; t >= 2; --t) {
-    for (int k0 = threadIdx.x; k0 < S; k0 += kBatch * nt) {
+    for (int k0 = pt.out0 + threadIdx.x; k0 < pt.out1; k0 += kBatch * nt) {
       int hd[kBatch], ki[kBatch];
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
-        hd[j] = k < S ? P.out_head[k] : 0;
-        ki[j] = k < S ? a.out_to_in[k] : 0;
+        hd[j] = k < pt.out1 ? P.out_head[k] : 0;
+        ki[j] = k < pt.out1 ? a.out_to_in[k] : 0;
       }
       float2 kap[kBatch], ld[kBatch];
       float wv[kBatch];
@@ -345,32 +450,32 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, 
         const size_t q = (size_t)t * S + ki[j];
         kap[j] = a.kappa[(size_t)t * a.krs + ki[j]];
         ld[j] = a.logd[(size_t)t * a.drs + ki[j]];
-        wv[j] = P.w[cur][q];
-        nu[j] = P.nu[q];
+        wv[j] = ldx<CL>(P.w[cur] + q);
+        nu[j] = ldx<CL>(P.nu + q);
       }
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
-        if (k < S) c[k] = rp[hd[j]] + kap[j].x + log2_u(ld[j], wv[j], nu[j]);
+        if (k < pt.out1) c[k] = ldx<CL>(rp + hd[j]) + kap[j].x + log2_u(ld[j], wv[j], nu[j]);
       }
     }
     __syncthreads();
-    for (int v = threadIdx.x; v < V; v += nt) {
+    for (int v = pt.v0 + threadIdx.x; v < pt.v1; v += nt) {
       const float r = lse_range(c, P.out_ptr[v], P.out_ptr[v + 1]);
       rc[v] = r;
       P.beta[(size_t)t * V + v] = r;
     }
-    __syncthreads();
+    step_sync<CL>();
     float *tmp = rp; rp = rc; rc = tmp;
   }
   // source update U01 <- R01 / Psi_1, then alpha_1[v] = log2 sum_{source i, head i = v} U01(i)
   const int su = update ? nxt : cur;
-  for (int v = threadIdx.x; v < V; v += nt) rc[v] = -INFINITY;
+  for (int v = pt.v0 + threadIdx.x; v < pt.v1; v += nt) rc[v] = -INFINITY;
   __syncthreads();
-  for (int s = threadIdx.x; s < a.n_sseg; s += nt) {
+  for (int s = pt.s0 + threadIdx.x; s < pt.s1; s += nt) {
     const int v = a.sseg_node[s];
     if (update) {
-      const double p1 = (double)P.beta[(size_t)2 * V + v];
+      const double p1 = (double)ldx<CL>(P.beta + (size_t)2 * V + v);
       for (int e = a.sseg_ptr[s]; e < a.sseg_ptr[s + 1]; ++e) {
         if (!(p1 > -INFINITY)) { bad = 1; a.lU01[nxt][e] = a.lU01[cur][e]; continue; }
         const double ln = dbl(a.src_logR[e]) - p1;
@@ -386,20 +491,21 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, 
   }
   __syncthreads();
   { float *tmp = rp; rp = rc; rc = tmp; }
-  for (int v = threadIdx.x; v < V; v += nt) P.alpha[(size_t)V + v] = rp[v];
+  for (int v = pt.v0 + threadIdx.x; v < pt.v1; v += nt) P.alpha[(size_t)V + v] = rp[v];
+  step_sync<CL>();
   // forward: capacity update of u_t (update) and alpha_t[v] = log2 sum_{head i = v} 2^(alpha_{t-1}[tail i]
   // + log2 K(i) + log2 u_t(i)),  t = 2..T-1
   for (int t = 2; t <= T - 1; ++t) {
     const size_t o = (size_t)t * S;
     float rsum = 0.f;
-    for (int k0 = threadIdx.x; k0 < S; k0 += kBatch * nt) {
+    for (int k0 = pt.in0 + threadIdx.x; k0 < pt.in1; k0 += kBatch * nt) {
       int ti[kBatch], hi[kBatch], nu[kBatch];
       float2 kap[kBatch], ld[kBatch];
       float wv[kBatch];
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
-        const bool in = k < S;
+        const bool in = k < pt.in1;
         ti[j] = in ? P.in_tail[k] : 0;
         hi[j] = in ? P.in_head[k] : 0;
         kap[j] = in ? a.kappa[(size_t)t * a.krs + k] : make_float2(-INFINITY, 0.f);
@@ -410,11 +516,11 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, 
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
-        if (k >= S) continue;
-        const float al = rp[ti[j]];
+        if (k >= pt.in1) continue;
+        const float al = ldx<CL>(rp + ti[j]);
         float lu = log2_u(ld[j], wv[j], nu[j]);
         if (update && ld[j].x != INFINITY) {
-          const float ls = al + P.beta[(size_t)(t + 1) * V + hi[j]] + kap[j].x;
+          const float ls = al + ldx<CL>(P.beta + (size_t)(t + 1) * V + hi[j]) + kap[j].x;
           float ln = 0.f;
           if (ls > -INFINITY) {
             ln = ld[j].x == -INFINITY ? -INFINITY : fminf(ld[j].x - ls, 0.f);
@@ -429,18 +535,18 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, 
     }
     res = ff_add(res, rsum);
     __syncthreads();
-    for (int v = threadIdx.x; v < V; v += nt) {
+    for (int v = pt.v0 + threadIdx.x; v < pt.v1; v += nt) {
       const float r = lse_range(c, P.in_ptr[v], P.in_ptr[v + 1]);
       rc[v] = r;
       P.alpha[(size_t)t * V + v] = r;
     }
-    __syncthreads();
+    step_sync<CL>();
     float *tmp = rp; rp = rc; rc = tmp;
   }
   // sink update U0T <- R0T / hatPsi_T
   if (update) {
-    for (int s = threadIdx.x; s < a.n_zseg; s += nt) {
-      const double p = (double)rp[a.zseg_node[s]];
+    for (int s = pt.z0 + threadIdx.x; s < pt.z1; s += nt) {
+      const double p = (double)ldx<CL>(rp + a.zseg_node[s]);
       for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) {
         if (!(p > -INFINITY)) { bad = 1; a.lU0T[nxt][e] = a.lU0T[cur][e]; continue; }
         a.lU0T[nxt][e] = split(dbl(a.snk_logR[e]) - p);
@@ -448,21 +554,24 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, int cur, bool update, 
     }
   }
   __syncthreads();
-  const FF ms = block_sum(mism, red);
-  const FF rs = block_sum(res, red);
-  const FF bd = block_sum(FF{(float)bad, 0.f}, red);
+  const FF ms = part_sum<CL>(mism, red, a.cred, pt);
+  const FF rs = part_sum<CL>(res, red, a.cred, pt);
+  const FF bd = part_sum<CL>(FF{(float)bad, 0.f}, red, a.cred, pt);
   if (mism_out) *mism_out = ms;
   if (res_out) *res_out = rs;
   return bd.h > 0.f ? OTS_ERR_INFEASIBLE : OTS_OK;
 }
 
 // Scale fold: w_t(i) = m 2^e with m in [1/2, 1) -> w = m, nu += e (exact).  Then the per-state
-// factors Gf, Gb, Dc, Fc and the backward weights gbw = Gb w from the current scales.
-__device__ void rebuild(const LinArgs &a, const Ptrs &P, int cur) {
+// factors Gf, Gb, Dc, Fc and the backward weights gbw = Gb w from the current scales (entries of
+// the block's own nodes).
+template <bool CL>
+__device__ void rebuild(const LinArgs &a, const Ptrs &P, const Part &pt, int cur) {
   const int V = a.V, S = a.S, T = a.T;
-  const int n = (T - 2) * S;
+  const int nown = pt.in1 - pt.in0;
+  const int n = (T - 2) * nown;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const int t = 2 + idx / S, k = idx - (t - 2) * S;
+    const int t = 2 + idx / nown, k = pt.in0 + idx - (t - 2) * nown;
     const size_t q = (size_t)t * S + k;
     const float2 kap = a.kappa[(size_t)t * a.krs + k];
     const float2 ld = a.logd[(size_t)t * a.drs + k];
@@ -476,8 +585,8 @@ __device__ void rebuild(const LinArgs &a, const Ptrs &P, int cur) {
       P.w[cur][q] = wv;
       P.nu[q] = nu;
     }
-    const float al0 = P.alpha[(size_t)(t - 1) * V + y], al1 = P.alpha[(size_t)t * V + v];
-    const float be1 = P.beta[(size_t)(t + 1) * V + v], be0 = P.beta[(size_t)t * V + y];
+    const float al0 = ldx<CL>(P.alpha + (size_t)(t - 1) * V + y), al1 = ldx<CL>(P.alpha + (size_t)t * V + v);
+    const float be1 = ldx<CL>(P.beta + (size_t)(t + 1) * V + v), be0 = ldx<CL>(P.beta + (size_t)t * V + y);
     const bool open = kap.x > -INFINITY;
     float gf = 0.f, gb = 0.f;
     if (open && al0 > -INFINITY && al1 > -INFINITY) gf = exp2_ff(ff_add(ff_add(FF{al0, 0.f}, -al1), kap), nu);
@@ -504,7 +613,7 @@ __device__ void rebuild(const LinArgs &a, const Ptrs &P, int cur) {
       P.Dc[q] = dc;
     }
   }
-  __syncthreads();
+  step_sync<CL>();
 }
 
 // One pass of Algorithm 2 on the scaled quantities; new duals to the next buffers.  Each step
@@ -513,8 +622,8 @@ __device__ void rebuild(const LinArgs &a, const Ptrs &P, int cur) {
 // entries in a fixed order.  Returns 1 if a scaled value left [2^-60, 2^60] (the pass must be
 // redone), sets *drift if one left [2^-30, 2^30], and the measures (unnormalised) in *mism,
 // *resid.  The boundary duals are float-float base-2 logarithms (about 48 bits).
-
-__device__ int linear_pass(const LinArgs &a, const Ptrs &P, int cur, FF *mism_out, FF *res_out, int *drift,
+template <bool CL>
+__device__ int linear_pass(const LinArgs &a, const Ptrs &P, Part &pt, int cur, FF *mism_out, FF *res_out, int *drift,
                            float2 *red, float *redf) {
   const int V = a.V, S = a.S, T = a.T, nxt = cur ^ 1;
   float *rp = P.rows, *rc = P.rows + V, *c = P.c;
@@ -523,56 +632,57 @@ __device__ int linear_pass(const LinArgs &a, const Ptrs &P, int cur, FF *mism_ou
   int lost = 0;
   FF mism{0.f, 0.f}, res{0.f, 0.f};
   // b_T[v] = sum_{sink j, tail j = v} U0T(j) 2^-beta_T[v]
-  for (int v = threadIdx.x; v < V; v += nt) rp[v] = 0.f;
+  for (int v = pt.v0 + threadIdx.x; v < pt.v1; v += nt) rp[v] = 0.f;
   __syncthreads();
-  for (int s = threadIdx.x; s < a.n_zseg; s += nt) {
+  for (int s = pt.z0 + threadIdx.x; s < pt.z1; s += nt) {
     const int v = a.zseg_node[s];
-    const float sc = P.beta[(size_t)T * V + v];
+    const float sc = ldx<CL>(P.beta + (size_t)T * V + v);
     float acc = 0.f;
     for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) acc += exp2_ff(ff_add(ff_of(a.lU0T[cur][e]), -sc), 0);
     rg.see(acc);
     rp[v] = acc;
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < V; v += nt) P.bm[(size_t)T * V + v] = rp[v];
+  for (int v = pt.v0 + threadIdx.x; v < pt.v1; v += nt) P.bm[(size_t)T * V + v] = rp[v];
+  step_sync<CL>();
   // backward sweep, t = T-1..2: term of out-entry j = b_{t+1}[head j] Gb_t(j) w_t(j)
   for (int t = T - 1; t >= 2; --t) {
     const float *gw = P.gbw + (size_t)t * S;
-    for (int k0 = threadIdx.x; k0 < S; k0 += kBatch * nt) {
+    for (int k0 = pt.out0 + threadIdx.x; k0 < pt.out1; k0 += kBatch * nt) {
       int hd[kBatch];
       float g[kBatch];
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
-        hd[j] = k < S ? P.out_head[k] : 0;
-        g[j] = k < S ? gw[k] : 0.f;
+        hd[j] = k < pt.out1 ? P.out_head[k] : 0;
+        g[j] = k < pt.out1 ? ldx<CL>(gw + k) : 0.f;
       }
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
-        if (k < S) c[k] = rp[hd[j]] * g[j];
+        if (k < pt.out1) c[k] = ldx<CL>(rp + hd[j]) * g[j];
       }
     }
     __syncthreads();
-    for (int v = threadIdx.x; v < V; v += nt) {
+    for (int v = pt.v0 + threadIdx.x; v < pt.v1; v += nt) {
       float acc = 0.f;
       for (int k = P.out_ptr[v]; k < P.out_ptr[v + 1]; ++k) acc += c[k];
       rg.see(acc);
       rc[v] = acc;
       P.bm[(size_t)t * V + v] = acc;
     }
-    __syncthreads();
+    step_sync<CL>();
     float *tmp = rp; rp = rc; rc = tmp;
   }
   // rp = b_2.  Source update U01 <- R01 / Psi_1 (mismatch taken before), then
   // a_1[v] = sum_{source i, head i = v} U01(i) 2^-alpha_1[v]
-  for (int v = threadIdx.x; v < V; v += nt) rc[v] = 0.f;
+  for (int v = pt.v0 + threadIdx.x; v < pt.v1; v += nt) rc[v] = 0.f;
   __syncthreads();
-  for (int s = threadIdx.x; s < a.n_sseg; s += nt) {
+  for (int s = pt.s0 + threadIdx.x; s < pt.s1; s += nt) {
     const int v = a.sseg_node[s];
-    const float bb = rp[v];
-    const FF p1 = bb > 0.f ? ff_add(ff_log2(bb), P.beta[(size_t)2 * V + v]) : FF{0.f, 0.f};
-    const float sc = P.alpha[(size_t)V + v];
+    const float bb = ldx<CL>(rp + v);
+    const FF p1 = bb > 0.f ? ff_add(ff_log2(bb), ldx<CL>(P.beta + (size_t)2 * V + v)) : FF{0.f, 0.f};
+    const float sc = ldx<CL>(P.alpha + (size_t)V + v);
     float acc = 0.f;
     for (int e = a.sseg_ptr[s]; e < a.sseg_ptr[s + 1]; ++e) {
       const FF lo = ff_of(a.lU01[cur][e]);
@@ -590,7 +700,7 @@ __device__ int linear_pass(const LinArgs &a, const Ptrs &P, int cur, FF *mism_ou
     rg.see(acc);
     rc[v] = acc;
   }
-  __syncthreads();
+  step_sync<CL>();
   { float *tmp = rp; rp = rc; rc = tmp; }
   // forward sweep with the capacity updates, t = 2..T-1: term of in-entry i =
   // a_{t-1}[tail i] Gf_t(i) w_t(i), w_t(i) updated first where the state has a capacity
@@ -598,13 +708,13 @@ __device__ int linear_pass(const LinArgs &a, const Ptrs &P, int cur, FF *mism_ou
     const size_t o = (size_t)t * S;
     const float *bn = P.bm + (size_t)(t + 1) * V;
     FF rsum{0.f, 0.f};
-    for (int k0 = threadIdx.x; k0 < S; k0 += kBatch * nt) {
+    for (int k0 = pt.in0 + threadIdx.x; k0 < pt.in1; k0 += kBatch * nt) {
       int ti[kBatch], hi[kBatch], nu[kBatch];
       float gf[kBatch], dc[kBatch], wo[kBatch], fc[kBatch], gb[kBatch];
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
-        const bool in = k < S;
+        const bool in = k < pt.in1;
         ti[j] = in ? P.in_tail[k] : 0;
         hi[j] = in ? P.in_head[k] : 0;
         gf[j] = in ? P.Gf[o + k] : 0.f;
@@ -617,11 +727,11 @@ __device__ int linear_pass(const LinArgs &a, const Ptrs &P, int cur, FF *mism_ou
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
-        if (k >= S) continue;
-        const float a0 = rp[ti[j]];
+        if (k >= pt.in1) continue;
+        const float a0 = ldx<CL>(rp + ti[j]);
         float g = gf[j];
         if (dc[j] != INFINITY) {
-          const float x = a0 * bn[hi[j]];
+          const float x = a0 * ldx<CL>(bn + hi[j]);
           const float uc = ldexpf(1.f, -nu[j]);
           const float un = x > 0.f ? fminf(__fdiv_rn(dc[j], x), uc) : uc;
           rsum = ff_add(rsum, fabsf(un - wo[j]) * fminf(x * fc[j], FLT_MAX));
@@ -635,42 +745,42 @@ __device__ int linear_pass(const LinArgs &a, const Ptrs &P, int cur, FF *mism_ou
     }
     res = ff_sum(res, rsum);
     __syncthreads();
-    for (int v = threadIdx.x; v < V; v += nt) {
+    for (int v = pt.v0 + threadIdx.x; v < pt.v1; v += nt) {
       float acc = 0.f;
       for (int k = P.in_ptr[v]; k < P.in_ptr[v + 1]; ++k) acc += c[k];
       rg.see(acc);
       rc[v] = acc;
     }
-    __syncthreads();
+    step_sync<CL>();
     float *tmp = rp; rp = rc; rc = tmp;
   }
   // rp = a_{T-1}.  Sink update U0T <- R0T / hatPsi_T
-  for (int s = threadIdx.x; s < a.n_zseg; s += nt) {
+  for (int s = pt.z0 + threadIdx.x; s < pt.z1; s += nt) {
     const int v = a.zseg_node[s];
-    const float aa = rp[v];
-    const FF p = aa > 0.f ? ff_add(ff_log2(aa), P.alpha[(size_t)(T - 1) * V + v]) : FF{0.f, 0.f};
+    const float aa = ldx<CL>(rp + v);
+    const FF p = aa > 0.f ? ff_add(ff_log2(aa), ldx<CL>(P.alpha + (size_t)(T - 1) * V + v)) : FF{0.f, 0.f};
     for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) {
       if (aa > 0.f) a.lU0T[nxt][e] = f2_of(ff_sum(ff_of(a.snk_logR[e]), ff_neg(p)));
       else { a.lU0T[nxt][e] = a.lU0T[cur][e]; lost = 1; }
     }
   }
   __syncthreads();
-  *mism_out = block_sum(mism, red);
-  *res_out = block_sum(res, red);
-  const FF nlost = block_sum(FF{(float)(lost | (rg.bad ? 1 : 0)), 0.f}, red);
-  const float hi = block_max(rg.hi, redf);
-  const float inv_lo = block_max(rg.lo > 0.f ? 1.f / rg.lo : 0.f, redf);
+  *mism_out = part_sum<CL>(mism, red, a.cred, pt);
+  *res_out = part_sum<CL>(res, red, a.cred, pt);
+  const FF nlost = part_sum<CL>(FF{(float)(lost | (rg.bad ? 1 : 0)), 0.f}, red, a.cred, pt);
+  const float hi = part_max<CL>(rg.hi, redf, a.cred, pt);
+  const float inv_lo = part_max<CL>(rg.lo > 0.f ? 1.f / rg.lo : 0.f, redf, a.cred, pt);
   *drift = (hi > kDrift || inv_lo > kDrift) ? 1 : 0;
   return (nlost.h > 0.f || hi > kLost || inv_lo > kLost) ? 1 : 0;
 }
 
 // Duals in from the problem (init = 2), or the initialisation of Algorithm 2 (init = 1:
 // u_t = 1, U01 = U0T = 1 on the supports).  States without a capacity at t keep w = 1, nu = 0 in
-// both buffers.
-__device__ void load_duals(const LinArgs &a, const Ptrs &P, int cur, int init) {
-  const int S = a.S, T = a.T, n = (T - 2) * S;
+// both buffers.  Entries and boundary segments of the block's own nodes.
+__device__ void load_duals(const LinArgs &a, const Ptrs &P, const Part &pt, int cur, int init) {
+  const int S = a.S, T = a.T, nown = pt.in1 - pt.in0, n = (T - 2) * nown;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const int t = 2 + idx / S, k = idx - (t - 2) * S;
+    const int t = 2 + idx / nown, k = pt.in0 + idx - (t - 2) * nown;
     const size_t q = (size_t)t * S + k;
     const float2 ld = a.logd[(size_t)t * a.drs + k];
     float wv = 1.f;
@@ -688,18 +798,20 @@ __device__ void load_duals(const LinArgs &a, const Ptrs &P, int cur, int init) {
     P.nu[q] = nu;
     if (ld.x == INFINITY) P.w[cur ^ 1][q] = 1.f;
   }
-  for (int e = threadIdx.x; e < a.n_src; e += blockDim.x)
+  const int e0 = a.sseg_ptr[pt.s0], e1 = a.sseg_ptr[pt.s1];
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
     a.lU01[cur][e] = init == 2 ? split(a.p_src_logU[a.src_tri[e]]) : make_float2(0.f, 0.f);
-  for (int e = threadIdx.x; e < a.n_snk; e += blockDim.x)
+  const int f0 = a.zseg_ptr[pt.z0], f1 = a.zseg_ptr[pt.z1];
+  for (int e = f0 + threadIdx.x; e < f1; e += blockDim.x)
     a.lU0T[cur][e] = init == 2 ? split(a.p_snk_logU[a.snk_tri[e]]) : make_float2(0.f, 0.f);
   __syncthreads();
 }
 
 // Duals out to the problem: log2 u_t = nu + log2 w as a float-float pair; U01, U0T per triple.
-__device__ void store_duals(const LinArgs &a, const Ptrs &P, int cur) {
-  const int S = a.S, T = a.T, n = (T - 2) * S;
+__device__ void store_duals(const LinArgs &a, const Ptrs &P, const Part &pt, int cur) {
+  const int S = a.S, T = a.T, nown = pt.in1 - pt.in0, n = (T - 2) * nown;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const int t = 2 + idx / S, k = idx - (t - 2) * S;
+    const int t = 2 + idx / nown, k = pt.in0 + idx - (t - 2) * nown;
     const size_t q = (size_t)t * S + k;
     const float2 ld = a.logd[(size_t)t * a.drs + k];
     float2 lu = make_float2(0.f, 0.f);
@@ -715,37 +827,53 @@ __device__ void store_duals(const LinArgs &a, const Ptrs &P, int cur) {
     }
     a.p_logu[(size_t)t * S + a.in_state[k]] = lu;
   }
-  for (int e = threadIdx.x; e < a.n_src; e += blockDim.x) a.p_src_logU[a.src_tri[e]] = dbl(a.lU01[cur][e]);
-  for (int e = threadIdx.x; e < a.n_snk; e += blockDim.x) a.p_snk_logU[a.snk_tri[e]] = dbl(a.lU0T[cur][e]);
+  const int e0 = a.sseg_ptr[pt.s0], e1 = a.sseg_ptr[pt.s1];
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) a.p_src_logU[a.src_tri[e]] = dbl(a.lU01[cur][e]);
+  const int f0 = a.zseg_ptr[pt.z0], f1 = a.zseg_ptr[pt.z1];
+  for (int e = f0 + threadIdx.x; e < f1; e += blockDim.x) a.p_snk_logU[a.snk_tri[e]] = dbl(a.lU0T[cur][e]);
 }
 
 struct LinShared {
   LinArgs a;
   Ptrs P;
+  Part pt;
   float2 red[32];
   float redf[32];
 };
 
-// Up to max_passes passes on problem blockIdx.x, stopping at tol (tol < 0: never).  init: 0 =
-// continue the previous launch, 1 = initial duals, 2 = the problem's duals.  Every launch starts
-// with a scale sweep (it does not change the iterate).
-__global__ void __launch_bounds__(kLinThreads) k_linear(LinArgs *const *args, int max_passes, double tol, int init) {
+// Up to max_passes passes on one problem, stopping at tol (tol < 0: never).  init: 0 = continue
+// the previous launch, 1 = initial duals, 2 = the problem's duals.  Every launch starts with a
+// scale sweep (it does not change the iterate).  CL: the problem runs on a cluster of R blocks
+// (blockIdx.x / R is the problem, the rank in the cluster its part); otherwise on one block.
+template <bool CL>
+__global__ void __launch_bounds__(kLinThreads) k_linear(LinArgs *const *args, int max_passes, double tol, int init,
+                                                        int R) {
   __shared__ LinShared sh;
   extern __shared__ __align__(16) float dyn[];
-  LinArgs *g = args[blockIdx.x];
+  const int prob = CL ? blockIdx.x / R : blockIdx.x;
+  const int rank = CL ? blockIdx.x % R : 0;
+  LinArgs *g = args[prob];
   if (threadIdx.x == 0) sh.a = *g;
   __syncthreads();
   const LinArgs &a = sh.a;
+  // (uniform over the cluster: every block reads the same flag)
   if (init == 0 && a.done) {   // finished in an earlier launch: report no new passes
-    if (threadIdx.x == 0) { a.rep->passes = 0; a.rep->log_passes = 0; a.rep->rescalings = 0; }
+    if (threadIdx.x == 0 && rank == 0) { a.rep->passes = 0; a.rep->log_passes = 0; a.rep->rescalings = 0; }
     return;
   }
-  if (threadIdx.x == 0) sh.P = make_ptrs(a, dyn);
+  if (threadIdx.x == 0) {
+    if (CL) sh.a.mode = 0;         // a cluster keeps the per-entry arrays in global memory
+    sh.P = make_ptrs(sh.a, dyn);
+    if (CL) sh.P.rows = a.arow;    // the step rows are read across the cluster: in L2
+    sh.pt = make_part(a, rank, CL ? R : 1);
+  }
   __syncthreads();
   const Ptrs &P = sh.P;
+  Part pt = sh.pt;                 // per-thread copy: the reduction slot advances in every thread
   stage_in(a, P, init == 0);
   int cur = a.cur, need = 1;
-  if (init) load_duals(a, P, cur, init);
+  if (init) load_duals(a, P, pt, cur, init);
+  step_sync<CL>();
   int passes = 0, log_passes = 0, rescalings = 0, status = OTS_OK, converged = 0;
   const float tolf = (float)tol;
   FF mism{0.f, 0.f}, res{0.f, 0.f};
@@ -755,32 +883,32 @@ __global__ void __launch_bounds__(kLinThreads) k_linear(LinArgs *const *args, in
     if (log_run > 0) {
       // a problem whose duals keep leaving the range (e.g. they diverge, with no feasible flow)
       // runs in log arithmetic for a while before the linear form is tried again
-      status = log_sweep(a, P, cur, true, &mism, &res, sh.red);
+      status = log_sweep<CL>(a, P, pt, cur, true, &mism, &res, sh.red);
       cur ^= 1;
       ++log_passes;
       lost = 1;
       if (status) { ++passes; break; }
-      if (--log_run == 0) { rebuild(a, P, cur); ++rescalings; }
+      if (--log_run == 0) { rebuild<CL>(a, P, pt, cur); ++rescalings; }
     } else {
       if (need) {
-        status = log_sweep(a, P, cur, false, nullptr, nullptr, sh.red);
+        status = log_sweep<CL>(a, P, pt, cur, false, nullptr, nullptr, sh.red);
         if (status) break;
-        rebuild(a, P, cur);
+        rebuild<CL>(a, P, pt, cur);
         ++rescalings;
         need = 0;
       }
       int drift = 0;
-      lost = linear_pass(a, P, cur, &mism, &res, &drift, sh.red, sh.redf);
+      lost = linear_pass<CL>(a, P, pt, cur, &mism, &res, &drift, sh.red, sh.redf);
       if (lost) {
         // thrown away: the same pass again in log arithmetic, from the same duals; the next
         // 1, 2, 4, ... 64 passes too while the linear form keeps failing
-        status = log_sweep(a, P, cur, true, &mism, &res, sh.red);
+        status = log_sweep<CL>(a, P, pt, cur, true, &mism, &res, sh.red);
         cur ^= 1;
         ++log_passes;
         if (status) { ++passes; break; }
         log_run = backoff - 1;
         backoff = min(2 * backoff, 64);
-        if (log_run == 0) { rebuild(a, P, cur); ++rescalings; }
+        if (log_run == 0) { rebuild<CL>(a, P, pt, cur); ++rescalings; }
       } else {
         cur ^= 1;
         need = drift;
@@ -792,10 +920,10 @@ __global__ void __launch_bounds__(kLinThreads) k_linear(LinArgs *const *args, in
     if (!(srcf == srcf) || !(capf == capf)) { status = OTS_ERR_NUMERIC; break; }
     if (!lost && srcf <= tolf && capf <= tolf) { converged = 1; break; }
   }
-  __syncthreads();
-  store_duals(a, P, cur);
+  step_sync<CL>();
+  store_duals(a, P, pt, cur);
   stage_out(a, P);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && rank == 0) {
     g->cur = cur;
     g->done = converged || status != OTS_OK;
     LinReport r;
@@ -933,7 +1061,8 @@ ots_status linear_prepare(ots_problem *p) {
                o_zR = m.take(4 * std::max(nz, 1)), o_zlR = m.take(8 * std::max(nz, 1)), o_u01a = m.take(8 * std::max(ns, 1)),
                o_u01b = m.take(8 * std::max(ns, 1)), o_u0ta = m.take(8 * std::max(nz, 1)), o_u0tb = m.take(8 * std::max(nz, 1)),
                o_stri = m.take(4 * std::max(ns, 1)), o_ztri = m.take(4 * std::max(nz, 1)), o_args = m.take(sizeof(LinArgs)),
-               o_argp = m.take(sizeof(LinArgs *)), o_rep = m.take(sizeof(LinReport));
+               o_argp = m.take(sizeof(LinArgs *)), o_rep = m.take(sizeof(LinReport)),
+               o_arow = m.take(4 * 2 * (size_t)V), o_cred = m.take(8 * 4 * 16);
   std::unique_ptr<LinearData> L(new LinearData);
   L->arena = problem_alloc(p, m.off);
   if (!L->arena) return fail(OTS_ERR_OOM, "device allocation of %zu bytes failed", m.off);
@@ -959,6 +1088,7 @@ ots_status linear_prepare(ots_problem *p) {
   h.lU01[0] = (float2 *)at(o_u01a); h.lU01[1] = (float2 *)at(o_u01b); h.lU0T[0] = (float2 *)at(o_u0ta); h.lU0T[1] = (float2 *)at(o_u0tb);
   h.src_tri = (int *)at(o_stri); h.snk_tri = (int *)at(o_ztri);
   h.p_logu = p->d_logu; h.p_src_logU = p->src.d_tri_logU; h.p_snk_logU = p->snk.d_tri_logU;
+  h.arow = (float *)at(o_arow); h.cred = (float2 *)at(o_cred);
   L->d_rep = (LinReport *)at(o_rep);
   h.rep = L->d_rep;
   h.cur = 0; h.done = 0;
@@ -1027,17 +1157,35 @@ void linear_release(ots_problem *p) {
   p->lin = nullptr;
 }
 
+// Blocks per problem: one up to kLinClusterMin states (a cluster's barriers cost more than they
+// gain there: 0.40 against 0.32 ms per pass at 2800 states), else a cluster with about
+// kLinClusterStates state entries per block (at most 8 blocks, the portable cluster size).
+constexpr int kLinClusterMin = 4096;
+constexpr int kLinClusterStates = 2048;
+
+int linear_blocks_per_problem(int S) {
+  if (S <= kLinClusterMin) return 1;
+  int R = 1;
+  while (R < 8 && (long long)R * kLinClusterStates < S) R <<= 1;
+  return R;
+}
+
 ots_status linear_run(ots_problem *const *ps, int n, int max_passes, double tol, int init, double *kernel_ms) {
-  int smem = 0, smax = 0;
+  int smax = 0;
+  for (int i = 0; i < n; ++i) smax = std::max(smax, ps[i]->S);
+  const int R = linear_blocks_per_problem(smax);
+  int smem = 0;
   for (int i = 0; i < n; ++i) {
-    smem = std::max(smem, ps[i]->lin->smem);
-    smax = std::max(smax, ps[i]->S);
+    const LinArgs &h = ps[i]->lin->h;
+    smem = std::max(smem, R > 1 ? (int)(lin_layout(h.V, h.S, h.T, 0).words * 4) : ps[i]->lin->smem);
   }
   // threads per block: enough for one state entry each up to kLinThreads (small problems take
-  // fewer warps, so their barriers are cheaper)
-  const int threads = std::min(kLinThreads, std::max(64, (smax + 31) / 32 * 32));
-  if (smem > 48 * 1024)
-    OTS_CUDA(cudaFuncSetAttribute(k_linear, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  // fewer warps, so their barriers are cheaper); 256 per block of a cluster
+  const int threads = R > 1 ? 256 : std::min(kLinThreads, std::max(64, (smax + 31) / 32 * 32));
+  if (smem > 48 * 1024) {
+    OTS_CUDA(cudaFuncSetAttribute(k_linear<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    OTS_CUDA(cudaFuncSetAttribute(k_linear<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  }
   cudaStream_t s = ps[0]->stream;
   for (int i = 1; i < n; ++i) OTS_CUDA(cudaStreamSynchronize(ps[i]->stream));
   LinArgs **argp = ps[0]->lin->d_argp;
@@ -1052,8 +1200,25 @@ ots_status linear_run(ots_problem *const *ps, int n, int max_passes, double tol,
   OTS_CUDA(cudaEventCreate(&e0));
   OTS_CUDA(cudaEventCreate(&e1));
   OTS_CUDA(cudaEventRecord(e0, s));
-  k_linear<<<n, threads, smem, s>>>(argp, max_passes, tol, init);
-  cudaError_t le = cudaGetLastError();
+  cudaError_t le = cudaSuccess;
+  if (R == 1) {
+    k_linear<false><<<n, threads, smem, s>>>(argp, max_passes, tol, init, 1);
+    le = cudaGetLastError();
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n * R), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)R;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    le = cudaLaunchKernelEx(&cfg, k_linear<true>, argp, max_passes, tol, init, R);
+  }
   OTS_CUDA(cudaEventRecord(e1, s));
   for (int i = 0; i < n; ++i)
     OTS_CUDA(cudaMemcpyAsync(ps[i]->lin->h_rep, ps[i]->lin->d_rep, sizeof(LinReport), cudaMemcpyDeviceToHost, s));

@@ -144,11 +144,40 @@ def test_capacitated_rgg_l1(O, seed, n, T):
     O.ots_destroy_problem(h)
 
 
+@pytest.mark.parametrize("seed,n,T", [(22, 800, 20), (24, 700, 30)])
+def test_cluster_path(O, seed, n, T):
+    """Problems of more than 4096 states run on a cluster of blocks (node ranges per block, step
+    rows read across the cluster, cluster-wide sums): iterates after 3 passes and the fixed
+    point against the oracle."""
+    inst = c4_single(seed, n, T)
+    assert inst.n_states > 4096
+    o3, (src3, cap3, _) = oracle_after(inst, 3)
+    h = O.ots_create_problem(inst)
+    r = O.ots_linear_iterate(h, 3, reset=True)
+    lu, U01, U0T = O.ots_get_duals(h)
+    F3 = o3.flows()
+    carry = F3[1:-1] > 1e-6 * F3.max()
+    assert np.abs(lu - o3.get_duals()[0])[carry].max() <= 5e-6
+    assert np.abs(U01 - o3.get_duals()[1][0, inst.src_state]).max() <= 5e-6
+    assert r["cap_violation"] == pytest.approx(cap3, rel=1e-4, abs=1e-9)
+    elementwise(O.ots_get_flows(h), F3, f"cluster n={n}, 3 passes")
+    o = Oracle(inst)
+    assert o.solve(max_iters=200000, tol=1e-11)["status"] == 0
+    Fref = o.flows()
+    r = O.ots_linear_solve(h, tol=1e-8, max_iters=200000)
+    assert r["status"] == 0
+    F = O.ots_get_flows(h)
+    assert rel_l1(F, Fref) <= FLOW_TOL
+    elementwise(F, Fref, f"cluster n={n} T={T}")
+    O.ots_destroy_problem(h)
+
+
 def test_solve_many_matches_one_at_a_time(O):
     """Several L = 1 problems of different sizes in one launch: each result equals its own
     log-domain solve within the parity bound, and the oracle's."""
     insts = [c4_single(10 + s, n, T) for s, (n, T) in enumerate([(50, 10), (90, 25), (160, 17), (70, 33), (120, 20)])]
     insts.append(I.grid_single_commodity(4))
+    insts.append(c4_single(21, 800, 20))          # > 4096 states: the launch runs on clusters
     hs = [O.ots_create_problem(x) for x in insts]
     reps, st = O.ots_linear_solve_many(hs, tol=1e-8, max_iters=200000)
     assert all(r["status"] == 0 for r in reps)
