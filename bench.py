@@ -67,8 +67,8 @@ def parse():
                     help="profiling case only: the first N batched-workload instances, 3 graph launches of the "
                          "tick kernel, then exit (for ncu captures of k_batch_tick)")
     ap.add_argument("--profile-linear", type=int, default=0,
-                    help="profiling mode: this many linear-domain passes on the 5x5 grid and 20 on a 400-node "
-                         "single-commodity graph (two kernel launches), then exit")
+                    help="profiling mode: this many linear-domain passes on the 5x5 grid, 20 on a 400-node and 10 on a 2000-node "
+                         "single-commodity graph (three kernel launches), then exit")
     ap.add_argument("--profile-rgg", type=int, default=0,
                     help="profiling case only: 3 untimed full solves of the n=400 random-geometric workload, then N "
                          "solves between cudaProfilerStart/Stop (for ncu --profile-from-start off), then exit")
@@ -1005,9 +1005,10 @@ def profile_rgg(args):
 
 
 def profile_linear(args):
-    """Two launches of the linear-domain kernel for an ncu capture: the 5x5 grid (every array in
-    shared memory) for args.profile_linear passes, and a 400-node single-commodity random
-    geometric graph (T = 50, arrays in L2) for 20 passes."""
+    """Three launches of the linear-domain kernel for an ncu capture: the 5x5 grid (every array in
+    shared memory) for args.profile_linear passes, a 400-node single-commodity random geometric
+    graph (T = 50, arrays in L2, one block) for 20 passes, and a 2000-node one (T = 80, an 8-block
+    cluster) for 10 passes."""
     import torch
     from paper_2106_14485_gb300 import build, instances, ots
     build.build()
@@ -1020,6 +1021,10 @@ def profile_linear(args):
     r = instances.rgg_instance(seed=3, n=400, L=1, T=50, eps=0.01, cap_div=2.0, connect="bridge")
     h = ots.ots_create_problem(r)
     out["rgg400_L1"] = ots.ots_linear_iterate(h, 20, reset=True)
+    ots.ots_destroy_problem(h)
+    r = instances.rgg_instance(seed=3, n=2000, L=1, T=80, eps=0.01, cap_div=2.0, connect="bridge")
+    h = ots.ots_create_problem(r)
+    out["rgg2000_L1"] = ots.ots_linear_iterate(h, 10, reset=True)
     ots.ots_destroy_problem(h)
     torch.cuda.synchronize()
     print(json.dumps(out), flush=True)

@@ -192,6 +192,31 @@ def test_solve_many_matches_one_at_a_time(O):
         O.ots_destroy_problem(h)
 
 
+def test_time_varying_costs_and_closures(O):
+    """Per-interval state costs (Section 3.3, C_t) with moving edges closed (+inf) in single
+    intervals, on top of per-interval capacities: iterates and the fixed point against the oracle."""
+    inst = I.with_time_varying_costs(I.single_commodity_instance(seed=5, rows=6, cols=6, T=14), seed=3,
+                                     lo=0.5, hi=2.0, closures=6)
+    assert np.isinf(inst.state_cost_t).sum() >= 1
+    o3, _ = oracle_after(inst, 3)
+    h = O.ots_create_problem(inst)
+    O.ots_linear_iterate(h, 3, reset=True)
+    lu = O.ots_get_duals(h)[0]
+    F3 = o3.flows()
+    carry = F3[1:-1] > 1e-6 * F3.max()
+    assert np.abs(lu - o3.get_duals()[0])[carry].max() <= 5e-6
+    elementwise(O.ots_get_flows(h), F3, "time-varying, 3 passes")
+    o = Oracle(inst)
+    assert o.solve(max_iters=200000, tol=1e-12)["status"] == 0
+    Fref = o.flows()
+    r = O.ots_linear_solve(h, tol=1e-8, max_iters=200000)
+    assert r["status"] == 0
+    F = O.ots_get_flows(h)
+    assert rel_l1(F, Fref) <= FLOW_TOL
+    elementwise(F, Fref, "time-varying fixed point")
+    O.ots_destroy_problem(h)
+
+
 def test_warm_start_and_iterate_continue(O):
     """Passes split over calls (warm start from the problem's duals) give the iterate of one call,
     and a linear-domain solve from a log-domain iterate ends at the same fixed point."""
