@@ -1180,8 +1180,8 @@ ots_status linear_run(ots_problem *const *ps, int n, int max_passes, double tol,
     smem = std::max(smem, R > 1 ? (int)(lin_layout(h.V, h.S, h.T, 0).words * 4) : ps[i]->lin->smem);
   }
   // threads per block: enough for one state entry each up to kLinThreads (small problems take
-  // fewer warps, so their barriers are cheaper); 256 per block of a cluster
-  const int threads = R > 1 ? 256 : std::min(kLinThreads, std::max(64, (smax + 31) / 32 * 32));
+  // fewer warps, so their barriers are cheaper)
+  const int threads = R > 1 ? kLinThreads : std::min(kLinThreads, std::max(64, (smax + 31) / 32 * 32));
   if (smem > 48 * 1024) {
     OTS_CUDA(cudaFuncSetAttribute(k_linear<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     OTS_CUDA(cudaFuncSetAttribute(k_linear<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
