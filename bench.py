@@ -911,10 +911,19 @@ def run_ours(args):
     achieved = fb / (fwd_launch_ms * 1e-3) / 1e9
     bb = backward_bytes_per_launch(info, inst)
     bwd_launch_ms = float(np.mean(bwd_ms))
+    # the state-level bytes of one forward step (read hatPsi_t and Psi_t, write hatPsi_{t+1}, FP32 per
+    # state and commodity: 12 S L): what the step moves without the node-level factorisation
+    sl_bytes = 12 * info["n_states"] * inst.L
     roof = {"kernel": "k_forward (fused capacity update + node-level LSE message step)",
             "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "peak_source": peak_src, "traffic": measured_traffic(args.horizon), "bytes_per_launch": fb,
             "launch_ms": fwd_launch_ms,
+            "state_level_equivalent": {
+                "bytes_per_launch": sl_bytes, "achieved": sl_bytes / (fwd_launch_ms * 1e-3) / 1e9,
+                "frac": sl_bytes / (fwd_launch_ms * 1e-3) / 1e9 / hbm,
+                "note": "12 bytes per state and commodity per forward step, as the state-level step counts them; the "
+                        "node-level factorisation moves bytes_per_launch instead, so frac above (own bytes) is the "
+                        "kernel's roofline and this one the step's rate in the state-level method's bytes"},
             "backward": {"kernel": "k_backward", "achieved": bb / (bwd_launch_ms * 1e-3) / 1e9,
                          "frac": bb / (bwd_launch_ms * 1e-3) / 1e9 / hbm, "bytes_per_launch": bb,
                          "launch_ms": bwd_launch_ms}}
