@@ -61,6 +61,7 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(ots_server_desc), offsetof(ots_server_desc, mode),
          sizeof(ots_server_stats));
   printf("%zu\n", offsetof(ots_server_stats, batch_ticks));
+  printf("%zu %zu\n", sizeof(ots_linear_stats), offsetof(ots_linear_stats, kernel_ms));
   return 0;
 }
 '''
@@ -83,6 +84,8 @@ int main(void) {
     SD, SS = ots.ServerDesc, ots.ServerStats
     assert vals[14] == ctypes.sizeof(SD) and vals[15] == SD.mode.offset and vals[16] == ctypes.sizeof(SS)
     assert vals[17] == SS.batch_ticks.offset
+    LS = ots.LinearStats
+    assert vals[18] == ctypes.sizeof(LS) and vals[19] == LS.kernel_ms.offset
 
 
 def test_oracle_is_not_imported_by_the_product():
