@@ -1599,6 +1599,10 @@ ots_status ots_linear_iterate(ots_problem *p, int32_t n, int32_t reset, ots_solv
   auto t0 = std::chrono::steady_clock::now();
   ots_status st = linear_prepare(p);
   if (st) return st;
+  if (n == 0) {                     // nothing to run: an empty report
+    if (rep) *rep = ots_solve_report{};
+    return OTS_OK;
+  }
   std::vector<int> done;
   st = linear_phase(&p, 1, n, -1.0, reset ? 1 : 2, 0.0, t0, done, stats);
   if (st) return st;
@@ -1609,7 +1613,7 @@ ots_status ots_linear_iterate(ots_problem *p, int32_t n, int32_t reset, ots_solv
   r.cap_violation = lr.cap;
   r.dual_objective = NAN;
   r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  r.status = n > 0 ? lr.status : OTS_OK;
+  r.status = lr.status;
   if (r.status) fail((ots_status)r.status, "linear-domain pass failed (status %d)", r.status);
   if (rep) *rep = r;
   return (ots_status)r.status;
