@@ -42,6 +42,17 @@ struct MinBlocksFwd { static constexpr int value = G > 32 ? 512 / G : 2; };
 
 constexpr int kBatch = 6;   // in-states gathered per batch (grid nodes have 5)
 
+// Programmatic dependent launch: a step kernel launched with programmatic stream serialisation
+// may start while the previous step's grid finishes.  Before pdl_wait a kernel touches only
+// shared memory and data no kernel of the pass writes before it (static per-state data, or data
+// of the previous pass); pdl_wait returns once the previous grid has completed and its writes
+// are visible, and pdl_trigger then lets the next step's grid launch (its blocks take the SM
+// slots this grid's blocks free).  The next grid starts only after every block of this one has
+// triggered or exited, so its blocks never hold slots this grid still needs.  Both are no-ops
+// for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------------------------
 // forward step t (t = 2..T-1): capacity update of every state entering v, then A_t[v]
 //
@@ -56,6 +67,8 @@ __global__ void __launch_bounds__(BlockOf<G>::value, MinBlocksFwd<G>::value) k_f
   constexpr int NW = G > 32 ? G / 32 : 1;
   __shared__ float red[1];                   // unused: reductions above stay within a warp
   __shared__ float xch[2 * 2 * KB * NW];     // per-warp (max, sum) pairs, two batch buffers
+  pdl_wait();
+  pdl_trigger();
   const float lo_unit = a.qs.lo_unit;
   int batch = 0;
   const int g = threadIdx.x % G;
@@ -279,6 +292,8 @@ __global__ void __launch_bounds__(BlockOf<G>::value, MinBlocks<G>::value) k_back
   constexpr int BS = BlockOf<G>::value;
   constexpr int NPB = BS / G;
   constexpr int KB = kBatch;
+  pdl_wait();
+  pdl_trigger();
   const int g = threadIdx.x % G;
   const int v = blockIdx.x * NPB + threadIdx.x / G;
   if (v >= a.V) return;
@@ -717,7 +732,9 @@ __device__ __forceinline__ void producer_loop(const StepArgs &a, Meta *meta, flo
   const int lane = threadIdx.x & 31;
   TmaItem it;
   bool have = item_first(a.ptr, a.V, KB, it);
-  LaneMeta lm = load_lane_meta<FWD>(a, it, have, lane);
+  LaneMeta lm = load_lane_meta<FWD>(a, it, have, lane);   // static data or the previous pass's
+  pdl_wait();
+  pdl_trigger();
   for (int i = 0;; ++i) {
     const int s = i % NS;
     TmaItem nx = it;
@@ -867,6 +884,8 @@ __global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_forward_tma(c
     producer_loop<true, Lp, FwdMeta>(a, meta, st_hi, st_lo, full, empty, ROWS, timed_out);
   } else {
     // ---------------- consumers ----------------
+    pdl_wait();      // the outputs overwrite a panel the previous step may still read
+    pdl_trigger();
     const float lo_unit = a.qs.lo_unit;
     float M[CH][4], acc[CH][4];
 #pragma unroll
@@ -1071,6 +1090,8 @@ __global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_backward_tma(
   if (wid == NW) {
     producer_loop<false, Lp, BwdMeta>(a, meta, st_hi, st_lo, full, empty, ROWS, timed_out);
   } else {
+    pdl_wait();      // the outputs overwrite a panel the previous step may still read
+    pdl_trigger();
     const float lo_unit = a.qs.lo_unit;
     float M[CH][4], acc[CH][4];
 #pragma unroll
@@ -1121,14 +1142,30 @@ __global__ void __launch_bounds__(G + 32, G * CH == 256 ? 3 : 1) k_backward_tma(
 
 int nodes_per_block(int G) { return (G > 32 ? G : kBlock) / G; }
 
+// Launch with programmatic stream serialisation (see pdl_wait).
+template <typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(Args...), int grid, int block, size_t smem, cudaStream_t s,
+                              const StepArgs &a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3((unsigned)block, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 template <bool FWD, int G, int C, bool PC>
 static cudaError_t launch_step_t(const StepArgs &a, cudaStream_t s) {
   constexpr int BS = BlockOf<G>::value;
   const int npb = BS / G;
   const int grid = (a.V + npb - 1) / npb;
-  if (FWD) k_forward<G, C, PC><<<grid, BS, 0, s>>>(a);
-  else k_backward<G, C, PC><<<grid, BS, 0, s>>>(a);
-  return cudaGetLastError();
+  if (FWD) return launch_pdl(k_forward<G, C, PC>, grid, BS, 0, s, a);
+  return launch_pdl(k_backward<G, C, PC>, grid, BS, 0, s, a);
 }
 
 template <bool FWD, bool PC>
@@ -1149,9 +1186,8 @@ static size_t tma_smem(bool fwd) {
 
 template <int G, int CH>
 static cudaError_t launch_tma_t(bool fwd, const StepArgs &a, int grid, cudaStream_t s) {
-  if (fwd) k_forward_tma<G, CH><<<grid, G + 32, tma_smem<G, CH>(true), s>>>(a);
-  else k_backward_tma<G, CH><<<grid, G + 32, tma_smem<G, CH>(false), s>>>(a);
-  return cudaGetLastError();
+  if (fwd) return launch_pdl(k_forward_tma<G, CH>, grid, G + 32, tma_smem<G, CH>(true), s, a);
+  return launch_pdl(k_backward_tma<G, CH>, grid, G + 32, tma_smem<G, CH>(false), s, a);
 }
 
 template <int G, int CH>
