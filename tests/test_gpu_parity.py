@@ -204,6 +204,40 @@ def test_rgg400_iterates_and_converged(O):
     assert rel_l1(O.ots_get_flows(h), o2.flows()) <= FLOW_TOL
 
 
+def test_widest_rows_L4096(O):
+    """The largest commodity count the ABI takes (L = 4096: 256 threads per node row, four chunks
+    of 4 commodities per thread) with binding capacities: passes 1 and 3 from the initialisation
+    against the oracle's (aggregate flows, the pass measures, log u on flow-carrying states), and
+    every commodity's flows entry by entry where the oracle evaluates Theorem 6 at the GPU's duals."""
+    inst = I.rgg_instance(seed=41, n=30, L=4096, T=8, eps=0.05, cap_lo=0.05, cap_hi=0.15, connect="bridge")
+    h = O.ots_create_problem(inst)
+    st = O.ots_problem_info(h)
+    assert st["padded_L"] == 4096 and st["threads_per_node"] == 256
+    o = Oracle(inst)
+    o.backward_sweep()
+    done = 0
+    for target in (1, 3):
+        n = target - done
+        r = O.ots_iterate(h, n, reset=(done == 0))
+        for _ in range(n):
+            ro, co, _ = o.iteration()
+        done = target
+        Fo = o.flows()
+        assert rel_l1(O.ots_get_flows(h), Fo) <= FLOW_TOL, target
+        assert abs(r["src_residual"] - ro) <= 1e-6 + 1e-4 * ro
+        assert abs(r["cap_violation"] - co) <= 1e-6 + 1e-4 * co
+    lu, U01, U0T = O.ots_get_duals(h)
+    logu_ref = o.get_duals()[0]
+    carry = Fo[1:-1] > 1e-6 * Fo.max()
+    assert (logu_ref[carry] < -1e-3).any(), "capacities should bind"
+    assert np.abs(lu - logu_ref)[carry].max() <= 1e-5
+    od = Oracle(inst)
+    od.set_duals(lu, *dense_duals(inst, U01, U0T))
+    e = assert_elementwise(O.ots_get_commodity_flows(h), od.projections(), "L=4096 per commodity at the GPU's duals")
+    print(f"L=4096: worst entry {e:.3g} of the bound")
+    O.ots_destroy_problem(h)
+
+
 def test_dual_objective_matches_and_increases(O):
     """Dual objective of Theorem 3 after each pass equals the oracle's and does not decrease
     (block-coordinate ascent, proof of Proposition 5)."""
