@@ -63,7 +63,6 @@ struct LinArgs {
   const int *src_tri, *snk_tri;      // entry -> boundary triple of the problem
   float2 *p_logu;                    // problem's log2 u_t [(T+1) S] by state (float-float)
   double *p_src_logU, *p_snk_logU;   // problem's log2 U01 / U0T per triple
-  float *arow;                       // [2 V] step rows of a problem on a cluster (read across its blocks)
   float2 *cred;                      // [4][16] cluster reduction slots
   LinReport *rep;
   int cur, done;                     // state kept between launches
@@ -272,6 +271,7 @@ struct Part {
   int rank, R;
   int v0, v1, in0, in1, out0, out1, s0, s1, z0, z1;
   int slot;                          // next reduction slot (cluster)
+  const int *vb;                     // [9] first node of every rank (vb[R] = V), in shared memory
 };
 
 __device__ int first_node_at(const int *ptr, int V, int target) {   // smallest v with ptr[v] >= target
@@ -294,14 +294,17 @@ __device__ int first_seg_at(const int *node, int n, int v) {        // first seg
   return lo;
 }
 
-__device__ Part make_part(const LinArgs &a, int rank, int R) {
+__device__ Part make_part(const LinArgs &a, int rank, int R, int *vb) {
   Part p;
   p.rank = rank;
   p.R = R;
   p.slot = 0;
   const long long S = a.S;
-  p.v0 = rank == 0 ? 0 : first_node_at(a.in_ptr, a.V, (int)(S * rank / R));
-  p.v1 = rank == R - 1 ? a.V : first_node_at(a.in_ptr, a.V, (int)(S * (rank + 1) / R));
+  for (int r = 0; r <= 8; ++r)
+    vb[r] = r == 0 ? 0 : (r >= R ? a.V : first_node_at(a.in_ptr, a.V, (int)(S * r / R)));
+  p.vb = vb;
+  p.v0 = vb[rank];
+  p.v1 = vb[rank + 1];
   p.in0 = a.in_ptr[p.v0];
   p.in1 = a.in_ptr[p.v1];
   p.out0 = a.out_ptr[p.v0];
@@ -329,6 +332,26 @@ template <bool CL, typename X>
 __device__ __forceinline__ X ldx(const X *p) {
   if constexpr (CL) return __ldcg(p);
   else return *p;
+}
+
+// Value of node x in a step row.  On a cluster every block keeps a whole row array in its shared
+// memory but writes only the entries of its own nodes; the entry of node x is read from the shared
+// memory of the block that owns x (distributed shared memory, same offset in every block).
+template <bool CL>
+__device__ __forceinline__ float ld_row(const float *rows, int x, const Part &pt) {
+  if constexpr (!CL) {
+    return rows[x];
+  } else {
+    int r = 0;
+#pragma unroll
+    for (int k = 1; k < 8; ++k) r += (k < pt.R && x >= pt.vb[k]) ? 1 : 0;
+    const uint32_t la = (uint32_t)__cvta_generic_to_shared(rows + x);
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(r));
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
+    return v;
+  }
 }
 
 // Sum / maximum over the whole problem: the block's value, then (cluster) every block adds the R
@@ -456,7 +479,7 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, Part &pt, int cur, boo
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
-        if (k < pt.out1) c[k] = ldx<CL>(rp + hd[j]) + kap[j].x + log2_u(ld[j], wv[j], nu[j]);
+        if (k < pt.out1) c[k] = ld_row<CL>(rp, hd[j], pt) + kap[j].x + log2_u(ld[j], wv[j], nu[j]);
       }
     }
     __syncthreads();
@@ -517,7 +540,7 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, Part &pt, int cur, boo
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
         if (k >= pt.in1) continue;
-        const float al = ldx<CL>(rp + ti[j]);
+        const float al = ld_row<CL>(rp, ti[j], pt);
         float lu = log2_u(ld[j], wv[j], nu[j]);
         if (update && ld[j].x != INFINITY) {
           const float ls = al + ldx<CL>(P.beta + (size_t)(t + 1) * V + hi[j]) + kap[j].x;
@@ -546,7 +569,7 @@ __device__ int log_sweep(const LinArgs &a, const Ptrs &P, Part &pt, int cur, boo
   // sink update U0T <- R0T / hatPsi_T
   if (update) {
     for (int s = pt.z0 + threadIdx.x; s < pt.z1; s += nt) {
-      const double p = (double)ldx<CL>(rp + a.zseg_node[s]);
+      const double p = (double)rp[a.zseg_node[s]];   // own node
       for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) {
         if (!(p > -INFINITY)) { bad = 1; a.lU0T[nxt][e] = a.lU0T[cur][e]; continue; }
         a.lU0T[nxt][e] = split(dbl(a.snk_logR[e]) - p);
@@ -660,7 +683,7 @@ __device__ int linear_pass(const LinArgs &a, const Ptrs &P, Part &pt, int cur, F
 #pragma unroll
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
-        if (k < pt.out1) c[k] = ldx<CL>(rp + hd[j]) * g[j];
+        if (k < pt.out1) c[k] = ld_row<CL>(rp, hd[j], pt) * g[j];
       }
     }
     __syncthreads();
@@ -680,7 +703,7 @@ __device__ int linear_pass(const LinArgs &a, const Ptrs &P, Part &pt, int cur, F
   __syncthreads();
   for (int s = pt.s0 + threadIdx.x; s < pt.s1; s += nt) {
     const int v = a.sseg_node[s];
-    const float bb = ldx<CL>(rp + v);
+    const float bb = rp[v];   // own node
     const FF p1 = bb > 0.f ? ff_add(ff_log2(bb), ldx<CL>(P.beta + (size_t)2 * V + v)) : FF{0.f, 0.f};
     const float sc = ldx<CL>(P.alpha + (size_t)V + v);
     float acc = 0.f;
@@ -728,7 +751,7 @@ __device__ int linear_pass(const LinArgs &a, const Ptrs &P, Part &pt, int cur, F
       for (int j = 0; j < kBatch; ++j) {
         const int k = k0 + j * nt;
         if (k >= pt.in1) continue;
-        const float a0 = ldx<CL>(rp + ti[j]);
+        const float a0 = ld_row<CL>(rp, ti[j], pt);
         float g = gf[j];
         if (dc[j] != INFINITY) {
           const float x = a0 * ldx<CL>(bn + hi[j]);
@@ -757,7 +780,7 @@ __device__ int linear_pass(const LinArgs &a, const Ptrs &P, Part &pt, int cur, F
   // rp = a_{T-1}.  Sink update U0T <- R0T / hatPsi_T
   for (int s = pt.z0 + threadIdx.x; s < pt.z1; s += nt) {
     const int v = a.zseg_node[s];
-    const float aa = ldx<CL>(rp + v);
+    const float aa = rp[v];   // own node
     const FF p = aa > 0.f ? ff_add(ff_log2(aa), ldx<CL>(P.alpha + (size_t)(T - 1) * V + v)) : FF{0.f, 0.f};
     for (int e = a.zseg_ptr[s]; e < a.zseg_ptr[s + 1]; ++e) {
       if (aa > 0.f) a.lU0T[nxt][e] = f2_of(ff_sum(ff_of(a.snk_logR[e]), ff_neg(p)));
@@ -837,6 +860,7 @@ struct LinShared {
   LinArgs a;
   Ptrs P;
   Part pt;
+  int vb[9];
   float2 red[32];
   float redf[32];
 };
@@ -864,8 +888,7 @@ __global__ void __launch_bounds__(kLinThreads) k_linear(LinArgs *const *args, in
   if (threadIdx.x == 0) {
     if (CL) sh.a.mode = 0;         // a cluster keeps the per-entry arrays in global memory
     sh.P = make_ptrs(sh.a, dyn);
-    if (CL) sh.P.rows = a.arow;    // the step rows are read across the cluster: in L2
-    sh.pt = make_part(a, rank, CL ? R : 1);
+    sh.pt = make_part(a, rank, CL ? R : 1, sh.vb);
   }
   __syncthreads();
   const Ptrs &P = sh.P;
@@ -1062,7 +1085,7 @@ ots_status linear_prepare(ots_problem *p) {
                o_u01b = m.take(8 * std::max(ns, 1)), o_u0ta = m.take(8 * std::max(nz, 1)), o_u0tb = m.take(8 * std::max(nz, 1)),
                o_stri = m.take(4 * std::max(ns, 1)), o_ztri = m.take(4 * std::max(nz, 1)), o_args = m.take(sizeof(LinArgs)),
                o_argp = m.take(sizeof(LinArgs *)), o_rep = m.take(sizeof(LinReport)),
-               o_arow = m.take(4 * 2 * (size_t)V), o_cred = m.take(8 * 4 * 16);
+               o_cred = m.take(8 * 4 * 16);
   std::unique_ptr<LinearData> L(new LinearData);
   L->arena = problem_alloc(p, m.off);
   if (!L->arena) return fail(OTS_ERR_OOM, "device allocation of %zu bytes failed", m.off);
@@ -1088,7 +1111,7 @@ ots_status linear_prepare(ots_problem *p) {
   h.lU01[0] = (float2 *)at(o_u01a); h.lU01[1] = (float2 *)at(o_u01b); h.lU0T[0] = (float2 *)at(o_u0ta); h.lU0T[1] = (float2 *)at(o_u0tb);
   h.src_tri = (int *)at(o_stri); h.snk_tri = (int *)at(o_ztri);
   h.p_logu = p->d_logu; h.p_src_logU = p->src.d_tri_logU; h.p_snk_logU = p->snk.d_tri_logU;
-  h.arow = (float *)at(o_arow); h.cred = (float2 *)at(o_cred);
+  h.cred = (float2 *)at(o_cred);
   L->d_rep = (LinReport *)at(o_rep);
   h.rep = L->d_rep;
   h.cur = 0; h.done = 0;
