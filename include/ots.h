@@ -290,8 +290,11 @@ typedef struct ots_linear_stats {
  * whenever a scaled value drifts out of [2^-30, 2^30]; a pass whose values leave [2^-60, 2^60]
  * is run again in log arithmetic.  So the iteration is Algorithm 2's at any epsilon; the linear
  * form pays off while rescalings are rare (epsilon not far below the cost differences that the
- * duals move by per pass).  One thread block runs whole passes of one problem (two message rows
- * of n_nodes floats in shared memory: n_nodes <= 16384).  Applies to problems with L = 1, state
+ * duals move by per pass).  One thread block runs whole passes of one problem, or a cluster of up
+ * to 8 blocks above 4096 states; every block holds two message rows of n_nodes floats and one
+ * float per state in shared memory, so 4 (2 n_nodes + n_states) bytes must not exceed 200 KB
+ * (about 5600 nodes on a road graph; larger problems give OTS_ERR_INVALID_ARG and stay on the
+ * log-domain path).  Applies to problems with L = 1, state
  * costs (also per interval) and capacities (also per interval); explicit state graphs, commodity
  * windows, per-commodity costs or capacities and batch members give OTS_ERR_INVALID_ARG.
  * The problem's device memory grows by about 36 bytes per state and interval on first use.
