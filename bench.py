@@ -682,7 +682,7 @@ def bench_single(args, ots, torch, local):
         for arm in ("linear", "log_domain"):
             for rep in range(2):                       # the first is a warm-up
                 torch.cuda.synchronize()
-                t0 = time.perf_counter()
+                ta = time.perf_counter()
                 hx = ots.ots_create_problem(x, device=local)
                 if arm == "linear":
                     rr = ots.ots_linear_solve(hx, tol=args.tol, max_iters=mp, raise_on_error=False)
@@ -690,7 +690,7 @@ def bench_single(args, ots, torch, local):
                     rr = ots.ots_sinkhorn_solve(hx, tol=args.tol, max_iters=mp, check_every=1, raise_on_error=False)
                 ots.ots_get_flows(hx)
                 ots.ots_destroy_problem(hx)
-                times[arm] = (time.perf_counter() - t0, rr["iterations"], rr["status"])
+                times[arm] = (time.perf_counter() - ta, rr["iterations"], rr["status"])
         alone = {"member": x.name, "states": x.n_states, "T": x.T,
                  **{arm: {"seconds": t, "passes": it, "status": stt,
                           "updates_per_s": it * x.n_updates_per_iteration() / t} for arm, (t, it, stt) in times.items()}}
