@@ -1,5 +1,6 @@
 // ots_linear.cu -- the single-commodity problem (L = 1, Section 4.2) with FP32 messages in
-// the linear domain, one thread block per problem for whole runs of passes.
+// the linear domain, one thread block per problem (a cluster of up to 8 blocks for problems of
+// more than 4096 states) for whole runs of passes.
 //
 // Algorithm 1 works with the messages themselves (products of K and the duals), not their
 // logarithms; Algorithm 2 at L = 1 is the same iteration (the boundary duals absorb the costs of
@@ -19,7 +20,7 @@
 //   capacity   w_t(i) <- min(Dc_t(i) / (a_{t-1}[tail i] b_{t+1}[head i]), 2^-nu_t(i))
 //   forward    a_t[v] = sum_{head i = v} a_{t-1}[tail i] w_t(i) Gf_t(i)
 // (the capacity update is u_t <- min(d_t / P_t(u_t = 1), 1) of Algorithm 2, written in the scaled
-// quantities).  The boundary duals stay FP64 base-2 logarithms: U01 <- R01 / Psi_1 with
+// quantities).  The boundary duals stay float-float base-2 logarithms: U01 <- R01 / Psi_1 with
 // Psi_1(i) = B_2[head i], U0T <- R0T / hatPsi_T with hatPsi_T(j) = A_{T-1}[tail j].
 //
 // The scales are taken from the messages themselves by a sweep in FP32 log arithmetic at the
@@ -28,7 +29,14 @@
 // run again in FP32 log arithmetic (with updates), which re-takes the scales; one that stays
 // inside but leaves [2^-30, 2^30] re-takes them before the next pass.  The measures are those
 // of Algorithm 2 (relative source mismatch before the U01 update, capacity residual
-// sum |P_t after - P_t before|), summed per block in a fixed order.
+// sum |P_t after - P_t before|), summed in float-float in a fixed order.
+//
+// A step is two phases: one thread per state entry forms its term, then one thread per node adds
+// its entries' terms from shared memory.  On a cluster every block owns a node range and the
+// state entries of those nodes, keeps the step rows in its shared memory (its own nodes' entries
+// written, the others read from the owning block through distributed shared memory), and the
+// blocks meet at a cluster barrier between steps; every block takes the same decisions from sums
+// that all of them add in rank order.
 #include <cuda_runtime.h>
 
 #include <cfloat>
